@@ -1,0 +1,412 @@
+"""Plain FP64 CPU oracle for one imaginary-time step of the superposition-of-
+Gaussian-states (SGS) variational method (Boutin & Bauer, arXiv:2105.01088).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously-correct
+reference against which the CUDA path is checked.  Only the test-suite, the
+package smoke check and the CPU-baseline leg of the benchmark may import it;
+the product path never does, and the CUDA path shares no code with it.
+
+Everything is numpy float64 / complex128.  Library primitives used as single
+steps: ``numpy.linalg.slogdet`` (log|det|), ``numpy.linalg.solve`` (a linear
+solve), ``numpy.linalg.eigh`` (Hermitian eigen-decomposition),
+``scipy.linalg.expm`` (matrix exponential).  The Pfaffian is written out here
+(Parlett-Reid elimination with pivoting), as the paper's PFAPACK is not used.
+
+Conventions (the paper fixes none of these; each is a stated reading):
+  * Majoranas c_{2m}, c_{2m+1} of fermion mode m (0-based) are
+    a_m + a_m^dag and -i(a_m - a_m^dag); the vacuum then has Gamma = J,
+    J = (+)_m [[0, 1], [-1, 0]], and the parity of a Gaussian state is Pf(Gamma).
+  * Mode order is site-major, spin-minor: mode 2s+sigma, impurity site s=0.
+  * The gauge reference state of Sec. II B is the first ansatz state, phi_0.
+  * Eq. (EOM-Gamma3) is used with lambda-tilde_mu conjugated (as in
+    Eq. (EOM-Gamma2)), and with its last term summed through h lambda = E G
+    lambda (Eq. eigLambda), so the bracket ends in -(h_mu,beta - E G_mu,beta)
+    Delta^{beta,mu}.
+  * The orthogonal step of App. A (Eq. ExpStep) uses
+    R = exp{(ds/4)[Gamma, dGamma]}, which agrees with the Euler step
+    Gamma + ds dGamma (Eq. RKstep) to first order in ds.
+
+Parity pins (tests/test_oracle_pins.py): every function here is checked
+against explicit Fock-space vectors, exact diagonalisation, the U=0 closed
+form or a paper-stated identity; none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+import scipy.linalg
+
+# ---------------------------------------------------------------------------
+# Model: fermion Hamiltonian -> Majorana form (Sec. II A; Sec. IV Eqs. for
+# H_0, H_I; Sec. V two-channel geometry)
+# ---------------------------------------------------------------------------
+
+
+class MajoranaModel:
+    """H = e_const + i sum_kl A_kl c_k c_l + sum_klpq U_klpq c_k c_l c_p c_q.
+
+    ``A`` is the real skew 2N x 2N matrix of Sec. II A.  The quartic tensor is
+    kept as its non-zero antisymmetrised entries: ``quartic`` is a list of
+    ((k, l, p, q), value) with the value of U_klpq for every ordering of each
+    monomial's four distinct indices (Sec. II A: U is skew under exchange of
+    neighbouring indices, hence fully antisymmetric).
+    """
+
+    def __init__(self, A, quartic, e_const):
+        self.A = np.asarray(A, dtype=np.float64)
+        self.quartic = list(quartic)
+        self.e_const = float(e_const)
+        self.n = self.A.shape[0]
+        self.N = self.n // 2
+
+
+def _perm_sign(p):
+    s = 1
+    p = list(p)
+    for i in range(len(p)):
+        for j in range(i + 1, len(p)):
+            if p[i] > p[j]:
+                s = -s
+    return s
+
+
+def antisymmetrise_monomials(monomials):
+    """Turn monomials v * c_k c_l c_p c_q (distinct k,l,p,q) into the fully
+    antisymmetric U of Sec. II A: U_{pi(klpq)} = sgn(pi) v / 24, so that
+    sum over all orderings reproduces v c_k c_l c_p c_q."""
+    out = {}
+    for idx, v in monomials:
+        assert len(set(idx)) == 4, "quartic monomial needs four distinct Majoranas"
+        for perm in itertools.permutations(range(4)):
+            key = tuple(idx[i] for i in perm)
+            out[key] = out.get(key, 0.0) + _perm_sign(perm) * v / 24.0
+    return [(k, v) for k, v in out.items() if v != 0.0]
+
+
+def majorana_from_fermions(h_sp, hubbard):
+    """Quadratic fermion part sum_ij h_ij a_i^dag a_j (h real symmetric) and
+    Hubbard terms U n_a n_b (list of (a, b, U), a != b) -> MajoranaModel.
+
+    With a_m = (c_{2m} + i c_{2m+1})/2:
+      sum_ij h_ij a_i^dag a_j = tr(h)/2 + (i/2) sum_ij h_ij c_{2i} c_{2j+1},
+    i.e. A_{2i,2j+1} = h_ij / 4 = -A_{2j+1,2i}.  With n_m = (1 + i c_{2m}
+    c_{2m+1})/2, U n_a n_b = U/4 + (U/4)(i c c)_a + (U/4)(i c c)_b
+    - (U/4) c_{2a} c_{2a+1} c_{2b} c_{2b+1}.
+    """
+    h_sp = np.asarray(h_sp, dtype=np.float64)
+    nm = h_sp.shape[0]
+    n = 2 * nm
+    A = np.zeros((n, n))
+    e_const = 0.5 * np.trace(h_sp)
+    for i in range(nm):
+        for j in range(nm):
+            if h_sp[i, j] != 0.0:
+                A[2 * i, 2 * j + 1] += h_sp[i, j] / 4.0
+                A[2 * j + 1, 2 * i] -= h_sp[i, j] / 4.0
+    monomials = []
+    for a, b, U in hubbard:
+        e_const += U / 4.0
+        for m in (a, b):
+            A[2 * m, 2 * m + 1] += U / 8.0
+            A[2 * m + 1, 2 * m] -= U / 8.0
+        monomials.append(((2 * a, 2 * a + 1, 2 * b, 2 * b + 1), -U / 4.0))
+    return MajoranaModel(A, antisymmetrise_monomials(monomials), e_const)
+
+
+def anderson_chain(n_bath, U, eps_d, V, t=1.0, mu=0.0, n_channels=1):
+    """Single-impurity Anderson model of Sec. IV (H_0 + H_I), generalised to
+    ``n_channels`` independent open bath chains of ``n_bath`` sites each,
+    every chain's first site hybridised with the impurity by V (= t').
+
+    Site order: impurity s=0, then the chains interleaved by channel
+    (channel c, chain site r = 1..n_bath -> s = 1 + (r-1)*n_channels + c),
+    so "impurity + first k chain sites of every channel" is a leading block.
+    Mode 2s + sigma.  Returns (h_sp, hubbard) for majorana_from_fermions.
+    """
+    n_sites = 1 + n_channels * n_bath
+    nm = 2 * n_sites
+    h = np.zeros((nm, nm))
+
+    def site(c, r):
+        return 1 + (r - 1) * n_channels + c
+
+    for sigma in range(2):
+        h[sigma, sigma] = eps_d
+        for c in range(n_channels):
+            a, b = 0, site(c, 1)
+            h[2 * a + sigma, 2 * b + sigma] = h[2 * b + sigma, 2 * a + sigma] = -V
+            for r in range(1, n_bath + 1):
+                s = site(c, r)
+                h[2 * s + sigma, 2 * s + sigma] = -mu
+                if r >= 2:
+                    p = site(c, r - 1)
+                    h[2 * p + sigma, 2 * s + sigma] = h[2 * s + sigma, 2 * p + sigma] = -t
+    return h, [(0, 1, U)]
+
+
+def anderson_model(n_bath, U, eps_d, V, t=1.0, mu=0.0, n_channels=1):
+    return majorana_from_fermions(*anderson_chain(n_bath, U, eps_d, V, t, mu, n_channels))
+
+
+# ---------------------------------------------------------------------------
+# Pfaffian (the paper computes Pfaffians with PFAPACK; this is a plain
+# Parlett-Reid elimination with partial pivoting)
+# ---------------------------------------------------------------------------
+
+
+def pfaffian_log(A):
+    """Return (phase, log|Pf A|) of a real or complex skew matrix A, with
+    Pf A = phase * exp(log|Pf A|).  phase is +-1 for real A.  A zero pivot
+    returns (0, -inf)."""
+    A = np.array(A, dtype=np.complex128 if np.iscomplexobj(A) else np.float64)
+    n = A.shape[0]
+    if n % 2:
+        return 0.0, -math.inf
+    phase = 1.0 + 0.0j if np.iscomplexobj(A) else 1.0
+    logabs = 0.0
+    for k in range(0, n - 1, 2):
+        # pivot: largest entry of column k below the diagonal
+        p = k + 1 + int(np.argmax(np.abs(A[k + 1:, k])))
+        if p != k + 1:
+            A[[k + 1, p], :] = A[[p, k + 1], :]
+            A[:, [k + 1, p]] = A[:, [p, k + 1]]
+            phase = -phase
+        piv = A[k, k + 1]
+        if piv == 0:
+            return 0.0, -math.inf
+        logabs += math.log(abs(piv))
+        phase = phase * (piv / abs(piv))
+        if k + 2 < n:
+            tau = A[k, k + 2:] / piv
+            u = A[k + 2:, k + 1].copy()
+            A[k + 2:, k + 2:] += np.outer(tau, u) - np.outer(u, tau)
+    return phase, logabs
+
+
+def pfaffian(A):
+    ph, la = pfaffian_log(A)
+    return ph * math.exp(la) if la > -math.inf else 0.0 * ph
+
+
+# ---------------------------------------------------------------------------
+# Pair quantities (Sec. II B-C, Sec. III B)
+# ---------------------------------------------------------------------------
+
+
+def log_overlap_magnitude(Ga, Gb):
+    """log |<phi_a|phi_b>| from |<phi_a|phi_b>|^2 = 2^-N |Pf(Ga + Gb)|
+    (overlap magnitude of Gaussian states, Sec. II B, following the paper's
+    Ref. [Bravyi2017]); |Pf S| = |det S|^(1/2)."""
+    N = Ga.shape[0] // 2
+    sign, logdet = np.linalg.slogdet(Ga + Gb)
+    if sign == 0:
+        return -math.inf
+    return 0.5 * (-N * math.log(2.0) + 0.5 * logdet)
+
+
+def transition_matrix(Ga, Gb):
+    """Delta^{a,b} = [i(Ga - Gb) - 2](Ga + Gb)^{-1}  (Eq. def-delta-matrix),
+    so that <phi_b| c_k c_l |phi_a> = i G_{b,a} Delta^{a,b}_kl for k != l."""
+    n = Ga.shape[0]
+    S = Ga + Gb
+    rhs = 1j * (Ga - Gb) - 2.0 * np.eye(n)
+    # X S = rhs  <=>  S^T X^T = rhs^T
+    return np.linalg.solve(S.T, rhs.T).T
+
+
+def wick_energy_density(model, Dlt):
+    """<phi_b|H|phi_a> / <phi_b|phi_a> for the transition matrix Delta^{a,b}:
+    e_const + Tr(A Delta) - 3 sum_klpq U_klpq Delta_kl Delta_pq.
+    (Generalised Wick theorem of Sec. III B: two-point elements i Delta_kl,
+    four-point elements the Pfaffian of the 4x4 sub-block of i Delta.)"""
+    e = model.e_const + np.sum(model.A * Dlt.T)
+    q = 0.0
+    for (k, l, p, r), v in model.quartic:
+        q += v * Dlt[k, l] * Dlt[p, r]
+    return e - 3.0 * q
+
+
+def fock_matrix(model, Dlt):
+    """Generalised Fock matrix F^{a,b}_kl = A_kl + 6 sum_mn U_klmn Delta^{a,b}_mn
+    (Sec. III B)."""
+    F = model.A.astype(np.complex128 if np.iscomplexobj(Dlt) else np.float64).copy()
+    for (k, l, m, r), v in model.quartic:
+        F[k, l] += 6.0 * v * Dlt[m, r]
+    return F
+
+
+def gram_and_hamiltonian(model, gammas):
+    """Gram matrix G_ab = <phi_a|phi_b> and h_ab = <phi_a|H|phi_b> (Sec. II C,
+    Eq. eigLambda) in the gauge of Sec. II B with reference phi_0 = the first
+    state: <phi_0|phi_mu> real and positive.
+
+    Magnitude: |G_ab| from the Pfaffian of Ga + Gb.  Phase: the Bargmann
+    product <phi_0|phi_a><phi_a|phi_b><phi_b|phi_0> equals
+    |G_ab|^2 2^-N Pf(G0) Pf(G0 + Delta^{a,b}) (the trace of the reference
+    projector against the transition operator |a><b|/<b|a>, whose two-point
+    function is Delta^{a,b}); with <phi_0|phi_a>, <phi_b|phi_0> > 0 its phase
+    is the phase of G_ab.
+    """
+    M = len(gammas)
+    n = model.n
+    N = n // 2
+    G = np.zeros((M, M), dtype=np.complex128)
+    h = np.zeros((M, M), dtype=np.complex128)
+    logmag = np.zeros((M, M))
+    for a in range(M):
+        for b in range(M):
+            logmag[a, b] = 0.0 if a == b else log_overlap_magnitude(gammas[a], gammas[b])
+    pf0, _ = pfaffian_log(gammas[0])
+    for a in range(M):
+        G[a, a] = 1.0
+        h[a, a] = wick_energy_density(model, gammas[a])
+        for b in range(a + 1, M):
+            Dab = transition_matrix(gammas[a], gammas[b])
+            mag = math.exp(logmag[a, b])
+            if a == 0:
+                g = mag + 0.0j
+            else:
+                ph, _ = pfaffian_log(gammas[0] + Dab)
+                ph = ph * pf0
+                g = mag * ph / abs(ph)
+            G[a, b] = g
+            G[b, a] = np.conj(g)
+            # h_ba = <phi_b|H|phi_a> = G_ba * (Wick with Delta^{a,b})
+            h[b, a] = G[b, a] * wick_energy_density(model, Dab)
+            h[a, b] = np.conj(h[b, a])
+    return G, h
+
+
+# ---------------------------------------------------------------------------
+# Amplitudes (Eq. eigLambda)
+# ---------------------------------------------------------------------------
+
+
+def solve_amplitudes(G, h, rel_cut=1e-12):
+    """Lowest solution of h lambda = E G lambda by canonical orthogonalisation:
+    diagonalise G, keep eigenvalues above rel_cut * max, solve the ordinary
+    Hermitian problem in that basis.  lambda is normalised to lambda^dag G
+    lambda = 1 and its global phase set so the largest |lambda_mu| is real
+    and positive.  Returns (E, lambda)."""
+    w, U = np.linalg.eigh(G)
+    keep = w > rel_cut * w.max()
+    X = U[:, keep] / np.sqrt(w[keep])
+    Hp = X.conj().T @ h @ X
+    Hp = 0.5 * (Hp + Hp.conj().T)
+    e, V = np.linalg.eigh(Hp)
+    lam = X @ V[:, 0]
+    lam = lam / math.sqrt(np.real(lam.conj() @ G @ lam))
+    j = int(np.argmax(np.abs(lam)))
+    lam = lam * (abs(lam[j]) / lam[j])
+    return float(e[0]), lam
+
+
+# ---------------------------------------------------------------------------
+# Equation of motion (Sec. III A-B)
+# ---------------------------------------------------------------------------
+
+C_INVERSE = 0      # c_mu = [lambda_mu lambda-tilde_mu^*]^{-1}      (Sec. III A)
+C_PHASE = 1        # c_mu = lambda-tilde_mu lambda_mu^* / |...|       (Sec. III A)
+
+
+def coupling_constants(G, lam, mode=C_INVERSE, tiny=1e-300):
+    """lambda-tilde = G lambda and the decoupling constants c_mu of Sec. III A.
+    A state whose |lambda_mu lambda-tilde_mu| is below ``tiny`` gets c_mu = 0
+    (its flow is frozen; the paper is silent on this case)."""
+    lt = G @ lam
+    c = np.zeros(len(lam), dtype=np.complex128)
+    for m in range(len(lam)):
+        z = lam[m] * np.conj(lt[m])
+        if abs(z) < tiny:
+            continue
+        c[m] = 1.0 / z if mode == C_INVERSE else np.conj(z) / abs(z)
+    return lt, c
+
+
+def eom(model, gammas, G, h, E, lam, mode=C_INVERSE):
+    """d Gamma^mu / ds of Eq. (EOM-Gamma3), for every state mu:
+
+    2 Re{ lt_mu^* c_mu sum_beta lambda_beta [ 2i G_mu,beta [D, F]
+          + 2 G_mu,beta (D F D + F) - (h_mu,beta - E G_mu,beta) D ] }
+
+    with D = Delta^{beta,mu}, F = F^{beta,mu}; "+ c.c." of the paper is
+    X + X^* = 2 Re X.  Delta^{mu,mu} = Gamma^mu (Sec. III B).
+    """
+    M = len(gammas)
+    lt, c = coupling_constants(G, lam, mode)
+    out = []
+    for mu in range(M):
+        acc = np.zeros((model.n, model.n), dtype=np.complex128)
+        for beta in range(M):
+            D = gammas[mu].astype(np.complex128) if beta == mu else transition_matrix(gammas[beta], gammas[mu])
+            F = fock_matrix(model, D)
+            term = (2j * G[mu, beta] * (D @ F - F @ D)
+                    + 2.0 * G[mu, beta] * (D @ F @ D + F)
+                    - (h[mu, beta] - E * G[mu, beta]) * D)
+            acc += lam[beta] * term
+        out.append(2.0 * np.real(np.conj(lt[mu]) * c[mu] * acc))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Integrator (App. A)
+# ---------------------------------------------------------------------------
+
+
+def orthogonal_step(Gm, dG, ds):
+    """Gamma <- R Gamma R^T with R = exp{(ds/4)[Gamma, dGamma]} (Eq. ExpStep)."""
+    X = 0.25 * ds * (Gm @ dG - dG @ Gm)
+    R = scipy.linalg.expm(X)
+    out = R @ Gm @ R.T
+    return 0.5 * (out - out.T)
+
+
+def purify(Gm):
+    """Canonical-form renormalisation of App. A (Eq. CM-normal-form with every
+    lambda_j set to 1): the orthogonal polar factor Gamma (Gamma^T Gamma)^{-1/2}."""
+    w, V = np.linalg.eigh(Gm.T @ Gm)
+    P = Gm @ (V / np.sqrt(w)) @ V.T
+    return 0.5 * (P - P.T)
+
+
+def euler_step(Gm, dG, ds):
+    """First-order step of Eq. (RKstep) followed by the canonical-form
+    renormalisation of App. A."""
+    return purify(Gm + ds * dG)
+
+
+# ---------------------------------------------------------------------------
+# One step and the energy (Sec. III C)
+# ---------------------------------------------------------------------------
+
+
+def energy(model, gammas):
+    """Energy of the current states with optimal amplitudes (Eq. eigLambda).
+    Returns (E, lambda, G, h)."""
+    G, h = gram_and_hamiltonian(model, gammas)
+    E, lam = solve_amplitudes(G, h)
+    return E, lam, G, h
+
+
+def sgs_step(model, gammas, ds, mode=C_INVERSE, purify_each=True):
+    """One step of Sec. III C: pairs -> amplitudes -> EOM -> orthogonal update
+    -> re-purification.  Returns (E before the update, lambda, new gammas)."""
+    E, lam, G, h = energy(model, gammas)
+    dGs = eom(model, gammas, G, h, E, lam, mode)
+    new = []
+    for Gm, dG in zip(gammas, dGs):
+        g = orthogonal_step(Gm, dG, ds)
+        new.append(purify(g) if purify_each else g)
+    return E, lam, new
+
+
+def run(model, gammas, ds, n_steps, mode=C_INVERSE):
+    """n_steps of sgs_step; returns (energies, lambda, gammas)."""
+    Es = []
+    lam = None
+    for _ in range(n_steps):
+        E, lam, gammas = sgs_step(model, gammas, ds, mode)
+        Es.append(E)
+    return np.array(Es), lam, gammas

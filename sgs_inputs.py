@@ -1,0 +1,112 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle
+checks.  Holds no arithmetic of the SGS method itself: it draws model
+parameters, random pure covariance matrices and random amplitudes.
+
+Random pure states: Gamma = O J O^T with O Haar-distributed on O(2N) (QR of a
+standard normal matrix with the signs of diag(R) folded into Q), one column
+flipped if needed so that det O (= Pf Gamma, the fermion parity) equals the
+requested parity.  Amplitudes: lambda_mu = exp(i theta), theta ~ U[0, 2 pi).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def vacuum_gamma(n_modes: int) -> np.ndarray:
+    n = 2 * n_modes
+    J = np.zeros((n, n))
+    for m in range(n_modes):
+        J[2 * m, 2 * m + 1] = 1.0
+        J[2 * m + 1, 2 * m] = -1.0
+    return J
+
+
+def haar_orthogonal(n: int, rng: np.random.Generator) -> np.ndarray:
+    Q, R = np.linalg.qr(rng.standard_normal((n, n)))
+    return Q * np.sign(np.diag(R))
+
+
+def random_pure_gamma(n_modes: int, rng: np.random.Generator, parity: int = 1) -> np.ndarray:
+    n = 2 * n_modes
+    O = haar_orthogonal(n, rng)
+    if np.linalg.det(O) * parity < 0:
+        O[:, 0] = -O[:, 0]
+    G = O @ vacuum_gamma(n_modes) @ O.T
+    return 0.5 * (G - G.T)
+
+
+def random_amplitudes(M: int, rng: np.random.Generator) -> np.ndarray:
+    return np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, size=M))
+
+
+@dataclass
+class AndersonParams:
+    """Anderson impurity with ``n_channels`` open bath chains (Sec. IV model;
+    two channels for the two-channel impurity workload)."""
+    n_bath: int
+    U: float
+    eps_d: float
+    V: float
+    t: float = 1.0
+    mu: float = 0.0
+    n_channels: int = 1
+
+    @property
+    def n_sites(self) -> int:
+        return 1 + self.n_channels * self.n_bath
+
+    @property
+    def n_modes(self) -> int:
+        return 2 * self.n_sites
+
+
+@dataclass
+class Workload:
+    name: str
+    model: AndersonParams
+    rank: int
+    dtau: float
+    n_steps: int
+    seed: int
+    parity: int = 1
+    extra: dict = field(default_factory=dict)
+
+
+def initial_state(n_modes: int, rank: int, seed: int, parity: int = 1):
+    """(gammas [rank, 2N, 2N] float64, lambdas [rank] complex128) from one seed."""
+    rng = np.random.default_rng(seed)
+    gammas = np.stack([random_pure_gamma(n_modes, rng, parity) for _ in range(rank)])
+    lam = random_amplitudes(rank, rng)
+    return np.ascontiguousarray(gammas), lam
+
+
+# Workloads: a small plain-FP64 case (16 sites, N=32 modes, M=4), the
+# throughput case (128 sites, N=256, M=32), the two-channel case (201 sites,
+# N=402, M=64), and the batched uneven case (256 instances).
+SMALL = Workload("anderson_L16_M4", AndersonParams(n_bath=15, U=2.0, eps_d=-1.0, V=0.5), rank=4,
+                 dtau=0.05, n_steps=200, seed=1)
+LARGE = Workload("anderson_L128_M32", AndersonParams(n_bath=127, U=4.0, eps_d=-2.0, V=0.5), rank=32,
+                 dtau=0.05, n_steps=500, seed=2)
+TWO_CHANNEL = Workload("two_channel_L201_M64",
+                       AndersonParams(n_bath=100, U=8.0, eps_d=-4.0, V=0.6, n_channels=2), rank=64,
+                       dtau=0.05, n_steps=1000, seed=3, parity=-1)
+
+
+def batched_workloads(n_instances: int = 256, seed: int = 4, dtau: float = 0.05):
+    """Uneven instances: bath length L ~ U{16..256} per spin, rank M in
+    {8, 16, 32}, U ~ U[0, 8], eps_d = -U/2, V ~ U[0.2, 1.0]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_instances):
+        L = int(rng.integers(16, 257))
+        M = int(rng.choice([8, 16, 32]))
+        U = float(rng.uniform(0.0, 8.0))
+        V = float(rng.uniform(0.2, 1.0))
+        # L bath sites plus the impurity; half filling puts L + 1 electrons
+        # in the particle-hole symmetric ground state, hence its parity
+        out.append(Workload(f"batched_{i}", AndersonParams(n_bath=L, U=U, eps_d=-U / 2, V=V), rank=M,
+                            dtau=dtau, n_steps=1, seed=int(rng.integers(1 << 31)),
+                            parity=1 if (L + 1) % 2 == 0 else -1))
+    return out

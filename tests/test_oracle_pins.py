@@ -1,0 +1,262 @@
+"""Pins of the FP64 oracle against things other than itself: explicit
+Fock-space vectors, exact diagonalisation, closed forms and identities stated
+in the paper.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import fock
+import sgs_inputs as inp
+from oracle import sgs_oracle as orc
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _fock_operator(model):
+    """The oracle's Majorana-form Hamiltonian as a Fock operator."""
+    N = model.N
+    c = fock.majoranas(N)
+    H = model.e_const * fock.sp.identity(2 ** N, dtype=np.complex128, format="csr")
+    for k in range(model.n):
+        for l in range(model.n):
+            if model.A[k, l] != 0.0:
+                H = H + (1j * model.A[k, l]) * (c[k] @ c[l])
+    for (k, l, p, q), v in model.quartic:
+        H = H + v * (c[k] @ c[l] @ c[p] @ c[q])
+    return H.tocsr()
+
+
+# ---------------------------------------------------------------- model (Sec. II A, IV)
+
+@pytest.mark.parametrize("n_bath,n_channels", [(1, 1), (2, 1), (1, 2)])
+def test_majorana_form_equals_fermion_hamiltonian(n_bath, n_channels):
+    rng = _rng(10 + n_bath + 7 * n_channels)
+    U, eps, V, t, mu = rng.uniform(0.5, 3.0), rng.uniform(-2, 0), rng.uniform(0.2, 1), rng.uniform(0.5, 1.5), rng.uniform(-0.3, 0.3)
+    model = orc.anderson_model(n_bath, U, eps, V, t, mu, n_channels)
+    Hf = fock.hamiltonian_anderson(n_bath, U, eps, V, t, mu, n_channels)
+    Hm = _fock_operator(model)
+    assert abs(Hf - Hm).max() < 1e-13
+
+
+def test_vacuum_and_parity_convention():
+    # vacuum has Gamma = J and Pf = +1; one occupied mode flips the parity
+    N = 3
+    J = inp.vacuum_gamma(N)
+    vac = np.zeros(2 ** N, complex)
+    vac[0] = 1
+    assert np.allclose(fock.covariance_of(vac), J)
+    a = fock.annihilators(N)
+    one = a[1].conj().T @ vac
+    G1 = fock.covariance_of(one)
+    assert orc.pfaffian(J) == pytest.approx(1.0)
+    assert orc.pfaffian(G1) == pytest.approx(-1.0)
+
+
+# ---------------------------------------------------------------- Pfaffian
+
+def test_pfaffian_closed_forms():
+    rng = _rng(3)
+    # 4x4 closed form
+    a = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    A = np.zeros((4, 4), complex)
+    A[0, 1], A[0, 2], A[0, 3], A[1, 2], A[1, 3], A[2, 3] = a
+    A = A - A.T
+    ref = A[0, 1] * A[2, 3] - A[0, 2] * A[1, 3] + A[0, 3] * A[1, 2]
+    assert abs(orc.pfaffian(A) - ref) < 1e-13
+    # block diagonal
+    vals = rng.standard_normal(5)
+    B = np.zeros((10, 10))
+    for j, v in enumerate(vals):
+        B[2 * j, 2 * j + 1], B[2 * j + 1, 2 * j] = v, -v
+    assert orc.pfaffian(B) == pytest.approx(np.prod(vals), rel=1e-13)
+    for n in (6, 12, 20):
+        X = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        X = X - X.T
+        p = orc.pfaffian(X)
+        assert abs(p * p - np.linalg.det(X)) < 1e-10 * abs(np.linalg.det(X))
+        # Pf(B X B^T) = det(B) Pf(X): fixes the sign, not only the square
+        Bm = rng.standard_normal((n, n))
+        assert abs(orc.pfaffian(Bm @ X @ Bm.T) - np.linalg.det(Bm) * p) < 1e-9 * abs(np.linalg.det(Bm) * p)
+
+
+# ---------------------------------------------------------------- pair quantities vs Fock
+
+def _states(N, M, seed, parity=1):
+    rng = _rng(seed)
+    gammas = [inp.random_pure_gamma(N, rng, parity) for _ in range(M)]
+    ref = fock.gaussian_vector(gammas[0])
+    vecs = [fock.gaussian_vector(g, ref) for g in gammas]
+    return gammas, vecs
+
+
+@pytest.mark.parametrize("parity", [1, -1])
+def test_gram_and_h_match_fock(parity):
+    model = orc.anderson_model(1, 2.0, -1.0, 0.5)         # 2 sites, N = 4 modes
+    gammas, vecs = _states(4, 4, 21 + parity, parity)
+    for g, v in zip(gammas, vecs):
+        assert np.allclose(fock.covariance_of(v), g, atol=1e-12)
+    G, h = orc.gram_and_hamiltonian(model, gammas)
+    H = fock.hamiltonian_anderson(1, 2.0, -1.0, 0.5)
+    assert np.abs(G - fock.gram(vecs)).max() < 1e-12
+    assert np.abs(h - fock.hmat(vecs, H)).max() < 1e-12
+    # G Hermitian, positive definite, gauge: G_0mu > 0
+    assert np.allclose(G, G.conj().T)
+    assert np.linalg.eigvalsh(G).min() > 0
+    assert np.all(np.abs(G[0].imag) < 1e-15) and np.all(G[0].real > 0)
+
+
+def test_transition_matrix_two_and_four_point():
+    gammas, vecs = _states(3, 2, 5)
+    N, n = 3, 6
+    c = fock.majoranas(N)
+    a, b = 0, 1
+    D = orc.transition_matrix(gammas[a], gammas[b])
+    Gba = np.vdot(vecs[b], vecs[a])
+    for k in range(n):
+        for l in range(n):
+            if k != l:
+                x = np.vdot(vecs[b], c[k] @ (c[l] @ vecs[a]))
+                assert abs(x - 1j * Gba * D[k, l]) < 1e-12
+    # n-point elements: Pfaffian of the sub-block of i Delta (Sec. III B)
+    for idx in [(0, 1, 2, 3), (0, 2, 3, 5), (1, 2, 4, 5)]:
+        x = np.vdot(vecs[b], c[idx[0]] @ c[idx[1]] @ c[idx[2]] @ (c[idx[3]] @ vecs[a]))
+        sub = 1j * D[np.ix_(idx, idx)]
+        assert abs(x - Gba * orc.pfaffian(sub)) < 1e-12
+    # Delta^{a,a} = Gamma^a (Sec. III B)
+    assert np.allclose(orc.transition_matrix(gammas[0], gammas[0]), gammas[0])
+    # skew-symmetry and Delta^{b,a} = conj(Delta^{a,b})
+    assert np.allclose(D, -D.T)
+    assert np.allclose(orc.transition_matrix(gammas[b], gammas[a]), D.conj())
+
+
+def test_phase_matches_three_state_grassmann_pfaffian():
+    """At N where Fock vectors are out of reach, the transition-form phase
+    must agree with the independent 3n x 3n Grassmann form of the Bargmann
+    product: <0|a><a|b><b|0> = Pf(G0) (i/4)^N Pf([[iG0,-1,1],[1,iGa,-1],[-1,1,iGb]])
+    (pinned itself against Fock vectors at small N below)."""
+    for N, seed in ((3, 1), (4, 2)):
+        gammas, vecs = _states(N, 3, seed)
+        g0, ga, gb = gammas
+        I = np.eye(2 * N)
+        R = np.block([[1j * g0, -I, I], [I, 1j * ga, -I], [-I, I, 1j * gb]])
+        B_fock = np.vdot(vecs[0], vecs[1]) * np.vdot(vecs[1], vecs[2]) * np.vdot(vecs[2], vecs[0])
+        B_grass = orc.pfaffian(g0) * (0.25j) ** N * orc.pfaffian(R)
+        assert abs(B_fock - B_grass) < 1e-12
+    model = orc.anderson_model(9, 2.0, -1.0, 0.5)          # N = 20 modes
+    rng = _rng(8)
+    gammas = [inp.random_pure_gamma(20, rng) for _ in range(3)]
+    G, _ = orc.gram_and_hamiltonian(model, gammas)
+    g0, ga, gb = gammas
+    I = np.eye(40)
+    R = np.block([[1j * g0, -I, I], [I, 1j * ga, -I], [-I, I, 1j * gb]])
+    ph, la = orc.pfaffian_log(R)
+    B = orc.pfaffian(g0) * (1j ** 20) * ph
+    Bo = G[0, 1] * G[1, 2] * G[2, 0]
+    assert abs(Bo / abs(Bo) - B / abs(B)) < 1e-10
+    # magnitude too: log|B| = 20 log(1/4) + log|Pf R|
+    assert abs(math.log(abs(Bo)) - (20 * math.log(0.25) + la)) < 1e-9
+
+
+# ---------------------------------------------------------------- amplitudes and energy
+
+def test_energy_is_rayleigh_quotient_and_variational():
+    model = orc.anderson_model(2, 2.0, -1.0, 0.5)           # 3 sites, N = 6 modes
+    H = fock.hamiltonian_anderson(2, 2.0, -1.0, 0.5)
+    gammas, vecs = _states(6, 3, 31)
+    E, lam, G, h = orc.energy(model, gammas)
+    psi = sum(l * v for l, v in zip(lam, vecs))
+    assert abs(np.vdot(psi, psi) - 1.0) < 1e-12
+    assert abs(np.vdot(psi, H @ psi) - E) < 1e-12
+    E2, _ = fock.lowest_amplitudes(fock.gram(vecs), fock.hmat(vecs, H))
+    assert abs(E - E2) < 1e-12
+    assert E >= fock.ground_energy(H) - 1e-12
+
+
+# ---------------------------------------------------------------- equation of motion
+
+@pytest.mark.parametrize("mode", [orc.C_INVERSE, orc.C_PHASE])
+def test_eom_matches_fock_flow(mode):
+    model = orc.anderson_model(1, 3.0, -1.5, 0.7, t=1.0, mu=0.1)
+    H = fock.hamiltonian_anderson(1, 3.0, -1.5, 0.7, t=1.0, mu=0.1)
+    gammas, vecs = _states(4, 3, 41)
+    E, lam, G, h = orc.energy(model, gammas)
+    dG = orc.eom(model, gammas, G, h, E, lam, mode)
+    ref = fock.eom_bruteforce(vecs, lam, H, "inverse" if mode == orc.C_INVERSE else "phase")
+    for a, b, g in zip(dG, ref, gammas):
+        assert np.abs(a - b).max() < 1e-11 * max(1.0, np.abs(b).max())
+        # tangency (d Gamma) Gamma + Gamma (d Gamma) = 0 (Sec. III B)
+        assert np.abs(a @ g + g @ a).max() < 1e-11 * max(1.0, np.abs(a).max())
+        assert np.allclose(a, -a.T)
+
+
+def test_rank_one_reduces_to_ghf():
+    """R = 1: Eq. (EOM-Gamma3) falls back onto the GHF flow 4(F + Gamma F Gamma)
+    with F the GHF Fock matrix (Sec. III B)."""
+    model = orc.anderson_model(3, 2.5, -1.25, 0.6)
+    rng = _rng(51)
+    g = inp.random_pure_gamma(model.N, rng)
+    E, lam, G, h = orc.energy(model, [g])
+    dG = orc.eom(model, [g], G, h, E, lam)[0]
+    F = np.zeros_like(model.A) + model.A
+    for (k, l, m, r), v in model.quartic:
+        F[k, l] += 6.0 * v * g[m, r]
+    assert np.abs(dG - 4.0 * (F + g @ F @ g)).max() < 1e-12
+
+
+# ---------------------------------------------------------------- integrator (App. A)
+
+def test_orthogonal_step_first_order_and_pure():
+    model = orc.anderson_model(2, 2.0, -1.0, 0.5)
+    rng = _rng(61)
+    gammas = [inp.random_pure_gamma(model.N, rng) for _ in range(3)]
+    E, lam, G, h = orc.energy(model, gammas)
+    dG = orc.eom(model, gammas, G, h, E, lam)
+    errs = []
+    for ds in (1e-2, 5e-3, 2.5e-3):
+        g1 = orc.orthogonal_step(gammas[1], dG[1], ds)
+        assert np.abs(g1 @ g1 + np.eye(model.n)).max() < 1e-13
+        errs.append(np.abs(g1 - (gammas[1] + ds * dG[1])).max())
+    # O(ds^2): halving ds quarters the gap to the Euler step
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_purify_recovers_canonical_form():
+    rng = _rng(71)
+    N = 6
+    O = inp.haar_orthogonal(2 * N, rng)
+    lam = rng.uniform(0.9, 1.1, N)
+    blk = np.zeros((2 * N, 2 * N))
+    for j in range(N):
+        blk[2 * j, 2 * j + 1], blk[2 * j + 1, 2 * j] = lam[j], -lam[j]
+    noisy = O @ blk @ O.T
+    clean = O @ inp.vacuum_gamma(N) @ O.T
+    assert np.abs(orc.purify(noisy) - clean).max() < 1e-13
+    assert np.abs(orc.purify(clean) - clean).max() < 1e-14
+
+
+# ---------------------------------------------------------------- whole-step ground truths
+
+def test_energy_descends():
+    model = orc.anderson_model(2, 2.0, -1.0, 0.5)
+    rng = _rng(81)
+    gammas = [inp.random_pure_gamma(model.N, rng) for _ in range(3)]
+    Es, _, _ = orc.run(model, gammas, 0.02, 30)
+    assert np.all(np.diff(Es) <= 1e-12)
+    H = fock.hamiltonian_anderson(2, 2.0, -1.0, 0.5)
+    assert Es[-1] >= fock.ground_energy(H) - 1e-12
+
+
+def test_noninteracting_closed_form():
+    """U = 0: a single Gaussian is exact, and the GHF flow reaches the sum of
+    the negative single-particle energies (Sec. II A)."""
+    h_sp, _ = orc.anderson_chain(7, 0.0, 0.0, 0.5)
+    model = orc.majorana_from_fermions(h_sp, [])
+    eps = np.linalg.eigvalsh(h_sp)
+    exact = eps[eps < 0].sum()
+    rng = _rng(91)
+    g = [inp.random_pure_gamma(model.N, rng, 1)]
+    Es, _, gs = orc.run(model, g, 0.25, 400)
+    assert abs(Es[-1] - exact) < 1e-9
