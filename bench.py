@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Imaginary-time steps per second of the SGS variational method on GB300.
+
+Workload: Anderson impurity, 127 bath sites per spin (N = 256 modes, 2N = 512),
+rank M = 32, U = 4, eps_d = -2, V = 0.5, ds = 0.05, seeded random pure states.
+A step is one pass of the whole hot path (pairs, amplitudes, equation of
+motion, update, re-purification) over all M states.  Inputs stay resident in
+HBM during the timed region (the per-step working set, several GB, is far
+larger than L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
+of the workload (independent problems, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sgs_inputs as inp  # noqa: E402
+
+METRIC = "imag-time steps/s at 2N=512,M=32"
+UNIT = "steps/s"
+PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
+DTYPES = {"fp64": "f64", "tf32": "f64+tf32", "bf16": "f64+bf16", "3xtf32": "f64+3xtf32"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sgs", choices=["sgs", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
+    ap.add_argument("--workload", default="large", choices=["large", "small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    return inp.LARGE if name == "large" else inp.SMALL
+
+
+def config_of(w, precision):
+    p = w.model
+    return {"workload": f"{w.name}: Anderson impurity, {p.n_bath} bath sites/spin, 2N={2 * p.n_modes}, "
+                        f"M={w.rank}, U={p.U}, eps_d={p.eps_d}, V={p.V}, t={p.t}, ds={w.dtau}",
+            "n": 2 * p.n_modes, "rank": w.rank, "precision": precision, "seed": w.seed,
+            "l2": "inputs larger than L2 (per-step working set of several GB, no flush needed)",
+            "inputs": "seeded random pure states Gamma = O J O^T, O Haar on O(2N)"}
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(w, n_pairs=4, n_states=1):
+    """Time the FP64 oracle on a bounded sample of one step of the workload:
+    n_pairs pair evaluations (overlap with phase, transition matrix, Wick
+    energy, both receivers' EOM terms) and n_states state updates, then scale
+    to the step's M(M-1)/2 pairs and M states.  Returns (seconds per step, sample)."""
+    from oracle import sgs_oracle as orc
+    p = w.model
+    model = orc.anderson_model(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels)
+    g, _ = inp.initial_state(p.n_modes, max(n_pairs + 1, 2), w.seed, w.parity)
+    gam = list(g)
+    t0 = time.perf_counter()
+    pf0, _ = orc.pfaffian_log(gam[0])
+    for k in range(n_pairs):
+        a, b = 1 + (k % (len(gam) - 1)), 1 + ((k + 1) % (len(gam) - 1))
+        if a == b:
+            b = 0
+        orc.log_overlap_magnitude(gam[a], gam[b])
+        D = orc.transition_matrix(gam[a], gam[b])
+        orc.pfaffian_log(gam[0] + D)
+        orc.wick_energy_density(model, D)
+        for X in (D, D.conj()):          # both receivers of the pair
+            F = orc.fock_matrix(model, X)
+            _ = 2j * (X @ F - F @ X) + 2.0 * (X @ F @ X + F) - X
+    t_pairs = (time.perf_counter() - t0) / n_pairs
+    t0 = time.perf_counter()
+    for k in range(n_states):
+        dG = 0.01 * (gam[k] @ gam[k + 1] - gam[k + 1] @ gam[k])
+        orc.purify(orc.orthogonal_step(gam[k], dG, w.dtau))
+    t_states = (time.perf_counter() - t0) / n_states
+    M = w.rank
+    t_step = t_pairs * M * (M - 1) / 2 + t_states * M
+    sample = (f"{n_pairs} pair evaluations + {n_states} state update(s) of the {w.name} step, "
+              f"scaled to {M * (M - 1) // 2} pairs + {M} states")
+    return t_step, sample
+
+
+def cpu_cores():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+# --------------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(w, n_pairs=1, n_states=1)
+    times = []
+    sample = ""
+    for _ in range(args.steps):
+        t, sample = oracle_sample(w, n_pairs=2, n_states=1)
+        times.append(t)
+    t_step = float(np.mean(times))
+    value = 1.0 / t_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": "per timed step: " + sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_sgs(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2105_01088_gb300 as sgs
+
+    sgs.use_torch_allocator()
+    w = workload(args.workload)
+    p = w.model
+    prec = PRECISIONS[args.precision]
+    g, lam = inp.initial_state(p.n_modes, w.rank, w.seed + 1000 * rank, w.parity)
+    model = sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels)
+    stream = torch.cuda.current_stream()
+    solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=prec, parity=w.parity, stream=stream)
+    peak_fp64_mma = sgs.probe_peak(0)
+
+    solver.step(args.warmup)
+    clocks = ClockSampler(local)
+    solver.set_profiling(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    E = solver.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof, launches = solver.profile()
+    solver.set_profiling(False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max * 1e-3)
+
+    # end to end through the public API with pinned host buffers
+    n = 2 * p.n_modes
+    g_host = torch.empty((w.rank, n, n), dtype=torch.float64, pin_memory=True).numpy()
+    g_host[:] = solver.get_state()[0]
+    lam_host = np.zeros(w.rank, complex)
+    k_e2e = max(1, min(args.steps, 3))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        solver.set_state(g_host, None)
+        solver.step(1)
+        _, lam_host[:] = solver.get_state(out=g_host)
+    t_e2e = time.perf_counter() - t0
+    te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * k_e2e / float(te.item())
+    h2d = w.rank * n * n * 8
+    d2h = w.rank * n * n * 8 + w.rank * 16 + 8
+
+    # roofline of the dominant stage
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    stage = max(prof, key=lambda s: prof[s][0])
+    s_ms, s_fl, s_by = prof[stage]
+    if s_fl > 0:
+        achieved = s_fl / (s_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_fp64_mma, "unit": "TFLOP/s",
+                "frac": achieved / peak_fp64_mma, "traffic": None, "kernel": stage,
+                "peak_source": "measured live: FP64 m8n8k4 MMA throughput probe (sgs_probe_peak)"}
+    else:
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = s_by / (s_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": stage,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
+    stages = {s: {"ms_per_step": v[0] / args.steps, "tflops": (v[1] / (v[0] * 1e-3) / 1e12) if v[0] > 0 and v[1] > 0
+                  else None} for s, v in prof.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": config_of(w, args.precision),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches), "roofline": roof, "clocks": ck, "stages": stages,
+            "energy_last": float(E[0, -1]), "fp64_mma_peak_tflops": peak_fp64_mma}
+    solver.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_step, sample = oracle_sample(w, n_pairs=6, n_states=2)
+        line["cpu_baseline"] = {"value": 1.0 / t_step, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_sgs(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

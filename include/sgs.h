@@ -1,0 +1,192 @@
+/*
+ * sgs.h -- C ABI of the GB300 (sm_103a) imaginary-time step of the
+ * superposition-of-Gaussian-states (SGS) variational method for quantum
+ * impurity models (Boutin & Bauer, arXiv:2105.01088).
+ *
+ * Problem statement (Sec. II): a fermion Hamiltonian in Majorana form
+ *   H = e_const + i sum_kl A_kl c_k c_l + sum_klpq U_klpq c_k c_l c_p c_q
+ * (Sec. II A), and a rank-M ansatz |psi> = sum_mu lambda_mu |phi_mu> of
+ * Gaussian states, each described by its real antisymmetric 2N x 2N
+ * covariance matrix Gamma^mu with (Gamma^mu)^2 = -1 (Sec. II B-C).
+ *
+ * One step (Sec. III C): all pair overlaps with phase, transition matrices
+ * and Hamiltonian matrix elements (Sec. II B-C, III B); the amplitudes from
+ * h lambda = E G lambda (Eq. eigLambda); the decoupled equation of motion of
+ * every Gamma^mu (Eq. EOM-Gamma3); the orthogonal update and the
+ * re-purification of App. A.
+ *
+ * Conventions for every call:
+ *   - All array arguments are HOST pointers owned by the caller; inputs are
+ *     copied during the call, outputs are written before the call returns.
+ *   - Matrices are row-major FP64.  Complex numbers are stored as (re, im)
+ *     pairs of doubles.
+ *   - Majoranas c_{2m}, c_{2m+1} of fermion mode m (0-based) are a_m + a_m^dag
+ *     and -i (a_m - a_m^dag); the vacuum has Gamma = (+)_m [[0,1],[-1,0]] and
+ *     the fermion parity of a Gaussian state is Pf(Gamma).
+ *   - The overlap gauge (Sec. II B) takes the first ansatz state as the
+ *     reference: <phi_0|phi_mu> is real and positive.
+ *   - Every call returns an sgs_status; nothing aborts or throws across the
+ *     ABI.  sgs_last_error() describes the last failure of a context.
+ *   - A context is not thread-safe: use one context per host thread.
+ *   - Device memory is owned by the context and released by sgs_free().
+ */
+#ifndef SGS_H
+#define SGS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgs_ctx sgs_ctx;
+
+typedef enum {
+    SGS_OK = 0,
+    SGS_EINVAL = 1,      /* bad argument (sizes, NULL pointers, rank, parity) */
+    SGS_ENOMEM = 2,      /* device allocation failed, or over the HBM budget */
+    SGS_ESINGULAR = 3,   /* two ansatz states orthogonal (Gamma_a + Gamma_b singular) */
+    SGS_ENOTCONV = 4,    /* amplitude solver or exponential step out of range */
+    SGS_ETIMEOUT = 5,    /* a bounded device wait ran out */
+    SGS_ECUDA = 6        /* CUDA runtime error (message in sgs_last_error) */
+} sgs_status;
+
+typedef enum {
+    SGS_FP64 = 0,        /* every product in FP64 (FP64 tensor path, mma.sync f64) */
+    SGS_MIXED_TF32 = 1,  /* pair GEMMs of the equation of motion in TF32, FP32 accumulate */
+    SGS_MIXED_BF16 = 2,  /* same in BF16 */
+    SGS_FP32_3XTF32 = 3  /* same with the 3xTF32 split (about FP32 accuracy) */
+} sgs_precision;
+
+typedef enum {
+    SGS_C_INVERSE = 0,   /* c_mu = [lambda_mu conj(lt_mu)]^{-1}           (Sec. III A) */
+    SGS_C_PHASE = 1      /* c_mu = lt_mu conj(lambda_mu) / |lambda_mu lt_mu|  (Sec. III A) */
+} sgs_cmode;
+
+/* Model, Sec. II A.  A: n x n row-major real antisymmetric, n = 2 * n_modes.
+ * Quartic part: n_quartic monomials value[j] * c_i0 c_i1 c_i2 c_i3 with four
+ * distinct indices idx[4j..4j+3]; the library antisymmetrises them into U
+ * (U_{pi(i)} = sgn(pi) value / 24).  At most 16 distinct Majoranas may
+ * appear in quartic terms (the impurity block). */
+typedef struct {
+    int n_modes;
+    const double* A;
+    int n_quartic;
+    const int* quartic_idx;
+    const double* quartic_val;
+    double e_const;
+} sgs_model;
+
+/* Per-instance options.  gamma0: [rank][n][n] pure states of one parity
+ * (Pf Gamma = parity); lambda0: [rank] complex, may be NULL (the first solve
+ * replaces the amplitudes).  stream: a cudaStream_t, or NULL for the
+ * context's own stream (the first instance's stream is used for all). */
+typedef struct {
+    int rank;
+    double dtau;             /* step ds of App. A */
+    int precision;           /* sgs_precision */
+    int cmode;               /* sgs_cmode */
+    int parity;              /* +1 or -1 */
+    const double* gamma0;
+    const double* lambda0;
+    void* stream;
+} sgs_options;
+
+/* Create a context holding n_instances independent problems (models[i],
+ * opts[i]); uploads the model and the initial states to device memory.
+ * Errors: SGS_EINVAL (n_modes < 1, rank < 1 or > 64, parity not +-1,
+ * gamma0 NULL), SGS_ENOMEM, SGS_ECUDA.  On error *out is NULL. */
+sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_instances, sgs_ctx** out);
+
+/* Advance every instance by n_steps imaginary-time steps (Sec. III C).
+ * energies (may be NULL): [n_instances][n_steps], the energy E of the
+ * states at the start of each step with optimal amplitudes.
+ * Errors: SGS_ESINGULAR, SGS_ENOTCONV (state left as after the failing
+ * step), SGS_ECUDA. */
+sgs_status sgs_step(sgs_ctx* ctx, int n_steps, double* energies);
+
+/* Energy of the current states with optimal amplitudes (Eq. eigLambda),
+ * without changing the states.  energies: [n_instances]. */
+sgs_status sgs_energy(sgs_ctx* ctx, double* energies);
+
+typedef enum {
+    SGS_CORR_SPIN_SPIN = 0,      /* C(r) = <S(0).S(r)> (Eq. Cr); sites[i] = r */
+    SGS_CORR_TWO_CHANNEL_K = 1,  /* K(r) = sum_alpha <S_imp.S_alpha(r)> (Eq. K2CK); sites[i] = r */
+    SGS_CORR_RENYI2 = 2          /* S_2 of the impurity plus the first l sites (App. B); sites[i] = l */
+} sgs_corr_kind;
+
+/* Observables of the current SGS state of one instance.  out: [n_sites]. */
+sgs_status sgs_correlator(sgs_ctx* ctx, int instance, sgs_corr_kind kind, const int* sites, int n_sites,
+                          double* out);
+
+void sgs_free(sgs_ctx* ctx);
+const char* sgs_last_error(const sgs_ctx* ctx);
+
+/* Checkpoint / resume.  gamma: [rank][n][n]; lambda: [rank] complex. */
+sgs_status sgs_get_state(const sgs_ctx* ctx, int instance, double* gamma, double* lambda);
+sgs_status sgs_set_state(sgs_ctx* ctx, int instance, const double* gamma, const double* lambda);
+
+/* Intermediate results of the last sgs_step / sgs_energy call of one
+ * instance: G and h ([rank][rank] complex, Eq. eigLambda) and, after
+ * sgs_step, dGamma/ds of the last step ([rank][n][n], Eq. EOM-Gamma3). */
+sgs_status sgs_get_pair_matrices(const sgs_ctx* ctx, int instance, double* G, double* h);
+sgs_status sgs_get_derivative(const sgs_ctx* ctx, int instance, double* dgamma);
+
+/* Device memory hook: if set before sgs_init, every device allocation of
+ * the library goes through alloc/release (e.g. a framework's caching
+ * allocator); otherwise cudaMalloc/cudaFree. */
+typedef void* (*sgs_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*sgs_free_fn)(void* ptr, void* user);
+void sgs_set_allocator(sgs_alloc_fn alloc, sgs_free_fn release, void* user);
+
+/* Stage profile.  sgs_set_profiling(ctx, 1) resets the counters and records
+ * CUDA events (on the context stream) around each stage of every following
+ * sgs_step / sgs_energy; sgs_get_profile returns per stage the summed device
+ * time (ms), the algorithmic FP64 flops (useful work: an antisymmetric
+ * product counts n^3, a general one 2 n^3, the Gauss-Jordan inverse 2 n^3,
+ * the complex Pfaffian 4 n^3 / 3), the algorithmic bytes of memory-bound
+ * stages, and the number of kernels the library launched. */
+typedef enum {
+    SGS_STAGE_PAIR_INVERSE = 0,    /* S = G_a + G_b, blocked Gauss-Jordan inverse */
+    SGS_STAGE_PAIR_DELTA = 1,      /* Im Delta = (G_a - G_b) S^{-1} */
+    SGS_STAGE_PHASE_PFAFFIAN = 2,  /* Pf(G_0 + Delta^{a,b}) */
+    SGS_STAGE_AMPLITUDES = 3,      /* G, h, Wick contractions, h lambda = E G lambda */
+    SGS_STAGE_EOM_GEMM = 4,        /* S^{-1} F S^{-1}, D W, (D W) D, Gamma F Gamma */
+    SGS_STAGE_EOM_ASSEMBLY = 5,    /* Delta F Delta planes, dGamma/ds */
+    SGS_STAGE_UPDATE = 6,          /* exp step, R Gamma R^T, re-purification */
+    SGS_N_STAGES = 7
+} sgs_stage;
+sgs_status sgs_set_profiling(sgs_ctx* ctx, int enable);
+sgs_status sgs_get_profile(const sgs_ctx* ctx, double* ms, double* flops, double* bytes, long long* launches);
+
+/* Measured throughput (TFLOP/s) of an FP64 pipe of the current device:
+ * kind 0 = the m8n8k4 FP64 MMA (the path of every FP64 product here),
+ * kind 1 = FP64 FMA on the CUDA cores. */
+sgs_status sgs_probe_peak(int kind, double* tflops);
+
+/* Majorana form of the Anderson impurity of Sec. IV (H_0 + H_I) with
+ * n_channels open bath chains of n_bath sites, hybridisation V, hopping t,
+ * chemical potential mu, interaction U n_up n_dn and level eps_d on the
+ * impurity.  Site order: impurity, then chain sites interleaved by channel;
+ * mode 2*site + spin.  Writes A ([n][n], n = 4 (1 + n_channels n_bath)), one
+ * quartic monomial (idx[4], val[1]) and e_const.  Returns the number of
+ * modes N, or -1 on bad arguments. */
+int sgs_build_anderson(int n_bath, int n_channels, double U, double eps_d, double V, double t, double mu,
+                       double* A, int* quartic_idx, double* quartic_val, double* e_const);
+
+/* Building blocks with host buffers, for tests and external callers.
+ * sgs_kernel_inverse: batch n x n matrices -> inverses (Gauss-Jordan,
+ *   partial pivoting, FP64) and log|det|.  Returns SGS_ESINGULAR on a zero
+ *   pivot.
+ * sgs_kernel_pfaffian: batch complex antisymmetric n x n matrices (re, im
+ *   interleaved) -> Pf = phase * exp(logabs), phase as (re, im).
+ * sgs_kernel_dgemm: batch C = A B (n x n, FP64). */
+sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, double* logabsdet);
+sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase, double* logabs);
+sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, double* C);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGS_H */

@@ -1,0 +1,325 @@
+"""GB300 (sm_103a) imaginary-time step of the superposition-of-Gaussian-states
+variational method (Boutin & Bauer, arXiv:2105.01088).
+
+Thin Python binding over the C ABI of include/sgs.h (libsgs.so, built in tree
+by ``paper_2105_01088_gb300.build``).  Every step of the method runs in the
+library's CUDA kernels; this module only marshals arguments.  PyTorch, when
+present with a GPU, provides the device memory (its caching allocator) and
+the CUDA stream.  The first call raises ImportError if the library has not
+been built; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgs.so")
+
+SGS_FP64, SGS_MIXED_TF32, SGS_MIXED_BF16, SGS_FP32_3XTF32 = 0, 1, 2, 3
+SGS_C_INVERSE, SGS_C_PHASE = 0, 1
+SGS_CORR_SPIN_SPIN, SGS_CORR_TWO_CHANNEL_K, SGS_CORR_RENYI2 = 0, 1, 2
+STATUS = {0: "SGS_OK", 1: "SGS_EINVAL", 2: "SGS_ENOMEM", 3: "SGS_ESINGULAR", 4: "SGS_ENOTCONV",
+          5: "SGS_ETIMEOUT", 6: "SGS_ECUDA"}
+
+
+class SGSError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("n_modes", ctypes.c_int), ("A", ctypes.POINTER(ctypes.c_double)), ("n_quartic", ctypes.c_int),
+                ("quartic_idx", ctypes.POINTER(ctypes.c_int)), ("quartic_val", ctypes.POINTER(ctypes.c_double)),
+                ("e_const", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int), ("dtau", ctypes.c_double), ("precision", ctypes.c_int),
+                ("cmode", ctypes.c_int), ("parity", ctypes.c_int), ("gamma0", ctypes.POINTER(ctypes.c_double)),
+                ("lambda0", ctypes.POINTER(ctypes.c_double)), ("stream", ctypes.c_void_p)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_ctxp = ctypes.c_void_p
+
+# exported symbols and their signatures (must match include/sgs.h)
+SIGNATURES = {
+    "sgs_init": (ctypes.c_int, [ctypes.POINTER(_Model), ctypes.POINTER(_Options), ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_void_p)]),
+    "sgs_step": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp]),
+    "sgs_energy": (ctypes.c_int, [_ctxp, _dp]),
+    "sgs_correlator": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _dp]),
+    "sgs_free": (None, [_ctxp]),
+    "sgs_last_error": (ctypes.c_char_p, [_ctxp]),
+    "sgs_get_state": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, _dp]),
+    "sgs_set_state": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, _dp]),
+    "sgs_get_pair_matrices": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, _dp]),
+    "sgs_get_derivative": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp]),
+    "sgs_set_allocator": (None, [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]),
+    "sgs_build_anderson": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _ip, _dp, _dp]),
+    "sgs_set_profiling": (ctypes.c_int, [_ctxp, ctypes.c_int]),
+    "sgs_get_profile": (ctypes.c_int, [_ctxp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "sgs_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
+    "sgs_kernel_inverse": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
+    "sgs_kernel_pfaffian": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
+    "sgs_kernel_dgemm": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp]),
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2105_01088_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+class _LazyLibrary:
+    """Loads libsgs.so on first use (so that ``paper_2105_01088_gb300.build``
+    can run before the library exists); raises ImportError if it is missing."""
+
+    _cdll = None
+
+    def __getattr__(self, name):
+        if _LazyLibrary._cdll is None:
+            _LazyLibrary._cdll = load_library()
+        return getattr(_LazyLibrary._cdll, name)
+
+
+_lib = _LazyLibrary()
+
+
+def _ptr(a, kind=_dp):
+    return a.ctypes.data_as(kind) if a is not None else None
+
+
+# ------------------------------------------------------------ device memory via PyTorch
+_torch_hooks = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching
+    allocator (call once, before creating solvers)."""
+    global _torch_hooks
+    if _torch_hooks is not None:
+        return
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            s = stream if stream else torch.cuda.current_stream().cuda_stream
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), s)
+        except Exception:
+            return None
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _torch_hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    _lib.sgs_set_allocator(_torch_hooks[0], _torch_hooks[1], None)
+
+
+# ------------------------------------------------------------ model builder
+
+class MajoranaModel:
+    """Model in the library's input form: A (n x n), quartic monomials
+    (idx [q, 4], val [q]) and the constant e_const (Sec. II A)."""
+
+    def __init__(self, A, quartic_idx, quartic_val, e_const):
+        self.A = np.ascontiguousarray(A, dtype=np.float64)
+        self.quartic_idx = np.ascontiguousarray(np.asarray(quartic_idx, dtype=np.int32).reshape(-1, 4))
+        self.quartic_val = np.ascontiguousarray(quartic_val, dtype=np.float64).reshape(-1)
+        self.e_const = float(e_const)
+        self.n = self.A.shape[0]
+        self.n_modes = self.n // 2
+
+
+def build_anderson(n_bath, U, eps_d, V, t=1.0, mu=0.0, n_channels=1) -> MajoranaModel:
+    n_sites = 1 + n_channels * n_bath
+    n = 4 * n_sites
+    A = np.zeros((n, n))
+    qi = np.zeros(4, dtype=np.int32)
+    qv = np.zeros(1)
+    ec = np.zeros(1)
+    nm = _lib.sgs_build_anderson(n_bath, n_channels, U, eps_d, V, t, mu, _ptr(A), _ptr(qi, _ip), _ptr(qv), _ptr(ec))
+    if nm < 0:
+        raise SGSError(1, "bad Anderson parameters")
+    return MajoranaModel(A, qi, qv, ec[0])
+
+
+# ------------------------------------------------------------ solver
+
+class Solver:
+    """A context of one or more independent SGS problems resident on the GPU.
+
+    models: MajoranaModel or list; gamma0: [M, n, n] or list; lambda0: [M]
+    complex or None.  stream: a CUDA stream handle (int), a torch stream, or
+    None (torch's current stream when torch is available)."""
+
+    def __init__(self, models, gamma0, lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE,
+                 parity=1, stream=None):
+        if isinstance(models, MajoranaModel):
+            models, gamma0, lambda0 = [models], [gamma0], [lambda0]
+            dtau, precision, cmode, parity = [dtau], [precision], [cmode], [parity]
+        k = len(models)
+
+        def per(x):
+            return list(x) if isinstance(x, (list, tuple)) else [x] * k
+
+        dtau, precision, cmode, parity = per(dtau), per(precision), per(cmode), per(parity)
+        if lambda0 is None:
+            lambda0 = [None] * k
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._keep = []
+        mods = (_Model * k)()
+        opts = (_Options * k)()
+        self.shapes = []
+        for i, m in enumerate(models):
+            g = np.ascontiguousarray(gamma0[i], dtype=np.float64)
+            M = g.shape[0]
+            if g.shape != (M, m.n, m.n):
+                raise SGSError(1, f"gamma0[{i}] has shape {g.shape}, expected ({M}, {m.n}, {m.n})")
+            lam = None
+            if lambda0[i] is not None:
+                lam = np.ascontiguousarray(np.stack([np.real(lambda0[i]), np.imag(lambda0[i])], -1), dtype=np.float64)
+            self._keep += [m, g, lam]
+            mods[i] = _Model(m.n_modes, _ptr(m.A), len(m.quartic_val), _ptr(m.quartic_idx, _ip), _ptr(m.quartic_val),
+                             m.e_const)
+            opts[i] = _Options(M, dtau[i], precision[i], cmode[i], parity[i], _ptr(g), _ptr(lam),
+                               ctypes.c_void_p(stream) if stream else None)
+            self.shapes.append((M, m.n))
+        ctx = ctypes.c_void_p()
+        st = _lib.sgs_init(mods, opts, k, ctypes.byref(ctx))
+        if st != 0:
+            raise SGSError(st, "sgs_init failed")
+        self._ctx = ctx
+        self.n_instances = k
+
+    def _check(self, st):
+        if st != 0:
+            raise SGSError(st, (_lib.sgs_last_error(self._ctx) or b"").decode())
+
+    def step(self, n_steps=1) -> np.ndarray:
+        """Advance every instance; returns energies [n_instances, n_steps]."""
+        E = np.zeros((self.n_instances, n_steps))
+        self._check(_lib.sgs_step(self._ctx, n_steps, _ptr(E)))
+        return E
+
+    def energy(self) -> np.ndarray:
+        E = np.zeros(self.n_instances)
+        self._check(_lib.sgs_energy(self._ctx, _ptr(E)))
+        return E
+
+    def correlator(self, kind, sites, instance=0) -> np.ndarray:
+        s = np.ascontiguousarray(sites, dtype=np.int32)
+        out = np.zeros(len(s))
+        self._check(_lib.sgs_correlator(self._ctx, instance, kind, _ptr(s, _ip), len(s), _ptr(out)))
+        return out
+
+    def get_state(self, instance=0, out=None):
+        """(gamma [M, n, n], lambda [M]); ``out`` may be a C-contiguous float64
+        [M, n, n] buffer (e.g. pinned host memory) to receive gamma."""
+        M, n = self.shapes[instance]
+        g = np.zeros((M, n, n)) if out is None else out
+        if g.shape != (M, n, n) or g.dtype != np.float64 or not g.flags.c_contiguous:
+            raise SGSError(1, "out must be a C-contiguous float64 array of shape (M, n, n)")
+        lam = np.zeros((M, 2))
+        self._check(_lib.sgs_get_state(self._ctx, instance, _ptr(g), _ptr(lam)))
+        return g, lam[:, 0] + 1j * lam[:, 1]
+
+    def set_state(self, gamma, lam=None, instance=0):
+        g = np.ascontiguousarray(gamma, dtype=np.float64)
+        l2 = None if lam is None else np.ascontiguousarray(np.stack([np.real(lam), np.imag(lam)], -1))
+        self._check(_lib.sgs_set_state(self._ctx, instance, _ptr(g), _ptr(l2)))
+
+    def pair_matrices(self, instance=0):
+        M, _ = self.shapes[instance]
+        G = np.zeros((M, M, 2))
+        h = np.zeros((M, M, 2))
+        self._check(_lib.sgs_get_pair_matrices(self._ctx, instance, _ptr(G), _ptr(h)))
+        return G[..., 0] + 1j * G[..., 1], h[..., 0] + 1j * h[..., 1]
+
+    def derivative(self, instance=0):
+        M, n = self.shapes[instance]
+        d = np.zeros((M, n, n))
+        self._check(_lib.sgs_get_derivative(self._ctx, instance, _ptr(d)))
+        return d
+
+    STAGES = ("pair_inverse", "pair_delta", "phase_pfaffian", "amplitudes", "eom_gemm", "eom_assembly", "update")
+
+    def set_profiling(self, enable=True):
+        self._check(_lib.sgs_set_profiling(self._ctx, 1 if enable else 0))
+
+    def profile(self):
+        """{stage: (ms, flops, bytes)}, launches"""
+        k = len(self.STAGES)
+        ms, fl, by = np.zeros(k), np.zeros(k), np.zeros(k)
+        nl = ctypes.c_longlong(0)
+        self._check(_lib.sgs_get_profile(self._ctx, _ptr(ms), _ptr(fl), _ptr(by), ctypes.byref(nl)))
+        return {s: (ms[i], fl[i], by[i]) for i, s in enumerate(self.STAGES)}, nl.value
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            _lib.sgs_free(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        self.close()
+
+
+# ------------------------------------------------------------ building blocks
+
+def probe_peak(kind=0):
+    """Measured TFLOP/s of the FP64 MMA (kind 0) or FP64 FMA (kind 1) pipe."""
+    out = np.zeros(1)
+    st = _lib.sgs_probe_peak(kind, _ptr(out))
+    if st != 0:
+        raise SGSError(st, "probe")
+    return float(out[0])
+
+
+def batched_inverse(S):
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    b, n, _ = S.shape
+    out = np.zeros_like(S)
+    ld = np.zeros(b)
+    st = _lib.sgs_kernel_inverse(_ptr(S), n, b, _ptr(out), _ptr(ld))
+    if st != 0:
+        raise SGSError(st, "batched inverse")
+    return out, ld
+
+
+def batched_pfaffian(Y):
+    Y = np.ascontiguousarray(Y, dtype=np.complex128)
+    b, n, _ = Y.shape
+    yv = Y.view(np.float64)
+    ph = np.zeros((b, 2))
+    la = np.zeros(b)
+    st = _lib.sgs_kernel_pfaffian(_ptr(yv), n, b, _ptr(ph), _ptr(la))
+    if st != 0:
+        raise SGSError(st, "batched pfaffian")
+    return ph[:, 0] + 1j * ph[:, 1], la
+
+
+def batched_dgemm(A, B):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    b, n, _ = A.shape
+    C = np.zeros_like(A)
+    st = _lib.sgs_kernel_dgemm(_ptr(A), _ptr(B), n, b, _ptr(C))
+    if st != 0:
+        raise SGSError(st, "batched dgemm")
+    return C

@@ -1,0 +1,331 @@
+// Batched FP64 factorisations of the pair matrices.
+//
+//  * Gauss-Jordan inverse with partial pivoting of S = Gamma_a + Gamma_b
+//    (Eq. def-delta-matrix needs S^{-1}; |Pf S| = |det S|^{1/2} gives the
+//    overlap magnitude of Sec. II B).  Blocked: a panel kernel eliminates b
+//    columns of every matrix (one CTA per matrix, panel in shared memory),
+//    then one batched DMMA GEMM applies the delayed rank-b update to the
+//    rest of each matrix.
+//  * Complex Pfaffian of Y = Gamma_0 + Delta^{a,b} (the phase of the overlap
+//    in the reference gauge of Sec. II B) by Parlett-Reid elimination with
+//    pivoting, blocked the same way: the panel kernel performs b elimination
+//    steps, materialising the two columns each step needs from the stored
+//    matrix plus the pending rank-2 updates, and the rank-2b trailing update
+//    is two real DMMA GEMMs (real and imaginary parts, k = 4b).
+#pragma once
+#include "common.cuh"
+
+namespace sgs {
+
+// ---------------------------------------------------------------- Gauss-Jordan
+
+struct GJPanelArgs {
+    double* const* W;        // [batch] n x n working matrices (row-major)
+    double* const* T;        // [batch] bb x n copy of the panel rows (update operand)
+    int* piv;                // [batch][n]
+    double* logdet;          // [batch] log|det S|
+    double* dsign;           // [batch] sign(det S)
+    int* err;                // error word (SGS_DEV_SINGULAR)
+    int n, k0, bb;
+    double tiny;             // a pivot of magnitude <= tiny counts as singular
+};
+
+__global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
+    extern __shared__ double sm[];
+    double* panel = sm;                       // n x bb
+    double* rowc = panel + (size_t)a.n * a.bb; // bb
+    __shared__ double red_v[32];
+    __shared__ int red_i[32];
+    __shared__ double s_logdet, s_sign;
+
+    const int b = blockIdx.x, n = a.n, k0 = a.k0, bb = a.bb;
+    double* W = a.W[b];
+    int* piv = a.piv + (size_t)b * n;
+
+    for (int e = threadIdx.x; e < n * bb; e += blockDim.x) {
+        int r = e / bb, q = e % bb;
+        panel[e] = W[(size_t)r * n + k0 + q];
+    }
+    if (threadIdx.x == 0) {
+        s_logdet = (k0 == 0) ? 0.0 : a.logdet[b];
+        s_sign = (k0 == 0) ? 1.0 : a.dsign[b];
+    }
+    __syncthreads();
+
+    for (int j = 0; j < bb; j++) {
+        const int c = k0 + j;
+        double best = -1.0;
+        int bi = 0x7fffffff;
+        for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+            double v = fabs(panel[r * bb + j]);
+            if (v > best) { best = v; bi = r; }
+        }
+        double mv;
+        int p;
+        block_argmax(best, bi, red_v, red_i, mv, p);
+        if (!(mv > a.tiny)) {          // singular (or NaN): flag, keep going with p = c
+            if (threadIdx.x == 0) { atomicOr(a.err, SGS_DEV_SINGULAR); s_logdet = -INFINITY; }
+            p = c;
+        }
+        if (p != c) {
+            for (int q = threadIdx.x; q < bb; q += blockDim.x) {
+                double t = panel[c * bb + q];
+                panel[c * bb + q] = panel[p * bb + q];
+                panel[p * bb + q] = t;
+            }
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                if (q >= k0 && q < k0 + bb) continue;
+                double t = W[(size_t)c * n + q];
+                W[(size_t)c * n + q] = W[(size_t)p * n + q];
+                W[(size_t)p * n + q] = t;
+            }
+        }
+        if (threadIdx.x == 0) piv[c] = p;
+        __syncthreads();
+        double pv = panel[c * bb + j];
+        if (!(mv > a.tiny)) pv = 1.0;
+        if (threadIdx.x == 0) {
+            if (mv > a.tiny) s_logdet += log(fabs(pv));
+            s_sign *= (pv < 0.0 ? -1.0 : 1.0) * (p != c ? -1.0 : 1.0);
+        }
+        const double inv = 1.0 / pv;
+        for (int q = threadIdx.x; q < bb; q += blockDim.x) {
+            double v = (q == j) ? inv : panel[c * bb + q] * inv;
+            rowc[q] = v;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < bb; q += blockDim.x) panel[c * bb + q] = rowc[q];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            if (r == c) continue;
+            double f = panel[r * bb + j];
+            if (f != 0.0) {
+                for (int q = 0; q < bb; q++)
+                    if (q != j) panel[r * bb + q] -= f * rowc[q];
+            }
+            panel[r * bb + j] = -f * inv;
+        }
+        __syncthreads();
+    }
+
+    for (int e = threadIdx.x; e < n * bb; e += blockDim.x) {
+        int r = e / bb, q = e % bb;
+        W[(size_t)r * n + k0 + q] = panel[e];
+    }
+    __syncthreads();
+    double* T = a.T[b];
+    for (int e = threadIdx.x; e < bb * n; e += blockDim.x) {
+        int r = e / n, q = e % n;
+        T[(size_t)r * n + q] = (q >= k0 && q < k0 + bb) ? 0.0 : W[(size_t)(k0 + r) * n + q];
+    }
+    if (threadIdx.x == 0) { a.logdet[b] = s_logdet; a.dsign[b] = s_sign; }
+}
+
+// Undo the row interchanges of Gauss-Jordan: inverse = X P, i.e. the column
+// interchanges applied in reverse order.  perm[c] = source column of column c.
+__global__ void gj_perm_kernel(const int* piv, int* perm, int n, int batch) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const int* pv = piv + (size_t)b * n;
+    int* pm = perm + (size_t)b * n;
+    for (int c = 0; c < n; c++) pm[c] = c;
+    for (int j = n - 1; j >= 0; j--) {
+        int p = pv[j];
+        if (p != j) { int t = pm[j]; pm[j] = pm[p]; pm[p] = t; }
+    }
+}
+
+__global__ void gj_gather_kernel(double* const* W, double* const* out, const int* perm, int n) {
+    const int b = blockIdx.y;
+    const int* pm = perm + (size_t)b * n;
+    const double* src = W[b];
+    double* dst = out[b];
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)n * n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(e / n), c = (int)(e % n);
+        dst[e] = src[(size_t)r * n + pm[c]];
+    }
+}
+
+// ---------------------------------------------------------------- Pfaffian
+
+struct PfPanelArgs {
+    double* const* Y;        // [batch] planes: Re (n x n) then Im (n x n)
+    double* const* TU;       // [batch] 4 x n x bs scratch: Tr, Ti, Ur, Ui (column t = step)
+    double* const* PA;       // [batch] packs, 4 consecutive n x 4bs blocks:
+                             //   A_re=[Tr,-Ti,-Ur,Ui] B_re=[Ur,Ui,Tr,Ti] A_im=[Tr,Ti,-Ur,-Ui] B_im=[Ui,Ur,Ti,Tr]
+    double* logabs;          // [batch]
+    double* phase;           // [batch][2]
+    int* err;
+    int n, k0, bs;           // bs = elimination steps in this panel
+    int bsmax;               // pack blocks are n x 4*bsmax apart (row stride 4*bs)
+};
+
+__global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
+    extern __shared__ double sm[];
+    const int n = a.n, k0 = a.k0, bs = a.bs;
+    double* ckr = sm;            // current column k (real)
+    double* cki = ckr + n;
+    double* c1r = cki + n;       // current column k+1
+    double* c1i = c1r + n;
+    double* rowTU = c1i + n;     // 4 x bs: T/U entries of the row being materialised
+    __shared__ double red_v[32];
+    __shared__ int red_i[32];
+    __shared__ double s_log, s_pr, s_pi;
+
+    const int b = blockIdx.x;
+    double* Yr = a.Y[b];
+    double* Yi = Yr + (size_t)n * n;
+    double* Tr = a.TU[b];
+    double* Ti = Tr + (size_t)n * bs;
+    double* Ur = Ti + (size_t)n * bs;
+    double* Ui = Ur + (size_t)n * bs;
+
+    if (threadIdx.x == 0) {
+        s_log = (k0 == 0) ? 0.0 : a.logabs[b];
+        s_pr = (k0 == 0) ? 1.0 : a.phase[2 * b];
+        s_pi = (k0 == 0) ? 0.0 : a.phase[2 * b + 1];
+    }
+
+    for (int s = 0; s < bs; s++) {
+        const int k = k0 + 2 * s;
+        // row k of the pending vectors
+        for (int t = threadIdx.x; t < s; t += blockDim.x) {
+            rowTU[t] = Tr[(size_t)k * bs + t];
+            rowTU[bs + t] = Ti[(size_t)k * bs + t];
+            rowTU[2 * bs + t] = Ur[(size_t)k * bs + t];
+            rowTU[3 * bs + t] = Ui[(size_t)k * bs + t];
+        }
+        __syncthreads();
+        // current column k: Y[i][k] + sum_t (T[i][t] U[k][t] - U[i][t] T[k][t])
+        double best = -1.0;
+        int bi = 0x7fffffff;
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            double vr = Yr[(size_t)i * n + k], vi = Yi[(size_t)i * n + k];
+            for (int t = 0; t < s; t++) {
+                double tr = Tr[(size_t)i * bs + t], ti = Ti[(size_t)i * bs + t];
+                double ur = Ur[(size_t)i * bs + t], ui = Ui[(size_t)i * bs + t];
+                double Ukr = rowTU[2 * bs + t], Uki = rowTU[3 * bs + t];
+                double Tkr = rowTU[t], Tki = rowTU[bs + t];
+                vr += tr * Ukr - ti * Uki - (ur * Tkr - ui * Tki);
+                vi += tr * Uki + ti * Ukr - (ur * Tki + ui * Tkr);
+            }
+            ckr[i] = vr;
+            cki[i] = vi;
+            double m = vr * vr + vi * vi;
+            if (m > best) { best = m; bi = i; }
+        }
+        double mv;
+        int p;
+        block_argmax(best, bi, red_v, red_i, mv, p);
+        if (!(mv > 0.0)) {
+            if (threadIdx.x == 0) { atomicOr(a.err, SGS_DEV_PF_ZERO); s_log = -INFINITY; }
+            p = k + 1;
+        }
+        if (p != k + 1) {
+            const int q = k + 1;
+            // symmetric interchange q <-> p on the live part (rows/cols >= k)
+            for (int j = k + threadIdx.x; j < n; j += blockDim.x) {
+                double t;
+                t = Yr[(size_t)q * n + j]; Yr[(size_t)q * n + j] = Yr[(size_t)p * n + j]; Yr[(size_t)p * n + j] = t;
+                t = Yi[(size_t)q * n + j]; Yi[(size_t)q * n + j] = Yi[(size_t)p * n + j]; Yi[(size_t)p * n + j] = t;
+            }
+            __syncthreads();
+            for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+                double t;
+                t = Yr[(size_t)i * n + q]; Yr[(size_t)i * n + q] = Yr[(size_t)i * n + p]; Yr[(size_t)i * n + p] = t;
+                t = Yi[(size_t)i * n + q]; Yi[(size_t)i * n + q] = Yi[(size_t)i * n + p]; Yi[(size_t)i * n + p] = t;
+            }
+            for (int t = threadIdx.x; t < s; t += blockDim.x) {
+                double x;
+                x = Tr[(size_t)q * bs + t]; Tr[(size_t)q * bs + t] = Tr[(size_t)p * bs + t]; Tr[(size_t)p * bs + t] = x;
+                x = Ti[(size_t)q * bs + t]; Ti[(size_t)q * bs + t] = Ti[(size_t)p * bs + t]; Ti[(size_t)p * bs + t] = x;
+                x = Ur[(size_t)q * bs + t]; Ur[(size_t)q * bs + t] = Ur[(size_t)p * bs + t]; Ur[(size_t)p * bs + t] = x;
+                x = Ui[(size_t)q * bs + t]; Ui[(size_t)q * bs + t] = Ui[(size_t)p * bs + t]; Ui[(size_t)p * bs + t] = x;
+            }
+            if (threadIdx.x == 0) {
+                double x = ckr[q]; ckr[q] = ckr[p]; ckr[p] = x;
+                x = cki[q]; cki[q] = cki[p]; cki[p] = x;
+                s_pr = -s_pr; s_pi = -s_pi;
+            }
+        }
+        __syncthreads();
+        // row k+1 of the pending vectors, then current column k+1 (rows >= k+2)
+        for (int t = threadIdx.x; t < s; t += blockDim.x) {
+            rowTU[t] = Tr[(size_t)(k + 1) * bs + t];
+            rowTU[bs + t] = Ti[(size_t)(k + 1) * bs + t];
+            rowTU[2 * bs + t] = Ur[(size_t)(k + 1) * bs + t];
+            rowTU[3 * bs + t] = Ui[(size_t)(k + 1) * bs + t];
+        }
+        __syncthreads();
+        for (int i = k + 2 + threadIdx.x; i < n; i += blockDim.x) {
+            double vr = Yr[(size_t)i * n + k + 1], vi = Yi[(size_t)i * n + k + 1];
+            for (int t = 0; t < s; t++) {
+                double tr = Tr[(size_t)i * bs + t], ti = Ti[(size_t)i * bs + t];
+                double ur = Ur[(size_t)i * bs + t], ui = Ui[(size_t)i * bs + t];
+                double Ukr = rowTU[2 * bs + t], Uki = rowTU[3 * bs + t];
+                double Tkr = rowTU[t], Tki = rowTU[bs + t];
+                vr += tr * Ukr - ti * Uki - (ur * Tkr - ui * Tki);
+                vi += tr * Uki + ti * Ukr - (ur * Tki + ui * Tkr);
+            }
+            c1r[i] = vr;
+            c1i[i] = vi;
+        }
+        // pivot Y[k][k+1] = -Y[k+1][k]
+        double pr = -ckr[k + 1], pi = -cki[k + 1];
+        if (!(mv > 0.0)) { pr = 1.0; pi = 0.0; }
+        const double pm2 = pr * pr + pi * pi;
+        if (threadIdx.x == 0) {
+            if (mv > 0.0) {
+                double am = sqrt(pm2);
+                s_log += log(am);
+                double ur = pr / am, ui = pi / am;
+                double nr = s_pr * ur - s_pi * ui, ni = s_pr * ui + s_pi * ur;
+                s_pr = nr; s_pi = ni;
+            }
+        }
+        __syncthreads();
+        // tau = (row k)/pivot = -(column k)/pivot, u = column k+1; zero above k+2
+        const double ir = pr / pm2, ii = -pi / pm2;   // 1/pivot
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double tr = 0.0, ti = 0.0, ur = 0.0, ui = 0.0;
+            if (i >= k + 2) {
+                double xr = -ckr[i], xi = -cki[i];
+                tr = xr * ir - xi * ii;
+                ti = xr * ii + xi * ir;
+                ur = c1r[i];
+                ui = c1i[i];
+            }
+            Tr[(size_t)i * bs + s] = tr;
+            Ti[(size_t)i * bs + s] = ti;
+            Ur[(size_t)i * bs + s] = ur;
+            Ui[(size_t)i * bs + s] = ui;
+        }
+        __syncthreads();
+    }
+
+    // packs for the trailing update (rows >= k0 + 2 bs are the only ones used)
+    const int e0 = k0 + 2 * bs;
+    const int kk = 4 * bs;
+    double* PAre = a.PA[b];
+    const size_t blk = (size_t)n * 4 * a.bsmax;
+    double* PBre = PAre + blk;
+    double* PAim = PBre + blk;
+    double* PBim = PAim + blk;
+    for (int e = threadIdx.x; e < (n - e0) * bs; e += blockDim.x) {
+        int i = e0 + e / bs, t = e % bs;
+        double tr = Tr[(size_t)i * bs + t], ti = Ti[(size_t)i * bs + t];
+        double ur = Ur[(size_t)i * bs + t], ui = Ui[(size_t)i * bs + t];
+        size_t row = (size_t)i * kk;
+        PAre[row + t] = tr; PAre[row + bs + t] = -ti; PAre[row + 2 * bs + t] = -ur; PAre[row + 3 * bs + t] = ui;
+        PBre[row + t] = ur; PBre[row + bs + t] = ui;  PBre[row + 2 * bs + t] = tr;  PBre[row + 3 * bs + t] = ti;
+        PAim[row + t] = tr; PAim[row + bs + t] = ti;  PAim[row + 2 * bs + t] = -ur; PAim[row + 3 * bs + t] = -ui;
+        PBim[row + t] = ui; PBim[row + bs + t] = ur;  PBim[row + 2 * bs + t] = ti;  PBim[row + 3 * bs + t] = tr;
+    }
+    if (threadIdx.x == 0) {
+        a.logabs[b] = s_log;
+        a.phase[2 * b] = s_pr;
+        a.phase[2 * b + 1] = s_pi;
+    }
+}
+
+}  // namespace sgs

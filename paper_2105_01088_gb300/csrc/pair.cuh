@@ -1,0 +1,232 @@
+// Pair-level kernels of one imaginary-time step (Sec. II B-C, III B).
+//
+// For an unordered pair (a < b): S = Gamma_a + Gamma_b, D = Gamma_a - Gamma_b,
+// Si = S^{-1}, Im = D Si, and the transition matrix of Eq. (def-delta-matrix)
+//   Delta^{a,b} = (iD - 2) Si = -2 Si + i Im,   Delta^{b,a} = conj(Delta^{a,b}).
+// Because D S = -S D for pure states, Delta^{a,b} = -Si (iD + 2) too, so
+//   Q = Delta F Delta = -(iD - 2) W (iD + 2),  W = Si F Si,
+//     = D W D - 2i (D W - W D) + 4 W,
+// and with F = Fr + i Fi (Fi non-zero only on the impurity block) every
+// dense product is real: Wr = (Si Fr) Si, V = D Wr, X = V D, W D = (D W)^T;
+// the Fi parts are rank <= (#impurity Majoranas) corrections.
+#pragma once
+#include "common.cuh"
+
+namespace sgs {
+
+struct InstDev {
+    int n, N, M, P, Ppf, nimp, nq;
+    double e_const;
+    double parity;
+    const int* pa;          // [P] first state of pair p
+    const int* pb;          // [P] second state
+    const int* pf_pair;     // [Ppf] pair of each phase-Pfaffian entry (pairs with a >= 1)
+    const int* pair_pf;     // [P] phase-Pfaffian entry of pair p, or -1 (a == 0)
+    const double* gamma;    // [M][n][n]
+    const int* a_rowptr;    // CSR of A (n+1)
+    const int* a_row;       // row of each non-zero (COO view of the same entries)
+    const int* a_col;
+    int a_nnz;
+    const double* a_val;
+    const int* q_idx;       // [nq][4] antisymmetrised quartic entries
+    const double* q_val;    // [nq]
+    const int* imp;         // [nimp] impurity Majoranas
+    const int* slot;        // [n] slot in imp, or -1
+};
+
+__device__ __forceinline__ size_t nn(const InstDev& d) { return (size_t)d.n * d.n; }
+
+// S_p = Gamma_a + Gamma_b into the Gauss-Jordan work matrix of pair p
+__global__ void pair_sum_kernel(InstDev d, double* work) {
+    const int p = blockIdx.y;
+    const double* ga = d.gamma + (size_t)d.pa[p] * nn(d);
+    const double* gb = d.gamma + (size_t)d.pb[p] * nn(d);
+    double* w = work + (size_t)p * nn(d);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn(d); e += (size_t)gridDim.x * blockDim.x)
+        w[e] = ga[e] + gb[e];
+}
+
+// Y_q = Gamma_0 + Delta^{a,b} = (Gamma_0 - 2 Si) + i Im for the phase Pfaffian
+__global__ void pf_build_kernel(InstDev d, const double* si, const double* imd, double* work) {
+    const int q = blockIdx.y;
+    const int p = d.pf_pair[q];
+    const double* g0 = d.gamma;
+    const double* s = si + (size_t)p * nn(d);
+    const double* im = imd + (size_t)p * nn(d);
+    double* yr = work + (size_t)q * 2 * nn(d);
+    double* yi = yr + nn(d);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn(d); e += (size_t)gridDim.x * blockDim.x) {
+        yr[e] = g0[e] - 2.0 * s[e];
+        yi[e] = im[e];
+    }
+}
+
+// Gram matrix, Hamiltonian matrix and the impurity block of the generalised
+// Fock matrices.  Blocks [0, P): pairs; blocks [P, P+M): diagonal states.
+//   G_ab = |G_ab| e^{i phi}, log|G_ab| = (-N log 2 + log|det S|/2)/2,
+//   phase from Pf(Gamma_0) Pf(Gamma_0 + Delta^{a,b}) (reference gauge), and
+//   h_ba = G_ba (e_const + Tr(A Delta^{a,b}) - 3 sum U Delta Delta).
+__global__ void __launch_bounds__(256) pair_gh_kernel(InstDev d, const double* si, const double* imd,
+                                                      const double* logdet, const double* pfphase,
+                                                      double* Gm, double* hm, double* fimp, double* fimp_state) {
+    __shared__ double red[32];
+    const int blk = blockIdx.x;
+    const bool diag = blk >= d.P;
+    const int p = diag ? -1 : blk;
+    const int a = diag ? blk - d.P : d.pa[p];
+    const int bq = diag ? a : d.pb[p];
+    const int n = d.n;
+    const double* dr = diag ? d.gamma + (size_t)a * nn(d) : si + (size_t)p * nn(d);
+    const double* di = diag ? nullptr : imd + (size_t)p * nn(d);
+    // Delta^{a,b}[k][l] = -2 Si[k][l] + i Im[k][l];  Delta^{a,a} = Gamma_a
+    auto delta = [&](int k, int l) -> cplx {
+        if (diag) return cmk(dr[(size_t)k * n + l], 0.0);
+        return cmk(-2.0 * dr[(size_t)k * n + l], di[(size_t)k * n + l]);
+    };
+    // Tr(A Delta) = sum_kl A_kl Delta_lk over the non-zeros of A
+    double tr_r = 0.0, tr_i = 0.0;
+    for (int e = threadIdx.x; e < d.a_nnz; e += blockDim.x) {
+        cplx v = delta(d.a_col[e], d.a_row[e]);
+        tr_r += d.a_val[e] * v.x;
+        tr_i += d.a_val[e] * v.y;
+    }
+    tr_r = block_sum(tr_r, red);
+    tr_i = block_sum(tr_i, red);
+    if (threadIdx.x == 0) {
+        cplx q = cmk(0.0, 0.0);
+        const int ni = d.nimp;
+        cplx F[SGS_MAX_IMP * SGS_MAX_IMP];
+        for (int e = 0; e < ni * ni; e++) F[e] = cmk(0.0, 0.0);
+        for (int e = 0; e < d.nq; e++) {
+            const int* ix = d.q_idx + 4 * e;
+            const double v = d.q_val[e];
+            cplx x = delta(ix[2], ix[3]);
+            q = cadd(q, cscale(cmul(delta(ix[0], ix[1]), x), v));
+            int s0 = d.slot[ix[0]], s1 = d.slot[ix[1]];
+            F[s0 * ni + s1] = cadd(F[s0 * ni + s1], cscale(x, 6.0 * v));
+        }
+        cplx dens = cmk(d.e_const + tr_r - 3.0 * q.x, tr_i - 3.0 * q.y);
+        const int M = d.M;
+        if (diag) {
+            Gm[2 * (a * M + a)] = 1.0;
+            Gm[2 * (a * M + a) + 1] = 0.0;
+            hm[2 * (a * M + a)] = dens.x;
+            hm[2 * (a * M + a) + 1] = 0.0;
+            for (int e = 0; e < ni * ni; e++) fimp_state[(size_t)a * ni * ni + e] = F[e].x;
+        } else {
+            double ld = logdet[p];
+            double mag = (ld == -INFINITY || ld != ld) ? 0.0 : exp(0.5 * (-d.N * 0.6931471805599453 + 0.5 * ld));
+            cplx ph = cmk(1.0, 0.0);
+            int q2 = d.pair_pf[p];
+            if (q2 >= 0) {
+                ph = cmk(d.parity * pfphase[2 * q2], d.parity * pfphase[2 * q2 + 1]);
+                double m2 = sqrt(cabs2(ph));
+                ph = m2 > 0.0 ? cscale(ph, 1.0 / m2) : cmk(0.0, 0.0);
+            }
+            cplx gab = cscale(ph, mag);
+            cplx gba = cconj(gab);
+            cplx hba = cmul(gba, dens);
+            Gm[2 * (a * M + bq)] = gab.x;
+            Gm[2 * (a * M + bq) + 1] = gab.y;
+            Gm[2 * (bq * M + a)] = gba.x;
+            Gm[2 * (bq * M + a) + 1] = gba.y;
+            hm[2 * (bq * M + a)] = hba.x;
+            hm[2 * (bq * M + a) + 1] = hba.y;
+            hm[2 * (a * M + bq)] = hba.x;
+            hm[2 * (a * M + bq) + 1] = -hba.y;
+            double* fp = fimp + (size_t)p * ni * ni * 2;
+            for (int e = 0; e < ni * ni; e++) { fp[2 * e] = F[e].x; fp[2 * e + 1] = F[e].y; }
+        }
+    }
+}
+
+// T1_p = Si (A + Re Fimp^{a,b}):  (Si A)[k][l] = -sum_{(m,v) in row l of A} Si[k][m] v
+__global__ void pair_sparse_right_kernel(InstDev d, const double* si, const double* fimp, double* t1) {
+    const int p = blockIdx.y;
+    const int n = d.n, ni = d.nimp;
+    const double* s = si + (size_t)p * nn(d);
+    const double* fp = fimp + (size_t)p * ni * ni * 2;
+    double* out = t1 + (size_t)p * nn(d);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn(d); e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n), l = (int)(e % n);
+        const double* srow = s + (size_t)k * n;
+        double v = 0.0;
+        for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) v -= srow[d.a_col[q]] * d.a_val[q];
+        const int sl = d.slot[l];
+        if (sl >= 0)
+            for (int m = 0; m < ni; m++) v += srow[d.imp[m]] * fp[2 * (m * ni + sl)];
+        out[e] = v;
+    }
+}
+
+// T2_mu = F_mu Gamma_mu with F_mu = A + 6 U:Gamma_mu (real)
+__global__ void state_sparse_left_kernel(InstDev d, const double* fimp_state, double* t2) {
+    const int mu = blockIdx.y;
+    const int n = d.n, ni = d.nimp;
+    const double* g = d.gamma + (size_t)mu * nn(d);
+    const double* fs = fimp_state + (size_t)mu * ni * ni;
+    double* out = t2 + (size_t)mu * nn(d);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn(d); e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n), l = (int)(e % n);
+        double v = 0.0;
+        for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) v += d.a_val[q] * g[(size_t)d.a_col[q] * n + l];
+        const int sk = d.slot[k];
+        if (sk >= 0)
+            for (int m = 0; m < ni; m++) v += fs[sk * ni + m] * g[(size_t)d.imp[m] * n + l];
+        out[e] = v;
+    }
+}
+
+// L1 = Im[:, imp] Fi, L2 = Si[:, imp] Fi  (n x nimp each), Fi = Im Fimp^{a,b}
+__global__ void pair_lr_kernel(InstDev d, const double* si, const double* imd, const double* fimp, double* lr) {
+    const int p = blockIdx.y;
+    const int n = d.n, ni = d.nimp;
+    const double* s = si + (size_t)p * nn(d);
+    const double* im = imd + (size_t)p * nn(d);
+    const double* fp = fimp + (size_t)p * ni * ni * 2;
+    double* L1 = lr + (size_t)p * 2 * n * ni;
+    double* L2 = L1 + (size_t)n * ni;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * ni; e += gridDim.x * blockDim.x) {
+        const int k = e / ni, j = e % ni;
+        double v1 = 0.0, v2 = 0.0;
+        for (int m = 0; m < ni; m++) {
+            double fi = fp[2 * (m * ni + j) + 1];
+            v1 += im[(size_t)k * n + d.imp[m]] * fi;
+            v2 += s[(size_t)k * n + d.imp[m]] * fi;
+        }
+        L1[e] = v1;
+        L2[e] = v2;
+    }
+}
+
+// Q = Delta F Delta (real and imaginary planes), in place of X (-> Qr) and Wr (-> Qi):
+//   Qr = X + 4 Wr + 2 (L1 Si[imp,:] + Si[:,imp] L1^T)
+//   Qi = 4 L2 Si[imp,:] - L1 Im[imp,:] - 2 (V - V^T)
+__global__ void pair_q_kernel(InstDev d, const double* si, const double* imd, const double* lr,
+                              const double* va, double* xa_qr, double* wr_qi) {
+    const int p = blockIdx.y;
+    const int n = d.n, ni = d.nimp;
+    const double* s = si + (size_t)p * nn(d);
+    const double* im = imd + (size_t)p * nn(d);
+    const double* L1 = lr + (size_t)p * 2 * n * ni;
+    const double* L2 = L1 + (size_t)n * ni;
+    const double* v = va + (size_t)p * nn(d);
+    double* X = xa_qr + (size_t)p * nn(d);
+    double* Wq = wr_qi + (size_t)p * nn(d);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn(d); e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n), l = (int)(e % n);
+        double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        for (int m = 0; m < ni; m++) {
+            const int im_m = d.imp[m];
+            const double s_ml = s[(size_t)im_m * n + l];
+            a1 += L1[k * ni + m] * s_ml + s[(size_t)k * n + im_m] * L1[l * ni + m];
+            a2 += 4.0 * L2[k * ni + m] * s_ml - L1[k * ni + m] * im[(size_t)im_m * n + l];
+        }
+        const double qr = X[e] + 4.0 * Wq[e] + 2.0 * a1;
+        const double qi = a2 - 2.0 * (v[e] - v[(size_t)l * n + k]);
+        X[e] = qr;
+        Wq[e] = qi;
+    }
+}
+
+}  // namespace sgs

@@ -1,0 +1,1005 @@
+// Host side of the SGS imaginary-time step library: context, device
+// buffers, the per-step launch sequence and the C ABI of include/sgs.h.
+//
+// One step (Sec. III C) per instance, all on one CUDA stream:
+//   pairs:   S = G_a + G_b -> blocked Gauss-Jordan (S^{-1}, log|det S|)
+//            Im = (G_a - G_b) S^{-1}                        [Eq. def-delta-matrix]
+//            Y = G_0 + Delta^{a,b} -> blocked complex Pfaffian (overlap phase)
+//            G_ab, h_ab, impurity block of F^{a,b}          [Sec. II B-C, III B]
+//   amplitudes: h lambda = E G lambda                        [Eq. eigLambda]
+//   EOM:     W = S^{-1} F S^{-1}, V = D W, X = V D, Q = Delta F Delta,
+//            dGamma^mu = sum_beta ...                        [Eq. EOM-Gamma3]
+//   update:  R = exp{(ds/4)[G, dG]}, G <- R G R^T, Newton-Schulz polar factor
+//                                                            [App. A]
+#include "../../include/sgs.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "gemm_f64.cuh"
+#include "factor.cuh"
+#include "pair.cuh"
+#include "eig.cuh"
+#include "eom.cuh"
+#include "update.cuh"
+#include "probe.cuh"
+
+using namespace sgs;
+
+namespace {
+
+// kernels launched by this library (host-side count; sgs_get_profile reports
+// the share of each context)
+long long g_launches = 0;
+inline void counted() { ++g_launches; }
+
+sgs_alloc_fn g_alloc = nullptr;
+sgs_free_fn g_release = nullptr;
+void* g_user = nullptr;
+
+struct Instance {
+    int N = 0, n = 0, M = 0, P = 0, Ppf = 0, nimp = 0, nq = 0, a_nnz = 0;
+    double dtau = 0.0, e_const = 0.0;
+    int prec = 0, cmode = 0, parity = 1;
+    int gj_b = 32, pf_bs = 16;
+    std::vector<int> h_pa, h_pb;
+
+    double *gamma = nullptr, *dgamma = nullptr;
+    int *pa = nullptr, *pb = nullptr, *pf_pair = nullptr, *pair_pf = nullptr, *pair_index = nullptr;
+    int *a_rowptr = nullptr, *a_row = nullptr, *a_col = nullptr;
+    double* a_val = nullptr;
+    int* q_idx = nullptr;
+    double* q_val = nullptr;
+    int *imp = nullptr, *slot = nullptr;
+
+    double *work = nullptr, *si = nullptr, *imd = nullptr, *wr = nullptr, *va = nullptr, *xa = nullptr;
+    double* tbuf = nullptr;
+    int *piv = nullptr, *perm = nullptr;
+    double *logdet = nullptr, *dsign = nullptr;
+    double *pfTU = nullptr, *pfpack = nullptr, *pflog = nullptr, *pfphase = nullptr;
+    double *fimp = nullptr, *fimp_state = nullptr, *lr = nullptr;
+    double* s[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int* sq = nullptr;
+    double* scale = nullptr;
+    double *Gm = nullptr, *hm = nullptr, *lam = nullptr, *lt = nullptr, *coef = nullptr;
+    double* Ehist = nullptr;
+    int Ecap = 0;
+    int steps_since_profile = 0;
+    double* eigscratch = nullptr;
+    int* err = nullptr;
+
+    // pointer arrays (device)
+    double **p_work = nullptr, **p_tbuf = nullptr, **p_si = nullptr, **p_imd = nullptr, **p_wr = nullptr,
+           **p_va = nullptr, **p_xa = nullptr, **p_ga = nullptr, **p_gb = nullptr;
+    double **p_Y = nullptr, **p_TU = nullptr, **p_pack = nullptr;
+    double **p_upA = nullptr, **p_upB = nullptr, **p_upC = nullptr;   // Pfaffian update (2 Ppf)
+    double **p_gamma = nullptr, **p_dgamma = nullptr, **p_s[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+
+    InstDev dev() const {
+        InstDev d{};
+        d.n = n; d.N = N; d.M = M; d.P = P; d.Ppf = Ppf; d.nimp = nimp; d.nq = nq;
+        d.e_const = e_const; d.parity = (double)parity;
+        d.pa = pa; d.pb = pb; d.pf_pair = pf_pair; d.pair_pf = pair_pf; d.gamma = gamma;
+        d.a_rowptr = a_rowptr; d.a_row = a_row; d.a_col = a_col; d.a_nnz = a_nnz; d.a_val = a_val;
+        d.q_idx = q_idx; d.q_val = q_val; d.imp = imp; d.slot = slot;
+        return d;
+    }
+};
+
+}  // namespace
+
+struct sgs_ctx {
+    std::vector<Instance> inst;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<void*> allocs;
+    int device = 0;
+
+    void* dalloc(size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        void* p = nullptr;
+        if (g_alloc) {
+            p = g_alloc(bytes, (void*)stream, g_user);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            p = nullptr;
+        }
+        if (p) allocs.push_back(p);
+        return p;
+    }
+    template <class T>
+    T* alloc(size_t count) { return static_cast<T*>(dalloc(count * sizeof(T))); }
+    sgs_free_fn release = nullptr;   // hook captured at creation, used for every free
+    void* release_user = nullptr;
+    void release_all() {
+        for (void* p : allocs) {
+            if (release) release(p, release_user);
+            else cudaFree(p);
+        }
+        allocs.clear();
+    }
+    sgs_ctx() : release(g_alloc ? g_release : nullptr), release_user(g_user) {}
+
+    // stage timing (CUDA events on the context stream) and algorithmic work
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Mark { int stage; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    int open_stage = -1;
+    cudaEvent_t open_ev = nullptr;
+    double stage_ms[SGS_N_STAGES] = {0};
+    double stage_flops[SGS_N_STAGES] = {0};
+    double stage_bytes[SGS_N_STAGES] = {0};
+    long long launches = 0;
+
+    cudaEvent_t next_event() {
+        if (ev_used == ev_pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ev_pool.push_back(e);
+        }
+        return ev_pool[ev_used++];
+    }
+    void stage(int s) {            // close the open stage, open stage s (-1: none)
+        if (!prof) return;
+        cudaEvent_t e = next_event();
+        cudaEventRecord(e, stream);
+        if (open_stage >= 0) marks.push_back({open_stage, open_ev, e});
+        open_stage = s;
+        open_ev = e;
+    }
+    void collect() {               // after a stream synchronisation
+        for (auto& m : marks) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, m.a, m.b);
+            stage_ms[m.stage] += ms;
+        }
+        marks.clear();
+        ev_used = 0;
+        open_stage = -1;
+    }
+};
+
+#define CUDA_TRY(ctx, call)                                                                 \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+            return SGS_ECUDA;                                                               \
+        }                                                                                   \
+    } while (0)
+
+namespace {
+
+template <class T>
+T** upload_ptrs(sgs_ctx* c, const std::vector<T*>& v) {
+    T** d = c->alloc<T*>(v.size());
+    if (!d) return nullptr;
+    cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T*), cudaMemcpyHostToDevice, c->stream);
+    return d;
+}
+
+int perm_sign4(const int* p) {
+    int s = 1;
+    for (int i = 0; i < 4; i++)
+        for (int j = i + 1; j < 4; j++)
+            if (p[i] > p[j]) s = -s;
+    return s;
+}
+
+unsigned grid_chunks(size_t work, int threads, unsigned cap) {
+    size_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs_options& o) {
+    const int n = 2 * m.n_modes;
+    I.N = m.n_modes;
+    I.n = n;
+    I.M = o.rank;
+    I.P = o.rank * (o.rank - 1) / 2;
+    I.dtau = o.dtau;
+    I.prec = o.precision;
+    I.cmode = o.cmode;
+    I.parity = o.parity;
+    I.e_const = m.e_const;
+    I.gj_b = (n <= 640) ? 32 : 16;
+    if (I.gj_b > n) I.gj_b = n;
+    I.pf_bs = 16;
+    if (2 * I.pf_bs > n) I.pf_bs = n / 2;
+
+    // sparse A
+    std::vector<int> rowptr(n + 1, 0), rows, cols;
+    std::vector<double> vals;
+    for (int k = 0; k < n; k++) {
+        for (int l = 0; l < n; l++) {
+            double v = m.A[(size_t)k * n + l];
+            if (v != 0.0) { rows.push_back(k); cols.push_back(l); vals.push_back(v); }
+        }
+        rowptr[k + 1] = (int)cols.size();
+    }
+    I.a_nnz = (int)cols.size();
+    // quartic: antisymmetrise
+    std::map<std::vector<int>, double> U;
+    for (int j = 0; j < m.n_quartic; j++) {
+        const int* ix = m.quartic_idx + 4 * j;
+        for (int a = 0; a < 4; a++) {
+            if (ix[a] < 0 || ix[a] >= n) { c->err = "quartic index out of range"; return SGS_EINVAL; }
+            for (int b = a + 1; b < 4; b++)
+                if (ix[a] == ix[b]) { c->err = "quartic monomial needs four distinct Majoranas"; return SGS_EINVAL; }
+        }
+        int p[4] = {0, 1, 2, 3};
+        do {
+            std::vector<int> key = {ix[p[0]], ix[p[1]], ix[p[2]], ix[p[3]]};
+            U[key] += perm_sign4(p) * m.quartic_val[j] / 24.0;
+        } while (std::next_permutation(p, p + 4));
+    }
+    std::vector<int> qidx;
+    std::vector<double> qval;
+    std::vector<int> impv;
+    for (auto& kv : U) {
+        if (kv.second == 0.0) continue;
+        for (int a = 0; a < 4; a++) {
+            qidx.push_back(kv.first[a]);
+            if (std::find(impv.begin(), impv.end(), kv.first[a]) == impv.end()) impv.push_back(kv.first[a]);
+        }
+        qval.push_back(kv.second);
+    }
+    std::sort(impv.begin(), impv.end());
+    if ((int)impv.size() > SGS_MAX_IMP) { c->err = "more than 16 Majoranas in quartic terms"; return SGS_EINVAL; }
+    I.nq = (int)qval.size();
+    I.nimp = (int)impv.size();
+    std::vector<int> slot(n, -1);
+    for (int j = 0; j < I.nimp; j++) slot[impv[j]] = j;
+
+    // pairs
+    const int M = I.M, P = I.P;
+    std::vector<int> pa, pb, pair_pf(std::max(P, 1), -1), pf_pair, pidx((size_t)M * M, -1);
+    for (int a = 0; a < M; a++)
+        for (int b = a + 1; b < M; b++) {
+            int p = (int)pa.size();
+            pa.push_back(a); pb.push_back(b);
+            pidx[a * M + b] = pidx[b * M + a] = p;
+            if (a >= 1) { pair_pf[p] = (int)pf_pair.size(); pf_pair.push_back(p); }
+        }
+    I.Ppf = (int)pf_pair.size();
+    I.h_pa = pa;
+    I.h_pb = pb;
+
+    const size_t nn = (size_t)n * n;
+    const size_t Pm = std::max(P, 1);
+    const size_t Pf = std::max(I.Ppf, 1);
+    const int ni = std::max(I.nimp, 1);
+    I.gamma = c->alloc<double>(M * nn);
+    I.dgamma = c->alloc<double>(M * nn);
+    I.pa = c->alloc<int>(Pm); I.pb = c->alloc<int>(Pm);
+    I.pf_pair = c->alloc<int>(Pf); I.pair_pf = c->alloc<int>(Pm); I.pair_index = c->alloc<int>((size_t)M * M);
+    I.a_rowptr = c->alloc<int>(n + 1); I.a_row = c->alloc<int>(std::max(I.a_nnz, 1));
+    I.a_col = c->alloc<int>(std::max(I.a_nnz, 1)); I.a_val = c->alloc<double>(std::max(I.a_nnz, 1));
+    I.q_idx = c->alloc<int>(std::max(4 * I.nq, 4)); I.q_val = c->alloc<double>(std::max(I.nq, 1));
+    I.imp = c->alloc<int>(ni); I.slot = c->alloc<int>(n);
+    I.work = c->alloc<double>(Pm * 2 * nn);
+    I.si = c->alloc<double>(Pm * nn); I.imd = c->alloc<double>(Pm * nn);
+    I.wr = c->alloc<double>(Pm * nn); I.va = c->alloc<double>(Pm * nn); I.xa = c->alloc<double>(Pm * nn);
+    I.tbuf = c->alloc<double>(Pm * I.gj_b * n);
+    I.piv = c->alloc<int>(Pm * n); I.perm = c->alloc<int>(Pm * n);
+    I.logdet = c->alloc<double>(Pm); I.dsign = c->alloc<double>(Pm);
+    I.pfTU = c->alloc<double>(Pf * 4 * n * I.pf_bs);
+    I.pfpack = c->alloc<double>(Pf * 4 * n * 4 * I.pf_bs);
+    I.pflog = c->alloc<double>(Pf); I.pfphase = c->alloc<double>(2 * Pf);
+    I.fimp = c->alloc<double>(Pm * ni * ni * 2); I.fimp_state = c->alloc<double>((size_t)M * ni * ni);
+    I.lr = c->alloc<double>(Pm * 2 * n * ni);
+    for (int j = 0; j < 5; j++) I.s[j] = c->alloc<double>(M * nn);
+    I.sq = c->alloc<int>(M); I.scale = c->alloc<double>(M);
+    I.Gm = c->alloc<double>(2 * M * M); I.hm = c->alloc<double>(2 * M * M);
+    I.lam = c->alloc<double>(2 * M); I.lt = c->alloc<double>(2 * M); I.coef = c->alloc<double>(6 * M * M);
+    I.Ecap = 1;
+    I.Ehist = c->alloc<double>(1);
+    I.eigscratch = c->alloc<double>(6 * (size_t)(2 * M) * (2 * M) + 8 * 2 * M);
+    I.err = c->alloc<int>(1);
+    void* check[] = {I.gamma, I.dgamma, I.work, I.si, I.imd, I.wr, I.va, I.xa, I.tbuf, I.pfTU, I.pfpack, I.s[0],
+                     I.s[1], I.s[2], I.s[3], I.s[4], I.eigscratch, I.err, I.lr, I.fimp};
+    for (void* p : check)
+        if (!p) { c->err = "device allocation failed"; return SGS_ENOMEM; }
+
+    cudaStream_t st = c->stream;
+    CUDA_TRY(c, cudaMemcpyAsync(I.gamma, o.gamma0, M * nn * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(c, cudaMemsetAsync(I.dgamma, 0, M * nn * sizeof(double), st));
+    if (P > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(I.pa, pa.data(), P * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(I.pb, pb.data(), P * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(I.pair_pf, pair_pf.data(), P * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    if (I.Ppf > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(I.pf_pair, pf_pair.data(), I.Ppf * sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(I.pair_index, pidx.data(), (size_t)M * M * sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(I.a_rowptr, rowptr.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (I.a_nnz > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(I.a_row, rows.data(), I.a_nnz * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(I.a_col, cols.data(), I.a_nnz * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(I.a_val, vals.data(), I.a_nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    if (I.nq > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(I.q_idx, qidx.data(), 4 * I.nq * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(I.q_val, qval.data(), I.nq * sizeof(double), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(I.imp, impv.data(), I.nimp * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(I.slot, slot.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    std::vector<double> lam0(2 * M, 0.0);
+    if (o.lambda0) std::memcpy(lam0.data(), o.lambda0, 2 * M * sizeof(double));
+    CUDA_TRY(c, cudaMemcpyAsync(I.lam, lam0.data(), 2 * M * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(c, cudaMemsetAsync(I.err, 0, sizeof(int), st));
+
+    // pointer arrays
+    std::vector<double*> w, t, s_, im, wr, va, xa, ga, gb;
+    for (int p = 0; p < P; p++) {
+        w.push_back(I.work + p * nn);
+        t.push_back(I.tbuf + (size_t)p * I.gj_b * n);
+        s_.push_back(I.si + p * nn);
+        im.push_back(I.imd + p * nn);
+        wr.push_back(I.wr + p * nn);
+        va.push_back(I.va + p * nn);
+        xa.push_back(I.xa + p * nn);
+        ga.push_back(I.gamma + pa[p] * nn);
+        gb.push_back(I.gamma + pb[p] * nn);
+    }
+    if (P > 0) {
+        I.p_work = upload_ptrs(c, w); I.p_tbuf = upload_ptrs(c, t); I.p_si = upload_ptrs(c, s_);
+        I.p_imd = upload_ptrs(c, im); I.p_wr = upload_ptrs(c, wr); I.p_va = upload_ptrs(c, va);
+        I.p_xa = upload_ptrs(c, xa); I.p_ga = upload_ptrs(c, ga); I.p_gb = upload_ptrs(c, gb);
+    }
+    std::vector<double*> Y, TU, PK, upA, upB, upC;
+    const size_t blk = (size_t)n * 4 * I.pf_bs;
+    for (int q = 0; q < I.Ppf; q++) {
+        Y.push_back(I.work + (size_t)q * 2 * nn);
+        TU.push_back(I.pfTU + (size_t)q * 4 * n * I.pf_bs);
+        PK.push_back(I.pfpack + (size_t)q * 4 * blk);
+    }
+    for (int q = 0; q < I.Ppf; q++) { upA.push_back(PK[q]); upB.push_back(PK[q] + blk); upC.push_back(Y[q]); }
+    for (int q = 0; q < I.Ppf; q++) { upA.push_back(PK[q] + 2 * blk); upB.push_back(PK[q] + 3 * blk); upC.push_back(Y[q] + nn); }
+    if (I.Ppf > 0) {
+        I.p_Y = upload_ptrs(c, Y); I.p_TU = upload_ptrs(c, TU); I.p_pack = upload_ptrs(c, PK);
+        I.p_upA = upload_ptrs(c, upA); I.p_upB = upload_ptrs(c, upB); I.p_upC = upload_ptrs(c, upC);
+    }
+    std::vector<double*> g, dg, ss[5];
+    for (int mu = 0; mu < M; mu++) {
+        g.push_back(I.gamma + mu * nn);
+        dg.push_back(I.dgamma + mu * nn);
+        for (int j = 0; j < 5; j++) ss[j].push_back(I.s[j] + mu * nn);
+    }
+    I.p_gamma = upload_ptrs(c, g);
+    I.p_dgamma = upload_ptrs(c, dg);
+    for (int j = 0; j < 5; j++) I.p_s[j] = upload_ptrs(c, ss[j]);
+    return SGS_OK;
+}
+
+// ------------------------------------------------------------------ launches
+
+inline cudaError_t gemm(const GemmBatch& g, cudaStream_t st) {
+    counted();
+    return gemm_f64(g, st);
+}
+
+GemmBatch gb_basic(int m, int n, int k, double** A, int lda, double** B, int ldb, double** C, int ldc, int batch) {
+    GemmBatch g = gemm_defaults();
+    g.m = m; g.n = n; g.k = k;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+    g.batch = batch;
+    return g;
+}
+
+cudaError_t launch_gj(int n, int batch, int bsz, double** W, double** T, int* piv, double* logdet, double* dsign,
+                      int* err, double tiny, cudaStream_t st) {
+    const size_t smem = (size_t)n * bsz * sizeof(double) + bsz * sizeof(double);
+    cudaFuncSetAttribute(gj_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int k0 = 0; k0 < n; k0 += bsz) {
+        const int bb = std::min(bsz, n - k0);
+        GJPanelArgs a{W, T, piv, logdet, dsign, err, n, k0, bb, tiny};
+        gj_panel_kernel<<<batch, 512, (size_t)n * bb * sizeof(double) + bb * sizeof(double), st>>>(a);
+        counted();
+        GemmBatch g = gb_basic(n, n, bb, W, n, T, n, W, n, batch);
+        g.offA = k0;
+        g.Cin = (const double* const*)W; g.ldcin = n; g.beta = 1.0;
+        g.mode = GEMM_GJ; g.gj_k0 = k0; g.gj_b = bb;
+        cudaError_t e = gemm(g, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pf(int n, int batch, int bsmax, double** Y, double** TU, double** PK, double** upA, double** upB,
+                      double** upC, double* logabs, double* phase, int* err, cudaStream_t st) {
+    const size_t smem = (4 * (size_t)n + 4 * bsmax) * sizeof(double);
+    cudaFuncSetAttribute(pf_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int k0 = 0; k0 < n; k0 += 2 * bsmax) {
+        const int bs = std::min(bsmax, (n - k0) / 2);
+        PfPanelArgs a{Y, TU, PK, logabs, phase, err, n, k0, bs, bsmax};
+        pf_panel_kernel<<<batch, 512, smem, st>>>(a);
+        counted();
+        const int e0 = k0 + 2 * bs;
+        if (e0 >= n) break;
+        GemmBatch g = gb_basic(n - e0, n - e0, 4 * bs, upA, 4 * bs, upB, 4 * bs, upC, n, 2 * batch);
+        g.offA = (long long)e0 * 4 * bs;
+        g.offB = (long long)e0 * 4 * bs;
+        g.transB = 1;
+        g.offC = (long long)e0 * n + e0;
+        g.Cin = (const double* const*)upC; g.offCin = g.offC; g.ldcin = n; g.beta = 1.0;
+        cudaError_t e = gemm(g, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+// pair pass + amplitude solve for one instance; E -> Ehist[slot]
+cudaError_t pair_pass(sgs_ctx* c, Instance& I, int eslot) {
+    cudaStream_t st = c->stream;
+    const int n = I.n, P = I.P, M = I.M;
+    const size_t nn = (size_t)n * n;
+    const double n3 = (double)n * n * n;
+    InstDev d = I.dev();
+    if (P > 0) {
+        c->stage(SGS_STAGE_PAIR_INVERSE);
+        c->stage_flops[SGS_STAGE_PAIR_INVERSE] += 2.0 * n3 * P;
+        pair_sum_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.work);
+        counted();
+        // S has entries of magnitude <= 2; two states of opposite parity give a
+        // pivot at rounding level (~1e-15), same-parity pairs O(0.1)
+        cudaError_t e = launch_gj(n, P, I.gj_b, I.p_work, I.p_tbuf, I.piv, I.logdet, I.dsign, I.err, 1e-12, st);
+        if (e != cudaSuccess) return e;
+        gj_perm_kernel<<<(P + 127) / 128, 128, 0, st>>>(I.piv, I.perm, n, P);
+        gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.p_work, I.p_si, I.perm, n);
+        counted(); counted();
+        // Im = (G_a - G_b) S^{-1}
+        c->stage(SGS_STAGE_PAIR_DELTA);
+        c->stage_flops[SGS_STAGE_PAIR_DELTA] += n3 * P;   // antisymmetric product: half of 2 n^3
+        GemmBatch g = gb_basic(n, n, n, I.p_ga, n, I.p_si, n, I.p_imd, n, P);
+        g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
+        g.mode = GEMM_SKEW;
+        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        if (I.Ppf > 0) {
+            c->stage(SGS_STAGE_PHASE_PFAFFIAN);
+            c->stage_flops[SGS_STAGE_PHASE_PFAFFIAN] += 4.0 / 3.0 * n3 * I.Ppf;
+            pf_build_kernel<<<dim3(grid_chunks(nn, 256, 64), I.Ppf), 256, 0, st>>>(d, I.si, I.imd, I.work);
+            counted();
+            e = launch_pf(n, I.Ppf, I.pf_bs, I.p_Y, I.p_TU, I.p_pack, I.p_upA, I.p_upB, I.p_upC, I.pflog,
+                          I.pfphase, I.err, st);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    c->stage(SGS_STAGE_AMPLITUDES);
+    pair_gh_kernel<<<P + M, 256, 0, st>>>(d, I.si, I.imd, I.logdet, I.pfphase, I.Gm, I.hm, I.fimp, I.fimp_state);
+    AmpArgs aa{M, I.Gm, I.hm, I.eigscratch, I.Ehist + eslot, I.lam, I.lt, I.coef, I.cmode, 1e-12, I.err};
+    amp_solve_kernel<<<1, 256, 0, st>>>(aa);
+    counted(); counted();
+    return cudaGetLastError();
+}
+
+cudaError_t eom_pass(sgs_ctx* c, Instance& I) {
+    cudaStream_t st = c->stream;
+    const int n = I.n, P = I.P, M = I.M;
+    const size_t nn = (size_t)n * n;
+    const double n3 = (double)n * n * n;
+    InstDev d = I.dev();
+    cudaError_t e;
+    c->stage(SGS_STAGE_EOM_GEMM);
+    c->stage_flops[SGS_STAGE_EOM_GEMM] += 4.0 * n3 * P + n3 * M;   // Wr, X antisymmetric; V full; GFG
+    // per state: T2 = F Gamma (s0), GFG = Gamma T2 (s4)
+    state_sparse_left_kernel<<<dim3(grid_chunks(nn, 256, 256), M), 256, 0, st>>>(d, I.fimp_state, I.s[0]);
+    counted();
+    {
+        GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_s[0], n, I.p_s[4], n, M);
+        g.mode = GEMM_SKEW;
+        if ((e = gemm(g, st)) != cudaSuccess) return e;
+    }
+    if (P > 0) {
+        // T1 = S^{-1} (A + Re Fimp)  (into work), Wr = T1 S^{-1}
+        pair_sparse_right_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.si, I.fimp, I.work);
+        counted();
+        GemmBatch g = gb_basic(n, n, n, I.p_work, n, I.p_si, n, I.p_wr, n, P);
+        g.mode = GEMM_SKEW;
+        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        // V = D Wr
+        g = gb_basic(n, n, n, I.p_ga, n, I.p_wr, n, I.p_va, n, P);
+        g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
+        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        // X = V D
+        g = gb_basic(n, n, n, I.p_va, n, I.p_ga, n, I.p_xa, n, P);
+        g.B2 = (const double* const*)I.p_gb; g.sB2 = -1.0;
+        g.mode = GEMM_SKEW;
+        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        c->stage(SGS_STAGE_EOM_ASSEMBLY);
+        if (I.nimp > 0) {
+            pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.fimp, I.lr);
+            counted();
+        }
+        pair_q_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va, I.xa, I.wr);
+        counted();
+    } else {
+        c->stage(SGS_STAGE_EOM_ASSEMBLY);
+    }
+    // algorithmic bytes: pair_q reads Si, Im, V (twice), X, Wr and writes Qr, Qi; the EOM
+    // reads Si, Im, Qr, Qi once per receiver of each pair plus Gamma, GFG and writes dGamma
+    c->stage_bytes[SGS_STAGE_EOM_ASSEMBLY] += 8.0 * nn * (7.0 * P + 8.0 * P + 3.0 * M);
+    eom_kernel<<<dim3(grid_chunks(nn, 256, 1024), M), 256, 0, st>>>(d, I.si, I.imd, I.xa, I.wr, I.fimp,
+                                                                   I.fimp_state, I.s[4], I.coef, I.pair_index,
+                                                                   I.dgamma);
+    counted();
+    return cudaGetLastError();
+}
+
+cudaError_t update_pass(sgs_ctx* c, Instance& I) {
+    cudaStream_t st = c->stream;
+    const int n = I.n, M = I.M;
+    const size_t nn = (size_t)n * n;
+    const double n3 = (double)n * n * n;
+    cudaError_t e;
+    c->stage(SGS_STAGE_UPDATE);
+    // Gamma dGamma, 9 Horner products, R Gamma, (R Gamma) R^T (antisymmetric),
+    // two Newton-Schulz iterations; squarings are added when profiles are read
+    c->stage_flops[SGS_STAGE_UPDATE] += (2.0 + 18.0 + 2.0 + 1.0 + 6.0) * n3 * M;
+    // Y = Gamma dGamma -> s0 ; X -> s1 ; P -> s2
+    GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_dgamma, n, I.p_s[0], n, M);
+    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    exp_prepare_kernel<<<M, 1024, 0, st>>>(I.s[0], I.s[1], I.s[2], n, I.dtau, I.sq, I.scale, I.err);
+    counted();
+    // Horner: P <- I + (X 2^-s / j) P, j = degree-1 .. 1
+    int cur = 2;
+    for (int j = EXP_TAYLOR_DEGREE - 1; j >= 1; j--) {
+        int nxt = (cur == 2) ? 3 : 2;
+        g = gb_basic(n, n, n, I.p_s[1], n, I.p_s[cur], n, I.p_s[nxt], n, M);
+        g.alpha = 1.0 / j; g.alpha_b = I.scale; g.diag = 1.0;
+        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        cur = nxt;
+    }
+    // squarings (states with fewer squarings pass their matrix through)
+    for (int j = 0; j < EXP_MAX_SQUARINGS; j++) {
+        int nxt = (cur == 2) ? 3 : 2;
+        g = gb_basic(n, n, n, I.p_s[cur], n, I.p_s[cur], n, I.p_s[nxt], n, M);
+        g.active_flag = I.sq; g.active_cmp = j;
+        g.Cin = (const double* const*)I.p_s[cur]; g.ldcin = n; g.beta = 0.0;
+        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        cur = nxt;
+    }
+    // T = R Gamma -> s0 ; Gamma' = T R^T -> s4
+    g = gb_basic(n, n, n, I.p_s[cur], n, I.p_gamma, n, I.p_s[0], n, M);
+    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    g = gb_basic(n, n, n, I.p_s[0], n, I.p_s[cur], n, I.p_s[4], n, M);
+    g.transB = 1; g.mode = GEMM_SKEW;
+    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    // Newton-Schulz polar factor: X <- 1.5 X + 0.5 X (X X), twice
+    double** src = I.p_s[4];
+    double** dst = I.p_gamma;
+    for (int it = 0; it < 2; it++) {
+        g = gb_basic(n, n, n, src, n, src, n, I.p_s[0], n, M);
+        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        g = gb_basic(n, n, n, src, n, I.p_s[0], n, dst, n, M);
+        g.alpha = 0.5; g.Cin = (const double* const*)src; g.ldcin = n; g.beta = 1.5; g.mode = GEMM_SKEW;
+        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        std::swap(src, dst);
+    }
+    // after two iterations the result is back in s4
+    copy_kernel<<<grid_chunks(M * nn, 256, 4096), 256, 0, st>>>(I.s[4], I.gamma, M * nn);
+    counted();
+    I.steps_since_profile++;
+    return cudaGetLastError();
+}
+
+sgs_status check_device_error(sgs_ctx* c) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < c->inst.size(); i++) {
+        int e = 0;
+        CUDA_TRY(c, cudaMemcpy(&e, c->inst[i].err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            CUDA_TRY(c, cudaMemset(c->inst[i].err, 0, sizeof(int)));
+            char buf[160];
+            if (e & SGS_DEV_SINGULAR) {
+                snprintf(buf, sizeof buf, "instance %zu: two ansatz states have a singular Gamma_a + Gamma_b", i);
+                c->err = buf;
+                return SGS_ESINGULAR;
+            }
+            if (e & SGS_DEV_PF_ZERO) {
+                snprintf(buf, sizeof buf, "instance %zu: a state is orthogonal to the reference state", i);
+                c->err = buf;
+                return SGS_ESINGULAR;
+            }
+            snprintf(buf, sizeof buf, "instance %zu: %s", i,
+                     (e & SGS_DEV_EIG) ? "amplitude solver did not converge" : "exponential step out of range");
+            c->err = buf;
+            return SGS_ENOTCONV;
+        }
+    }
+    return SGS_OK;
+}
+
+sgs_status ensure_ehist(sgs_ctx* c, Instance& I, int n) {
+    if (I.Ecap >= n) return SGS_OK;
+    double* p = c->alloc<double>(n);
+    if (!p) { c->err = "device allocation failed"; return SGS_ENOMEM; }
+    I.Ehist = p;
+    I.Ecap = n;
+    return SGS_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+void sgs_set_allocator(sgs_alloc_fn alloc, sgs_free_fn release, void* user) {
+    g_alloc = alloc;
+    g_release = release;
+    g_user = user;
+}
+
+sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_instances, sgs_ctx** out) {
+    if (!out) return SGS_EINVAL;
+    *out = nullptr;
+    if (!models || !opts || n_instances < 1) return SGS_EINVAL;
+    for (int i = 0; i < n_instances; i++) {
+        const sgs_model& m = models[i];
+        const sgs_options& o = opts[i];
+        if (m.n_modes < 1 || !m.A || (m.n_quartic > 0 && (!m.quartic_idx || !m.quartic_val))) return SGS_EINVAL;
+        if (o.rank < 1 || o.rank > SGS_MAX_RANK || (o.parity != 1 && o.parity != -1) || !o.gamma0) return SGS_EINVAL;
+        if (o.precision < 0 || o.precision > 3 || (o.cmode != 0 && o.cmode != 1)) return SGS_EINVAL;
+    }
+    sgs_ctx* c = new sgs_ctx();
+    cudaGetDevice(&c->device);
+    if (opts[0].stream) {
+        c->stream = (cudaStream_t)opts[0].stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return SGS_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    c->inst.resize(n_instances);
+    for (int i = 0; i < n_instances; i++) {
+        sgs_status s = setup_instance(c, c->inst[i], models[i], opts[i]);
+        if (s != SGS_OK) {
+            sgs_free(c);
+            return s;
+        }
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        sgs_free(c);
+        return SGS_ECUDA;
+    }
+    *out = c;
+    return SGS_OK;
+}
+
+sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
+    if (!c || n_steps < 0) return SGS_EINVAL;
+    for (auto& I : c->inst) {
+        sgs_status s = ensure_ehist(c, I, std::max(n_steps, 1));
+        if (s != SGS_OK) return s;
+    }
+    const long long l0 = g_launches;
+    for (int step = 0; step < n_steps; step++) {
+        for (auto& I : c->inst) {
+            CUDA_TRY(c, pair_pass(c, I, step));
+            CUDA_TRY(c, eom_pass(c, I));
+            CUDA_TRY(c, update_pass(c, I));
+        }
+    }
+    c->stage(-1);
+    c->launches += g_launches - l0;
+    sgs_status s = check_device_error(c);
+    c->collect();
+    if (s != SGS_OK) return s;
+    if (energies) {
+        for (size_t i = 0; i < c->inst.size(); i++)
+            CUDA_TRY(c, cudaMemcpy(energies + i * n_steps, c->inst[i].Ehist, n_steps * sizeof(double),
+                                   cudaMemcpyDeviceToHost));
+    }
+    return SGS_OK;
+}
+
+sgs_status sgs_energy(sgs_ctx* c, double* energies) {
+    if (!c) return SGS_EINVAL;
+    const long long l0 = g_launches;
+    for (auto& I : c->inst) CUDA_TRY(c, pair_pass(c, I, 0));
+    c->stage(-1);
+    c->launches += g_launches - l0;
+    sgs_status s = check_device_error(c);
+    c->collect();
+    if (s != SGS_OK) return s;
+    if (energies)
+        for (size_t i = 0; i < c->inst.size(); i++)
+            CUDA_TRY(c, cudaMemcpy(energies + i, c->inst[i].Ehist, sizeof(double), cudaMemcpyDeviceToHost));
+    return SGS_OK;
+}
+
+sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const int* sites, int n_sites, double* out) {
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !sites || !out || n_sites < 0) return SGS_EINVAL;
+    (void)kind;
+    c->err = "correlator kind not available";
+    return SGS_EINVAL;
+}
+
+void sgs_free(sgs_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    c->release_all();
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* sgs_last_error(const sgs_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+sgs_status sgs_get_state(const sgs_ctx* cc, int instance, double* gamma, double* lambda) {
+    sgs_ctx* c = const_cast<sgs_ctx*>(cc);
+    if (!c || instance < 0 || instance >= (int)c->inst.size()) return SGS_EINVAL;
+    const Instance& I = c->inst[instance];
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (gamma)
+        CUDA_TRY(c, cudaMemcpy(gamma, I.gamma, (size_t)I.M * I.n * I.n * sizeof(double), cudaMemcpyDeviceToHost));
+    if (lambda) CUDA_TRY(c, cudaMemcpy(lambda, I.lam, 2 * I.M * sizeof(double), cudaMemcpyDeviceToHost));
+    return SGS_OK;
+}
+
+sgs_status sgs_set_state(sgs_ctx* c, int instance, const double* gamma, const double* lambda) {
+    if (!c || instance < 0 || instance >= (int)c->inst.size()) return SGS_EINVAL;
+    Instance& I = c->inst[instance];
+    if (gamma)
+        CUDA_TRY(c, cudaMemcpyAsync(I.gamma, gamma, (size_t)I.M * I.n * I.n * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream));
+    if (lambda)
+        CUDA_TRY(c, cudaMemcpyAsync(I.lam, lambda, 2 * I.M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return SGS_OK;
+}
+
+sgs_status sgs_get_pair_matrices(const sgs_ctx* cc, int instance, double* G, double* h) {
+    sgs_ctx* c = const_cast<sgs_ctx*>(cc);
+    if (!c || instance < 0 || instance >= (int)c->inst.size()) return SGS_EINVAL;
+    const Instance& I = c->inst[instance];
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (G) CUDA_TRY(c, cudaMemcpy(G, I.Gm, 2 * I.M * I.M * sizeof(double), cudaMemcpyDeviceToHost));
+    if (h) CUDA_TRY(c, cudaMemcpy(h, I.hm, 2 * I.M * I.M * sizeof(double), cudaMemcpyDeviceToHost));
+    return SGS_OK;
+}
+
+sgs_status sgs_get_derivative(const sgs_ctx* cc, int instance, double* dgamma) {
+    sgs_ctx* c = const_cast<sgs_ctx*>(cc);
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !dgamma) return SGS_EINVAL;
+    const Instance& I = c->inst[instance];
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaMemcpy(dgamma, I.dgamma, (size_t)I.M * I.n * I.n * sizeof(double), cudaMemcpyDeviceToHost));
+    return SGS_OK;
+}
+
+sgs_status sgs_set_profiling(sgs_ctx* c, int enable) {
+    if (!c) return SGS_EINVAL;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->collect();
+    c->prof = enable != 0;
+    for (int j = 0; j < SGS_N_STAGES; j++) c->stage_ms[j] = c->stage_flops[j] = c->stage_bytes[j] = 0.0;
+    c->launches = 0;
+    for (auto& I : c->inst) I.steps_since_profile = 0;
+    return SGS_OK;
+}
+
+sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double* bytes, long long* launches) {
+    sgs_ctx* c = const_cast<sgs_ctx*>(cc);
+    if (!c) return SGS_EINVAL;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->collect();
+    // squarings of the exponential step: 2 n^3 per squaring actually applied (last step's counts)
+    double sq_flops = 0.0;
+    for (auto& I : c->inst) {
+        std::vector<int> sq(I.M);
+        CUDA_TRY(c, cudaMemcpy(sq.data(), I.sq, I.M * sizeof(int), cudaMemcpyDeviceToHost));
+        double tot = 0;
+        for (int v : sq) tot += v;
+        sq_flops += 2.0 * (double)I.n * I.n * I.n * tot * I.steps_since_profile;
+    }
+    for (int j = 0; j < SGS_N_STAGES; j++) {
+        if (ms) ms[j] = c->stage_ms[j];
+        if (flops) flops[j] = c->stage_flops[j] + (j == SGS_STAGE_UPDATE ? sq_flops : 0.0);
+        if (bytes) bytes[j] = c->stage_bytes[j];
+    }
+    if (launches) *launches = c->launches;
+    return SGS_OK;
+}
+
+sgs_status sgs_probe_peak(int kind, double* tflops) {
+    if (!tflops || kind < 0 || kind > 1) return SGS_EINVAL;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * 8, thr = 256;
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * blocks * thr) != cudaSuccess) return SGS_ENOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {
+        cudaEventRecord(e0);
+        if (kind == 0) probe_dmma_kernel<<<blocks, thr>>>(out, 0.999);
+        else probe_dfma_kernel<<<blocks, thr>>>(out, 0.999);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaError_t err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (err != cudaSuccess) return SGS_ECUDA;
+    // m8n8k4: 512 flops per warp-instruction; FMA: 2 flops per thread-instruction
+    const double fl = (kind == 0) ? (double)blocks * (thr / 32) * PROBE_ITERS * 512.0
+                                  : (double)blocks * thr * PROBE_ITERS * 8 * 2.0;
+    *tflops = fl / (best * 1e-3) / 1e12;
+    return SGS_OK;
+}
+
+int sgs_build_anderson(int n_bath, int n_channels, double U, double eps_d, double V, double t, double mu, double* A,
+                       int* quartic_idx, double* quartic_val, double* e_const) {
+    if (n_bath < 1 || n_channels < 1 || !A || !quartic_idx || !quartic_val || !e_const) return -1;
+    const int n_sites = 1 + n_channels * n_bath;
+    const int nm = 2 * n_sites;
+    const int n = 2 * nm;
+    std::vector<double> h((size_t)nm * nm, 0.0);
+    auto site = [&](int ch, int r) { return 1 + (r - 1) * n_channels + ch; };
+    for (int sp = 0; sp < 2; sp++) {
+        h[(size_t)sp * nm + sp] = eps_d;
+        for (int ch = 0; ch < n_channels; ch++) {
+            int b = 2 * site(ch, 1) + sp;
+            h[(size_t)sp * nm + b] = h[(size_t)b * nm + sp] = -V;
+            for (int r = 1; r <= n_bath; r++) {
+                int m = 2 * site(ch, r) + sp;
+                h[(size_t)m * nm + m] = -mu;
+                if (r >= 2) {
+                    int q = 2 * site(ch, r - 1) + sp;
+                    h[(size_t)q * nm + m] = h[(size_t)m * nm + q] = -t;
+                }
+            }
+        }
+    }
+    // sum_ij h_ij a_i^dag a_j = tr(h)/2 + i sum_kl A_kl c_k c_l with A_{2i,2j+1} = h_ij/4
+    std::fill(A, A + (size_t)n * n, 0.0);
+    double ec = 0.0;
+    for (int i = 0; i < nm; i++) {
+        ec += 0.5 * h[(size_t)i * nm + i];
+        for (int j = 0; j < nm; j++) {
+            double v = h[(size_t)i * nm + j];
+            if (v == 0.0) continue;
+            A[(size_t)(2 * i) * n + 2 * j + 1] += 0.25 * v;
+            A[(size_t)(2 * j + 1) * n + 2 * i] -= 0.25 * v;
+        }
+    }
+    // U n_0up n_0dn = U/4 + (U/4)(i c0 c1 + i c2 c3) - (U/4) c0 c1 c2 c3
+    ec += 0.25 * U;
+    for (int m = 0; m < 2; m++) {
+        A[(size_t)(2 * m) * n + 2 * m + 1] += 0.125 * U;
+        A[(size_t)(2 * m + 1) * n + 2 * m] -= 0.125 * U;
+    }
+    quartic_idx[0] = 0; quartic_idx[1] = 1; quartic_idx[2] = 2; quartic_idx[3] = 3;
+    quartic_val[0] = -0.25 * U;
+    *e_const = ec;
+    return nm;
+}
+
+// ------------------------------------------------------------ building blocks
+
+sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, double* C) {
+    if (!A || !B || !C || n < 1 || batch < 1) return SGS_EINVAL;
+    sgs_ctx tmp;
+    cudaStreamCreateWithFlags(&tmp.stream, cudaStreamNonBlocking);
+    tmp.own_stream = true;
+    const size_t nn = (size_t)n * n;
+    double *dA = tmp.alloc<double>(batch * nn), *dB = tmp.alloc<double>(batch * nn), *dC = tmp.alloc<double>(batch * nn);
+    sgs_status st = SGS_OK;
+    if (!dA || !dB || !dC) st = SGS_ENOMEM;
+    if (st == SGS_OK) {
+        std::vector<double*> pa, pb, pc;
+        for (int b = 0; b < batch; b++) { pa.push_back(dA + b * nn); pb.push_back(dB + b * nn); pc.push_back(dC + b * nn); }
+        double **PA = upload_ptrs(&tmp, pa), **PB = upload_ptrs(&tmp, pb), **PC = upload_ptrs(&tmp, pc);
+        cudaMemcpyAsync(dA, A, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
+        cudaMemcpyAsync(dB, B, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
+        GemmBatch g = gb_basic(n, n, n, PA, n, PB, n, PC, n, batch);
+        if (gemm(g, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        cudaMemcpyAsync(C, dC, batch * nn * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
+        if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+    }
+    cudaStreamSynchronize(tmp.stream);
+    tmp.release_all();
+    cudaStreamDestroy(tmp.stream);
+    tmp.stream = nullptr;
+    return st;
+}
+
+sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, double* logabsdet) {
+    if (!S || !inv || n < 1 || batch < 1) return SGS_EINVAL;
+    sgs_ctx tmp;
+    cudaStreamCreateWithFlags(&tmp.stream, cudaStreamNonBlocking);
+    const size_t nn = (size_t)n * n;
+    const int bsz = (n <= 640) ? std::min(32, n) : 16;
+    double *W = tmp.alloc<double>(batch * nn), *O = tmp.alloc<double>(batch * nn), *T = tmp.alloc<double>((size_t)batch * bsz * n);
+    int *piv = tmp.alloc<int>((size_t)batch * n), *perm = tmp.alloc<int>((size_t)batch * n), *err = tmp.alloc<int>(1);
+    double *ld = tmp.alloc<double>(batch), *ds = tmp.alloc<double>(batch);
+    sgs_status st = SGS_OK;
+    if (!W || !O || !T || !piv || !perm || !err || !ld || !ds) st = SGS_ENOMEM;
+    if (st == SGS_OK) {
+        std::vector<double*> pw, pt, po;
+        for (int b = 0; b < batch; b++) { pw.push_back(W + b * nn); pt.push_back(T + (size_t)b * bsz * n); po.push_back(O + b * nn); }
+        double **PW = upload_ptrs(&tmp, pw), **PT = upload_ptrs(&tmp, pt), **PO = upload_ptrs(&tmp, po);
+        cudaMemcpyAsync(W, S, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
+        cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
+        if (launch_gj(n, batch, bsz, PW, PT, piv, ld, ds, err, 0.0, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        gj_perm_kernel<<<(batch + 127) / 128, 128, 0, tmp.stream>>>(piv, perm, n, batch);
+        gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), batch), 256, 0, tmp.stream>>>(PW, PO, perm, n);
+        cudaMemcpyAsync(inv, O, batch * nn * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
+        if (logabsdet) cudaMemcpyAsync(logabsdet, ld, batch * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
+        int herr = 0;
+        cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, tmp.stream);
+        if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        else if (herr) st = SGS_ESINGULAR;
+    }
+    cudaStreamSynchronize(tmp.stream);
+    tmp.release_all();
+    cudaStreamDestroy(tmp.stream);
+    tmp.stream = nullptr;
+    return st;
+}
+
+sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase, double* logabs) {
+    if (!Y || !phase || !logabs || n < 2 || (n & 1) || batch < 1) return SGS_EINVAL;
+    sgs_ctx tmp;
+    cudaStreamCreateWithFlags(&tmp.stream, cudaStreamNonBlocking);
+    const size_t nn = (size_t)n * n;
+    const int bs = std::min(16, n / 2);
+    double* W = tmp.alloc<double>(batch * 2 * nn);
+    double* TU = tmp.alloc<double>((size_t)batch * 4 * n * bs);
+    double* PK = tmp.alloc<double>((size_t)batch * 16 * n * bs);
+    double *la = tmp.alloc<double>(batch), *ph = tmp.alloc<double>(2 * batch);
+    int* err = tmp.alloc<int>(1);
+    sgs_status st = SGS_OK;
+    if (!W || !TU || !PK || !la || !ph || !err) st = SGS_ENOMEM;
+    if (st == SGS_OK) {
+        // de-interleave (re, im) into planes on the host
+        std::vector<double> planes(batch * 2 * nn);
+        for (int b = 0; b < batch; b++)
+            for (size_t e = 0; e < nn; e++) {
+                planes[b * 2 * nn + e] = Y[(b * nn + e) * 2];
+                planes[b * 2 * nn + nn + e] = Y[(b * nn + e) * 2 + 1];
+            }
+        const size_t blk = (size_t)n * 4 * bs;
+        std::vector<double*> py, ptu, ppk, ua, ub, uc;
+        for (int b = 0; b < batch; b++) {
+            py.push_back(W + b * 2 * nn); ptu.push_back(TU + (size_t)b * 4 * n * bs); ppk.push_back(PK + (size_t)b * 4 * blk);
+        }
+        for (int b = 0; b < batch; b++) { ua.push_back(ppk[b]); ub.push_back(ppk[b] + blk); uc.push_back(py[b]); }
+        for (int b = 0; b < batch; b++) { ua.push_back(ppk[b] + 2 * blk); ub.push_back(ppk[b] + 3 * blk); uc.push_back(py[b] + nn); }
+        double **PY = upload_ptrs(&tmp, py), **PTU = upload_ptrs(&tmp, ptu), **PPK = upload_ptrs(&tmp, ppk);
+        double **UA = upload_ptrs(&tmp, ua), **UB = upload_ptrs(&tmp, ub), **UC = upload_ptrs(&tmp, uc);
+        cudaMemcpyAsync(W, planes.data(), planes.size() * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
+        cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
+        if (launch_pf(n, batch, bs, PY, PTU, PPK, UA, UB, UC, la, ph, err, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        cudaMemcpyAsync(phase, ph, 2 * batch * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
+        cudaMemcpyAsync(logabs, la, batch * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
+        if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+    }
+    cudaStreamSynchronize(tmp.stream);
+    tmp.release_all();
+    cudaStreamDestroy(tmp.stream);
+    tmp.stream = nullptr;
+    return st;
+}
+
+}  // extern "C"

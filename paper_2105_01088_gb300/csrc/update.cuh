@@ -1,0 +1,59 @@
+// Per-state update of App. A: Gamma <- R Gamma R^T with R = exp(X),
+// X = (ds/4)[Gamma, dGamma] (Eq. ExpStep; the factor 1/4 makes the step agree
+// with Gamma + ds dGamma of Eq. RKstep to first order), followed by the
+// canonical-form renormalisation (polar factor, Newton-Schulz in FP64).
+//
+// exp(X) by scaling and squaring: X_s = X / 2^s with ||X_s||_F <= 1/8, Taylor
+// polynomial of degree 10 in Horner form (truncation < 3e-18), then s
+// squarings.  The products run on the batched FP64 GEMM; this file holds the
+// elementwise pieces.
+#pragma once
+#include "common.cuh"
+
+namespace sgs {
+
+#define EXP_TAYLOR_DEGREE 10
+#define EXP_MAX_SQUARINGS 14
+#define EXP_THETA 0.125
+
+// X = (ds/4)(Y - Y^T) with Y = Gamma dGamma (so [Gamma, dGamma] = Y - Y^T),
+// its Frobenius norm -> squarings s, 2^-s, and the first Horner factor
+// P = I + X_s / degree.
+__global__ void __launch_bounds__(1024) exp_prepare_kernel(const double* Y, double* X, double* P, int n,
+                                                            double ds, int* sq, double* scale, int* err) {
+    __shared__ double red[32];
+    const int mu = blockIdx.x;
+    const size_t nn = (size_t)n * n;
+    const double* y = Y + mu * nn;
+    double* x = X + mu * nn;
+    double ss = 0.0;
+    for (size_t e = threadIdx.x; e < nn; e += blockDim.x) {
+        int k = (int)(e / n), l = (int)(e % n);
+        double v = 0.25 * ds * (y[e] - y[(size_t)l * n + k]);
+        x[e] = v;
+        ss += v * v;
+    }
+    ss = block_sum(ss, red);
+    const double nrm = sqrt(ss);
+    int s = 0;
+    while (nrm * ldexp(1.0, -s) > EXP_THETA && s < 64) s++;
+    if (s > EXP_MAX_SQUARINGS) {
+        if (threadIdx.x == 0) atomicOr(err, SGS_DEV_EXPNORM);
+        s = EXP_MAX_SQUARINGS;
+    }
+    const double sc = ldexp(1.0, -s);
+    if (threadIdx.x == 0) { sq[mu] = s; scale[mu] = sc; }
+    double* pp = P + mu * nn;
+    const double f = sc / EXP_TAYLOR_DEGREE;
+    for (size_t e = threadIdx.x; e < nn; e += blockDim.x) {
+        int k = (int)(e / n), l = (int)(e % n);
+        pp[e] = f * x[e] + (k == l ? 1.0 : 0.0);
+    }
+}
+
+__global__ void copy_kernel(const double* src, double* dst, size_t count) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        dst[e] = src[e];
+}
+
+}  // namespace sgs

@@ -37,6 +37,25 @@ def random_pure_gamma(n_modes: int, rng: np.random.Generator, parity: int = 1) -
     return 0.5 * (G - G.T)
 
 
+def clustered_pure_gammas(n_modes: int, M: int, rng: np.random.Generator, parity: int = 1,
+                          spread: float = 0.5) -> np.ndarray:
+    """M pure states Gamma_mu = O_mu Gamma_0 O_mu^T around one Haar-random
+    Gamma_0, with O_mu = exp(K_mu), K_mu antisymmetric with N(0, s^2) entries
+    and s = spread / (2 n_modes): mutual overlaps of order one, as between
+    the states of an ansatz grown by small rotations of existing states."""
+    import scipy.linalg
+    n = 2 * n_modes
+    base = random_pure_gamma(n_modes, rng, parity)
+    out = []
+    for _ in range(M):
+        K = rng.standard_normal((n, n)) * (spread / n)
+        K = K - K.T
+        O = scipy.linalg.expm(K)
+        G = O @ base @ O.T
+        out.append(0.5 * (G - G.T))
+    return np.ascontiguousarray(np.stack(out))
+
+
 def random_amplitudes(M: int, rng: np.random.Generator) -> np.ndarray:
     return np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, size=M))
 
