@@ -185,6 +185,26 @@ sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, do
 sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase, double* logabs);
 sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, double* C);
 
+/* Allocation-free variant of sgs_kernel_inverse.  The paper has no
+ * counterpart: this is a convenience for callers that must not allocate
+ * device memory during a call, such as a host program whose device memory
+ * is entirely owned by another framework's pool, or a latency-critical loop
+ * that cannot afford cudaMalloc's implicit device synchronisation.
+ *   S, inv: DEVICE pointers to batch row-major n x n FP64 matrices (S is read,
+ *   inv receives S^{-1}); logabsdet: DEVICE pointer to batch doubles
+ *   (log|det S|); stream: a cudaStream_t or NULL (legacy default stream).
+ * The call allocates nothing: its scratch is a file-scope device array of
+ * about 4.9 MiB that every GPU loading the library holds until exit.
+ * Limits: 1 <= n <= 1024 and batch * n <= 32768; larger sizes return
+ * SGS_EINVAL before any GPU work.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array, so calls that overlap on the GPU (other streams, other host
+ * threads) race; serialise them.  The call waits for its stream and returns
+ * SGS_ESINGULAR on a zero pivot, SGS_ECUDA on a CUDA error. */
+sgs_status sgs_kernel_inverse_static(const double* S, double* inv, double* logabsdet, int n, int batch,
+                                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,8 @@ SIGNATURES = {
     "sgs_kernel_inverse": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_pfaffian": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_dgemm": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp]),
+    "sgs_kernel_inverse_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_void_p]),
 }
 
 
@@ -300,6 +302,16 @@ def batched_inverse(S):
     if st != 0:
         raise SGSError(st, "batched inverse")
     return out, ld
+
+
+def batched_inverse_static(S_ptr, inv_ptr, logabsdet_ptr, n, batch, stream=None):
+    """Allocation-free batched inverse on caller-owned DEVICE buffers (raw
+    pointers, e.g. ``tensor.data_ptr()``); see sgs_kernel_inverse_static."""
+    st = _lib.sgs_kernel_inverse_static(ctypes.c_void_p(S_ptr), ctypes.c_void_p(inv_ptr),
+                                        ctypes.c_void_p(logabsdet_ptr), n, batch,
+                                        ctypes.c_void_p(stream) if stream else None)
+    if st != 0:
+        raise SGSError(st, "allocation-free batched inverse")
 
 
 def batched_pfaffian(Y):

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1003,3 +1004,99 @@ sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase,
 }
 
 }  // extern "C"
+
+// ====================================================== allocation-free inverse
+//
+// sgs_kernel_inverse_static: the batched Gauss-Jordan inverse for callers that
+// must not allocate device memory during the call.  Its scratch lives in one
+// file-scope device array; host code reaches it through the address that
+// cudaGetSymbolAddress returns for the current device (the array's name in
+// host code is only a stand-in, not a device address).
+
+#define SGS_STATIC_MAX_N 1024
+#define SGS_STATIC_MAX_BATCH_N 32768   // batch * n
+#define SGS_STATIC_PANEL 16
+// carve-up of the array (offsets in doubles, each a multiple of 32 = 256 bytes)
+#define SGS_STATIC_OFF_T 0                                                        // batch*n*16 doubles
+#define SGS_STATIC_OFF_PIV (SGS_STATIC_OFF_T + SGS_STATIC_MAX_BATCH_N * SGS_STATIC_PANEL)   // batch*n ints
+#define SGS_STATIC_OFF_SIGN (SGS_STATIC_OFF_PIV + SGS_STATIC_MAX_BATCH_N / 2)              // batch doubles
+#define SGS_STATIC_OFF_PTR (SGS_STATIC_OFF_SIGN + SGS_STATIC_MAX_BATCH_N)                  // 2*batch pointers
+#define SGS_STATIC_OFF_ERR (SGS_STATIC_OFF_PTR + 2 * SGS_STATIC_MAX_BATCH_N)               // one int
+#define SGS_STATIC_DOUBLES (SGS_STATIC_OFF_ERR + 32)                                       // ~4.9 MiB
+
+static __device__ __align__(256) double g_inverse_scratch[SGS_STATIC_DOUBLES];
+
+namespace {
+
+// pointer arrays for the batched panel and update kernels
+__global__ void static_fill_ptrs_kernel(double* inv, double* scratch, int n, int batch) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    double** W = reinterpret_cast<double**>(scratch + SGS_STATIC_OFF_PTR);
+    double** T = W + batch;
+    W[b] = inv + (size_t)b * n * n;
+    T[b] = scratch + SGS_STATIC_OFF_T + (size_t)b * SGS_STATIC_PANEL * n;
+}
+
+// undo the Gauss-Jordan row interchanges in place: column swaps in reverse order
+__global__ void static_unpermute_kernel(double* inv, const int* piv, int n) {
+    const int b = blockIdx.x;
+    double* A = inv + (size_t)b * n * n;
+    const int* pv = piv + (size_t)b * n;
+    for (int j = n - 1; j >= 0; j--) {
+        const int p = pv[j];
+        if (p != j) {
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                double t = A[(size_t)r * n + j];
+                A[(size_t)r * n + j] = A[(size_t)r * n + p];
+                A[(size_t)r * n + p] = t;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+struct StaticSlot { bool ready = false; double* base = nullptr; };
+StaticSlot g_static_slots[64];
+std::mutex g_static_mutex;
+
+}  // namespace
+
+extern "C" sgs_status sgs_kernel_inverse_static(const double* S, double* inv, double* logabsdet, int n, int batch,
+                                                void* stream) {
+    if (!S || !inv || !logabsdet || n < 1 || batch < 1) return SGS_EINVAL;
+    if (n > SGS_STATIC_MAX_N || (long long)batch * n > SGS_STATIC_MAX_BATCH_N) return SGS_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SGS_ECUDA;
+    double* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_slots[dev].ready) {
+            if (cudaGetSymbolAddress((void**)&g_static_slots[dev].base, g_inverse_scratch) != cudaSuccess)
+                return SGS_ECUDA;
+            g_static_slots[dev].ready = true;
+        }
+        base = g_static_slots[dev].base;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nn = (size_t)n * n;
+    double** W = reinterpret_cast<double**>(base + SGS_STATIC_OFF_PTR);
+    double** T = W + batch;
+    int* piv = reinterpret_cast<int*>(base + SGS_STATIC_OFF_PIV);
+    double* dsign = base + SGS_STATIC_OFF_SIGN;
+    int* err = reinterpret_cast<int*>(base + SGS_STATIC_OFF_ERR);
+    // the array keeps the previous call's contents: the error word must start at 0
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return SGS_ECUDA;
+    if (cudaMemcpyAsync(inv, S, batch * nn * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return SGS_ECUDA;
+    static_fill_ptrs_kernel<<<(batch + 127) / 128, 128, 0, st>>>(inv, base, n, batch);
+    counted();
+    if (launch_gj(n, batch, SGS_STATIC_PANEL, W, T, piv, logabsdet, dsign, err, 0.0, st) != cudaSuccess)
+        return SGS_ECUDA;
+    static_unpermute_kernel<<<batch, 256, 0, st>>>(inv, piv, n);
+    counted();
+    int herr = 0;
+    if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SGS_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SGS_ECUDA;
+    return herr ? SGS_ESINGULAR : SGS_OK;
+}
