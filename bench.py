@@ -44,12 +44,17 @@ def parse():
     ap.add_argument("--impl", default="sgs", choices=["sgs", "reference"])
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
     ap.add_argument("--workload", default="large", choices=["large", "small"])
+    ap.add_argument("--rank", type=int, default=0, help="override the ansatz rank M (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
-def workload(name):
-    return inp.LARGE if name == "large" else inp.SMALL
+def workload(name, rank=0):
+    import dataclasses
+    w = inp.LARGE if name == "large" else inp.SMALL
+    if rank > 0:
+        w = dataclasses.replace(w, rank=rank, name=f"{w.name.rsplit('_M', 1)[0]}_M{rank}")
+    return w
 
 
 def config_of(w, precision):
@@ -164,7 +169,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    w = workload(args.workload)
+    w = workload(args.workload, args.rank)
     for _ in range(args.warmup):
         oracle_sample(w, n_pairs=1, n_states=1)
     times = []
@@ -199,7 +204,7 @@ def run_sgs(args):
     import paper_2105_01088_gb300 as sgs
 
     sgs.use_torch_allocator()
-    w = workload(args.workload)
+    w = workload(args.workload, args.rank)
     p = w.model
     prec = PRECISIONS[args.precision]
     g, lam = inp.initial_state(p.n_modes, w.rank, w.seed + 1000 * rank, w.parity)
@@ -254,25 +259,30 @@ def run_sgs(args):
     h2d = w.rank * n * n * 8
     d2h = w.rank * n * n * 8 + w.rank * 16 + 8
 
-    # roofline of the dominant stage
+    # roofline of the dominant kernel, gemm_f64_kernel (the FP64 MMA GEMM: ~89% of the step's kernel time
+    # in the launch list), measured on its largest launch, V = D W over all pairs (2 n^3 P flops)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    stage = max(prof, key=lambda s: prof[s][0])
-    s_ms, s_fl, s_by = prof[stage]
-    if s_fl > 0:
+    s_ms, s_fl, s_by = prof["eom_v"]
+    roof = None
+    if s_ms > 0 and s_fl > 0:
         achieved = s_fl / (s_ms * 1e-3) / 1e12
+        launches_v = args.steps
+        traffic = None
+        tfile = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tfile) and args.precision == "fp64":
+            t = json.load(open(tfile)).get("gemm_f64_eom_V", {})
+            if t.get("n") == n and t.get("pairs") == w.rank * (w.rank - 1) // 2:
+                traffic = t.get("bytes_per_launch")
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_fp64_mma, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp64_mma, "traffic": None, "kernel": stage,
-                "peak_source": "measured live: FP64 m8n8k4 MMA throughput probe (sgs_probe_peak)"}
-    else:
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        achieved = s_by / (s_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": stage,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
+                "frac": achieved / peak_fp64_mma, "traffic": traffic,
+                "kernel": "gemm_f64_kernel (V = D W, all pairs, FP64 m8n8k4 MMA)",
+                "flops_per_launch": s_fl / launches_v, "ms_per_launch": s_ms / launches_v,
+                "peak_source": "measured live: FP64 m8n8k4 MMA throughput probe (sgs_probe_peak); "
+                               "not in MEASURED_PEAKS.json"}
     stages = {s: {"ms_per_step": v[0] / args.steps, "tflops": (v[1] / (v[0] * 1e-3) / 1e12) if v[0] > 0 and v[1] > 0
                   else None} for s, v in prof.items()}
 

@@ -151,17 +151,20 @@ typedef enum {
     SGS_STAGE_PAIR_DELTA = 1,      /* Im Delta = (G_a - G_b) S^{-1} */
     SGS_STAGE_PHASE_PFAFFIAN = 2,  /* Pf(G_0 + Delta^{a,b}) */
     SGS_STAGE_AMPLITUDES = 3,      /* G, h, Wick contractions, h lambda = E G lambda */
-    SGS_STAGE_EOM_GEMM = 4,        /* S^{-1} F S^{-1}, D W, (D W) D, Gamma F Gamma */
-    SGS_STAGE_EOM_ASSEMBLY = 5,    /* Delta F Delta planes, dGamma/ds */
-    SGS_STAGE_UPDATE = 6,          /* exp step, R Gamma R^T, re-purification */
-    SGS_N_STAGES = 7
+    SGS_STAGE_EOM_W = 4,           /* W = (S^{-1} F) S^{-1} and Gamma F Gamma (antisymmetric products) */
+    SGS_STAGE_EOM_V = 5,           /* V = D W: one batched general product over all pairs */
+    SGS_STAGE_EOM_X = 6,           /* X = V D (antisymmetric) */
+    SGS_STAGE_EOM_ASSEMBLY = 7,    /* Delta F Delta planes, dGamma/ds */
+    SGS_STAGE_UPDATE = 8,          /* exp step, R Gamma R^T, re-purification */
+    SGS_N_STAGES = 9
 } sgs_stage;
 sgs_status sgs_set_profiling(sgs_ctx* ctx, int enable);
 sgs_status sgs_get_profile(const sgs_ctx* ctx, double* ms, double* flops, double* bytes, long long* launches);
 
 /* Measured throughput (TFLOP/s) of an FP64 pipe of the current device:
  * kind 0 = the m8n8k4 FP64 MMA (the path of every FP64 product here),
- * kind 1 = FP64 FMA on the CUDA cores. */
+ * kind 1 = FP64 FMA on the CUDA cores, kind 2 = both interleaved in one
+ * kernel (their sum shows whether the two share one pipe). */
 sgs_status sgs_probe_peak(int kind, double* tflops);
 
 /* Majorana form of the Anderson impurity of Sec. IV (H_0 + H_I) with

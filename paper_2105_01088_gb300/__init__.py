@@ -260,7 +260,8 @@ class Solver:
         self._check(_lib.sgs_get_derivative(self._ctx, instance, _ptr(d)))
         return d
 
-    STAGES = ("pair_inverse", "pair_delta", "phase_pfaffian", "amplitudes", "eom_gemm", "eom_assembly", "update")
+    STAGES = ("pair_inverse", "pair_delta", "phase_pfaffian", "amplitudes", "eom_w", "eom_v", "eom_x",
+              "eom_assembly", "update")
 
     def set_profiling(self, enable=True):
         self._check(_lib.sgs_set_profiling(self._ctx, 1 if enable else 0))
@@ -285,7 +286,8 @@ class Solver:
 # ------------------------------------------------------------ building blocks
 
 def probe_peak(kind=0):
-    """Measured TFLOP/s of the FP64 MMA (kind 0) or FP64 FMA (kind 1) pipe."""
+    """Measured TFLOP/s of the FP64 MMA (kind 0), FP64 FMA (kind 1), or both
+    interleaved (kind 2)."""
     out = np.zeros(1)
     st = _lib.sgs_probe_peak(kind, _ptr(out))
     if st != 0:

@@ -490,8 +490,8 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I) {
     const double n3 = (double)n * n * n;
     InstDev d = I.dev();
     cudaError_t e;
-    c->stage(SGS_STAGE_EOM_GEMM);
-    c->stage_flops[SGS_STAGE_EOM_GEMM] += 4.0 * n3 * P + n3 * M;   // Wr, X antisymmetric; V full; GFG
+    c->stage(SGS_STAGE_EOM_W);
+    c->stage_flops[SGS_STAGE_EOM_W] += n3 * P + n3 * M;   // Wr, Gamma F Gamma: antisymmetric
     // per state: T2 = F Gamma (s0), GFG = Gamma T2 (s4)
     state_sparse_left_kernel<<<dim3(grid_chunks(nn, 256, 256), M), 256, 0, st>>>(d, I.fimp_state, I.s[0]);
     counted();
@@ -508,10 +508,15 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I) {
         g.mode = GEMM_SKEW;
         if ((e = gemm(g, st)) != cudaSuccess) return e;
         // V = D Wr
+        c->stage(SGS_STAGE_EOM_V);
+        c->stage_flops[SGS_STAGE_EOM_V] += 2.0 * n3 * P;
+        c->stage_bytes[SGS_STAGE_EOM_V] += 8.0 * nn * (2.0 * P + M);   // read Wr, write V; Gamma once
         g = gb_basic(n, n, n, I.p_ga, n, I.p_wr, n, I.p_va, n, P);
         g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
         if ((e = gemm(g, st)) != cudaSuccess) return e;
         // X = V D
+        c->stage(SGS_STAGE_EOM_X);
+        c->stage_flops[SGS_STAGE_EOM_X] += n3 * P;
         g = gb_basic(n, n, n, I.p_va, n, I.p_ga, n, I.p_xa, n, P);
         g.B2 = (const double* const*)I.p_gb; g.sB2 = -1.0;
         g.mode = GEMM_SKEW;
@@ -816,7 +821,7 @@ sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double*
 }
 
 sgs_status sgs_probe_peak(int kind, double* tflops) {
-    if (!tflops || kind < 0 || kind > 1) return SGS_EINVAL;
+    if (!tflops || kind < 0 || kind > 2) return SGS_EINVAL;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -830,7 +835,8 @@ sgs_status sgs_probe_peak(int kind, double* tflops) {
     for (int rep = 0; rep < 4; rep++) {
         cudaEventRecord(e0);
         if (kind == 0) probe_dmma_kernel<<<blocks, thr>>>(out, 0.999);
-        else probe_dfma_kernel<<<blocks, thr>>>(out, 0.999);
+        else if (kind == 1) probe_dfma_kernel<<<blocks, thr>>>(out, 0.999);
+        else probe_mixed_kernel<<<blocks, thr>>>(out, 0.999);
         cudaEventRecord(e1);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -843,8 +849,9 @@ sgs_status sgs_probe_peak(int kind, double* tflops) {
     cudaFree(out);
     if (err != cudaSuccess) return SGS_ECUDA;
     // m8n8k4: 512 flops per warp-instruction; FMA: 2 flops per thread-instruction
-    const double fl = (kind == 0) ? (double)blocks * (thr / 32) * PROBE_ITERS * 512.0
-                                  : (double)blocks * thr * PROBE_ITERS * 8 * 2.0;
+    const double fmma = (double)blocks * (thr / 32) * PROBE_ITERS * 512.0;
+    const double ffma = (double)blocks * thr * PROBE_ITERS * 8 * 2.0;
+    const double fl = (kind == 0) ? fmma : (kind == 1) ? ffma : 0.5 * fmma + 0.5 * ffma;
     *tflops = fl / (best * 1e-3) / 1e12;
     return SGS_OK;
 }
