@@ -230,7 +230,7 @@ def run_sgs(args):
         dist.barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
-    prof, launches = solver.profile()
+    prof, launches, gemm_prof = solver.profile()
     solver.set_profiling(False)
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if dist:
@@ -259,30 +259,40 @@ def run_sgs(args):
     h2d = w.rank * n * n * 8
     d2h = w.rank * n * n * 8 + w.rank * 16 + 8
 
-    # roofline of the dominant kernel, gemm_f64_kernel (the FP64 MMA GEMM: ~89% of the step's kernel time
-    # in the launch list), measured on its largest launch, V = D W over all pairs (2 n^3 P flops)
+    # roofline of the dominant kernel, gemm_f64_kernel (the FP64 m8n8k4 MMA GEMM: ~89% of the FP64 step's
+    # kernel time, most of the mixed step's): algorithmic flops of all its launches / their summed time
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    s_ms, s_fl, s_by = prof["eom_v"]
+    g_ms, g_fl, g_n = gemm_prof
     roof = None
-    if s_ms > 0 and s_fl > 0:
-        achieved = s_fl / (s_ms * 1e-3) / 1e12
-        launches_v = args.steps
+    if g_ms > 0:
+        achieved = g_fl / (g_ms * 1e-3) / 1e12
         traffic = None
         tfile = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tfile) and args.precision == "fp64":
-            t = json.load(open(tfile)).get("gemm_f64_eom_V", {})
-            if t.get("n") == n and t.get("pairs") == w.rank * (w.rank - 1) // 2:
+        if os.path.exists(tfile):
+            t = json.load(open(tfile)).get(f"gemm_f64_all_{args.precision}", {})
+            if t.get("n") == n and t.get("rank") == w.rank:
                 traffic = t.get("bytes_per_launch")
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_fp64_mma, "unit": "TFLOP/s",
                 "frac": achieved / peak_fp64_mma, "traffic": traffic,
-                "kernel": "gemm_f64_kernel (V = D W, all pairs, FP64 m8n8k4 MMA)",
-                "flops_per_launch": s_fl / launches_v, "ms_per_launch": s_ms / launches_v,
+                "kernel": "gemm_f64_kernel (FP64 m8n8k4 MMA; all its launches: Gauss-Jordan and Pfaffian "
+                          "updates, pair and state products)",
+                "launches": int(g_n), "flops_per_launch": g_fl / max(g_n, 1), "ms_per_launch": g_ms / max(g_n, 1),
                 "peak_source": "measured live: FP64 m8n8k4 MMA throughput probe (sgs_probe_peak); "
                                "not in MEASURED_PEAKS.json"}
+    tc_roof = None
+    if args.precision != "fp64" and prof["eom_v"][0] > 0:
+        bf16 = peaks.get("bf16_tflops", 1900.0)
+        ratio = {"tf32": 1.1 / 2.25, "3xtf32": 1.1 / 2.25 / 3.0, "bf16": 1.0}[args.precision]
+        v_ms, v_fl, _ = prof["eom_v"]
+        a = v_fl / (v_ms * 1e-3) / 1e12
+        tc_roof = {"bound": "tensor", "kernel": f"gemm_tc_kernel (tcgen05 {args.precision}, V = D W)",
+                   "achieved": a, "peak": bf16 * ratio, "unit": "TFLOP/s", "frac": a / (bf16 * ratio),
+                   "peak_source": "MEASURED_PEAKS.json bf16_tflops x nominal ratio "
+                                  f"({args.precision}: {ratio:.3f})"}
     stages = {s: {"ms_per_step": v[0] / args.steps, "tflops": (v[1] / (v[0] * 1e-3) / 1e12) if v[0] > 0 and v[1] > 0
                   else None} for s, v in prof.items()}
 
@@ -291,7 +301,7 @@ def run_sgs(args):
             "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": config_of(w, args.precision),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(launches), "roofline": roof, "clocks": ck, "stages": stages,
+            "gpu_launches": int(launches), "roofline": roof, "tc_roofline": tc_roof, "clocks": ck, "stages": stages,
             "energy_last": float(E[0, -1]), "fp64_mma_peak_tflops": peak_fp64_mma}
     solver.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -145,7 +145,10 @@ void sgs_set_allocator(sgs_alloc_fn alloc, sgs_free_fn release, void* user);
  * time (ms), the algorithmic FP64 flops (useful work: an antisymmetric
  * product counts n^3, a general one 2 n^3, the Gauss-Jordan inverse 2 n^3,
  * the complex Pfaffian 4 n^3 / 3), the algorithmic bytes of memory-bound
- * stages, and the number of kernels the library launched. */
+ * stages, and the number of kernels the library launched.  gemm_f64 (may be
+ * NULL) receives [total ms, algorithmic flops, launches] of the FP64 MMA GEMM
+ * kernel over all its launches (timed one by one; the pass-through squaring
+ * launches of the exponential are left out). */
 typedef enum {
     SGS_STAGE_PAIR_INVERSE = 0,    /* S = G_a + G_b, blocked Gauss-Jordan inverse */
     SGS_STAGE_PAIR_DELTA = 1,      /* Im Delta = (G_a - G_b) S^{-1} */
@@ -159,7 +162,8 @@ typedef enum {
     SGS_N_STAGES = 9
 } sgs_stage;
 sgs_status sgs_set_profiling(sgs_ctx* ctx, int enable);
-sgs_status sgs_get_profile(const sgs_ctx* ctx, double* ms, double* flops, double* bytes, long long* launches);
+sgs_status sgs_get_profile(const sgs_ctx* ctx, double* ms, double* flops, double* bytes, long long* launches,
+                           double* gemm_f64);
 
 /* Measured throughput (TFLOP/s) of an FP64 pipe of the current device:
  * kind 0 = the m8n8k4 FP64 MMA (the path of every FP64 product here),
@@ -187,6 +191,14 @@ int sgs_build_anderson(int n_bath, int n_channels, double U, double eps_d, doubl
 sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, double* logabsdet);
 sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase, double* logabs);
 sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, double* C);
+
+/* sgs_kernel_gemm_tc: batch C = A B on the tcgen05 tensor cores, A: m x k
+ * row-major, Bt: n x k row-major (= B^T, the K-major form the tensor core
+ * reads), C: m x n FP64.  kind 0 = TF32, 1 = BF16, 2 = 3xTF32 (split
+ * operands, three products, fp32 accumulation).  k must be a multiple of 8.
+ * Returns SGS_ETIMEOUT if a bounded on-device wait ran out. */
+sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, int k, int batch, int kind,
+                              double* C);
 
 /* Allocation-free variant of sgs_kernel_inverse.  The paper has no
  * counterpart: this is a convenience for callers that must not allocate

@@ -67,11 +67,13 @@ SIGNATURES = {
     "sgs_build_anderson": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _ip, _dp, _dp]),
     "sgs_set_profiling": (ctypes.c_int, [_ctxp, ctypes.c_int]),
-    "sgs_get_profile": (ctypes.c_int, [_ctxp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "sgs_get_profile": (ctypes.c_int, [_ctxp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "sgs_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
     "sgs_kernel_inverse": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_pfaffian": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_dgemm": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp]),
+    "sgs_kernel_gemm_tc": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _dp]),
     "sgs_kernel_inverse_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_void_p]),
 }
@@ -267,12 +269,13 @@ class Solver:
         self._check(_lib.sgs_set_profiling(self._ctx, 1 if enable else 0))
 
     def profile(self):
-        """{stage: (ms, flops, bytes)}, launches"""
+        """({stage: (ms, flops, bytes)}, launches, (gemm_f64 ms, flops, launches))"""
         k = len(self.STAGES)
         ms, fl, by = np.zeros(k), np.zeros(k), np.zeros(k)
+        gk = np.zeros(3)
         nl = ctypes.c_longlong(0)
-        self._check(_lib.sgs_get_profile(self._ctx, _ptr(ms), _ptr(fl), _ptr(by), ctypes.byref(nl)))
-        return {s: (ms[i], fl[i], by[i]) for i, s in enumerate(self.STAGES)}, nl.value
+        self._check(_lib.sgs_get_profile(self._ctx, _ptr(ms), _ptr(fl), _ptr(by), ctypes.byref(nl), _ptr(gk)))
+        return {s: (ms[i], fl[i], by[i]) for i, s in enumerate(self.STAGES)}, nl.value, tuple(gk)
 
     def close(self):
         if getattr(self, "_ctx", None):
@@ -314,6 +317,19 @@ def batched_inverse_static(S_ptr, inv_ptr, logabsdet_ptr, n, batch, stream=None)
                                         ctypes.c_void_p(stream) if stream else None)
     if st != 0:
         raise SGSError(st, "allocation-free batched inverse")
+
+
+def batched_gemm_tc(A, B, kind=0):
+    """batch C = A B on the tcgen05 tensor cores (kind 0 TF32, 1 BF16, 2 3xTF32)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    Bt = np.ascontiguousarray(np.swapaxes(np.asarray(B, dtype=np.float64), 1, 2))
+    b, m, k = A.shape
+    n = Bt.shape[1]
+    C = np.zeros((b, m, n))
+    st = _lib.sgs_kernel_gemm_tc(_ptr(A), _ptr(Bt), m, n, k, b, kind, _ptr(C))
+    if st != 0:
+        raise SGSError(st, "tensor-core gemm")
+    return C
 
 
 def batched_pfaffian(Y):

@@ -10,6 +10,7 @@
 // dense product is real: Wr = (Si Fr) Si, V = D Wr, X = V D, W D = (D W)^T;
 // the Fi parts are rank <= (#impurity Majoranas) corrections.
 #pragma once
+#include <cuda_bf16.h>
 #include "common.cuh"
 
 namespace sgs {
@@ -199,33 +200,71 @@ __global__ void pair_lr_kernel(InstDev d, const double* si, const double* imd, c
     }
 }
 
-// Q = Delta F Delta (real and imaginary planes), in place of X (-> Qr) and Wr (-> Qi):
+// Q = Delta F Delta (real and imaginary planes) from X = D Wr D, Wr and V = D Wr
+// (T: double on the FP64 path, float on the tensor-core path):
 //   Qr = X + 4 Wr + 2 (L1 Si[imp,:] + Si[:,imp] L1^T)
 //   Qi = 4 L2 Si[imp,:] - L1 Im[imp,:] - 2 (V - V^T)
-__global__ void pair_q_kernel(InstDev d, const double* si, const double* imd, const double* lr,
-                              const double* va, double* xa_qr, double* wr_qi) {
+// On the FP64 path the outputs alias the inputs (qr_out = xa_in, qi_out = wr_in):
+// each element is read and then written by the same thread.
+template <typename T>
+__global__ void pair_q_kernel(InstDev d, const double* si, const double* imd, const double* lr, const T* va,
+                              const T* xa_in, const T* wr_in, double* qr_out, double* qi_out) {
     const int p = blockIdx.y;
     const int n = d.n, ni = d.nimp;
     const double* s = si + (size_t)p * nn(d);
     const double* im = imd + (size_t)p * nn(d);
     const double* L1 = lr + (size_t)p * 2 * n * ni;
     const double* L2 = L1 + (size_t)n * ni;
-    const double* v = va + (size_t)p * nn(d);
-    double* X = xa_qr + (size_t)p * nn(d);
-    double* Wq = wr_qi + (size_t)p * nn(d);
+    const T* v = va + (size_t)p * nn(d);
+    const T* X = xa_in + (size_t)p * nn(d);
+    const T* W = wr_in + (size_t)p * nn(d);
+    double* Qr = qr_out + (size_t)p * nn(d);
+    double* Qi = qi_out + (size_t)p * nn(d);
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn(d); e += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(e / n), l = (int)(e % n);
-        double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        double a1 = 0.0, a2 = 0.0;
         for (int m = 0; m < ni; m++) {
             const int im_m = d.imp[m];
             const double s_ml = s[(size_t)im_m * n + l];
             a1 += L1[k * ni + m] * s_ml + s[(size_t)k * n + im_m] * L1[l * ni + m];
             a2 += 4.0 * L2[k * ni + m] * s_ml - L1[k * ni + m] * im[(size_t)im_m * n + l];
         }
-        const double qr = X[e] + 4.0 * Wq[e] + 2.0 * a1;
-        const double qi = a2 - 2.0 * (v[e] - v[(size_t)l * n + k]);
-        X[e] = qr;
-        Wq[e] = qi;
+        const double qr = (double)X[e] + 4.0 * (double)W[e] + 2.0 * a1;
+        const double qi = a2 - 2.0 * ((double)v[e] - (double)v[(size_t)l * n + k]);
+        Qr[e] = qr;
+        Qi[e] = qi;
+    }
+}
+
+// Tensor-core operands from FP64 (or fp32) data: x = src - src2 (src2 optional)
+// to fp32 (TF32 kind), bf16, or an exact fp32 split hi + lo with hi on the
+// tf32 grid (3xTF32).  Sources are n x n with leading dimension n; operands
+// have leading dimension ldp >= n (a multiple of 8: a 16-byte chunk holds 8
+// bf16 values), columns n..ldp-1 zero.
+template <typename S>
+__global__ void lp_convert_kernel(const S* const* src, const double* const* src2, void* const* hi, void* const* lo,
+                                  int n, int ldp, int kind) {
+    const int b = blockIdx.y;
+    const S* x0 = src[b];
+    const double* x1 = src2 ? src2[b] : nullptr;
+    const size_t count = (size_t)n * ldp;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / ldp), q = (int)(e % ldp);
+        double x = 0.0;
+        if (q < n) {
+            const size_t o = (size_t)r * n + q;
+            x = (double)x0[o] - (x1 ? x1[o] : 0.0);
+        }
+        if (kind == 1) {
+            static_cast<__nv_bfloat16*>(hi[b])[e] = __float2bfloat16_rn((float)x);
+        } else if (kind == 2) {
+            const float f = (float)x;
+            const float h = __uint_as_float(__float_as_uint(f) & 0xffffe000u);
+            static_cast<float*>(hi[b])[e] = h;
+            static_cast<float*>(lo[b])[e] = (float)(x - (double)h);
+        } else {
+            static_cast<float*>(hi[b])[e] = (float)x;
+        }
     }
 }
 

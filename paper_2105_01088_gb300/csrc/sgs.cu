@@ -29,6 +29,7 @@
 #include "eom.cuh"
 #include "update.cuh"
 #include "probe.cuh"
+#include "gemm_tc.cuh"
 
 using namespace sgs;
 
@@ -73,6 +74,18 @@ struct Instance {
     int steps_since_profile = 0;
     double* eigscratch = nullptr;
     int* err = nullptr;
+
+    // tensor-core (mixed precision) operands of the equation of motion, per pair:
+    // low-precision hi (fp32 or bf16) and lo (3xTF32) parts of S^{-1}, T1 = S^{-1} F,
+    // D = G_a - G_b, W and V, fp32 results W, V, X
+    int tc_kind = -1;
+    int ldp = 0;          // leading dimension of the low-precision operands (multiple of 8)
+    void *si_hi = nullptr, *si_lo = nullptr, *t1_hi = nullptr, *t1_lo = nullptr, *d_hi = nullptr, *d_lo = nullptr;
+    void *wr_hi = nullptr, *wr_lo = nullptr, *va_hi = nullptr, *va_lo = nullptr;
+    float *wr32 = nullptr, *va32 = nullptr, *xa32 = nullptr;
+    void **q_si_hi = nullptr, **q_si_lo = nullptr, **q_t1_hi = nullptr, **q_t1_lo = nullptr, **q_d_hi = nullptr,
+         **q_d_lo = nullptr, **q_wr_hi = nullptr, **q_wr_lo = nullptr, **q_va_hi = nullptr, **q_va_lo = nullptr,
+         **q_wr32 = nullptr, **q_va32 = nullptr, **q_xa32 = nullptr;
 
     // pointer arrays (device)
     double **p_work = nullptr, **p_tbuf = nullptr, **p_si = nullptr, **p_imd = nullptr, **p_wr = nullptr,
@@ -138,6 +151,10 @@ struct sgs_ctx {
     double stage_flops[SGS_N_STAGES] = {0};
     double stage_bytes[SGS_N_STAGES] = {0};
     long long launches = 0;
+    // every FP64 GEMM launch (except the pass-through squarings) timed on its own
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gmarks;
+    double gemm_ms = 0.0, gemm_flops = 0.0;
+    long long gemm_count = 0;
 
     cudaEvent_t next_event() {
         if (ev_used == ev_pool.size()) {
@@ -162,6 +179,12 @@ struct sgs_ctx {
             stage_ms[m.stage] += ms;
         }
         marks.clear();
+        for (auto& m : gmarks) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, m.first, m.second);
+            gemm_ms += ms;
+        }
+        gmarks.clear();
         ev_used = 0;
         open_stage = -1;
     }
@@ -379,13 +402,64 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.p_gamma = upload_ptrs(c, g);
     I.p_dgamma = upload_ptrs(c, dg);
     for (int j = 0; j < 5; j++) I.p_s[j] = upload_ptrs(c, ss[j]);
+
+    if (I.prec != SGS_FP64 && P > 0) {
+        I.tc_kind = (I.prec == SGS_MIXED_TF32) ? TC_TF32 : (I.prec == SGS_MIXED_BF16) ? TC_BF16 : TC_3XTF32;
+        const size_t esz = (I.tc_kind == TC_BF16) ? 2 : 4;
+        const bool split = I.tc_kind == TC_3XTF32;
+        I.ldp = (n + 7) & ~7;
+        const size_t lpn = (size_t)n * I.ldp;           // elements of one padded operand
+        const size_t bytes = (size_t)P * lpn * esz;
+        I.si_hi = c->dalloc(bytes); I.t1_hi = c->dalloc(bytes); I.d_hi = c->dalloc(bytes);
+        I.wr32 = c->alloc<float>(P * nn); I.va32 = c->alloc<float>(P * nn); I.xa32 = c->alloc<float>(P * nn);
+        if (I.tc_kind == TC_TF32 && I.ldp == n) {
+            I.wr_hi = I.wr32;   // fp32 results feed the next product directly
+            I.va_hi = I.va32;
+        } else {
+            I.wr_hi = c->dalloc(bytes);
+            I.va_hi = c->dalloc(bytes);
+        }
+        if (split) {
+            I.si_lo = c->dalloc(bytes); I.t1_lo = c->dalloc(bytes); I.d_lo = c->dalloc(bytes);
+            I.wr_lo = c->dalloc(bytes); I.va_lo = c->dalloc(bytes);
+        }
+        if (!I.si_hi || !I.t1_hi || !I.d_hi || !I.wr32 || !I.va32 || !I.xa32 || !I.wr_hi || !I.va_hi ||
+            (split && (!I.si_lo || !I.t1_lo || !I.d_lo || !I.wr_lo || !I.va_lo))) {
+            c->err = "device allocation failed (tensor-core operands)";
+            return SGS_ENOMEM;
+        }
+        auto arr = [&](void* base, size_t stride) {
+            std::vector<void*> v;
+            for (int p = 0; p < P; p++) v.push_back(base ? (uint8_t*)base + p * stride : nullptr);
+            return upload_ptrs(c, v);
+        };
+        const size_t lp = lpn * esz, f4 = nn * 4;
+        I.q_si_hi = arr(I.si_hi, lp); I.q_t1_hi = arr(I.t1_hi, lp); I.q_d_hi = arr(I.d_hi, lp);
+        I.q_wr_hi = arr(I.wr_hi, lp);
+        I.q_va_hi = arr(I.va_hi, lp);
+        I.q_wr32 = arr(I.wr32, f4); I.q_va32 = arr(I.va32, f4); I.q_xa32 = arr(I.xa32, f4);
+        I.q_si_lo = arr(I.si_lo, lp); I.q_t1_lo = arr(I.t1_lo, lp); I.q_d_lo = arr(I.d_lo, lp);
+        I.q_wr_lo = arr(I.wr_lo, lp); I.q_va_lo = arr(I.va_lo, lp);
+    }
     return SGS_OK;
 }
 
 // ------------------------------------------------------------------ launches
 
-inline cudaError_t gemm(const GemmBatch& g, cudaStream_t st) {
+// every FP64 product of the library goes through here; flops = algorithmic work of
+// the launch (antisymmetric outputs count half), < 0 = not profiled
+inline cudaError_t gemm(sgs_ctx* c, const GemmBatch& g, cudaStream_t st, double flops) {
     counted();
+    if (c && c->prof && flops >= 0.0) {
+        cudaEvent_t a = c->next_event(), b = c->next_event();
+        cudaEventRecord(a, st);
+        cudaError_t e = gemm_f64(g, st);
+        cudaEventRecord(b, st);
+        c->gmarks.push_back({a, b});
+        c->gemm_flops += flops;
+        c->gemm_count++;
+        return e;
+    }
     return gemm_f64(g, st);
 }
 
@@ -397,8 +471,8 @@ GemmBatch gb_basic(int m, int n, int k, double** A, int lda, double** B, int ldb
     return g;
 }
 
-cudaError_t launch_gj(int n, int batch, int bsz, double** W, double** T, int* piv, double* logdet, double* dsign,
-                      int* err, double tiny, cudaStream_t st) {
+cudaError_t launch_gj(sgs_ctx* c, int n, int batch, int bsz, double** W, double** T, int* piv, double* logdet,
+                      double* dsign, int* err, double tiny, cudaStream_t st) {
     const size_t smem = (size_t)n * bsz * sizeof(double) + bsz * sizeof(double);
     cudaFuncSetAttribute(gj_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int k0 = 0; k0 < n; k0 += bsz) {
@@ -410,14 +484,14 @@ cudaError_t launch_gj(int n, int batch, int bsz, double** W, double** T, int* pi
         g.offA = k0;
         g.Cin = (const double* const*)W; g.ldcin = n; g.beta = 1.0;
         g.mode = GEMM_GJ; g.gj_k0 = k0; g.gj_b = bb;
-        cudaError_t e = gemm(g, st);
+        cudaError_t e = gemm(c, g, st, 2.0 * n * (double)(n - bb) * bb * batch);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_pf(int n, int batch, int bsmax, double** Y, double** TU, double** PK, double** upA, double** upB,
-                      double** upC, double* logabs, double* phase, int* err, cudaStream_t st) {
+cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, double** TU, double** PK, double** upA,
+                      double** upB, double** upC, double* logabs, double* phase, int* err, cudaStream_t st) {
     const size_t smem = (4 * (size_t)n + 4 * bsmax) * sizeof(double);
     cudaFuncSetAttribute(pf_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int k0 = 0; k0 < n; k0 += 2 * bsmax) {
@@ -433,7 +507,9 @@ cudaError_t launch_pf(int n, int batch, int bsmax, double** Y, double** TU, doub
         g.transB = 1;
         g.offC = (long long)e0 * n + e0;
         g.Cin = (const double* const*)upC; g.offCin = g.offC; g.ldcin = n; g.beta = 1.0;
-        cudaError_t e = gemm(g, st);
+        // the rank-2b complex update is antisymmetric: half of each real product is needed
+        const double m2 = (double)(n - e0) * (n - e0);
+        cudaError_t e = gemm(c, g, st, m2 * 4.0 * bs * 2 * batch);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -453,7 +529,7 @@ cudaError_t pair_pass(sgs_ctx* c, Instance& I, int eslot) {
         counted();
         // S has entries of magnitude <= 2; two states of opposite parity give a
         // pivot at rounding level (~1e-15), same-parity pairs O(0.1)
-        cudaError_t e = launch_gj(n, P, I.gj_b, I.p_work, I.p_tbuf, I.piv, I.logdet, I.dsign, I.err, 1e-12, st);
+        cudaError_t e = launch_gj(c, n, P, I.gj_b, I.p_work, I.p_tbuf, I.piv, I.logdet, I.dsign, I.err, 1e-12, st);
         if (e != cudaSuccess) return e;
         gj_perm_kernel<<<(P + 127) / 128, 128, 0, st>>>(I.piv, I.perm, n, P);
         gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.p_work, I.p_si, I.perm, n);
@@ -464,13 +540,13 @@ cudaError_t pair_pass(sgs_ctx* c, Instance& I, int eslot) {
         GemmBatch g = gb_basic(n, n, n, I.p_ga, n, I.p_si, n, I.p_imd, n, P);
         g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
         g.mode = GEMM_SKEW;
-        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        if ((e = gemm(c, g, st, n3 * P)) != cudaSuccess) return e;
         if (I.Ppf > 0) {
             c->stage(SGS_STAGE_PHASE_PFAFFIAN);
             c->stage_flops[SGS_STAGE_PHASE_PFAFFIAN] += 4.0 / 3.0 * n3 * I.Ppf;
             pf_build_kernel<<<dim3(grid_chunks(nn, 256, 64), I.Ppf), 256, 0, st>>>(d, I.si, I.imd, I.work);
             counted();
-            e = launch_pf(n, I.Ppf, I.pf_bs, I.p_Y, I.p_TU, I.p_pack, I.p_upA, I.p_upB, I.p_upC, I.pflog,
+            e = launch_pf(c, n, I.Ppf, I.pf_bs, I.p_Y, I.p_TU, I.p_pack, I.p_upA, I.p_upB, I.p_upC, I.pflog,
                           I.pfphase, I.err, st);
             if (e != cudaSuccess) return e;
         }
@@ -498,35 +574,91 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I) {
     {
         GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_s[0], n, I.p_s[4], n, M);
         g.mode = GEMM_SKEW;
-        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
     }
-    if (P > 0) {
+    if (P > 0 && I.tc_kind >= 0) {
+        // tensor-core path: W = T1 S^{-1}, V = D W, X = V D, every B antisymmetric, so its
+        // K-major form is -B and alpha = -1
+        const int kind = I.tc_kind;
+        const unsigned gch = grid_chunks(nn, 256, 64);
+        pair_sparse_right_kernel<<<dim3(gch, P), 256, 0, st>>>(d, I.si, I.fimp, I.work);
+        const int ldp = I.ldp;
+        const bool direct = (I.wr_hi == I.wr32);   // fp32 results used as operands as they are
+        lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_si, nullptr, I.q_si_hi,
+                                                                  I.q_si_lo, n, ldp, kind);
+        lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_work, nullptr, I.q_t1_hi,
+                                                                  I.q_t1_lo, n, ldp, kind);
+        lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_ga,
+                                                                  (const double* const*)I.p_gb, I.q_d_hi, I.q_d_lo,
+                                                                  n, ldp, kind);
+        counted(); counted(); counted(); counted();
+        TcBatch t{};
+        t.m = n; t.n = n; t.k = n; t.lda = ldp; t.ldb = ldp; t.ldc = n; t.alpha = -1.0; t.out_f64 = 0;
+        t.err = I.err; t.batch = P;
+        t.A = (const void* const*)I.q_t1_hi; t.A2 = (const void* const*)I.q_t1_lo;
+        t.B = (const void* const*)I.q_si_hi; t.B2 = (const void* const*)I.q_si_lo;
+        t.C = I.q_wr32; t.skew = 1;
+        if ((e = gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        counted();
+        if (!direct) {
+            lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_wr32, nullptr, I.q_wr_hi,
+                                                                     I.q_wr_lo, n, ldp, kind);
+            counted();
+        }
+        c->stage(SGS_STAGE_EOM_V);
+        c->stage_flops[SGS_STAGE_EOM_V] += 2.0 * n3 * P;
+        t.A = (const void* const*)I.q_d_hi; t.A2 = (const void* const*)I.q_d_lo;
+        t.B = (const void* const*)I.q_wr_hi; t.B2 = (const void* const*)I.q_wr_lo;
+        t.C = I.q_va32; t.skew = 0;
+        if ((e = gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        counted();
+        c->stage(SGS_STAGE_EOM_X);
+        c->stage_flops[SGS_STAGE_EOM_X] += n3 * P;
+        if (!direct) {
+            lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_va32, nullptr, I.q_va_hi,
+                                                                     I.q_va_lo, n, ldp, kind);
+            counted();
+        }
+        t.A = (const void* const*)I.q_va_hi; t.A2 = (const void* const*)I.q_va_lo;
+        t.B = (const void* const*)I.q_d_hi; t.B2 = (const void* const*)I.q_d_lo;
+        t.C = I.q_xa32; t.skew = 1;
+        if ((e = gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        counted();
+        c->stage(SGS_STAGE_EOM_ASSEMBLY);
+        if (I.nimp > 0) {
+            pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.fimp, I.lr);
+            counted();
+        }
+        pair_q_kernel<float><<<dim3(gch, P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va32, I.xa32, I.wr32, I.xa, I.wr);
+        counted();
+    } else if (P > 0) {
         // T1 = S^{-1} (A + Re Fimp)  (into work), Wr = T1 S^{-1}
         pair_sparse_right_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.si, I.fimp, I.work);
         counted();
         GemmBatch g = gb_basic(n, n, n, I.p_work, n, I.p_si, n, I.p_wr, n, P);
         g.mode = GEMM_SKEW;
-        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        if ((e = gemm(c, g, st, n3 * P)) != cudaSuccess) return e;
         // V = D Wr
         c->stage(SGS_STAGE_EOM_V);
         c->stage_flops[SGS_STAGE_EOM_V] += 2.0 * n3 * P;
         c->stage_bytes[SGS_STAGE_EOM_V] += 8.0 * nn * (2.0 * P + M);   // read Wr, write V; Gamma once
         g = gb_basic(n, n, n, I.p_ga, n, I.p_wr, n, I.p_va, n, P);
         g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
-        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        if ((e = gemm(c, g, st, 2.0 * n3 * P)) != cudaSuccess) return e;
         // X = V D
         c->stage(SGS_STAGE_EOM_X);
         c->stage_flops[SGS_STAGE_EOM_X] += n3 * P;
         g = gb_basic(n, n, n, I.p_va, n, I.p_ga, n, I.p_xa, n, P);
         g.B2 = (const double* const*)I.p_gb; g.sB2 = -1.0;
         g.mode = GEMM_SKEW;
-        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        if ((e = gemm(c, g, st, n3 * P)) != cudaSuccess) return e;
         c->stage(SGS_STAGE_EOM_ASSEMBLY);
         if (I.nimp > 0) {
             pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.fimp, I.lr);
             counted();
         }
-        pair_q_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va, I.xa, I.wr);
+        pair_q_kernel<double><<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va, I.xa,
+                                                                                   I.wr, I.xa, I.wr);
         counted();
     } else {
         c->stage(SGS_STAGE_EOM_ASSEMBLY);
@@ -553,7 +685,7 @@ cudaError_t update_pass(sgs_ctx* c, Instance& I) {
     c->stage_flops[SGS_STAGE_UPDATE] += (2.0 + 18.0 + 2.0 + 1.0 + 6.0) * n3 * M;
     // Y = Gamma dGamma -> s0 ; X -> s1 ; P -> s2
     GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_dgamma, n, I.p_s[0], n, M);
-    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    if ((e = gemm(c, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
     exp_prepare_kernel<<<M, 1024, 0, st>>>(I.s[0], I.s[1], I.s[2], n, I.dtau, I.sq, I.scale, I.err);
     counted();
     // Horner: P <- I + (X 2^-s / j) P, j = degree-1 .. 1
@@ -562,7 +694,7 @@ cudaError_t update_pass(sgs_ctx* c, Instance& I) {
         int nxt = (cur == 2) ? 3 : 2;
         g = gb_basic(n, n, n, I.p_s[1], n, I.p_s[cur], n, I.p_s[nxt], n, M);
         g.alpha = 1.0 / j; g.alpha_b = I.scale; g.diag = 1.0;
-        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        if ((e = gemm(c, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
         cur = nxt;
     }
     // squarings (states with fewer squarings pass their matrix through)
@@ -571,24 +703,24 @@ cudaError_t update_pass(sgs_ctx* c, Instance& I) {
         g = gb_basic(n, n, n, I.p_s[cur], n, I.p_s[cur], n, I.p_s[nxt], n, M);
         g.active_flag = I.sq; g.active_cmp = j;
         g.Cin = (const double* const*)I.p_s[cur]; g.ldcin = n; g.beta = 0.0;
-        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        if ((e = gemm(c, g, st, -1.0)) != cudaSuccess) return e;
         cur = nxt;
     }
     // T = R Gamma -> s0 ; Gamma' = T R^T -> s4
     g = gb_basic(n, n, n, I.p_s[cur], n, I.p_gamma, n, I.p_s[0], n, M);
-    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    if ((e = gemm(c, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
     g = gb_basic(n, n, n, I.p_s[0], n, I.p_s[cur], n, I.p_s[4], n, M);
     g.transB = 1; g.mode = GEMM_SKEW;
-    if ((e = gemm(g, st)) != cudaSuccess) return e;
+    if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
     // Newton-Schulz polar factor: X <- 1.5 X + 0.5 X (X X), twice
     double** src = I.p_s[4];
     double** dst = I.p_gamma;
     for (int it = 0; it < 2; it++) {
         g = gb_basic(n, n, n, src, n, src, n, I.p_s[0], n, M);
-        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
         g = gb_basic(n, n, n, src, n, I.p_s[0], n, dst, n, M);
         g.alpha = 0.5; g.Cin = (const double* const*)src; g.ldcin = n; g.beta = 1.5; g.mode = GEMM_SKEW;
-        if ((e = gemm(g, st)) != cudaSuccess) return e;
+        if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
         std::swap(src, dst);
     }
     // after two iterations the result is back in s4
@@ -610,6 +742,11 @@ sgs_status check_device_error(sgs_ctx* c) {
                 snprintf(buf, sizeof buf, "instance %zu: two ansatz states have a singular Gamma_a + Gamma_b", i);
                 c->err = buf;
                 return SGS_ESINGULAR;
+            }
+            if (e & SGS_DEV_TC_TIMEOUT) {
+                snprintf(buf, sizeof buf, "instance %zu: a bounded tensor-core pipeline wait ran out", i);
+                c->err = buf;
+                return SGS_ETIMEOUT;
             }
             if (e & SGS_DEV_PF_ZERO) {
                 snprintf(buf, sizeof buf, "instance %zu: a state is orthogonal to the reference state", i);
@@ -793,11 +930,14 @@ sgs_status sgs_set_profiling(sgs_ctx* c, int enable) {
     c->prof = enable != 0;
     for (int j = 0; j < SGS_N_STAGES; j++) c->stage_ms[j] = c->stage_flops[j] = c->stage_bytes[j] = 0.0;
     c->launches = 0;
+    c->gemm_ms = c->gemm_flops = 0.0;
+    c->gemm_count = 0;
     for (auto& I : c->inst) I.steps_since_profile = 0;
     return SGS_OK;
 }
 
-sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double* bytes, long long* launches) {
+sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double* bytes, long long* launches,
+                           double* gemm_f64) {
     sgs_ctx* c = const_cast<sgs_ctx*>(cc);
     if (!c) return SGS_EINVAL;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -817,6 +957,11 @@ sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double*
         if (bytes) bytes[j] = c->stage_bytes[j];
     }
     if (launches) *launches = c->launches;
+    if (gemm_f64) {
+        gemm_f64[0] = c->gemm_ms;
+        gemm_f64[1] = c->gemm_flops;
+        gemm_f64[2] = (double)c->gemm_count;
+    }
     return SGS_OK;
 }
 
@@ -921,9 +1066,85 @@ sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, 
         cudaMemcpyAsync(dA, A, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemcpyAsync(dB, B, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         GemmBatch g = gb_basic(n, n, n, PA, n, PB, n, PC, n, batch);
-        if (gemm(g, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        if (gemm(nullptr, g, tmp.stream, -1.0) != cudaSuccess) st = SGS_ECUDA;
         cudaMemcpyAsync(C, dC, batch * nn * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
         if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+    }
+    cudaStreamSynchronize(tmp.stream);
+    tmp.release_all();
+    cudaStreamDestroy(tmp.stream);
+    tmp.stream = nullptr;
+    return st;
+}
+
+sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, int k, int batch, int kind,
+                              double* C) {
+    if (!A || !Bt || !C || m < 1 || n < 1 || k < 1 || batch < 1 || kind < 0 || kind > 2 || (k & 7)) return SGS_EINVAL;
+    sgs_ctx tmp;
+    cudaStreamCreateWithFlags(&tmp.stream, cudaStreamNonBlocking);
+    const size_t na = (size_t)m * k, nb = (size_t)n * k, nc = (size_t)m * n;
+    const size_t esz = (kind == TC_BF16) ? 2 : 4;
+    const int parts = (kind == TC_3XTF32) ? 2 : 1;
+    void* dA = tmp.dalloc(parts * batch * na * esz);
+    void* dB = tmp.dalloc(parts * batch * nb * esz);
+    double* dC = tmp.alloc<double>(batch * nc);
+    int* err = tmp.alloc<int>(1);
+    sgs_status st = SGS_OK;
+    if (!dA || !dB || !dC || !err) st = SGS_ENOMEM;
+    if (st == SGS_OK) {
+        // operand conversion on the host (building block only): fp32 / bf16, hi + lo for 3xTF32
+        std::vector<uint8_t> ha(parts * batch * na * esz), hb(parts * batch * nb * esz);
+        auto conv = [&](const double* src, size_t cnt, uint8_t* hi, uint8_t* lo) {
+            for (size_t e = 0; e < cnt; e++) {
+                if (kind == TC_BF16) {
+                    __nv_bfloat16 v = __float2bfloat16_rn((float)src[e]);
+                    std::memcpy(hi + 2 * e, &v, 2);
+                } else {
+                    float h = (float)src[e];
+                    if (kind == TC_3XTF32) {
+                        // hi keeps the top 10 mantissa bits (tf32), lo the remainder
+                        uint32_t u;
+                        std::memcpy(&u, &h, 4);
+                        u &= 0xffffe000u;
+                        float th;
+                        std::memcpy(&th, &u, 4);
+                        float tl = (float)(src[e] - (double)th);
+                        std::memcpy(hi + 4 * e, &th, 4);
+                        std::memcpy(lo + 4 * e, &tl, 4);
+                    } else {
+                        std::memcpy(hi + 4 * e, &h, 4);
+                    }
+                }
+            }
+        };
+        conv(A, batch * na, ha.data(), ha.data() + batch * na * esz);
+        conv(Bt, batch * nb, hb.data(), hb.data() + batch * nb * esz);
+        cudaMemcpyAsync(dA, ha.data(), ha.size(), cudaMemcpyHostToDevice, tmp.stream);
+        cudaMemcpyAsync(dB, hb.data(), hb.size(), cudaMemcpyHostToDevice, tmp.stream);
+        cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
+        std::vector<const void*> pa, pb, pa2, pb2;
+        std::vector<void*> pc;
+        for (int b = 0; b < batch; b++) {
+            pa.push_back((const uint8_t*)dA + b * na * esz);
+            pb.push_back((const uint8_t*)dB + b * nb * esz);
+            pa2.push_back((const uint8_t*)dA + (batch + b) * na * esz);
+            pb2.push_back((const uint8_t*)dB + (batch + b) * nb * esz);
+            pc.push_back(dC + b * nc);
+        }
+        TcBatch g{};
+        g.m = m; g.n = n; g.k = k;
+        g.A = upload_ptrs(&tmp, pa); g.lda = k;
+        g.B = upload_ptrs(&tmp, pb); g.ldb = k;
+        g.A2 = upload_ptrs(&tmp, pa2); g.B2 = upload_ptrs(&tmp, pb2);
+        g.C = upload_ptrs(&tmp, pc); g.ldc = n;
+        g.alpha = 1.0; g.out_f64 = 1; g.skew = 0; g.err = err; g.batch = batch;
+        if (gemm_tc(g, kind, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        counted();
+        int herr = 0;
+        cudaMemcpyAsync(C, dC, batch * nc * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
+        cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, tmp.stream);
+        if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        else if (herr) st = SGS_ETIMEOUT;
     }
     cudaStreamSynchronize(tmp.stream);
     tmp.release_all();
@@ -949,7 +1170,7 @@ sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, do
         double **PW = upload_ptrs(&tmp, pw), **PT = upload_ptrs(&tmp, pt), **PO = upload_ptrs(&tmp, po);
         cudaMemcpyAsync(W, S, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
-        if (launch_gj(n, batch, bsz, PW, PT, piv, ld, ds, err, 0.0, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        if (launch_gj(nullptr, n, batch, bsz, PW, PT, piv, ld, ds, err, 0.0, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
         gj_perm_kernel<<<(batch + 127) / 128, 128, 0, tmp.stream>>>(piv, perm, n, batch);
         gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), batch), 256, 0, tmp.stream>>>(PW, PO, perm, n);
         cudaMemcpyAsync(inv, O, batch * nn * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
@@ -998,7 +1219,8 @@ sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase,
         double **UA = upload_ptrs(&tmp, ua), **UB = upload_ptrs(&tmp, ub), **UC = upload_ptrs(&tmp, uc);
         cudaMemcpyAsync(W, planes.data(), planes.size() * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
-        if (launch_pf(n, batch, bs, PY, PTU, PPK, UA, UB, UC, la, ph, err, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        if (launch_pf(nullptr, n, batch, bs, PY, PTU, PPK, UA, UB, UC, la, ph, err, tmp.stream) != cudaSuccess)
+            st = SGS_ECUDA;
         cudaMemcpyAsync(phase, ph, 2 * batch * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
         cudaMemcpyAsync(logabs, la, batch * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
         if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
@@ -1098,7 +1320,7 @@ extern "C" sgs_status sgs_kernel_inverse_static(const double* S, double* inv, do
         return SGS_ECUDA;
     static_fill_ptrs_kernel<<<(batch + 127) / 128, 128, 0, st>>>(inv, base, n, batch);
     counted();
-    if (launch_gj(n, batch, SGS_STATIC_PANEL, W, T, piv, logabsdet, dsign, err, 0.0, st) != cudaSuccess)
+    if (launch_gj(nullptr, n, batch, SGS_STATIC_PANEL, W, T, piv, logabsdet, dsign, err, 0.0, st) != cudaSuccess)
         return SGS_ECUDA;
     static_unpermute_kernel<<<batch, 256, 0, st>>>(inv, piv, n);
     counted();
