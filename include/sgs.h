@@ -110,12 +110,20 @@ sgs_status sgs_step(sgs_ctx* ctx, int n_steps, double* energies);
 sgs_status sgs_energy(sgs_ctx* ctx, double* energies);
 
 typedef enum {
-    SGS_CORR_SPIN_SPIN = 0,      /* C(r) = <S(0).S(r)> (Eq. Cr); sites[i] = r */
-    SGS_CORR_TWO_CHANNEL_K = 1,  /* K(r) = sum_alpha <S_imp.S_alpha(r)> (Eq. K2CK); sites[i] = r */
+    SGS_CORR_SPIN_SPIN = 0,      /* C(s) = <S(0).S(s)> (Eq. Cr); sites[i] = s, a site index */
+    SGS_CORR_TWO_CHANNEL_K = 1,  /* K(r) = sum_alpha <S_imp.S_alpha(r)> (Eq. K2CK); sites[i] = r >= 1 */
     SGS_CORR_RENYI2 = 2          /* S_2 of the impurity plus the first l sites (App. B); sites[i] = l */
 } sgs_corr_kind;
 
-/* Observables of the current SGS state of one instance.  out: [n_sites]. */
+/* Observables of the current SGS state of one instance, evaluated on its
+ * current covariance matrices with optimal amplitudes (a pair pass runs
+ * first; the states are not changed).  out: [n_sites].  Sites are spinful
+ * sites in the library's mode order: site s holds modes 2s, 2s+1 (Majoranas
+ * 4s..4s+3), the impurity is site 0.  For a single chain site s is at
+ * distance s from the impurity; for two channels interleaved (as
+ * sgs_build_anderson lays them out) channel alpha's r-th site is
+ * 1 + 2(r - 1) + alpha.  Renyi-2: A = sites 0..l (the leading 4(1 + l)
+ * Majoranas), l <= 12.  Errors: SGS_EINVAL for sites out of range. */
 sgs_status sgs_correlator(sgs_ctx* ctx, int instance, sgs_corr_kind kind, const int* sites, int n_sites,
                           double* out);
 

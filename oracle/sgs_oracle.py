@@ -410,3 +410,179 @@ def run(model, gammas, ds, n_steps, mode=C_INVERSE):
         E, lam, gammas = sgs_step(model, gammas, ds, mode)
         Es.append(E)
     return np.array(Es), lam, gammas
+
+
+# ---------------------------------------------------------------------------
+# Observables: spin-spin correlators (Eq. Cr, Eq. K2CK)
+# ---------------------------------------------------------------------------
+#
+# Operators are Majorana polynomials {(i1 < i2 < ...): coefficient}.  The
+# expectation of a monomial c_I (distinct, increasing indices) in the
+# transition "state" with matrix Delta is the Pfaffian of the sub-block of
+# i Delta on I (Sec. III B: n-point elements are Pfaffians of n x n
+# sub-matrices), 1 for the empty monomial.
+
+
+def _mono_mul(a, b):
+    """Product of two normal-ordered Majorana monomials: (sign, monomial)."""
+    seq = list(a) + list(b)
+    sign = 1
+    # bubble sort with anticommutation signs, then cancel c_p c_p = 1
+    for i in range(len(seq)):
+        for j in range(len(seq) - 1 - i):
+            if seq[j] > seq[j + 1]:
+                seq[j], seq[j + 1] = seq[j + 1], seq[j]
+                sign = -sign
+    out = []
+    for x in seq:
+        if out and out[-1] == x:
+            out.pop()
+        else:
+            out.append(x)
+    return sign, tuple(out)
+
+
+def poly_mul(P, Q):
+    R = {}
+    for a, ca in P.items():
+        for b, cb in Q.items():
+            s, m = _mono_mul(a, b)
+            R[m] = R.get(m, 0.0) + s * ca * cb
+    return {m: c for m, c in R.items() if c != 0}
+
+
+def poly_add(P, Q, q=1.0):
+    R = dict(P)
+    for m, c in Q.items():
+        R[m] = R.get(m, 0.0) + q * c
+    return {m: c for m, c in R.items() if c != 0}
+
+
+def _annihilator(mode):
+    """a_m = (c_{2m} + i c_{2m+1}) / 2 as a polynomial."""
+    return {(2 * mode,): 0.5, (2 * mode + 1,): 0.5j}
+
+
+def _creator(mode):
+    return {(2 * mode,): 0.5, (2 * mode + 1,): -0.5j}
+
+
+def spin_operators(site):
+    """S^x, S^y, S^z of a spinful site (modes 2 site + sigma) from
+    S = 1/2 sum_ss' d^dag_s sigma_ss' d_s' (Eq. Cr), as Majorana polynomials."""
+    up, dn = 2 * site, 2 * site + 1
+    updn = poly_mul(_creator(up), _annihilator(dn))
+    dnup = poly_mul(_creator(dn), _annihilator(up))
+    nu = poly_mul(_creator(up), _annihilator(up))
+    nd = poly_mul(_creator(dn), _annihilator(dn))
+    Sx = {m: 0.5 * c for m, c in poly_add(updn, dnup).items()}
+    Sy = {m: -0.5j * c for m, c in poly_add(updn, dnup, -1.0).items()}
+    Sz = {m: 0.5 * c for m, c in poly_add(nu, nd, -1.0).items()}
+    return Sx, Sy, Sz
+
+
+def spin_dot(site_a, site_b):
+    A, B = spin_operators(site_a), spin_operators(site_b)
+    out = {}
+    for x, y in zip(A, B):
+        out = poly_add(out, poly_mul(x, y))
+    return out
+
+
+def poly_expectation(P, Dlt):
+    """<O>_t = sum_I coeff_I Pf((i Delta)[I, I])."""
+    tot = 0.0 + 0.0j
+    for m, c in P.items():
+        if len(m) == 0:
+            tot += c
+        elif len(m) % 2 == 0:
+            idx = list(m)
+            tot += c * pfaffian(1j * Dlt[np.ix_(idx, idx)])
+    return tot
+
+
+def sgs_expectation(P, gammas, lam, G):
+    """<psi|O|psi> = sum_ab conj(lambda_a) lambda_b <phi_a|O|phi_b>, with
+    <phi_a|O|phi_b> = G_ab <O>_t evaluated on Delta^{b,a} (Sec. III B)."""
+    M = len(gammas)
+    tot = 0.0 + 0.0j
+    for a in range(M):
+        for b in range(M):
+            D = gammas[a].astype(np.complex128) if a == b else transition_matrix(gammas[b], gammas[a])
+            tot += np.conj(lam[a]) * lam[b] * G[a, b] * poly_expectation(P, D)
+    return tot
+
+
+def spin_correlator(gammas, lam, G, sites):
+    """C(r) = <S(0) . S(r)> for the impurity site 0 and each site in ``sites``."""
+    return np.array([np.real(sgs_expectation(spin_dot(0, s), gammas, lam, G)) for s in sites])
+
+
+def two_channel_correlator(gammas, lam, G, distances, n_channels=2):
+    """K(r) = sum_alpha <S_imp . S_alpha(r)> (Eq. K2CK) with the interleaved
+    site order of anderson_chain: channel alpha, chain site r -> 1 + (r-1) n_ch + alpha."""
+    out = []
+    for r in distances:
+        tot = 0.0
+        for al in range(n_channels):
+            tot += np.real(sgs_expectation(spin_dot(0, 1 + (r - 1) * n_channels + al), gammas, lam, G))
+        out.append(tot)
+    return np.array(out)
+
+
+# ---------------------------------------------------------------------------
+# Renyi-2 entropy of the leading modes (App. B, Eqs. S2_SGS, T_tensor,
+# TrArho2_final)
+# ---------------------------------------------------------------------------
+
+
+def _m_block(Ga, Gb, sl):
+    """M_J^{a,b} = [[Gamma_J^a, i 1], [-i 1, Gamma_J^b]] (Eq. MB)."""
+    m = sl.stop - sl.start
+    I = np.eye(m)
+    return np.block([[Ga[sl, sl], 1j * I], [-1j * I, Gb[sl, sl]]])
+
+
+def renyi2_trace_term(Ga, Gb, Gc, Gd, n_modes_A):
+    """I^{a,b}_{c,d} = Tr_A(Tr_B(rho_a rho_b) Tr_B(rho_c rho_d)) by Eq. TrArho2_final:
+    2^{N_B}/8^N Pf[M_B^{ab}] Pf[M_B^{cd}] Pf[M_A^{cd} + Sigma_A^{cd}]
+    Pf[M_A^{ab} + Sigma_A^{ab} + sigma_A^{dc}], with Sigma_A (Eq. MB) and
+    sigma_A^{dc} = -X (M_A^{cd} + Sigma_A^{cd})^{-1} X, X = [[-1, 1], [1, -1]]."""
+    n = Ga.shape[0]
+    N = n // 2
+    NA = n_modes_A
+    NB = N - NA
+    A = slice(0, 2 * NA)
+    B = slice(2 * NA, n)
+
+    def sigma_A(G1, G2):
+        if NB == 0:
+            return np.zeros((4 * NA, 4 * NA), dtype=np.complex128)
+        Z = np.zeros((2 * NA, 2 * NB))
+        GAB = np.block([[G1[A, B], Z], [Z, G2[A, B]]])
+        MB = _m_block(G1, G2, B)
+        return GAB @ np.linalg.solve(MB, GAB.T)
+
+    pfB_ab = pfaffian(_m_block(Ga, Gb, B)) if NB > 0 else 1.0
+    pfB_cd = pfaffian(_m_block(Gc, Gd, B)) if NB > 0 else 1.0
+    MA_ab = _m_block(Ga, Gb, A) + sigma_A(Ga, Gb)
+    MA_cd = _m_block(Gc, Gd, A) + sigma_A(Gc, Gd)
+    I2 = np.eye(2 * NA)
+    X = np.block([[-I2, I2], [I2, -I2]])
+    sig = -X @ np.linalg.solve(MA_cd, X)
+    return 2.0 ** NB / 8.0 ** N * pfB_ab * pfB_cd * pfaffian(MA_cd) * pfaffian(MA_ab + sig)
+
+
+def renyi2(gammas, lam, G, n_modes_A):
+    """S_2(A) = -ln sum_abcd T^{ab}_{cd} (Eq. S2_SGS) with
+    T^{ab}_{cd} = lambda_a conj(lambda_b) lambda_c conj(lambda_d) I^{ab}_{cd} / (G_ab G_cd)
+    (Eq. T_tensor); A = the first n_modes_A fermion modes."""
+    M = len(gammas)
+    tot = 0.0 + 0.0j
+    for a in range(M):
+        for b in range(M):
+            for c in range(M):
+                for d in range(M):
+                    I = renyi2_trace_term(gammas[a], gammas[b], gammas[c], gammas[d], n_modes_A)
+                    tot += lam[a] * np.conj(lam[b]) * lam[c] * np.conj(lam[d]) * I / (G[a, b] * G[c, d])
+    return float(-math.log(tot.real))

@@ -14,6 +14,7 @@
 #include "../../include/sgs.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -30,6 +31,8 @@
 #include "update.cuh"
 #include "probe.cuh"
 #include "gemm_tc.cuh"
+#include "corr.cuh"
+#include "renyi.cuh"
 
 using namespace sgs;
 
@@ -72,6 +75,8 @@ struct Instance {
     double* Ehist = nullptr;
     int Ecap = 0;
     int steps_since_profile = 0;
+    double* corr_scratch = nullptr;     // observables: partial sums, sites, outputs
+    size_t corr_cap = 0;
     double* eigscratch = nullptr;
     int* err = nullptr;
 
@@ -865,8 +870,90 @@ sgs_status sgs_energy(sgs_ctx* c, double* energies) {
 
 sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const int* sites, int n_sites, double* out) {
     if (!c || instance < 0 || instance >= (int)c->inst.size() || !sites || !out || n_sites < 0) return SGS_EINVAL;
-    (void)kind;
-    c->err = "correlator kind not available";
+    if (n_sites == 0) return SGS_OK;
+    Instance& I = c->inst[instance];
+    const int nsite_tot = I.n / 4;          // spinful sites: modes 2s, 2s+1 -> Majoranas 4s..4s+3
+    if (kind == SGS_CORR_SPIN_SPIN || kind == SGS_CORR_TWO_CHANNEL_K) {
+        const int nch = (kind == SGS_CORR_TWO_CHANNEL_K) ? 2 : 1;
+        for (int i = 0; i < n_sites; i++) {
+            const int s = sites[i];
+            const bool ok = (kind == SGS_CORR_SPIN_SPIN) ? (s >= 0 && s < nsite_tot)
+                                                         : (s >= 1 && 1 + (s - 1) * nch + nch - 1 < nsite_tot);
+            if (!ok) { c->err = "correlator site out of range"; return SGS_EINVAL; }
+        }
+        // current states: pair pass and amplitudes (the states are not changed)
+        CUDA_TRY(c, pair_pass(c, I, 0));
+        c->stage(-1);
+        const size_t rows = (size_t)I.P + I.M;
+        const size_t need = rows * n_sites + 2 * (size_t)n_sites + 8;
+        if (I.corr_cap < need) {
+            I.corr_scratch = c->alloc<double>(need);
+            if (!I.corr_scratch) { c->err = "device allocation failed"; return SGS_ENOMEM; }
+            I.corr_cap = need;
+        }
+        double* partial = I.corr_scratch;
+        double* dout = partial + rows * n_sites;
+        int* dsites = reinterpret_cast<int*>(dout + n_sites);
+        CUDA_TRY(c, cudaMemcpyAsync(dsites, sites, n_sites * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        spin_corr_kernel<<<(unsigned)rows, 128, 0, c->stream>>>(I.dev(), I.si, I.imd, I.Gm, I.lam, dsites, n_sites,
+                                                               kind == SGS_CORR_SPIN_SPIN ? 0 : 1, nch, partial);
+        column_sum_kernel<<<(n_sites + 127) / 128, 128, 0, c->stream>>>(partial, (int)rows, n_sites, dout);
+        counted(); counted();
+        sgs_status st = check_device_error(c);
+        c->collect();
+        if (st != SGS_OK) return st;
+        CUDA_TRY(c, cudaMemcpy(out, dout, n_sites * sizeof(double), cudaMemcpyDeviceToHost));
+        return SGS_OK;
+    }
+    if (kind == SGS_CORR_RENYI2) {
+        for (int i = 0; i < n_sites; i++) {
+            const int na2 = 4 * (1 + sites[i]);
+            if (sites[i] < 0 || na2 > I.n || 2 * na2 > RENYI_MAX_DIM) {
+                c->err = "Renyi-2 subsystem out of range (impurity + l sites, 4(1+l) <= 2N, l <= 12)";
+                return SGS_EINVAL;
+            }
+        }
+        CUDA_TRY(c, pair_pass(c, I, 0));
+        c->stage(-1);
+        const long long M2 = (long long)I.M * I.M;
+        const long long npairs = M2 * (M2 + 1) / 2;
+        const int nred = 1024;
+        int maxna2 = 0;
+        for (int i = 0; i < n_sites; i++) maxna2 = std::max(maxna2, 4 * (1 + sites[i]));
+        const size_t need = (size_t)M2 * maxna2 * maxna2 * 2 + 2 * M2 + 2 * (size_t)npairs + 2 * nred + 8;
+        if (I.corr_cap < need) {
+            I.corr_scratch = c->alloc<double>(need);
+            if (!I.corr_scratch) { c->err = "device allocation failed"; return SGS_ENOMEM; }
+            I.corr_cap = need;
+        }
+        double* blocks = I.corr_scratch;
+        double* wts = blocks + (size_t)M2 * maxna2 * maxna2 * 2;
+        double* partial = wts + 2 * M2;
+        double* sums = partial + 2 * (size_t)npairs;
+        for (int i = 0; i < n_sites; i++) {
+            const int na2 = 4 * (1 + sites[i]);
+            const int m = 2 * na2;
+            renyi_blocks_kernel<<<(unsigned)M2, 128, 0, c->stream>>>(I.dev(), I.si, I.imd, I.Gm, I.lam, I.pair_index,
+                                                                     na2, blocks, wts);
+            const size_t smem = 2 * (size_t)m * (m + 1) * sizeof(double);
+            CUDA_TRY(c, cudaFuncSetAttribute(renyi_pf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const unsigned gx = (unsigned)std::min<long long>(npairs, 65535);
+            const unsigned gy = (unsigned)((npairs + gx - 1) / gx);
+            renyi_pf_kernel<<<dim3(gx, gy), 256, smem, c->stream>>>(blocks, wts, npairs, na2,
+                                                                     -(na2 / 2) * 0.6931471805599453, partial);
+            complex_sum_kernel<<<nred, 256, 0, c->stream>>>(partial, npairs, sums);
+            complex_sum_kernel<<<1, 256, 0, c->stream>>>(sums, nred, sums + 2 * nred);
+            counted(); counted(); counted(); counted();
+            double tr[2];
+            CUDA_TRY(c, cudaMemcpyAsync(tr, sums + 2 * nred, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            out[i] = -std::log(tr[0]);
+        }
+        sgs_status st = check_device_error(c);
+        c->collect();
+        return st;
+    }
+    c->err = "unknown correlator kind";
     return SGS_EINVAL;
 }
 

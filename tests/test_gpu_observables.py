@@ -1,0 +1,81 @@
+"""Observables of the SGS state on the GPU against the FP64 oracle:
+spin-spin C(s) (Eq. Cr), two-channel K(r) (Eq. K2CK) and the Renyi-2
+entropy of the impurity plus its first sites (App. B).  Bar: 1e-10 of the
+largest value (FP64 throughout)."""
+import numpy as np
+import pytest
+
+import sgs_inputs as inp
+from oracle import sgs_oracle as orc
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2105_01088_gb300 as p
+    return p
+
+
+def _setup(pkg, n_bath, U, eps, V, M, seed, clustered, parity=1, n_channels=1):
+    p = inp.AndersonParams(n_bath=n_bath, U=U, eps_d=eps, V=V, n_channels=n_channels)
+    rng = np.random.default_rng(seed)
+    if clustered:
+        g = inp.clustered_pure_gammas(p.n_modes, M, rng, parity, spread=1.0)
+    else:
+        g = np.stack([inp.random_pure_gamma(p.n_modes, rng, parity) for _ in range(M)])
+    m = pkg.build_anderson(n_bath, U, eps, V, 1.0, 0.0, n_channels)
+    s = pkg.Solver(m, g, None, parity=parity)
+    model = orc.anderson_model(n_bath, U, eps, V, n_channels=n_channels)
+    E, lam, G, h = orc.energy(model, list(g))
+    return s, g, lam, G
+
+
+@pytest.mark.parametrize("clustered", [False, True])
+def test_spin_correlator(pkg, clustered):
+    s, g, lam, G = _setup(pkg, 15, 2.0, -1.0, 0.5, 4, 7, clustered)
+    sites = list(range(0, 9))
+    got = s.correlator(pkg.SGS_CORR_SPIN_SPIN, sites)
+    ref = orc.spin_correlator(list(g), lam, G, sites)
+    assert np.abs(got - ref).max() <= TOL * np.abs(ref).max()
+
+
+def test_two_channel_correlator(pkg):
+    s, g, lam, G = _setup(pkg, 6, 8.0, -4.0, 0.6, 4, 9, True, parity=-1, n_channels=2)
+    rs = [1, 2, 3, 4, 5]
+    got = s.correlator(pkg.SGS_CORR_TWO_CHANNEL_K, rs)
+    ref = orc.two_channel_correlator(list(g), lam, G, rs)
+    assert np.abs(got - ref).max() <= TOL * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("clustered", [False, True])
+def test_renyi2(pkg, clustered):
+    s, g, lam, G = _setup(pkg, 7, 3.0, -1.5, 0.6, 3, 11, clustered)
+    ls = [0, 1, 2, 3]
+    got = s.correlator(pkg.SGS_CORR_RENYI2, ls)
+    ref = np.array([orc.renyi2(list(g), lam, G, 2 * (1 + l)) for l in ls])
+    assert np.abs(got - ref).max() <= TOL * max(1.0, np.abs(ref).max())
+
+
+def test_renyi2_single_gaussian_full_size(pkg):
+    """M = 1 at 2N = 512: S_2 = -sum_j ln[(1 + nu_j^2)/2] over the eigenvalues
+    +-i nu_j of Gamma_A (closed form for one Gaussian state)."""
+    p = inp.AndersonParams(n_bath=127, U=4.0, eps_d=-2.0, V=0.5)
+    g, _ = inp.initial_state(p.n_modes, 1, 5, 1)
+    m = pkg.build_anderson(127, 4.0, -2.0, 0.5)
+    s = pkg.Solver(m, g)
+    ls = [0, 4, 12]
+    got = s.correlator(pkg.SGS_CORR_RENYI2, ls)
+    for l, v in zip(ls, got):
+        GA = g[0][:4 * (1 + l), :4 * (1 + l)]
+        nu = np.sort(np.abs(np.linalg.eigvalsh(1j * GA)))[::2]
+        assert abs(v + np.sum(np.log((1.0 + nu ** 2) / 2.0))) < 1e-10
+
+
+def test_observable_arguments_are_checked(pkg):
+    s, g, lam, G = _setup(pkg, 3, 2.0, -1.0, 0.5, 2, 3, False)
+    with pytest.raises(pkg.SGSError):
+        s.correlator(pkg.SGS_CORR_SPIN_SPIN, [4])        # 4 sites: 0..3
+    with pytest.raises(pkg.SGSError):
+        s.correlator(pkg.SGS_CORR_RENYI2, [4])

@@ -260,3 +260,77 @@ def test_noninteracting_closed_form():
     g = [inp.random_pure_gamma(model.N, rng, 1)]
     Es, _, gs = orc.run(model, g, 0.25, 400)
     assert abs(Es[-1] - exact) < 1e-9
+
+
+# ---------------------------------------------------------------- observables (Eq. Cr, Eq. K2CK)
+
+def test_spin_correlator_matches_fock():
+    model = orc.anderson_model(2, 2.0, -1.0, 0.5)          # 3 sites, N = 6 modes
+    gammas, vecs = _states(6, 3, 101)
+    E, lam, G, h = orc.energy(model, gammas)
+    psi = sum(l * v for l, v in zip(lam, vecs))
+    for s in range(3):
+        ref = fock.spin_spin(psi, 6, 0, s)
+        got = orc.spin_correlator(gammas, lam, G, [s])[0]
+        assert abs(got - ref) < 1e-12, (s, got, ref)
+
+
+def test_two_channel_correlator_matches_fock():
+    model = orc.anderson_model(1, 2.0, -1.0, 0.5, n_channels=2)   # impurity + 2 channels x 1 site
+    gammas, vecs = _states(6, 2, 103, parity=-1)
+    E, lam, G, h = orc.energy(model, gammas)
+    psi = sum(l * v for l, v in zip(lam, vecs))
+    ref = fock.spin_spin(psi, 6, 0, 1) + fock.spin_spin(psi, 6, 0, 2)
+    assert abs(orc.two_channel_correlator(gammas, lam, G, [1])[0] - ref) < 1e-12
+
+
+def test_spin_sum_rule_for_exact_singlet():
+    """Sum_r C(r) = <S(0) . S_tot> = 0 for the even-L singlet ground state
+    (the sum rule Sigma(L-1) = 0 of Sec. IV B), checked on the operator
+    algebra: the exact ground state from ED, expectation of the oracle's
+    Majorana polynomials through explicit Fock matrices."""
+    H = fock.hamiltonian_anderson(1, 2.0, -1.0, 0.5)       # 2 sites, N = 4 modes: singlet ground state
+    w, v = np.linalg.eigh(H.toarray())
+    g = v[:, 0]
+    c = fock.majoranas(4)
+    tot = 0.0
+    for s in range(2):
+        P = orc.spin_dot(0, s)
+        op = sum(coef * (np.linalg.multi_dot([c[i].toarray() for i in m]) if len(m) > 1 else
+                         (c[m[0]].toarray() if len(m) == 1 else np.eye(16))) for m, coef in P.items())
+        val = np.vdot(g, op @ g)
+        assert abs(val - fock.spin_spin(g, 4, 0, s)) < 1e-12
+        tot += val
+    assert abs(tot) < 1e-12
+
+
+# ---------------------------------------------------------------- Renyi-2 (App. B)
+
+@pytest.mark.parametrize("n_sites_A", [1, 2])
+def test_renyi2_matches_fock_reduced_density_matrix(n_sites_A):
+    gammas, vecs = _states(6, 3, 111)                        # 3 sites
+    model = orc.anderson_model(2, 2.0, -1.0, 0.5)
+    E, lam, G, h = orc.energy(model, gammas)
+    psi = sum(l * v for l, v in zip(lam, vecs))
+    ref = fock.renyi2_leading_modes(psi, 2 * n_sites_A)
+    assert abs(orc.renyi2(gammas, lam, G, 2 * n_sites_A) - ref) < 1e-10
+
+
+def test_renyi2_single_gaussian_closed_form_and_pure_limits():
+    """R = 1: S_2 = -sum_j ln[(1 + nu_j^2)/2], +-i nu_j the eigenvalues of
+    Gamma_A (the single-Gaussian result the paper cites in Sec. IV C); the
+    whole system (N_B = 0) is pure: S_2 = 0."""
+    rng = _rng(121)
+    N = 8
+    g = inp.random_pure_gamma(N, rng)
+    for NA in (1, 3, 5):
+        GA = g[:2 * NA, :2 * NA]
+        ev = np.linalg.eigvalsh(1j * GA)                      # +-nu_j
+        nu = np.sort(np.abs(ev))[::2]
+        ref = -np.sum(np.log((1.0 + nu ** 2) / 2.0))
+        got = orc.renyi2([g], np.array([1.0 + 0j]), np.ones((1, 1)), NA)
+        assert abs(got - ref) < 1e-10
+    gammas, vecs = _states(4, 2, 123)
+    model = orc.anderson_model(1, 2.0, -1.0, 0.5)
+    E, lam, G, h = orc.energy(model, gammas)
+    assert abs(orc.renyi2(gammas, lam, G, 4)) < 1e-10
