@@ -32,8 +32,9 @@ struct GJPanelArgs {
 
 __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
     extern __shared__ double sm[];
-    double* panel = sm;                       // n x bb
-    double* rowc = panel + (size_t)a.n * a.bb; // bb
+    const int ps = a.bb + 1;                   // odd row stride: column walks hit distinct banks
+    double* panel = sm;                        // n x ps
+    double* rowc = panel + (size_t)a.n * ps;   // bb
     __shared__ double red_v[32];
     __shared__ int red_i[32];
     __shared__ double s_logdet, s_sign;
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
 
     for (int e = threadIdx.x; e < n * bb; e += blockDim.x) {
         int r = e / bb, q = e % bb;
-        panel[e] = W[(size_t)r * n + k0 + q];
+        panel[r * ps + q] = W[(size_t)r * n + k0 + q];
     }
     if (threadIdx.x == 0) {
         s_logdet = (k0 == 0) ? 0.0 : a.logdet[b];
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
         double best = -1.0;
         int bi = 0x7fffffff;
         for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
-            double v = fabs(panel[r * bb + j]);
+            double v = fabs(panel[r * ps + j]);
             if (v > best) { best = v; bi = r; }
         }
         double mv;
@@ -69,9 +70,9 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
         }
         if (p != c) {
             for (int q = threadIdx.x; q < bb; q += blockDim.x) {
-                double t = panel[c * bb + q];
-                panel[c * bb + q] = panel[p * bb + q];
-                panel[p * bb + q] = t;
+                double t = panel[c * ps + q];
+                panel[c * ps + q] = panel[p * ps + q];
+                panel[p * ps + q] = t;
             }
             for (int q = threadIdx.x; q < n; q += blockDim.x) {
                 if (q >= k0 && q < k0 + bb) continue;
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
         }
         if (threadIdx.x == 0) piv[c] = p;
         __syncthreads();
-        double pv = panel[c * bb + j];
+        double pv = panel[c * ps + j];
         if (!(mv > a.tiny)) pv = 1.0;
         if (threadIdx.x == 0) {
             if (mv > a.tiny) s_logdet += log(fabs(pv));
@@ -90,26 +91,26 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
         }
         const double inv = 1.0 / pv;
         for (int q = threadIdx.x; q < bb; q += blockDim.x) {
-            double v = (q == j) ? inv : panel[c * bb + q] * inv;
+            double v = (q == j) ? inv : panel[c * ps + q] * inv;
             rowc[q] = v;
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < bb; q += blockDim.x) panel[c * bb + q] = rowc[q];
+        for (int q = threadIdx.x; q < bb; q += blockDim.x) panel[c * ps + q] = rowc[q];
         for (int r = threadIdx.x; r < n; r += blockDim.x) {
             if (r == c) continue;
-            double f = panel[r * bb + j];
+            double f = panel[r * ps + j];
             if (f != 0.0) {
                 for (int q = 0; q < bb; q++)
-                    if (q != j) panel[r * bb + q] -= f * rowc[q];
+                    if (q != j) panel[r * ps + q] -= f * rowc[q];
             }
-            panel[r * bb + j] = -f * inv;
+            panel[r * ps + j] = -f * inv;
         }
         __syncthreads();
     }
 
     for (int e = threadIdx.x; e < n * bb; e += blockDim.x) {
         int r = e / bb, q = e % bb;
-        W[(size_t)r * n + k0 + q] = panel[e];
+        W[(size_t)r * n + k0 + q] = panel[r * ps + q];
     }
     __syncthreads();
     double* T = a.T[b];
@@ -149,9 +150,9 @@ __global__ void gj_gather_kernel(double* const* W, double* const* out, const int
 // ---------------------------------------------------------------- Pfaffian
 
 struct PfPanelArgs {
-    double* const* Y;        // [batch] planes: Re (n x n) then Im (n x n)
-    double* const* TU;       // [batch] 4 x n x bs scratch: Tr, Ti, Ur, Ui (column t = step)
-    double* const* PA;       // [batch] packs, 4 consecutive n x 4bs blocks:
+    double* const* Y;        // [batch] planes: Re (n x n) then Im (n x n), antisymmetric
+    double* const* TU;       // [batch] 4 x bs x n scratch: Tr, Ti, Ur, Ui (row t = step, contiguous in i)
+    double* const* PA;       // [batch] packs, 4 blocks n x 4*bsmax apart:
                              //   A_re=[Tr,-Ti,-Ur,Ui] B_re=[Ur,Ui,Tr,Ti] A_im=[Tr,Ti,-Ur,-Ui] B_im=[Ui,Ur,Ti,Tr]
     double* logabs;          // [batch]
     double* phase;           // [batch][2]
@@ -160,6 +161,8 @@ struct PfPanelArgs {
     int bsmax;               // pack blocks are n x 4*bsmax apart (row stride 4*bs)
 };
 
+// Columns of the antisymmetric Y are read as negated rows (coalesced); the
+// pending rank-2 updates of the panel are added on the fly.
 __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
     extern __shared__ double sm[];
     const int n = a.n, k0 = a.k0, bs = a.bs;
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
     const int b = blockIdx.x;
     double* Yr = a.Y[b];
     double* Yi = Yr + (size_t)n * n;
-    double* Tr = a.TU[b];
+    double* Tr = a.TU[b];                  // Tr[t * n + i]
     double* Ti = Tr + (size_t)n * bs;
     double* Ur = Ti + (size_t)n * bs;
     double* Ui = Ur + (size_t)n * bs;
@@ -188,31 +191,30 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
 
     for (int s = 0; s < bs; s++) {
         const int k = k0 + 2 * s;
-        // row k of the pending vectors
         for (int t = threadIdx.x; t < s; t += blockDim.x) {
-            rowTU[t] = Tr[(size_t)k * bs + t];
-            rowTU[bs + t] = Ti[(size_t)k * bs + t];
-            rowTU[2 * bs + t] = Ur[(size_t)k * bs + t];
-            rowTU[3 * bs + t] = Ui[(size_t)k * bs + t];
+            rowTU[t] = Tr[(size_t)t * n + k];
+            rowTU[bs + t] = Ti[(size_t)t * n + k];
+            rowTU[2 * bs + t] = Ur[(size_t)t * n + k];
+            rowTU[3 * bs + t] = Ui[(size_t)t * n + k];
         }
         __syncthreads();
-        // current column k: Y[i][k] + sum_t (T[i][t] U[k][t] - U[i][t] T[k][t])
+        // current column k: -Y[k][i] + sum_t (T[i][t] U[k][t] - U[i][t] T[k][t])
         double best = -1.0;
         int bi = 0x7fffffff;
         for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-            double vr = Yr[(size_t)i * n + k], vi = Yi[(size_t)i * n + k];
+            double vr = -Yr[(size_t)k * n + i], vi = -Yi[(size_t)k * n + i];
             for (int t = 0; t < s; t++) {
-                double tr = Tr[(size_t)i * bs + t], ti = Ti[(size_t)i * bs + t];
-                double ur = Ur[(size_t)i * bs + t], ui = Ui[(size_t)i * bs + t];
-                double Ukr = rowTU[2 * bs + t], Uki = rowTU[3 * bs + t];
-                double Tkr = rowTU[t], Tki = rowTU[bs + t];
+                const double tr = Tr[(size_t)t * n + i], ti = Ti[(size_t)t * n + i];
+                const double ur = Ur[(size_t)t * n + i], ui = Ui[(size_t)t * n + i];
+                const double Ukr = rowTU[2 * bs + t], Uki = rowTU[3 * bs + t];
+                const double Tkr = rowTU[t], Tki = rowTU[bs + t];
                 vr += tr * Ukr - ti * Uki - (ur * Tkr - ui * Tki);
                 vi += tr * Uki + ti * Ukr - (ur * Tki + ui * Tkr);
             }
             ckr[i] = vr;
             cki[i] = vi;
-            double m = vr * vr + vi * vi;
-            if (m > best) { best = m; bi = i; }
+            const double m2 = vr * vr + vi * vi;
+            if (m2 > best) { best = m2; bi = i; }
         }
         double mv;
         int p;
@@ -237,10 +239,10 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
             }
             for (int t = threadIdx.x; t < s; t += blockDim.x) {
                 double x;
-                x = Tr[(size_t)q * bs + t]; Tr[(size_t)q * bs + t] = Tr[(size_t)p * bs + t]; Tr[(size_t)p * bs + t] = x;
-                x = Ti[(size_t)q * bs + t]; Ti[(size_t)q * bs + t] = Ti[(size_t)p * bs + t]; Ti[(size_t)p * bs + t] = x;
-                x = Ur[(size_t)q * bs + t]; Ur[(size_t)q * bs + t] = Ur[(size_t)p * bs + t]; Ur[(size_t)p * bs + t] = x;
-                x = Ui[(size_t)q * bs + t]; Ui[(size_t)q * bs + t] = Ui[(size_t)p * bs + t]; Ui[(size_t)p * bs + t] = x;
+                x = Tr[(size_t)t * n + q]; Tr[(size_t)t * n + q] = Tr[(size_t)t * n + p]; Tr[(size_t)t * n + p] = x;
+                x = Ti[(size_t)t * n + q]; Ti[(size_t)t * n + q] = Ti[(size_t)t * n + p]; Ti[(size_t)t * n + p] = x;
+                x = Ur[(size_t)t * n + q]; Ur[(size_t)t * n + q] = Ur[(size_t)t * n + p]; Ur[(size_t)t * n + p] = x;
+                x = Ui[(size_t)t * n + q]; Ui[(size_t)t * n + q] = Ui[(size_t)t * n + p]; Ui[(size_t)t * n + p] = x;
             }
             if (threadIdx.x == 0) {
                 double x = ckr[q]; ckr[q] = ckr[p]; ckr[p] = x;
@@ -249,21 +251,21 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
             }
         }
         __syncthreads();
-        // row k+1 of the pending vectors, then current column k+1 (rows >= k+2)
         for (int t = threadIdx.x; t < s; t += blockDim.x) {
-            rowTU[t] = Tr[(size_t)(k + 1) * bs + t];
-            rowTU[bs + t] = Ti[(size_t)(k + 1) * bs + t];
-            rowTU[2 * bs + t] = Ur[(size_t)(k + 1) * bs + t];
-            rowTU[3 * bs + t] = Ui[(size_t)(k + 1) * bs + t];
+            rowTU[t] = Tr[(size_t)t * n + k + 1];
+            rowTU[bs + t] = Ti[(size_t)t * n + k + 1];
+            rowTU[2 * bs + t] = Ur[(size_t)t * n + k + 1];
+            rowTU[3 * bs + t] = Ui[(size_t)t * n + k + 1];
         }
         __syncthreads();
+        // current column k+1 (rows >= k+2): -Y[k+1][i] + pending
         for (int i = k + 2 + threadIdx.x; i < n; i += blockDim.x) {
-            double vr = Yr[(size_t)i * n + k + 1], vi = Yi[(size_t)i * n + k + 1];
+            double vr = -Yr[(size_t)(k + 1) * n + i], vi = -Yi[(size_t)(k + 1) * n + i];
             for (int t = 0; t < s; t++) {
-                double tr = Tr[(size_t)i * bs + t], ti = Ti[(size_t)i * bs + t];
-                double ur = Ur[(size_t)i * bs + t], ui = Ui[(size_t)i * bs + t];
-                double Ukr = rowTU[2 * bs + t], Uki = rowTU[3 * bs + t];
-                double Tkr = rowTU[t], Tki = rowTU[bs + t];
+                const double tr = Tr[(size_t)t * n + i], ti = Ti[(size_t)t * n + i];
+                const double ur = Ur[(size_t)t * n + i], ui = Ui[(size_t)t * n + i];
+                const double Ukr = rowTU[2 * bs + t], Uki = rowTU[3 * bs + t];
+                const double Tkr = rowTU[t], Tki = rowTU[bs + t];
                 vr += tr * Ukr - ti * Uki - (ur * Tkr - ui * Tki);
                 vi += tr * Uki + ti * Ukr - (ur * Tki + ui * Tkr);
             }
@@ -276,10 +278,10 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
         const double pm2 = pr * pr + pi * pi;
         if (threadIdx.x == 0) {
             if (mv > 0.0) {
-                double am = sqrt(pm2);
+                const double am = sqrt(pm2);
                 s_log += log(am);
-                double ur = pr / am, ui = pi / am;
-                double nr = s_pr * ur - s_pi * ui, ni = s_pr * ui + s_pi * ur;
+                const double ur = pr / am, ui = pi / am;
+                const double nr = s_pr * ur - s_pi * ui, ni = s_pr * ui + s_pi * ur;
                 s_pr = nr; s_pi = ni;
             }
         }
@@ -289,16 +291,16 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             double tr = 0.0, ti = 0.0, ur = 0.0, ui = 0.0;
             if (i >= k + 2) {
-                double xr = -ckr[i], xi = -cki[i];
+                const double xr = -ckr[i], xi = -cki[i];
                 tr = xr * ir - xi * ii;
                 ti = xr * ii + xi * ir;
                 ur = c1r[i];
                 ui = c1i[i];
             }
-            Tr[(size_t)i * bs + s] = tr;
-            Ti[(size_t)i * bs + s] = ti;
-            Ur[(size_t)i * bs + s] = ur;
-            Ui[(size_t)i * bs + s] = ui;
+            Tr[(size_t)s * n + i] = tr;
+            Ti[(size_t)s * n + i] = ti;
+            Ur[(size_t)s * n + i] = ur;
+            Ui[(size_t)s * n + i] = ui;
         }
         __syncthreads();
     }
@@ -312,10 +314,10 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
     double* PAim = PBre + blk;
     double* PBim = PAim + blk;
     for (int e = threadIdx.x; e < (n - e0) * bs; e += blockDim.x) {
-        int i = e0 + e / bs, t = e % bs;
-        double tr = Tr[(size_t)i * bs + t], ti = Ti[(size_t)i * bs + t];
-        double ur = Ur[(size_t)i * bs + t], ui = Ui[(size_t)i * bs + t];
-        size_t row = (size_t)i * kk;
+        const int t = e / (n - e0), i = e0 + e % (n - e0);
+        const double tr = Tr[(size_t)t * n + i], ti = Ti[(size_t)t * n + i];
+        const double ur = Ur[(size_t)t * n + i], ui = Ui[(size_t)t * n + i];
+        const size_t row = (size_t)i * kk;
         PAre[row + t] = tr; PAre[row + bs + t] = -ti; PAre[row + 2 * bs + t] = -ur; PAre[row + 3 * bs + t] = ui;
         PBre[row + t] = ur; PBre[row + bs + t] = ui;  PBre[row + 2 * bs + t] = tr;  PBre[row + 3 * bs + t] = ti;
         PAim[row + t] = tr; PAim[row + bs + t] = ti;  PAim[row + 2 * bs + t] = -ur; PAim[row + 3 * bs + t] = -ui;

@@ -478,12 +478,12 @@ GemmBatch gb_basic(int m, int n, int k, double** A, int lda, double** B, int ldb
 
 cudaError_t launch_gj(sgs_ctx* c, int n, int batch, int bsz, double** W, double** T, int* piv, double* logdet,
                       double* dsign, int* err, double tiny, cudaStream_t st) {
-    const size_t smem = (size_t)n * bsz * sizeof(double) + bsz * sizeof(double);
+    const size_t smem = (size_t)n * (bsz + 1) * sizeof(double) + bsz * sizeof(double);
     cudaFuncSetAttribute(gj_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int k0 = 0; k0 < n; k0 += bsz) {
         const int bb = std::min(bsz, n - k0);
         GJPanelArgs a{W, T, piv, logdet, dsign, err, n, k0, bb, tiny};
-        gj_panel_kernel<<<batch, 512, (size_t)n * bb * sizeof(double) + bb * sizeof(double), st>>>(a);
+        gj_panel_kernel<<<batch, 512, (size_t)n * (bb + 1) * sizeof(double) + bb * sizeof(double), st>>>(a);
         counted();
         GemmBatch g = gb_basic(n, n, bb, W, n, T, n, W, n, batch);
         g.offA = k0;
@@ -512,7 +512,9 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
         g.transB = 1;
         g.offC = (long long)e0 * n + e0;
         g.Cin = (const double* const*)upC; g.offCin = g.offC; g.ldcin = n; g.beta = 1.0;
-        // the rank-2b complex update is antisymmetric: half of each real product is needed
+        // the rank-2b complex update T U^T - U T^T is antisymmetric, as is the trailing
+        // block it updates: compute the lower tiles and mirror them
+        g.mode = GEMM_SKEW;
         const double m2 = (double)(n - e0) * (n - e0);
         cudaError_t e = gemm(c, g, st, m2 * 4.0 * bs * 2 * batch);
         if (e != cudaSuccess) return e;
