@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
     ap.add_argument("--workload", default="large", choices=["large", "small"])
     ap.add_argument("--rank", type=int, default=0, help="override the ansatz rank M (profiling cases)")
+    ap.add_argument("--fp64-path", default="fma", choices=["fma", "mma"], help="FP64 product pipe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -204,6 +205,7 @@ def run_sgs(args):
     import paper_2105_01088_gb300 as sgs
 
     sgs.use_torch_allocator()
+    sgs.set_fp64_gemm_path(args.fp64_path == "fma")
     w = workload(args.workload, args.rank)
     p = w.model
     prec = PRECISIONS[args.precision]
@@ -212,6 +214,8 @@ def run_sgs(args):
     stream = torch.cuda.current_stream()
     solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=prec, parity=w.parity, stream=stream)
     peak_fp64_mma = sgs.probe_peak(0)
+    peak_fp64_fma = sgs.probe_peak(1)
+    peak_fp64 = peak_fp64_fma if args.fp64_path == "fma" else peak_fp64_mma
 
     solver.step(args.warmup)
     clocks = ClockSampler(local)
@@ -276,13 +280,13 @@ def run_sgs(args):
             t = json.load(open(tfile)).get(f"gemm_f64_all_{args.precision}", {})
             if t.get("n") == n and t.get("rank") == w.rank:
                 traffic = t.get("bytes_per_launch")
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_fp64_mma, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp64_mma, "traffic": traffic,
-                "kernel": "gemm_f64_kernel (FP64 m8n8k4 MMA; all its launches: Gauss-Jordan and Pfaffian "
-                          "updates, pair and state products)",
+        roof = {"bound": "alu" if args.fp64_path == "fma" else "tensor", "achieved": achieved, "peak": peak_fp64,
+                "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": traffic,
+                "kernel": f"gemm_f64_kernel (FP64 {args.fp64_path.upper()}; all its launches: Gauss-Jordan and "
+                          "Pfaffian updates, pair and state products)",
                 "launches": int(g_n), "flops_per_launch": g_fl / max(g_n, 1), "ms_per_launch": g_ms / max(g_n, 1),
-                "peak_source": "measured live: FP64 m8n8k4 MMA throughput probe (sgs_probe_peak); "
-                               "not in MEASURED_PEAKS.json"}
+                "peak_source": f"measured live: FP64 {args.fp64_path.upper()} throughput probe (sgs_probe_peak "
+                               f"kind {1 if args.fp64_path == 'fma' else 0}); not in MEASURED_PEAKS.json"}
     tc_roof = None
     if args.precision != "fp64" and prof["eom_v"][0] > 0:
         bf16 = peaks.get("bf16_tflops", 1900.0)
@@ -302,7 +306,8 @@ def run_sgs(args):
             "config": config_of(w, args.precision),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "roofline": roof, "tc_roofline": tc_roof, "clocks": ck, "stages": stages,
-            "energy_last": float(E[0, -1]), "fp64_mma_peak_tflops": peak_fp64_mma}
+            "energy_last": float(E[0, -1]), "fp64_mma_peak_tflops": peak_fp64_mma,
+            "fp64_fma_peak_tflops": peak_fp64_fma}
     solver.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_step, sample = oracle_sample(w, n_pairs=6, n_states=2)

@@ -179,6 +179,11 @@ sgs_status sgs_get_profile(const sgs_ctx* ctx, double* ms, double* flops, double
  * kernel (their sum shows whether the two share one pipe). */
 sgs_status sgs_probe_peak(int kind, double* tflops);
 
+/* Compute path of every FP64 product (process-wide): 1 = FP64 FMA on the CUDA
+ * cores (default), 0 = the m8n8k4 FP64 MMA.  Both give FP64 results; on GB300
+ * they share one pipe and FMA issues faster. */
+void sgs_set_fp64_gemm_path(int use_fma);
+
 /* Majorana form of the Anderson impurity of Sec. IV (H_0 + H_I) with
  * n_channels open bath chains of n_bath sites, hybridisation V, hopping t,
  * chemical potential mu, interaction U n_up n_dn and level eps_d on the

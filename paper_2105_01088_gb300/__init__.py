@@ -69,6 +69,7 @@ SIGNATURES = {
     "sgs_set_profiling": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_get_profile": (ctypes.c_int, [_ctxp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "sgs_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
+    "sgs_set_fp64_gemm_path": (None, [ctypes.c_int]),
     "sgs_kernel_inverse": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_pfaffian": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_dgemm": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp]),
@@ -287,6 +288,11 @@ class Solver:
 
 
 # ------------------------------------------------------------ building blocks
+
+def set_fp64_gemm_path(use_fma=True):
+    """FP64 products on the FMA pipe (default) or the m8n8k4 MMA."""
+    _lib.sgs_set_fp64_gemm_path(1 if use_fma else 0)
+
 
 def probe_peak(kind=0):
     """Measured TFLOP/s of the FP64 MMA (kind 0), FP64 FMA (kind 1), or both

@@ -1,9 +1,9 @@
-// Batched FP64 GEMM on the FP64 tensor path (mma.sync m8n8k4 .f64).
-//
-// tcgen05 has no f64 kind; on GB300 the m8n8k4 FP64 MMA runs about 3.5x
-// faster than FP64 FMA on the CUDA cores, so every FP64 product of the step
-// (pair products, the delayed updates of the blocked factorisations, the
-// per-state exponential and purification) goes through this one kernel.
+// Batched FP64 GEMM.  tcgen05 has no f64 kind.  On GB300 the FP64 FMA of the
+// CUDA cores and the m8n8k4 FP64 MMA (mma.sync .f64) share one FP64 pipe,
+// measured at 1.25 and 1.09 TFLOP/s; this kernel has both compute paths over
+// the same tiles (FMA by default) and every FP64 product of the step (pair
+// products, the delayed updates of the blocked factorisations, the per-state
+// exponential and purification) goes through it.
 //
 // C_b = alpha * alpha_b[b] * op(A_b) op(B_b) + beta * Cin_b + diag * I
 // with A_b = A1_b + sA2 * A2_b (the pair difference Gamma_a - Gamma_b is
@@ -47,10 +47,13 @@ __device__ __forceinline__ void dmma_8x8x4(double& c0, double& c1, double a, dou
                  : "+d"(c0), "+d"(c1) : "d"(a), "d"(b));
 }
 
-template <int TA, int TB>
+// FMA = false: m8n8k4 FP64 MMA, 4 warps of 32x32.  FMA = true: FP64 FMA on the
+// CUDA cores, each thread a 4 x 8 register tile (rows 4*(t/8).., cols 8*(t%8)..);
+// on GB300 both share one FP64 pipe, FMA issuing at the higher rate.
+template <int TA, int TB, bool FMA>
 __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
-    __shared__ double As[2][GBM * GAS];
-    __shared__ double Bs[2][GBK * GBS];
+    __shared__ __align__(16) double As[2][GBM * GAS];
+    __shared__ __align__(16) double Bs[2][GBK * GBS];
 
     const int b = blockIdx.y;
     int tm, tn;
@@ -142,19 +145,42 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
         for (int kt = 0; kt < nk; kt++) {
             const int s = kt & 1;
             if (kt + 1 < nk) load_tiles((kt + 1) * GBK);
+            if (FMA) {
+                const int r0 = (tid >> 3) * 4, c0 = (tid & 7) * 8;
 #pragma unroll
-            for (int ks = 0; ks < GBK / 4; ks++) {
-                double af[4], bf[4];
+                for (int kk = 0; kk < GBK; kk++) {
+                    double af[4], bf[8];
 #pragma unroll
-                for (int i = 0; i < 4; i++)
-                    af[i] = As[s][(wm + i * 8 + (lane >> 2)) * GAS + ks * 4 + (lane & 3)];
+                    for (int i = 0; i < 4; i++) af[i] = As[s][(r0 + i) * GAS + kk];
 #pragma unroll
-                for (int j = 0; j < 4; j++)
-                    bf[j] = Bs[s][(ks * 4 + (lane & 3)) * GBS + wn + j * 8 + (lane >> 2)];
+                    for (int j = 0; j < 8; j += 2) {
+                        const double2 v = *reinterpret_cast<const double2*>(&Bs[s][kk * GBS + c0 + j]);
+                        bf[j] = v.x;
+                        bf[j + 1] = v.y;
+                    }
 #pragma unroll
-                for (int i = 0; i < 4; i++)
+                    for (int i = 0; i < 4; i++)
 #pragma unroll
-                    for (int j = 0; j < 4; j++) dmma_8x8x4(acc[i][j][0], acc[i][j][1], af[i], bf[j]);
+                        for (int j = 0; j < 4; j++) {
+                            acc[i][j][0] = fma(af[i], bf[2 * j], acc[i][j][0]);
+                            acc[i][j][1] = fma(af[i], bf[2 * j + 1], acc[i][j][1]);
+                        }
+                }
+            } else {
+#pragma unroll
+                for (int ks = 0; ks < GBK / 4; ks++) {
+                    double af[4], bf[4];
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+                        af[i] = As[s][(wm + i * 8 + (lane >> 2)) * GAS + ks * 4 + (lane & 3)];
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        bf[j] = Bs[s][(ks * 4 + (lane & 3)) * GBS + wn + j * 8 + (lane >> 2)];
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+#pragma unroll
+                        for (int j = 0; j < 4; j++) dmma_8x8x4(acc[i][j][0], acc[i][j][1], af[i], bf[j]);
+                }
             }
             if (kt + 1 < nk) store_tiles(s ^ 1);
             __syncthreads();
@@ -168,10 +194,10 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
     for (int i = 0; i < 4; i++) {
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const int r = m0 + wm + i * 8 + (lane >> 2);
+            const int r = FMA ? m0 + (tid >> 3) * 4 + i : m0 + wm + i * 8 + (lane >> 2);
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const int c = n0 + wn + j * 8 + 2 * (lane & 3) + h;
+                const int c = FMA ? n0 + (tid & 7) * 8 + 2 * j + h : n0 + wn + j * 8 + 2 * (lane & 3) + h;
                 if (r >= g.m || c >= g.n) continue;
                 double v;
                 if (!active) {
@@ -203,15 +229,25 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
     }
 }
 
+// FP64 compute path of gemm_f64: 1 = FMA (default), 0 = m8n8k4 MMA
+inline int g_gemm_fma = 1;
+
 inline cudaError_t gemm_f64(const GemmBatch& g, cudaStream_t st) {
     if (g.batch <= 0 || g.m <= 0 || g.n <= 0) return cudaSuccess;
     const int tmn = (g.m + GBM - 1) / GBM, tnn = (g.n + GBN - 1) / GBN;
     unsigned gx = (g.mode == GEMM_SKEW) ? (unsigned)(tmn * (tmn + 1) / 2) : (unsigned)(tmn * tnn);
     dim3 grid(gx, g.batch);
-    if (!g.transA && !g.transB) gemm_f64_kernel<0, 0><<<grid, 128, 0, st>>>(g);
-    else if (!g.transA && g.transB) gemm_f64_kernel<0, 1><<<grid, 128, 0, st>>>(g);
-    else if (g.transA && !g.transB) gemm_f64_kernel<1, 0><<<grid, 128, 0, st>>>(g);
-    else gemm_f64_kernel<1, 1><<<grid, 128, 0, st>>>(g);
+    if (g_gemm_fma) {
+        if (!g.transA && !g.transB) gemm_f64_kernel<0, 0, true><<<grid, 128, 0, st>>>(g);
+        else if (!g.transA && g.transB) gemm_f64_kernel<0, 1, true><<<grid, 128, 0, st>>>(g);
+        else if (g.transA && !g.transB) gemm_f64_kernel<1, 0, true><<<grid, 128, 0, st>>>(g);
+        else gemm_f64_kernel<1, 1, true><<<grid, 128, 0, st>>>(g);
+    } else {
+        if (!g.transA && !g.transB) gemm_f64_kernel<0, 0, false><<<grid, 128, 0, st>>>(g);
+        else if (!g.transA && g.transB) gemm_f64_kernel<0, 1, false><<<grid, 128, 0, st>>>(g);
+        else if (g.transA && !g.transB) gemm_f64_kernel<1, 0, false><<<grid, 128, 0, st>>>(g);
+        else gemm_f64_kernel<1, 1, false><<<grid, 128, 0, st>>>(g);
+    }
     return cudaGetLastError();
 }
 

@@ -1054,6 +1054,8 @@ sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double*
     return SGS_OK;
 }
 
+void sgs_set_fp64_gemm_path(int use_fma) { g_gemm_fma = use_fma ? 1 : 0; }
+
 sgs_status sgs_probe_peak(int kind, double* tflops) {
     if (!tflops || kind < 0 || kind > 2) return SGS_EINVAL;
     int dev = 0, sms = 0;
