@@ -211,7 +211,7 @@ def run_sgs(args):
     prec = PRECISIONS[args.precision]
     g, lam = inp.initial_state(p.n_modes, w.rank, w.seed + 1000 * rank, w.parity)
     model = sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()          # a capturable stream: steps replay a CUDA graph
     solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=prec, parity=w.parity, stream=stream)
     peak_fp64_mma = sgs.probe_peak(0)
     peak_fp64_fma = sgs.probe_peak(1)
@@ -219,7 +219,6 @@ def run_sgs(args):
 
     solver.step(args.warmup)
     clocks = ClockSampler(local)
-    solver.set_profiling(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     if dist:
@@ -234,6 +233,10 @@ def run_sgs(args):
         dist.barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
+    # second timed region of the same length with per-stage and per-GEMM-launch events (direct
+    # launches) for the roofline of the dominant kernel
+    solver.set_profiling(True)
+    solver.step(args.steps)
     prof, launches, gemm_prof = solver.profile()
     solver.set_profiling(False)
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")

@@ -98,6 +98,12 @@ typedef struct {
  * gamma0 NULL), SGS_ENOMEM, SGS_ECUDA.  On error *out is NULL. */
 sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_instances, sgs_ctx** out);
 
+/* Graph replay (default on): the first sgs_step of a context captures one step
+ * of every instance into a CUDA graph, later steps replay it.  Needs a
+ * context stream other than the legacy default stream; off while profiling.
+ * The capture keeps the FP64 GEMM path in force when it was taken. */
+sgs_status sgs_set_graphs(sgs_ctx* ctx, int enable);
+
 /* Advance every instance by n_steps imaginary-time steps (Sec. III C).
  * energies (may be NULL): [n_instances][n_steps], the energy E of the
  * states at the start of each step with optimal amplitudes.

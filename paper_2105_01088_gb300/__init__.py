@@ -55,6 +55,7 @@ SIGNATURES = {
     "sgs_init": (ctypes.c_int, [ctypes.POINTER(_Model), ctypes.POINTER(_Options), ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_void_p)]),
     "sgs_step": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp]),
+    "sgs_set_graphs": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_energy": (ctypes.c_int, [_ctxp, _dp]),
     "sgs_correlator": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _dp]),
     "sgs_free": (None, [_ctxp]),
@@ -222,6 +223,10 @@ class Solver:
         E = np.zeros((self.n_instances, n_steps))
         self._check(_lib.sgs_step(self._ctx, n_steps, _ptr(E)))
         return E
+
+    def set_graphs(self, enable=True):
+        """Replay a captured CUDA graph of one step (default on)."""
+        self._check(_lib.sgs_set_graphs(self._ctx, 1 if enable else 0))
 
     def energy(self) -> np.ndarray:
         E = np.zeros(self.n_instances)

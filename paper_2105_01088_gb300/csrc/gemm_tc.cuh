@@ -283,8 +283,8 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(TcBatch g) {
 template <int BN, int KIND>
 inline cudaError_t gemm_tc_launch(const TcBatch& g, cudaStream_t st) {
     constexpr int NS = (KIND == TC_3XTF32) ? 2 : 1;
+    // the dynamic shared-memory limit is raised once per process by the library, outside stream capture
     constexpr int smem = 2 * NS * (TC_BM * 128 + BN * 128) + 1024;
-    cudaFuncSetAttribute(gemm_tc_kernel<BN, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int tmn = (g.m + TC_BM - 1) / TC_BM, tnn = (g.n + BN - 1) / BN;
     const unsigned gx = g.skew ? (unsigned)(tmn * (tmn + 1) / 2) : (unsigned)(tmn * tnn);
     gemm_tc_kernel<BN, KIND><<<dim3(gx, g.batch), 128, smem, st>>>(g);

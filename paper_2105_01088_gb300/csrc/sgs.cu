@@ -74,6 +74,7 @@ struct Instance {
     double *Gm = nullptr, *hm = nullptr, *lam = nullptr, *lt = nullptr, *coef = nullptr;
     double* Ehist = nullptr;
     int Ecap = 0;
+    double* Ecur = nullptr;             // energy slot written by the captured step
     int steps_since_profile = 0;
     double* corr_scratch = nullptr;     // observables: partial sums, sites, outputs
     size_t corr_cap = 0;
@@ -156,6 +157,11 @@ struct sgs_ctx {
     double stage_flops[SGS_N_STAGES] = {0};
     double stage_bytes[SGS_N_STAGES] = {0};
     long long launches = 0;
+    // one captured step of every instance, replayed by sgs_step
+    bool use_graph = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_launches = 0;
     // every FP64 GEMM launch (except the pass-through squarings) timed on its own
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gmarks;
     double gemm_ms = 0.0, gemm_flops = 0.0;
@@ -332,6 +338,7 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.lam = c->alloc<double>(2 * M); I.lt = c->alloc<double>(2 * M); I.coef = c->alloc<double>(6 * M * M);
     I.Ecap = 1;
     I.Ehist = c->alloc<double>(1);
+    I.Ecur = c->alloc<double>(1);
     I.eigscratch = c->alloc<double>(6 * (size_t)(2 * M) * (2 * M) + 8 * 2 * M);
     I.err = c->alloc<int>(1);
     void* check[] = {I.gamma, I.dgamma, I.work, I.si, I.imd, I.wr, I.va, I.xa, I.tbuf, I.pfTU, I.pfpack, I.s[0],
@@ -451,6 +458,31 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
 
 // ------------------------------------------------------------------ launches
 
+// Kernels with large dynamic shared memory: raise their limit once per process,
+// outside any stream capture (227 KB, the per-block maximum of sm_100-class GPUs).
+std::once_flag g_attr_once;
+template <class K>
+void raise_smem_limit(K kernel, int optin) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
+    // the limit applies to dynamic shared memory on top of the kernel's static shared memory
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+void set_kernel_attributes() {
+    std::call_once(g_attr_once, [] {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        raise_smem_limit(gj_panel_kernel, optin);
+        raise_smem_limit(pf_panel_kernel, optin);
+        raise_smem_limit(renyi_pf_kernel, optin);
+        raise_smem_limit(gemm_tc_kernel<128, TC_TF32>, optin);
+        raise_smem_limit(gemm_tc_kernel<128, TC_BF16>, optin);
+        raise_smem_limit(gemm_tc_kernel<128, TC_3XTF32>, optin);
+        cudaGetLastError();
+    });
+}
+
 // every FP64 product of the library goes through here; flops = algorithmic work of
 // the launch (antisymmetric outputs count half), < 0 = not profiled
 inline cudaError_t gemm(sgs_ctx* c, const GemmBatch& g, cudaStream_t st, double flops) {
@@ -478,8 +510,7 @@ GemmBatch gb_basic(int m, int n, int k, double** A, int lda, double** B, int ldb
 
 cudaError_t launch_gj(sgs_ctx* c, int n, int batch, int bsz, double** W, double** T, int* piv, double* logdet,
                       double* dsign, int* err, double tiny, cudaStream_t st) {
-    const size_t smem = (size_t)n * (bsz + 1) * sizeof(double) + bsz * sizeof(double);
-    cudaFuncSetAttribute(gj_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_kernel_attributes();
     for (int k0 = 0; k0 < n; k0 += bsz) {
         const int bb = std::min(bsz, n - k0);
         GJPanelArgs a{W, T, piv, logdet, dsign, err, n, k0, bb, tiny};
@@ -498,7 +529,7 @@ cudaError_t launch_gj(sgs_ctx* c, int n, int batch, int bsz, double** W, double*
 cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, double** TU, double** PK, double** upA,
                       double** upB, double** upC, double* logabs, double* phase, int* err, cudaStream_t st) {
     const size_t smem = (4 * (size_t)n + 4 * bsmax) * sizeof(double);
-    cudaFuncSetAttribute(pf_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_kernel_attributes();
     for (int k0 = 0; k0 < n; k0 += 2 * bsmax) {
         const int bs = std::min(bsmax, (n - k0) / 2);
         PfPanelArgs a{Y, TU, PK, logabs, phase, err, n, k0, bs, bsmax};
@@ -523,7 +554,7 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
 }
 
 // pair pass + amplitude solve for one instance; E -> Ehist[slot]
-cudaError_t pair_pass(sgs_ctx* c, Instance& I, int eslot) {
+cudaError_t pair_pass(sgs_ctx* c, Instance& I, double* Eout) {
     cudaStream_t st = c->stream;
     const int n = I.n, P = I.P, M = I.M;
     const size_t nn = (size_t)n * n;
@@ -560,7 +591,7 @@ cudaError_t pair_pass(sgs_ctx* c, Instance& I, int eslot) {
     }
     c->stage(SGS_STAGE_AMPLITUDES);
     pair_gh_kernel<<<P + M, 256, 0, st>>>(d, I.si, I.imd, I.logdet, I.pfphase, I.Gm, I.hm, I.fimp, I.fimp_state);
-    AmpArgs aa{M, I.Gm, I.hm, I.eigscratch, I.Ehist + eslot, I.lam, I.lt, I.coef, I.cmode, 1e-12, I.err};
+    AmpArgs aa{M, I.Gm, I.hm, I.eigscratch, Eout, I.lam, I.lt, I.coef, I.cmode, 1e-12, I.err};
     amp_solve_kernel<<<1, 256, 0, st>>>(aa);
     counted(); counted();
     return cudaGetLastError();
@@ -801,6 +832,7 @@ sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_inst
         if (o.rank < 1 || o.rank > SGS_MAX_RANK || (o.parity != 1 && o.parity != -1) || !o.gamma0) return SGS_EINVAL;
         if (o.precision < 0 || o.precision > 3 || (o.cmode != 0 && o.cmode != 1)) return SGS_EINVAL;
     }
+    set_kernel_attributes();
     sgs_ctx* c = new sgs_ctx();
     cudaGetDevice(&c->device);
     if (opts[0].stream) {
@@ -835,11 +867,40 @@ sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
         if (s != SGS_OK) return s;
     }
     const long long l0 = g_launches;
-    for (int step = 0; step < n_steps; step++) {
+    // graph replay needs a capturable stream (not the legacy default stream) and no profiling
+    const bool graph = c->use_graph && !c->prof && c->stream != nullptr && n_steps > 0;
+    if (graph && !c->graph_exec) {
+        const long long g0 = g_launches;
+        CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaSuccess;
         for (auto& I : c->inst) {
-            CUDA_TRY(c, pair_pass(c, I, step));
-            CUDA_TRY(c, eom_pass(c, I));
-            CUDA_TRY(c, update_pass(c, I));
+            if (ce == cudaSuccess) ce = pair_pass(c, I, I.Ecur);
+            if (ce == cudaSuccess) ce = eom_pass(c, I);
+            if (ce == cudaSuccess) ce = update_pass(c, I);
+        }
+        cudaError_t ee = cudaStreamEndCapture(c->stream, &c->graph);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            c->err = std::string("graph capture failed: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee);
+            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            return SGS_ECUDA;
+        }
+        CUDA_TRY(c, cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
+        c->graph_launches = g_launches - g0;
+        g_launches = g0;   // captured, not launched
+    }
+    for (int step = 0; step < n_steps; step++) {
+        if (graph) {
+            CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, c->stream));
+            g_launches += c->graph_launches;
+            for (auto& I : c->inst)
+                CUDA_TRY(c, cudaMemcpyAsync(I.Ehist + step, I.Ecur, sizeof(double), cudaMemcpyDeviceToDevice,
+                                            c->stream));
+        } else {
+            for (auto& I : c->inst) {
+                CUDA_TRY(c, pair_pass(c, I, I.Ehist + step));
+                CUDA_TRY(c, eom_pass(c, I));
+                CUDA_TRY(c, update_pass(c, I));
+            }
         }
     }
     c->stage(-1);
@@ -858,7 +919,7 @@ sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
 sgs_status sgs_energy(sgs_ctx* c, double* energies) {
     if (!c) return SGS_EINVAL;
     const long long l0 = g_launches;
-    for (auto& I : c->inst) CUDA_TRY(c, pair_pass(c, I, 0));
+    for (auto& I : c->inst) CUDA_TRY(c, pair_pass(c, I, I.Ehist));
     c->stage(-1);
     c->launches += g_launches - l0;
     sgs_status s = check_device_error(c);
@@ -884,7 +945,7 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
             if (!ok) { c->err = "correlator site out of range"; return SGS_EINVAL; }
         }
         // current states: pair pass and amplitudes (the states are not changed)
-        CUDA_TRY(c, pair_pass(c, I, 0));
+        CUDA_TRY(c, pair_pass(c, I, I.Ehist));
         c->stage(-1);
         const size_t rows = (size_t)I.P + I.M;
         const size_t need = rows * n_sites + 2 * (size_t)n_sites + 8;
@@ -915,7 +976,7 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
                 return SGS_EINVAL;
             }
         }
-        CUDA_TRY(c, pair_pass(c, I, 0));
+        CUDA_TRY(c, pair_pass(c, I, I.Ehist));
         c->stage(-1);
         const long long M2 = (long long)I.M * I.M;
         const long long npairs = M2 * (M2 + 1) / 2;
@@ -938,7 +999,7 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
             renyi_blocks_kernel<<<(unsigned)M2, 128, 0, c->stream>>>(I.dev(), I.si, I.imd, I.Gm, I.lam, I.pair_index,
                                                                      na2, blocks, wts);
             const size_t smem = 2 * (size_t)m * (m + 1) * sizeof(double);
-            CUDA_TRY(c, cudaFuncSetAttribute(renyi_pf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            set_kernel_attributes();
             const unsigned gx = (unsigned)std::min<long long>(npairs, 65535);
             const unsigned gy = (unsigned)((npairs + gx - 1) / gx);
             renyi_pf_kernel<<<dim3(gx, gy), 256, smem, c->stream>>>(blocks, wts, npairs, na2,
@@ -963,6 +1024,8 @@ void sgs_free(sgs_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     c->release_all();
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1055,6 +1118,12 @@ sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double*
 }
 
 void sgs_set_fp64_gemm_path(int use_fma) { g_gemm_fma = use_fma ? 1 : 0; }
+
+sgs_status sgs_set_graphs(sgs_ctx* c, int enable) {
+    if (!c) return SGS_EINVAL;
+    c->use_graph = enable != 0;
+    return SGS_OK;
+}
 
 sgs_status sgs_probe_peak(int kind, double* tflops) {
     if (!tflops || kind < 0 || kind > 2) return SGS_EINVAL;
@@ -1171,6 +1240,7 @@ sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, 
 sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, int k, int batch, int kind,
                               double* C) {
     if (!A || !Bt || !C || m < 1 || n < 1 || k < 1 || batch < 1 || kind < 0 || kind > 2 || (k & 7)) return SGS_EINVAL;
+    set_kernel_attributes();
     sgs_ctx tmp;
     cudaStreamCreateWithFlags(&tmp.stream, cudaStreamNonBlocking);
     const size_t na = (size_t)m * k, nb = (size_t)n * k, nc = (size_t)m * n;
