@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sgs", choices=["sgs", "reference"])
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
-    ap.add_argument("--workload", default="large", choices=["large", "small"])
+    ap.add_argument("--workload", default="large", choices=["large", "small", "serving"])
+    ap.add_argument("--rate", type=float, default=100.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--requests", type=int, default=16, help="serving: number of requests")
+    ap.add_argument("--max-steps", type=int, default=300, help="serving: step cap per solve")
     ap.add_argument("--rank", type=int, default=0, help="override the ansatz rank M (profiling cases)")
     ap.add_argument("--fp64-path", default="fma", choices=["fma", "mma"], help="FP64 product pipe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -323,10 +326,58 @@ def run_sgs(args):
     return 0
 
 
+def run_serving(args):
+    """Continuous batching of a Poisson stream of impurity solves (mixed precision,
+    resident slots admitted by an HBM budget) against the same solves run one at
+    a time with the plain FP64 step."""
+    import torch
+    import paper_2105_01088_gb300 as sgs
+    from paper_2105_01088_gb300.serving import Request, ServingLoop, latency_stats, run_sequential
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    sgs.use_torch_allocator()
+    prec = PRECISIONS[args.precision]
+    reqs = []
+    for i, (t, p, M, seed, par) in enumerate(inp.serving_requests(args.rate, args.requests, seed=7)):
+        g, lam = inp.initial_state(p.n_modes, M, seed, par)
+        reqs.append(Request(i, t, sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V), g, lam, par))
+    stream = torch.cuda.Stream()
+    budget = int(torch.cuda.get_device_properties(0).total_memory * 0.5)
+    # warm-up: one solve in each mode (kernel loading, allocator pools)
+    for pr in (prec, 0):
+        w = sgs.Solver(stream=stream)
+        k = w.admit(reqs[0].model, reqs[0].gamma0, reqs[0].lambda0, 0.05, pr, 0, reqs[0].parity)
+        w.step(3)
+        w.close()
+    solver = sgs.Solver(stream=stream, hbm_budget=budget)
+    loop = ServingLoop(solver, dtau=0.05, precision=prec, tol=1e-8, max_steps=args.max_steps)
+    res = loop.run(reqs)
+    solver.close()
+    seq = run_sequential(lambda: sgs.Solver(stream=stream), reqs, dtau=0.05, precision=0, tol=1e-8,
+                         max_steps=args.max_steps)
+    a, b = latency_stats(res), latency_stats(seq)
+    dE = max(abs(x.energy - y.energy) / abs(y.energy) for x, y in zip(res, seq))
+    line = {"metric": "impurity solves/s (continuous batching, Poisson arrivals)", "value": a["throughput_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "steps": int(sum(r.steps for r in res)), "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": {"workload": f"serving: {args.requests} Anderson solves, Poisson rate {args.rate}/s, "
+                                   "bath L ~ U{8..40}, M in {4, 8}, U ~ U[0,8], V ~ U[0.2,1], run to |dE| < 1e-8 "
+                                   f"per step or {args.max_steps} steps", "hbm_budget_bytes": budget},
+            "latency": {"p50_s": a["p50_s"], "p99_s": a["p99_s"], "mean_s": a["mean_s"]},
+            "sequential_fp64": {"throughput_per_s": b["throughput_per_s"], "p50_s": b["p50_s"], "p99_s": b["p99_s"]},
+            "converged": int(sum(r.converged for r in res)), "max_rel_energy_diff_vs_sequential_fp64": dE}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_sgs(args)
 
 

@@ -98,8 +98,24 @@ typedef struct {
  * gamma0 NULL), SGS_ENOMEM, SGS_ECUDA.  On error *out is NULL. */
 sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_instances, sgs_ctx** out);
 
+/* Continuous batching.  sgs_create makes an empty context on `stream` (NULL:
+ * a stream of its own) whose live instances may not hold more than
+ * hbm_budget bytes of device memory (0: no budget).  sgs_admit adds one
+ * instance (a solve request) while others are live: it returns its slot, or
+ * SGS_ENOMEM without allocating if the instance's estimated footprint would
+ * exceed the budget.  sgs_retire releases a slot's device memory for later
+ * admissions.  Slot ids are stable; retired slots are skipped by sgs_step /
+ * sgs_energy (their rows of `energies` are left untouched) and rejected by
+ * the per-instance calls.  Instances never interact: a slot's results are the
+ * same whatever else is live.  sgs_init = sgs_create + one sgs_admit each. */
+sgs_status sgs_create(void* stream, size_t hbm_budget, sgs_ctx** out);
+sgs_status sgs_admit(sgs_ctx* ctx, const sgs_model* model, const sgs_options* opts, int* slot);
+sgs_status sgs_retire(sgs_ctx* ctx, int slot);
+size_t sgs_bytes_in_use(const sgs_ctx* ctx);
+
 /* Graph replay (default on): the first sgs_step of a context captures one step
- * of every instance into a CUDA graph, later steps replay it.  Needs a
+ * of every live instance into a CUDA graph (one branch per instance, so their
+ * kernels overlap), later steps replay it; admit/retire re-capture.  Needs a
  * context stream other than the legacy default stream; off while profiling.
  * The capture keeps the FP64 GEMM path in force when it was taken. */
 sgs_status sgs_set_graphs(sgs_ctx* ctx, int enable);

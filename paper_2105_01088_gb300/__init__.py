@@ -55,6 +55,10 @@ SIGNATURES = {
     "sgs_init": (ctypes.c_int, [ctypes.POINTER(_Model), ctypes.POINTER(_Options), ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_void_p)]),
     "sgs_step": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp]),
+    "sgs_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
+    "sgs_admit": (ctypes.c_int, [_ctxp, ctypes.POINTER(_Model), ctypes.POINTER(_Options), ctypes.POINTER(ctypes.c_int)]),
+    "sgs_retire": (ctypes.c_int, [_ctxp, ctypes.c_int]),
+    "sgs_bytes_in_use": (ctypes.c_size_t, [_ctxp]),
     "sgs_set_graphs": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_energy": (ctypes.c_int, [_ctxp, _dp]),
     "sgs_correlator": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _dp]),
@@ -167,60 +171,97 @@ def build_anderson(n_bath, U, eps_d, V, t=1.0, mu=0.0, n_channels=1) -> Majorana
 
 # ------------------------------------------------------------ solver
 
+def _check_slot_args(model, gamma0, parity):
+    g = np.asarray(gamma0)
+    if g.ndim != 3 or g.shape[1:] != (model.n, model.n):
+        raise SGSError(1, f"gamma0 has shape {g.shape}, expected (M, {model.n}, {model.n})")
+    if not 1 <= g.shape[0] <= 64:
+        raise SGSError(1, f"rank {g.shape[0]} outside 1..64")
+    if parity not in (1, -1):
+        raise SGSError(1, f"parity {parity} is not +-1")
+
+
 class Solver:
-    """A context of one or more independent SGS problems resident on the GPU.
+    """A context of independent SGS problems (slots) resident on the GPU.
 
     models: MajoranaModel or list; gamma0: [M, n, n] or list; lambda0: [M]
     complex or None.  stream: a CUDA stream handle (int), a torch stream, or
-    None (torch's current stream when torch is available)."""
+    None (a stream of the library's own).  hbm_budget: bytes the live slots may
+    hold (0: no budget).  Slots can be added (admit) and released (retire)
+    while others are live: continuous batching."""
 
-    def __init__(self, models, gamma0, lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE,
-                 parity=1, stream=None):
+    def __init__(self, models=(), gamma0=(), lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE,
+                 parity=1, stream=None, hbm_budget=0):
         if isinstance(models, MajoranaModel):
             models, gamma0, lambda0 = [models], [gamma0], [lambda0]
-            dtau, precision, cmode, parity = [dtau], [precision], [cmode], [parity]
+        models = list(models)
         k = len(models)
 
         def per(x):
             return list(x) if isinstance(x, (list, tuple)) else [x] * k
 
-        dtau, precision, cmode, parity = per(dtau), per(precision), per(cmode), per(parity)
         if lambda0 is None:
             lambda0 = [None] * k
+        for m, g, pa in zip(models, gamma0, per(parity)):
+            _check_slot_args(m, g, pa)          # before any CUDA call
         if stream is not None and hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream
-        self._keep = []
-        mods = (_Model * k)()
-        opts = (_Options * k)()
-        self.shapes = []
-        for i, m in enumerate(models):
-            g = np.ascontiguousarray(gamma0[i], dtype=np.float64)
-            M = g.shape[0]
-            if g.shape != (M, m.n, m.n):
-                raise SGSError(1, f"gamma0[{i}] has shape {g.shape}, expected ({M}, {m.n}, {m.n})")
-            lam = None
-            if lambda0[i] is not None:
-                lam = np.ascontiguousarray(np.stack([np.real(lambda0[i]), np.imag(lambda0[i])], -1), dtype=np.float64)
-            self._keep += [m, g, lam]
-            mods[i] = _Model(m.n_modes, _ptr(m.A), len(m.quartic_val), _ptr(m.quartic_idx, _ip), _ptr(m.quartic_val),
-                             m.e_const)
-            opts[i] = _Options(M, dtau[i], precision[i], cmode[i], parity[i], _ptr(g), _ptr(lam),
-                               ctypes.c_void_p(stream) if stream else None)
-            self.shapes.append((M, m.n))
+        self._stream = stream
         ctx = ctypes.c_void_p()
-        st = _lib.sgs_init(mods, opts, k, ctypes.byref(ctx))
+        st = _lib.sgs_create(ctypes.c_void_p(stream) if stream else None, int(hbm_budget), ctypes.byref(ctx))
         if st != 0:
-            raise SGSError(st, "sgs_init failed")
+            raise SGSError(st, "sgs_create failed")
         self._ctx = ctx
-        self.n_instances = k
+        self.shapes = []
+        self.live = []
+        self._keep = {}
+        for i, m, g, l0, dt, pr, cm, pa in zip(range(k), models, gamma0, lambda0, per(dtau), per(precision),
+                                               per(cmode), per(parity)):
+            try:
+                self.admit(m, g, l0, dt, pr, cm, pa)
+            except SGSError:
+                self.close()
+                raise
+
+    @property
+    def n_instances(self):
+        return len(self.shapes)
+
+    def admit(self, model, gamma0, lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE, parity=1):
+        """Add one problem; returns its slot.  Raises SGSError(SGS_ENOMEM) if it
+        does not fit the HBM budget (nothing is allocated then)."""
+        _check_slot_args(model, gamma0, parity)
+        g = np.ascontiguousarray(gamma0, dtype=np.float64)
+        M = g.shape[0]
+        lam = None
+        if lambda0 is not None:
+            lam = np.ascontiguousarray(np.stack([np.real(lambda0), np.imag(lambda0)], -1), dtype=np.float64)
+        mod = _Model(model.n_modes, _ptr(model.A), len(model.quartic_val), _ptr(model.quartic_idx, _ip),
+                     _ptr(model.quartic_val), model.e_const)
+        opt = _Options(M, dtau, precision, cmode, parity, _ptr(g), _ptr(lam), None)
+        slot = ctypes.c_int(-1)
+        st = _lib.sgs_admit(self._ctx, ctypes.byref(mod), ctypes.byref(opt), ctypes.byref(slot))
+        if st != 0:
+            raise SGSError(st, (_lib.sgs_last_error(self._ctx) or b"").decode())
+        self.shapes.append((M, model.n))
+        self.live.append(True)
+        return slot.value
+
+    def retire(self, slot):
+        self._check(_lib.sgs_retire(self._ctx, slot))
+        self.live[slot] = False
+
+    def bytes_in_use(self):
+        return int(_lib.sgs_bytes_in_use(self._ctx))
 
     def _check(self, st):
         if st != 0:
             raise SGSError(st, (_lib.sgs_last_error(self._ctx) or b"").decode())
 
     def step(self, n_steps=1) -> np.ndarray:
-        """Advance every instance; returns energies [n_instances, n_steps]."""
-        E = np.zeros((self.n_instances, n_steps))
+        """Advance every live slot; returns energies [n_slots, n_steps] (NaN rows
+        for retired slots)."""
+        E = np.full((self.n_instances, n_steps), np.nan)
         self._check(_lib.sgs_step(self._ctx, n_steps, _ptr(E)))
         return E
 
@@ -229,7 +270,7 @@ class Solver:
         self._check(_lib.sgs_set_graphs(self._ctx, 1 if enable else 0))
 
     def energy(self) -> np.ndarray:
-        E = np.zeros(self.n_instances)
+        E = np.full(self.n_instances, np.nan)
         self._check(_lib.sgs_energy(self._ctx, _ptr(E)))
         return E
 

@@ -48,6 +48,11 @@ sgs_free_fn g_release = nullptr;
 void* g_user = nullptr;
 
 struct Instance {
+    bool live = true;                   // false once retired (slot ids stay stable)
+    std::vector<void*> allocs;          // device memory owned by this instance
+    size_t bytes = 0;
+    cudaStream_t st = nullptr;          // branch stream of the captured step
+    cudaEvent_t join = nullptr;
     int N = 0, n = 0, M = 0, P = 0, Ppf = 0, nimp = 0, nq = 0, a_nnz = 0;
     double dtau = 0.0, e_const = 0.0;
     int prec = 0, cmode = 0, parity = 1;
@@ -115,11 +120,19 @@ struct Instance {
 
 struct sgs_ctx {
     std::vector<Instance> inst;
+    // one captured step of every live instance (a branch each), replayed by sgs_step
+    bool use_graph = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_launches = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::string err;
     std::vector<void*> allocs;
     int device = 0;
+    Instance* owner = nullptr;          // instance being set up: its allocations are its own
+    size_t bytes_in_use = 0, budget = 0;  // budget 0 = unlimited
+    cudaEvent_t fork = nullptr;
 
     void* dalloc(size_t bytes) {
         if (bytes == 0) bytes = 16;
@@ -129,8 +142,25 @@ struct sgs_ctx {
         } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
             p = nullptr;
         }
-        if (p) allocs.push_back(p);
+        if (p) {
+            if (owner) { owner->allocs.push_back(p); owner->bytes += bytes; }
+            else allocs.push_back(p);
+            bytes_in_use += bytes;
+        }
         return p;
+    }
+    void release_instance(Instance& I) {
+        for (void* p : I.allocs) {
+            if (release) release(p, release_user);
+            else cudaFree(p);
+        }
+        I.allocs.clear();
+        bytes_in_use -= I.bytes;
+        I.bytes = 0;
+    }
+    void drop_graph() {
+        if (graph_exec) { cudaGraphExecDestroy(graph_exec); graph_exec = nullptr; }
+        if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
     }
     template <class T>
     T* alloc(size_t count) { return static_cast<T*>(dalloc(count * sizeof(T))); }
@@ -157,11 +187,6 @@ struct sgs_ctx {
     double stage_flops[SGS_N_STAGES] = {0};
     double stage_bytes[SGS_N_STAGES] = {0};
     long long launches = 0;
-    // one captured step of every instance, replayed by sgs_step
-    bool use_graph = true;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    long long graph_launches = 0;
     // every FP64 GEMM launch (except the pass-through squarings) timed on its own
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gmarks;
     double gemm_ms = 0.0, gemm_flops = 0.0;
@@ -233,6 +258,22 @@ unsigned grid_chunks(size_t work, int threads, unsigned cap) {
     if (g < 1) g = 1;
     if (g > cap) g = cap;
     return (unsigned)g;
+}
+
+// device bytes one instance holds (the allocations of setup_instance, up to small terms)
+size_t instance_bytes(int n, int M, int prec, int nimp) {
+    const size_t nn = (size_t)n * n, P = (size_t)M * (M - 1) / 2, Ppf = P > 0 ? P - (M - 1) : 0;
+    const size_t gj_b = (n <= 640) ? 32 : 16, bs = 16;
+    const size_t ni = std::max(nimp, 1);
+    size_t d = 7 * (size_t)M * nn + std::max<size_t>(P, 1) * nn * 7 + P * gj_b * n + Ppf * 20 * n * bs +
+               P * ni * ni * 2 + P * 2 * n * ni + 6 * (size_t)(2 * M) * (2 * M) + 16 * (size_t)M * M;
+    size_t bytes = 8 * d + 8 * P * n;   // + pivots and permutations
+    if (prec != SGS_FP64 && P > 0) {
+        const size_t ldp = (n + 7) & ~7, esz = (prec == SGS_MIXED_BF16) ? 2 : 4;
+        const size_t ops = (prec == SGS_FP32_3XTF32) ? 10 : 5;
+        bytes += P * n * ldp * esz * ops + 3 * P * nn * 4;
+    }
+    return bytes + (1 << 20);
 }
 
 sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs_options& o) {
@@ -554,8 +595,7 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
 }
 
 // pair pass + amplitude solve for one instance; E -> Ehist[slot]
-cudaError_t pair_pass(sgs_ctx* c, Instance& I, double* Eout) {
-    cudaStream_t st = c->stream;
+cudaError_t pair_pass(sgs_ctx* c, Instance& I, double* Eout, cudaStream_t st) {
     const int n = I.n, P = I.P, M = I.M;
     const size_t nn = (size_t)n * n;
     const double n3 = (double)n * n * n;
@@ -597,8 +637,7 @@ cudaError_t pair_pass(sgs_ctx* c, Instance& I, double* Eout) {
     return cudaGetLastError();
 }
 
-cudaError_t eom_pass(sgs_ctx* c, Instance& I) {
-    cudaStream_t st = c->stream;
+cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     const int n = I.n, P = I.P, M = I.M;
     const size_t nn = (size_t)n * n;
     const double n3 = (double)n * n * n;
@@ -711,8 +750,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I) {
     return cudaGetLastError();
 }
 
-cudaError_t update_pass(sgs_ctx* c, Instance& I) {
-    cudaStream_t st = c->stream;
+cudaError_t update_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     const int n = I.n, M = I.M;
     const size_t nn = (size_t)n * n;
     const double n3 = (double)n * n * n;
@@ -771,6 +809,7 @@ cudaError_t update_pass(sgs_ctx* c, Instance& I) {
 sgs_status check_device_error(sgs_ctx* c) {
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     for (size_t i = 0; i < c->inst.size(); i++) {
+        if (!c->inst[i].live) continue;
         int e = 0;
         CUDA_TRY(c, cudaMemcpy(&e, c->inst[i].err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e) {
@@ -821,22 +860,24 @@ void sgs_set_allocator(sgs_alloc_fn alloc, sgs_free_fn release, void* user) {
     g_user = user;
 }
 
-sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_instances, sgs_ctx** out) {
+namespace {
+sgs_status check_args(const sgs_model& m, const sgs_options& o) {
+    if (m.n_modes < 1 || !m.A || (m.n_quartic > 0 && (!m.quartic_idx || !m.quartic_val))) return SGS_EINVAL;
+    if (o.rank < 1 || o.rank > SGS_MAX_RANK || (o.parity != 1 && o.parity != -1) || !o.gamma0) return SGS_EINVAL;
+    if (o.precision < 0 || o.precision > 3 || (o.cmode != 0 && o.cmode != 1)) return SGS_EINVAL;
+    return SGS_OK;
+}
+}  // namespace
+
+sgs_status sgs_create(void* stream, size_t hbm_budget, sgs_ctx** out) {
     if (!out) return SGS_EINVAL;
     *out = nullptr;
-    if (!models || !opts || n_instances < 1) return SGS_EINVAL;
-    for (int i = 0; i < n_instances; i++) {
-        const sgs_model& m = models[i];
-        const sgs_options& o = opts[i];
-        if (m.n_modes < 1 || !m.A || (m.n_quartic > 0 && (!m.quartic_idx || !m.quartic_val))) return SGS_EINVAL;
-        if (o.rank < 1 || o.rank > SGS_MAX_RANK || (o.parity != 1 && o.parity != -1) || !o.gamma0) return SGS_EINVAL;
-        if (o.precision < 0 || o.precision > 3 || (o.cmode != 0 && o.cmode != 1)) return SGS_EINVAL;
-    }
     set_kernel_attributes();
     sgs_ctx* c = new sgs_ctx();
     cudaGetDevice(&c->device);
-    if (opts[0].stream) {
-        c->stream = (cudaStream_t)opts[0].stream;
+    c->budget = hbm_budget;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
     } else {
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
             delete c;
@@ -844,17 +885,66 @@ sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_inst
         }
         c->own_stream = true;
     }
-    c->inst.resize(n_instances);
+    *out = c;
+    return SGS_OK;
+}
+
+sgs_status sgs_admit(sgs_ctx* c, const sgs_model* model, const sgs_options* opt, int* slot) {
+    if (!c || !model || !opt || !slot) return SGS_EINVAL;
+    *slot = -1;
+    sgs_status s = check_args(*model, *opt);
+    if (s != SGS_OK) { c->err = "invalid model or options"; return s; }
+    const size_t need = instance_bytes(2 * model->n_modes, opt->rank, opt->precision, 16);
+    if (c->budget && c->bytes_in_use + need > c->budget) {
+        c->err = "over the HBM budget: " + std::to_string(c->bytes_in_use + need) + " > " + std::to_string(c->budget);
+        return SGS_ENOMEM;
+    }
+    c->inst.emplace_back();
+    Instance& I = c->inst.back();
+    c->owner = &I;
+    s = setup_instance(c, I, *model, *opt);
+    c->owner = nullptr;
+    if (s == SGS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) s = SGS_ECUDA;
+    if (s != SGS_OK) {
+        cudaStreamSynchronize(c->stream);
+        c->release_instance(I);
+        c->inst.pop_back();
+        return s;
+    }
+    c->drop_graph();     // the captured step no longer covers every live instance
+    *slot = (int)c->inst.size() - 1;
+    return SGS_OK;
+}
+
+sgs_status sgs_retire(sgs_ctx* c, int slot) {
+    if (!c || slot < 0 || slot >= (int)c->inst.size() || !c->inst[slot].live) return SGS_EINVAL;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    Instance& I = c->inst[slot];
+    c->release_instance(I);
+    I.live = false;
+    c->drop_graph();
+    return SGS_OK;
+}
+
+size_t sgs_bytes_in_use(const sgs_ctx* c) { return c ? c->bytes_in_use : 0; }
+
+sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_instances, sgs_ctx** out) {
+    if (!out) return SGS_EINVAL;
+    *out = nullptr;
+    if (!models || !opts || n_instances < 1) return SGS_EINVAL;
+    for (int i = 0; i < n_instances; i++)
+        if (check_args(models[i], opts[i]) != SGS_OK) return SGS_EINVAL;
+    sgs_ctx* c = nullptr;
+    sgs_status s = sgs_create(opts[0].stream, 0, &c);
+    if (s != SGS_OK) return s;
+    c->inst.reserve(n_instances);
     for (int i = 0; i < n_instances; i++) {
-        sgs_status s = setup_instance(c, c->inst[i], models[i], opts[i]);
+        int slot;
+        s = sgs_admit(c, &models[i], &opts[i], &slot);
         if (s != SGS_OK) {
             sgs_free(c);
             return s;
         }
-    }
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
-        sgs_free(c);
-        return SGS_ECUDA;
     }
     *out = c;
     return SGS_OK;
@@ -863,25 +953,39 @@ sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_inst
 sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
     if (!c || n_steps < 0) return SGS_EINVAL;
     for (auto& I : c->inst) {
+        if (!I.live) continue;
+        c->owner = &I;
         sgs_status s = ensure_ehist(c, I, std::max(n_steps, 1));
+        c->owner = nullptr;
         if (s != SGS_OK) return s;
     }
     const long long l0 = g_launches;
     // graph replay needs a capturable stream (not the legacy default stream) and no profiling
     const bool graph = c->use_graph && !c->prof && c->stream != nullptr && n_steps > 0;
     if (graph && !c->graph_exec) {
+        if (!c->fork) CUDA_TRY(c, cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+        for (auto& I : c->inst) {
+            if (!I.live) continue;
+            if (!I.st) CUDA_TRY(c, cudaStreamCreateWithFlags(&I.st, cudaStreamNonBlocking));
+            if (!I.join) CUDA_TRY(c, cudaEventCreateWithFlags(&I.join, cudaEventDisableTiming));
+        }
         const long long g0 = g_launches;
         CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t ce = cudaSuccess;
+        cudaError_t ce = cudaEventRecord(c->fork, c->stream);
+        // independent instances are independent branches of the graph: their kernels overlap
         for (auto& I : c->inst) {
-            if (ce == cudaSuccess) ce = pair_pass(c, I, I.Ecur);
-            if (ce == cudaSuccess) ce = eom_pass(c, I);
-            if (ce == cudaSuccess) ce = update_pass(c, I);
+            if (!I.live) continue;
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(I.st, c->fork, 0);
+            if (ce == cudaSuccess) ce = pair_pass(c, I, I.Ecur, I.st);
+            if (ce == cudaSuccess) ce = eom_pass(c, I, I.st);
+            if (ce == cudaSuccess) ce = update_pass(c, I, I.st);
+            if (ce == cudaSuccess) ce = cudaEventRecord(I.join, I.st);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(c->stream, I.join, 0);
         }
         cudaError_t ee = cudaStreamEndCapture(c->stream, &c->graph);
         if (ce != cudaSuccess || ee != cudaSuccess) {
             c->err = std::string("graph capture failed: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee);
-            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            c->drop_graph();
             return SGS_ECUDA;
         }
         CUDA_TRY(c, cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
@@ -893,13 +997,15 @@ sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
             CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, c->stream));
             g_launches += c->graph_launches;
             for (auto& I : c->inst)
-                CUDA_TRY(c, cudaMemcpyAsync(I.Ehist + step, I.Ecur, sizeof(double), cudaMemcpyDeviceToDevice,
-                                            c->stream));
+                if (I.live)
+                    CUDA_TRY(c, cudaMemcpyAsync(I.Ehist + step, I.Ecur, sizeof(double), cudaMemcpyDeviceToDevice,
+                                                c->stream));
         } else {
             for (auto& I : c->inst) {
-                CUDA_TRY(c, pair_pass(c, I, I.Ehist + step));
-                CUDA_TRY(c, eom_pass(c, I));
-                CUDA_TRY(c, update_pass(c, I));
+                if (!I.live) continue;
+                CUDA_TRY(c, pair_pass(c, I, I.Ehist + step, c->stream));
+                CUDA_TRY(c, eom_pass(c, I, c->stream));
+                CUDA_TRY(c, update_pass(c, I, c->stream));
             }
         }
     }
@@ -910,8 +1016,9 @@ sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
     if (s != SGS_OK) return s;
     if (energies) {
         for (size_t i = 0; i < c->inst.size(); i++)
-            CUDA_TRY(c, cudaMemcpy(energies + i * n_steps, c->inst[i].Ehist, n_steps * sizeof(double),
-                                   cudaMemcpyDeviceToHost));
+            if (c->inst[i].live)
+                CUDA_TRY(c, cudaMemcpy(energies + i * n_steps, c->inst[i].Ehist, n_steps * sizeof(double),
+                                       cudaMemcpyDeviceToHost));
     }
     return SGS_OK;
 }
@@ -919,7 +1026,8 @@ sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
 sgs_status sgs_energy(sgs_ctx* c, double* energies) {
     if (!c) return SGS_EINVAL;
     const long long l0 = g_launches;
-    for (auto& I : c->inst) CUDA_TRY(c, pair_pass(c, I, I.Ehist));
+    for (auto& I : c->inst)
+        if (I.live) CUDA_TRY(c, pair_pass(c, I, I.Ehist, c->stream));
     c->stage(-1);
     c->launches += g_launches - l0;
     sgs_status s = check_device_error(c);
@@ -927,12 +1035,13 @@ sgs_status sgs_energy(sgs_ctx* c, double* energies) {
     if (s != SGS_OK) return s;
     if (energies)
         for (size_t i = 0; i < c->inst.size(); i++)
-            CUDA_TRY(c, cudaMemcpy(energies + i, c->inst[i].Ehist, sizeof(double), cudaMemcpyDeviceToHost));
+            if (c->inst[i].live)
+                CUDA_TRY(c, cudaMemcpy(energies + i, c->inst[i].Ehist, sizeof(double), cudaMemcpyDeviceToHost));
     return SGS_OK;
 }
 
 sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const int* sites, int n_sites, double* out) {
-    if (!c || instance < 0 || instance >= (int)c->inst.size() || !sites || !out || n_sites < 0) return SGS_EINVAL;
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live || !sites || !out || n_sites < 0) return SGS_EINVAL;
     if (n_sites == 0) return SGS_OK;
     Instance& I = c->inst[instance];
     const int nsite_tot = I.n / 4;          // spinful sites: modes 2s, 2s+1 -> Majoranas 4s..4s+3
@@ -945,12 +1054,14 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
             if (!ok) { c->err = "correlator site out of range"; return SGS_EINVAL; }
         }
         // current states: pair pass and amplitudes (the states are not changed)
-        CUDA_TRY(c, pair_pass(c, I, I.Ehist));
+        CUDA_TRY(c, pair_pass(c, I, I.Ehist, c->stream));
         c->stage(-1);
         const size_t rows = (size_t)I.P + I.M;
         const size_t need = rows * n_sites + 2 * (size_t)n_sites + 8;
         if (I.corr_cap < need) {
+            c->owner = &I;
             I.corr_scratch = c->alloc<double>(need);
+            c->owner = nullptr;
             if (!I.corr_scratch) { c->err = "device allocation failed"; return SGS_ENOMEM; }
             I.corr_cap = need;
         }
@@ -976,7 +1087,7 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
                 return SGS_EINVAL;
             }
         }
-        CUDA_TRY(c, pair_pass(c, I, I.Ehist));
+        CUDA_TRY(c, pair_pass(c, I, I.Ehist, c->stream));
         c->stage(-1);
         const long long M2 = (long long)I.M * I.M;
         const long long npairs = M2 * (M2 + 1) / 2;
@@ -985,7 +1096,9 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
         for (int i = 0; i < n_sites; i++) maxna2 = std::max(maxna2, 4 * (1 + sites[i]));
         const size_t need = (size_t)M2 * maxna2 * maxna2 * 2 + 2 * M2 + 2 * (size_t)npairs + 2 * nred + 8;
         if (I.corr_cap < need) {
+            c->owner = &I;
             I.corr_scratch = c->alloc<double>(need);
+            c->owner = nullptr;
             if (!I.corr_scratch) { c->err = "device allocation failed"; return SGS_ENOMEM; }
             I.corr_cap = need;
         }
@@ -1024,8 +1137,13 @@ void sgs_free(sgs_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-    if (c->graph) cudaGraphDestroy(c->graph);
+    c->drop_graph();
+    for (auto& I : c->inst) {
+        c->release_instance(I);
+        if (I.st) cudaStreamDestroy(I.st);
+        if (I.join) cudaEventDestroy(I.join);
+    }
+    if (c->fork) cudaEventDestroy(c->fork);
     c->release_all();
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1035,7 +1153,7 @@ const char* sgs_last_error(const sgs_ctx* c) { return c ? c->err.c_str() : "no c
 
 sgs_status sgs_get_state(const sgs_ctx* cc, int instance, double* gamma, double* lambda) {
     sgs_ctx* c = const_cast<sgs_ctx*>(cc);
-    if (!c || instance < 0 || instance >= (int)c->inst.size()) return SGS_EINVAL;
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
     const Instance& I = c->inst[instance];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (gamma)
@@ -1045,7 +1163,7 @@ sgs_status sgs_get_state(const sgs_ctx* cc, int instance, double* gamma, double*
 }
 
 sgs_status sgs_set_state(sgs_ctx* c, int instance, const double* gamma, const double* lambda) {
-    if (!c || instance < 0 || instance >= (int)c->inst.size()) return SGS_EINVAL;
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
     Instance& I = c->inst[instance];
     if (gamma)
         CUDA_TRY(c, cudaMemcpyAsync(I.gamma, gamma, (size_t)I.M * I.n * I.n * sizeof(double), cudaMemcpyHostToDevice,
@@ -1058,7 +1176,7 @@ sgs_status sgs_set_state(sgs_ctx* c, int instance, const double* gamma, const do
 
 sgs_status sgs_get_pair_matrices(const sgs_ctx* cc, int instance, double* G, double* h) {
     sgs_ctx* c = const_cast<sgs_ctx*>(cc);
-    if (!c || instance < 0 || instance >= (int)c->inst.size()) return SGS_EINVAL;
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
     const Instance& I = c->inst[instance];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (G) CUDA_TRY(c, cudaMemcpy(G, I.Gm, 2 * I.M * I.M * sizeof(double), cudaMemcpyDeviceToHost));
@@ -1068,7 +1186,7 @@ sgs_status sgs_get_pair_matrices(const sgs_ctx* cc, int instance, double* G, dou
 
 sgs_status sgs_get_derivative(const sgs_ctx* cc, int instance, double* dgamma) {
     sgs_ctx* c = const_cast<sgs_ctx*>(cc);
-    if (!c || instance < 0 || instance >= (int)c->inst.size() || !dgamma) return SGS_EINVAL;
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live || !dgamma) return SGS_EINVAL;
     const Instance& I = c->inst[instance];
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     CUDA_TRY(c, cudaMemcpy(dgamma, I.dgamma, (size_t)I.M * I.n * I.n * sizeof(double), cudaMemcpyDeviceToHost));

@@ -129,3 +129,22 @@ def batched_workloads(n_instances: int = 256, seed: int = 4, dtau: float = 0.05)
                             dtau=dtau, n_steps=1, seed=int(rng.integers(1 << 31)),
                             parity=1 if (L + 1) % 2 == 0 else -1))
     return out
+
+
+def serving_requests(rate: float, n_requests: int, seed: int = 5, n_bath=(8, 40), ranks=(4, 8)):
+    """A seeded Poisson stream of impurity solves: exponential inter-arrival times
+    at ``rate`` per second; per request an Anderson model with bath length
+    L ~ U{n_bath}, rank M from ``ranks``, U ~ U[0, 8], eps_d = -U/2, V ~ U[0.2, 1.0],
+    and random pure initial states.  Returns [(arrival, AndersonParams, M, seed, parity)]."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        L = int(rng.integers(n_bath[0], n_bath[1] + 1))
+        M = int(rng.choice(ranks))
+        U = float(rng.uniform(0.0, 8.0))
+        V = float(rng.uniform(0.2, 1.0))
+        out.append((t, AndersonParams(n_bath=L, U=U, eps_d=-U / 2, V=V), M, int(rng.integers(1 << 31)),
+                    1 if (L + 1) % 2 == 0 else -1))
+    return out

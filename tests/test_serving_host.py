@@ -1,0 +1,86 @@
+"""Host logic of the continuous-batching loop with a fake solver (CPU)."""
+import numpy as np
+
+from paper_2105_01088_gb300.serving import Request, ServingLoop, latency_stats, run_sequential
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 0.0)
+
+
+class FakeSolver:
+    """Energies relax geometrically per slot; each step costs 1 ms per live slot;
+    at most `capacity` slots fit the budget."""
+
+    def __init__(self, clock, capacity=2):
+        self.clock, self.capacity = clock, capacity
+        self.slots, self.live = [], []
+        self.log = []
+
+    def admit(self, model, gamma0, lambda0, dtau, precision, cmode, parity):
+        if sum(self.live) >= self.capacity:
+            e = RuntimeError("over budget")
+            e.status = 2
+            raise e
+        self.slots.append([float(model), 0])
+        self.live.append(True)
+        self.log.append(("admit", len(self.slots) - 1, self.clock.t))
+        return len(self.slots) - 1
+
+    def retire(self, slot):
+        self.live[slot] = False
+        self.log.append(("retire", slot, self.clock.t))
+
+    def step(self, n):
+        E = np.full((len(self.slots), 1), np.nan)
+        for i, (target, k) in enumerate(self.slots):
+            if self.live[i]:
+                self.slots[i][1] = k + 1
+                E[i, 0] = target * (1.0 - 0.5 ** (k + 1))
+        self.clock.t += 1e-3 * sum(self.live)
+        return E
+
+    def close(self):
+        pass
+
+
+def _reqs(arrivals):
+    return [Request(i, a, 1.0 + i, None) for i, a in enumerate(arrivals)]
+
+
+def test_fifo_admission_budget_and_retirement():
+    clk = FakeClock()
+    s = FakeSolver(clk, capacity=2)
+    loop = ServingLoop(s, tol=1e-6, max_steps=100, clock=clk, sleep=clk.sleep)
+    res = loop.run(_reqs([0.0, 0.0, 0.0, 0.5]))
+    assert [r.rid for r in res] == [0, 1, 2, 3]
+    assert all(r.converged for r in res)
+    admits = [x for x in s.log if x[0] == "admit"]
+    # the third request waits until a slot is retired (budget of two)
+    first_retire = min(t for k, _, t in s.log if k == "retire")
+    assert admits[2][2] >= first_retire
+    # energies converge to each request's own target (no cross talk between slots)
+    for r in res:
+        assert abs(r.energy - (1.0 + r.rid)) < 1e-5
+    st = latency_stats(res)
+    assert st["n"] == 4 and st["p99_s"] >= st["p50_s"] > 0
+
+
+def test_request_too_large_alone_is_rejected():
+    clk = FakeClock()
+    s = FakeSolver(clk, capacity=0)
+    loop = ServingLoop(s, clock=clk, sleep=clk.sleep)
+    assert loop.run(_reqs([0.0])) == [] and loop.rejected == [0]
+
+
+def test_sequential_baseline_serialises():
+    clk = FakeClock()
+    res = run_sequential(lambda: FakeSolver(clk), _reqs([0.0, 0.0, 0.0]), tol=1e-6, clock=clk, sleep=clk.sleep)
+    assert all(res[i].admitted >= res[i - 1].finished for i in range(1, 3))
