@@ -52,7 +52,7 @@ typedef enum {
 } sgs_status;
 
 typedef enum {
-    SGS_FP64 = 0,        /* every product in FP64 (FP64 tensor path, mma.sync f64) */
+    SGS_FP64 = 0,        /* every product in FP64 (FMA pipe by default, see sgs_set_fp64_gemm_path) */
     SGS_MIXED_TF32 = 1,  /* pair GEMMs of the equation of motion in TF32, FP32 accumulate */
     SGS_MIXED_BF16 = 2,  /* same in BF16 */
     SGS_FP32_3XTF32 = 3  /* same with the 3xTF32 split (about FP32 accuracy) */
@@ -77,6 +77,14 @@ typedef struct {
     double e_const;
 } sgs_model;
 
+typedef enum {
+    SGS_INTEGRATOR_EXP = 0,    /* Gamma <- R Gamma R^T, R = exp{(ds/4)[Gamma, dGamma]} (App. A, Eq. ExpStep),
+                                  then the canonical-form renormalisation */
+    SGS_INTEGRATOR_EULER = 1   /* Gamma <- Gamma + ds dGamma (Eq. RKstep), then the canonical-form
+                                  renormalisation (App. A): the polar factor, by six Newton-Schulz
+                                  iterations (enough while ds ||dGamma||_2 <= 0.5) */
+} sgs_integrator;
+
 /* Per-instance options.  gamma0: [rank][n][n] pure states of one parity
  * (Pf Gamma = parity); lambda0: [rank] complex, may be NULL (the first solve
  * replaces the amplitudes).  stream: a cudaStream_t, or NULL for the
@@ -90,6 +98,7 @@ typedef struct {
     const double* gamma0;
     const double* lambda0;
     void* stream;
+    int integrator;          /* sgs_integrator (0: the exponential step) */
 } sgs_options;
 
 /* Create a context holding n_instances independent problems (models[i],
@@ -112,6 +121,21 @@ sgs_status sgs_create(void* stream, size_t hbm_budget, sgs_ctx** out);
 sgs_status sgs_admit(sgs_ctx* ctx, const sgs_model* model, const sgs_options* opts, int* slot);
 sgs_status sgs_retire(sgs_ctx* ctx, int slot);
 size_t sgs_bytes_in_use(const sgs_ctx* ctx);
+
+/* Rank growth (Sec. III C): append to the live instance `slot` the state
+ * Q Gamma_src Q^T with Q = exp(K), a special orthogonal matrix.  The paper
+ * grows the ansatz one state at a time from the mean-field (rank-1) solution,
+ * copying a state of high amplitude through a random Q close to the identity;
+ * the caller draws K (host [n][n], row-major, exactly antisymmetric,
+ * ||K||_F <= 8; copied) and so fixes ||Q - 1||_F ~ ||K||_F.  src: index of the
+ * state to copy, or -1 for the state with the largest |lambda_mu| of the last
+ * amplitude solve (the initial amplitudes before the first step).  The rank
+ * grows by one, the slot keeps its index, the new state's amplitude is 0 until
+ * the next solve, and all device buffers of the instance are re-allocated
+ * (checked against the HBM budget).  Errors: SGS_EINVAL (slot not live, src
+ * out of range, rank already 64, K not antisymmetric or too large),
+ * SGS_ENOMEM, SGS_ECUDA; on error the instance is unchanged. */
+sgs_status sgs_add_state(sgs_ctx* ctx, int slot, const double* K, int src);
 
 /* Graph replay (default on): the first sgs_step of a context captures one step
  * of every live instance into a CUDA graph (one branch per instance, so their

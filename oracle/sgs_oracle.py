@@ -412,6 +412,48 @@ def run(model, gammas, ds, n_steps, mode=C_INVERSE):
     return np.array(Es), lam, gammas
 
 
+def euler_run(model, gammas, ds, n_steps, mode=C_INVERSE):
+    """n_steps with the first-order integrator of Eq. (RKstep) in place of the
+    orthogonal step; returns (energies, lambda, gammas)."""
+    Es = []
+    lam = None
+    for _ in range(n_steps):
+        E, lam, G, h = energy(model, gammas)
+        dGs = eom(model, gammas, G, h, E, lam, mode)
+        gammas = [euler_step(Gm, dG, ds) for Gm, dG in zip(gammas, dGs)]
+        Es.append(E)
+    return np.array(Es), lam, gammas
+
+
+# ---------------------------------------------------------------------------
+# Rank growth (Sec. III C)
+# ---------------------------------------------------------------------------
+
+
+def add_state(gammas, K, src):
+    """Append the state Q Gamma_src Q^T, Q = exp(K) with K antisymmetric (a
+    special orthogonal Q; the paper draws it at random close to the identity
+    and applies it to a state of high amplitude)."""
+    Q = scipy.linalg.expm(K)
+    g = Q @ gammas[src] @ Q.T
+    return list(gammas) + [0.5 * (g - g.T)]
+
+
+def grow(model, gammas, ds, steps_per_rank, Ks, mode=C_INVERSE):
+    """The paper's schedule: evolve steps_per_rank steps, then add one state
+    copied (through exp(K_j)) from the state of largest |lambda_mu| at the last
+    amplitude solve, once per K_j; finish with steps_per_rank steps at the final
+    rank.  Returns (energies of every step, final gammas)."""
+    Es = []
+    for K in list(Ks) + [None]:
+        E, lam, gammas = run(model, gammas, ds, steps_per_rank, mode)
+        Es.extend(E)
+        if K is None:
+            break
+        gammas = add_state(gammas, K, int(np.argmax(np.abs(lam))))
+    return np.array(Es), gammas
+
+
 # ---------------------------------------------------------------------------
 # Observables: spin-spin correlators (Eq. Cr, Eq. K2CK)
 # ---------------------------------------------------------------------------

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libsgs.so")
 
 SGS_FP64, SGS_MIXED_TF32, SGS_MIXED_BF16, SGS_FP32_3XTF32 = 0, 1, 2, 3
 SGS_C_INVERSE, SGS_C_PHASE = 0, 1
+SGS_INTEGRATOR_EXP, SGS_INTEGRATOR_EULER = 0, 1
 SGS_CORR_SPIN_SPIN, SGS_CORR_TWO_CHANNEL_K, SGS_CORR_RENYI2 = 0, 1, 2
 STATUS = {0: "SGS_OK", 1: "SGS_EINVAL", 2: "SGS_ENOMEM", 3: "SGS_ESINGULAR", 4: "SGS_ENOTCONV",
           5: "SGS_ETIMEOUT", 6: "SGS_ECUDA"}
@@ -40,7 +41,8 @@ class _Model(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int), ("dtau", ctypes.c_double), ("precision", ctypes.c_int),
                 ("cmode", ctypes.c_int), ("parity", ctypes.c_int), ("gamma0", ctypes.POINTER(ctypes.c_double)),
-                ("lambda0", ctypes.POINTER(ctypes.c_double)), ("stream", ctypes.c_void_p)]
+                ("lambda0", ctypes.POINTER(ctypes.c_double)), ("stream", ctypes.c_void_p),
+                ("integrator", ctypes.c_int)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -59,6 +61,7 @@ SIGNATURES = {
     "sgs_admit": (ctypes.c_int, [_ctxp, ctypes.POINTER(_Model), ctypes.POINTER(_Options), ctypes.POINTER(ctypes.c_int)]),
     "sgs_retire": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_bytes_in_use": (ctypes.c_size_t, [_ctxp]),
+    "sgs_add_state": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, ctypes.c_int]),
     "sgs_set_graphs": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_energy": (ctypes.c_int, [_ctxp, _dp]),
     "sgs_correlator": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _dp]),
@@ -191,7 +194,7 @@ class Solver:
     while others are live: continuous batching."""
 
     def __init__(self, models=(), gamma0=(), lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE,
-                 parity=1, stream=None, hbm_budget=0):
+                 parity=1, stream=None, hbm_budget=0, integrator=SGS_INTEGRATOR_EXP):
         if isinstance(models, MajoranaModel):
             models, gamma0, lambda0 = [models], [gamma0], [lambda0]
         models = list(models)
@@ -215,10 +218,10 @@ class Solver:
         self.shapes = []
         self.live = []
         self._keep = {}
-        for i, m, g, l0, dt, pr, cm, pa in zip(range(k), models, gamma0, lambda0, per(dtau), per(precision),
-                                               per(cmode), per(parity)):
+        for i, m, g, l0, dt, pr, cm, pa, it in zip(range(k), models, gamma0, lambda0, per(dtau), per(precision),
+                                                   per(cmode), per(parity), per(integrator)):
             try:
-                self.admit(m, g, l0, dt, pr, cm, pa)
+                self.admit(m, g, l0, dt, pr, cm, pa, it)
             except SGSError:
                 self.close()
                 raise
@@ -227,7 +230,8 @@ class Solver:
     def n_instances(self):
         return len(self.shapes)
 
-    def admit(self, model, gamma0, lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE, parity=1):
+    def admit(self, model, gamma0, lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE, parity=1,
+              integrator=SGS_INTEGRATOR_EXP):
         """Add one problem; returns its slot.  Raises SGSError(SGS_ENOMEM) if it
         does not fit the HBM budget (nothing is allocated then)."""
         _check_slot_args(model, gamma0, parity)
@@ -238,7 +242,7 @@ class Solver:
             lam = np.ascontiguousarray(np.stack([np.real(lambda0), np.imag(lambda0)], -1), dtype=np.float64)
         mod = _Model(model.n_modes, _ptr(model.A), len(model.quartic_val), _ptr(model.quartic_idx, _ip),
                      _ptr(model.quartic_val), model.e_const)
-        opt = _Options(M, dtau, precision, cmode, parity, _ptr(g), _ptr(lam), None)
+        opt = _Options(M, dtau, precision, cmode, parity, _ptr(g), _ptr(lam), None, integrator)
         slot = ctypes.c_int(-1)
         st = _lib.sgs_admit(self._ctx, ctypes.byref(mod), ctypes.byref(opt), ctypes.byref(slot))
         if st != 0:
@@ -253,6 +257,16 @@ class Solver:
 
     def bytes_in_use(self):
         return int(_lib.sgs_bytes_in_use(self._ctx))
+
+    def add_state(self, K, src=-1, slot=0):
+        """Rank growth (Sec. III C): append Q Gamma_src Q^T, Q = exp(K), to a
+        slot (K antisymmetric [n, n]; src -1: the state of largest amplitude)."""
+        M, n = self.shapes[slot]
+        k = np.ascontiguousarray(K, dtype=np.float64)
+        if k.shape != (n, n):
+            raise SGSError(1, f"K has shape {k.shape}, expected ({n}, {n})")
+        self._check(_lib.sgs_add_state(self._ctx, slot, _ptr(k), int(src)))
+        self.shapes[slot] = (M + 1, n)
 
     def _check(self, st):
         if st != 0:

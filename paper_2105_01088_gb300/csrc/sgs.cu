@@ -55,9 +55,11 @@ struct Instance {
     cudaEvent_t join = nullptr;
     int N = 0, n = 0, M = 0, P = 0, Ppf = 0, nimp = 0, nq = 0, a_nnz = 0;
     double dtau = 0.0, e_const = 0.0;
-    int prec = 0, cmode = 0, parity = 1;
+    int prec = 0, cmode = 0, parity = 1, integrator = 0;
     int gj_b = 32, pf_bs = 16;
     std::vector<int> h_pa, h_pb;
+    std::vector<double> hA, hq_val;     // host copy of the model: rank growth rebuilds the instance
+    std::vector<int> hq_idx;
 
     double *gamma = nullptr, *dgamma = nullptr;
     int *pa = nullptr, *pb = nullptr, *pf_pair = nullptr, *pair_pf = nullptr, *pair_index = nullptr;
@@ -286,7 +288,11 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.prec = o.precision;
     I.cmode = o.cmode;
     I.parity = o.parity;
+    I.integrator = o.integrator;
     I.e_const = m.e_const;
+    I.hA.assign(m.A, m.A + (size_t)n * n);
+    I.hq_idx.assign(m.quartic_idx, m.quartic_idx + (m.n_quartic > 0 ? 4 * m.n_quartic : 0));
+    I.hq_val.assign(m.quartic_val, m.quartic_val + (m.n_quartic > 0 ? m.n_quartic : 0));
     I.gj_b = (n <= 640) ? 32 : 16;
     if (I.gj_b > n) I.gj_b = n;
     I.pf_bs = 16;
@@ -388,8 +394,11 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         if (!p) { c->err = "device allocation failed"; return SGS_ENOMEM; }
 
     cudaStream_t st = c->stream;
-    CUDA_TRY(c, cudaMemcpyAsync(I.gamma, o.gamma0, M * nn * sizeof(double), cudaMemcpyHostToDevice, st));
+    // gamma0 == nullptr: the caller fills the states on the device (rank growth)
+    if (o.gamma0)
+        CUDA_TRY(c, cudaMemcpyAsync(I.gamma, o.gamma0, M * nn * sizeof(double), cudaMemcpyHostToDevice, st));
     CUDA_TRY(c, cudaMemsetAsync(I.dgamma, 0, M * nn * sizeof(double), st));
+    CUDA_TRY(c, cudaMemsetAsync(I.sq, 0, M * sizeof(int), st));
     if (P > 0) {
         CUDA_TRY(c, cudaMemcpyAsync(I.pa, pa.data(), P * sizeof(int), cudaMemcpyHostToDevice, st));
         CUDA_TRY(c, cudaMemcpyAsync(I.pb, pb.data(), P * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -750,58 +759,92 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// exp(X) for the first `batch` states (App. A): X in s1 and the first Horner factor in s2, as
+// exp_prepare_kernel leaves them; the Horner products, then the squarings each state needs (states
+// with fewer pass their matrix through).  *cur_out <- the s buffer that holds R.
+cudaError_t exp_products(sgs_ctx* c, Instance& I, int batch, cudaStream_t st, int* cur_out) {
+    const int n = I.n;
+    const double n3 = (double)n * n * n;
+    cudaError_t e;
+    // Horner: P <- I + (X 2^-s / j) P, j = degree-1 .. 1
+    int cur = 2;
+    for (int j = EXP_TAYLOR_DEGREE - 1; j >= 1; j--) {
+        int nxt = (cur == 2) ? 3 : 2;
+        GemmBatch g = gb_basic(n, n, n, I.p_s[1], n, I.p_s[cur], n, I.p_s[nxt], n, batch);
+        g.alpha = 1.0 / j; g.alpha_b = I.scale; g.diag = 1.0;
+        if ((e = gemm(c, g, st, 2.0 * n3 * batch)) != cudaSuccess) return e;
+        cur = nxt;
+    }
+    for (int j = 0; j < EXP_MAX_SQUARINGS; j++) {
+        int nxt = (cur == 2) ? 3 : 2;
+        GemmBatch g = gb_basic(n, n, n, I.p_s[cur], n, I.p_s[cur], n, I.p_s[nxt], n, batch);
+        g.active_flag = I.sq; g.active_cmp = j;
+        g.Cin = (const double* const*)I.p_s[cur]; g.ldcin = n; g.beta = 0.0;
+        if ((e = gemm(c, g, st, -1.0)) != cudaSuccess) return e;
+        cur = nxt;
+    }
+    *cur_out = cur;
+    return cudaSuccess;
+}
+
+// Canonical-form renormalisation (App. A, Eq. CM-normal-form with every lambda_j = 1): the polar
+// factor of the matrices in s4 by `iters` Newton-Schulz steps X <- 1.5 X + 0.5 X (X X); the result
+// goes to gamma.
+cudaError_t polar_pass(sgs_ctx* c, Instance& I, int iters, cudaStream_t st) {
+    const int n = I.n, M = I.M;
+    const size_t nn = (size_t)n * n;
+    const double n3 = (double)n * n * n;
+    cudaError_t e;
+    double** src = I.p_s[4];
+    double** dst = I.p_gamma;
+    for (int it = 0; it < iters; it++) {
+        GemmBatch g = gb_basic(n, n, n, src, n, src, n, I.p_s[0], n, M);
+        if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;     // X X: symmetric, half counted
+        g = gb_basic(n, n, n, src, n, I.p_s[0], n, dst, n, M);
+        g.alpha = 0.5; g.Cin = (const double* const*)src; g.ldcin = n; g.beta = 1.5; g.mode = GEMM_SKEW;
+        if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
+        std::swap(src, dst);
+    }
+    if (src == I.p_s[4]) {     // an even number of iterations ends in s4
+        copy_kernel<<<grid_chunks(M * nn, 256, 4096), 256, 0, st>>>(I.s[4], I.gamma, M * nn);
+        counted();
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t update_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     const int n = I.n, M = I.M;
     const size_t nn = (size_t)n * n;
     const double n3 = (double)n * n * n;
     cudaError_t e;
     c->stage(SGS_STAGE_UPDATE);
-    // Gamma dGamma, 9 Horner products, R Gamma, (R Gamma) R^T (antisymmetric),
-    // two Newton-Schulz iterations; squarings are added when profiles are read
-    c->stage_flops[SGS_STAGE_UPDATE] += (2.0 + 18.0 + 2.0 + 1.0 + 6.0) * n3 * M;
+    if (I.integrator == SGS_INTEGRATOR_EULER) {
+        // Eq. RKstep: Gamma + ds dGamma -> s4, then the polar factor
+        c->stage_flops[SGS_STAGE_UPDATE] += 2.0 * EULER_NS_ITERS * n3 * M;
+        axpy_kernel<<<grid_chunks(M * nn, 256, 4096), 256, 0, st>>>(I.gamma, I.dgamma, I.dtau, I.s[4], M * nn);
+        counted();
+        if ((e = polar_pass(c, I, EULER_NS_ITERS, st)) != cudaSuccess) return e;
+        I.steps_since_profile++;
+        return cudaGetLastError();
+    }
+    // Gamma dGamma, 9 Horner products, R Gamma, (R Gamma) R^T (antisymmetric), two
+    // Newton-Schulz iterations (X X and X (X X), half each); squarings are added when
+    // profiles are read
+    c->stage_flops[SGS_STAGE_UPDATE] += (2.0 + 18.0 + 2.0 + 1.0 + 4.0) * n3 * M;
     // Y = Gamma dGamma -> s0 ; X -> s1 ; P -> s2
     GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_dgamma, n, I.p_s[0], n, M);
     if ((e = gemm(c, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
     exp_prepare_kernel<<<M, 1024, 0, st>>>(I.s[0], I.s[1], I.s[2], n, I.dtau, I.sq, I.scale, I.err);
     counted();
-    // Horner: P <- I + (X 2^-s / j) P, j = degree-1 .. 1
     int cur = 2;
-    for (int j = EXP_TAYLOR_DEGREE - 1; j >= 1; j--) {
-        int nxt = (cur == 2) ? 3 : 2;
-        g = gb_basic(n, n, n, I.p_s[1], n, I.p_s[cur], n, I.p_s[nxt], n, M);
-        g.alpha = 1.0 / j; g.alpha_b = I.scale; g.diag = 1.0;
-        if ((e = gemm(c, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
-        cur = nxt;
-    }
-    // squarings (states with fewer squarings pass their matrix through)
-    for (int j = 0; j < EXP_MAX_SQUARINGS; j++) {
-        int nxt = (cur == 2) ? 3 : 2;
-        g = gb_basic(n, n, n, I.p_s[cur], n, I.p_s[cur], n, I.p_s[nxt], n, M);
-        g.active_flag = I.sq; g.active_cmp = j;
-        g.Cin = (const double* const*)I.p_s[cur]; g.ldcin = n; g.beta = 0.0;
-        if ((e = gemm(c, g, st, -1.0)) != cudaSuccess) return e;
-        cur = nxt;
-    }
+    if ((e = exp_products(c, I, M, st, &cur)) != cudaSuccess) return e;
     // T = R Gamma -> s0 ; Gamma' = T R^T -> s4
     g = gb_basic(n, n, n, I.p_s[cur], n, I.p_gamma, n, I.p_s[0], n, M);
     if ((e = gemm(c, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
     g = gb_basic(n, n, n, I.p_s[0], n, I.p_s[cur], n, I.p_s[4], n, M);
     g.transB = 1; g.mode = GEMM_SKEW;
     if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
-    // Newton-Schulz polar factor: X <- 1.5 X + 0.5 X (X X), twice
-    double** src = I.p_s[4];
-    double** dst = I.p_gamma;
-    for (int it = 0; it < 2; it++) {
-        g = gb_basic(n, n, n, src, n, src, n, I.p_s[0], n, M);
-        if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
-        g = gb_basic(n, n, n, src, n, I.p_s[0], n, dst, n, M);
-        g.alpha = 0.5; g.Cin = (const double* const*)src; g.ldcin = n; g.beta = 1.5; g.mode = GEMM_SKEW;
-        if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
-        std::swap(src, dst);
-    }
-    // after two iterations the result is back in s4
-    copy_kernel<<<grid_chunks(M * nn, 256, 4096), 256, 0, st>>>(I.s[4], I.gamma, M * nn);
-    counted();
+    if ((e = polar_pass(c, I, 2, st)) != cudaSuccess) return e;
     I.steps_since_profile++;
     return cudaGetLastError();
 }
@@ -865,6 +908,7 @@ sgs_status check_args(const sgs_model& m, const sgs_options& o) {
     if (m.n_modes < 1 || !m.A || (m.n_quartic > 0 && (!m.quartic_idx || !m.quartic_val))) return SGS_EINVAL;
     if (o.rank < 1 || o.rank > SGS_MAX_RANK || (o.parity != 1 && o.parity != -1) || !o.gamma0) return SGS_EINVAL;
     if (o.precision < 0 || o.precision > 3 || (o.cmode != 0 && o.cmode != 1)) return SGS_EINVAL;
+    if (o.integrator != SGS_INTEGRATOR_EXP && o.integrator != SGS_INTEGRATOR_EULER) return SGS_EINVAL;
     return SGS_OK;
 }
 }  // namespace
@@ -927,6 +971,93 @@ sgs_status sgs_retire(sgs_ctx* c, int slot) {
 }
 
 size_t sgs_bytes_in_use(const sgs_ctx* c) { return c ? c->bytes_in_use : 0; }
+
+sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
+    if (!c || slot < 0 || slot >= (int)c->inst.size() || !c->inst[slot].live || !K) return SGS_EINVAL;
+    const int n = c->inst[slot].n, M = c->inst[slot].M;
+    if (M + 1 > SGS_MAX_RANK) { c->err = "the rank is already at its maximum"; return SGS_EINVAL; }
+    if (src < -1 || src >= M) { c->err = "src out of range"; return SGS_EINVAL; }
+    double fro = 0.0;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            const double v = K[(size_t)i * n + j];
+            if (!std::isfinite(v) || v != -K[(size_t)j * n + i]) { c->err = "K is not antisymmetric"; return SGS_EINVAL; }
+            fro += v * v;
+        }
+    if (std::sqrt(fro) > 8.0) { c->err = "||K||_F > 8"; return SGS_EINVAL; }
+    cudaStream_t st = c->stream;
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    Instance& I = c->inst[slot];
+    if (src < 0) {
+        std::vector<double> lam(2 * (size_t)M);
+        CUDA_TRY(c, cudaMemcpy(lam.data(), I.lam, 2 * M * sizeof(double), cudaMemcpyDeviceToHost));
+        double best = -1.0;
+        for (int mu = 0; mu < M; mu++) {
+            const double a = std::hypot(lam[2 * mu], lam[2 * mu + 1]);
+            if (a > best) { best = a; src = mu; }
+        }
+    }
+    const size_t need = instance_bytes(n, M + 1, I.prec, 16);
+    if (c->budget && c->bytes_in_use - I.bytes + need > c->budget) {
+        c->err = "over the HBM budget: " + std::to_string(c->bytes_in_use - I.bytes + need) + " > " +
+                 std::to_string(c->budget);
+        return SGS_ENOMEM;
+    }
+    // the grown instance: same model and options, rank M + 1, states filled on the device
+    Instance J;
+    sgs_model m{I.N, I.hA.data(), (int)I.hq_val.size(), I.hq_idx.data(), I.hq_val.data(), I.e_const};
+    sgs_options o{M + 1, I.dtau, I.prec, I.cmode, I.parity, nullptr, nullptr, nullptr, I.integrator};
+    c->owner = &J;
+    sgs_status s = setup_instance(c, J, m, o);
+    c->owner = nullptr;
+    const size_t nn = (size_t)n * n;
+    cudaError_t e = cudaSuccess;
+    if (s == SGS_OK) {
+        e = cudaMemcpyAsync(J.gamma, I.gamma, M * nn * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(J.lam, I.lam, 2 * M * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        // X = K: exp_prepare_kernel forms (ds/4)(Y - Y^T), which is K for Y = K and ds = 2
+        if (e == cudaSuccess) e = cudaMemcpyAsync(J.s[0], K, nn * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            exp_prepare_kernel<<<1, 1024, 0, st>>>(J.s[0], J.s[1], J.s[2], n, 2.0, J.sq, J.scale, J.err);
+            counted();
+            e = cudaGetLastError();
+        }
+        int cur = 2;
+        if (e == cudaSuccess) e = exp_products(c, J, 1, st, &cur);
+        // Q Gamma_src -> s0 ; (Q Gamma_src) Q^T -> Gamma_M
+        if (e == cudaSuccess) {
+            GemmBatch g = gb_basic(n, n, n, J.p_s[cur], n, J.p_gamma + src, n, J.p_s[0], n, 1);
+            e = gemm(c, g, st, -1.0);
+        }
+        if (e == cudaSuccess) {
+            GemmBatch g = gb_basic(n, n, n, J.p_s[0], n, J.p_s[cur], n, J.p_gamma + M, n, 1);
+            g.transB = 1; g.mode = GEMM_SKEW;
+            e = gemm(c, g, st, -1.0);
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(J.sq, 0, (M + 1) * sizeof(int), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        int derr = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&derr, J.err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            c->err = std::string("rank growth: ") + cudaGetErrorString(e);
+            s = SGS_ECUDA;
+        } else if (derr) {
+            c->err = "rank growth: exponential out of range";
+            s = SGS_ENOTCONV;
+        }
+    }
+    if (s != SGS_OK) {
+        cudaStreamSynchronize(st);
+        c->release_instance(J);
+        return s;
+    }
+    J.st = I.st; J.join = I.join;        // the slot keeps its branch stream and event
+    I.st = nullptr; I.join = nullptr;
+    c->release_instance(I);
+    c->inst[slot] = std::move(J);
+    c->drop_graph();
+    return SGS_OK;
+}
 
 sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_instances, sgs_ctx** out) {
     if (!out) return SGS_EINVAL;

@@ -15,6 +15,8 @@ namespace sgs {
 #define EXP_TAYLOR_DEGREE 10
 #define EXP_MAX_SQUARINGS 14
 #define EXP_THETA 0.125
+#define EULER_NS_ITERS 6       // Newton-Schulz steps after an Euler step: singular values 1 + d with
+                               // |d| <= 0.3 reach 1 to rounding (d -> -1.5 d^2 per step)
 
 // X = (ds/4)(Y - Y^T) with Y = Gamma dGamma (so [Gamma, dGamma] = Y - Y^T),
 // its Frobenius norm -> squarings s, 2^-s, and the first Horner factor
@@ -49,6 +51,12 @@ __global__ void __launch_bounds__(1024) exp_prepare_kernel(const double* Y, doub
         int k = (int)(e / n), l = (int)(e % n);
         pp[e] = f * x[e] + (k == l ? 1.0 : 0.0);
     }
+}
+
+// out = x + a y (the Euler step of Eq. RKstep)
+__global__ void axpy_kernel(const double* x, const double* y, double a, double* out, size_t count) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = x[e] + a * y[e];
 }
 
 __global__ void copy_kernel(const double* src, double* dst, size_t count) {

@@ -56,6 +56,16 @@ def clustered_pure_gammas(n_modes: int, M: int, rng: np.random.Generator, parity
     return np.ascontiguousarray(np.stack(out))
 
 
+def random_generator(n: int, norm: float, rng: np.random.Generator) -> np.ndarray:
+    """A random antisymmetric n x n matrix K with ||K||_F = norm (exactly
+    antisymmetric: K = X - X^T, scaled), so that exp(K) is a random special
+    orthogonal matrix with ||exp(K) - 1||_F ~ norm."""
+    X = rng.standard_normal((n, n))
+    K = X - X.T
+    K *= norm / np.linalg.norm(K)
+    return 0.5 * (K - K.T)
+
+
 def random_amplitudes(M: int, rng: np.random.Generator) -> np.ndarray:
     return np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, size=M))
 
@@ -113,14 +123,16 @@ TWO_CHANNEL = Workload("two_channel_L201_M64",
                        dtau=0.05, n_steps=1000, seed=3, parity=-1)
 
 
-def batched_workloads(n_instances: int = 256, seed: int = 4, dtau: float = 0.05):
-    """Uneven instances: bath length L ~ U{16..256} per spin, rank M in
-    {8, 16, 32}, U ~ U[0, 8], eps_d = -U/2, V ~ U[0.2, 1.0]."""
+def batched_workloads(n_instances: int = 256, seed: int = 4, dtau: float = 0.05, n_bath=(16, 256),
+                      ranks=(8, 16, 32)):
+    """Uneven instances: bath length L ~ U{n_bath} per spin (default 16..256),
+    rank M from ``ranks`` (default {8, 16, 32}), U ~ U[0, 8], eps_d = -U/2,
+    V ~ U[0.2, 1.0]."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n_instances):
-        L = int(rng.integers(16, 257))
-        M = int(rng.choice([8, 16, 32]))
+        L = int(rng.integers(n_bath[0], n_bath[1] + 1))
+        M = int(rng.choice(list(ranks)))
         U = float(rng.uniform(0.0, 8.0))
         V = float(rng.uniform(0.2, 1.0))
         # L bath sites plus the impurity; half filling puts L + 1 electrons

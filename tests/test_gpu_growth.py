@@ -1,0 +1,117 @@
+"""Rank growth (Sec. III C) and the Euler integrator (Eq. RKstep) on the GPU
+against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import sgs_inputs as inp
+from oracle import sgs_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2105_01088_gb300 as p
+    return p
+
+
+def _model(pkg, p):
+    return pkg.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels)
+
+
+def test_add_state_matches_oracle(pkg):
+    import torch
+    p = inp.AndersonParams(n_bath=20, U=3.0, eps_d=-1.5, V=0.7)
+    rng = np.random.default_rng(31)
+    g = inp.clustered_pure_gammas(p.n_modes, 3, rng, 1, spread=1.0)
+    lam = inp.random_amplitudes(3, rng)
+    s = pkg.Solver(_model(pkg, p), g, lam, stream=torch.cuda.Stream())
+    s.step(3)
+    g3, lam3 = s.get_state()
+    K = inp.random_generator(2 * p.n_modes, 0.3, rng)
+    s.add_state(K)                                   # src = state of largest amplitude
+    g4, lam4 = s.get_state()
+    ref = orc.add_state(list(g3), K, int(np.argmax(np.abs(lam3))))
+    assert g4.shape == (4, 2 * p.n_modes, 2 * p.n_modes)
+    assert np.array_equal(g4[:3], g3) and np.array_equal(lam4[:3], lam3) and lam4[3] == 0
+    assert np.abs(g4[3] - ref[3]).max() < 1e-12
+    s.add_state(-K, src=0)
+    g5, _ = s.get_state()
+    assert np.abs(g5[4] - orc.add_state(list(g4), -K, 0)[4]).max() < 1e-12
+    # the grown slot steps like the oracle (graph re-captured for the new rank)
+    E = s.step(2)[0]
+    Eo, _, _ = orc.run(orc.anderson_model(p.n_bath, p.U, p.eps_d, p.V), list(g5), 0.05, 2)
+    assert np.abs(E - Eo).max() <= 1e-10 * np.abs(Eo).max()
+    s.close()
+
+
+def test_growth_schedule_matches_oracle(pkg):
+    """One state added every 60 steps from rank 1 to rank 6 (4 sites, U = 4):
+    the GPU energies follow the oracle's through the whole schedule and end
+    within 3e-4 of exact diagonalisation (-5.0968247393, the oracle pin's
+    value)."""
+    import torch
+    p = inp.AndersonParams(n_bath=3, U=4.0, eps_d=-2.0, V=0.5)
+    g, _ = inp.initial_state(p.n_modes, 1, 3, 1)
+    rng = np.random.default_rng(0)
+    Ks = [inp.random_generator(2 * p.n_modes, 0.1, rng) for _ in range(5)]
+    s = pkg.Solver(_model(pkg, p), g, None, dtau=0.1, stream=torch.cuda.Stream())
+    Es = []
+    for K in Ks + [None]:
+        Es.extend(s.step(60)[0])
+        if K is not None:
+            s.add_state(K)
+    s.close()
+    Es = np.array(Es)
+    Eo, _ = orc.grow(orc.anderson_model(p.n_bath, p.U, p.eps_d, p.V), list(g), 0.1, 60, Ks)
+    assert np.abs(Es - Eo).max() <= 1e-8 * np.abs(Eo).max()
+    E_ed = -5.0968247393
+    assert 0 < (Es[-1] - E_ed) / abs(E_ed) < 3e-4
+
+
+def test_euler_integrator_matches_oracle(pkg):
+    import torch
+    p = inp.AndersonParams(n_bath=20, U=3.0, eps_d=-1.5, V=0.7)
+    rng = np.random.default_rng(37)
+    g = inp.clustered_pure_gammas(p.n_modes, 4, rng, 1, spread=1.0)
+    lam = inp.random_amplitudes(4, rng)
+    s = pkg.Solver(_model(pkg, p), g, lam, stream=torch.cuda.Stream(), integrator=pkg.SGS_INTEGRATOR_EULER)
+    E = s.step(5)[0]
+    g5, _ = s.get_state()
+    s.close()
+    Eo, _, go = orc.euler_run(orc.anderson_model(p.n_bath, p.U, p.eps_d, p.V), list(g), 0.05, 5)
+    assert np.abs(E - Eo).max() <= 1e-10 * np.abs(Eo).max()
+    assert np.abs(g5 - np.array(go)).max() < 1e-9
+    assert np.abs(np.einsum("mij,mjk->mik", g5, g5) + np.eye(g5.shape[1])).max() < 1e-12
+
+
+def test_add_state_argument_checks(pkg):
+    p = inp.AndersonParams(n_bath=7, U=2.0, eps_d=-1.0, V=0.5)
+    g, lam = inp.initial_state(p.n_modes, 2, 5, 1)
+    n = 2 * p.n_modes
+    s = pkg.Solver(_model(pkg, p), g, lam)
+    rng = np.random.default_rng(3)
+    K = inp.random_generator(n, 0.2, rng)
+    bad = K.copy()
+    bad[0, 1] += 1e-3                                  # not antisymmetric
+    for args in ((bad, -1), (K, 2), (K, -2), (10.0 * K / np.linalg.norm(K), -1)):
+        with pytest.raises(pkg.SGSError) as e:
+            s.add_state(*args)
+        assert e.value.status == 1
+    with pytest.raises(pkg.SGSError):
+        s.add_state(K[:-1, :-1])
+    assert s.get_state()[0].shape == (2, n, n)         # unchanged after the errors
+    s.close()
+    # growth is checked against the HBM budget (pair buffers grow from 6 to 10 pairs)
+    q = inp.AndersonParams(n_bath=40, U=2.0, eps_d=-1.0, V=0.5)
+    g4, lam4 = inp.initial_state(q.n_modes, 4, 6, 1)
+    one = pkg.Solver(_model(pkg, q), g4, lam4)
+    b = one.bytes_in_use()
+    one.close()
+    tight = pkg.Solver(hbm_budget=int(1.2 * b))
+    k = tight.admit(_model(pkg, q), g4, lam4)
+    with pytest.raises(pkg.SGSError) as e:
+        tight.add_state(inp.random_generator(2 * q.n_modes, 0.2, rng), slot=k)
+    assert e.value.status == 2
+    assert tight.get_state(k)[0].shape[0] == 4
+    tight.close()

@@ -237,6 +237,77 @@ def test_purify_recovers_canonical_form():
     assert np.abs(orc.purify(clean) - clean).max() < 1e-14
 
 
+def test_euler_step_first_order_and_pure():
+    """Eq. (RKstep) with the canonical-form renormalisation of App. A: pure, and
+    within O(ds^3) of the orthogonal step (for a tangent dGamma both expand to
+    Gamma + ds dGamma + (ds^2/2) Gamma dGamma^2)."""
+    model = orc.anderson_model(2, 2.0, -1.0, 0.5)
+    rng = _rng(63)
+    gammas = [inp.random_pure_gamma(model.N, rng) for _ in range(3)]
+    E, lam, G, h = orc.energy(model, gammas)
+    dG = orc.eom(model, gammas, G, h, E, lam)
+    errs = []
+    for ds in (1e-2, 5e-3):
+        g1 = orc.euler_step(gammas[2], dG[2], ds)
+        assert np.abs(g1 @ g1 + np.eye(model.n)).max() < 1e-13
+        errs.append(np.abs(g1 - orc.orthogonal_step(gammas[2], dG[2], ds)).max())
+    assert 7.0 < errs[0] / errs[1] < 9.0
+    Es, _, _ = orc.euler_run(model, gammas, 0.02, 20)
+    assert np.all(np.diff(Es) <= 1e-12)
+
+
+# ---------------------------------------------------------------- rank growth (Sec. III C)
+
+def test_added_state_is_the_gaussian_unitary_image():
+    """Q Gamma Q^T with Q = exp(K) is the covariance of U|phi>, U = exp((1/4)
+    sum K_kl c_k c_l) the Gaussian unitary of K (Fock brute force); it keeps
+    the parity (det Q = 1) and the purity."""
+    rng = _rng(101)
+    N = 4
+    g = inp.random_pure_gamma(N, rng, -1)
+    K = inp.random_generator(2 * N, 0.4, rng)
+    new = orc.add_state([g], K, 0)[1]
+    c = fock.majoranas(N)
+    gen = sum(K[k, l] * (c[k] @ c[l]) for k in range(2 * N) for l in range(2 * N))
+    import scipy.linalg
+    phi = scipy.linalg.expm(0.25 * gen.toarray()) @ fock.gaussian_vector(g)
+    assert np.abs(fock.covariance_of(phi) - new).max() < 1e-12
+    assert abs(orc.pfaffian(new) - orc.pfaffian(g)) < 1e-12
+    assert np.abs(new @ new + np.eye(2 * N)).max() < 1e-13
+
+
+def test_added_state_never_raises_the_energy():
+    """With optimal amplitudes the enlarged ansatz contains the old one, so the
+    energy cannot rise; a copy with K = 0 makes G singular and the canonical
+    orthogonalisation drops it (energy unchanged)."""
+    model = orc.anderson_model(3, 4.0, -2.0, 0.5)
+    rng = _rng(103)
+    gammas = [inp.random_pure_gamma(model.N, rng) for _ in range(2)]
+    E0 = orc.energy(model, gammas)[0]
+    for src in (0, 1):
+        E1 = orc.energy(model, orc.add_state(gammas, inp.random_generator(model.n, 0.2, rng), src))[0]
+        assert E1 <= E0 + 1e-12
+    E2 = orc.energy(model, orc.add_state(gammas, np.zeros((model.n, model.n)), 0))[0]
+    assert abs(E2 - E0) < 1e-12 * abs(E0)
+
+
+def test_rank_growth_approaches_exact_ground_state():
+    """The paper's route to the ground state (Sec. III C): from a single
+    Gaussian, one state added every 60 steps up to rank 6; the energy stays above
+    the exact ground state (variational) and ends within 3e-4 of it (4 sites,
+    U = 4)."""
+    model = orc.anderson_model(3, 4.0, -2.0, 0.5)
+    E_ed = fock.ground_energy(fock.hamiltonian_anderson(3, 4.0, -2.0, 0.5))
+    g, _ = inp.initial_state(model.N, 1, 3, 1)
+    rng = _rng(0)
+    Ks = [inp.random_generator(model.n, 0.1, rng) for _ in range(5)]
+    Es, gs = orc.grow(model, list(g), 0.1, 60, Ks)
+    assert len(gs) == 6 and len(Es) == 360
+    assert np.all(Es >= E_ed - 1e-12)
+    assert (Es[-1] - E_ed) / abs(E_ed) < 3e-4
+    assert (Es[59] - E_ed) / abs(E_ed) > 1e-2          # the single Gaussian is far off
+
+
 # ---------------------------------------------------------------- whole-step ground truths
 
 def test_energy_descends():
