@@ -173,6 +173,16 @@ typedef enum {
 sgs_status sgs_correlator(sgs_ctx* ctx, int instance, sgs_corr_kind kind, const int* sites, int n_sites,
                           double* out);
 
+/* Hamiltonian variance (Eq. residual, Sec. IV A): delta_H^2 = <psi|H^2|psi>
+ * - <psi|H|psi>^2 of the current states of one instance with optimal
+ * amplitudes normalised to <psi|psi> = 1 (a pair pass runs first; the states
+ * are not changed).  <H^2> comes from Wick's theorem on each pair's
+ * transition matrix in O(n^2) per pair (the quadratic part of H must be
+ * sparse for that bound; at most 64 distinct quartic monomials).  The paper
+ * extrapolates the energy linearly in delta_H^2 -> 0.  energy, variance: host
+ * doubles, either may be NULL.  Errors: SGS_EINVAL, SGS_ESINGULAR, SGS_ECUDA. */
+sgs_status sgs_variance(sgs_ctx* ctx, int instance, double* energy, double* variance);
+
 void sgs_free(sgs_ctx* ctx);
 const char* sgs_last_error(const sgs_ctx* ctx);
 

@@ -455,6 +455,106 @@ def grow(model, gammas, ds, steps_per_rank, Ks, mode=C_INVERSE):
 
 
 # ---------------------------------------------------------------------------
+# Hamiltonian variance (Eq. residual) and the energy extrapolation (Sec. IV A)
+# ---------------------------------------------------------------------------
+#
+# H = e + H2 + H4 with H2 = i sum_kl A_kl c_k c_l and H4 = sum_m v_m c_m0 c_m1 c_m2 c_m3
+# (monomials with increasing indices).  In the transition "state" of a pair the
+# ordered contraction of c_x (left) with c_y (right) is g_xy = delta_xy + i Delta_xy,
+# and by Wick's theorem a product of Majoranas (repeats allowed) is the Pfaffian
+# of the ordered contractions.  Summing the Wick terms of H^2 over the quadratic
+# indices in matrix form:
+#   <H2>      = T = Tr(A Delta)
+#   <H2 H2>   = T^2 - 2 tr(A^2) - 2 tr(A Delta A Delta)
+#   <H2 H4_m> = T Pf4_m - i dPf4_m[C],   C  = B - B^T,   B  = g^T A g
+#   <H4_m H2> = T Pf4_m - i dPf4_m[C'],  C' = B' - B'^T, B' = g A g^T
+#   <H4_m H4_m'> = Pf8 of the ordered contractions of (m, m')
+# with Pf4_m the Pfaffian of g on the monomial's indices and dPf4_m[C] its
+# derivative in the direction C (C on one pair of indices, g on the other).
+
+
+def canonical_quartic(model):
+    """The quartic part as monomials with increasing indices: coefficient of
+    c_k c_l c_p c_q (k < l < p < q) = 24 U_klpq of the antisymmetric U."""
+    return [(idx, 24.0 * v) for idx, v in model.quartic if list(idx) == sorted(idx)]
+
+
+def _ordered_contractions(g, idx):
+    m = len(idx)
+    X = np.zeros((m, m), dtype=np.complex128)
+    for a in range(m):
+        for b in range(a + 1, m):
+            X[a, b] = g[idx[a], idx[b]]
+            X[b, a] = -X[a, b]
+    return X
+
+
+def _pf4(X):
+    return X[0, 1] * X[2, 3] - X[0, 2] * X[1, 3] + X[0, 3] * X[1, 2]
+
+
+def _dpf4(X, C):
+    return (C[0, 1] * X[2, 3] + X[0, 1] * C[2, 3] - C[0, 2] * X[1, 3] - X[0, 2] * C[1, 3]
+            + C[0, 3] * X[1, 2] + X[0, 3] * C[1, 2])
+
+
+def hamiltonian_square_density(model, Dlt):
+    """<H^2> in the transition state with matrix Dlt: <phi_a|H^2|phi_b> / G_ab
+    for Dlt = Delta^{b,a} (Gamma_a itself for a = b)."""
+    A = model.A
+    n = model.n
+    e = model.e_const
+    g = np.eye(n) + 1j * Dlt
+    T = np.trace(A @ Dlt)
+    X = A @ Dlt
+    h22 = T * T - 2.0 * np.trace(A @ A) - 2.0 * np.trace(X @ X)
+    B = g.T @ A @ g
+    Bp = g @ A @ g.T
+    C, Cp = B - B.T, Bp - Bp.T
+    mons = canonical_quartic(model)
+    Q = h24 = h42 = h44 = 0.0 + 0.0j
+    for idx, v in mons:
+        Xm = _ordered_contractions(g, idx)
+        p4 = _pf4(Xm)
+        Q += v * p4
+        h24 += v * (T * p4 - 1j * _dpf4(Xm, C[np.ix_(idx, idx)]))
+        h42 += v * (T * p4 - 1j * _dpf4(Xm, Cp[np.ix_(idx, idx)]))
+        for idx2, v2 in mons:
+            h44 += v * v2 * pfaffian(_ordered_contractions(g, list(idx) + list(idx2)))
+    return e * e + 2.0 * e * (T + Q) + h22 + h24 + h42 + h44
+
+
+def variance(model, gammas):
+    """delta_H^2 = <psi|H^2|psi> - <psi|H|psi>^2 (Eq. residual) for the optimal
+    amplitudes normalised to <psi|psi> = 1.  Returns (E, delta_H^2)."""
+    E, lam, G, h = energy(model, gammas)
+    M = len(gammas)
+    tot = 0.0 + 0.0j
+    for a in range(M):
+        for b in range(M):
+            D = gammas[a].astype(np.complex128) if a == b else transition_matrix(gammas[b], gammas[a])
+            tot += np.conj(lam[a]) * lam[b] * G[a, b] * hamiltonian_square_density(model, D)
+    return E, float(tot.real) - E * E
+
+
+def extrapolate_energy(energies, variances, var_max=2e-5):
+    """Linear fit E = E* + k delta_H^2 over the points with delta_H^2 < var_max
+    (Sec. IV A); returns (E*, standard error of the intercept)."""
+    E = np.asarray(energies, dtype=float)
+    v = np.asarray(variances, dtype=float)
+    keep = v < var_max
+    E, v = E[keep], v[keep]
+    if len(E) < 3:
+        raise ValueError("need at least three points below var_max")
+    Xd = np.stack([np.ones_like(v), v], 1)
+    coef, res, _, _ = np.linalg.lstsq(Xd, E, rcond=None)
+    r = E - Xd @ coef
+    s2 = float(r @ r) / (len(E) - 2)
+    cov = s2 * np.linalg.inv(Xd.T @ Xd)
+    return float(coef[0]), float(math.sqrt(cov[0, 0]))
+
+
+# ---------------------------------------------------------------------------
 # Observables: spin-spin correlators (Eq. Cr, Eq. K2CK)
 # ---------------------------------------------------------------------------
 #

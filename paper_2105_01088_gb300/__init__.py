@@ -65,6 +65,7 @@ SIGNATURES = {
     "sgs_set_graphs": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_energy": (ctypes.c_int, [_ctxp, _dp]),
     "sgs_correlator": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _dp]),
+    "sgs_variance": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, _dp]),
     "sgs_free": (None, [_ctxp]),
     "sgs_last_error": (ctypes.c_char_p, [_ctxp]),
     "sgs_get_state": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, _dp]),
@@ -293,6 +294,13 @@ class Solver:
         out = np.zeros(len(s))
         self._check(_lib.sgs_correlator(self._ctx, instance, kind, _ptr(s, _ip), len(s), _ptr(out)))
         return out
+
+    def variance(self, instance=0):
+        """(E, delta_H^2) of the current states (Eq. residual)."""
+        e = np.zeros(1)
+        v = np.zeros(1)
+        self._check(_lib.sgs_variance(self._ctx, instance, _ptr(e), _ptr(v)))
+        return float(e[0]), float(v[0])
 
     def get_state(self, instance=0, out=None):
         """(gamma [M, n, n], lambda [M]); ``out`` may be a C-contiguous float64

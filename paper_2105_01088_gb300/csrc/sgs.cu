@@ -33,6 +33,7 @@
 #include "gemm_tc.cuh"
 #include "corr.cuh"
 #include "renyi.cuh"
+#include "var.cuh"
 
 using namespace sgs;
 
@@ -67,6 +68,10 @@ struct Instance {
     double* a_val = nullptr;
     int* q_idx = nullptr;
     double* q_val = nullptr;
+    int nc = 0;                         // quartic part as monomials with increasing indices
+    int* c_idx = nullptr;
+    double* c_val = nullptr;
+    double trA2 = 0.0;                  // tr(A^2)
     int *imp = nullptr, *slot = nullptr;
 
     double *work = nullptr, *si = nullptr, *imd = nullptr, *wr = nullptr, *va = nullptr, *xa = nullptr;
@@ -337,6 +342,19 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     }
     std::sort(impv.begin(), impv.end());
     if ((int)impv.size() > SGS_MAX_IMP) { c->err = "more than 16 Majoranas in quartic terms"; return SGS_EINVAL; }
+    // canonical monomials: coefficient of c_k c_l c_p c_q (k < l < p < q) = 24 U_klpq
+    std::vector<int> cidx;
+    std::vector<double> cval;
+    for (auto& kv : U) {
+        const auto& k = kv.first;
+        if (kv.second != 0.0 && k[0] < k[1] && k[1] < k[2] && k[2] < k[3]) {
+            cidx.insert(cidx.end(), k.begin(), k.end());
+            cval.push_back(24.0 * kv.second);
+        }
+    }
+    I.nc = (int)cval.size();
+    I.trA2 = 0.0;
+    for (size_t e = 0; e < (size_t)n * n; e++) I.trA2 -= m.A[e] * m.A[e];   // tr(A^2) = -||A||_F^2
     I.nq = (int)qval.size();
     I.nimp = (int)impv.size();
     std::vector<int> slot(n, -1);
@@ -367,6 +385,7 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.a_rowptr = c->alloc<int>(n + 1); I.a_row = c->alloc<int>(std::max(I.a_nnz, 1));
     I.a_col = c->alloc<int>(std::max(I.a_nnz, 1)); I.a_val = c->alloc<double>(std::max(I.a_nnz, 1));
     I.q_idx = c->alloc<int>(std::max(4 * I.nq, 4)); I.q_val = c->alloc<double>(std::max(I.nq, 1));
+    I.c_idx = c->alloc<int>(std::max(4 * I.nc, 4)); I.c_val = c->alloc<double>(std::max(I.nc, 1));
     I.imp = c->alloc<int>(ni); I.slot = c->alloc<int>(n);
     I.work = c->alloc<double>(Pm * 2 * nn);
     I.si = c->alloc<double>(Pm * nn); I.imd = c->alloc<double>(Pm * nn);
@@ -417,6 +436,10 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         CUDA_TRY(c, cudaMemcpyAsync(I.q_idx, qidx.data(), 4 * I.nq * sizeof(int), cudaMemcpyHostToDevice, st));
         CUDA_TRY(c, cudaMemcpyAsync(I.q_val, qval.data(), I.nq * sizeof(double), cudaMemcpyHostToDevice, st));
         CUDA_TRY(c, cudaMemcpyAsync(I.imp, impv.data(), I.nimp * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    if (I.nc > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(I.c_idx, cidx.data(), 4 * I.nc * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(I.c_val, cval.data(), I.nc * sizeof(double), cudaMemcpyHostToDevice, st));
     }
     CUDA_TRY(c, cudaMemcpyAsync(I.slot, slot.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
     std::vector<double> lam0(2 * M, 0.0);
@@ -1262,6 +1285,38 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
     }
     c->err = "unknown correlator kind";
     return SGS_EINVAL;
+}
+
+sgs_status sgs_variance(sgs_ctx* c, int instance, double* energy, double* variance) {
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
+    Instance& I = c->inst[instance];
+    if (I.nc > VAR_MAX_MON) { c->err = "more quartic monomials than the variance kernel handles"; return SGS_EINVAL; }
+    CUDA_TRY(c, pair_pass(c, I, I.Ehist, c->stream));
+    c->stage(-1);
+    const size_t rows = (size_t)I.P + I.M;
+    const size_t need = rows + 8;
+    if (I.corr_cap < need) {
+        c->owner = &I;
+        I.corr_scratch = c->alloc<double>(need);
+        c->owner = nullptr;
+        if (!I.corr_scratch) { c->err = "device allocation failed"; return SGS_ENOMEM; }
+        I.corr_cap = need;
+    }
+    double* partial = I.corr_scratch;
+    double* dout = partial + rows;
+    VarArgs va{I.dev(), I.si, I.imd, I.Gm, I.lam, I.c_idx, I.c_val, I.nc, I.trA2, partial};
+    variance_kernel<<<(unsigned)rows, 256, 0, c->stream>>>(va);
+    column_sum_kernel<<<1, 32, 0, c->stream>>>(partial, (int)rows, 1, dout);
+    counted(); counted();
+    sgs_status st = check_device_error(c);
+    c->collect();
+    if (st != SGS_OK) return st;
+    double h[2];
+    CUDA_TRY(c, cudaMemcpy(h, dout, sizeof(double), cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(h + 1, I.Ehist, sizeof(double), cudaMemcpyDeviceToHost));
+    if (energy) *energy = h[1];
+    if (variance) *variance = h[0] - h[1] * h[1];
+    return SGS_OK;
 }
 
 void sgs_free(sgs_ctx* c) {

@@ -79,3 +79,35 @@ def test_observable_arguments_are_checked(pkg):
         s.correlator(pkg.SGS_CORR_SPIN_SPIN, [4])        # 4 sites: 0..3
     with pytest.raises(pkg.SGSError):
         s.correlator(pkg.SGS_CORR_RENYI2, [4])
+
+
+@pytest.mark.parametrize("case", [(20, 3.0, -1.5, 0.7, 5, 13, True, 1, 1), (15, 2.0, -1.0, 0.5, 4, 7, False, 1, 1),
+                                  (6, 8.0, -4.0, 0.6, 4, 9, True, -1, 2)])
+def test_variance(pkg, case):
+    """delta_H^2 (Eq. residual): <H^2> within 1e-10 relative of the oracle's,
+    so the variance within 1e-10 <H^2> absolute."""
+    nb, U, eps, V, M, seed, cl, par, nch = case
+    s, g, lam, G = _setup(pkg, nb, U, eps, V, M, seed, cl, parity=par, n_channels=nch)
+    E, var = s.variance()
+    Eo, vo = orc.variance(orc.anderson_model(nb, U, eps, V, n_channels=nch), list(g))
+    assert abs(E - Eo) <= TOL * abs(Eo)
+    assert abs(var - vo) <= TOL * (Eo * Eo + abs(vo)) and vo > 0
+
+
+def test_variance_several_monomials(pkg):
+    """A model with three density-density terms, two sharing Majoranas (repeated
+    indices in <H4 H4>), passed through the library's general model input."""
+    h = np.array([[0.3, 0.0, -1.0, 0.0, 0.0, 0.0], [0.0, -0.2, 0.0, -0.7, 0.0, 0.0],
+                  [-1.0, 0.0, 0.1, 0.0, -0.5, 0.0], [0.0, -0.7, 0.0, 0.4, 0.0, -0.6],
+                  [0.0, 0.0, -0.5, 0.0, -0.3, 0.0], [0.0, 0.0, 0.0, -0.6, 0.0, 0.2]])
+    model = orc.majorana_from_fermions(h, [(0, 1, 2.0), (2, 3, 1.5), (0, 3, 0.8)])
+    idx = np.array([k for k, _ in model.quartic], dtype=np.int32)
+    val = np.array([v for _, v in model.quartic])
+    m = pkg.MajoranaModel(model.A, idx, val, model.e_const)
+    rng = np.random.default_rng(17)
+    g = inp.clustered_pure_gammas(model.N, 3, rng, 1, spread=1.0)
+    s = pkg.Solver(m, g, None)
+    E, var = s.variance()
+    Eo, vo = orc.variance(model, list(g))
+    assert abs(E - Eo) <= TOL * abs(Eo)
+    assert abs(var - vo) <= TOL * (Eo * Eo + abs(vo))

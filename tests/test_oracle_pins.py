@@ -308,6 +308,82 @@ def test_rank_growth_approaches_exact_ground_state():
     assert (Es[59] - E_ed) / abs(E_ed) > 1e-2          # the single Gaussian is far off
 
 
+# ---------------------------------------------------------------- variance (Eq. residual)
+
+def _two_site_hubbard():
+    """Two spinful sites with hopping and three density-density terms, two of
+    which share Majoranas: H4 H4 then has repeated indices."""
+    h = np.array([[0.3, 0.0, -1.0, 0.0], [0.0, -0.2, 0.0, -0.7],
+                  [-1.0, 0.0, 0.1, 0.0], [0.0, -0.7, 0.0, 0.4]])
+    return orc.majorana_from_fermions(h, [(0, 1, 2.0), (2, 3, 1.5), (0, 3, 0.8)])
+
+
+@pytest.mark.parametrize("which", ["hubbard", "anderson2"])
+def test_hamiltonian_square_matches_fock(which):
+    model = _two_site_hubbard() if which == "hubbard" else orc.anderson_model(1, 3.0, -1.5, 0.6, n_channels=2)
+    assert len(orc.canonical_quartic(model)) == (3 if which == "hubbard" else 1)
+    H = _fock_operator(model).toarray()
+    H2 = H @ H
+    gammas, vecs = _states(model.N, 3, 111)
+    for a in range(3):
+        for b in range(3):
+            D = gammas[a].astype(np.complex128) if a == b else orc.transition_matrix(gammas[b], gammas[a])
+            x = orc.hamiltonian_square_density(model, D)
+            y = np.vdot(vecs[a], H2 @ vecs[b]) / np.vdot(vecs[a], vecs[b])
+            assert abs(x - y) < 1e-12 * max(1.0, abs(y)), (a, b)
+
+
+def test_variance_matches_fock():
+    model = orc.anderson_model(2, 2.0, -1.0, 0.5)
+    H = _fock_operator(model).toarray()
+    gammas, vecs = _states(model.N, 3, 113)
+    E, var = orc.variance(model, gammas)
+    _, lam, _, _ = orc.energy(model, gammas)
+    psi = sum(l * v for l, v in zip(lam, vecs))
+    nrm = np.vdot(psi, psi).real
+    e1 = np.vdot(psi, H @ psi).real / nrm
+    e2 = np.vdot(psi, H @ (H @ psi)).real / nrm
+    assert abs(E - e1) < 1e-12 and abs(var - (e2 - e1 * e1)) < 1e-12 and var > 0
+
+
+def test_variance_vanishes_on_an_eigenstate():
+    """U = 0: the GHF flow reaches the exact (Gaussian) ground state, an
+    eigenstate of H, where delta_H^2 = 0."""
+    h_sp, _ = orc.anderson_chain(7, 0.0, 0.0, 0.5)
+    model = orc.majorana_from_fermions(h_sp, [])
+    g = [inp.random_pure_gamma(model.N, _rng(117), 1)]
+    assert orc.variance(model, g)[1] > 1e-2
+    _, _, gs = orc.run(model, g, 0.25, 400)
+    assert abs(orc.variance(model, gs)[1]) < 1e-9
+
+
+def test_energy_extrapolation():
+    """Linear fit of E against delta_H^2 (Sec. IV A): exact on a line, equal to
+    numpy.polyfit on scattered points, and on a rank-growth run (4 sites,
+    ranks 1..8) the intercept brackets the exact ground energy within 3 sigma."""
+    v = np.array([1e-6, 3e-6, 7e-6, 1.2e-5, 1.9e-5, 5e-5])
+    Es, err = orc.extrapolate_energy(-3.25 + 41.0 * v, v)
+    assert abs(Es + 3.25) < 1e-12 and err < 1e-12
+    noisy = -3.25 + 41.0 * v + np.array([3e-7, -2e-7, 1e-7, 4e-7, -5e-7, 9.0])
+    Es, err = orc.extrapolate_energy(noisy, v)
+    k, b = np.polyfit(v[:5], noisy[:5], 1)
+    assert abs(Es - b) < 1e-12 and err > 0
+    model = orc.anderson_model(3, 4.0, -2.0, 0.5)
+    E_ed = fock.ground_energy(fock.hamiltonian_anderson(3, 4.0, -2.0, 0.5))
+    g, _ = inp.initial_state(model.N, 1, 3, 1)
+    rng = _rng(0)
+    gam, pts = list(g), []
+    for M in range(1, 9):
+        _, lam, gam = orc.run(model, gam, 0.1, 60)
+        E, var = orc.variance(model, gam)
+        assert E >= E_ed - 1e-12 and var > 0
+        pts.append((E, var))
+        gam = orc.add_state(gam, inp.random_generator(model.n, 0.1, rng), int(np.argmax(np.abs(lam))))
+    E, var = np.array(pts).T
+    Es, err = orc.extrapolate_energy(E, var, var_max=1e-2)
+    assert abs(Es - E_ed) < 3.0 * err and err < 1e-3
+
+
 # ---------------------------------------------------------------- whole-step ground truths
 
 def test_energy_descends():
