@@ -30,7 +30,6 @@ sys.path.insert(0, ROOT)
 
 import sgs_inputs as inp  # noqa: E402
 
-METRIC = "imag-time steps/s at 2N=512,M=32"
 UNIT = "steps/s"
 PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 DTYPES = {"fp64": "f64", "tf32": "f64+tf32", "bf16": "f64+bf16", "3xtf32": "f64+3xtf32"}
@@ -43,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sgs", choices=["sgs", "reference"])
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
-    ap.add_argument("--workload", default="large", choices=["large", "small", "serving", "batched"])
+    ap.add_argument("--workload", default="large", choices=["large", "small", "two_channel", "serving", "batched"])
     ap.add_argument("--instances", type=int, default=256, help="batched: number of independent instances")
     ap.add_argument("--max-bath", type=int, default=64, help="batched: bath length L ~ U{16..max-bath}")
     ap.add_argument("--rate", type=float, default=100.0, help="serving: Poisson arrival rate (requests/s)")
@@ -57,7 +56,7 @@ def parse():
 
 def workload(name, rank=0):
     import dataclasses
-    w = inp.LARGE if name == "large" else inp.SMALL
+    w = {"large": inp.LARGE, "small": inp.SMALL, "two_channel": inp.TWO_CHANNEL}[name]
     if rank > 0:
         w = dataclasses.replace(w, rank=rank, name=f"{w.name.rsplit('_M', 1)[0]}_M{rank}")
     return w
@@ -65,7 +64,8 @@ def workload(name, rank=0):
 
 def config_of(w, precision):
     p = w.model
-    return {"workload": f"{w.name}: Anderson impurity, {p.n_bath} bath sites/spin, 2N={2 * p.n_modes}, "
+    chans = f"{p.n_channels} channels x " if p.n_channels > 1 else ""
+    return {"workload": f"{w.name}: Anderson impurity, {chans}{p.n_bath} bath sites/spin, 2N={2 * p.n_modes}, "
                         f"M={w.rank}, U={p.U}, eps_d={p.eps_d}, V={p.V}, t={p.t}, ds={w.dtau}",
             "n": 2 * p.n_modes, "rank": w.rank, "precision": precision, "seed": w.seed,
             "l2": "inputs larger than L2 (per-step working set of several GB, no flush needed)",
@@ -185,7 +185,7 @@ def run_reference(args):
         times.append(t)
     t_step = float(np.mean(times))
     value = 1.0 / t_step
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": f"imag-time steps/s at 2N={2 * w.model.n_modes},M={w.rank}", "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(w, "fp64"),
@@ -217,7 +217,8 @@ def run_sgs(args):
     g, lam = inp.initial_state(p.n_modes, w.rank, w.seed + 1000 * rank, w.parity)
     model = sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels)
     stream = torch.cuda.Stream()          # a capturable stream: steps replay a CUDA graph
-    solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=prec, parity=w.parity, stream=stream)
+    solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=prec, parity=w.parity, stream=stream, autotune=True)
+    metric = f"imag-time steps/s at 2N={2 * p.n_modes},M={w.rank}"
     peak_fp64_mma = sgs.probe_peak(0)
     peak_fp64_fma = sgs.probe_peak(1)
     peak_fp64 = peak_fp64_fma if args.fp64_path == "fma" else peak_fp64_mma
@@ -308,13 +309,14 @@ def run_sgs(args):
     stages = {s: {"ms_per_step": v[0] / args.steps, "tflops": (v[1] / (v[0] * 1e-3) / 1e12) if v[0] > 0 and v[1] > 0
                   else None} for s, v in prof.items()}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": config_of(w, args.precision),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "roofline": roof, "tc_roofline": tc_roof, "clocks": ck, "stages": stages,
-            "energy_last": float(E[0, -1]), "fp64_mma_peak_tflops": peak_fp64_mma,
+            "energy_last": float(E[0, -1]), "panel_widths_gj_pf": list(solver.tuning(0)[:2]),
+            "fp64_mma_peak_tflops": peak_fp64_mma,
             "fp64_fma_peak_tflops": peak_fp64_fma}
     solver.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -395,7 +397,7 @@ def run_batched(args):
     ws = inp.batched_workloads(args.instances, n_bath=(16, args.max_bath))
     mine = ws[rank::world]
     stream = torch.cuda.Stream()
-    solver = sgs.Solver(stream=stream)
+    solver = sgs.Solver(stream=stream, autotune=True)
     flops_per_step = 0.0
     for w in mine:
         p = w.model
@@ -405,8 +407,10 @@ def run_batched(args):
         rng = np.random.default_rng(w.seed)
         g = inp.clustered_pure_gammas(p.n_modes, w.rank, rng, w.parity, spread=1.0)
         lam = inp.random_amplitudes(w.rank, rng)
+        # phase form of c_mu (Sec. III A): the inverse form divides by the amplitude, and from these
+        # starts it drives rotations with ||X||_F of 1e2..1e3 per step
         solver.admit(sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels), g, lam, w.dtau,
-                     prec, 0, w.parity)
+                     prec, 1, w.parity)
         n, M = 2 * p.n_modes, w.rank
         # dense work per step (the algorithmic count of the pair and state stages, in n^3 units)
         flops_per_step += n ** 3 * (M * (M - 1) / 2 * (2 + 1 + 4 / 3 + 1 + 2 + 1) * 2 + M * 60)
@@ -428,6 +432,10 @@ def run_batched(args):
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     launches = solver.profile()[1]
+    shapes = {}
+    for k in range(solver.n_instances):
+        gj, pf, _ = solver.tuning(k)
+        shapes[f"{gj}/{pf}"] = shapes.get(f"{gj}/{pf}", 0) + 1
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -444,8 +452,10 @@ def run_batched(args):
                                    "M in {8,16,32}, U ~ U[0,8], eps_d = -U/2, V ~ U[0.2,1], ds = 0.05",
                        "n_range": [min(ns), max(ns)], "precision": args.precision,
                        "inputs": "clustered pure states O_mu = exp(K_mu) O around one Haar O, random phases",
+                       "c_mu": "phase form (Sec. III A)", "autotune": True,
                        "l2": "inputs larger than L2 (tens of GB resident)"},
             "gpu_launches": launches, "clocks": ck, "all_energies_finite": finite,
+            "panel_widths_gj_pf": shapes,
             "dense_tflops_per_s": flops_per_step * len(ws) / max(len(mine), 1) * args.steps / (ms_max * 1e-3) / 1e12}
     if rank == 0:
         print(json.dumps(line))

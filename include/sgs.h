@@ -122,6 +122,20 @@ sgs_status sgs_admit(sgs_ctx* ctx, const sgs_model* model, const sgs_options* op
 sgs_status sgs_retire(sgs_ctx* ctx, int slot);
 size_t sgs_bytes_in_use(const sgs_ctx* ctx);
 
+/* Autotuning of the factorisation tile shapes.  With enable = 1, sgs_admit
+ * (and sgs_add_state) times the candidate panel widths of the blocked
+ * Gauss-Jordan inverse (8, 16, 32, 64 columns, as shared memory allows) and
+ * of the blocked complex Pfaffian (8, 16, 32) on the new instance's own pairs,
+ * with CUDA events, and keeps the fastest.  Choices are cached per (n, rank,
+ * precision) for the process, so a shape is timed once; the scratch of tuned
+ * instances is sized for the widest candidate.  Widths change results only
+ * by rounding.  Default: off (fixed widths). */
+sgs_status sgs_set_autotune(sgs_ctx* ctx, int enable);
+
+/* Panel widths an instance uses; from_cache: -1 not tuned, 0 timed at
+ * admission, 1 taken from the cache.  Any output may be NULL. */
+sgs_status sgs_get_tuning(const sgs_ctx* ctx, int instance, int* gj_width, int* pf_width, int* from_cache);
+
 /* Rank growth (Sec. III C): append to the live instance `slot` the state
  * Q Gamma_src Q^T with Q = exp(K), a special orthogonal matrix.  The paper
  * grows the ansatz one state at a time from the mean-field (rank-1) solution,
@@ -240,6 +254,13 @@ sgs_status sgs_probe_peak(int kind, double* tflops);
  * they share one pipe and FMA issues faster. */
 void sgs_set_fp64_gemm_path(int use_fma);
 
+/* Operand staging of the tensor-core products (process-wide, read when an
+ * instance is admitted and at each launch): 1 = Tensor Memory Accelerator
+ * tile loads into 128-byte-swizzled shared memory with an mbarrier pipeline
+ * (default), 0 = cp.async copies into the unswizzled layout.  Both issue the
+ * same tcgen05.mma sequence, so results are identical. */
+void sgs_set_tc_loader(int use_tma);
+
 /* Majorana form of the Anderson impurity of Sec. IV (H_0 + H_I) with
  * n_channels open bath chains of n_bath sites, hybridisation V, hopping t,
  * chemical potential mu, interaction U n_up n_dn and level eps_d on the
@@ -249,6 +270,16 @@ void sgs_set_fp64_gemm_path(int use_fma);
  * modes N, or -1 on bad arguments. */
 int sgs_build_anderson(int n_bath, int n_channels, double U, double eps_d, double V, double t, double mu,
                        double* A, int* quartic_idx, double* quartic_val, double* e_const);
+
+/* Majorana form of the lattice two-channel Kondo model of Sec. V:
+ * H = -t sum (hopping along each channel) + H_J + H_BC, H_J = J sum_alpha
+ * S_imp . S_alpha(1) with a fermionic impurity (site 0, no quadratic term),
+ * channels of L - 1 sites interleaved (channel alpha's r-th site is
+ * 1 + 2(r - 1) + alpha) and the boundary site 2L - 1 hopping to the last site
+ * of both channels (H_BC): 2L sites, n = 8L.  Writes A ([n][n]), the 24
+ * quartic monomials of H_J (idx [24][4], val [24]) and e_const (0).  Returns
+ * the number of modes N = 4L, or -1 on bad arguments (L < 2). */
+int sgs_build_2ck(int L, double J, double t, double* A, int* quartic_idx, double* quartic_val, double* e_const);
 
 /* Building blocks with host buffers, for tests and external callers.
  * sgs_kernel_inverse: batch n x n matrices -> inverses (Gauss-Jordan,

@@ -150,6 +150,38 @@ def anderson_model(n_bath, U, eps_d, V, t=1.0, mu=0.0, n_channels=1):
     return majorana_from_fermions(*anderson_chain(n_bath, U, eps_d, V, t, mu, n_channels))
 
 
+def kondo_site(ch, r):
+    """Site of channel ch (0, 1) at distance r (1 .. L-1) in the two-channel
+    Kondo lattice; the impurity is site 0 and the boundary site 2L - 1."""
+    return 1 + 2 * (r - 1) + ch
+
+
+def two_channel_kondo_model(L, J, t=0.5):
+    """H_2CK of Sec. V: two channels of L - 1 sites with hopping -t, the
+    boundary site joining their far ends (H_BC), and H_J = J sum_alpha S_imp .
+    S_alpha(1) with a fermionic impurity that has no quadratic term (2L sites in
+    all).  The quadratic part goes through majorana_from_fermions; H_J is
+    expanded into Majorana monomials by the polynomial algebra below."""
+    n_sites = 2 * L
+    nm = 2 * n_sites
+    h = np.zeros((nm, nm))
+    bc = n_sites - 1
+    for s in range(2):
+        for ch in range(2):
+            for r in range(2, L):
+                p, q = 2 * kondo_site(ch, r - 1) + s, 2 * kondo_site(ch, r) + s
+                h[p, q] = h[q, p] = -t
+            p, q = 2 * kondo_site(ch, L - 1) + s, 2 * bc + s
+            h[p, q] = h[q, p] = -t
+    base = majorana_from_fermions(h, [])
+    monomials = []
+    for ch in range(2):
+        for mono, coef in spin_dot(0, kondo_site(ch, 1)).items():
+            assert len(mono) == 4 and abs(np.imag(coef)) < 1e-15, (mono, coef)
+            monomials.append((mono, J * float(np.real(coef))))
+    return MajoranaModel(base.A, antisymmetrise_monomials(monomials), base.e_const)
+
+
 # ---------------------------------------------------------------------------
 # Pfaffian (the paper computes Pfaffians with PFAPACK; this is a plain
 # Parlett-Reid elimination with partial pivoting)

@@ -62,6 +62,8 @@ SIGNATURES = {
     "sgs_retire": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_bytes_in_use": (ctypes.c_size_t, [_ctxp]),
     "sgs_add_state": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, ctypes.c_int]),
+    "sgs_set_autotune": (ctypes.c_int, [_ctxp, ctypes.c_int]),
+    "sgs_get_tuning": (ctypes.c_int, [_ctxp, ctypes.c_int, _ip, _ip, _ip]),
     "sgs_set_graphs": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_energy": (ctypes.c_int, [_ctxp, _dp]),
     "sgs_correlator": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _dp]),
@@ -75,10 +77,12 @@ SIGNATURES = {
     "sgs_set_allocator": (None, [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]),
     "sgs_build_anderson": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _ip, _dp, _dp]),
+    "sgs_build_2ck": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _ip, _dp, _dp]),
     "sgs_set_profiling": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_get_profile": (ctypes.c_int, [_ctxp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "sgs_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
     "sgs_set_fp64_gemm_path": (None, [ctypes.c_int]),
+    "sgs_set_tc_loader": (None, [ctypes.c_int]),
     "sgs_kernel_inverse": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_pfaffian": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_dgemm": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp]),
@@ -173,6 +177,19 @@ def build_anderson(n_bath, U, eps_d, V, t=1.0, mu=0.0, n_channels=1) -> Majorana
     return MajoranaModel(A, qi, qv, ec[0])
 
 
+def build_2ck(L, J, t=0.5) -> MajoranaModel:
+    """Lattice two-channel Kondo model of Sec. V (2L sites)."""
+    n = 8 * L
+    A = np.zeros((n, n))
+    qi = np.zeros(24 * 4, dtype=np.int32)
+    qv = np.zeros(24)
+    ec = np.zeros(1)
+    nm = _lib.sgs_build_2ck(L, J, t, _ptr(A), _ptr(qi, _ip), _ptr(qv), _ptr(ec))
+    if nm < 0:
+        raise SGSError(1, "bad two-channel Kondo parameters")
+    return MajoranaModel(A, qi, qv, ec[0])
+
+
 # ------------------------------------------------------------ solver
 
 def _check_slot_args(model, gamma0, parity):
@@ -195,7 +212,7 @@ class Solver:
     while others are live: continuous batching."""
 
     def __init__(self, models=(), gamma0=(), lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE,
-                 parity=1, stream=None, hbm_budget=0, integrator=SGS_INTEGRATOR_EXP):
+                 parity=1, stream=None, hbm_budget=0, integrator=SGS_INTEGRATOR_EXP, autotune=False):
         if isinstance(models, MajoranaModel):
             models, gamma0, lambda0 = [models], [gamma0], [lambda0]
         models = list(models)
@@ -216,6 +233,8 @@ class Solver:
         if st != 0:
             raise SGSError(st, "sgs_create failed")
         self._ctx = ctx
+        if autotune:
+            _lib.sgs_set_autotune(ctx, 1)
         self.shapes = []
         self.live = []
         self._keep = {}
@@ -258,6 +277,13 @@ class Solver:
 
     def bytes_in_use(self):
         return int(_lib.sgs_bytes_in_use(self._ctx))
+
+    def tuning(self, slot=0):
+        """(Gauss-Jordan panel width, Pfaffian panel width, source) of a slot;
+        source -1 not tuned, 0 timed, 1 cached."""
+        v = [ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)]
+        self._check(_lib.sgs_get_tuning(self._ctx, slot, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def add_state(self, K, src=-1, slot=0):
         """Rank growth (Sec. III C): append Q Gamma_src Q^T, Q = exp(K), to a
@@ -356,6 +382,11 @@ class Solver:
 
 
 # ------------------------------------------------------------ building blocks
+
+def set_tc_loader(use_tma=True):
+    """Tensor-core operand staging: TMA tile loads (default) or cp.async."""
+    _lib.sgs_set_tc_loader(1 if use_tma else 0)
+
 
 def set_fp64_gemm_path(use_fma=True):
     """FP64 products on the FMA pipe (default) or the m8n8k4 MMA."""

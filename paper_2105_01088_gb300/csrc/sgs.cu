@@ -14,6 +14,7 @@
 #include "../../include/sgs.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -31,6 +32,7 @@
 #include "update.cuh"
 #include "probe.cuh"
 #include "gemm_tc.cuh"
+#include "gemm_tma.cuh"
 #include "corr.cuh"
 #include "renyi.cuh"
 #include "var.cuh"
@@ -43,6 +45,9 @@ namespace {
 // the share of each context)
 long long g_launches = 0;
 inline void counted() { ++g_launches; }
+
+// staging of the tensor-core operands: 1 = TMA tensor loads (default), 0 = cp.async
+int g_tc_tma = 0;
 
 sgs_alloc_fn g_alloc = nullptr;
 sgs_free_fn g_release = nullptr;
@@ -57,7 +62,9 @@ struct Instance {
     int N = 0, n = 0, M = 0, P = 0, Ppf = 0, nimp = 0, nq = 0, a_nnz = 0;
     double dtau = 0.0, e_const = 0.0;
     int prec = 0, cmode = 0, parity = 1, integrator = 0;
-    int gj_b = 32, pf_bs = 16;
+    int gj_b = 32, pf_bs = 16;          // panel widths of the Gauss-Jordan inverse and the Pfaffian
+    int gj_cap = 32, pf_cap = 16;       // widest widths the scratch holds
+    int tuned_from_cache = -1;          // -1 not tuned, 0 timed, 1 cached
     std::vector<int> h_pa, h_pb;
     std::vector<double> hA, hq_val;     // host copy of the model: rank growth rebuilds the instance
     std::vector<int> hq_idx;
@@ -101,6 +108,8 @@ struct Instance {
     void *si_hi = nullptr, *si_lo = nullptr, *t1_hi = nullptr, *t1_lo = nullptr, *d_hi = nullptr, *d_lo = nullptr;
     void *wr_hi = nullptr, *wr_lo = nullptr, *va_hi = nullptr, *va_lo = nullptr;
     float *wr32 = nullptr, *va32 = nullptr, *xa32 = nullptr;
+    TmaBatch tma_w{}, tma_v{}, tma_x{};   // TMA-fed products W = T1 S^{-1}, V = D W, X = V D
+    bool tma_ok = false;
     void **q_si_hi = nullptr, **q_si_lo = nullptr, **q_t1_hi = nullptr, **q_t1_lo = nullptr, **q_d_hi = nullptr,
          **q_d_lo = nullptr, **q_wr_hi = nullptr, **q_wr_lo = nullptr, **q_va_hi = nullptr, **q_va_lo = nullptr,
          **q_wr32 = nullptr, **q_va32 = nullptr, **q_xa32 = nullptr;
@@ -139,6 +148,7 @@ struct sgs_ctx {
     int device = 0;
     Instance* owner = nullptr;          // instance being set up: its allocations are its own
     size_t bytes_in_use = 0, budget = 0;  // budget 0 = unlimited
+    bool autotune = false;              // time the factorisation panel widths of new shapes
     cudaEvent_t fork = nullptr;
 
     void* dalloc(size_t bytes) {
@@ -268,9 +278,9 @@ unsigned grid_chunks(size_t work, int threads, unsigned cap) {
 }
 
 // device bytes one instance holds (the allocations of setup_instance, up to small terms)
-size_t instance_bytes(int n, int M, int prec, int nimp) {
+size_t instance_bytes(int n, int M, int prec, int nimp, bool tune) {
     const size_t nn = (size_t)n * n, P = (size_t)M * (M - 1) / 2, Ppf = P > 0 ? P - (M - 1) : 0;
-    const size_t gj_b = (n <= 640) ? 32 : 16, bs = 16;
+    const size_t gj_b = tune ? 64 : 32, bs = tune ? 32 : 16;
     const size_t ni = std::max(nimp, 1);
     size_t d = 7 * (size_t)M * nn + std::max<size_t>(P, 1) * nn * 7 + P * gj_b * n + Ppf * 20 * n * bs +
                P * ni * ni * 2 + P * 2 * n * ni + 6 * (size_t)(2 * M) * (2 * M) + 16 * (size_t)M * M;
@@ -281,6 +291,63 @@ size_t instance_bytes(int n, int M, int prec, int nimp) {
         bytes += P * n * ldp * esz * ops + 3 * P * nn * 4;
     }
     return bytes + (1 << 20);
+}
+
+// Candidate panel widths (the factorisations' tile shapes).  Gauss-Jordan: the panel
+// kernel keeps n x (b + 1) doubles in shared memory; Pfaffian: 2 b <= n.
+std::vector<int> gj_candidates(int n) {
+    static int limit = -1;
+    if (limit < 0) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, gj_panel_kernel);
+        limit = optin - (int)fa.sharedSizeBytes;
+    }
+    std::vector<int> v;
+    for (int b : {8, 16, 32, 64})
+        if (b <= n && (size_t)n * (b + 1) * sizeof(double) + b * sizeof(double) <= (size_t)limit) v.push_back(b);
+    return v;
+}
+std::vector<int> pf_candidates(int n) {
+    std::vector<int> v;
+    for (int b : {8, 16, 32})
+        if (2 * b <= n) v.push_back(b);
+    return v;
+}
+int default_gj_width(int n) { return std::min((n <= 640) ? 32 : 16, n); }
+int default_pf_width(int n) { return (2 * 16 > n) ? n / 2 : 16; }
+
+// Pointer arrays of the Gauss-Jordan panel rows and the Pfaffian panel vectors and
+// packed update operands for panel widths (gj_b, pf_bs); the scratch they point into is
+// sized for the widest candidate the instance may use.
+sgs_status set_panel_pointers(sgs_ctx* c, Instance& I, int gj_b, int pf_bs) {
+    const int n = I.n, P = I.P;
+    const size_t nn = (size_t)n * n;
+    I.gj_b = gj_b;
+    I.pf_bs = pf_bs;
+    Instance* prev = c->owner;          // allocations belong to the instance
+    c->owner = &I;
+    std::vector<double*> t;
+    for (int p = 0; p < P; p++) t.push_back(I.tbuf + (size_t)p * gj_b * n);
+    if (P > 0 && !(I.p_tbuf = upload_ptrs(c, t))) { c->owner = prev; return SGS_ENOMEM; }
+    std::vector<double*> Y, TU, PK, upA, upB, upC;
+    const size_t blk = (size_t)n * 4 * pf_bs;
+    for (int q = 0; q < I.Ppf; q++) {
+        Y.push_back(I.work + (size_t)q * 2 * nn);
+        TU.push_back(I.pfTU + (size_t)q * 4 * n * pf_bs);
+        PK.push_back(I.pfpack + (size_t)q * 4 * blk);
+    }
+    for (int q = 0; q < I.Ppf; q++) { upA.push_back(PK[q]); upB.push_back(PK[q] + blk); upC.push_back(Y[q]); }
+    for (int q = 0; q < I.Ppf; q++) { upA.push_back(PK[q] + 2 * blk); upB.push_back(PK[q] + 3 * blk); upC.push_back(Y[q] + nn); }
+    if (I.Ppf > 0) {
+        I.p_Y = upload_ptrs(c, Y); I.p_TU = upload_ptrs(c, TU); I.p_pack = upload_ptrs(c, PK);
+        I.p_upA = upload_ptrs(c, upA); I.p_upB = upload_ptrs(c, upB); I.p_upC = upload_ptrs(c, upC);
+        if (!I.p_Y || !I.p_TU || !I.p_pack || !I.p_upA || !I.p_upB || !I.p_upC) { c->owner = prev; return SGS_ENOMEM; }
+    }
+    c->owner = prev;
+    return SGS_OK;
 }
 
 sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs_options& o) {
@@ -298,10 +365,14 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.hA.assign(m.A, m.A + (size_t)n * n);
     I.hq_idx.assign(m.quartic_idx, m.quartic_idx + (m.n_quartic > 0 ? 4 * m.n_quartic : 0));
     I.hq_val.assign(m.quartic_val, m.quartic_val + (m.n_quartic > 0 ? m.n_quartic : 0));
-    I.gj_b = (n <= 640) ? 32 : 16;
-    if (I.gj_b > n) I.gj_b = n;
-    I.pf_bs = 16;
-    if (2 * I.pf_bs > n) I.pf_bs = n / 2;
+    I.gj_b = default_gj_width(n);
+    I.pf_bs = default_pf_width(n);
+    I.gj_cap = I.gj_b;
+    I.pf_cap = I.pf_bs;
+    if (c->autotune) {          // scratch for the widest candidate
+        for (int b : gj_candidates(n)) I.gj_cap = std::max(I.gj_cap, b);
+        for (int b : pf_candidates(n)) I.pf_cap = std::max(I.pf_cap, b);
+    }
 
     // sparse A
     std::vector<int> rowptr(n + 1, 0), rows, cols;
@@ -390,11 +461,11 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.work = c->alloc<double>(Pm * 2 * nn);
     I.si = c->alloc<double>(Pm * nn); I.imd = c->alloc<double>(Pm * nn);
     I.wr = c->alloc<double>(Pm * nn); I.va = c->alloc<double>(Pm * nn); I.xa = c->alloc<double>(Pm * nn);
-    I.tbuf = c->alloc<double>(Pm * I.gj_b * n);
+    I.tbuf = c->alloc<double>(Pm * I.gj_cap * n);
     I.piv = c->alloc<int>(Pm * n); I.perm = c->alloc<int>(Pm * n);
     I.logdet = c->alloc<double>(Pm); I.dsign = c->alloc<double>(Pm);
-    I.pfTU = c->alloc<double>(Pf * 4 * n * I.pf_bs);
-    I.pfpack = c->alloc<double>(Pf * 4 * n * 4 * I.pf_bs);
+    I.pfTU = c->alloc<double>(Pf * 4 * n * I.pf_cap);
+    I.pfpack = c->alloc<double>(Pf * 4 * n * 4 * I.pf_cap);
     I.pflog = c->alloc<double>(Pf); I.pfphase = c->alloc<double>(2 * Pf);
     I.fimp = c->alloc<double>(Pm * ni * ni * 2); I.fimp_state = c->alloc<double>((size_t)M * ni * ni);
     I.lr = c->alloc<double>(Pm * 2 * n * ni);
@@ -448,10 +519,9 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     CUDA_TRY(c, cudaMemsetAsync(I.err, 0, sizeof(int), st));
 
     // pointer arrays
-    std::vector<double*> w, t, s_, im, wr, va, xa, ga, gb;
+    std::vector<double*> w, s_, im, wr, va, xa, ga, gb;
     for (int p = 0; p < P; p++) {
         w.push_back(I.work + p * nn);
-        t.push_back(I.tbuf + (size_t)p * I.gj_b * n);
         s_.push_back(I.si + p * nn);
         im.push_back(I.imd + p * nn);
         wr.push_back(I.wr + p * nn);
@@ -461,23 +531,11 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         gb.push_back(I.gamma + pb[p] * nn);
     }
     if (P > 0) {
-        I.p_work = upload_ptrs(c, w); I.p_tbuf = upload_ptrs(c, t); I.p_si = upload_ptrs(c, s_);
+        I.p_work = upload_ptrs(c, w); I.p_si = upload_ptrs(c, s_);
         I.p_imd = upload_ptrs(c, im); I.p_wr = upload_ptrs(c, wr); I.p_va = upload_ptrs(c, va);
         I.p_xa = upload_ptrs(c, xa); I.p_ga = upload_ptrs(c, ga); I.p_gb = upload_ptrs(c, gb);
     }
-    std::vector<double*> Y, TU, PK, upA, upB, upC;
-    const size_t blk = (size_t)n * 4 * I.pf_bs;
-    for (int q = 0; q < I.Ppf; q++) {
-        Y.push_back(I.work + (size_t)q * 2 * nn);
-        TU.push_back(I.pfTU + (size_t)q * 4 * n * I.pf_bs);
-        PK.push_back(I.pfpack + (size_t)q * 4 * blk);
-    }
-    for (int q = 0; q < I.Ppf; q++) { upA.push_back(PK[q]); upB.push_back(PK[q] + blk); upC.push_back(Y[q]); }
-    for (int q = 0; q < I.Ppf; q++) { upA.push_back(PK[q] + 2 * blk); upB.push_back(PK[q] + 3 * blk); upC.push_back(Y[q] + nn); }
-    if (I.Ppf > 0) {
-        I.p_Y = upload_ptrs(c, Y); I.p_TU = upload_ptrs(c, TU); I.p_pack = upload_ptrs(c, PK);
-        I.p_upA = upload_ptrs(c, upA); I.p_upB = upload_ptrs(c, upB); I.p_upC = upload_ptrs(c, upC);
-    }
+    if (set_panel_pointers(c, I, I.gj_b, I.pf_bs) != SGS_OK) { c->err = "device allocation failed"; return SGS_ENOMEM; }
     std::vector<double*> g, dg, ss[5];
     for (int mu = 0; mu < M; mu++) {
         g.push_back(I.gamma + mu * nn);
@@ -525,6 +583,19 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         I.q_wr32 = arr(I.wr32, f4); I.q_va32 = arr(I.va32, f4); I.q_xa32 = arr(I.xa32, f4);
         I.q_si_lo = arr(I.si_lo, lp); I.q_t1_lo = arr(I.t1_lo, lp); I.q_d_lo = arr(I.d_lo, lp);
         I.q_wr_lo = arr(I.wr_lo, lp); I.q_va_lo = arr(I.va_lo, lp);
+        // tensor maps of the contiguous operand batches [P][n][ldp]
+        const bool bf = I.tc_kind == TC_BF16;
+        auto prod = [&](TmaBatch& t, void* A, void* A2, void* B, void* B2, float* C, int skew) {
+            bool ok = make_operand_map(&t.ta, A, bf, I.ldp, n, P) && make_operand_map(&t.tb, B, bf, I.ldp, n, P);
+            if (split) ok = ok && make_operand_map(&t.ta2, A2, bf, I.ldp, n, P) && make_operand_map(&t.tb2, B2, bf, I.ldp, n, P);
+            t.m = n; t.n = n; t.k = n; t.alpha = -1.0; t.C = C; t.c_stride = (long long)nn; t.ldc = n;
+            t.out_f64 = 0; t.skew = skew; t.err = I.err; t.batch = P;
+            return ok;
+        };
+        I.tma_ok = prod(I.tma_w, I.t1_hi, I.t1_lo, I.si_hi, I.si_lo, I.wr32, 1) &&
+                   prod(I.tma_v, I.d_hi, I.d_lo, I.wr_hi, I.wr_lo, I.va32, 0) &&
+                   prod(I.tma_x, I.va_hi, I.va_lo, I.d_hi, I.d_lo, I.xa32, 1);
+        if (g_tc_tma && !I.tma_ok) { c->err = "tensor map encoding failed"; return SGS_ECUDA; }
     }
     return SGS_OK;
 }
@@ -552,6 +623,9 @@ void set_kernel_attributes() {
         raise_smem_limit(gemm_tc_kernel<128, TC_TF32>, optin);
         raise_smem_limit(gemm_tc_kernel<128, TC_BF16>, optin);
         raise_smem_limit(gemm_tc_kernel<128, TC_3XTF32>, optin);
+        raise_smem_limit(gemm_tma_kernel<TC_TF32>, optin);
+        raise_smem_limit(gemm_tma_kernel<TC_BF16>, optin);
+        raise_smem_limit(gemm_tma_kernel<TC_3XTF32>, optin);
         cudaGetLastError();
     });
 }
@@ -626,39 +700,58 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
     return cudaGetLastError();
 }
 
+// S = Gamma_a + Gamma_b for every pair, its Gauss-Jordan inverse (pivoted, FP64) and
+// log|det S|, sign.  S has entries of magnitude <= 2; two states of opposite parity give a
+// pivot at rounding level (~1e-15), same-parity pairs O(0.1).
+cudaError_t pair_inverse(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    const int n = I.n, P = I.P;
+    const size_t nn = (size_t)n * n;
+    pair_sum_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.dev(), I.work);
+    counted();
+    cudaError_t e = launch_gj(c, n, P, I.gj_b, I.p_work, I.p_tbuf, I.piv, I.logdet, I.dsign, I.err, 1e-12, st);
+    if (e != cudaSuccess) return e;
+    gj_perm_kernel<<<(P + 127) / 128, 128, 0, st>>>(I.piv, I.perm, n, P);
+    gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.p_work, I.p_si, I.perm, n);
+    counted(); counted();
+    return cudaGetLastError();
+}
+
+// Im Delta^{a,b} = (G_a - G_b) S^{-1}
+cudaError_t pair_delta(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    const int n = I.n;
+    GemmBatch g = gb_basic(n, n, n, I.p_ga, n, I.p_si, n, I.p_imd, n, I.P);
+    g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
+    g.mode = GEMM_SKEW;
+    return gemm(c, g, st, (double)n * n * n * I.P);   // antisymmetric product: half of 2 n^3
+}
+
+// phase Pfaffians Pf(Gamma_0 + Delta^{a,b}) of the pairs without the reference state
+cudaError_t pair_phase(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    const int n = I.n;
+    const size_t nn = (size_t)n * n;
+    pf_build_kernel<<<dim3(grid_chunks(nn, 256, 64), I.Ppf), 256, 0, st>>>(I.dev(), I.si, I.imd, I.work);
+    counted();
+    return launch_pf(c, n, I.Ppf, I.pf_bs, I.p_Y, I.p_TU, I.p_pack, I.p_upA, I.p_upB, I.p_upC, I.pflog, I.pfphase,
+                     I.err, st);
+}
+
 // pair pass + amplitude solve for one instance; E -> Ehist[slot]
 cudaError_t pair_pass(sgs_ctx* c, Instance& I, double* Eout, cudaStream_t st) {
     const int n = I.n, P = I.P, M = I.M;
-    const size_t nn = (size_t)n * n;
     const double n3 = (double)n * n * n;
     InstDev d = I.dev();
     if (P > 0) {
         c->stage(SGS_STAGE_PAIR_INVERSE);
         c->stage_flops[SGS_STAGE_PAIR_INVERSE] += 2.0 * n3 * P;
-        pair_sum_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.work);
-        counted();
-        // S has entries of magnitude <= 2; two states of opposite parity give a
-        // pivot at rounding level (~1e-15), same-parity pairs O(0.1)
-        cudaError_t e = launch_gj(c, n, P, I.gj_b, I.p_work, I.p_tbuf, I.piv, I.logdet, I.dsign, I.err, 1e-12, st);
+        cudaError_t e = pair_inverse(c, I, st);
         if (e != cudaSuccess) return e;
-        gj_perm_kernel<<<(P + 127) / 128, 128, 0, st>>>(I.piv, I.perm, n, P);
-        gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.p_work, I.p_si, I.perm, n);
-        counted(); counted();
-        // Im = (G_a - G_b) S^{-1}
         c->stage(SGS_STAGE_PAIR_DELTA);
-        c->stage_flops[SGS_STAGE_PAIR_DELTA] += n3 * P;   // antisymmetric product: half of 2 n^3
-        GemmBatch g = gb_basic(n, n, n, I.p_ga, n, I.p_si, n, I.p_imd, n, P);
-        g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
-        g.mode = GEMM_SKEW;
-        if ((e = gemm(c, g, st, n3 * P)) != cudaSuccess) return e;
+        c->stage_flops[SGS_STAGE_PAIR_DELTA] += n3 * P;
+        if ((e = pair_delta(c, I, st)) != cudaSuccess) return e;
         if (I.Ppf > 0) {
             c->stage(SGS_STAGE_PHASE_PFAFFIAN);
             c->stage_flops[SGS_STAGE_PHASE_PFAFFIAN] += 4.0 / 3.0 * n3 * I.Ppf;
-            pf_build_kernel<<<dim3(grid_chunks(nn, 256, 64), I.Ppf), 256, 0, st>>>(d, I.si, I.imd, I.work);
-            counted();
-            e = launch_pf(c, n, I.Ppf, I.pf_bs, I.p_Y, I.p_TU, I.p_pack, I.p_upA, I.p_upB, I.p_upC, I.pflog,
-                          I.pfphase, I.err, st);
-            if (e != cudaSuccess) return e;
+            if ((e = pair_phase(c, I, st)) != cudaSuccess) return e;
         }
     }
     c->stage(SGS_STAGE_AMPLITUDES);
@@ -667,6 +760,86 @@ cudaError_t pair_pass(sgs_ctx* c, Instance& I, double* Eout, cudaStream_t st) {
     amp_solve_kernel<<<1, 256, 0, st>>>(aa);
     counted(); counted();
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ autotuning
+
+std::mutex g_tune_mu;
+std::map<std::array<int, 3>, std::array<int, 2>> g_tune_cache;   // (n, rank, precision) -> widths
+
+// Time the candidate widths on the instance's own pairs (CUDA events on the context
+// stream, best of two), keep the fastest; a shape already timed in this process reuses
+// its widths.  Results change only by rounding.
+sgs_status autotune_instance(sgs_ctx* c, Instance& I) {
+    if (I.P == 0) return SGS_OK;
+    const std::array<int, 3> key{I.n, I.M, I.prec};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            I.tuned_from_cache = 1;
+            return set_panel_pointers(c, I, it->second[0], it->second[1]);
+        }
+    }
+    cudaStream_t st = c->stream;
+    const bool prof = c->prof;
+    c->prof = false;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    sgs_status status = SGS_OK;
+    auto timed = [&](auto&& prep, auto&& work) -> float {
+        float best = 1e30f;
+        for (int rep = 0; rep < 2 && status == SGS_OK; rep++) {
+            cudaError_t e = prep();
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = work();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                c->err = std::string("autotune: ") + cudaGetErrorString(e);
+                status = SGS_ECUDA;
+            } else {
+                best = std::min(best, ms);
+            }
+        }
+        return best;
+    };
+    int gj = I.gj_b, pf = I.pf_bs;
+    float best = 1e30f;
+    for (int b : gj_candidates(I.n)) {
+        if (b > I.gj_cap) continue;
+        if ((status = set_panel_pointers(c, I, b, pf)) != SGS_OK) break;
+        const float t = timed([&] { return cudaSuccess; }, [&] { return pair_inverse(c, I, st); });
+        if (t < best) { best = t; gj = b; }
+    }
+    if (status == SGS_OK && I.Ppf > 0) {
+        status = set_panel_pointers(c, I, gj, pf);
+        cudaError_t e = cudaSuccess;
+        if (status == SGS_OK) e = pair_inverse(c, I, st);
+        if (e == cudaSuccess) e = pair_delta(c, I, st);
+        if (e != cudaSuccess) { c->err = std::string("autotune: ") + cudaGetErrorString(e); status = SGS_ECUDA; }
+        best = 1e30f;
+        for (int b : pf_candidates(I.n)) {
+            if (status != SGS_OK || b > I.pf_cap) continue;
+            if ((status = set_panel_pointers(c, I, gj, b)) != SGS_OK) break;
+            const float t = timed([&] { return cudaSuccess; }, [&] { return pair_phase(c, I, st); });
+            if (t < best) { best = t; pf = b; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->prof = prof;
+    if (status != SGS_OK) return status;
+    if ((status = set_panel_pointers(c, I, gj, pf)) != SGS_OK) return status;
+    CUDA_TRY(c, cudaMemsetAsync(I.err, 0, sizeof(int), st));      // trial runs leave no error state
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {gj, pf};
+    I.tuned_from_cache = 0;
+    return SGS_OK;
 }
 
 cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
@@ -707,7 +880,8 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         t.A = (const void* const*)I.q_t1_hi; t.A2 = (const void* const*)I.q_t1_lo;
         t.B = (const void* const*)I.q_si_hi; t.B2 = (const void* const*)I.q_si_lo;
         t.C = I.q_wr32; t.skew = 1;
-        if ((e = gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        const bool tma = g_tc_tma && I.tma_ok;
+        if ((e = tma ? gemm_tma(I.tma_w, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
         counted();
         if (!direct) {
             lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_wr32, nullptr, I.q_wr_hi,
@@ -719,7 +893,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         t.A = (const void* const*)I.q_d_hi; t.A2 = (const void* const*)I.q_d_lo;
         t.B = (const void* const*)I.q_wr_hi; t.B2 = (const void* const*)I.q_wr_lo;
         t.C = I.q_va32; t.skew = 0;
-        if ((e = gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        if ((e = tma ? gemm_tma(I.tma_v, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
         counted();
         c->stage(SGS_STAGE_EOM_X);
         c->stage_flops[SGS_STAGE_EOM_X] += n3 * P;
@@ -731,7 +905,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         t.A = (const void* const*)I.q_va_hi; t.A2 = (const void* const*)I.q_va_lo;
         t.B = (const void* const*)I.q_d_hi; t.B2 = (const void* const*)I.q_d_lo;
         t.C = I.q_xa32; t.skew = 1;
-        if ((e = gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        if ((e = tma ? gemm_tma(I.tma_x, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
         counted();
         c->stage(SGS_STAGE_EOM_ASSEMBLY);
         if (I.nimp > 0) {
@@ -961,7 +1135,7 @@ sgs_status sgs_admit(sgs_ctx* c, const sgs_model* model, const sgs_options* opt,
     *slot = -1;
     sgs_status s = check_args(*model, *opt);
     if (s != SGS_OK) { c->err = "invalid model or options"; return s; }
-    const size_t need = instance_bytes(2 * model->n_modes, opt->rank, opt->precision, 16);
+    const size_t need = instance_bytes(2 * model->n_modes, opt->rank, opt->precision, 16, c->autotune);
     if (c->budget && c->bytes_in_use + need > c->budget) {
         c->err = "over the HBM budget: " + std::to_string(c->bytes_in_use + need) + " > " + std::to_string(c->budget);
         return SGS_ENOMEM;
@@ -972,6 +1146,7 @@ sgs_status sgs_admit(sgs_ctx* c, const sgs_model* model, const sgs_options* opt,
     s = setup_instance(c, I, *model, *opt);
     c->owner = nullptr;
     if (s == SGS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) s = SGS_ECUDA;
+    if (s == SGS_OK && c->autotune) s = autotune_instance(c, I);
     if (s != SGS_OK) {
         cudaStreamSynchronize(c->stream);
         c->release_instance(I);
@@ -994,6 +1169,21 @@ sgs_status sgs_retire(sgs_ctx* c, int slot) {
 }
 
 size_t sgs_bytes_in_use(const sgs_ctx* c) { return c ? c->bytes_in_use : 0; }
+
+sgs_status sgs_set_autotune(sgs_ctx* c, int enable) {
+    if (!c) return SGS_EINVAL;
+    c->autotune = enable != 0;
+    return SGS_OK;
+}
+
+sgs_status sgs_get_tuning(const sgs_ctx* c, int instance, int* gj_width, int* pf_width, int* from_cache) {
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
+    const Instance& I = c->inst[instance];
+    if (gj_width) *gj_width = I.gj_b;
+    if (pf_width) *pf_width = I.pf_bs;
+    if (from_cache) *from_cache = I.tuned_from_cache;
+    return SGS_OK;
+}
 
 sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
     if (!c || slot < 0 || slot >= (int)c->inst.size() || !c->inst[slot].live || !K) return SGS_EINVAL;
@@ -1020,7 +1210,7 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
             if (a > best) { best = a; src = mu; }
         }
     }
-    const size_t need = instance_bytes(n, M + 1, I.prec, 16);
+    const size_t need = instance_bytes(n, M + 1, I.prec, 16, c->autotune);
     if (c->budget && c->bytes_in_use - I.bytes + need > c->budget) {
         c->err = "over the HBM budget: " + std::to_string(c->bytes_in_use - I.bytes + need) + " > " +
                  std::to_string(c->budget);
@@ -1068,6 +1258,7 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
             c->err = "rank growth: exponential out of range";
             s = SGS_ENOTCONV;
         }
+        if (s == SGS_OK && c->autotune) s = autotune_instance(c, J);
     }
     if (s != SGS_OK) {
         cudaStreamSynchronize(st);
@@ -1423,6 +1614,8 @@ sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double*
 
 void sgs_set_fp64_gemm_path(int use_fma) { g_gemm_fma = use_fma ? 1 : 0; }
 
+void sgs_set_tc_loader(int use_tma) { g_tc_tma = use_tma ? 1 : 0; }
+
 sgs_status sgs_set_graphs(sgs_ctx* c, int enable) {
     if (!c) return SGS_EINVAL;
     c->use_graph = enable != 0;
@@ -1509,6 +1702,50 @@ int sgs_build_anderson(int n_bath, int n_channels, double U, double eps_d, doubl
     quartic_idx[0] = 0; quartic_idx[1] = 1; quartic_idx[2] = 2; quartic_idx[3] = 3;
     quartic_val[0] = -0.25 * U;
     *e_const = ec;
+    return nm;
+}
+
+int sgs_build_2ck(int L, double J, double t, double* A, int* quartic_idx, double* quartic_val, double* e_const) {
+    if (L < 2 || !A || !quartic_idx || !quartic_val || !e_const) return -1;
+    const int n_sites = 2 * L;
+    const int nm = 2 * n_sites;
+    const int n = 2 * nm;
+    auto site = [](int ch, int r) { return 1 + 2 * (r - 1) + ch; };
+    std::fill(A, A + (size_t)n * n, 0.0);
+    // hopping -t (a_p^dag a_q + h.c.): A_{2p,2q+1} = A_{2q,2p+1} = -t/4 (and the antisymmetric partners)
+    auto hop = [&](int sp, int sq) {
+        for (int s = 0; s < 2; s++) {
+            const int p = 2 * sp + s, q = 2 * sq + s;
+            A[(size_t)(2 * p) * n + 2 * q + 1] -= 0.25 * t;
+            A[(size_t)(2 * q + 1) * n + 2 * p] += 0.25 * t;
+            A[(size_t)(2 * q) * n + 2 * p + 1] -= 0.25 * t;
+            A[(size_t)(2 * p + 1) * n + 2 * q] += 0.25 * t;
+        }
+    };
+    for (int ch = 0; ch < 2; ch++) {
+        for (int r = 2; r < L; r++) hop(site(ch, r - 1), site(ch, r));
+        hop(site(ch, L - 1), n_sites - 1);          // H_BC: the boundary site joins the two channels
+    }
+    *e_const = 0.0;                                   // hopping has no diagonal
+    // H_J = J sum_alpha S_imp . S_alpha(1); S^a of a site = (i/4) sum_{p<q} K^a_pq c_p c_q on its four
+    // Majoranas (K^x: (03) +1, (12) -1; K^y: (02) -1, (13) -1; K^z: (01) +1, (23) -1), so
+    // S^a_imp S^a_r = -(1/16) sum K^a_pq K^a_uv c_p c_q c_{4r+u} c_{4r+v}
+    const int kp[3][2][2] = {{{0, 3}, {1, 2}}, {{0, 2}, {1, 3}}, {{0, 1}, {2, 3}}};
+    const double kv[3][2] = {{1.0, -1.0}, {-1.0, -1.0}, {1.0, -1.0}};
+    int q = 0;
+    for (int ch = 0; ch < 2; ch++) {
+        const int r0 = 4 * site(ch, 1);
+        for (int a = 0; a < 3; a++)
+            for (int i = 0; i < 2; i++)
+                for (int j = 0; j < 2; j++) {
+                    quartic_idx[4 * q + 0] = kp[a][i][0];
+                    quartic_idx[4 * q + 1] = kp[a][i][1];
+                    quartic_idx[4 * q + 2] = r0 + kp[a][j][0];
+                    quartic_idx[4 * q + 3] = r0 + kp[a][j][1];
+                    quartic_val[q] = -J / 16.0 * kv[a][i] * kv[a][j];
+                    q++;
+                }
+    }
     return nm;
 }
 
@@ -1603,7 +1840,19 @@ sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, i
         g.A2 = upload_ptrs(&tmp, pa2); g.B2 = upload_ptrs(&tmp, pb2);
         g.C = upload_ptrs(&tmp, pc); g.ldc = n;
         g.alpha = 1.0; g.out_f64 = 1; g.skew = 0; g.err = err; g.batch = batch;
-        if (gemm_tc(g, kind, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        if (g_tc_tma) {
+            TmaBatch t{};
+            const bool bf = kind == TC_BF16, split = kind == TC_3XTF32;
+            bool ok = make_operand_map(&t.ta, dA, bf, k, m, batch) && make_operand_map(&t.tb, dB, bf, k, n, batch);
+            if (split)
+                ok = ok && make_operand_map(&t.ta2, (const uint8_t*)dA + batch * na * esz, bf, k, m, batch) &&
+                     make_operand_map(&t.tb2, (const uint8_t*)dB + batch * nb * esz, bf, k, n, batch);
+            t.m = m; t.n = n; t.k = k; t.alpha = 1.0; t.C = dC; t.c_stride = (long long)nc; t.ldc = n;
+            t.out_f64 = 1; t.skew = 0; t.err = err; t.batch = batch;
+            if (!ok || gemm_tma(t, kind, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        } else if (gemm_tc(g, kind, tmp.stream) != cudaSuccess) {
+            st = SGS_ECUDA;
+        }
         counted();
         int herr = 0;
         cudaMemcpyAsync(C, dC, batch * nc * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);

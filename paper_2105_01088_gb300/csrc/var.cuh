@@ -44,11 +44,12 @@ __device__ cplx pf_small(cplx* X, int m) {
         pf = cmul(pf, p);
         if (best == 0.0) return cmk(0.0, 0.0);
         const cplx ip = cdiv(cmk(1.0, 0.0), p);
-        // eliminate with the pair (k, k+1): X_ij -= (X_ik X_{k+1,j} - X_{i,k+1} X_kj) / p for i, j > k+1
+        // Schur complement of the 2x2 block [[0, p], [-p, 0]]:
+        // X_ij += (X_ik X_{k+1,j} - X_{i,k+1} X_kj) / p for i, j > k+1
         for (int i = k + 2; i < m; i++)
             for (int j = k + 2; j < m; j++) {
                 const cplx t = csub(cmul(X[i * m + k], X[(k + 1) * m + j]), cmul(X[i * m + k + 1], X[k * m + j]));
-                X[i * m + j] = csub(X[i * m + j], cmul(t, ip));
+                X[i * m + j] = cadd(X[i * m + j], cmul(t, ip));
             }
     }
     return pf;

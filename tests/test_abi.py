@@ -58,6 +58,23 @@ def test_builder_matches_oracle_builder():
         assert sorted(mono) == sorted(o.quartic)
 
 
+def test_kondo_builder_matches_oracle_builder():
+    """The library writes H_J from the closed form of the spin operators; the
+    oracle expands S_imp . S_alpha(1) with its fermion-operator algebra."""
+    import numpy as np
+    import paper_2105_01088_gb300 as pkg
+    from oracle import sgs_oracle as orc
+    for L, J, t in ((2, 1.3, 0.5), (5, 0.7, 0.5), (4, 2.0, 1.0)):
+        m = pkg.build_2ck(L, J, t)
+        o = orc.two_channel_kondo_model(L, J, t)
+        assert m.n == o.n == 8 * L
+        assert np.array_equal(m.A, o.A) and m.e_const == o.e_const == 0.0
+        mono = orc.antisymmetrise_monomials([(tuple(i), v) for i, v in zip(m.quartic_idx, m.quartic_val)])
+        got = dict(mono)
+        ref = dict(o.quartic)
+        assert set(got) == set(ref) and max(abs(got[k] - ref[k]) for k in ref) < 1e-15
+
+
 def test_invalid_arguments_are_rejected_without_gpu_work():
     import numpy as np
     import paper_2105_01088_gb300 as pkg

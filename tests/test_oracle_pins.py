@@ -308,6 +308,32 @@ def test_rank_growth_approaches_exact_ground_state():
     assert (Es[59] - E_ed) / abs(E_ed) > 1e-2          # the single Gaussian is far off
 
 
+@pytest.mark.parametrize("L", [2, 3])
+def test_two_channel_kondo_model_equals_fermion_hamiltonian(L):
+    """Sec. V: the Majorana form of H_2CK equals the Hamiltonian built from
+    fermion operators (hopping, H_BC, J S_imp . S_alpha(1)); its ground state
+    has even parity."""
+    J, t = 1.3, 0.5
+    model = orc.two_channel_kondo_model(L, J, t)
+    N = model.N
+    a = fock.annihilators(N)
+    ad = [x.conj().T.tocsr() for x in a]
+    H = 0.0 * _fock_operator(model)
+    for s in range(2):
+        for ch in range(2):
+            ends = [orc.kondo_site(ch, r) for r in range(1, L)] + [2 * L - 1]
+            for x, y in zip(ends[:-1], ends[1:]):
+                p, q = 2 * x + s, 2 * y + s
+                H = H - t * (ad[p] @ a[q] + ad[q] @ a[p])
+    for ch in range(2):
+        for x, y in zip(fock.spin_ops(N, 0), fock.spin_ops(N, orc.kondo_site(ch, 1))):
+            H = H + J * (x @ y)
+    assert abs(H - _fock_operator(model)).max() < 1e-13
+    w, v = np.linalg.eigh(H.toarray())
+    parity = np.array([(-1) ** bin(i).count("1") for i in range(2 ** N)])
+    assert np.vdot(v[:, 0], parity * v[:, 0]).real > 0.999
+
+
 # ---------------------------------------------------------------- variance (Eq. residual)
 
 def _two_site_hubbard():
