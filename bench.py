@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--max-steps", type=int, default=300, help="serving: step cap per solve")
     ap.add_argument("--rank", type=int, default=0, help="override the ansatz rank M (profiling cases)")
     ap.add_argument("--fp64-path", default="fma", choices=["fma", "mma"], help="FP64 product pipe")
+    ap.add_argument("--tc-loader", default="tma", choices=["tma", "cp"], help="tensor-core operand staging")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -211,6 +212,7 @@ def run_sgs(args):
 
     sgs.use_torch_allocator()
     sgs.set_fp64_gemm_path(args.fp64_path == "fma")
+    sgs.set_tc_loader(args.tc_loader == "tma")
     w = workload(args.workload, args.rank)
     p = w.model
     prec = PRECISIONS[args.precision]
@@ -287,7 +289,9 @@ def run_sgs(args):
         tfile = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tfile):
             t = json.load(open(tfile)).get(f"gemm_f64_all_{args.precision}", {})
-            if t.get("n") == n and t.get("rank") == w.rank:
+            # counters hold for the same shape, panel widths and FP64 path only
+            if (t.get("n") == n and t.get("rank") == w.rank and t.get("fp64_path") == args.fp64_path
+                    and t.get("panel_widths_gj_pf") == list(solver.tuning(0)[:2])):
                 traffic = t.get("bytes_per_launch")
         roof = {"bound": "alu" if args.fp64_path == "fma" else "tensor", "achieved": achieved, "peak": peak_fp64,
                 "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": traffic,
@@ -302,7 +306,8 @@ def run_sgs(args):
         ratio = {"tf32": 1.1 / 2.25, "3xtf32": 1.1 / 2.25 / 3.0, "bf16": 1.0}[args.precision]
         v_ms, v_fl, _ = prof["eom_v"]
         a = v_fl / (v_ms * 1e-3) / 1e12
-        tc_roof = {"bound": "tensor", "kernel": f"gemm_tc_kernel (tcgen05 {args.precision}, V = D W)",
+        kname = "gemm_tma_kernel (TMA-fed" if args.tc_loader == "tma" else "gemm_tc_kernel (cp.async-fed"
+        tc_roof = {"bound": "tensor", "kernel": f"{kname} tcgen05 {args.precision}, V = D W)",
                    "achieved": a, "peak": bf16 * ratio, "unit": "TFLOP/s", "frac": a / (bf16 * ratio),
                    "peak_source": "MEASURED_PEAKS.json bf16_tflops x nominal ratio "
                                   f"({args.precision}: {ratio:.3f})"}
@@ -393,6 +398,7 @@ def run_batched(args):
 
     sgs.use_torch_allocator()
     sgs.set_fp64_gemm_path(args.fp64_path == "fma")
+    sgs.set_tc_loader(args.tc_loader == "tma")
     prec = PRECISIONS[args.precision]
     ws = inp.batched_workloads(args.instances, n_bath=(16, args.max_bath))
     mine = ws[rank::world]

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(TcBatch g) {
                 for (int j = 0; j < 32; j++) {
                     const int c = n0 + c0 + j;
                     if (c >= g.n) continue;
-                    double x = g.alpha * (double)__uint_as_float(v[j]);
+                    const float x = (float)g.alpha * __uint_as_float(v[j]);   // alpha is +-1 here
                     if (g.skew) {
                         if (tm == tn && r <= c) {
                             if (r == c) {
@@ -259,15 +259,15 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(TcBatch g) {
                             continue;
                         }
                         if (g.out_f64) {
-                            static_cast<double*>(g.C[b])[(size_t)r * g.ldc + c] = x;
-                            static_cast<double*>(g.C[b])[(size_t)c * g.ldc + r] = -x;
+                            static_cast<double*>(g.C[b])[(size_t)r * g.ldc + c] = (double)x;
+                            static_cast<double*>(g.C[b])[(size_t)c * g.ldc + r] = -(double)x;
                         } else {
-                            static_cast<float*>(g.C[b])[(size_t)r * g.ldc + c] = (float)x;
-                            static_cast<float*>(g.C[b])[(size_t)c * g.ldc + r] = (float)-x;
+                            static_cast<float*>(g.C[b])[(size_t)r * g.ldc + c] = x;
+                            static_cast<float*>(g.C[b])[(size_t)c * g.ldc + r] = -x;
                         }
                     } else {
-                        if (g.out_f64) static_cast<double*>(g.C[b])[(size_t)r * g.ldc + c] = x;
-                        else static_cast<float*>(g.C[b])[(size_t)r * g.ldc + c] = (float)x;
+                        if (g.out_f64) static_cast<double*>(g.C[b])[(size_t)r * g.ldc + c] = (double)x;
+                        else static_cast<float*>(g.C[b])[(size_t)r * g.ldc + c] = x;
                     }
                 }
             }

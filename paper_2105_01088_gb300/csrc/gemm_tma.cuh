@@ -227,23 +227,20 @@ __global__ void __launch_bounds__(128) gemm_tma_kernel(const __grid_constant__ T
             for (int j = 0; j < 32; j++) tile[r * TS + c0 + j] = __uint_as_float(v[j]);
         }
         __syncthreads();
-        const double alpha = g.alpha;
-        auto put = [&](int row, int col, double x) {
-            if (g.out_f64) static_cast<double*>(g.C)[(size_t)b * g.c_stride + (size_t)row * g.ldc + col] = x;
-            else static_cast<float*>(g.C)[(size_t)b * g.c_stride + (size_t)row * g.ldc + col] = (float)x;
+        // fp32 epilogue (alpha is +-1 here; FP64 arithmetic is slow on this part)
+        const float alpha = (float)g.alpha;
+        auto put = [&](int row, int col, float x) {
+            if (g.out_f64) static_cast<double*>(g.C)[(size_t)b * g.c_stride + (size_t)row * g.ldc + col] = (double)x;
+            else static_cast<float*>(g.C)[(size_t)b * g.c_stride + (size_t)row * g.ldc + col] = x;
         };
         for (int e = tid; e < TMA_BM * TMA_BN; e += 128) {
             const int rr = e / TMA_BN, cc = e % TMA_BN;
             const int row = m0 + rr, col = n0 + cc;
             if (row >= g.m || col >= g.n) continue;
-            if (!g.skew) {
-                put(row, col, alpha * (double)tile[rr * TS + cc]);
-            } else if (tm != tn) {
-                put(row, col, alpha * (double)tile[rr * TS + cc]);
+            if (!g.skew || tm != tn) {
+                put(row, col, alpha * tile[rr * TS + cc]);
             } else {       // diagonal tile: lower part from the tile, upper part mirrored, zero diagonal
-                const double x = rr > cc ? alpha * (double)tile[rr * TS + cc]
-                                         : (rr < cc ? -alpha * (double)tile[cc * TS + rr] : 0.0);
-                put(row, col, x);
+                put(row, col, rr > cc ? alpha * tile[rr * TS + cc] : (rr < cc ? -alpha * tile[cc * TS + rr] : 0.0f));
             }
         }
         if (g.skew && tm != tn) {
@@ -252,7 +249,7 @@ __global__ void __launch_bounds__(128) gemm_tma_kernel(const __grid_constant__ T
                 const int cc = e / TMA_BM, rr = e % TMA_BM;
                 const int row = n0 + cc, col = m0 + rr;
                 if (row >= g.n || col >= g.m) continue;
-                put(row, col, -alpha * (double)tile[rr * TS + cc]);
+                put(row, col, -alpha * tile[rr * TS + cc]);
             }
         }
     }

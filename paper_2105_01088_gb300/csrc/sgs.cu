@@ -47,7 +47,7 @@ long long g_launches = 0;
 inline void counted() { ++g_launches; }
 
 // staging of the tensor-core operands: 1 = TMA tensor loads (default), 0 = cp.async
-int g_tc_tma = 0;
+int g_tc_tma = 1;
 
 sgs_alloc_fn g_alloc = nullptr;
 sgs_free_fn g_release = nullptr;
