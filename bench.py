@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--max-bath", type=int, default=64, help="batched: bath length L ~ U{16..max-bath}")
     ap.add_argument("--rate", type=float, default=100.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--requests", type=int, default=16, help="serving: number of requests")
-    ap.add_argument("--max-steps", type=int, default=300, help="serving: step cap per solve")
+    ap.add_argument("--max-steps", type=int, default=400, help="serving: step cap per solve")
+    ap.add_argument("--serving-dtau", type=float, default=0.2, help="serving: imaginary-time step")
     ap.add_argument("--rank", type=int, default=0, help="override the ansatz rank M (profiling cases)")
     ap.add_argument("--fp64-path", default="fma", choices=["fma", "mma"], help="FP64 product pipe")
     ap.add_argument("--tc-loader", default="tma", choices=["tma", "cp"], help="tensor-core operand staging")
@@ -360,10 +361,10 @@ def run_serving(args):
         w.step(3)
         w.close()
     solver = sgs.Solver(stream=stream, hbm_budget=budget)
-    loop = ServingLoop(solver, dtau=0.05, precision=prec, tol=1e-8, max_steps=args.max_steps)
+    loop = ServingLoop(solver, dtau=args.serving_dtau, precision=prec, tol=1e-8, max_steps=args.max_steps)
     res = loop.run(reqs)
     solver.close()
-    seq = run_sequential(lambda: sgs.Solver(stream=stream), reqs, dtau=0.05, precision=0, tol=1e-8,
+    seq = run_sequential(lambda: sgs.Solver(stream=stream), reqs, dtau=args.serving_dtau, precision=0, tol=1e-8,
                          max_steps=args.max_steps)
     a, b = latency_stats(res), latency_stats(seq)
     dE = max(abs(x.energy - y.energy) / abs(y.energy) for x, y in zip(res, seq))
@@ -373,7 +374,8 @@ def run_serving(args):
             "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": f"serving: {args.requests} Anderson solves, Poisson rate {args.rate}/s, "
                                    "bath L ~ U{8..40}, M in {4, 8}, U ~ U[0,8], V ~ U[0.2,1], run to |dE| < 1e-8 "
-                                   f"per step or {args.max_steps} steps", "hbm_budget_bytes": budget},
+                                   f"per step or {args.max_steps} steps at ds = {args.serving_dtau}",
+                       "hbm_budget_bytes": budget},
             "latency": {"p50_s": a["p50_s"], "p99_s": a["p99_s"], "mean_s": a["mean_s"]},
             "sequential_fp64": {"throughput_per_s": b["throughput_per_s"], "p50_s": b["p50_s"], "p99_s": b["p99_s"]},
             "converged": int(sum(r.converged for r in res)), "max_rel_energy_diff_vs_sequential_fp64": dE}

@@ -13,6 +13,14 @@
 #define SGS_DEV_EIG        4    // amplitude solver failed to converge / empty subspace
 #define SGS_DEV_EXPNORM    8    // exponential step needs more squarings than provisioned
 
+// fp32 -> nearest TF32 value (10 explicit mantissa bits; ties away from zero): add half
+// an ulp of TF32 to the magnitude bits, then clear the 13 dropped bits.  The tensor
+// core reads a TF32 operand by dropping those bits, i.e. truncating toward zero, a
+// bias that accumulates along product chains; operands rounded here carry none.
+__device__ __forceinline__ float round_tf32(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+}
+
 struct cplx { double x, y; };
 __device__ __forceinline__ cplx cmk(double a, double b) { cplx r; r.x = a; r.y = b; return r; }
 __device__ __forceinline__ cplx cadd(cplx a, cplx b) { return cmk(a.x + b.x, a.y + b.y); }

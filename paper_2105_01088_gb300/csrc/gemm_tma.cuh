@@ -41,6 +41,13 @@ struct TmaBatch {
     int skew;                       // 1: lower tiles only, write C and -C^T, zero diagonal
     int* err;
     int batch;
+    // optional epilogue terms (fp32 output, skew = 0): C = alpha A B + beta Cin + diag I,
+    // and a transposed copy CT = C^T
+    const float* Cin; long long cin_stride; int ldcin; float beta; float diag;
+    float* CT; long long ct_stride; int ldct;
+    // optional pass-through: batch b with pass_flag[b] <= pass_cmp skips the product and
+    // copies Cin (C = Cin, CT = Cin^T)
+    const int* pass_flag; int pass_cmp;
 };
 
 template <int KIND> struct TmaCfg {
@@ -148,7 +155,8 @@ __global__ void __launch_bounds__(128) gemm_tma_kernel(const __grid_constant__ T
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    const int nk = (g.k + KSLAB - 1) / KSLAB;
+    const bool pass = g.pass_flag && g.pass_flag[b] <= g.pass_cmp;     // uniform in the CTA
+    const int nk = pass ? 0 : (g.k + KSLAB - 1) / KSLAB;
 
     if (tid == 0) {
         // producer
@@ -202,14 +210,23 @@ __global__ void __launch_bounds__(128) gemm_tma_kernel(const __grid_constant__ T
     __syncthreads();
     bool ok = mbar_wait(smem_u32(&done), 0u, g.err);
     asm volatile("tcgen05.fence::after_thread_sync;");
-    ok = __syncthreads_and(ok && abort_flag == 0 && nk > 0);
+    ok = __syncthreads_and(ok && abort_flag == 0 && (nk > 0 || pass));
 
     if (ok) {
-        // TMEM -> padded shared tile (row stride 129 floats: conflict-free both ways)
+        // TMEM (or, passing through, Cin) -> padded shared tile (row stride 129 floats:
+        // conflict-free both ways)
         float* tile = reinterpret_cast<float*>(gbase);
         constexpr int TS = TMA_BN + 1;
         const int r = warp * 32 + lane;
-        for (int c0 = 0; c0 < TMA_BN; c0 += 32) {
+        if (pass) {
+            for (int e = tid; e < TMA_BM * TMA_BN; e += 128) {
+                const int rr = e / TMA_BN, cc = e % TMA_BN;
+                const int row = m0 + rr, col = n0 + cc;
+                tile[rr * TS + cc] = (row < g.m && col < g.n)
+                                         ? g.Cin[(size_t)b * g.cin_stride + (size_t)row * g.ldcin + col] : 0.0f;
+            }
+        }
+        for (int c0 = 0; c0 < TMA_BN && !pass; c0 += 32) {
             uint32_t v[32];
             const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + c0;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -227,8 +244,9 @@ __global__ void __launch_bounds__(128) gemm_tma_kernel(const __grid_constant__ T
             for (int j = 0; j < 32; j++) tile[r * TS + c0 + j] = __uint_as_float(v[j]);
         }
         __syncthreads();
-        // fp32 epilogue (alpha is +-1 here; FP64 arithmetic is slow on this part)
-        const float alpha = (float)g.alpha;
+        // fp32 epilogue (FP64 arithmetic is slow on this part)
+        const float alpha = pass ? 1.0f : (float)g.alpha;
+        const bool extra = !pass && (g.Cin || g.diag != 0.0f);
         auto put = [&](int row, int col, float x) {
             if (g.out_f64) static_cast<double*>(g.C)[(size_t)b * g.c_stride + (size_t)row * g.ldc + col] = (double)x;
             else static_cast<float*>(g.C)[(size_t)b * g.c_stride + (size_t)row * g.ldc + col] = x;
@@ -238,9 +256,26 @@ __global__ void __launch_bounds__(128) gemm_tma_kernel(const __grid_constant__ T
             const int row = m0 + rr, col = n0 + cc;
             if (row >= g.m || col >= g.n) continue;
             if (!g.skew || tm != tn) {
-                put(row, col, alpha * tile[rr * TS + cc]);
+                float x = alpha * tile[rr * TS + cc];
+                if (extra) {
+                    if (g.Cin) x += g.beta * g.Cin[(size_t)b * g.cin_stride + (size_t)row * g.ldcin + col];
+                    if (row == col) x += g.diag;
+                    tile[rr * TS + cc] = x;            // kept for the transposed copy
+                }
+                put(row, col, x);
             } else {       // diagonal tile: lower part from the tile, upper part mirrored, zero diagonal
                 put(row, col, rr > cc ? alpha * tile[rr * TS + cc] : (rr < cc ? -alpha * tile[cc * TS + rr] : 0.0f));
+            }
+        }
+        if (g.CT) {
+            // CT[n0 + cc][m0 + rr] = C[m0 + rr][n0 + cc], rows of CT coalesced
+            __syncthreads();
+            const float a2 = extra ? 1.0f : alpha;
+            for (int e = tid; e < TMA_BM * TMA_BN; e += 128) {
+                const int cc = e / TMA_BM, rr = e % TMA_BM;
+                const int row = n0 + cc, col = m0 + rr;
+                if (row >= g.n || col >= g.m) continue;
+                g.CT[(size_t)b * g.ct_stride + (size_t)row * g.ldct + col] = a2 * tile[rr * TS + cc];
             }
         }
         if (g.skew && tm != tn) {

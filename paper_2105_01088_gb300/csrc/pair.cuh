@@ -263,7 +263,7 @@ __global__ void lp_convert_kernel(const S* const* src, const double* const* src2
             static_cast<float*>(hi[b])[e] = h;
             static_cast<float*>(lo[b])[e] = (float)(x - (double)h);
         } else {
-            static_cast<float*>(hi[b])[e] = (float)x;
+            static_cast<float*>(hi[b])[e] = round_tf32((float)x);
         }
     }
 }

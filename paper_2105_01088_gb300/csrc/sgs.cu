@@ -30,6 +30,7 @@
 #include "eig.cuh"
 #include "eom.cuh"
 #include "update.cuh"
+#include "update_lp.cuh"
 #include "probe.cuh"
 #include "gemm_tc.cuh"
 #include "gemm_tma.cuh"
@@ -110,6 +111,14 @@ struct Instance {
     float *wr32 = nullptr, *va32 = nullptr, *xa32 = nullptr;
     TmaBatch tma_w{}, tma_v{}, tma_x{};   // TMA-fed products W = T1 S^{-1}, V = D W, X = V D
     bool tma_ok = false;
+    // mixed-precision state update: fp32 masters [M][n][ldp] (0 X_s, 1-2 Q, 3 E^T, 4 E, 5 E^T,
+    // 6 E, 7 F, 8 G) and tensor-core operands (0 Gamma, 1 dGamma, 2 + j = master j, j < 8)
+    bool u_ok = false;
+    float* u_y = nullptr;
+    float* u_f32[9] = {};
+    void* u_hi[10] = {};
+    void* u_lo[10] = {};
+    CUtensorMap u_map_hi[10], u_map_lo[10];
     void **q_si_hi = nullptr, **q_si_lo = nullptr, **q_t1_hi = nullptr, **q_t1_lo = nullptr, **q_d_hi = nullptr,
          **q_d_lo = nullptr, **q_wr_hi = nullptr, **q_wr_lo = nullptr, **q_va_hi = nullptr, **q_va_lo = nullptr,
          **q_wr32 = nullptr, **q_va32 = nullptr, **q_xa32 = nullptr;
@@ -289,6 +298,8 @@ size_t instance_bytes(int n, int M, int prec, int nimp, bool tune) {
         const size_t ldp = (n + 7) & ~7, esz = (prec == SGS_MIXED_BF16) ? 2 : 4;
         const size_t ops = (prec == SGS_FP32_3XTF32) ? 10 : 5;
         bytes += P * n * ldp * esz * ops + 3 * P * nn * 4;
+        if (prec != SGS_FP32_3XTF32)
+            bytes += (size_t)M * nn * 4 + (size_t)M * n * ldp * (9 * 4 + 10 * esz);   // mixed update
     }
     return bytes + (1 << 20);
 }
@@ -555,13 +566,9 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         const size_t bytes = (size_t)P * lpn * esz;
         I.si_hi = c->dalloc(bytes); I.t1_hi = c->dalloc(bytes); I.d_hi = c->dalloc(bytes);
         I.wr32 = c->alloc<float>(P * nn); I.va32 = c->alloc<float>(P * nn); I.xa32 = c->alloc<float>(P * nn);
-        if (I.tc_kind == TC_TF32 && I.ldp == n) {
-            I.wr_hi = I.wr32;   // fp32 results feed the next product directly
-            I.va_hi = I.va32;
-        } else {
-            I.wr_hi = c->dalloc(bytes);
-            I.va_hi = c->dalloc(bytes);
-        }
+        // fp32 results become operands through a rounding conversion (TF32: to nearest)
+        I.wr_hi = c->dalloc(bytes);
+        I.va_hi = c->dalloc(bytes);
         if (split) {
             I.si_lo = c->dalloc(bytes); I.t1_lo = c->dalloc(bytes); I.d_lo = c->dalloc(bytes);
             I.wr_lo = c->dalloc(bytes); I.va_lo = c->dalloc(bytes);
@@ -596,6 +603,28 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
                    prod(I.tma_v, I.d_hi, I.d_lo, I.wr_hi, I.wr_lo, I.va32, 0) &&
                    prod(I.tma_x, I.va_hi, I.va_lo, I.d_hi, I.d_lo, I.xa32, 1);
         if (g_tc_tma && !I.tma_ok) { c->err = "tensor map encoding failed"; return SGS_ECUDA; }
+
+        // mixed-precision state update (TMA-fed products; TF32 and BF16 forms): 3xTF32 keeps
+        // the FP64 update, since its products accumulate in fp32 and would hold the step to
+        // ~1e-6 relative, below the form's purpose
+        if (I.tma_ok && I.tc_kind != TC_3XTF32) {
+            const size_t mp = (size_t)M * n * I.ldp;
+            I.u_y = c->alloc<float>((size_t)M * nn);
+            bool ok = I.u_y != nullptr;
+            for (int j = 0; j < 9 && ok; j++) {
+                I.u_f32[j] = c->alloc<float>(mp);
+                ok = I.u_f32[j] != nullptr && cudaMemsetAsync(I.u_f32[j], 0, mp * sizeof(float), c->stream) == cudaSuccess;
+            }
+            for (int i = 0; i < 10 && ok; i++) {
+                I.u_hi[i] = c->dalloc(mp * esz);       // rounded operand copies of the fp32 results
+                ok = I.u_hi[i] != nullptr;
+                if (ok && split) ok = (I.u_lo[i] = c->dalloc(mp * esz)) != nullptr;
+                if (ok) ok = make_operand_map(&I.u_map_hi[i], I.u_hi[i], bf, I.ldp, n, M);
+                if (ok && split) ok = make_operand_map(&I.u_map_lo[i], I.u_lo[i], bf, I.ldp, n, M);
+            }
+            if (!ok) { c->err = "device allocation failed (mixed-precision update)"; return SGS_ENOMEM; }
+            I.u_ok = true;
+        }
     }
     return SGS_OK;
 }
@@ -865,7 +894,6 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         const unsigned gch = grid_chunks(nn, 256, 64);
         pair_sparse_right_kernel<<<dim3(gch, P), 256, 0, st>>>(d, I.si, I.fimp, I.work);
         const int ldp = I.ldp;
-        const bool direct = (I.wr_hi == I.wr32);   // fp32 results used as operands as they are
         lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_si, nullptr, I.q_si_hi,
                                                                   I.q_si_lo, n, ldp, kind);
         lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_work, nullptr, I.q_t1_hi,
@@ -883,11 +911,9 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         const bool tma = g_tc_tma && I.tma_ok;
         if ((e = tma ? gemm_tma(I.tma_w, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
         counted();
-        if (!direct) {
-            lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_wr32, nullptr, I.q_wr_hi,
-                                                                     I.q_wr_lo, n, ldp, kind);
-            counted();
-        }
+        lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_wr32, nullptr, I.q_wr_hi,
+                                                                 I.q_wr_lo, n, ldp, kind);
+        counted();
         c->stage(SGS_STAGE_EOM_V);
         c->stage_flops[SGS_STAGE_EOM_V] += 2.0 * n3 * P;
         t.A = (const void* const*)I.q_d_hi; t.A2 = (const void* const*)I.q_d_lo;
@@ -897,11 +923,9 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         counted();
         c->stage(SGS_STAGE_EOM_X);
         c->stage_flops[SGS_STAGE_EOM_X] += n3 * P;
-        if (!direct) {
-            lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_va32, nullptr, I.q_va_hi,
-                                                                     I.q_va_lo, n, ldp, kind);
-            counted();
-        }
+        lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_va32, nullptr, I.q_va_hi,
+                                                                 I.q_va_lo, n, ldp, kind);
+        counted();
         t.A = (const void* const*)I.q_va_hi; t.A2 = (const void* const*)I.q_va_lo;
         t.B = (const void* const*)I.q_d_hi; t.B2 = (const void* const*)I.q_d_lo;
         t.C = I.q_xa32; t.skew = 1;
@@ -1009,7 +1033,88 @@ cudaError_t polar_pass(sgs_ctx* c, Instance& I, int iters, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// the mixed forms' state update: products on the tensor cores, sums and purification in FP64
+TmaBatch lp_product(const Instance& I, int a_op, int b_op, double alpha, float* C, int ldc, long long cstride) {
+    TmaBatch t{};
+    t.ta = I.u_map_hi[a_op];
+    t.tb = I.u_map_hi[b_op];
+    if (I.tc_kind == TC_3XTF32) { t.ta2 = I.u_map_lo[a_op]; t.tb2 = I.u_map_lo[b_op]; }
+    t.m = t.n = t.k = I.n;
+    t.alpha = alpha;
+    t.C = C; t.ldc = ldc; t.c_stride = cstride;
+    t.out_f64 = 0; t.skew = 0; t.err = I.err; t.batch = I.M;
+    return t;
+}
+
+cudaError_t update_pass_lp(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    const int n = I.n, M = I.M, ldp = I.ldp, kind = I.tc_kind;
+    const size_t nn = (size_t)n * n, np = (size_t)n * ldp, mp = (size_t)M * np;
+    const double n3 = (double)n * n * n;
+    cudaError_t e;
+    c->stage(SGS_STAGE_UPDATE);
+    // Gamma dGamma 2, four Horner products 8, E^T 2, F 2, G 2, purification 2 per iteration
+    // (squarings are added when profiles are read)
+    c->stage_flops[SGS_STAGE_UPDATE] += (16.0 + 2.0 * LP_NS_ITERS) * n3 * M;
+    const unsigned gch = grid_chunks(np, 256, 256);
+    auto split = [&](int f32, int op) {
+        lp_split_kernel<<<grid_chunks(mp, 256, 4096), 256, 0, st>>>(I.u_f32[f32], I.u_hi[op], I.u_lo[op], mp, kind);
+        counted();
+    };
+    auto run = [&](const TmaBatch& t) { counted(); return gemm_tma(t, kind, st); };
+    lp_from_f64_kernel<<<dim3(gch, M), 256, 0, st>>>(I.gamma, n, ldp, I.u_hi[0], I.u_lo[0], kind);
+    lp_from_f64_kernel<<<dim3(gch, M), 256, 0, st>>>(I.dgamma, n, ldp, I.u_hi[1], I.u_lo[1], kind);
+    counted(); counted();
+    // Y = Gamma dGamma (dGamma antisymmetric: its K-major form is -dGamma)
+    if ((e = run(lp_product(I, 0, 1, -1.0, I.u_y, n, (long long)nn))) != cudaSuccess) return e;
+    exp_prepare_lp_kernel<<<M, 1024, 0, st>>>(I.u_y, n, ldp, I.dtau, I.u_f32[0], I.u_f32[1], I.sq, I.err);
+    counted();
+    split(0, 2);
+    split(1, 3);
+    // Horner on transposes: Q_j = I + (1/j) Q_{j+1} X_s^T (X_s^T's K-major form is X_s)
+    int cur = 1, nxt = 2;
+    for (int j = EXP_LP_DEGREE - 1; j >= 2; j--) {
+        TmaBatch t = lp_product(I, 2 + cur, 2, 1.0 / j, I.u_f32[nxt], ldp, (long long)np);
+        t.diag = 1.0f;
+        if ((e = run(t)) != cudaSuccess) return e;
+        split(nxt, 2 + nxt);
+        std::swap(cur, nxt);
+    }
+    // E^T = Q_2 X_s^T, and E
+    {
+        TmaBatch t = lp_product(I, 2 + cur, 2, 1.0, I.u_f32[3], ldp, (long long)np);
+        t.CT = I.u_f32[4]; t.ldct = ldp; t.ct_stride = (long long)np;
+        if ((e = run(t)) != cudaSuccess) return e;
+        split(3, 5);
+        split(4, 6);
+    }
+    // squarings E^T <- E^T E^T + 2 E^T (K-major form of E^T is E); states that need
+    // fewer pass theirs through
+    int et = 3, ee = 4, et2 = 5, ee2 = 6;
+    for (int j = 0; j < EXP_MAX_SQUARINGS; j++) {
+        TmaBatch t = lp_product(I, 2 + et, 2 + ee, 1.0, I.u_f32[et2], ldp, (long long)np);
+        t.Cin = I.u_f32[et]; t.ldcin = ldp; t.cin_stride = (long long)np; t.beta = 2.0f;
+        t.CT = I.u_f32[ee2]; t.ldct = ldp; t.ct_stride = (long long)np;
+        t.pass_flag = I.sq; t.pass_cmp = j;
+        if ((e = run(t)) != cudaSuccess) return e;
+        split(et2, 2 + et2);
+        split(ee2, 2 + ee2);
+        std::swap(et, et2);
+        std::swap(ee, ee2);
+    }
+    // F = E Gamma (Gamma's K-major form is -Gamma), G = F E^T (K-major form E)
+    if ((e = run(lp_product(I, 2 + ee, 0, -1.0, I.u_f32[7], ldp, (long long)np))) != cudaSuccess) return e;
+    split(7, 9);
+    if ((e = run(lp_product(I, 9, 2 + ee, 1.0, I.u_f32[8], ldp, (long long)np))) != cudaSuccess) return e;
+    assemble_lp_kernel<<<dim3(grid_chunks(nn, 256, 256), M), 256, 0, st>>>(I.gamma, I.u_f32[7], I.u_f32[8], n, ldp,
+                                                                          I.s[4]);
+    counted();
+    if ((e = polar_pass(c, I, LP_NS_ITERS, st)) != cudaSuccess) return e;
+    I.steps_since_profile++;
+    return cudaGetLastError();
+}
+
 cudaError_t update_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    if (I.u_ok && I.integrator == SGS_INTEGRATOR_EXP) return update_pass_lp(c, I, st);
     const int n = I.n, M = I.M;
     const size_t nn = (size_t)n * n;
     const double n3 = (double)n * n * n;
@@ -1814,7 +1919,11 @@ sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, i
                         std::memcpy(hi + 4 * e, &th, 4);
                         std::memcpy(lo + 4 * e, &tl, 4);
                     } else {
-                        std::memcpy(hi + 4 * e, &h, 4);
+                        // nearest TF32 value, as the device-side conversions round
+                        uint32_t u;
+                        std::memcpy(&u, &h, 4);
+                        u = (u + 0x1000u) & 0xffffe000u;
+                        std::memcpy(hi + 4 * e, &u, 4);
                     }
                 }
             }

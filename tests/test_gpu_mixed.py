@@ -16,6 +16,10 @@ pytestmark = pytest.mark.gpu
 
 DG_TOL = {1: 1e-2, 2: 6e-2, 3: 1e-5}
 E_TOL = {1: 2e-4, 2: 2e-3, 3: 1e-7}
+# the state update of the TF32 and BF16 forms (exponential on the tensor cores, FP64 sums
+# and purification; 3xTF32 updates in FP64): deviation from the exact step, relative to the
+# step ds max|dGamma|.  Measured: TF32 3.8e-4, BF16 2.8e-3.
+UPD_TOL = {1: 3e-3, 2: 2e-2, 3: 1e-9}
 
 
 @pytest.fixture(scope="module")
@@ -63,3 +67,26 @@ def test_mixed_trajectory_energy(pkg, prec):
     n = 2 * p.n_modes
     for G in gg:
         assert np.abs(G @ G + np.eye(n)).max() < 1e-12     # purity kept in FP64
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_mixed_update_against_exact_step(pkg, prec):
+    """Gamma after one step equals the exact orthogonal step (oracle expm) taken with
+    the GPU's own dGamma, to the tensor-core rounding of the step's size; the
+    result is pure to FP64 rounding."""
+    p = inp.AndersonParams(n_bath=40, U=4.0, eps_d=-2.0, V=0.5)       # n = 164: ragged tiles
+    rng = np.random.default_rng(33)
+    g = inp.clustered_pure_gammas(p.n_modes, 5, rng, 1, spread=1.0)
+    lam = inp.random_amplitudes(5, rng)
+    s = _solver(pkg, p, g, lam, prec, dtau=0.2)
+    s.step(1)
+    dg = s.derivative()
+    g1, _ = s.get_state()
+    n = 2 * p.n_modes
+    errs = []
+    for mu in range(5):
+        go = orc.purify(orc.orthogonal_step(g[mu], dg[mu], 0.2))
+        errs.append(np.abs(g1[mu] - go).max() / (0.2 * np.abs(dg[mu]).max()))
+        assert np.abs(g1[mu] @ g1[mu] + np.eye(n)).max() < 1e-12
+    print(f"precision {prec}: update deviation relative to the step {max(errs):.3e}")
+    assert max(errs) < UPD_TOL[prec]

@@ -51,6 +51,8 @@ def test_tma_and_cp_async_staging_agree(pkg, kind):
 
 @pytest.mark.parametrize("prec", [1, 2, 3])
 def test_mixed_step_identical_under_both_stagings(pkg, prec):
+    """The loader switch applies to the equation of motion's products; the state
+    update always runs on the TMA-fed kernel.  Both give identical steps."""
     import sgs_inputs as inp
     p = inp.AndersonParams(n_bath=40, U=4.0, eps_d=-2.0, V=0.5)        # n = 164: ragged 128-tiles
     rng = np.random.default_rng(3)
