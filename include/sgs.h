@@ -122,6 +122,13 @@ sgs_status sgs_admit(sgs_ctx* ctx, const sgs_model* model, const sgs_options* op
 sgs_status sgs_retire(sgs_ctx* ctx, int slot);
 size_t sgs_bytes_in_use(const sgs_ctx* ctx);
 
+/* Index of the instance whose device-side error (SGS_ESINGULAR, SGS_ENOTCONV,
+ * SGS_ETIMEOUT) ended the last call, or -1.  The other instances of that
+ * sgs_step completed the failing step (their states advanced) but its
+ * energies were not returned; a request loop retires the failed slot and
+ * carries on. */
+int sgs_failed_instance(const sgs_ctx* ctx);
+
 /* Autotuning of the factorisation tile shapes.  With enable = 1, sgs_admit
  * (and sgs_add_state) times the candidate panel widths of the blocked
  * Gauss-Jordan inverse (8, 16, 32, 64 columns, as shared memory allows) and

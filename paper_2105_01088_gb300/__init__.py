@@ -63,6 +63,7 @@ SIGNATURES = {
     "sgs_bytes_in_use": (ctypes.c_size_t, [_ctxp]),
     "sgs_add_state": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, ctypes.c_int]),
     "sgs_set_autotune": (ctypes.c_int, [_ctxp, ctypes.c_int]),
+    "sgs_failed_instance": (ctypes.c_int, [_ctxp]),
     "sgs_get_tuning": (ctypes.c_int, [_ctxp, ctypes.c_int, _ip, _ip, _ip]),
     "sgs_set_graphs": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_energy": (ctypes.c_int, [_ctxp, _dp]),
@@ -277,6 +278,10 @@ class Solver:
 
     def bytes_in_use(self):
         return int(_lib.sgs_bytes_in_use(self._ctx))
+
+    def failed_instance(self):
+        """Slot whose device-side error ended the last call (-1: none)."""
+        return int(_lib.sgs_failed_instance(self._ctx))
 
     def tuning(self, slot=0):
         """(Gauss-Jordan panel width, Pfaffian panel width, source) of a slot;

@@ -19,7 +19,7 @@
 
 namespace sgs {
 
-#define RENYI_MAX_DIM 104     // 2 * 2 N_A <= 104: impurity + up to 12 sites
+#define RENYI_MAX_DIM 104     // 2 * 2 N_A <= 104 (impurity + up to 12 sites) in one CTA's shared memory
 
 // blocks[u] = Delta^{ab}_A (complex, na2 x na2), w[u] = lambda_a conj(lambda_b) G_ba, u = a M + b
 __global__ void renyi_blocks_kernel(InstDev d, const double* si, const double* imd, const double* Gm,
@@ -138,6 +138,66 @@ __global__ void __launch_bounds__(256) renyi_pf_kernel(const double* blocks, con
             const cplx wu = cmk(w[2 * u], w[2 * u + 1]), wv = cmk(w[2 * v], w[2 * v + 1]);
             cplx x = cmul(cmul(wu, wv), cmk(s_pr, s_pi));
             const double mag = exp(s_log + log_norm) * (u < v ? 2.0 : 1.0);
+            tr = x.x * mag;
+            ti = x.y * mag;
+        }
+        partial[2 * q] = tr;
+        partial[2 * q + 1] = ti;
+    }
+}
+
+// Subsystems too large for one CTA's shared memory: the Pfaffians of a chunk of
+// pairs go through the batched blocked Pfaffian of the pair pass.  Z_q =
+// [[Delta_u, i 1], [-i 1, Delta_v]] in planes (re, im) of m x m, m = 2 na2; entries past
+// the last pair get the pairing matrix J (Pf = 1) and are ignored.
+__global__ void renyi_build_kernel(const double* blocks, long long q0, long long npairs, int na2, double* Y) {
+    const long long q = q0 + blockIdx.x;
+    const int m = 2 * na2;
+    const size_t mm = (size_t)m * m;
+    double* zr = Y + (size_t)blockIdx.x * 2 * mm;
+    double* zi = zr + mm;
+    if (q >= npairs) {
+        for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
+            const int r = (int)(e / m), c = (int)(e % m);
+            zr[e] = (c == r + 1 && (r & 1) == 0) ? 1.0 : ((r == c + 1 && (c & 1) == 0) ? -1.0 : 0.0);
+            zi[e] = 0.0;
+        }
+        return;
+    }
+    long long v = (long long)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+    while ((v + 1) * (v + 2) / 2 <= q) ++v;
+    while (v * (v + 1) / 2 > q) --v;
+    const long long u = q - v * (v + 1) / 2;
+    const double* Bu = blocks + (size_t)u * na2 * na2 * 2;
+    const double* Bv = blocks + (size_t)v * na2 * na2 * 2;
+    for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
+        const int r = (int)(e / m), c = (int)(e % m);
+        double xr = 0.0, xi = 0.0;
+        if (r < na2 && c < na2) { xr = Bu[2 * (r * na2 + c)]; xi = Bu[2 * (r * na2 + c) + 1]; }
+        else if (r >= na2 && c >= na2) { xr = Bv[2 * ((r - na2) * na2 + c - na2)]; xi = Bv[2 * ((r - na2) * na2 + c - na2) + 1]; }
+        else if (c == r + na2) xi = 1.0;
+        else if (r == c + na2) xi = -1.0;
+        zr[e] = xr;
+        zi[e] = xi;
+    }
+}
+
+// T of each pair of the chunk from the Pfaffian (phase, log|Pf|)
+__global__ void renyi_combine_kernel(const double* logabs, const double* phase, const double* w, long long q0,
+                                     long long cnt, long long npairs, double log_norm, double* partial) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += (long long)gridDim.x * blockDim.x) {
+        const long long q = q0 + j;
+        if (q >= npairs) continue;
+        long long v = (long long)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+        while ((v + 1) * (v + 2) / 2 <= q) ++v;
+        while (v * (v + 1) / 2 > q) --v;
+        const long long u = q - v * (v + 1) / 2;
+        double tr = 0.0, ti = 0.0;
+        const double la = logabs[j];
+        if (la > -1e300) {
+            const cplx x = cmul(cmul(cmk(w[2 * u], w[2 * u + 1]), cmk(w[2 * v], w[2 * v + 1])),
+                                cmk(phase[2 * j], phase[2 * j + 1]));
+            const double mag = exp(la + log_norm) * (u < v ? 2.0 : 1.0);
             tr = x.x * mag;
             ti = x.y * mag;
         }

@@ -98,6 +98,12 @@ struct Instance {
     int steps_since_profile = 0;
     double* corr_scratch = nullptr;     // observables: partial sums, sites, outputs
     size_t corr_cap = 0;
+    double* renyi_scratch = nullptr;    // large Renyi subsystems: chunk of Pfaffian operands
+    size_t renyi_cap = 0;
+    long long renyi_chunk = 0;
+    int renyi_m = 0;
+    int* renyi_err = nullptr;
+    double **r_Y = nullptr, **r_TU = nullptr, **r_PK = nullptr, **r_upA = nullptr, **r_upB = nullptr, **r_upC = nullptr;
     double* eigscratch = nullptr;
     int* err = nullptr;
 
@@ -153,6 +159,7 @@ struct sgs_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::string err;
+    int failed = -1;                    // instance whose device error ended the last call
     std::vector<void*> allocs;
     int device = 0;
     Instance* owner = nullptr;          // instance being set up: its allocations are its own
@@ -1152,6 +1159,7 @@ cudaError_t update_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
 }
 
 sgs_status check_device_error(sgs_ctx* c) {
+    c->failed = -1;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     for (size_t i = 0; i < c->inst.size(); i++) {
         if (!c->inst[i].live) continue;
@@ -1159,6 +1167,7 @@ sgs_status check_device_error(sgs_ctx* c) {
         CUDA_TRY(c, cudaMemcpy(&e, c->inst[i].err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e) {
             CUDA_TRY(c, cudaMemset(c->inst[i].err, 0, sizeof(int)));
+            c->failed = (int)i;
             char buf[160];
             if (e & SGS_DEV_SINGULAR) {
                 snprintf(buf, sizeof buf, "instance %zu: two ansatz states have a singular Gamma_a + Gamma_b", i);
@@ -1190,6 +1199,63 @@ sgs_status ensure_ehist(sgs_ctx* c, Instance& I, int n) {
     if (!p) { c->err = "device allocation failed"; return SGS_ENOMEM; }
     I.Ehist = p;
     I.Ecap = n;
+    return SGS_OK;
+}
+
+// Renyi-2 terms of subsystems too large for the shared-memory Pfaffian: chunks of pairs
+// through the batched blocked Pfaffian (the phase Pfaffians' kernels), scratch owned by
+// the instance and reused
+sgs_status renyi_large(sgs_ctx* c, Instance& I, const double* blocks, const double* wts, long long npairs, int na2,
+                       double log_norm, double* partial) {
+    cudaStream_t st = c->stream;
+    const int m = 2 * na2, bs = std::min(16, m / 2);
+    const size_t mm = (size_t)m * m;
+    const size_t per = 2 * mm + 4 * (size_t)m * bs + 16 * (size_t)m * bs + 3;     // doubles per chunk entry
+    const long long chunk = std::max<long long>(1, std::min<long long>(npairs, (long long)((1ull << 30) / (per * 8))));
+    const size_t need = (size_t)chunk * per + 8;
+    if (I.renyi_cap < need || I.renyi_chunk != chunk || I.renyi_m != m) {
+        c->owner = &I;
+        I.renyi_scratch = c->alloc<double>(need);
+        if (!I.renyi_scratch) { c->owner = nullptr; c->err = "device allocation failed"; return SGS_ENOMEM; }
+        double* Y = I.renyi_scratch;
+        double* TU = Y + (size_t)chunk * 2 * mm;
+        double* PK = TU + (size_t)chunk * 4 * m * bs;
+        const size_t blk = (size_t)m * 4 * bs;
+        std::vector<double*> y, tu, pk, upA, upB, upC;
+        for (long long q = 0; q < chunk; q++) {
+            y.push_back(Y + (size_t)q * 2 * mm);
+            tu.push_back(TU + (size_t)q * 4 * m * bs);
+            pk.push_back(PK + (size_t)q * 4 * blk);
+        }
+        for (long long q = 0; q < chunk; q++) { upA.push_back(pk[q]); upB.push_back(pk[q] + blk); upC.push_back(y[q]); }
+        for (long long q = 0; q < chunk; q++) { upA.push_back(pk[q] + 2 * blk); upB.push_back(pk[q] + 3 * blk); upC.push_back(y[q] + mm); }
+        I.r_Y = upload_ptrs(c, y); I.r_TU = upload_ptrs(c, tu); I.r_PK = upload_ptrs(c, pk);
+        I.r_upA = upload_ptrs(c, upA); I.r_upB = upload_ptrs(c, upB); I.r_upC = upload_ptrs(c, upC);
+        I.renyi_err = c->alloc<int>(1);
+        c->owner = nullptr;
+        if (!I.r_Y || !I.r_TU || !I.r_PK || !I.r_upA || !I.r_upB || !I.r_upC || !I.renyi_err) {
+            c->err = "device allocation failed";
+            return SGS_ENOMEM;
+        }
+        I.renyi_cap = need;
+        I.renyi_chunk = chunk;
+        I.renyi_m = m;
+    }
+    double* Y = I.renyi_scratch;
+    double* logabs = Y + (size_t)chunk * (2 * mm + 20 * (size_t)m * bs);
+    double* phase = logabs + chunk;
+    for (long long q0 = 0; q0 < npairs; q0 += chunk) {
+        renyi_build_kernel<<<(unsigned)chunk, 256, 0, st>>>(blocks, q0, npairs, na2, Y);
+        counted();
+        cudaError_t e = launch_pf(c, m, (int)chunk, bs, I.r_Y, I.r_TU, I.r_PK, I.r_upA, I.r_upB, I.r_upC, logabs,
+                                  phase, I.renyi_err, st);
+        if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return SGS_ECUDA; }
+        renyi_combine_kernel<<<(unsigned)((chunk + 255) / 256), 256, 0, st>>>(logabs, phase, wts, q0, chunk, npairs,
+                                                                             log_norm, partial);
+        counted();
+    }
+    // a zero Pfaffian is a zero term here, not an error
+    CUDA_TRY(c, cudaMemsetAsync(I.renyi_err, 0, sizeof(int), st));
     return SGS_OK;
 }
 
@@ -1274,6 +1340,8 @@ sgs_status sgs_retire(sgs_ctx* c, int slot) {
 }
 
 size_t sgs_bytes_in_use(const sgs_ctx* c) { return c ? c->bytes_in_use : 0; }
+
+int sgs_failed_instance(const sgs_ctx* c) { return c ? c->failed : -1; }
 
 sgs_status sgs_set_autotune(sgs_ctx* c, int enable) {
     if (!c) return SGS_EINVAL;
@@ -1532,8 +1600,8 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
     if (kind == SGS_CORR_RENYI2) {
         for (int i = 0; i < n_sites; i++) {
             const int na2 = 4 * (1 + sites[i]);
-            if (sites[i] < 0 || na2 > I.n || 2 * na2 > RENYI_MAX_DIM) {
-                c->err = "Renyi-2 subsystem out of range (impurity + l sites, 4(1+l) <= 2N, l <= 12)";
+            if (sites[i] < 0 || na2 > I.n) {
+                c->err = "Renyi-2 subsystem out of range (impurity + l sites, 4(1+l) <= 2N)";
                 return SGS_EINVAL;
             }
         }
@@ -1561,15 +1629,22 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
             const int m = 2 * na2;
             renyi_blocks_kernel<<<(unsigned)M2, 128, 0, c->stream>>>(I.dev(), I.si, I.imd, I.Gm, I.lam, I.pair_index,
                                                                      na2, blocks, wts);
-            const size_t smem = 2 * (size_t)m * (m + 1) * sizeof(double);
-            set_kernel_attributes();
-            const unsigned gx = (unsigned)std::min<long long>(npairs, 65535);
-            const unsigned gy = (unsigned)((npairs + gx - 1) / gx);
-            renyi_pf_kernel<<<dim3(gx, gy), 256, smem, c->stream>>>(blocks, wts, npairs, na2,
-                                                                     -(na2 / 2) * 0.6931471805599453, partial);
+            counted();
+            const double log_norm = -(na2 / 2) * 0.6931471805599453;
+            if (m <= RENYI_MAX_DIM) {
+                const size_t smem = 2 * (size_t)m * (m + 1) * sizeof(double);
+                set_kernel_attributes();
+                const unsigned gx = (unsigned)std::min<long long>(npairs, 65535);
+                const unsigned gy = (unsigned)((npairs + gx - 1) / gx);
+                renyi_pf_kernel<<<dim3(gx, gy), 256, smem, c->stream>>>(blocks, wts, npairs, na2, log_norm, partial);
+                counted();
+            } else {
+                sgs_status rs = renyi_large(c, I, blocks, wts, npairs, na2, log_norm, partial);
+                if (rs != SGS_OK) return rs;
+            }
             complex_sum_kernel<<<nred, 256, 0, c->stream>>>(partial, npairs, sums);
             complex_sum_kernel<<<1, 256, 0, c->stream>>>(sums, nred, sums + 2 * nred);
-            counted(); counted(); counted(); counted();
+            counted(); counted();
             double tr[2];
             CUDA_TRY(c, cudaMemcpyAsync(tr, sums + 2 * nred, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
             CUDA_TRY(c, cudaStreamSynchronize(c->stream));

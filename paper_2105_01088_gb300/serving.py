@@ -21,6 +21,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 SGS_ENOMEM = 2
+SGS_DEVICE_FAILURES = (3, 4, 5)      # ESINGULAR, ENOTCONV, ETIMEOUT: one slot's solve failed
 
 
 @dataclass
@@ -43,6 +44,7 @@ class Result:
     energy: float
     converged: bool
     energies: list = field(default_factory=list)
+    failed: str = ""                  # device-side error that ended the solve, if any
 
     @property
     def latency(self):
@@ -71,6 +73,7 @@ class ServingLoop:
         self.clock, self.sleep = clock, sleep
         self.keep_energies = keep_energies
         self.rejected = []
+        self.failures = []
 
     def _admit(self, req):
         return self.solver.admit(req.model, req.gamma0, req.lambda0, self.dtau, self.precision, self.cmode,
@@ -101,7 +104,23 @@ class ServingLoop:
                 if pending:
                     self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
                 continue
-            E = self.solver.step(1)
+            try:
+                E = self.solver.step(1)
+            except Exception as e:                          # noqa: BLE001 (status carried on the error)
+                bad = self.solver.failed_instance() if hasattr(self.solver, "failed_instance") else -1
+                if getattr(e, "status", None) not in SGS_DEVICE_FAILURES or bad not in live:
+                    raise
+                # that slot's solve failed: retire it and report it; the others took the step
+                # (their energies of this step are not available)
+                st = live.pop(bad)
+                self.solver.retire(bad)
+                req = st[0]
+                now = self.clock() - t0
+                results.append(Result(req.rid, req.arrival, st[1], now, st[2], float("nan"), False, st[4], str(e)))
+                self.failures.append(req.rid)
+                for other in live.values():
+                    other[2] += 1
+                continue
             now = self.clock() - t0
             for slot in list(live):
                 st = live[slot]

@@ -111,3 +111,15 @@ def test_variance_several_monomials(pkg):
     Eo, vo = orc.variance(model, list(g))
     assert abs(E - Eo) <= TOL * abs(Eo)
     assert abs(var - vo) <= TOL * (Eo * Eo + abs(vo))
+
+
+def test_renyi2_large_subsystems(pkg):
+    """Subsystems past the shared-memory Pfaffian (4(1 + l) > 52) go through the
+    batched blocked Pfaffian in chunks; l = 12 is the last shared-memory size,
+    and the whole system (l = 16 here) has S_2 = 0."""
+    s, g, lam, G = _setup(pkg, 16, 3.0, -1.5, 0.6, 3, 13, True)
+    ls = [12, 13, 15, 16]
+    got = s.correlator(pkg.SGS_CORR_RENYI2, ls)
+    ref = np.array([orc.renyi2(list(g), lam, G, 2 * (1 + l)) for l in ls])
+    assert np.abs(got - ref).max() <= TOL * max(1.0, np.abs(ref).max())
+    assert abs(got[-1]) < 1e-10

@@ -84,3 +84,39 @@ def test_sequential_baseline_serialises():
     clk = FakeClock()
     res = run_sequential(lambda: FakeSolver(clk), _reqs([0.0, 0.0, 0.0]), tol=1e-6, clock=clk, sleep=clk.sleep)
     assert all(res[i].admitted >= res[i - 1].finished for i in range(1, 3))
+
+
+class FailingSolver(FakeSolver):
+    """Slot 1's solve fails on its third step (a device-side error reported for it)."""
+
+    def __init__(self, clock):
+        super().__init__(clock, capacity=3)
+        self.bad = -1
+
+    def step(self, n):
+        if len(self.slots) > 1 and self.live[1] and self.slots[1][1] == 2:
+            for i in range(len(self.slots)):
+                if self.live[i] and i != 1:
+                    self.slots[i][1] += 1
+            self.bad = 1
+            e = RuntimeError("SGS_ENOTCONV: instance 1: exponential step out of range")
+            e.status = 4
+            raise e
+        self.bad = -1
+        return super().step(n)
+
+    def failed_instance(self):
+        return self.bad
+
+
+def test_failed_solve_is_retired_and_reported():
+    clk = FakeClock()
+    s = FailingSolver(clk)
+    loop = ServingLoop(s, tol=1e-6, max_steps=100, clock=clk, sleep=clk.sleep)
+    res = loop.run(_reqs([0.0, 0.0, 0.0]))
+    assert loop.failures == [1]
+    bad = res[1]
+    assert bad.failed.startswith("SGS_ENOTCONV") and not bad.converged and np.isnan(bad.energy)
+    assert ("retire", 1, bad.finished) in s.log
+    for r in (res[0], res[2]):                      # the others finish normally
+        assert r.converged and not r.failed and abs(r.energy - (1.0 + r.rid)) < 1e-5
