@@ -190,7 +190,9 @@ typedef enum {
  * distance s from the impurity; for two channels interleaved (as
  * sgs_build_anderson lays them out) channel alpha's r-th site is
  * 1 + 2(r - 1) + alpha.  Renyi-2: A = sites 0..l (the leading 4(1 + l)
- * Majoranas), l <= 12.  Errors: SGS_EINVAL for sites out of range. */
+ * Majoranas, 4(1 + l) <= 2N); up to l = 12 each Pfaffian runs in one CTA's
+ * shared memory, beyond that in chunks through the batched blocked Pfaffian.
+ * Errors: SGS_EINVAL for sites out of range. */
 sgs_status sgs_correlator(sgs_ctx* ctx, int instance, sgs_corr_kind kind, const int* sites, int n_sites,
                           double* out);
 
