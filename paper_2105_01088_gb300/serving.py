@@ -151,14 +151,20 @@ def run_sequential(make_solver, requests, dtau=0.05, precision=0, cmode=0, tol=1
         start = clock() - t0
         solver = make_solver()
         slot = solver.admit(req.model, req.gamma0, req.lambda0, dtau, precision, cmode, req.parity)
-        last, steps, converged = None, 0, False
+        last, steps, converged, failed, e = None, 0, False, "", float("nan")
         while steps < max_steps:
-            e = float(solver.step(1)[slot, 0])
+            try:
+                e = float(solver.step(1)[slot, 0])
+            except Exception as err:                    # noqa: BLE001 (status carried on the error)
+                if getattr(err, "status", None) not in SGS_DEVICE_FAILURES:
+                    raise
+                failed, e = str(err), float("nan")
+                break
             steps += 1
             if last is not None and abs(e - last) < tol:
                 converged = True
                 break
             last = e
         solver.close()
-        results.append(Result(req.rid, req.arrival, start, clock() - t0, steps, e, converged))
+        results.append(Result(req.rid, req.arrival, start, clock() - t0, steps, e, converged, failed=failed))
     return results
