@@ -332,6 +332,18 @@ def run_sgs(args):
         t_step, sample = oracle_sample(w, n_pairs=6, n_states=2)
         line["cpu_baseline"] = {"value": 1.0 / t_step, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                                 "sample": sample}
+        # the same sample with one BLAS thread, in a child process (thread counts are fixed at import)
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = ("import bench, sgs_inputs; w = bench.workload(%r, %d); "
+                "t, s = bench.oracle_sample(w, n_pairs=2, n_states=1); print(t)" % (args.workload, args.rank))
+        try:
+            r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                               timeout=600)
+            t1 = float(r.stdout.strip().splitlines()[-1])
+            line["cpu_baseline_1_thread"] = {"value": 1.0 / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                             "sample": "2 pair evaluations + 1 state update, scaled to the step"}
+        except (subprocess.SubprocessError, ValueError, IndexError):
+            line["cpu_baseline_1_thread"] = None
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -86,8 +86,13 @@ typedef enum {
 } sgs_integrator;
 
 /* Per-instance options.  gamma0: [rank][n][n] pure states of one parity
- * (Pf Gamma = parity); lambda0: [rank] complex, may be NULL (the first solve
- * replaces the amplitudes).  stream: a cudaStream_t, or NULL for the
+ * (Pf Gamma = parity), or NULL for seeded random states: Gamma = O J O^T with O
+ * Haar on O(2N) (QR of a standard-normal matrix, signs of diag R folded in, first
+ * column negated to reach det O = parity), drawn from Philox4x32-10 keyed by
+ * `seed` (state mu's matrix entries 2j, 2j+1 from counter (j, mu, 0, 0) by
+ * Box-Muller on the first two words; the phase of lambda_mu, 2 pi x0 / 2^32,
+ * from counter (0, mu, 1, 0)).  lambda0: [rank] complex, may be NULL (the first
+ * solve replaces the amplitudes).  stream: a cudaStream_t, or NULL for the
  * context's own stream (the first instance's stream is used for all). */
 typedef struct {
     int rank;
@@ -99,12 +104,13 @@ typedef struct {
     const double* lambda0;
     void* stream;
     int integrator;          /* sgs_integrator (0: the exponential step) */
+    unsigned long long seed; /* initial states when gamma0 is NULL */
 } sgs_options;
 
 /* Create a context holding n_instances independent problems (models[i],
  * opts[i]); uploads the model and the initial states to device memory.
- * Errors: SGS_EINVAL (n_modes < 1, rank < 1 or > 64, parity not +-1,
- * gamma0 NULL), SGS_ENOMEM, SGS_ECUDA.  On error *out is NULL. */
+ * Errors: SGS_EINVAL (n_modes < 1, rank < 1 or > 64, parity not +-1),
+ * SGS_ENOMEM, SGS_ECUDA.  On error *out is NULL. */
 sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_instances, sgs_ctx** out);
 
 /* Continuous batching.  sgs_create makes an empty context on `stream` (NULL:
@@ -121,6 +127,11 @@ sgs_status sgs_create(void* stream, size_t hbm_budget, sgs_ctx** out);
 sgs_status sgs_admit(sgs_ctx* ctx, const sgs_model* model, const sgs_options* opts, int* slot);
 sgs_status sgs_retire(sgs_ctx* ctx, int slot);
 size_t sgs_bytes_in_use(const sgs_ctx* ctx);
+
+/* The seeded initial states sgs_admit generates when gamma0 is NULL (host only,
+ * no device work): gamma [rank][2N][2N], lambda [rank] complex (re, im). */
+sgs_status sgs_seeded_states(int n_modes, int rank, unsigned long long seed, int parity, double* gamma,
+                             double* lambda);
 
 /* Index of the instance whose device-side error (SGS_ESINGULAR, SGS_ENOTCONV,
  * SGS_ETIMEOUT) ended the last call, or -1.  The other instances of that

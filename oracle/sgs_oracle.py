@@ -282,33 +282,33 @@ def gram_and_hamiltonian(model, gammas):
     is the phase of G_ab.
     """
     M = len(gammas)
-    n = model.n
-    N = n // 2
     G = np.zeros((M, M), dtype=np.complex128)
     h = np.zeros((M, M), dtype=np.complex128)
-    logmag = np.zeros((M, M))
-    for a in range(M):
-        for b in range(M):
-            logmag[a, b] = 0.0 if a == b else log_overlap_magnitude(gammas[a], gammas[b])
-    pf0, _ = pfaffian_log(gammas[0])
     for a in range(M):
         G[a, a] = 1.0
         h[a, a] = wick_energy_density(model, gammas[a])
         for b in range(a + 1, M):
-            Dab = transition_matrix(gammas[a], gammas[b])
-            mag = math.exp(logmag[a, b])
-            if a == 0:
-                g = mag + 0.0j
-            else:
-                ph, _ = pfaffian_log(gammas[0] + Dab)
-                ph = ph * pf0
-                g = mag * ph / abs(ph)
-            G[a, b] = g
-            G[b, a] = np.conj(g)
-            # h_ba = <phi_b|H|phi_a> = G_ba * (Wick with Delta^{a,b})
-            h[b, a] = G[b, a] * wick_energy_density(model, Dab)
+            G[a, b], h[b, a] = pair_elements(model, gammas, a, b)
+            G[b, a] = np.conj(G[a, b])
             h[a, b] = np.conj(h[b, a])
     return G, h
+
+
+def pair_elements(model, gammas, a, b):
+    """(G_ab, h_ba) of one pair a < b in the gauge of the first state: the
+    magnitude from Pf(Ga + Gb), the phase from the Bargmann product with the
+    reference state (gram_and_hamiltonian), h_ba = G_ba * Wick(Delta^{a,b})."""
+    Dab = transition_matrix(gammas[a], gammas[b])
+    mag = math.exp(log_overlap_magnitude(gammas[a], gammas[b]))
+    if a == 0:
+        g = mag + 0.0j
+    else:
+        pf0, _ = pfaffian_log(gammas[0])
+        ph, _ = pfaffian_log(gammas[0] + Dab)
+        ph = ph * pf0
+        g = mag * ph / abs(ph)
+    # h_ba = <phi_b|H|phi_a> = G_ba * (Wick with Delta^{a,b})
+    return g, np.conj(g) * wick_energy_density(model, Dab)
 
 
 # ---------------------------------------------------------------------------
@@ -357,19 +357,20 @@ def coupling_constants(G, lam, mode=C_INVERSE, tiny=1e-300):
     return lt, c
 
 
-def eom(model, gammas, G, h, E, lam, mode=C_INVERSE):
+def eom(model, gammas, G, h, E, lam, mode=C_INVERSE, mus=None):
     """d Gamma^mu / ds of Eq. (EOM-Gamma3), for every state mu:
 
     2 Re{ lt_mu^* c_mu sum_beta lambda_beta [ 2i G_mu,beta [D, F]
           + 2 G_mu,beta (D F D + F) - (h_mu,beta - E G_mu,beta) D ] }
 
     with D = Delta^{beta,mu}, F = F^{beta,mu}; "+ c.c." of the paper is
-    X + X^* = 2 Re X.  Delta^{mu,mu} = Gamma^mu (Sec. III B).
+    X + X^* = 2 Re X.  Delta^{mu,mu} = Gamma^mu (Sec. III B).  ``mus``: the
+    states to evaluate (default all).
     """
     M = len(gammas)
     lt, c = coupling_constants(G, lam, mode)
     out = []
-    for mu in range(M):
+    for mu in (range(M) if mus is None else mus):
         acc = np.zeros((model.n, model.n), dtype=np.complex128)
         for beta in range(M):
             D = gammas[mu].astype(np.complex128) if beta == mu else transition_matrix(gammas[beta], gammas[mu])

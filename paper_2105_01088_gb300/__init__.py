@@ -42,7 +42,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int), ("dtau", ctypes.c_double), ("precision", ctypes.c_int),
                 ("cmode", ctypes.c_int), ("parity", ctypes.c_int), ("gamma0", ctypes.POINTER(ctypes.c_double)),
                 ("lambda0", ctypes.POINTER(ctypes.c_double)), ("stream", ctypes.c_void_p),
-                ("integrator", ctypes.c_int)]
+                ("integrator", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -64,6 +64,7 @@ SIGNATURES = {
     "sgs_add_state": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, ctypes.c_int]),
     "sgs_set_autotune": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_failed_instance": (ctypes.c_int, [_ctxp]),
+    "sgs_seeded_states": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, _dp, _dp]),
     "sgs_get_tuning": (ctypes.c_int, [_ctxp, ctypes.c_int, _ip, _ip, _ip]),
     "sgs_set_graphs": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_energy": (ctypes.c_int, [_ctxp, _dp]),
@@ -191,14 +192,31 @@ def build_2ck(L, J, t=0.5) -> MajoranaModel:
     return MajoranaModel(A, qi, qv, ec[0])
 
 
+def seeded_states(n_modes, rank, seed, parity=1):
+    """The states sgs_admit generates without gamma0: (gamma [rank, 2N, 2N], lambda [rank])."""
+    n = 2 * n_modes
+    g = np.zeros((rank, n, n))
+    lam = np.zeros((rank, 2))
+    st = _lib.sgs_seeded_states(n_modes, rank, int(seed), parity, _ptr(g), _ptr(lam))
+    if st != 0:
+        raise SGSError(st, "bad arguments")
+    return g, lam[:, 0] + 1j * lam[:, 1]
+
+
 # ------------------------------------------------------------ solver
 
-def _check_slot_args(model, gamma0, parity):
-    g = np.asarray(gamma0)
-    if g.ndim != 3 or g.shape[1:] != (model.n, model.n):
-        raise SGSError(1, f"gamma0 has shape {g.shape}, expected (M, {model.n}, {model.n})")
-    if not 1 <= g.shape[0] <= 64:
-        raise SGSError(1, f"rank {g.shape[0]} outside 1..64")
+def _check_slot_args(model, gamma0, parity, rank=None):
+    if gamma0 is None:
+        M = rank
+        if M is None:
+            raise SGSError(1, "without gamma0 the rank must be given")
+    else:
+        g = np.asarray(gamma0)
+        if g.ndim != 3 or g.shape[1:] != (model.n, model.n):
+            raise SGSError(1, f"gamma0 has shape {g.shape}, expected (M, {model.n}, {model.n})")
+        M = g.shape[0]
+    if not 1 <= M <= 64:
+        raise SGSError(1, f"rank {M} outside 1..64")
     if parity not in (1, -1):
         raise SGSError(1, f"parity {parity} is not +-1")
 
@@ -252,18 +270,19 @@ class Solver:
         return len(self.shapes)
 
     def admit(self, model, gamma0, lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE, parity=1,
-              integrator=SGS_INTEGRATOR_EXP):
-        """Add one problem; returns its slot.  Raises SGSError(SGS_ENOMEM) if it
+              integrator=SGS_INTEGRATOR_EXP, rank=None, seed=0):
+        """Add one problem; returns its slot.  gamma0 None: seeded random states of
+        the given rank, generated by the library.  Raises SGSError(SGS_ENOMEM) if it
         does not fit the HBM budget (nothing is allocated then)."""
-        _check_slot_args(model, gamma0, parity)
-        g = np.ascontiguousarray(gamma0, dtype=np.float64)
-        M = g.shape[0]
+        _check_slot_args(model, gamma0, parity, rank)
+        g = None if gamma0 is None else np.ascontiguousarray(gamma0, dtype=np.float64)
+        M = rank if g is None else g.shape[0]
         lam = None
         if lambda0 is not None:
             lam = np.ascontiguousarray(np.stack([np.real(lambda0), np.imag(lambda0)], -1), dtype=np.float64)
         mod = _Model(model.n_modes, _ptr(model.A), len(model.quartic_val), _ptr(model.quartic_idx, _ip),
                      _ptr(model.quartic_val), model.e_const)
-        opt = _Options(M, dtau, precision, cmode, parity, _ptr(g), _ptr(lam), None, integrator)
+        opt = _Options(M, dtau, precision, cmode, parity, _ptr(g), _ptr(lam), None, integrator, int(seed))
         slot = ctypes.c_int(-1)
         st = _lib.sgs_admit(self._ctx, ctypes.byref(mod), ctypes.byref(opt), ctypes.byref(slot))
         if st != 0:

@@ -5,7 +5,7 @@
 // products, the delayed updates of the blocked factorisations, the per-state
 // exponential and purification) goes through it.
 //
-// C_b = alpha * alpha_b[b] * op(A_b) op(B_b) + beta * Cin_b + diag * I
+// C_b = alpha * alpha_b[b] * op(A_b) op(B_b) + beta * Cin_b + beta2 * Cin2_b + diag * I
 // with A_b = A1_b + sA2 * A2_b (the pair difference Gamma_a - Gamma_b is
 // fused into the operand load), likewise for B.
 //
@@ -27,6 +27,7 @@ struct GemmBatch {
     const double* const* B; long long offB; int ldb; int transB;
     const double* const* B2; double sB2;  // optional (nullptr)
     const double* const* Cin; long long offCin; int ldcin; double beta;  // optional
+    const double* const* Cin2; double beta2;   // optional second addend (same offset and stride as Cin)
     double* const* C; long long offC; int ldc;
     double alpha; double diag;
     const double* alpha_b;               // optional per-batch multiplier of alpha
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
 
     // epilogue
     const double* Cinb = g.Cin ? g.Cin[b] + g.offCin : nullptr;
+    const double* Cin2b = g.Cin2 ? g.Cin2[b] + g.offCin : nullptr;
     double* Cb = g.C[b] + g.offC;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
                         if (g.mode == GEMM_GJ && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b) use = false;
                         if (use) v += g.beta * Cinb[(long long)r * g.ldcin + c];
                     }
+                    if (Cin2b) v += g.beta2 * Cin2b[(long long)r * g.ldcin + c];
                     if (r == c) v += g.diag;
                 }
                 if (g.mode == GEMM_FULL) {
@@ -253,7 +256,7 @@ inline cudaError_t gemm_f64(const GemmBatch& g, cudaStream_t st) {
 
 inline GemmBatch gemm_defaults() {
     GemmBatch g{};
-    g.alpha = 1.0; g.beta = 0.0; g.diag = 0.0; g.sA2 = 0.0; g.sB2 = 0.0;
+    g.alpha = 1.0; g.beta = 0.0; g.diag = 0.0; g.sA2 = 0.0; g.sB2 = 0.0; g.Cin2 = nullptr; g.beta2 = 0.0;
     g.mode = GEMM_FULL; g.active_flag = nullptr; g.alpha_b = nullptr; g.active_cmp = 0;
     return g;
 }

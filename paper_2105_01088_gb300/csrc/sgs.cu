@@ -37,6 +37,7 @@
 #include "corr.cuh"
 #include "renyi.cuh"
 #include "var.cuh"
+#include "host_init.hpp"
 
 using namespace sgs;
 
@@ -987,25 +988,43 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// exp(X) for the first `batch` states (App. A): X in s1 and the first Horner factor in s2, as
-// exp_prepare_kernel leaves them; the Horner products, then the squarings each state needs (states
-// with fewer pass their matrix through).  *cur_out <- the s buffer that holds R.
+// exp(X_s) for the first `batch` states (App. A), X_s = 2^-s X in s1 as exp_prepare_kernel
+// leaves it: the degree-10 Taylor polynomial by Paterson-Stockmeyer in blocks of three,
+//   X2 = X_s^2 (s0), Y = X_s^3 (s2, antisymmetric), P = B3 (s3),
+//   P <- P Y + B_j for j = 2, 1, 0, B_j = c_{3j} I + c_{3j+1} X_s + c_{3j+2} X2, c_k = 1/k!
+// (the addends fused into the products' epilogue), then the squarings each state needs
+// (states with fewer pass their matrix through).  *cur_out <- the s buffer (3 or 4) that holds R.
 cudaError_t exp_products(sgs_ctx* c, Instance& I, int batch, cudaStream_t st, int* cur_out) {
     const int n = I.n;
+    const size_t nn = (size_t)n * n;
     const double n3 = (double)n * n * n;
+    static_assert(EXP_TAYLOR_DEGREE == 10, "blocks of three cover degrees 0..11");
+    double cf[12];
+    cf[0] = 1.0;
+    for (int k = 1; k < 12; k++) cf[k] = cf[k - 1] / k;
+    cf[11] = 0.0;                                         // degree 10
     cudaError_t e;
-    // Horner: P <- I + (X 2^-s / j) P, j = degree-1 .. 1
-    int cur = 2;
-    for (int j = EXP_TAYLOR_DEGREE - 1; j >= 1; j--) {
-        int nxt = (cur == 2) ? 3 : 2;
-        GemmBatch g = gb_basic(n, n, n, I.p_s[1], n, I.p_s[cur], n, I.p_s[nxt], n, batch);
-        g.alpha = 1.0 / j; g.alpha_b = I.scale; g.diag = 1.0;
+    GemmBatch g = gb_basic(n, n, n, I.p_s[1], n, I.p_s[1], n, I.p_s[0], n, batch);
+    if ((e = gemm(c, g, st, 2.0 * n3 * batch)) != cudaSuccess) return e;         // X2
+    g = gb_basic(n, n, n, I.p_s[0], n, I.p_s[1], n, I.p_s[2], n, batch);
+    g.mode = GEMM_SKEW;                                                            // Y = X2 X_s
+    if ((e = gemm(c, g, st, n3 * batch)) != cudaSuccess) return e;
+    scaled_plus_identity_kernel<<<grid_chunks(batch * nn, 256, 4096), 256, 0, st>>>(I.s[1], cf[10], cf[9], n, I.s[3],
+                                                                                   batch * nn);
+    counted();
+    int cur = 3;
+    for (int j = 2; j >= 0; j--) {
+        const int nxt = (cur == 3) ? 4 : 3;
+        g = gb_basic(n, n, n, I.p_s[cur], n, I.p_s[2], n, I.p_s[nxt], n, batch);
+        g.Cin = (const double* const*)I.p_s[0]; g.ldcin = n; g.beta = cf[3 * j + 2];
+        g.Cin2 = (const double* const*)I.p_s[1]; g.beta2 = cf[3 * j + 1];
+        g.diag = cf[3 * j];
         if ((e = gemm(c, g, st, 2.0 * n3 * batch)) != cudaSuccess) return e;
         cur = nxt;
     }
     for (int j = 0; j < EXP_MAX_SQUARINGS; j++) {
-        int nxt = (cur == 2) ? 3 : 2;
-        GemmBatch g = gb_basic(n, n, n, I.p_s[cur], n, I.p_s[cur], n, I.p_s[nxt], n, batch);
+        const int nxt = (cur == 3) ? 4 : 3;
+        g = gb_basic(n, n, n, I.p_s[cur], n, I.p_s[cur], n, I.p_s[nxt], n, batch);
         g.active_flag = I.sq; g.active_cmp = j;
         g.Cin = (const double* const*)I.p_s[cur]; g.ldcin = n; g.beta = 0.0;
         if ((e = gemm(c, g, st, -1.0)) != cudaSuccess) return e;
@@ -1018,12 +1037,12 @@ cudaError_t exp_products(sgs_ctx* c, Instance& I, int batch, cudaStream_t st, in
 // Canonical-form renormalisation (App. A, Eq. CM-normal-form with every lambda_j = 1): the polar
 // factor of the matrices in s4 by `iters` Newton-Schulz steps X <- 1.5 X + 0.5 X (X X); the result
 // goes to gamma.
-cudaError_t polar_pass(sgs_ctx* c, Instance& I, int iters, cudaStream_t st) {
+cudaError_t polar_pass(sgs_ctx* c, Instance& I, int iters, cudaStream_t st, int from = 4) {
     const int n = I.n, M = I.M;
     const size_t nn = (size_t)n * n;
     const double n3 = (double)n * n * n;
     cudaError_t e;
-    double** src = I.p_s[4];
+    double** src = I.p_s[from];
     double** dst = I.p_gamma;
     for (int it = 0; it < iters; it++) {
         GemmBatch g = gb_basic(n, n, n, src, n, src, n, I.p_s[0], n, M);
@@ -1033,8 +1052,8 @@ cudaError_t polar_pass(sgs_ctx* c, Instance& I, int iters, cudaStream_t st) {
         if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
         std::swap(src, dst);
     }
-    if (src == I.p_s[4]) {     // an even number of iterations ends in s4
-        copy_kernel<<<grid_chunks(M * nn, 256, 4096), 256, 0, st>>>(I.s[4], I.gamma, M * nn);
+    if (src == I.p_s[from]) {  // an even number of iterations ends in the source buffer
+        copy_kernel<<<grid_chunks(M * nn, 256, 4096), 256, 0, st>>>(I.s[from], I.gamma, M * nn);
         counted();
     }
     return cudaGetLastError();
@@ -1136,24 +1155,24 @@ cudaError_t update_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         I.steps_since_profile++;
         return cudaGetLastError();
     }
-    // Gamma dGamma, 9 Horner products, R Gamma, (R Gamma) R^T (antisymmetric), two
-    // Newton-Schulz iterations (X X and X (X X), half each); squarings are added when
-    // profiles are read
-    c->stage_flops[SGS_STAGE_UPDATE] += (2.0 + 18.0 + 2.0 + 1.0 + 4.0) * n3 * M;
-    // Y = Gamma dGamma -> s0 ; X -> s1 ; P -> s2
+    // Gamma dGamma 2, the exponential's X^2 2, X^3 1 (antisymmetric) and three block products 6,
+    // R Gamma 2, (R Gamma) R^T 1 (antisymmetric), two Newton-Schulz iterations (X X and
+    // X (X X), half each) 4; squarings are added when profiles are read
+    c->stage_flops[SGS_STAGE_UPDATE] += (2.0 + 9.0 + 2.0 + 1.0 + 4.0) * n3 * M;
+    // Y = Gamma dGamma -> s0 ; X_s -> s1
     GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_dgamma, n, I.p_s[0], n, M);
     if ((e = gemm(c, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
-    exp_prepare_kernel<<<M, 1024, 0, st>>>(I.s[0], I.s[1], I.s[2], n, I.dtau, I.sq, I.scale, I.err);
+    exp_prepare_kernel<<<M, 1024, 0, st>>>(I.s[0], I.s[1], n, I.dtau, I.sq, I.scale, I.err);
     counted();
-    int cur = 2;
+    int cur = 3;
     if ((e = exp_products(c, I, M, st, &cur)) != cudaSuccess) return e;
-    // T = R Gamma -> s0 ; Gamma' = T R^T -> s4
+    // T = R Gamma -> s0 ; Gamma' = T R^T -> s2
     g = gb_basic(n, n, n, I.p_s[cur], n, I.p_gamma, n, I.p_s[0], n, M);
     if ((e = gemm(c, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
-    g = gb_basic(n, n, n, I.p_s[0], n, I.p_s[cur], n, I.p_s[4], n, M);
+    g = gb_basic(n, n, n, I.p_s[0], n, I.p_s[cur], n, I.p_s[2], n, M);
     g.transB = 1; g.mode = GEMM_SKEW;
     if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
-    if ((e = polar_pass(c, I, 2, st)) != cudaSuccess) return e;
+    if ((e = polar_pass(c, I, 2, st, 2)) != cudaSuccess) return e;
     I.steps_since_profile++;
     return cudaGetLastError();
 }
@@ -1274,7 +1293,7 @@ void sgs_set_allocator(sgs_alloc_fn alloc, sgs_free_fn release, void* user) {
 namespace {
 sgs_status check_args(const sgs_model& m, const sgs_options& o) {
     if (m.n_modes < 1 || !m.A || (m.n_quartic > 0 && (!m.quartic_idx || !m.quartic_val))) return SGS_EINVAL;
-    if (o.rank < 1 || o.rank > SGS_MAX_RANK || (o.parity != 1 && o.parity != -1) || !o.gamma0) return SGS_EINVAL;
+    if (o.rank < 1 || o.rank > SGS_MAX_RANK || (o.parity != 1 && o.parity != -1)) return SGS_EINVAL;
     if (o.precision < 0 || o.precision > 3 || (o.cmode != 0 && o.cmode != 1)) return SGS_EINVAL;
     if (o.integrator != SGS_INTEGRATOR_EXP && o.integrator != SGS_INTEGRATOR_EULER) return SGS_EINVAL;
     return SGS_OK;
@@ -1311,10 +1330,21 @@ sgs_status sgs_admit(sgs_ctx* c, const sgs_model* model, const sgs_options* opt,
         c->err = "over the HBM budget: " + std::to_string(c->bytes_in_use + need) + " > " + std::to_string(c->budget);
         return SGS_ENOMEM;
     }
+    // no initial states: seeded Haar states and phases generated here
+    std::vector<double> g0, l0;
+    sgs_options o = *opt;
+    if (!o.gamma0) {
+        const int n = 2 * model->n_modes;
+        g0.resize((size_t)o.rank * n * n);
+        l0.resize(2 * (size_t)o.rank);
+        seeded_states(n, o.rank, o.seed, o.parity, g0.data(), l0.data());
+        o.gamma0 = g0.data();
+        if (!o.lambda0) o.lambda0 = l0.data();
+    }
     c->inst.emplace_back();
     Instance& I = c->inst.back();
     c->owner = &I;
-    s = setup_instance(c, I, *model, *opt);
+    s = setup_instance(c, I, *model, o);
     c->owner = nullptr;
     if (s == SGS_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) s = SGS_ECUDA;
     if (s == SGS_OK && c->autotune) s = autotune_instance(c, I);
@@ -1342,6 +1372,12 @@ sgs_status sgs_retire(sgs_ctx* c, int slot) {
 size_t sgs_bytes_in_use(const sgs_ctx* c) { return c ? c->bytes_in_use : 0; }
 
 int sgs_failed_instance(const sgs_ctx* c) { return c ? c->failed : -1; }
+
+sgs_status sgs_seeded_states(int n_modes, int rank, unsigned long long seed, int parity, double* gamma, double* lambda) {
+    if (n_modes < 1 || rank < 1 || (parity != 1 && parity != -1) || !gamma || !lambda) return SGS_EINVAL;
+    seeded_states(2 * n_modes, rank, seed, parity, gamma, lambda);
+    return SGS_OK;
+}
 
 sgs_status sgs_set_autotune(sgs_ctx* c, int enable) {
     if (!c) return SGS_EINVAL;
@@ -1392,7 +1428,7 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
     // the grown instance: same model and options, rank M + 1, states filled on the device
     Instance J;
     sgs_model m{I.N, I.hA.data(), (int)I.hq_val.size(), I.hq_idx.data(), I.hq_val.data(), I.e_const};
-    sgs_options o{M + 1, I.dtau, I.prec, I.cmode, I.parity, nullptr, nullptr, nullptr, I.integrator};
+    sgs_options o{M + 1, I.dtau, I.prec, I.cmode, I.parity, nullptr, nullptr, nullptr, I.integrator, 0};
     c->owner = &J;
     sgs_status s = setup_instance(c, J, m, o);
     c->owner = nullptr;
@@ -1404,11 +1440,11 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
         // X = K: exp_prepare_kernel forms (ds/4)(Y - Y^T), which is K for Y = K and ds = 2
         if (e == cudaSuccess) e = cudaMemcpyAsync(J.s[0], K, nn * sizeof(double), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) {
-            exp_prepare_kernel<<<1, 1024, 0, st>>>(J.s[0], J.s[1], J.s[2], n, 2.0, J.sq, J.scale, J.err);
+            exp_prepare_kernel<<<1, 1024, 0, st>>>(J.s[0], J.s[1], n, 2.0, J.sq, J.scale, J.err);
             counted();
             e = cudaGetLastError();
         }
-        int cur = 2;
+        int cur = 3;
         if (e == cudaSuccess) e = exp_products(c, J, 1, st, &cur);
         // Q Gamma_src -> s0 ; (Q Gamma_src) Q^T -> Gamma_M
         if (e == cudaSuccess) {

@@ -3,8 +3,10 @@
 // with Gamma + ds dGamma of Eq. RKstep to first order), followed by the
 // canonical-form renormalisation (polar factor, Newton-Schulz in FP64).
 //
-// exp(X) by scaling and squaring: X_s = X / 2^s with ||X_s||_F <= 1/8, Taylor
-// polynomial of degree 10 in Horner form (truncation < 3e-18), then s
+// exp(X) by scaling and squaring: X_s = X / 2^s with ||X_s||_F <= 1/8, the Taylor
+// polynomial of degree 10 (truncation < 3e-18) evaluated by Paterson-Stockmeyer in
+// blocks of three, p = B0 + B1 Y + B2 Y^2 + B3 Y^3 with Y = X_s^3 and
+// B_j = sum_i X_s^i / (3j + i)!, i < 3 (five products instead of Horner's nine), then s
 // squarings.  The products run on the batched FP64 GEMM; this file holds the
 // elementwise pieces.
 #pragma once
@@ -18,21 +20,19 @@ namespace sgs {
 #define EULER_NS_ITERS 6       // Newton-Schulz steps after an Euler step: singular values 1 + d with
                                // |d| <= 0.3 reach 1 to rounding (d -> -1.5 d^2 per step)
 
-// X = (ds/4)(Y - Y^T) with Y = Gamma dGamma (so [Gamma, dGamma] = Y - Y^T),
-// its Frobenius norm -> squarings s, 2^-s, and the first Horner factor
-// P = I + X_s / degree.
-__global__ void __launch_bounds__(1024) exp_prepare_kernel(const double* Y, double* X, double* P, int n,
-                                                            double ds, int* sq, double* scale, int* err) {
+// X = (ds/4)(Y - Y^T) with Y = Gamma dGamma (so [Gamma, dGamma] = Y - Y^T), its
+// Frobenius norm -> squarings s (||X 2^-s||_F <= 1/8), and X_s = 2^-s X -> Xs.
+__global__ void __launch_bounds__(1024) exp_prepare_kernel(const double* Y, double* Xs, int n, double ds, int* sq,
+                                                            double* scale, int* err) {
     __shared__ double red[32];
     const int mu = blockIdx.x;
     const size_t nn = (size_t)n * n;
     const double* y = Y + mu * nn;
-    double* x = X + mu * nn;
+    double* x = Xs + mu * nn;
     double ss = 0.0;
     for (size_t e = threadIdx.x; e < nn; e += blockDim.x) {
         int k = (int)(e / n), l = (int)(e % n);
         double v = 0.25 * ds * (y[e] - y[(size_t)l * n + k]);
-        x[e] = v;
         ss += v * v;
     }
     ss = block_sum(ss, red);
@@ -45,11 +45,18 @@ __global__ void __launch_bounds__(1024) exp_prepare_kernel(const double* Y, doub
     }
     const double sc = ldexp(1.0, -s);
     if (threadIdx.x == 0) { sq[mu] = s; scale[mu] = sc; }
-    double* pp = P + mu * nn;
-    const double f = sc / EXP_TAYLOR_DEGREE;
     for (size_t e = threadIdx.x; e < nn; e += blockDim.x) {
         int k = (int)(e / n), l = (int)(e % n);
-        pp[e] = f * x[e] + (k == l ? 1.0 : 0.0);
+        x[e] = sc * 0.25 * ds * (y[e] - y[(size_t)l * n + k]);
+    }
+}
+
+// out = a X + d I (the leading block of the Paterson-Stockmeyer evaluation)
+__global__ void scaled_plus_identity_kernel(const double* X, double a, double d, int n, double* out, size_t count) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t w = e % ((size_t)n * n);
+        const int k = (int)(w / n), l = (int)(w % n);
+        out[e] = a * X[e] + (k == l ? d : 0.0);
     }
 }
 

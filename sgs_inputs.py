@@ -56,6 +56,58 @@ def clustered_pure_gammas(n_modes: int, M: int, rng: np.random.Generator, parity
     return np.ascontiguousarray(np.stack(out))
 
 
+# ---------------------------------------------------------------------------
+# Counter-based seeded states (the same definition the library uses when it
+# generates initial states itself): Philox4x32-10 (Salmon et al., SC11), key =
+# the 64-bit seed; state mu's standard-normal matrix entries 2j, 2j+1 from
+# counter (j, mu, 0, 0) by Box-Muller on the first two words; the phase of
+# lambda_mu from counter (0, mu, 1, 0); O Haar from QR with sign(diag R).
+
+_PHILOX_M0, _PHILOX_M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+_PHILOX_W0, _PHILOX_W1 = np.uint64(0x9E3779B9), np.uint64(0xBB67AE85)
+_MASK32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32(counters: np.ndarray, seed: int) -> np.ndarray:
+    """Philox4x32-10 of each row of counters ([k, 4] integers < 2^32); returns [k, 4] uint64."""
+    x = [np.asarray(counters[:, i], dtype=np.uint64) for i in range(4)]
+    k0, k1 = np.uint64(seed & 0xFFFFFFFF), np.uint64((seed >> 32) & 0xFFFFFFFF)
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + _PHILOX_W0) & _MASK32
+            k1 = (k1 + _PHILOX_W1) & _MASK32
+        p0 = _PHILOX_M0 * x[0]
+        p1 = _PHILOX_M1 * x[2]
+        x = [(p1 >> np.uint64(32)) ^ x[1] ^ k0, p1 & _MASK32, (p0 >> np.uint64(32)) ^ x[3] ^ k1, p0 & _MASK32]
+    return np.stack(x, 1)
+
+
+def seeded_state(n_modes: int, mu: int, seed: int, parity: int = 1):
+    n = 2 * n_modes
+    j = np.arange(n * n // 2, dtype=np.uint64)
+    ctr = np.stack([j, np.full_like(j, mu), np.zeros_like(j), np.zeros_like(j)], 1)
+    x = philox4x32(ctr, seed)
+    u1 = (x[:, 0].astype(np.float64) + 1.0) / 4294967296.0
+    u2 = x[:, 1].astype(np.float64) / 4294967296.0
+    r = np.sqrt(-2.0 * np.log(u1))
+    Z = np.empty(n * n)
+    Z[0::2] = r * np.cos(2.0 * np.pi * u2)
+    Z[1::2] = r * np.sin(2.0 * np.pi * u2)
+    Q, R = np.linalg.qr(Z.reshape(n, n))
+    O = Q * np.sign(np.diag(R))
+    if np.sign(np.linalg.det(O)) != parity:
+        O[:, 0] = -O[:, 0]
+    g = O @ vacuum_gamma(n_modes) @ O.T
+    x = philox4x32(np.array([[0, mu, 1, 0]], dtype=np.uint64), seed)
+    th = 2.0 * np.pi * float(x[0, 0]) / 4294967296.0
+    return 0.5 * (g - g.T), np.exp(1j * th)
+
+
+def seeded_states(n_modes: int, M: int, seed: int, parity: int = 1):
+    out = [seeded_state(n_modes, mu, seed, parity) for mu in range(M)]
+    return np.stack([g for g, _ in out]), np.array([l for _, l in out])
+
+
 def random_generator(n: int, norm: float, rng: np.random.Generator) -> np.ndarray:
     """A random antisymmetric n x n matrix K with ||K||_F = norm (exactly
     antisymmetric: K = X - X^T, scaled), so that exp(K) is a random special

@@ -181,3 +181,18 @@ def test_graph_replay_is_bitwise_identical(pkg):
         s.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_library_seeded_states_step(pkg):
+    """Admission without gamma0: the library's seeded states equal the test
+    generator's, and one step matches the oracle from them."""
+    p = inp.AndersonParams(n_bath=20, U=3.0, eps_d=-1.5, V=0.7)
+    s = pkg.Solver()
+    k = s.admit(pkg.build_anderson(p.n_bath, p.U, p.eps_d, p.V), None, rank=4, seed=77, parity=1)
+    g0, lam0 = s.get_state(k)
+    gi, li = inp.seeded_states(p.n_modes, 4, 77, 1)
+    assert np.abs(g0 - gi).max() < 1e-13 and np.abs(lam0 - li).max() < 1e-15
+    E = s.step(1)[k, 0]
+    s.close()
+    Eo, _, _ = orc.sgs_step(_oracle_model(p), list(gi), 0.05)
+    assert abs(E - Eo) <= RTOL * abs(Eo)
