@@ -133,6 +133,16 @@ size_t sgs_bytes_in_use(const sgs_ctx* ctx);
 sgs_status sgs_seeded_states(int n_modes, int rank, unsigned long long seed, int parity, double* gamma,
                              double* lambda);
 
+/* Health of one instance's current states (a per-step check a caller may run):
+ * out[0] = max over states of max_kl |(Gamma^2)_kl + delta_kl| (purity residual),
+ * out[1] = number of non-finite entries of Gamma, out[2] = smallest / largest
+ * eigenvalue of the Gram matrix G at the last amplitude solve (1 for orthonormal
+ * states, near 0 for nearly dependent ones), out[3] = the energy of that solve.
+ * Admission itself rejects initial states that are not finite or not
+ * antisymmetric (SGS_EINVAL); a wrong parity shows as SGS_ESINGULAR at the first
+ * step. */
+sgs_status sgs_health(sgs_ctx* ctx, int instance, double* out);
+
 /* Index of the instance whose device-side error (SGS_ESINGULAR, SGS_ENOTCONV,
  * SGS_ETIMEOUT) ended the last call, or -1.  The other instances of that
  * sgs_step completed the failing step (their states advanced) but its

@@ -64,6 +64,7 @@ SIGNATURES = {
     "sgs_add_state": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, ctypes.c_int]),
     "sgs_set_autotune": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_failed_instance": (ctypes.c_int, [_ctxp]),
+    "sgs_health": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp]),
     "sgs_seeded_states": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, _dp, _dp]),
     "sgs_get_tuning": (ctypes.c_int, [_ctxp, ctypes.c_int, _ip, _ip, _ip]),
     "sgs_set_graphs": (ctypes.c_int, [_ctxp, ctypes.c_int]),
@@ -297,6 +298,12 @@ class Solver:
 
     def bytes_in_use(self):
         return int(_lib.sgs_bytes_in_use(self._ctx))
+
+    def health(self, instance=0):
+        """{purity_residual, nonfinite, gram_eig_ratio, energy} of the current states."""
+        out = np.zeros(4)
+        self._check(_lib.sgs_health(self._ctx, instance, _ptr(out)))
+        return {"purity_residual": out[0], "nonfinite": int(out[1]), "gram_eig_ratio": out[2], "energy": out[3]}
 
     def failed_instance(self):
         """Slot whose device-side error ended the last call (-1: none)."""

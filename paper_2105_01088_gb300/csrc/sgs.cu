@@ -12,6 +12,7 @@
 //   update:  R = exp{(ds/4)[G, dG]}, G <- R G R^T, Newton-Schulz polar factor
 //                                                            [App. A]
 #include "../../include/sgs.h"
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <array>
@@ -234,11 +235,21 @@ struct sgs_ctx {
         }
         return ev_pool[ev_used++];
     }
-    void stage(int s) {            // close the open stage, open stage s (-1: none)
+    // close the open stage, open stage s (-1: none); in profiling mode the stages are
+    // CUDA-event intervals and NVTX ranges (named as sgs_stage)
+    void stage(int s) {
         if (!prof) return;
         cudaEvent_t e = next_event();
         cudaEventRecord(e, stream);
-        if (open_stage >= 0) marks.push_back({open_stage, open_ev, e});
+        if (open_stage >= 0) {
+            marks.push_back({open_stage, open_ev, e});
+            nvtxRangePop();
+        }
+        if (s >= 0) {
+            static const char* names[SGS_N_STAGES] = {"pair_inverse", "pair_delta", "phase_pfaffian", "amplitudes",
+                                                      "eom_w", "eom_v", "eom_x", "eom_assembly", "update"};
+            nvtxRangePushA(names[s]);
+        }
         open_stage = s;
         open_ev = e;
     }
@@ -1296,6 +1307,17 @@ sgs_status check_args(const sgs_model& m, const sgs_options& o) {
     if (o.rank < 1 || o.rank > SGS_MAX_RANK || (o.parity != 1 && o.parity != -1)) return SGS_EINVAL;
     if (o.precision < 0 || o.precision > 3 || (o.cmode != 0 && o.cmode != 1)) return SGS_EINVAL;
     if (o.integrator != SGS_INTEGRATOR_EXP && o.integrator != SGS_INTEGRATOR_EULER) return SGS_EINVAL;
+    if (o.gamma0) {           // finite and antisymmetric (purity is reported by sgs_health)
+        const int n = 2 * m.n_modes;
+        for (int mu = 0; mu < o.rank; mu++) {
+            const double* g = o.gamma0 + (size_t)mu * n * n;
+            for (int i = 0; i < n; i++)
+                for (int j = i; j < n; j++) {
+                    const double a = g[(size_t)i * n + j], b = g[(size_t)j * n + i];
+                    if (!std::isfinite(a) || !std::isfinite(b) || std::fabs(a + b) > 1e-8) return SGS_EINVAL;
+                }
+        }
+    }
     return SGS_OK;
 }
 }  // namespace
@@ -1324,7 +1346,7 @@ sgs_status sgs_admit(sgs_ctx* c, const sgs_model* model, const sgs_options* opt,
     if (!c || !model || !opt || !slot) return SGS_EINVAL;
     *slot = -1;
     sgs_status s = check_args(*model, *opt);
-    if (s != SGS_OK) { c->err = "invalid model or options"; return s; }
+    if (s != SGS_OK) { c->err = "invalid model, options or initial states (non-finite or not antisymmetric)"; return s; }
     const size_t need = instance_bytes(2 * model->n_modes, opt->rank, opt->precision, 16, c->autotune);
     if (c->budget && c->bytes_in_use + need > c->budget) {
         c->err = "over the HBM budget: " + std::to_string(c->bytes_in_use + need) + " > " + std::to_string(c->budget);
@@ -1372,6 +1394,35 @@ sgs_status sgs_retire(sgs_ctx* c, int slot) {
 size_t sgs_bytes_in_use(const sgs_ctx* c) { return c ? c->bytes_in_use : 0; }
 
 int sgs_failed_instance(const sgs_ctx* c) { return c ? c->failed : -1; }
+
+sgs_status sgs_health(sgs_ctx* c, int instance, double* out) {
+    if (!c || !out || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
+    Instance& I = c->inst[instance];
+    const int n = I.n, M = I.M;
+    const size_t nn = (size_t)n * n;
+    cudaStream_t st = c->stream;
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    // Gamma_mu^2 -> s0, then max |Gamma^2 + 1|, non-finite entries of Gamma, and the extreme eigenvalues of G
+    // of the last amplitude solve (diagonal of its Jacobi result)
+    GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_gamma, n, I.p_s[0], n, M);
+    const bool prof = c->prof;
+    c->prof = false;
+    cudaError_t e = gemm(c, g, st, -1.0);
+    c->prof = prof;
+    if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return SGS_ECUDA; }
+    if (I.corr_cap < 8) {
+        c->owner = &I;
+        I.corr_scratch = c->alloc<double>(8);
+        c->owner = nullptr;
+        if (!I.corr_scratch) { c->err = "device allocation failed"; return SGS_ENOMEM; }
+        I.corr_cap = 8;
+    }
+    health_kernel<<<1, 1024, 0, st>>>(I.s[0], I.gamma, M * nn, n, I.eigscratch, 2 * M, I.Ecur, I.corr_scratch);
+    counted();
+    CUDA_TRY(c, cudaMemcpyAsync(out, I.corr_scratch, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    return SGS_OK;
+}
 
 sgs_status sgs_seeded_states(int n_modes, int rank, unsigned long long seed, int parity, double* gamma, double* lambda) {
     if (n_modes < 1 || rank < 1 || (parity != 1 && parity != -1) || !gamma || !lambda) return SGS_EINVAL;
@@ -1557,7 +1608,9 @@ sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
         } else {
             for (auto& I : c->inst) {
                 if (!I.live) continue;
-                CUDA_TRY(c, pair_pass(c, I, I.Ehist + step, c->stream));
+                CUDA_TRY(c, pair_pass(c, I, I.Ecur, c->stream));
+                CUDA_TRY(c, cudaMemcpyAsync(I.Ehist + step, I.Ecur, sizeof(double), cudaMemcpyDeviceToDevice,
+                                            c->stream));
                 CUDA_TRY(c, eom_pass(c, I, c->stream));
                 CUDA_TRY(c, update_pass(c, I, c->stream));
             }
@@ -1581,7 +1634,7 @@ sgs_status sgs_energy(sgs_ctx* c, double* energies) {
     if (!c) return SGS_EINVAL;
     const long long l0 = g_launches;
     for (auto& I : c->inst)
-        if (I.live) CUDA_TRY(c, pair_pass(c, I, I.Ehist, c->stream));
+        if (I.live) CUDA_TRY(c, pair_pass(c, I, I.Ecur, c->stream));
     c->stage(-1);
     c->launches += g_launches - l0;
     sgs_status s = check_device_error(c);
@@ -1590,7 +1643,7 @@ sgs_status sgs_energy(sgs_ctx* c, double* energies) {
     if (energies)
         for (size_t i = 0; i < c->inst.size(); i++)
             if (c->inst[i].live)
-                CUDA_TRY(c, cudaMemcpy(energies + i, c->inst[i].Ehist, sizeof(double), cudaMemcpyDeviceToHost));
+                CUDA_TRY(c, cudaMemcpy(energies + i, c->inst[i].Ecur, sizeof(double), cudaMemcpyDeviceToHost));
     return SGS_OK;
 }
 
@@ -1608,7 +1661,7 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
             if (!ok) { c->err = "correlator site out of range"; return SGS_EINVAL; }
         }
         // current states: pair pass and amplitudes (the states are not changed)
-        CUDA_TRY(c, pair_pass(c, I, I.Ehist, c->stream));
+        CUDA_TRY(c, pair_pass(c, I, I.Ecur, c->stream));
         c->stage(-1);
         const size_t rows = (size_t)I.P + I.M;
         const size_t need = rows * n_sites + 2 * (size_t)n_sites + 8;
@@ -1641,7 +1694,7 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
                 return SGS_EINVAL;
             }
         }
-        CUDA_TRY(c, pair_pass(c, I, I.Ehist, c->stream));
+        CUDA_TRY(c, pair_pass(c, I, I.Ecur, c->stream));
         c->stage(-1);
         const long long M2 = (long long)I.M * I.M;
         const long long npairs = M2 * (M2 + 1) / 2;
@@ -1698,7 +1751,7 @@ sgs_status sgs_variance(sgs_ctx* c, int instance, double* energy, double* varian
     if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
     Instance& I = c->inst[instance];
     if (I.nc > VAR_MAX_MON) { c->err = "more quartic monomials than the variance kernel handles"; return SGS_EINVAL; }
-    CUDA_TRY(c, pair_pass(c, I, I.Ehist, c->stream));
+    CUDA_TRY(c, pair_pass(c, I, I.Ecur, c->stream));
     c->stage(-1);
     const size_t rows = (size_t)I.P + I.M;
     const size_t need = rows + 8;
@@ -1720,7 +1773,7 @@ sgs_status sgs_variance(sgs_ctx* c, int instance, double* energy, double* varian
     if (st != SGS_OK) return st;
     double h[2];
     CUDA_TRY(c, cudaMemcpy(h, dout, sizeof(double), cudaMemcpyDeviceToHost));
-    CUDA_TRY(c, cudaMemcpy(h + 1, I.Ehist, sizeof(double), cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(h + 1, I.Ecur, sizeof(double), cudaMemcpyDeviceToHost));
     if (energy) *energy = h[1];
     if (variance) *variance = h[0] - h[1] * h[1];
     return SGS_OK;

@@ -60,6 +60,43 @@ __global__ void scaled_plus_identity_kernel(const double* X, double a, double d,
     }
 }
 
+// health of an instance: out[0] = max |(Gamma^2)_kl + delta_kl| over the states (G2 holds
+// Gamma^2), out[1] = number of non-finite entries of Gamma, out[2] = smallest / largest
+// eigenvalue of G at the last amplitude solve (the diagonal of its Jacobi result, m x m
+// real embedding), out[3] = the energy of that solve
+__global__ void __launch_bounds__(1024) health_kernel(const double* G2, const double* gamma, size_t count, int n,
+                                                       const double* eig, int m, const double* E, double* out) {
+    __shared__ double red[32];
+    double worst = 0.0, bad = 0.0;
+    const size_t nn = (size_t)n * n;
+    for (size_t e = threadIdx.x; e < count; e += blockDim.x) {
+        const size_t w = e % nn;
+        const double d = G2[e] + ((w / n) == (w % n) ? 1.0 : 0.0);
+        worst = fmax(worst, fabs(d));
+        if (!isfinite(gamma[e])) bad += 1.0;
+        if (!isfinite(d)) worst = INFINITY;
+    }
+    // block max via a sum of per-warp maxima is not a max: reduce with shuffles, then shared memory
+    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_down_sync(0xffffffffu, worst, o));
+    __shared__ double wmax[32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = worst;
+    bad = block_sum(bad, red);
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) mx = fmax(mx, wmax[w]);
+        double lo = INFINITY, hi = 0.0;
+        for (int j = 0; j < m; j++) {
+            const double v = eig[(size_t)j * m + j];
+            lo = fmin(lo, v);
+            hi = fmax(hi, v);
+        }
+        out[0] = mx;
+        out[1] = bad;
+        out[2] = hi > 0.0 ? lo / hi : 0.0;
+        out[3] = E[0];
+    }
+}
+
 // out = x + a y (the Euler step of Eq. RKstep)
 __global__ void axpy_kernel(const double* x, const double* y, double a, double* out, size_t count) {
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
