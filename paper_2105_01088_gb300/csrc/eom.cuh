@@ -12,6 +12,10 @@
 
 namespace sgs {
 
+// R: arithmetic type of the assembly.  The FP64 form assembles in double; the mixed
+// forms, whose dense products already carry tensor-core rounding, assemble in float
+// (FP64 arithmetic is slow on this part and the assembly would otherwise be bound by it).
+template <typename R>
 __global__ void __launch_bounds__(256) eom_kernel(InstDev d, const double* si, const double* imd,
                                                   const double* qr, const double* qi, const double* fimp,
                                                   const double* fimp_state, const double* gfg,
@@ -26,53 +30,82 @@ __global__ void __launch_bounds__(256) eom_kernel(InstDev d, const double* si, c
         const int k = (int)(e / n), l = (int)(e % n);
         const int sk = d.slot[k], sl = d.slot[l];
         // A_kl (row k of the CSR)
-        double akl = 0.0;
+        R akl = 0;
         for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++)
-            if (d.a_col[q] == l) akl = d.a_val[q];
-        double acc = 0.0;
+            if (d.a_col[q] == l) akl = (R)d.a_val[q];
+        R acc = 0;
         {   // beta = mu
             const double* co = coef + (size_t)(mu * M + mu) * 6;
-            double g = gm[e];
-            double f = akl + ((sk >= 0 && sl >= 0) ? fs[sk * ni + sl] : 0.0);
-            double gf = 0.0, fg = 0.0;   // (Gamma F)_kl, (F Gamma)_kl
-            for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) gf -= gm[(size_t)k * n + d.a_col[q]] * d.a_val[q];
-            for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) fg += d.a_val[q] * gm[(size_t)d.a_col[q] * n + l];
-            if (sl >= 0) for (int m = 0; m < ni; m++) gf += gm[(size_t)k * n + d.imp[m]] * fs[m * ni + sl];
-            if (sk >= 0) for (int m = 0; m < ni; m++) fg += fs[sk * ni + m] * gm[(size_t)d.imp[m] * n + l];
-            acc += 2.0 * (co[0] * (gf - fg) + co[2] * (gfgm[e] + f) + co[4] * g);
+            const R g = (R)gm[e];
+            const R f = akl + ((sk >= 0 && sl >= 0) ? (R)fs[sk * ni + sl] : (R)0);
+            R gf = 0, fg = 0;   // (Gamma F)_kl, (F Gamma)_kl
+            for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) gf -= (R)gm[(size_t)k * n + d.a_col[q]] * (R)d.a_val[q];
+            for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) fg += (R)d.a_val[q] * (R)gm[(size_t)d.a_col[q] * n + l];
+            if (sl >= 0) for (int m = 0; m < ni; m++) gf += (R)gm[(size_t)k * n + d.imp[m]] * (R)fs[m * ni + sl];
+            if (sk >= 0) for (int m = 0; m < ni; m++) fg += (R)fs[sk * ni + m] * (R)gm[(size_t)d.imp[m] * n + l];
+            acc += (R)2 * ((R)co[0] * (gf - fg) + (R)co[2] * ((R)gfgm[e] + f) + (R)co[4] * g);
         }
         for (int be = 0; be < M; be++) {
             if (be == mu) continue;
             const int p = pair_index[mu * M + be];
-            const double sgn = (d.pa[p] == mu) ? -1.0 : 1.0;   // receiver a: complex conjugate
+            const R sgn = (d.pa[p] == mu) ? (R)-1 : (R)1;    // receiver a: complex conjugate
             const double* s = si + (size_t)p * nn(d);
             const double* im = imd + (size_t)p * nn(d);
             const double* fp = fimp + (size_t)p * ni * ni * 2;
-            auto dl = [&](int r, int c) -> cplx {
-                size_t o = (size_t)r * n + c;
-                return cmk(-2.0 * s[o], sgn * im[o]);
-            };
-            cplx D = dl(k, l);
-            cplx F = cmk(akl, 0.0);
-            if (sk >= 0 && sl >= 0) F = cadd(F, cmk(fp[2 * (sk * ni + sl)], sgn * fp[2 * (sk * ni + sl) + 1]));
+            // Delta = -2 S^{-1} + i sgn Im
+            auto dre = [&](int r, int c) -> R { return (R)-2 * (R)s[(size_t)r * n + c]; };
+            auto dim = [&](int r, int c) -> R { return sgn * (R)im[(size_t)r * n + c]; };
+            const R Dx = dre(k, l), Dy = dim(k, l);
+            R Fx = akl, Fy = 0;
+            if (sk >= 0 && sl >= 0) { Fx += (R)fp[2 * (sk * ni + sl)]; Fy += sgn * (R)fp[2 * (sk * ni + sl) + 1]; }
             // C = Delta F - F Delta
-            cplx df = cmk(0.0, 0.0), fd = cmk(0.0, 0.0);
-            for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) df = csub(df, cscale(dl(k, d.a_col[q]), d.a_val[q]));
-            for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) fd = cadd(fd, cscale(dl(d.a_col[q], l), d.a_val[q]));
+            R dfx = 0, dfy = 0, fdx = 0, fdy = 0;
+            for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) {
+                const R a = (R)d.a_val[q];
+                dfx -= dre(k, d.a_col[q]) * a;
+                dfy -= dim(k, d.a_col[q]) * a;
+            }
+            for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) {
+                const R a = (R)d.a_val[q];
+                fdx += a * dre(d.a_col[q], l);
+                fdy += a * dim(d.a_col[q], l);
+            }
             if (sl >= 0)
-                for (int m = 0; m < ni; m++)
-                    df = cadd(df, cmul(dl(k, d.imp[m]), cmk(fp[2 * (m * ni + sl)], sgn * fp[2 * (m * ni + sl) + 1])));
+                for (int m = 0; m < ni; m++) {
+                    const R ax = dre(k, d.imp[m]), ay = dim(k, d.imp[m]);
+                    const R bx = (R)fp[2 * (m * ni + sl)], by = sgn * (R)fp[2 * (m * ni + sl) + 1];
+                    dfx += ax * bx - ay * by;
+                    dfy += ax * by + ay * bx;
+                }
             if (sk >= 0)
-                for (int m = 0; m < ni; m++)
-                    fd = cadd(fd, cmul(cmk(fp[2 * (sk * ni + m)], sgn * fp[2 * (sk * ni + m) + 1]), dl(d.imp[m], l)));
-            cplx C = csub(df, fd);
-            cplx Q = cmk(qr[(size_t)p * nn(d) + e], sgn * qi[(size_t)p * nn(d) + e]);
+                for (int m = 0; m < ni; m++) {
+                    const R ax = (R)fp[2 * (sk * ni + m)], ay = sgn * (R)fp[2 * (sk * ni + m) + 1];
+                    const R bx = dre(d.imp[m], l), by = dim(d.imp[m], l);
+                    fdx += ax * bx - ay * by;
+                    fdy += ax * by + ay * bx;
+                }
+            const R Cx = dfx - fdx, Cy = dfy - fdy;
+            const R QFx = (R)qr[(size_t)p * nn(d) + e] + Fx, QFy = sgn * (R)qi[(size_t)p * nn(d) + e] + Fy;
             const double* co = coef + (size_t)(mu * M + be) * 6;
-            cplx QF = cadd(Q, F);
             // 2 Re{a1 C + a2 (Q + F) + a3 Delta}
-            acc += 2.0 * (co[0] * C.x - co[1] * C.y + co[2] * QF.x - co[3] * QF.y + co[4] * D.x - co[5] * D.y);
+            acc += (R)2 * ((R)co[0] * Cx - (R)co[1] * Cy + (R)co[2] * QFx - (R)co[3] * QFy + (R)co[4] * Dx -
+                           (R)co[5] * Dy);
         }
-        out[e] = acc;
+        out[e] = (double)acc;
+    }
+}
+
+// dGamma <- (dGamma - dGamma^T) / 2: the float assembly of the mixed forms computes each
+// element on its own, so its rounding leaves a symmetric part of relative size 1e-7 that the
+// exact dGamma (tangent to the pure states) does not have
+__global__ void antisymmetrise_kernel(double* a, int n) {
+    double* x = a + (size_t)blockIdx.y * n * n;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)n * n; e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n), l = (int)(e % n);
+        if (k > l) continue;
+        const double v = k == l ? 0.0 : 0.5 * (x[e] - x[(size_t)l * n + k]);
+        x[e] = v;
+        x[(size_t)l * n + k] = -v;
     }
 }
 

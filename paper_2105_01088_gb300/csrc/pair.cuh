@@ -207,10 +207,16 @@ __global__ void pair_lr_kernel(InstDev d, const double* si, const double* imd, c
 // On the FP64 path the outputs alias the inputs (qr_out = xa_in, qi_out = wr_in):
 // each element is read and then written by the same thread.
 template <typename T>
-__global__ void pair_q_kernel(InstDev d, const double* si, const double* imd, const double* lr, const T* va,
-                              const T* xa_in, const T* wr_in, double* qr_out, double* qi_out) {
+__global__ void __launch_bounds__(256) pair_q_kernel(InstDev d, const double* si, const double* imd, const double* lr,
+                                                     const T* va, const T* xa_in, const T* wr_in, double* qr_out,
+                                                     double* qi_out) {
+    // 32 x 32 output tiles; V^T is staged through shared memory so both reads of V coalesce
+    __shared__ double vt[32][33];
     const int p = blockIdx.y;
     const int n = d.n, ni = d.nimp;
+    const int ntile = (n + 31) / 32;
+    const int k0 = (blockIdx.x / ntile) * 32, l0 = (blockIdx.x % ntile) * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const double* s = si + (size_t)p * nn(d);
     const double* im = imd + (size_t)p * nn(d);
     const double* L1 = lr + (size_t)p * 2 * n * ni;
@@ -220,8 +226,15 @@ __global__ void pair_q_kernel(InstDev d, const double* si, const double* imd, co
     const T* W = wr_in + (size_t)p * nn(d);
     double* Qr = qr_out + (size_t)p * nn(d);
     double* Qi = qi_out + (size_t)p * nn(d);
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn(d); e += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e / n), l = (int)(e % n);
+    for (int j = ty; j < 32; j += 8) {            // vt[j][c] = V[l0 + j][k0 + c]
+        const int r = l0 + j, c = k0 + tx;
+        vt[j][tx] = (r < n && c < n) ? (double)v[(size_t)r * n + c] : 0.0;
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int k = k0 + j, l = l0 + tx;
+        if (k >= n || l >= n) continue;
+        const size_t e = (size_t)k * n + l;
         double a1 = 0.0, a2 = 0.0;
         for (int m = 0; m < ni; m++) {
             const int im_m = d.imp[m];
@@ -230,7 +243,7 @@ __global__ void pair_q_kernel(InstDev d, const double* si, const double* imd, co
             a2 += 4.0 * L2[k * ni + m] * s_ml - L1[k * ni + m] * im[(size_t)im_m * n + l];
         }
         const double qr = (double)X[e] + 4.0 * (double)W[e] + 2.0 * a1;
-        const double qi = a2 - 2.0 * ((double)v[e] - (double)v[(size_t)l * n + k]);
+        const double qi = a2 - 2.0 * ((double)v[e] - vt[tx][j]);      // V[l][k] = vt[l - l0][k - k0]
         Qr[e] = qr;
         Qi[e] = qi;
     }

@@ -955,7 +955,8 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
             pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.fimp, I.lr);
             counted();
         }
-        pair_q_kernel<float><<<dim3(gch, P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va32, I.xa32, I.wr32, I.xa, I.wr);
+        const unsigned qt = (unsigned)(((n + 31) / 32) * ((n + 31) / 32));
+        pair_q_kernel<float><<<dim3(qt, P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va32, I.xa32, I.wr32, I.xa, I.wr);
         counted();
     } else if (P > 0) {
         // T1 = S^{-1} (A + Re Fimp)  (into work), Wr = T1 S^{-1}
@@ -983,7 +984,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
             pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.fimp, I.lr);
             counted();
         }
-        pair_q_kernel<double><<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va, I.xa,
+        pair_q_kernel<double><<<dim3((unsigned)(((n + 31) / 32) * ((n + 31) / 32)), P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va, I.xa,
                                                                                    I.wr, I.xa, I.wr);
         counted();
     } else {
@@ -992,9 +993,16 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     // algorithmic bytes: pair_q reads Si, Im, V (twice), X, Wr and writes Qr, Qi; the EOM
     // reads Si, Im, Qr, Qi once per receiver of each pair plus Gamma, GFG and writes dGamma
     c->stage_bytes[SGS_STAGE_EOM_ASSEMBLY] += 8.0 * nn * (7.0 * P + 8.0 * P + 3.0 * M);
-    eom_kernel<<<dim3(grid_chunks(nn, 256, 1024), M), 256, 0, st>>>(d, I.si, I.imd, I.xa, I.wr, I.fimp,
-                                                                   I.fimp_state, I.s[4], I.coef, I.pair_index,
-                                                                   I.dgamma);
+    if (I.tc_kind >= 0) {
+        eom_kernel<float><<<dim3(grid_chunks(nn, 256, 1024), M), 256, 0, st>>>(d, I.si, I.imd, I.xa, I.wr, I.fimp,
+                                                                              I.fimp_state, I.s[4], I.coef,
+                                                                              I.pair_index, I.dgamma);
+        antisymmetrise_kernel<<<dim3(grid_chunks(nn, 256, 1024), M), 256, 0, st>>>(I.dgamma, n);
+        counted();
+    } else
+        eom_kernel<double><<<dim3(grid_chunks(nn, 256, 1024), M), 256, 0, st>>>(d, I.si, I.imd, I.xa, I.wr, I.fimp,
+                                                                               I.fimp_state, I.s[4], I.coef,
+                                                                               I.pair_index, I.dgamma);
     counted();
     return cudaGetLastError();
 }
