@@ -294,8 +294,10 @@ def run_sgs(args):
         if os.path.exists(tfile):
             t = json.load(open(tfile)).get(f"gemm_f64_all_{args.precision}", {})
             # counters hold for the same shape, panel widths and FP64 path only
+            # and for the same launch sequence (a changed step shows as another launch count)
             if (t.get("n") == n and t.get("rank") == w.rank and t.get("fp64_path") == args.fp64_path
-                    and t.get("panel_widths_gj_pf") == list(solver.tuning(0)[:2])):
+                    and t.get("panel_widths_gj_pf") == list(solver.tuning(0)[:2])
+                    and t.get("launches_per_step") * args.steps == int(g_n)):
                 traffic = t.get("bytes_per_launch")
         roof = {"bound": "alu" if args.fp64_path == "fma" else "tensor", "achieved": achieved, "peak": peak_fp64,
                 "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": traffic,
