@@ -308,14 +308,31 @@ def run_sgs(args):
                                f"kind {1 if args.fp64_path == 'fma' else 0}); not in MEASURED_PEAKS.json"}
     tc_roof = None
     if args.precision != "fp64" and prof["eom_v"][0] > 0:
+        # V = D W on the tensor cores, per pair: 2 n^3 flops; algorithmic bytes = the two operands
+        # (n x ldp, hi and lo parts for 3xTF32) read once and the fp32 product written once
         bf16 = peaks.get("bf16_tflops", 1900.0)
+        hbm = peaks.get("hbm_gbs", 6800.0)
         ratio = {"tf32": 1.1 / 2.25, "3xtf32": 1.1 / 2.25 / 3.0, "bf16": 1.0}[args.precision]
+        tc_peak = bf16 * ratio
         v_ms, v_fl, _ = prof["eom_v"]
-        a = v_fl / (v_ms * 1e-3) / 1e12
+        ldp = (n + 7) // 8 * 8
+        esz = 2 if args.precision == "bf16" else 4
+        parts = 2 if args.precision == "3xtf32" else 1
+        pairs = w.rank * (w.rank - 1) // 2
+        v_bytes = pairs * (2.0 * parts * n * ldp * esz + 4.0 * n * n) * args.steps
+        flops_s = v_fl / (v_ms * 1e-3)
+        bytes_s = v_bytes / (v_ms * 1e-3)
+        intensity = v_fl / v_bytes
+        hbm_bound = intensity * hbm * 1e9 / 1e12 < tc_peak
         kname = "gemm_tma_kernel (TMA-fed" if args.tc_loader == "tma" else "gemm_tc_kernel (cp.async-fed"
-        tc_roof = {"bound": "tensor", "kernel": f"{kname} tcgen05 {args.precision}, V = D W)",
-                   "achieved": a, "peak": bf16 * ratio, "unit": "TFLOP/s", "frac": a / (bf16 * ratio),
-                   "peak_source": "MEASURED_PEAKS.json bf16_tflops x nominal ratio "
+        tc_roof = {"bound": "hbm" if hbm_bound else "tensor",
+                   "kernel": f"{kname} tcgen05 {args.precision}, V = D W)",
+                   "achieved": bytes_s / 1e9 if hbm_bound else flops_s / 1e12,
+                   "peak": hbm if hbm_bound else tc_peak, "unit": "GB/s" if hbm_bound else "TFLOP/s",
+                   "frac": (bytes_s / 1e9 / hbm) if hbm_bound else (flops_s / 1e12 / tc_peak),
+                   "tflops": flops_s / 1e12, "tensor_peak_tflops": tc_peak,
+                   "arithmetic_intensity_flops_per_byte": intensity,
+                   "peak_source": "MEASURED_PEAKS.json hbm_gbs; tensor peak = bf16_tflops x nominal ratio "
                                   f"({args.precision}: {ratio:.3f})"}
     stages = {s: {"ms_per_step": v[0] / args.steps, "tflops": (v[1] / (v[0] * 1e-3) / 1e12) if v[0] > 0 and v[1] > 0
                   else None} for s, v in prof.items()}
