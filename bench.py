@@ -50,8 +50,12 @@ def parse():
     ap.add_argument("--max-steps", type=int, default=400, help="serving: step cap per solve")
     ap.add_argument("--serving-dtau", type=float, default=0.2, help="serving: imaginary-time step")
     ap.add_argument("--rank", type=int, default=0, help="override the ansatz rank M (profiling cases)")
-    ap.add_argument("--fp64-path", default="fma", choices=["fma", "mma"], help="FP64 product pipe")
-    ap.add_argument("--tc-loader", default="tma", choices=["tma", "cp"], help="tensor-core operand staging")
+    ap.add_argument("--fp64-path", default="fma", choices=["fma", "mma", "emulated"],
+                    help="FP64 products: FMA pipe, m8n8k4 MMA, or emulated on the bf16 tensor cores")
+    ap.add_argument("--emulation-scratch-gb", type=float, default=6.0,
+                    help="emulated FP64 products: slice scratch per instance (GB)")
+    ap.add_argument("--tc-loader", default="tma", choices=["tma", "tmap", "cp"],
+                    help="tensor-core operand staging: TMA one CTA per tile, TMA persistent, or cp.async")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--accuracy-steps", type=int, default=0,
                     help="run the FP64 form and --precision side by side for this many steps and report the "
@@ -201,6 +205,20 @@ def run_reference(args):
     return 0
 
 
+FP64_PATHS = {"mma": 0, "fma": 1, "emulated": 2}
+
+
+def set_fp64_path(sgs, args):
+    sgs.set_fp64_gemm_path(FP64_PATHS[args.fp64_path])
+    if args.fp64_path == "emulated":
+        sgs.set_emulation_scratch(int(args.emulation_scratch_gb * 1e9))
+
+
+def dtype_of(args):
+    d = DTYPES[args.precision]
+    return d.replace("f64", "f64e", 1) if args.fp64_path == "emulated" else d
+
+
 def run_sgs(args):
     import torch
 
@@ -215,8 +233,8 @@ def run_sgs(args):
     import paper_2105_01088_gb300 as sgs
 
     sgs.use_torch_allocator()
-    sgs.set_fp64_gemm_path(args.fp64_path == "fma")
-    sgs.set_tc_loader(args.tc_loader == "tma")
+    set_fp64_path(sgs, args)
+    sgs.set_tc_loader(args.tc_loader != "cp", persistent=args.tc_loader == "tmap")
     w = workload(args.workload, args.rank)
     p = w.model
     prec = PRECISIONS[args.precision]
@@ -227,7 +245,15 @@ def run_sgs(args):
     metric = f"imag-time steps/s at 2N={2 * p.n_modes},M={w.rank}"
     peak_fp64_mma = sgs.probe_peak(0)
     peak_fp64_fma = sgs.probe_peak(1)
-    peak_fp64 = peak_fp64_fma if args.fp64_path == "fma" else peak_fp64_mma
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    # the emulated path issues 36 bf16 slice products per FP64 product: its ceiling is the
+    # measured bf16 rate / 36
+    peak_fp64 = {"fma": peak_fp64_fma, "mma": peak_fp64_mma,
+                 "emulated": peaks.get("bf16_tflops", 1900.0) / 36.0}[args.fp64_path]
 
     solver.step(args.warmup)
     clocks = ClockSampler(local)
@@ -280,11 +306,6 @@ def run_sgs(args):
 
     # roofline of the dominant kernel, gemm_f64_kernel (the FP64 m8n8k4 MMA GEMM: ~89% of the FP64 step's
     # kernel time, most of the mixed step's): algorithmic flops of all its launches / their summed time
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
     g_ms, g_fl, g_n = gemm_prof
     roof = None
     if g_ms > 0:
@@ -299,13 +320,20 @@ def run_sgs(args):
                     and t.get("panel_widths_gj_pf") == list(solver.tuning(0)[:2])
                     and t.get("launches_per_step") * args.steps == int(g_n)):
                 traffic = t.get("bytes_per_launch")
+        if args.fp64_path == "emulated":
+            kern = ("oz_gemm_kernel with its slicing kernels (FP64 products emulated on the bf16 tensor cores; "
+                    "all FP64 products: Gauss-Jordan and Pfaffian updates, pair and state products)")
+            src = ("MEASURED_PEAKS.json bf16_tflops / 36 (36 bf16 slice products per FP64 product); achieved = "
+                   "algorithmic FP64 flops / time of the products including slicing")
+        else:
+            kern = (f"gemm_f64_kernel (FP64 {args.fp64_path.upper()}; all its launches: Gauss-Jordan and "
+                    "Pfaffian updates, pair and state products)")
+            src = (f"measured live: FP64 {args.fp64_path.upper()} throughput probe (sgs_probe_peak "
+                   f"kind {1 if args.fp64_path == 'fma' else 0}); not in MEASURED_PEAKS.json")
         roof = {"bound": "alu" if args.fp64_path == "fma" else "tensor", "achieved": achieved, "peak": peak_fp64,
-                "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": traffic,
-                "kernel": f"gemm_f64_kernel (FP64 {args.fp64_path.upper()}; all its launches: Gauss-Jordan and "
-                          "Pfaffian updates, pair and state products)",
+                "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": traffic, "kernel": kern,
                 "launches": int(g_n), "flops_per_launch": g_fl / max(g_n, 1), "ms_per_launch": g_ms / max(g_n, 1),
-                "peak_source": f"measured live: FP64 {args.fp64_path.upper()} throughput probe (sgs_probe_peak "
-                               f"kind {1 if args.fp64_path == 'fma' else 0}); not in MEASURED_PEAKS.json"}
+                "peak_source": src}
     tc_roof = None
     if args.precision != "fp64" and prof["eom_v"][0] > 0:
         # V = D W on the tensor cores, per pair: 2 n^3 flops; algorithmic bytes = the two operands
@@ -324,7 +352,8 @@ def run_sgs(args):
         bytes_s = v_bytes / (v_ms * 1e-3)
         intensity = v_fl / v_bytes
         hbm_bound = intensity * hbm * 1e9 / 1e12 < tc_peak
-        kname = "gemm_tma_kernel (TMA-fed" if args.tc_loader == "tma" else "gemm_tc_kernel (cp.async-fed"
+        kname = {"tma": "gemm_tma_kernel (TMA-fed", "tmap": "gemm_tmap_kernel (persistent TMA-fed",
+                 "cp": "gemm_tc_kernel (cp.async-fed"}[args.tc_loader]
         tc_roof = {"bound": "hbm" if hbm_bound else "tensor",
                    "kernel": f"{kname} tcgen05 {args.precision}, V = D W)",
                    "achieved": bytes_s / 1e9 if hbm_bound else flops_s / 1e12,
@@ -339,8 +368,8 @@ def run_sgs(args):
 
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
-            "config": config_of(w, args.precision),
+            "vs_baseline": None, "dtype": dtype_of(args), "data": "synthetic",
+            "config": dict(config_of(w, args.precision), fp64_products=args.fp64_path),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "roofline": roof, "tc_roofline": tc_roof, "clocks": ck, "stages": stages,
             "energy_last": float(E[0, -1]), "panel_widths_gj_pf": list(solver.tuning(0)[:2]),
@@ -437,8 +466,8 @@ def run_batched(args):
     import paper_2105_01088_gb300 as sgs
 
     sgs.use_torch_allocator()
-    sgs.set_fp64_gemm_path(args.fp64_path == "fma")
-    sgs.set_tc_loader(args.tc_loader == "tma")
+    set_fp64_path(sgs, args)
+    sgs.set_tc_loader(args.tc_loader != "cp", persistent=args.tc_loader == "tmap")
     prec = PRECISIONS[args.precision]
     ws = inp.batched_workloads(args.instances, n_bath=(16, args.max_bath))
     mine = ws[rank::world]
@@ -493,7 +522,7 @@ def run_batched(args):
     line = {"metric": "instance-steps/s (batched uneven impurity instances)", "value": value,
             "unit": "instance-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "strong",
-            "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
+            "vs_baseline": None, "dtype": dtype_of(args), "data": "synthetic",
             "config": {"workload": f"batched: {len(ws)} Anderson instances, bath L ~ U{{16..{args.max_bath}}}, "
                                    "M in {8,16,32}, U ~ U[0,8], eps_d = -U/2, V ~ U[0.2,1], ds = 0.05",
                        "n_range": [min(ns), max(ns)], "precision": args.precision,

@@ -279,17 +279,33 @@ sgs_status sgs_get_profile(const sgs_ctx* ctx, double* ms, double* flops, double
  * kernel (their sum shows whether the two share one pipe). */
 sgs_status sgs_probe_peak(int kind, double* tflops);
 
-/* Compute path of every FP64 product (process-wide): 1 = FP64 FMA on the CUDA
- * cores (default), 0 = the m8n8k4 FP64 MMA.  Both give FP64 results; on GB300
- * they share one pipe and FMA issues faster. */
-void sgs_set_fp64_gemm_path(int use_fma);
+/* Compute path of every FP64 product (process-wide; path 2 is read when an
+ * instance is admitted, which then owns its slice scratch): 1 = FP64 FMA on
+ * the CUDA cores (default), 0 = the m8n8k4 FP64 MMA (both FP64; on GB300 they
+ * share one pipe and FMA issues faster), 2 = emulated on the bf16 tensor
+ * cores: each operand row is split into eight signed 7-bit integer slices
+ * under a common power of two, the 36 slice products of combined weight above
+ * 2^-63 are accumulated exactly in fp32 (K in chunks of 512) and combined in
+ * 64-bit integers; the error is at most that of the FP64 kernel's own
+ * rounding.  Any other nonzero value selects 1. */
+void sgs_set_fp64_gemm_path(int path);
+
+/* Emulated FP64 products (path 2): device scratch per instance for the
+ * operand slices, 16 (m + n) k bytes per batch entry of an m x n x k product
+ * (default cap 2 GiB; batches that do not fit run in chunks).  Read at
+ * admission; at least 1 MiB. */
+void sgs_set_emulation_scratch(size_t bytes);
 
 /* Operand staging of the tensor-core products (process-wide, read when an
  * instance is admitted and at each launch): 1 = Tensor Memory Accelerator
- * tile loads into 128-byte-swizzled shared memory with an mbarrier pipeline
- * (default), 0 = cp.async copies into the unswizzled layout.  Both issue the
- * same tcgen05.mma sequence, so results are identical. */
-void sgs_set_tc_loader(int use_tma);
+ * tile loads into 128-byte-swizzled shared memory with an mbarrier pipeline,
+ * one CTA per output tile (default); 2 = the same loads in a persistent
+ * kernel, one CTA per SM looping over the tiles with two TMEM accumulators so
+ * that one tile's epilogue overlaps the next tile's loads and MMAs; 0 =
+ * cp.async copies into the unswizzled layout.  All three issue the same
+ * tcgen05.mma sequence per tile, so results are identical.  Any other nonzero
+ * value selects 1. */
+void sgs_set_tc_loader(int loader);
 
 /* Majorana form of the Anderson impurity of Sec. IV (H_0 + H_I) with
  * n_channels open bath chains of n_bath sites, hybridisation V, hopping t,
@@ -317,10 +333,21 @@ int sgs_build_2ck(int L, double J, double t, double* A, int* quartic_idx, double
  *   pivot.
  * sgs_kernel_pfaffian: batch complex antisymmetric n x n matrices (re, im
  *   interleaved) -> Pf = phase * exp(logabs), phase as (re, im).
- * sgs_kernel_dgemm: batch C = A B (n x n, FP64). */
+ * sgs_kernel_dgemm: batch C = A B (n x n, FP64).
+ * sgs_kernel_gemm: batch C = alpha op(A) op(B) + beta Cin + diag I through the
+ *   library's FP64 product on the current path, op(A) m x k, op(B) k x n, all
+ *   row-major and contiguous per batch entry (A stored k x m if trans_a, B
+ *   stored n x k if trans_b); Cin may be NULL.  C is in/out: mode 0 writes
+ *   every element; mode 1 (m = n) computes the strictly lower part and
+ *   writes C and -C^T with a zero diagonal; mode 2 (m = n, Gauss-Jordan
+ *   delayed update) leaves columns gj_k0 .. gj_k0 + gj_b - 1 of C unchanged
+ *   and does not add Cin on rows in that range. */
 sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, double* logabsdet);
 sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase, double* logabs);
 sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, double* C);
+sgs_status sgs_kernel_gemm(const double* A, const double* B, const double* Cin, int m, int n, int k, int trans_a,
+                           int trans_b, double alpha, double beta, double diag, int mode, int gj_k0, int gj_b,
+                           int batch, double* C);
 
 /* sgs_kernel_gemm_tc: batch C = A B on the tcgen05 tensor cores, A: m x k
  * row-major, Bt: n x k row-major (= B^T, the K-major form the tensor core

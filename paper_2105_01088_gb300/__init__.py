@@ -85,10 +85,14 @@ SIGNATURES = {
     "sgs_get_profile": (ctypes.c_int, [_ctxp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "sgs_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
     "sgs_set_fp64_gemm_path": (None, [ctypes.c_int]),
+    "sgs_set_emulation_scratch": (None, [ctypes.c_size_t]),
     "sgs_set_tc_loader": (None, [ctypes.c_int]),
     "sgs_kernel_inverse": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_pfaffian": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_dgemm": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp]),
+    "sgs_kernel_gemm": (ctypes.c_int, [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]),
     "sgs_kernel_gemm_tc": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, _dp]),
     "sgs_kernel_inverse_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -414,14 +418,27 @@ class Solver:
 
 # ------------------------------------------------------------ building blocks
 
-def set_tc_loader(use_tma=True):
-    """Tensor-core operand staging: TMA tile loads (default) or cp.async."""
-    _lib.sgs_set_tc_loader(1 if use_tma else 0)
+def set_tc_loader(use_tma=True, persistent=False):
+    """Tensor-core operand staging: TMA tile loads (default; persistent=True
+    selects the one-CTA-per-SM form) or cp.async."""
+    _lib.sgs_set_tc_loader((2 if persistent else 1) if use_tma else 0)
 
 
-def set_fp64_gemm_path(use_fma=True):
-    """FP64 products on the FMA pipe (default) or the m8n8k4 MMA."""
-    _lib.sgs_set_fp64_gemm_path(1 if use_fma else 0)
+FP64_MMA, FP64_FMA, FP64_EMULATED = 0, 1, 2
+
+
+def set_fp64_gemm_path(path=FP64_FMA):
+    """FP64 products on the FMA pipe (1, default), the m8n8k4 MMA (0), or
+    emulated on the bf16 tensor cores (2; read when an instance is admitted).
+    True / False select 1 / 0."""
+    if path is True or path is False:
+        path = int(path)
+    _lib.sgs_set_fp64_gemm_path(int(path))
+
+
+def set_emulation_scratch(nbytes):
+    """Per-instance slice scratch of the emulated FP64 path (read at admission)."""
+    _lib.sgs_set_emulation_scratch(int(nbytes))
 
 
 def probe_peak(kind=0):
@@ -478,6 +495,26 @@ def batched_pfaffian(Y):
     if st != 0:
         raise SGSError(st, "batched pfaffian")
     return ph[:, 0] + 1j * ph[:, 1], la
+
+
+def batched_gemm(A, B, Cin=None, alpha=1.0, beta=0.0, diag=0.0, trans_a=False, trans_b=False, mode=0,
+                 gj=(0, 1), C=None):
+    """batch C = alpha op(A) op(B) + beta Cin + diag I through the library's FP64
+    product on the current path (mode 0 full, 1 antisymmetric, 2 Gauss-Jordan
+    update with panel columns gj = (k0, b) left unchanged).  C (optional) holds
+    the output's initial values."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    b = A.shape[0]
+    m, k = (A.shape[2], A.shape[1]) if trans_a else (A.shape[1], A.shape[2])
+    n = B.shape[1] if trans_b else B.shape[2]
+    out = np.zeros((b, m, n)) if C is None else np.array(C, dtype=np.float64, order="C", copy=True)
+    cin = None if Cin is None else np.ascontiguousarray(Cin, dtype=np.float64)
+    st = _lib.sgs_kernel_gemm(_ptr(A), _ptr(B), _ptr(cin) if cin is not None else None, m, n, k, int(trans_a),
+                              int(trans_b), alpha, beta, diag, mode, gj[0], gj[1], b, _ptr(out))
+    if st != 0:
+        raise SGSError(st, "batched gemm")
+    return out
 
 
 def batched_dgemm(A, B):

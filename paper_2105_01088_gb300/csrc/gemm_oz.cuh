@@ -1,0 +1,674 @@
+// Batched FP64 GEMM emulated on the bf16 tensor cores (tcgen05 kind::f16) by
+// splitting both operands into integer slices (the Ozaki scheme: Ozaki, Ogita,
+// Oishi and Rump, Numer. Algorithms 59 (2012); its tensor-core forms by Mukunoki
+// et al. and Ootomo et al.).  GB300's FP64 pipe issues about 1.25 TFLOP/s while
+// its bf16 tensor cores issue over 2 PFLOP/s, so the products of the step run
+// here when the emulated path is selected; results are at least as accurate as
+// the FP64 FMA kernel's (see the error budget below).
+//
+// Slicing.  Every row r of op(A) (K-major) gets the exponent field E_r of its
+// largest element, so |a_rk| < 2^(E_r - 1022).  The element is rounded to the
+// signed integer X = a_rk 2^(56 - (E_r - 1022)) (|X| < 2^56) and written as
+// eight balanced base-128 digits, most significant first:
+//     X = sum_{i=0..7} t_i 2^(7 (7 - i)),  |t_0| <= 128, |t_i| <= 64 (i >= 1),
+// so a_rk = 2^(E_r - 1022) sum_i t_i 2^(-7 (i + 1)) up to 2^-57 of the row's
+// scale.  Each digit is a bf16 (at most 8 significant bits: exact).  Columns of
+// op(B) are sliced the same way.  The digit extraction is integer arithmetic on
+// the IEEE bit pattern (FP64 arithmetic is the scarce resource here).
+//
+// Products.  The slice products t_i(A) t_j(B) with i + j <= 7 (36 of the 64)
+// are accumulated into eight fp32 TMEM accumulators, one per group G = i + j
+// (weight 2^(-7 (G + 2))).  Each product term is an integer of magnitude at
+// most 2^14 (i = j = 0), 2^13 (one index 0) or 2^12, so over a K chunk of 512
+// the sums of groups G <= 5 stay within 2^24 and are exact in fp32; groups 6
+// and 7 may round, by at most 2^-47 of the output scale, below FP64's own
+// rounding of a 512-term dot product.  K beyond 512 runs as further launches
+// that add onto the output (one FP64 rounding per chunk).  The dropped products
+// (i + j >= 8) weigh at most 2^-63 per term.
+//
+// Combination.  The eight group sums are converted to integers and combined
+// exactly, hi = sum_{G<4} v_G 2^(7 (3 - G)), lo = sum_{G>=4} v_G 2^(7 (7 - G)),
+// V = hi 2^28 + lo in 128-bit integer arithmetic; V is rounded once to 53 bits
+// and given the exponent E_r + F_c - 2107 (plus that of alpha when alpha is a
+// power of two, else one multiplication), all in integer arithmetic on the bit
+// pattern.  The GemmBatch epilogue (beta Cin, beta2 Cin2, diag, FULL / SKEW / GJ
+// modes, pass-through of inactive batch entries) is applied as in gemm_f64.
+//
+// Kernels per batch chunk: exponents of op(A) and of op(B), slices of each (a
+// 32 x 32 tile transpose through shared memory where the operand is stored
+// K-strided), then the product kernel: 128 x 64 output tile per CTA of 10 warps.
+// Warp 8 (lane 0) streams, per 64-element K slab, the eight B slices (64 x 128 B
+// each, double-buffered: the next slab's are issued while the current slab's
+// MMAs run) and the eight A slices (128 x 128 B) through a six-deep ring with
+// TMA (128-byte swizzle, zero fill beyond K); warp 9 (lane 0) issues the MMAs
+// into the eight accumulators (all 512 TMEM columns), one MMA of N up to 256
+// per A slice and K16 step (the B slices and the groups they feed are adjacent); warps 0-7 load
+// the tile's Cin terms while the MMAs run (for in-place updates every Cin
+// element is read before the CTA stores any), then drain TMEM, combine, and
+// write the output through a shared-memory tile (coalesced rows).
+// Every mbarrier wait is bounded; on a timeout the launch records
+// SGS_DEV_TC_TIMEOUT in the error word, waits (bounded) for its loads and MMAs
+// in flight, frees TMEM and returns.
+#pragma once
+#include "gemm_f64.cuh"
+#include "gemm_tma.cuh"
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace sgs {
+
+#define OZ_S 8                // slices per operand
+#define OZ_G 8                // accumulator groups G = i + j <= 7
+#define OZ_BM 128
+#define OZ_BN 64
+#define OZ_KS 64              // K elements of one 128-byte slab row
+#define OZ_KC 512             // K per exactly accumulated chunk
+#define OZ_RING 6             // depth of the A-slice ring
+#define OZ_SLAB_A (OZ_BM * 128)
+#define OZ_SLAB_B (OZ_BN * 128)
+#define OZ_SMEM (2 * OZ_S * OZ_SLAB_B + OZ_RING * OZ_SLAB_A + 1024)
+#define OZ_TS (OZ_BN + 1)     // padded row stride (doubles) of the epilogue tile
+#define OZ_EPI_WARPS 8        // epilogue warps (two per TMEM lane quarter: one per column half)
+#define OZ_THREADS (32 * (OZ_EPI_WARPS + 2))
+
+// device scratch of one owner (an instance, or a temporary context): slices and
+// exponent fields of one batch chunk
+struct OzBuf {
+    uint8_t* base = nullptr;
+    size_t bytes = 0;
+};
+
+// K-major operand rows as seen by the slicer: element (r, k) of op(X) is
+// X[b][off + r * ld + k] (strided = 0) or X[b][off + k * ld + r] (strided = 1),
+// plus s2 times the same element of X2 when X2 is given
+struct OzOperand {
+    const double* const* X;
+    const double* const* X2;
+    double s2;
+    long long off;
+    int ld, strided;
+    int rows, k;              // K-major rows and K
+    int rows_pad, kp;         // padded rows (a multiple of the tile) and row pitch (a multiple of 8)
+    int b0;                   // first batch entry of the chunk
+    const int* active; int active_cmp;
+    int* expo;                // [chunk][rows_pad] exponent fields
+    uint16_t* slices;         // [chunk][OZ_S][rows_pad][kp] bf16 digits
+};
+
+__device__ __forceinline__ int oz_expo_field(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    int e = (int)((u >> 52) & 0x7ff);
+    if (e == 0 && (u << 1) != 0ull) e = 1;       // subnormal: scale of the smallest normal
+    return e;
+}
+
+__device__ __forceinline__ double oz_load(const OzOperand& o, const double* x, const double* x2, int r, int k) {
+    const long long off = o.strided ? (long long)k * o.ld + r : (long long)r * o.ld + k;
+    double v = x[off];
+    if (x2) v = fma(o.s2, x2[off], v);
+    return v;
+}
+
+__device__ __forceinline__ bool oz_active(const int* flag, int cmp, int b) {
+    return flag == nullptr || flag[b] > cmp;
+}
+
+// exponent field E_r = max_k field(op(X)[r][k]) of every K-major row.  Strided operands:
+// a block of 32 x 8 threads reduces 32 rows (threads along r read coalesced, eight k
+// apart); contiguous rows: one warp per row
+__global__ void __launch_bounds__(256) oz_expo_kernel(OzOperand o) {
+    const int bl = blockIdx.y, b = o.b0 + bl;
+    if (!oz_active(o.active, o.active_cmp, b)) return;
+    const double* x = o.X[b] + o.off;
+    const double* x2 = o.X2 ? o.X2[b] + o.off : nullptr;
+    if (o.strided) {
+        __shared__ int red[8][32];
+        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+        const int r = blockIdx.x * 32 + tx;
+        int e = 0;
+        if (r < o.rows) {
+#pragma unroll 4
+            for (int k = ty; k < o.k; k += 8) e = max(e, oz_expo_field(oz_load(o, x, x2, r, k)));
+        }
+        red[ty][tx] = e;
+        __syncthreads();
+        if (ty == 0 && r < o.rows) {
+#pragma unroll
+            for (int t = 1; t < 8; t++) e = max(e, red[t][tx]);
+            o.expo[(size_t)bl * o.rows_pad + r] = e;
+        }
+    } else {
+        const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+        if (r >= o.rows) return;
+        int e = 0;
+#pragma unroll 4
+        for (int k = lane; k < o.k; k += 32) e = max(e, oz_expo_field(oz_load(o, x, x2, r, k)));
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, s));
+        if (lane == 0) o.expo[(size_t)bl * o.rows_pad + r] = e;
+    }
+}
+
+// the eight digits of X = round(v 2^(1078 - E)) (E = the row's exponent field, E > 0)
+__device__ __forceinline__ void oz_digits(double v, int E, int t[OZ_S]) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    int f = (int)((u >> 52) & 0x7ff);
+    unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    if (f == 0) f = 1;
+    else m |= 1ull << 52;
+    const int sh = f - E + 3;                     // v 2^(1078 - E) = m 2^sh, sh <= 3
+    unsigned long long a;
+    if (sh >= 0) a = m << sh;
+    else if (sh <= -63) a = 0;
+    else a = (m + (1ull << (-sh - 1))) >> (-sh);  // round half up on the magnitude
+    long long X = (long long)a;
+    if (u >> 63) X = -X;
+#pragma unroll
+    for (int i = OZ_S - 1; i >= 1; --i) {
+        int d = (int)(X & 127);
+        d = d >= 64 ? d - 128 : d;                // balanced digit in [-64, 63]
+        t[i] = d;
+        X = (X - d) >> 7;                         // exact: X - d is a multiple of 128
+    }
+    t[0] = (int)X;                                // |t_0| <= 128
+}
+
+__device__ __forceinline__ uint16_t oz_bf16_bits(int d) {
+    // d has at most 8 significant bits, so the float's top half is the exact bf16
+    return (uint16_t)(__float_as_uint((float)d) >> 16);
+}
+
+// slices of a 32 (rows) x 32 (K) tile; rows in [rows, rows_pad) are written as zeros,
+// K beyond k is left to the tensor map's zero fill
+__global__ void __launch_bounds__(256) oz_slice_kernel(OzOperand o) {
+    __shared__ double tile[32][33];
+    const int bl = blockIdx.z, b = o.b0 + bl;
+    if (!oz_active(o.active, o.active_cmp, b)) return;
+    const double* x = o.X[b] + o.off;
+    const double* x2 = o.X2 ? o.X2[b] + o.off : nullptr;
+    const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        if (o.strided) {
+            const int k = k0 + ty + 8 * j, r = r0 + tx;
+            tile[tx][ty + 8 * j] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0.0;
+        } else {
+            const int r = r0 + ty + 8 * j, k = k0 + tx;
+            tile[ty + 8 * j][tx] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0.0;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int rr = ty + 8 * j, r = r0 + rr, k = k0 + tx;
+        if (r >= o.rows_pad || k >= o.k) continue;
+        const int E = r < o.rows ? o.expo[(size_t)bl * o.rows_pad + r] : 0;
+        int t[OZ_S];
+        if (E > 0) oz_digits(tile[rr][tx], E, t);
+        else {
+#pragma unroll
+            for (int i = 0; i < OZ_S; i++) t[i] = 0;
+        }
+#pragma unroll
+        for (int i = 0; i < OZ_S; i++)
+            o.slices[(((size_t)bl * OZ_S + i) * o.rows_pad + r) * o.kp + k] = oz_bf16_bits(t[i]);
+    }
+}
+
+struct OzGemm {
+    CUtensorMap ta, tb;       // slices: 3-D [chunk * 8][rows_pad][k] bf16, box 64 x rows x 1
+    GemmBatch g;              // sizes, output and epilogue fields (batch index = b0 + local)
+    int b0;
+    int m_pad, n_pad;
+    const int* ea; const int* eb;
+    int* err;
+    int alpha_pow2;           // alpha = +-2^alpha_e (no per-batch factor): folded into the exponent
+    int alpha_e, alpha_neg;
+};
+
+__device__ __forceinline__ void oz_tma_load(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar) : "memory");
+}
+
+// The eight group sums (integers held exactly in fp32, or rounded to even integers for
+// the two lowest groups) of output column j, combined exactly:
+//   V = hi 2^28 + lo,  hi = sum_{G<4} v_G 2^(7 (3 - G)),  lo = sum_{G>=4} v_G 2^(7 (7 - G)),
+// |hi|, |lo| < 2^47, |V| < 2^76.
+__device__ __forceinline__ __int128 oz_combine(const uint32_t (&u)[OZ_G][4], int j) {
+    long long hi = 0, lo = 0;
+#pragma unroll
+    for (int G = 0; G < 4; G++) hi = hi * 128 + (long long)__float2int_rn(__uint_as_float(u[G][j]));
+#pragma unroll
+    for (int G = 4; G < 8; G++) lo = lo * 128 + (long long)__float2int_rn(__uint_as_float(u[G][j]));
+    return (__int128)hi * 268435456 + (__int128)lo;
+}
+
+// (-1)^neg V 2^e as a double, V rounded once to 53 bits (to nearest, ties to even), in
+// integer arithmetic; results outside the normal range take scalbn
+__device__ __forceinline__ double oz_to_double(__int128 V, int e, bool neg) {
+    if (V == 0) return 0.0;
+    bool sgn = V < 0;
+    if (neg) sgn = !sgn;
+    const unsigned __int128 A = V < 0 ? (unsigned __int128)(-V) : (unsigned __int128)V;
+    const unsigned long long ah = (unsigned long long)(A >> 64), al = (unsigned long long)A;
+    int p = ah ? 127 - __clzll((long long)ah) : 63 - __clzll((long long)al);     // leading bit
+    unsigned long long q;
+    if (p <= 52) {
+        q = al << (52 - p);
+    } else {
+        const int sh = p - 52;                                                    // 1 .. 75
+        const unsigned __int128 Q = A >> sh;
+        const unsigned __int128 R = A - (Q << sh);
+        const unsigned __int128 H = (unsigned __int128)1 << (sh - 1);
+        q = (unsigned long long)Q;
+        if (R > H || (R == H && (q & 1ull))) {
+            q++;
+            if (q == (1ull << 53)) { q >>= 1; p++; }
+        }
+    }
+    const int be = p + e + 1023;
+    if (be < 1 || be > 2046) return scalbn(sgn ? -(double)q : (double)q, p - 52 + e);
+    return __longlong_as_double((long long)(((unsigned long long)sgn << 63) | ((unsigned long long)be << 52) |
+                                            (q & 0xFFFFFFFFFFFFFull)));
+}
+
+// order in which the A slices of a slab are taken: 0 first (it opens every accumulator),
+// then long and short rows of the product triangle alternately (8 - i products each), so
+// the slice ring's loads always have work in flight to hide behind
+__device__ __forceinline__ int oz_order(int ii) {
+    return (ii & 1) ? (OZ_S - 1 - (ii >> 1)) : (ii >> 1);     // 0 7 1 6 2 5 3 4
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzGemm p) {
+    extern __shared__ uint8_t oz_smem_raw[];
+    __shared__ uint64_t bfull[2], bempty[2], afull[OZ_RING], aempty[OZ_RING], tfull, done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int skip, abort_flag, s_ok;
+    __shared__ int col_e[OZ_BN];
+
+    const GemmBatch& g = p.g;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) skip = (*(volatile int*)p.err & SGS_DEV_TC_TIMEOUT) != 0;
+    __syncthreads();
+    if (skip) return;
+    const int bl = blockIdx.y, b = p.b0 + bl;
+    const int tnn = (g.n + OZ_BN - 1) / OZ_BN;
+    int tm, tn;
+    if (g.mode == GEMM_SKEW) {      // tiles holding an element on or below the diagonal
+        int t = blockIdx.x;
+        tm = 0;
+        while (true) {
+            const int cnt = min(2 * tm + 2, tnn);
+            if (t < cnt) break;
+            t -= cnt;
+            tm++;
+        }
+        tn = t;
+    } else {
+        tm = blockIdx.x / tnn;
+        tn = blockIdx.x % tnn;
+    }
+    const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
+    const bool active = oz_active(g.active_flag, g.active_cmp, b);
+    const int nslab = active ? (g.k + OZ_KS - 1) / OZ_KS : 0;      // k <= OZ_KC (the host splits K)
+
+    const uint32_t raw = smem_u32(oz_smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    auto sB = [&](int bb, int j) { return sbase + (uint32_t)(bb * OZ_S + j) * OZ_SLAB_B; };
+    auto sA = [&](int slot) { return sbase + 2u * OZ_S * OZ_SLAB_B + (uint32_t)slot * OZ_SLAB_A; };
+
+    if (warp == OZ_EPI_WARPS + 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_base)), "r"(512u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bfull[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bempty[s])));
+        }
+        for (int s = 0; s < OZ_RING; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&afull[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&aempty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&tfull)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&done)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        abort_flag = 0;
+    }
+    if (tid < OZ_BN) col_e[tid] = (active && n0 + tid < g.n) ? p.eb[(size_t)bl * p.n_pad + n0 + tid] : 0;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+
+    if (warp == OZ_EPI_WARPS) {
+        if (lane == 0) {            // producer
+            // order: B(0); then per slab s: A(s, 0..3), B(s + 1) (once slab s - 1 has released its
+            // buffer), A(s, 4..7), so the next slab's B slices load during all of slab s's MMAs
+            int nb = 0, q = 0;      // B slabs and A slices issued
+            bool ok = true;
+            auto issue_b = [&](int sb) {
+                const int bb = sb & 1;
+                mbar_expect_tx(smem_u32(&bfull[bb]), (uint32_t)(OZ_S * OZ_SLAB_B));
+                for (int j = 0; j < OZ_S; j++)
+                    oz_tma_load(sB(bb, j), &p.tb, sb * OZ_KS, n0, bl * OZ_S + j, smem_u32(&bfull[bb]));
+                nb = sb + 1;
+            };
+            if (nslab > 0) issue_b(0);
+            for (int s = 0; s < nslab && ok; s++) {
+                for (int ii = 0; ii < OZ_S; ii++) {
+                    if (ii == OZ_S / 2 && s + 1 < nslab) {
+                        if (s >= 1 && !mbar_wait_or_abort(smem_u32(&bempty[(s + 1) & 1]),
+                                                          (uint32_t)(((s - 1) >> 1) & 1), p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        issue_b(s + 1);
+                    }
+                    const int slot = q % OZ_RING;
+                    if (q >= OZ_RING &&
+                        !mbar_wait_or_abort(smem_u32(&aempty[slot]), (uint32_t)(((q / OZ_RING) - 1) & 1), p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(smem_u32(&afull[slot]), (uint32_t)OZ_SLAB_A);
+                    oz_tma_load(sA(slot), &p.ta, s * OZ_KS, m0, bl * OZ_S + oz_order(ii), smem_u32(&afull[slot]));
+                    q++;
+                }
+                if (*(volatile int*)&abort_flag) ok = false;
+            }
+            if (!ok) abort_flag = 1;
+            // every load issued has landed before the CTA can leave
+            for (int x = (nb > 2 ? nb - 2 : 0); x < nb; x++)
+                mbar_wait(smem_u32(&bfull[x & 1]), (uint32_t)((x >> 1) & 1), p.err);
+            for (int x = (q > OZ_RING ? q - OZ_RING : 0); x < q; x++)
+                mbar_wait(smem_u32(&afull[x % OZ_RING]), (uint32_t)((x / OZ_RING) & 1), p.err);
+        }
+    } else if (warp == OZ_EPI_WARPS + 1) {
+        if (lane == 0) {            // MMA issuer
+            constexpr uint32_t IDESC1 = tc_idesc(TC_BF16, OZ_BN), IDESC2 = tc_idesc(TC_BF16, 2 * OZ_BN),
+                               IDESC3 = tc_idesc(TC_BF16, 3 * OZ_BN), IDESC4 = tc_idesc(TC_BF16, 4 * OZ_BN);
+            // descriptors of slot 0 / buffer 0 slice 0; other slabs offset the 16-byte address field
+            const uint64_t dA0 = tma_smem_desc(sA(0)), dB0 = tma_smem_desc(sB(0, 0));
+            int q = 0;
+            bool ok = true;
+            for (int s = 0; s < nslab && ok; s++) {
+                const int bb = s & 1;
+                if (!mbar_wait_or_abort(smem_u32(&bfull[bb]), (uint32_t)((s >> 1) & 1), p.err)) {
+                    ok = false;
+                    break;
+                }
+                const int kv = min(OZ_KS, g.k - s * OZ_KS);
+                const int nk16 = (kv + 15) / 16;
+                const uint64_t dB = dB0 + (uint64_t)((bb * OZ_S * OZ_SLAB_B) >> 4);
+                for (int ii = 0; ii < OZ_S; ii++, q++) {
+                    const int i = oz_order(ii);
+                    const int slot = q % OZ_RING;
+                    if (!mbar_wait_or_abort(smem_u32(&afull[slot]), (uint32_t)((q / OZ_RING) & 1), p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint64_t da = dA0 + (uint64_t)((slot * OZ_SLAB_A) >> 4);
+                    // the first slice (i = 0, taken first) opens every group's accumulator
+                    const uint32_t first = (s == 0 && ii == 0) ? 1u : 0u;
+                    // products (i, j), j = 0 .. 7 - i, land in groups i .. 7: adjacent 64-column
+                    // accumulators, and the B slices j are adjacent 64-row blocks in shared memory,
+                    // so one MMA of N = 64 (8 - i) (at most 256 per instruction) covers them
+#pragma unroll
+                    for (int kk = 0; kk < OZ_KS / 16; kk++) {
+                        if (kk < nk16) {
+#pragma unroll
+                            for (int c = 0; c < OZ_S; c += 4) {
+                                const int nb = min(4, OZ_S - i - c);
+                                if (nb > 0) {
+                                    const uint32_t acc = tmem + (uint32_t)((i + c) * OZ_BN);
+                                    const uint64_t db = dB + (uint64_t)((c * OZ_SLAB_B) >> 4) + 2 * kk;
+                                    const uint32_t idesc = nb == 4 ? IDESC4 : nb == 3 ? IDESC3 : nb == 2 ? IDESC2 : IDESC1;
+                                    tc_mma(acc, da + 2 * kk, db, idesc, (first && kk == 0) ? 0u : 1u, TC_BF16);
+                                }
+                            }
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(smem_u32(&aempty[slot])) : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_u32(&bempty[bb])) : "memory");
+                if (s == nslab - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(smem_u32(&tfull)) : "memory");
+                if (*(volatile int*)&abort_flag) ok = false;
+            }
+            if (!ok) abort_flag = 1;
+            // every MMA issued has completed before TMEM is freed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&done)) : "memory");
+            mbar_wait(smem_u32(&done), 0u, p.err);
+        }
+    } else {
+        // epilogue: warps 0-7.  Warp w drains TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 (output rows)
+        // for the columns of half w / 4; the store pass gives thread tid the elements tid + 256 q.
+        constexpr int NE = 32 * OZ_EPI_WARPS, PER = OZ_BM * OZ_BN / NE;
+        const double* Cinb = g.Cin ? g.Cin[b] + g.offCin : nullptr;
+        const double* Cin2b = g.Cin2 ? g.Cin2[b] + g.offCin : nullptr;
+        double* Cb = g.C[b] + g.offC;
+        const bool skew = g.mode == GEMM_SKEW, gj = g.mode == GEMM_GJ;
+        // the additive terms of the thread's elements (beta Cin + beta2 Cin2, or Cin itself when
+        // the batch entry passes through), loaded while the MMAs run; Cin may be C itself, and
+        // every element is read before this CTA stores any
+        double extra[PER];
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            const int e = tid + NE * q, rr = e / OZ_BN, cc = e % OZ_BN;
+            const int r = m0 + rr, c = n0 + cc;
+            double x = 0.0;
+            if (r < g.m && c < g.n && !(skew && r < c)) {
+                const long long off = (long long)r * g.ldcin + c;
+                if (!active) {
+                    if (Cinb) x = Cinb[off];
+                } else {
+                    if (Cinb && g.beta != 0.0 && !(gj && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b)) x = g.beta * Cinb[off];
+                    if (Cin2b) x = fma(g.beta2, Cin2b[off], x);
+                }
+            }
+            extra[q] = x;
+        }
+        bool ok = true;
+        if (nslab > 0) {
+            if (tid == 0) s_ok = mbar_wait_or_abort(smem_u32(&tfull), 0u, p.err) ? 1 : 0;
+            asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
+            ok = s_ok != 0;
+        }
+        if (ok) {
+            // every MMA has completed, so every load has been consumed: the stage buffers
+            // become the (padded) FP64 output tile
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            double* tile = reinterpret_cast<double*>(oz_smem_raw + (sbase - raw));
+            const double alpha = g.alpha * (g.alpha_b ? g.alpha_b[b] : 1.0);
+            const int lq = warp & 3, half = warp >> 2;
+            const int rr0 = lq * 32 + lane, row = m0 + rr0;
+            const int er = (active && row < g.m) ? p.ea[(size_t)bl * p.m_pad + row] : 0;
+            const int ae = p.alpha_pow2 ? p.alpha_e : 0;
+            const bool an = p.alpha_pow2 && p.alpha_neg;
+            if (nslab > 0) {
+#pragma unroll 1
+                for (int cb = half * (OZ_BN / 8); cb < (half + 1) * (OZ_BN / 8); cb++) {
+                    uint32_t u[OZ_G][4];
+#pragma unroll
+                    for (int G = 0; G < OZ_G; G++) {
+                        const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(G * OZ_BN + cb * 4);
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                     : "=r"(u[G][0]), "=r"(u[G][1]), "=r"(u[G][2]), "=r"(u[G][3])
+                                     : "r"(ta));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const int c = cb * 4 + j, fc = col_e[c];
+                        double v = 0.0;
+                        if (er > 0 && fc > 0) {
+                            v = oz_to_double(oz_combine(u, j), er + fc - 2107 + ae, an);
+                            if (!p.alpha_pow2) v *= alpha;
+                        }
+                        tile[rr0 * OZ_TS + c] = v;
+                    }
+                }
+            }
+            asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
+#pragma unroll
+            for (int q = 0; q < PER; q++) {
+                const int e = tid + NE * q, rr = e / OZ_BN, cc = e % OZ_BN;
+                const int r = m0 + rr, c = n0 + cc;
+                if (r >= g.m || c >= g.n || (skew && r < c)) continue;
+                double v = extra[q];
+                if (active) {
+                    v += tile[rr * OZ_TS + cc];
+                    if (r == c) v += g.diag;
+                }
+                if (skew && r == c) v = 0.0;
+                tile[rr * OZ_TS + cc] = v;            // kept for the mirrored block
+                if (!gj || c < g.gj_k0 || c >= g.gj_k0 + g.gj_b) Cb[(long long)r * g.ldc + c] = v;
+            }
+            if (skew) {
+                // mirrored block: C[c][r] = -C[r][c] below the diagonal, rows of the mirror coalesced
+                asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
+                for (int e = tid; e < OZ_BM * OZ_BN; e += NE) {
+                    const int cc = e / OZ_BM, rr = e % OZ_BM;
+                    const int r = m0 + rr, c = n0 + cc;
+                    if (r >= g.m || c >= g.n || r <= c) continue;
+                    Cb[(long long)c * g.ldc + r] = -tile[rr * OZ_TS + cc];
+                }
+            }
+        } else if (tid == 0) {
+            abort_flag = 1;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == OZ_EPI_WARPS + 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512u));
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+inline size_t oz_round(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// scratch bytes of one batch entry of an m x n x k product (slices and exponent fields)
+inline size_t oz_entry_bytes(int m, int n, int k) {
+    const size_t kp = oz_round((size_t)k, 8), mp = oz_round((size_t)m, OZ_BM), np = oz_round((size_t)n, OZ_BN);
+    return (size_t)OZ_S * 2 * (mp + np) * kp + 4 * (mp + np);
+}
+
+// Tensor map of a slice batch [nmat][rows_pad][kp] bf16 with x extent k (zero fill beyond),
+// box 64 x box_rows x 1 (128-byte rows, 128-byte swizzle)
+inline bool make_slice_map(CUtensorMap* map, const void* base, int k, int kp, int rows_pad, int nmat, int box_rows) {
+    TmaEncodeFn fn = tma_encode_fn();
+    if (!fn || !base || ((uintptr_t)base & 15) || (kp & 7)) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows_pad, (cuuint64_t)nmat};
+    const cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)kp * rows_pad * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)OZ_KS, (cuuint32_t)box_rows, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline void oz_prepare(const OzOperand& o, int bc, cudaStream_t st) {
+    if (o.strided) oz_expo_kernel<<<dim3((o.rows + 31) / 32, bc), 256, 0, st>>>(o);
+    else oz_expo_kernel<<<dim3((o.rows + 7) / 8, bc), 256, 0, st>>>(o);
+    oz_slice_kernel<<<dim3((o.k + 31) / 32, o.rows_pad / 32, bc), 256, 0, st>>>(o);
+}
+
+// number of output tiles of one batch entry
+inline int oz_tiles(const GemmBatch& g) {
+    const int tmn = (g.m + OZ_BM - 1) / OZ_BM, tnn = (g.n + OZ_BN - 1) / OZ_BN;
+    if (g.mode != GEMM_SKEW) return tmn * tnn;
+    int t = 0;
+    for (int tm = 0; tm < tmn; tm++) t += std::min(2 * tm + 2, tnn);
+    return t;
+}
+
+// launches of one product (5 per batch chunk and K chunk), for launch accounting
+inline int oz_launches(const GemmBatch& g, const OzBuf& buf) {
+    if (g.batch <= 0 || g.m <= 0 || g.n <= 0 || g.k <= 0 || !buf.base) return 1;
+    if (g.mode == GEMM_GJ && g.k > OZ_KC) return 1;
+    int total = 0;
+    for (int k0 = 0; k0 < g.k; k0 += OZ_KC) {
+        const size_t per = oz_entry_bytes(g.m, g.n, std::min(OZ_KC, g.k - k0));
+        const size_t chunk = std::min<size_t>(g.batch, buf.bytes > 8192 ? (buf.bytes - 8192) / per : 0);
+        if (chunk == 0) return 1;
+        total += 5 * (int)((g.batch + chunk - 1) / chunk);
+    }
+    return total;
+}
+
+// one K chunk (k <= OZ_KC) of the emulated product, in batch chunks that fit the scratch
+inline cudaError_t gemm_oz_chunk(const GemmBatch& g, const OzBuf& buf, int* err, cudaStream_t st) {
+    const int kp = (int)oz_round(g.k, 8), mp = (int)oz_round(g.m, OZ_BM), np = (int)oz_round(g.n, OZ_BN);
+    const size_t sa = (size_t)OZ_S * mp * kp * 2, sb = (size_t)OZ_S * np * kp * 2;
+    const size_t per = oz_entry_bytes(g.m, g.n, g.k);
+    const int chunk = (int)std::min<size_t>(g.batch, buf.bytes > 8192 ? (buf.bytes - 8192) / per : 0);
+    if (chunk <= 0) return gemm_f64(g, st);
+    const int tiles = oz_tiles(g);
+    for (int b0 = 0; b0 < g.batch; b0 += chunk) {
+        const int bc = std::min(chunk, g.batch - b0);
+        uint16_t* as = reinterpret_cast<uint16_t*>(buf.base);
+        uint16_t* bs = reinterpret_cast<uint16_t*>(buf.base + oz_round((size_t)bc * sa, 1024));
+        int* ea = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(bs) + oz_round((size_t)bc * sb, 1024));
+        int* eb = ea + oz_round((size_t)bc * mp, 64);
+        OzOperand oa{g.A, g.A2, g.sA2, g.offA, g.lda, g.transA ? 1 : 0, g.m, g.k, mp, kp, b0,
+                     g.active_flag, g.active_cmp, ea, as};
+        OzOperand ob{g.B, g.B2, g.sB2, g.offB, g.ldb, g.transB ? 0 : 1, g.n, g.k, np, kp, b0,
+                     g.active_flag, g.active_cmp, eb, bs};
+        oz_prepare(oa, bc, st);
+        oz_prepare(ob, bc, st);
+        OzGemm p;
+        std::memset(&p, 0, sizeof(p));
+        if (!make_slice_map(&p.ta, as, g.k, kp, mp, bc * OZ_S, OZ_BM) ||
+            !make_slice_map(&p.tb, bs, g.k, kp, np, bc * OZ_S, OZ_BN))
+            return cudaErrorInvalidValue;
+        p.g = g; p.b0 = b0; p.m_pad = mp; p.n_pad = np; p.ea = ea; p.eb = eb; p.err = err;
+        int ex = 0;
+        const double fr = std::frexp(g.alpha, &ex);
+        if (!g.alpha_b && (fr == 0.5 || fr == -0.5)) {
+            p.alpha_pow2 = 1; p.alpha_e = ex - 1; p.alpha_neg = g.alpha < 0.0;
+        }
+        oz_gemm_kernel<<<dim3(tiles, bc), OZ_THREADS, OZ_SMEM, st>>>(p);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// the emulated product; K beyond OZ_KC runs as further launches that add onto C (the
+// chunks' sums are FP64 roundings).  Falls back to gemm_f64 where there is nothing to
+// slice or no scratch for one batch entry.  err: the owner's device error word.
+inline cudaError_t gemm_oz(const GemmBatch& g, const OzBuf& buf, int* err, cudaStream_t st) {
+    if (g.batch <= 0 || g.m <= 0 || g.n <= 0) return cudaSuccess;
+    if (g.k <= 0 || !buf.base || !err) return gemm_f64(g, st);
+    if (g.mode == GEMM_SKEW && g.m != g.n) return cudaErrorInvalidValue;
+    if (g.mode == GEMM_GJ && g.k > OZ_KC) return gemm_f64(g, st);
+    if (oz_entry_bytes(g.m, g.n, std::min(g.k, OZ_KC)) + 8192 > buf.bytes) return gemm_f64(g, st);
+    for (int k0 = 0; k0 < g.k; k0 += OZ_KC) {
+        GemmBatch h = g;
+        h.k = std::min(OZ_KC, g.k - k0);
+        h.offA += g.transA ? (long long)k0 * g.lda : k0;
+        h.offB += g.transB ? k0 : (long long)k0 * g.ldb;
+        if (k0 > 0) {
+            h.Cin = (const double* const*)g.C; h.offCin = g.offC; h.ldcin = g.ldc; h.beta = 1.0;
+            h.Cin2 = nullptr; h.beta2 = 0.0; h.diag = 0.0;
+        }
+        const cudaError_t e = gemm_oz_chunk(h, buf, err, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace sgs

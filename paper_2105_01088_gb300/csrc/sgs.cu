@@ -33,6 +33,7 @@
 #include "update.cuh"
 #include "update_lp.cuh"
 #include "probe.cuh"
+#include "gemm_oz.cuh"
 #include "gemm_tc.cuh"
 #include "gemm_tma.cuh"
 #include "corr.cuh"
@@ -108,6 +109,7 @@ struct Instance {
     double **r_Y = nullptr, **r_TU = nullptr, **r_PK = nullptr, **r_upA = nullptr, **r_upB = nullptr, **r_upC = nullptr;
     double* eigscratch = nullptr;
     int* err = nullptr;
+    OzBuf oz;                           // emulated FP64 products: slice scratch (path 2 only)
 
     // tensor-core (mixed precision) operands of the equation of motion, per pair:
     // low-precision hi (fp32 or bf16) and lo (3xTF32) parts of S^{-1}, T1 = S^{-1} F,
@@ -306,6 +308,16 @@ unsigned grid_chunks(size_t work, int threads, unsigned cap) {
 }
 
 // device bytes one instance holds (the allocations of setup_instance, up to small terms)
+// emulated FP64 products (path 2): slice scratch of one instance, enough for its widest
+// batch (pairs, Pfaffian halves or states) of n x n x n products, capped per instance (the
+// products then run in batch chunks)
+size_t g_oz_cap = (size_t)2 << 30;
+size_t oz_scratch_bytes(int n, int M) {
+    const size_t P = (size_t)M * (M - 1) / 2, Ppf = P > 0 ? P - (M - 1) : 0;
+    const size_t batch = std::max<size_t>(std::max<size_t>(P, 2 * Ppf), std::max<size_t>((size_t)M, 1));
+    return std::min(batch * oz_entry_bytes(n, n, std::min(n, OZ_KC)) + 16384, g_oz_cap);
+}
+
 size_t instance_bytes(int n, int M, int prec, int nimp, bool tune) {
     const size_t nn = (size_t)n * n, P = (size_t)M * (M - 1) / 2, Ppf = P > 0 ? P - (M - 1) : 0;
     const size_t gj_b = tune ? 64 : 32, bs = tune ? 32 : 16;
@@ -320,6 +332,7 @@ size_t instance_bytes(int n, int M, int prec, int nimp, bool tune) {
         if (prec != SGS_FP32_3XTF32)
             bytes += (size_t)M * nn * 4 + (size_t)M * n * ldp * (9 * 4 + 10 * esz);   // mixed update
     }
+    if (g_gemm_fma == 2) bytes += oz_scratch_bytes(n, M);
     return bytes + (1 << 20);
 }
 
@@ -645,6 +658,13 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
             I.u_ok = true;
         }
     }
+    if (g_gemm_fma == 2) {
+        // emulated FP64 products: slice scratch for one batch chunk
+        const size_t b = oz_scratch_bytes(n, M);
+        I.oz.base = static_cast<uint8_t*>(c->dalloc(b));
+        if (!I.oz.base) { c->err = "device allocation failed (emulated-product scratch)"; return SGS_ENOMEM; }
+        I.oz.bytes = b;
+    }
     return SGS_OK;
 }
 
@@ -674,25 +694,43 @@ void set_kernel_attributes() {
         raise_smem_limit(gemm_tma_kernel<TC_TF32>, optin);
         raise_smem_limit(gemm_tma_kernel<TC_BF16>, optin);
         raise_smem_limit(gemm_tma_kernel<TC_3XTF32>, optin);
+        raise_smem_limit(gemm_tmap_kernel<TC_TF32>, optin);
+        raise_smem_limit(gemm_tmap_kernel<TC_BF16>, optin);
+        raise_smem_limit(gemm_tmap_kernel<TC_3XTF32>, optin);
+        raise_smem_limit(oz_gemm_kernel, optin);
         cudaGetLastError();
     });
 }
 
+// a TMA-fed tensor-core product: one CTA per output tile, or (loader 2) the persistent
+// form with one CTA per SM
+inline cudaError_t tma_product(const TmaBatch& t, int kind, cudaStream_t st) {
+    return g_tc_tma == 2 ? gemm_tma_persistent(t, kind, st) : gemm_tma(t, kind, st);
+}
+
 // every FP64 product of the library goes through here; flops = algorithmic work of
 // the launch (antisymmetric outputs count half), < 0 = not profiled
-inline cudaError_t gemm(sgs_ctx* c, const GemmBatch& g, cudaStream_t st, double flops) {
-    counted();
+// (path 2 with the owner's slice scratch: the emulated product on the bf16 tensor cores)
+inline cudaError_t gemm(sgs_ctx* c, const GemmBatch& g, cudaStream_t st, double flops, const OzBuf* oz = nullptr,
+                        int* oz_err = nullptr) {
+    const bool emulate = g_gemm_fma == 2 && oz && oz->base && oz_err;
+    if (emulate) for (int i = oz_launches(g, *oz); i > 0; i--) counted();
+    else counted();
+    auto run = [&]() { return emulate ? gemm_oz(g, *oz, oz_err, st) : gemm_f64(g, st); };
     if (c && c->prof && flops >= 0.0) {
         cudaEvent_t a = c->next_event(), b = c->next_event();
         cudaEventRecord(a, st);
-        cudaError_t e = gemm_f64(g, st);
+        cudaError_t e = run();
         cudaEventRecord(b, st);
         c->gmarks.push_back({a, b});
         c->gemm_flops += flops;
         c->gemm_count++;
         return e;
     }
-    return gemm_f64(g, st);
+    return run();
+}
+inline cudaError_t gemm(sgs_ctx* c, Instance& I, const GemmBatch& g, cudaStream_t st, double flops) {
+    return gemm(c, g, st, flops, &I.oz, I.err);
 }
 
 GemmBatch gb_basic(int m, int n, int k, double** A, int lda, double** B, int ldb, double** C, int ldc, int batch) {
@@ -704,7 +742,7 @@ GemmBatch gb_basic(int m, int n, int k, double** A, int lda, double** B, int ldb
 }
 
 cudaError_t launch_gj(sgs_ctx* c, int n, int batch, int bsz, double** W, double** T, int* piv, double* logdet,
-                      double* dsign, int* err, double tiny, cudaStream_t st) {
+                      double* dsign, int* err, double tiny, cudaStream_t st, const OzBuf* oz = nullptr) {
     set_kernel_attributes();
     for (int k0 = 0; k0 < n; k0 += bsz) {
         const int bb = std::min(bsz, n - k0);
@@ -715,14 +753,15 @@ cudaError_t launch_gj(sgs_ctx* c, int n, int batch, int bsz, double** W, double*
         g.offA = k0;
         g.Cin = (const double* const*)W; g.ldcin = n; g.beta = 1.0;
         g.mode = GEMM_GJ; g.gj_k0 = k0; g.gj_b = bb;
-        cudaError_t e = gemm(c, g, st, 2.0 * n * (double)(n - bb) * bb * batch);
+        cudaError_t e = gemm(c, g, st, 2.0 * n * (double)(n - bb) * bb * batch, oz, err);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, double** TU, double** PK, double** upA,
-                      double** upB, double** upC, double* logabs, double* phase, int* err, cudaStream_t st) {
+                      double** upB, double** upC, double* logabs, double* phase, int* err, cudaStream_t st,
+                      const OzBuf* oz = nullptr) {
     const size_t smem = (4 * (size_t)n + 4 * bsmax) * sizeof(double);
     set_kernel_attributes();
     for (int k0 = 0; k0 < n; k0 += 2 * bsmax) {
@@ -742,7 +781,7 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
         // block it updates: compute the lower tiles and mirror them
         g.mode = GEMM_SKEW;
         const double m2 = (double)(n - e0) * (n - e0);
-        cudaError_t e = gemm(c, g, st, m2 * 4.0 * bs * 2 * batch);
+        cudaError_t e = gemm(c, g, st, m2 * 4.0 * bs * 2 * batch, oz, err);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -756,7 +795,7 @@ cudaError_t pair_inverse(sgs_ctx* c, Instance& I, cudaStream_t st) {
     const size_t nn = (size_t)n * n;
     pair_sum_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.dev(), I.work);
     counted();
-    cudaError_t e = launch_gj(c, n, P, I.gj_b, I.p_work, I.p_tbuf, I.piv, I.logdet, I.dsign, I.err, 1e-12, st);
+    cudaError_t e = launch_gj(c, n, P, I.gj_b, I.p_work, I.p_tbuf, I.piv, I.logdet, I.dsign, I.err, 1e-12, st, &I.oz);
     if (e != cudaSuccess) return e;
     gj_perm_kernel<<<(P + 127) / 128, 128, 0, st>>>(I.piv, I.perm, n, P);
     gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.p_work, I.p_si, I.perm, n);
@@ -770,7 +809,7 @@ cudaError_t pair_delta(sgs_ctx* c, Instance& I, cudaStream_t st) {
     GemmBatch g = gb_basic(n, n, n, I.p_ga, n, I.p_si, n, I.p_imd, n, I.P);
     g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
     g.mode = GEMM_SKEW;
-    return gemm(c, g, st, (double)n * n * n * I.P);   // antisymmetric product: half of 2 n^3
+    return gemm(c, I, g, st, (double)n * n * n * I.P);   // antisymmetric product: half of 2 n^3
 }
 
 // phase Pfaffians Pf(Gamma_0 + Delta^{a,b}) of the pairs without the reference state
@@ -780,7 +819,7 @@ cudaError_t pair_phase(sgs_ctx* c, Instance& I, cudaStream_t st) {
     pf_build_kernel<<<dim3(grid_chunks(nn, 256, 64), I.Ppf), 256, 0, st>>>(I.dev(), I.si, I.imd, I.work);
     counted();
     return launch_pf(c, n, I.Ppf, I.pf_bs, I.p_Y, I.p_TU, I.p_pack, I.p_upA, I.p_upB, I.p_upC, I.pflog, I.pfphase,
-                     I.err, st);
+                     I.err, st, &I.oz);
 }
 
 // pair pass + amplitude solve for one instance; E -> Ehist[slot]
@@ -904,7 +943,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     {
         GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_s[0], n, I.p_s[4], n, M);
         g.mode = GEMM_SKEW;
-        if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
+        if ((e = gemm(c, I, g, st, n3 * M)) != cudaSuccess) return e;
     }
     if (P > 0 && I.tc_kind >= 0) {
         // tensor-core path: W = T1 S^{-1}, V = D W, X = V D, every B antisymmetric, so its
@@ -928,7 +967,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         t.B = (const void* const*)I.q_si_hi; t.B2 = (const void* const*)I.q_si_lo;
         t.C = I.q_wr32; t.skew = 1;
         const bool tma = g_tc_tma && I.tma_ok;
-        if ((e = tma ? gemm_tma(I.tma_w, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        if ((e = tma ? tma_product(I.tma_w, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
         counted();
         lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_wr32, nullptr, I.q_wr_hi,
                                                                  I.q_wr_lo, n, ldp, kind);
@@ -938,7 +977,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         t.A = (const void* const*)I.q_d_hi; t.A2 = (const void* const*)I.q_d_lo;
         t.B = (const void* const*)I.q_wr_hi; t.B2 = (const void* const*)I.q_wr_lo;
         t.C = I.q_va32; t.skew = 0;
-        if ((e = tma ? gemm_tma(I.tma_v, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        if ((e = tma ? tma_product(I.tma_v, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
         counted();
         c->stage(SGS_STAGE_EOM_X);
         c->stage_flops[SGS_STAGE_EOM_X] += n3 * P;
@@ -948,7 +987,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         t.A = (const void* const*)I.q_va_hi; t.A2 = (const void* const*)I.q_va_lo;
         t.B = (const void* const*)I.q_d_hi; t.B2 = (const void* const*)I.q_d_lo;
         t.C = I.q_xa32; t.skew = 1;
-        if ((e = tma ? gemm_tma(I.tma_x, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        if ((e = tma ? tma_product(I.tma_x, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
         counted();
         c->stage(SGS_STAGE_EOM_ASSEMBLY);
         if (I.nimp > 0) {
@@ -964,21 +1003,21 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         counted();
         GemmBatch g = gb_basic(n, n, n, I.p_work, n, I.p_si, n, I.p_wr, n, P);
         g.mode = GEMM_SKEW;
-        if ((e = gemm(c, g, st, n3 * P)) != cudaSuccess) return e;
+        if ((e = gemm(c, I, g, st, n3 * P)) != cudaSuccess) return e;
         // V = D Wr
         c->stage(SGS_STAGE_EOM_V);
         c->stage_flops[SGS_STAGE_EOM_V] += 2.0 * n3 * P;
         c->stage_bytes[SGS_STAGE_EOM_V] += 8.0 * nn * (2.0 * P + M);   // read Wr, write V; Gamma once
         g = gb_basic(n, n, n, I.p_ga, n, I.p_wr, n, I.p_va, n, P);
         g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
-        if ((e = gemm(c, g, st, 2.0 * n3 * P)) != cudaSuccess) return e;
+        if ((e = gemm(c, I, g, st, 2.0 * n3 * P)) != cudaSuccess) return e;
         // X = V D
         c->stage(SGS_STAGE_EOM_X);
         c->stage_flops[SGS_STAGE_EOM_X] += n3 * P;
         g = gb_basic(n, n, n, I.p_va, n, I.p_ga, n, I.p_xa, n, P);
         g.B2 = (const double* const*)I.p_gb; g.sB2 = -1.0;
         g.mode = GEMM_SKEW;
-        if ((e = gemm(c, g, st, n3 * P)) != cudaSuccess) return e;
+        if ((e = gemm(c, I, g, st, n3 * P)) != cudaSuccess) return e;
         c->stage(SGS_STAGE_EOM_ASSEMBLY);
         if (I.nimp > 0) {
             pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.fimp, I.lr);
@@ -1024,10 +1063,10 @@ cudaError_t exp_products(sgs_ctx* c, Instance& I, int batch, cudaStream_t st, in
     cf[11] = 0.0;                                         // degree 10
     cudaError_t e;
     GemmBatch g = gb_basic(n, n, n, I.p_s[1], n, I.p_s[1], n, I.p_s[0], n, batch);
-    if ((e = gemm(c, g, st, 2.0 * n3 * batch)) != cudaSuccess) return e;         // X2
+    if ((e = gemm(c, I, g, st, 2.0 * n3 * batch)) != cudaSuccess) return e;         // X2
     g = gb_basic(n, n, n, I.p_s[0], n, I.p_s[1], n, I.p_s[2], n, batch);
     g.mode = GEMM_SKEW;                                                            // Y = X2 X_s
-    if ((e = gemm(c, g, st, n3 * batch)) != cudaSuccess) return e;
+    if ((e = gemm(c, I, g, st, n3 * batch)) != cudaSuccess) return e;
     scaled_plus_identity_kernel<<<grid_chunks(batch * nn, 256, 4096), 256, 0, st>>>(I.s[1], cf[10], cf[9], n, I.s[3],
                                                                                    batch * nn);
     counted();
@@ -1038,7 +1077,7 @@ cudaError_t exp_products(sgs_ctx* c, Instance& I, int batch, cudaStream_t st, in
         g.Cin = (const double* const*)I.p_s[0]; g.ldcin = n; g.beta = cf[3 * j + 2];
         g.Cin2 = (const double* const*)I.p_s[1]; g.beta2 = cf[3 * j + 1];
         g.diag = cf[3 * j];
-        if ((e = gemm(c, g, st, 2.0 * n3 * batch)) != cudaSuccess) return e;
+        if ((e = gemm(c, I, g, st, 2.0 * n3 * batch)) != cudaSuccess) return e;
         cur = nxt;
     }
     for (int j = 0; j < EXP_MAX_SQUARINGS; j++) {
@@ -1046,7 +1085,7 @@ cudaError_t exp_products(sgs_ctx* c, Instance& I, int batch, cudaStream_t st, in
         g = gb_basic(n, n, n, I.p_s[cur], n, I.p_s[cur], n, I.p_s[nxt], n, batch);
         g.active_flag = I.sq; g.active_cmp = j;
         g.Cin = (const double* const*)I.p_s[cur]; g.ldcin = n; g.beta = 0.0;
-        if ((e = gemm(c, g, st, -1.0)) != cudaSuccess) return e;
+        if ((e = gemm(c, I, g, st, -1.0)) != cudaSuccess) return e;
         cur = nxt;
     }
     *cur_out = cur;
@@ -1065,10 +1104,10 @@ cudaError_t polar_pass(sgs_ctx* c, Instance& I, int iters, cudaStream_t st, int 
     double** dst = I.p_gamma;
     for (int it = 0; it < iters; it++) {
         GemmBatch g = gb_basic(n, n, n, src, n, src, n, I.p_s[0], n, M);
-        if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;     // X X: symmetric, half counted
+        if ((e = gemm(c, I, g, st, n3 * M)) != cudaSuccess) return e;     // X X: symmetric, half counted
         g = gb_basic(n, n, n, src, n, I.p_s[0], n, dst, n, M);
         g.alpha = 0.5; g.Cin = (const double* const*)src; g.ldcin = n; g.beta = 1.5; g.mode = GEMM_SKEW;
-        if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
+        if ((e = gemm(c, I, g, st, n3 * M)) != cudaSuccess) return e;
         std::swap(src, dst);
     }
     if (src == I.p_s[from]) {  // an even number of iterations ends in the source buffer
@@ -1105,7 +1144,7 @@ cudaError_t update_pass_lp(sgs_ctx* c, Instance& I, cudaStream_t st) {
         lp_split_kernel<<<grid_chunks(mp, 256, 4096), 256, 0, st>>>(I.u_f32[f32], I.u_hi[op], I.u_lo[op], mp, kind);
         counted();
     };
-    auto run = [&](const TmaBatch& t) { counted(); return gemm_tma(t, kind, st); };
+    auto run = [&](const TmaBatch& t) { counted(); return tma_product(t, kind, st); };
     lp_from_f64_kernel<<<dim3(gch, M), 256, 0, st>>>(I.gamma, n, ldp, I.u_hi[0], I.u_lo[0], kind);
     lp_from_f64_kernel<<<dim3(gch, M), 256, 0, st>>>(I.dgamma, n, ldp, I.u_hi[1], I.u_lo[1], kind);
     counted(); counted();
@@ -1180,17 +1219,17 @@ cudaError_t update_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     c->stage_flops[SGS_STAGE_UPDATE] += (2.0 + 9.0 + 2.0 + 1.0 + 2.0) * n3 * M;
     // Y = Gamma dGamma -> s0 ; X_s -> s1
     GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_dgamma, n, I.p_s[0], n, M);
-    if ((e = gemm(c, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
+    if ((e = gemm(c, I, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
     exp_prepare_kernel<<<M, 1024, 0, st>>>(I.s[0], I.s[1], n, I.dtau, I.sq, I.scale, I.err);
     counted();
     int cur = 3;
     if ((e = exp_products(c, I, M, st, &cur)) != cudaSuccess) return e;
     // T = R Gamma -> s0 ; Gamma' = T R^T -> s2
     g = gb_basic(n, n, n, I.p_s[cur], n, I.p_gamma, n, I.p_s[0], n, M);
-    if ((e = gemm(c, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
+    if ((e = gemm(c, I, g, st, 2.0 * n3 * M)) != cudaSuccess) return e;
     g = gb_basic(n, n, n, I.p_s[0], n, I.p_s[cur], n, I.p_s[2], n, M);
     g.transB = 1; g.mode = GEMM_SKEW;
-    if ((e = gemm(c, g, st, n3 * M)) != cudaSuccess) return e;
+    if ((e = gemm(c, I, g, st, n3 * M)) != cudaSuccess) return e;
     // R is orthogonal to rounding, so R Gamma R^T leaves purity only at rounding level, which one
     // Newton-Schulz iteration (error -> 1.5 error^2) removes
     if ((e = polar_pass(c, I, 1, st, 2)) != cudaSuccess) return e;
@@ -1417,7 +1456,7 @@ sgs_status sgs_health(sgs_ctx* c, int instance, double* out) {
     GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_gamma, n, I.p_s[0], n, M);
     const bool prof = c->prof;
     c->prof = false;
-    cudaError_t e = gemm(c, g, st, -1.0);
+    cudaError_t e = gemm(c, I, g, st, -1.0);
     c->prof = prof;
     if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return SGS_ECUDA; }
     if (I.corr_cap < 8) {
@@ -1510,12 +1549,12 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
         // Q Gamma_src -> s0 ; (Q Gamma_src) Q^T -> Gamma_M
         if (e == cudaSuccess) {
             GemmBatch g = gb_basic(n, n, n, J.p_s[cur], n, J.p_gamma + src, n, J.p_s[0], n, 1);
-            e = gemm(c, g, st, -1.0);
+            e = gemm(c, J, g, st, -1.0);
         }
         if (e == cudaSuccess) {
             GemmBatch g = gb_basic(n, n, n, J.p_s[0], n, J.p_s[cur], n, J.p_gamma + M, n, 1);
             g.transB = 1; g.mode = GEMM_SKEW;
-            e = gemm(c, g, st, -1.0);
+            e = gemm(c, J, g, st, -1.0);
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(J.sq, 0, (M + 1) * sizeof(int), st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1891,9 +1930,10 @@ sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double*
     return SGS_OK;
 }
 
-void sgs_set_fp64_gemm_path(int use_fma) { g_gemm_fma = use_fma ? 1 : 0; }
+void sgs_set_fp64_gemm_path(int path) { g_gemm_fma = (path == 2) ? 2 : (path ? 1 : 0); }
+void sgs_set_emulation_scratch(size_t bytes) { g_oz_cap = std::max<size_t>(bytes, (size_t)1 << 20); }
 
-void sgs_set_tc_loader(int use_tma) { g_tc_tma = use_tma ? 1 : 0; }
+void sgs_set_tc_loader(int loader) { g_tc_tma = loader == 2 ? 2 : (loader ? 1 : 0); }
 
 sgs_status sgs_set_graphs(sgs_ctx* c, int enable) {
     if (!c) return SGS_EINVAL;
@@ -2030,6 +2070,20 @@ int sgs_build_2ck(int L, double J, double t, double* A, int* quartic_idx, double
 
 // ------------------------------------------------------------ building blocks
 
+}  // extern "C"
+
+// slice scratch of a temporary context for the emulated FP64 path (empty on the other paths)
+static OzBuf tmp_oz(sgs_ctx& tmp, size_t need) {
+    OzBuf o;
+    if (g_gemm_fma != 2) return o;
+    const size_t b = std::min(need + 16384, g_oz_cap);
+    o.base = static_cast<uint8_t*>(tmp.dalloc(b));
+    o.bytes = o.base ? b : 0;
+    return o;
+}
+
+extern "C" {
+
 sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, double* C) {
     if (!A || !B || !C || n < 1 || batch < 1) return SGS_EINVAL;
     sgs_ctx tmp;
@@ -2046,9 +2100,19 @@ sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, 
         cudaMemcpyAsync(dA, A, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemcpyAsync(dB, B, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         GemmBatch g = gb_basic(n, n, n, PA, n, PB, n, PC, n, batch);
-        if (gemm(nullptr, g, tmp.stream, -1.0) != cudaSuccess) st = SGS_ECUDA;
-        cudaMemcpyAsync(C, dC, batch * nn * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
-        if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(n, n, n));
+        int* err = tmp.alloc<int>(1);
+        int herr = 0;
+        if (!err) st = SGS_ENOMEM;
+        else {
+            set_kernel_attributes();
+            cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
+            if (gemm(nullptr, g, tmp.stream, -1.0, &oz, err) != cudaSuccess) st = SGS_ECUDA;
+            cudaMemcpyAsync(C, dC, batch * nn * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
+            cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, tmp.stream);
+            if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+            else if (herr) st = SGS_ETIMEOUT;
+        }
     }
     cudaStreamSynchronize(tmp.stream);
     tmp.release_all();
@@ -2132,7 +2196,7 @@ sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, i
                      make_operand_map(&t.tb2, (const uint8_t*)dB + batch * nb * esz, bf, k, n, batch);
             t.m = m; t.n = n; t.k = k; t.alpha = 1.0; t.C = dC; t.c_stride = (long long)nc; t.ldc = n;
             t.out_f64 = 1; t.skew = 0; t.err = err; t.batch = batch;
-            if (!ok || gemm_tma(t, kind, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+            if (!ok || tma_product(t, kind, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
         } else if (gemm_tc(g, kind, tmp.stream) != cudaSuccess) {
             st = SGS_ECUDA;
         }
@@ -2142,6 +2206,54 @@ sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, i
         cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, tmp.stream);
         if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
         else if (herr) st = SGS_ETIMEOUT;
+    }
+    cudaStreamSynchronize(tmp.stream);
+    tmp.release_all();
+    cudaStreamDestroy(tmp.stream);
+    tmp.stream = nullptr;
+    return st;
+}
+
+sgs_status sgs_kernel_gemm(const double* A, const double* B, const double* Cin, int m, int n, int k, int trans_a,
+                           int trans_b, double alpha, double beta, double diag, int mode, int gj_k0, int gj_b,
+                           int batch, double* C) {
+    if (!A || !B || !C || m < 1 || n < 1 || k < 1 || batch < 1 || mode < 0 || mode > 2) return SGS_EINVAL;
+    if (mode == GEMM_SKEW && m != n) return SGS_EINVAL;
+    if (mode == GEMM_GJ && (m != n || gj_k0 < 0 || gj_b < 1 || gj_k0 + gj_b > n)) return SGS_EINVAL;
+    sgs_ctx tmp;
+    cudaStreamCreateWithFlags(&tmp.stream, cudaStreamNonBlocking);
+    tmp.own_stream = true;
+    const size_t na = (size_t)m * k, nb = (size_t)k * n, nc = (size_t)m * n;
+    double *dA = tmp.alloc<double>(batch * na), *dB = tmp.alloc<double>(batch * nb), *dC = tmp.alloc<double>(batch * nc);
+    double* dI = Cin ? tmp.alloc<double>(batch * nc) : nullptr;
+    int* err = tmp.alloc<int>(1);
+    sgs_status st = SGS_OK;
+    if (!dA || !dB || !dC || !err || (Cin && !dI)) st = SGS_ENOMEM;
+    if (st == SGS_OK) {
+        std::vector<double*> pa, pb, pc, pi;
+        for (int b = 0; b < batch; b++) {
+            pa.push_back(dA + b * na); pb.push_back(dB + b * nb); pc.push_back(dC + b * nc);
+            pi.push_back(dI ? dI + b * nc : nullptr);
+        }
+        double **PA = upload_ptrs(&tmp, pa), **PB = upload_ptrs(&tmp, pb), **PC = upload_ptrs(&tmp, pc);
+        double** PI = dI ? upload_ptrs(&tmp, pi) : nullptr;
+        cudaMemcpyAsync(dA, A, batch * na * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
+        cudaMemcpyAsync(dB, B, batch * nb * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
+        cudaMemcpyAsync(dC, C, batch * nc * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
+        if (dI) cudaMemcpyAsync(dI, Cin, batch * nc * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
+        cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
+        GemmBatch g = gb_basic(m, n, k, PA, trans_a ? m : k, PB, trans_b ? k : n, PC, n, batch);
+        g.transA = trans_a ? 1 : 0; g.transB = trans_b ? 1 : 0;
+        g.alpha = alpha; g.diag = diag; g.mode = mode; g.gj_k0 = gj_k0; g.gj_b = gj_b;
+        if (PI) { g.Cin = (const double* const*)PI; g.ldcin = n; g.beta = beta; }
+        set_kernel_attributes();
+        const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(m, n, k));
+        if (gemm(nullptr, g, tmp.stream, -1.0, &oz, err) != cudaSuccess) st = SGS_ECUDA;
+        int herr = 0;
+        cudaMemcpyAsync(C, dC, batch * nc * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
+        cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, tmp.stream);
+        if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        else if (st == SGS_OK && herr) st = SGS_ETIMEOUT;
     }
     cudaStreamSynchronize(tmp.stream);
     tmp.release_all();
@@ -2167,7 +2279,9 @@ sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, do
         double **PW = upload_ptrs(&tmp, pw), **PT = upload_ptrs(&tmp, pt), **PO = upload_ptrs(&tmp, po);
         cudaMemcpyAsync(W, S, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
-        if (launch_gj(nullptr, n, batch, bsz, PW, PT, piv, ld, ds, err, 0.0, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(n, n, bsz));
+        if (launch_gj(nullptr, n, batch, bsz, PW, PT, piv, ld, ds, err, 0.0, tmp.stream, &oz) != cudaSuccess)
+            st = SGS_ECUDA;
         gj_perm_kernel<<<(batch + 127) / 128, 128, 0, tmp.stream>>>(piv, perm, n, batch);
         gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), batch), 256, 0, tmp.stream>>>(PW, PO, perm, n);
         cudaMemcpyAsync(inv, O, batch * nn * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
@@ -2175,6 +2289,7 @@ sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, do
         int herr = 0;
         cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, tmp.stream);
         if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        else if (herr & SGS_DEV_TC_TIMEOUT) st = SGS_ETIMEOUT;
         else if (herr) st = SGS_ESINGULAR;
     }
     cudaStreamSynchronize(tmp.stream);
@@ -2216,11 +2331,15 @@ sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase,
         double **UA = upload_ptrs(&tmp, ua), **UB = upload_ptrs(&tmp, ub), **UC = upload_ptrs(&tmp, uc);
         cudaMemcpyAsync(W, planes.data(), planes.size() * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
-        if (launch_pf(nullptr, n, batch, bs, PY, PTU, PPK, UA, UB, UC, la, ph, err, tmp.stream) != cudaSuccess)
+        const OzBuf oz = tmp_oz(tmp, (size_t)2 * batch * oz_entry_bytes(n, n, 4 * bs));
+        if (launch_pf(nullptr, n, batch, bs, PY, PTU, PPK, UA, UB, UC, la, ph, err, tmp.stream, &oz) != cudaSuccess)
             st = SGS_ECUDA;
+        int herr = 0;
         cudaMemcpyAsync(phase, ph, 2 * batch * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
         cudaMemcpyAsync(logabs, la, batch * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
+        cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, tmp.stream);
         if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
+        else if (herr & SGS_DEV_TC_TIMEOUT) st = SGS_ETIMEOUT;
     }
     cudaStreamSynchronize(tmp.stream);
     tmp.release_all();

@@ -1,0 +1,99 @@
+"""The arithmetic of the emulated FP64 product (FP64 path 2), checked in exact
+integer and rational arithmetic on the CPU: the slicing of a double into eight
+balanced base-128 digits under its row's power of two, the exactness budget of
+the fp32 group sums, and the error of the whole scheme against the exact
+product.  These pin the claims the CUDA kernel is built on; the kernel itself is
+checked against an extended-precision reference by the GPU tests."""
+from fractions import Fraction
+
+import numpy as np
+
+S, BETA, KC = 8, 7, 512
+
+
+def expo_field(v):
+    u = np.float64(v).view(np.uint64)
+    e = int((u >> np.uint64(52)) & np.uint64(0x7FF))
+    return 1 if (e == 0 and v != 0) else e
+
+
+def digits(v, E):
+    """Balanced base-128 digits of X = round(v 2^(1078 - E)), most significant first."""
+    u = int(np.float64(v).view(np.uint64))
+    f = (u >> 52) & 0x7FF
+    m = u & ((1 << 52) - 1)
+    if f == 0:
+        f = 1
+    else:
+        m |= 1 << 52
+    sh = f - E + 3
+    if sh >= 0:
+        a = m << sh
+    elif sh <= -63:
+        a = 0
+    else:
+        a = (m + (1 << (-sh - 1))) >> (-sh)
+    X = -a if u >> 63 else a
+    t = [0] * S
+    for i in range(S - 1, 0, -1):
+        d = X & 127
+        d = d - 128 if d >= 64 else d
+        t[i] = d
+        X = (X - d) >> 7
+    t[0] = X
+    return t
+
+
+def test_digits_reconstruct_the_scaled_value():
+    rng = np.random.default_rng(0)
+    vals = np.concatenate([rng.standard_normal(300) * 10.0 ** rng.uniform(-8, 8, 300), [0.0, -0.0, 1.0, -1.0]])
+    E = max(expo_field(v) for v in vals)
+    scale = Fraction(2) ** (E - 1022)
+    for v in vals:
+        t = digits(v, E)
+        assert abs(t[0]) <= 128 and all(-64 <= d <= 63 for d in t[1:])
+        rec = scale * sum(Fraction(d) * Fraction(2) ** (-BETA * (i + 1)) for i, d in enumerate(t))
+        # rounding to 57 fractional bits of the row scale: |v - rec| <= 2^-57 scale
+        assert abs(Fraction(float(v)) - rec) <= scale * Fraction(1, 2 ** 57)
+        # every digit is exact in bf16 (at most 8 significant bits)
+        for d in t:
+            f = np.float32(d)
+            assert (f.view(np.uint32) & 0xFFFF) == 0
+
+
+def test_group_sums_within_fp32_exact_range():
+    """Worst case over K = 512 terms: group G collects the products (i, G - i);
+    the groups G <= 5 stay within 2^24 (exact in fp32), the two lowest may round."""
+    top = {}
+    for G in range(8):
+        members = [(i, G - i) for i in range(G + 1) if G - i < S]
+        per_term = sum((128 if i == 0 else 64) * (128 if j == 0 else 64) for i, j in members)
+        top[G] = KC * per_term
+    assert all(top[G] <= 2 ** 24 for G in range(6))
+    assert top[6] > 2 ** 24 and top[7] < 2 ** 31        # still exact as integers after conversion
+    # their rounding is at most K ulps of 2 at weights 2^-56 and 2^-63 of the output scale
+    assert KC * 2 * 2.0 ** (-7 * 8) <= 2.0 ** -46
+
+
+def test_scheme_error_against_exact_product():
+    rng = np.random.default_rng(1)
+    m, n, k = 6, 5, 40
+    A = rng.standard_normal((m, k)) * 10.0 ** rng.uniform(-4, 4, (m, 1))
+    B = rng.standard_normal((k, n)) * 10.0 ** rng.uniform(-4, 4, (1, n))
+    A[0, 3] *= 1e-12
+    Ea = [max(expo_field(v) for v in A[r]) for r in range(m)]
+    Eb = [max(expo_field(v) for v in B[:, c]) for c in range(n)]
+    ta = [[digits(A[r, q], Ea[r]) for q in range(k)] for r in range(m)]
+    tb = [[digits(B[q, c], Eb[c]) for q in range(k)] for c in range(n)]
+    u = 2.0 ** -53
+    for r in range(m):
+        for c in range(n):
+            acc = [sum(ta[r][q][i] * tb[c][q][G - i] for q in range(k) for i in range(G + 1)) for G in range(8)]
+            acc = [int(np.float32(a)) for a in acc]                  # the fp32 accumulators
+            hi = ((acc[0] * 128 + acc[1]) * 128 + acc[2]) * 128 + acc[3]
+            lo = ((acc[4] * 128 + acc[5]) * 128 + acc[6]) * 128 + acc[7]
+            t = float(Fraction(hi) * 2 ** 28 + lo)                   # one rounding
+            val = t * 2.0 ** (Ea[r] + Eb[c] - 2107)
+            exact = sum(Fraction(float(A[r, q])) * Fraction(float(B[q, c])) for q in range(k))
+            bound = 4 * u * float(np.abs(A[r]) @ np.abs(B[:, c]))
+            assert abs(Fraction(val) - exact) <= Fraction(bound), (r, c)
