@@ -50,10 +50,11 @@ def parse():
     ap.add_argument("--max-steps", type=int, default=400, help="serving: step cap per solve")
     ap.add_argument("--serving-dtau", type=float, default=0.2, help="serving: imaginary-time step")
     ap.add_argument("--rank", type=int, default=0, help="override the ansatz rank M (profiling cases)")
-    ap.add_argument("--fp64-path", default="fma", choices=["fma", "mma", "emulated"],
+    ap.add_argument("--fp64-path", default="emulated", choices=["fma", "mma", "emulated"],
                     help="FP64 products: FMA pipe, m8n8k4 MMA, or emulated on the bf16 tensor cores")
-    ap.add_argument("--emulation-scratch-gb", type=float, default=6.0,
-                    help="emulated FP64 products: slice scratch per instance (GB)")
+    ap.add_argument("--emulation-scratch-gb", type=float, default=0.0,
+                    help="emulated FP64 products: slice scratch per instance (GB; default 6 for one instance, "
+                         "0.125 per instance for the batched and serving workloads)")
     ap.add_argument("--tc-loader", default="tma", choices=["tma", "tmap", "cp"],
                     help="tensor-core operand staging: TMA one CTA per tile, TMA persistent, or cp.async")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -211,7 +212,8 @@ FP64_PATHS = {"mma": 0, "fma": 1, "emulated": 2}
 def set_fp64_path(sgs, args):
     sgs.set_fp64_gemm_path(FP64_PATHS[args.fp64_path])
     if args.fp64_path == "emulated":
-        sgs.set_emulation_scratch(int(args.emulation_scratch_gb * 1e9))
+        gb = args.emulation_scratch_gb or (0.125 if args.workload in ("batched", "serving") else 6.0)
+        sgs.set_emulation_scratch(int(gb * 1e9))
 
 
 def dtype_of(args):
@@ -313,7 +315,8 @@ def run_sgs(args):
         traffic = None
         tfile = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tfile):
-            t = json.load(open(tfile)).get(f"gemm_f64_all_{args.precision}", {})
+            key = f"oz_all_{args.precision}" if args.fp64_path == "emulated" else f"gemm_f64_all_{args.precision}"
+            t = json.load(open(tfile)).get(key, {})
             # counters hold for the same shape, panel widths and FP64 path only
             # and for the same launch sequence (a changed step shows as another launch count)
             if (t.get("n") == n and t.get("rank") == w.rank and t.get("fp64_path") == args.fp64_path

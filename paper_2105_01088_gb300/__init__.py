@@ -108,6 +108,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    # process-wide FP64 product path from the environment (0 MMA, 1 FMA, 2 emulated)
+    env = os.environ.get("SGS_FP64_GEMM_PATH")
+    if env is not None:
+        lib.sgs_set_fp64_gemm_path(int(env))
     return lib
 
 

@@ -58,18 +58,20 @@ __global__ void __launch_bounds__(256) eom_kernel(InstDev d, const double* si, c
             const R Dx = dre(k, l), Dy = dim(k, l);
             R Fx = akl, Fy = 0;
             if (sk >= 0 && sl >= 0) { Fx += (R)fp[2 * (sk * ni + sl)]; Fy += sgn * (R)fp[2 * (sk * ni + sl) + 1]; }
-            // C = Delta F - F Delta
-            R dfx = 0, dfy = 0, fdx = 0, fdy = 0;
+            // C = Delta F - F Delta; the sparse (quadratic) part sums S^{-1} and Im against A
+            // first and scales by -2 and sgn once
+            R ss = 0, si_ = 0;
             for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) {
                 const R a = (R)d.a_val[q];
-                dfx -= dre(k, d.a_col[q]) * a;
-                dfy -= dim(k, d.a_col[q]) * a;
+                ss -= (R)s[(size_t)k * n + d.a_col[q]] * a;
+                si_ -= (R)im[(size_t)k * n + d.a_col[q]] * a;
             }
             for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) {
                 const R a = (R)d.a_val[q];
-                fdx += a * dre(d.a_col[q], l);
-                fdy += a * dim(d.a_col[q], l);
+                ss -= a * (R)s[(size_t)d.a_col[q] * n + l];
+                si_ -= a * (R)im[(size_t)d.a_col[q] * n + l];
             }
+            R dfx = (R)-2 * ss, dfy = sgn * si_, fdx = 0, fdy = 0;
             if (sl >= 0)
                 for (int m = 0; m < ni; m++) {
                     const R ax = dre(k, d.imp[m]), ay = dim(k, d.imp[m]);

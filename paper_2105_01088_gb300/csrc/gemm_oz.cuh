@@ -36,14 +36,16 @@
 //
 // Kernels per batch chunk: exponents of op(A) and of op(B), slices of each (a
 // 32 x 32 tile transpose through shared memory where the operand is stored
-// K-strided), then the product kernel: 128 x 64 output tile per CTA of 10 warps.
-// Warp 8 (lane 0) streams, per 64-element K slab, the eight B slices (64 x 128 B
-// each, double-buffered: the next slab's are issued while the current slab's
-// MMAs run) and the eight A slices (128 x 128 B) through a six-deep ring with
-// TMA (128-byte swizzle, zero fill beyond K); warp 9 (lane 0) issues the MMAs
+// K-strided), then the product kernel: 128 x 64 output tile per CTA of 18 warps.
+// Warp 16 (lane 0) streams, per 64-element K slab, the eight B slices (64 x 128 B
+// each, one 64 KB TMA box, double-buffered: the next slab's is issued while the
+// current slab's MMAs run) and the A slices in pairs (two 128 x 128 B planes, one
+// 32 KB box; TMA issue costs about the same per box whatever its size, so boxes
+// are made large) through a three-deep ring (128-byte swizzle, zero fill beyond K); warp 17 (lane 0) issues the MMAs
 // into the eight accumulators (all 512 TMEM columns), one MMA of N up to 256
-// per A slice and K16 step (the B slices and the groups they feed are adjacent); warps 0-7 load
-// the tile's Cin terms while the MMAs run (for in-place updates every Cin
+// per A slice and K16 step (the B slices and the groups they feed are
+// adjacent); warps 0-15 load the tile's Cin terms while the MMAs run (for
+// in-place updates every Cin
 // element is read before the CTA stores any), then drain TMEM, combine, and
 // write the output through a shared-memory tile (coalesced rows).
 // Every mbarrier wait is bounded; on a timeout the launch records
@@ -61,16 +63,23 @@ namespace sgs {
 #define OZ_S 8                // slices per operand
 #define OZ_G 8                // accumulator groups G = i + j <= 7
 #define OZ_BM 128
-#define OZ_BN 64
 #define OZ_KS 64              // K elements of one 128-byte slab row
 #define OZ_KC 512             // K per exactly accumulated chunk
-#define OZ_RING 6             // depth of the A-slice ring
+#define OZ_UNIT 2             // A slices per TMA box (one ring slot)
 #define OZ_SLAB_A (OZ_BM * 128)
-#define OZ_SLAB_B (OZ_BN * 128)
-#define OZ_SMEM (2 * OZ_S * OZ_SLAB_B + OZ_RING * OZ_SLAB_A + 1024)
-#define OZ_TS (OZ_BN + 1)     // padded row stride (doubles) of the epilogue tile
-#define OZ_EPI_WARPS 8        // epilogue warps (two per TMEM lane quarter: one per column half)
-#define OZ_THREADS (32 * (OZ_EPI_WARPS + 2))
+
+// Kernel shapes: BN output columns per tile (TMEM: 8 BN columns), EPIW epilogue warps,
+// RING A-ring depth (units), BDBL double-buffered B slabs.  The wide form (64, 16, 3,
+// double) takes all of an SM; the narrow form (32, 8, 2, single) is for K <= 64 (one
+// slab: the delayed factorisation updates) and fits two CTAs per SM, so one CTA's
+// epilogue overlaps the other's loads and MMAs.
+template <int BN, int EPIW, int RING, bool BDBL> struct OzCfg {
+    static constexpr int SLAB_B = BN * 128;
+    static constexpr int SMEM = (BDBL ? 2 : 1) * OZ_S * SLAB_B + RING * OZ_UNIT * OZ_SLAB_A + 1024;
+    static constexpr int THREADS = 32 * (EPIW + 2);
+};
+#define OZ_WIDE 64, 16, 3, true
+#define OZ_NARROW 32, 8, 2, false
 
 // device scratch of one owner (an instance, or a temporary context): slices and
 // exponent fields of one batch chunk
@@ -93,8 +102,20 @@ struct OzOperand {
     int b0;                   // first batch entry of the chunk
     const int* active; int active_cmp;
     int* expo;                // [chunk][rows_pad] exponent fields
-    uint16_t* slices;         // [chunk][OZ_S][rows_pad][kp] bf16 digits
+    uint16_t* slices;         // [chunk][OZ_S][rows_pad][kp] bf16 digits (planes)
+    int interleave;           // 1: slice i in plane oz_plane(i) (A operands), 0: plane i (B operands)
 };
+
+// Order in which the A slices of a slab are taken: 0 first (it opens every accumulator),
+// then long and short rows of the product triangle in pairs, (0, 7) (1, 6) (2, 5) (3, 4):
+// every pair feeds nine 64-column groups.  A operands store slice oz_order(t) in plane t,
+// so that each pair is two adjacent planes, one TMA box.
+__host__ __device__ __forceinline__ int oz_order(int t) {
+    return (t & 1) ? (OZ_S - 1 - (t >> 1)) : (t >> 1);       // 0 7 1 6 2 5 3 4
+}
+__host__ __device__ __forceinline__ int oz_plane(int i) {
+    return i < OZ_S / 2 ? 2 * i : 2 * (OZ_S - 1 - i) + 1;     // inverse of oz_order
+}
 
 __device__ __forceinline__ int oz_expo_field(double v) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(v);
@@ -212,8 +233,10 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(OzOperand o) {
             for (int i = 0; i < OZ_S; i++) t[i] = 0;
         }
 #pragma unroll
-        for (int i = 0; i < OZ_S; i++)
-            o.slices[(((size_t)bl * OZ_S + i) * o.rows_pad + r) * o.kp + k] = oz_bf16_bits(t[i]);
+        for (int i = 0; i < OZ_S; i++) {
+            const int pl = o.interleave ? oz_plane(i) : i;
+            o.slices[(((size_t)bl * OZ_S + pl) * o.rows_pad + r) * o.kp + k] = oz_bf16_bits(t[i]);
+        }
     }
 }
 
@@ -275,19 +298,15 @@ __device__ __forceinline__ double oz_to_double(__int128 V, int e, bool neg) {
                                             (q & 0xFFFFFFFFFFFFFull)));
 }
 
-// order in which the A slices of a slab are taken: 0 first (it opens every accumulator),
-// then long and short rows of the product triangle alternately (8 - i products each), so
-// the slice ring's loads always have work in flight to hide behind
-__device__ __forceinline__ int oz_order(int ii) {
-    return (ii & 1) ? (OZ_S - 1 - (ii >> 1)) : (ii >> 1);     // 0 7 1 6 2 5 3 4
-}
-
-__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ OzGemm p) {
+template <int BN, int EPIW, int RING, bool BDBL>
+__global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(const __grid_constant__ OzGemm p) {
+    constexpr int SLAB_B = BN * 128, TS = BN + 1, NB = BDBL ? 2 : 1;
+    constexpr uint32_t TCOLS = 8u * BN;          // TMEM columns: eight groups of BN
     extern __shared__ uint8_t oz_smem_raw[];
-    __shared__ uint64_t bfull[2], bempty[2], afull[OZ_RING], aempty[OZ_RING], tfull, done;
+    __shared__ uint64_t bfull[2], bempty[2], afull[RING], aempty[RING], tfull, done;
     __shared__ uint32_t tmem_base;
     __shared__ int skip, abort_flag, s_ok;
-    __shared__ int col_e[OZ_BN];
+    __shared__ int col_e[BN];
 
     const GemmBatch& g = p.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -295,13 +314,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     __syncthreads();
     if (skip) return;
     const int bl = blockIdx.y, b = p.b0 + bl;
-    const int tnn = (g.n + OZ_BN - 1) / OZ_BN;
+    const int tnn = (g.n + BN - 1) / BN;
     int tm, tn;
     if (g.mode == GEMM_SKEW) {      // tiles holding an element on or below the diagonal
         int t = blockIdx.x;
         tm = 0;
         while (true) {
-            const int cnt = min(2 * tm + 2, tnn);
+            const int cnt = min((tm + 1) * (OZ_BM / BN), tnn);
             if (t < cnt) break;
             t -= cnt;
             tm++;
@@ -311,18 +330,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         tm = blockIdx.x / tnn;
         tn = blockIdx.x % tnn;
     }
-    const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
+    const int m0 = tm * OZ_BM, n0 = tn * BN;
     const bool active = oz_active(g.active_flag, g.active_cmp, b);
     const int nslab = active ? (g.k + OZ_KS - 1) / OZ_KS : 0;      // k <= OZ_KC (the host splits K)
 
     const uint32_t raw = smem_u32(oz_smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
-    auto sB = [&](int bb, int j) { return sbase + (uint32_t)(bb * OZ_S + j) * OZ_SLAB_B; };
-    auto sA = [&](int slot) { return sbase + 2u * OZ_S * OZ_SLAB_B + (uint32_t)slot * OZ_SLAB_A; };
+    auto sB = [&](int bb, int j) { return sbase + (uint32_t)(bb * OZ_S + j) * SLAB_B; };
+    auto sA = [&](int slot) { return sbase + (uint32_t)NB * OZ_S * SLAB_B + (uint32_t)slot * (OZ_UNIT * OZ_SLAB_A); };
+    auto bslot = [&](int sb) { return BDBL ? (sb & 1) : 0; };
+    auto bphase = [&](int sb) { return (uint32_t)((BDBL ? (sb >> 1) : sb) & 1); };
 
-    if (warp == OZ_EPI_WARPS + 1) {
+    if (warp == EPIW + 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_base)), "r"(512u));
+                     :: "r"(smem_u32(&tmem_base)), "r"(TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -330,7 +351,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bfull[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bempty[s])));
         }
-        for (int s = 0; s < OZ_RING; s++) {
+        for (int s = 0; s < RING; s++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&afull[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&aempty[s])));
         }
@@ -339,97 +360,104 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         asm volatile("fence.mbarrier_init.release.cluster;");
         abort_flag = 0;
     }
-    if (tid < OZ_BN) col_e[tid] = (active && n0 + tid < g.n) ? p.eb[(size_t)bl * p.n_pad + n0 + tid] : 0;
+    if (tid < BN) col_e[tid] = (active && n0 + tid < g.n) ? p.eb[(size_t)bl * p.n_pad + n0 + tid] : 0;
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
 
-    if (warp == OZ_EPI_WARPS) {
+    if (warp == EPIW) {
         if (lane == 0) {            // producer
-            // order: B(0); then per slab s: A(s, 0..3), B(s + 1) (once slab s - 1 has released its
-            // buffer), A(s, 4..7), so the next slab's B slices load during all of slab s's MMAs
-            int nb = 0, q = 0;      // B slabs and A slices issued
+            // one TMA box per B slab (the eight slices, 8 BN rows) and per A unit (two slices, 32 KB).
+            // Double-buffered B: B(0); then per slab s: A units 0 and 1, B(s + 1) (once slab s - 1 has
+            // released its buffer), A units 2 and 3, so the next slab's B loads during slab s's MMAs.
+            // Single buffer: B(s) once slab s - 1 has released it.
+            constexpr int NU = OZ_S / OZ_UNIT;
+            int nb = 0, q = 0;      // B slabs and A units issued
             bool ok = true;
             auto issue_b = [&](int sb) {
-                const int bb = sb & 1;
-                mbar_expect_tx(smem_u32(&bfull[bb]), (uint32_t)(OZ_S * OZ_SLAB_B));
-                for (int j = 0; j < OZ_S; j++)
-                    oz_tma_load(sB(bb, j), &p.tb, sb * OZ_KS, n0, bl * OZ_S + j, smem_u32(&bfull[bb]));
+                const int bb = bslot(sb);
+                mbar_expect_tx(smem_u32(&bfull[bb]), (uint32_t)(OZ_S * SLAB_B));
+                oz_tma_load(sB(bb, 0), &p.tb, sb * OZ_KS, n0, bl * OZ_S, smem_u32(&bfull[bb]));
                 nb = sb + 1;
             };
             if (nslab > 0) issue_b(0);
             for (int s = 0; s < nslab && ok; s++) {
-                for (int ii = 0; ii < OZ_S; ii++) {
-                    if (ii == OZ_S / 2 && s + 1 < nslab) {
-                        if (s >= 1 && !mbar_wait_or_abort(smem_u32(&bempty[(s + 1) & 1]),
-                                                          (uint32_t)(((s - 1) >> 1) & 1), p.err)) {
+                if (!BDBL && s > 0) {
+                    if (!mbar_wait_or_abort(smem_u32(&bempty[0]), bphase(s - 1), p.err)) { ok = false; break; }
+                    issue_b(s);
+                }
+                for (int u = 0; u < NU; u++) {
+                    if (BDBL && u == NU / 2 && s + 1 < nslab) {
+                        if (s >= 1 && !mbar_wait_or_abort(smem_u32(&bempty[(s + 1) & 1]), bphase(s - 1), p.err)) {
                             ok = false;
                             break;
                         }
                         issue_b(s + 1);
                     }
-                    const int slot = q % OZ_RING;
-                    if (q >= OZ_RING &&
-                        !mbar_wait_or_abort(smem_u32(&aempty[slot]), (uint32_t)(((q / OZ_RING) - 1) & 1), p.err)) {
+                    const int slot = q % RING;
+                    if (q >= RING &&
+                        !mbar_wait_or_abort(smem_u32(&aempty[slot]), (uint32_t)(((q / RING) - 1) & 1), p.err)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(smem_u32(&afull[slot]), (uint32_t)OZ_SLAB_A);
-                    oz_tma_load(sA(slot), &p.ta, s * OZ_KS, m0, bl * OZ_S + oz_order(ii), smem_u32(&afull[slot]));
+                    mbar_expect_tx(smem_u32(&afull[slot]), (uint32_t)(OZ_UNIT * OZ_SLAB_A));
+                    oz_tma_load(sA(slot), &p.ta, s * OZ_KS, m0, bl * OZ_S + OZ_UNIT * u, smem_u32(&afull[slot]));
                     q++;
                 }
                 if (*(volatile int*)&abort_flag) ok = false;
             }
             if (!ok) abort_flag = 1;
             // every load issued has landed before the CTA can leave
-            for (int x = (nb > 2 ? nb - 2 : 0); x < nb; x++)
-                mbar_wait(smem_u32(&bfull[x & 1]), (uint32_t)((x >> 1) & 1), p.err);
-            for (int x = (q > OZ_RING ? q - OZ_RING : 0); x < q; x++)
-                mbar_wait(smem_u32(&afull[x % OZ_RING]), (uint32_t)((x / OZ_RING) & 1), p.err);
+            for (int x = (nb > NB ? nb - NB : 0); x < nb; x++)
+                mbar_wait(smem_u32(&bfull[bslot(x)]), bphase(x), p.err);
+            for (int x = (q > RING ? q - RING : 0); x < q; x++)
+                mbar_wait(smem_u32(&afull[x % RING]), (uint32_t)((x / RING) & 1), p.err);
         }
-    } else if (warp == OZ_EPI_WARPS + 1) {
+    } else if (warp == EPIW + 1) {
         if (lane == 0) {            // MMA issuer
-            constexpr uint32_t IDESC1 = tc_idesc(TC_BF16, OZ_BN), IDESC2 = tc_idesc(TC_BF16, 2 * OZ_BN),
-                               IDESC3 = tc_idesc(TC_BF16, 3 * OZ_BN), IDESC4 = tc_idesc(TC_BF16, 4 * OZ_BN);
+            constexpr int MAXB = 256 / BN;             // B slices per MMA (N <= 256)
             // descriptors of slot 0 / buffer 0 slice 0; other slabs offset the 16-byte address field
             const uint64_t dA0 = tma_smem_desc(sA(0)), dB0 = tma_smem_desc(sB(0, 0));
             int q = 0;
             bool ok = true;
             for (int s = 0; s < nslab && ok; s++) {
-                const int bb = s & 1;
-                if (!mbar_wait_or_abort(smem_u32(&bfull[bb]), (uint32_t)((s >> 1) & 1), p.err)) {
+                const int bb = bslot(s);
+                if (!mbar_wait_or_abort(smem_u32(&bfull[bb]), bphase(s), p.err)) {
                     ok = false;
                     break;
                 }
                 const int kv = min(OZ_KS, g.k - s * OZ_KS);
                 const int nk16 = (kv + 15) / 16;
-                const uint64_t dB = dB0 + (uint64_t)((bb * OZ_S * OZ_SLAB_B) >> 4);
-                for (int ii = 0; ii < OZ_S; ii++, q++) {
-                    const int i = oz_order(ii);
-                    const int slot = q % OZ_RING;
-                    if (!mbar_wait_or_abort(smem_u32(&afull[slot]), (uint32_t)((q / OZ_RING) & 1), p.err)) {
+                const uint64_t dB = dB0 + (uint64_t)((bb * OZ_S * SLAB_B) >> 4);
+                for (int u = 0; u < OZ_S / OZ_UNIT; u++, q++) {
+                    const int slot = q % RING;
+                    if (!mbar_wait_or_abort(smem_u32(&afull[slot]), (uint32_t)((q / RING) & 1), p.err)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint64_t da = dA0 + (uint64_t)((slot * OZ_SLAB_A) >> 4);
-                    // the first slice (i = 0, taken first) opens every group's accumulator
-                    const uint32_t first = (s == 0 && ii == 0) ? 1u : 0u;
-                    // products (i, j), j = 0 .. 7 - i, land in groups i .. 7: adjacent 64-column
-                    // accumulators, and the B slices j are adjacent 64-row blocks in shared memory,
-                    // so one MMA of N = 64 (8 - i) (at most 256 per instruction) covers them
 #pragma unroll
-                    for (int kk = 0; kk < OZ_KS / 16; kk++) {
-                        if (kk < nk16) {
+                    for (int h = 0; h < OZ_UNIT; h++) {
+                        const int i = oz_order(OZ_UNIT * u + h);
+                        const uint64_t da = dA0 + (uint64_t)(((slot * OZ_UNIT + h) * OZ_SLAB_A) >> 4);
+                        // the first slice (i = 0, taken first) opens every group's accumulator
+                        const uint32_t first = (s == 0 && u == 0 && h == 0) ? 1u : 0u;
+                        // products (i, j), j = 0 .. 7 - i, land in groups i .. 7: adjacent 64-column
+                        // accumulators, and the B slices j are adjacent 64-row blocks in shared
+                        // memory, so one MMA of N = 64 (8 - i) (at most 256 per instruction) covers them
 #pragma unroll
-                            for (int c = 0; c < OZ_S; c += 4) {
-                                const int nb = min(4, OZ_S - i - c);
-                                if (nb > 0) {
-                                    const uint32_t acc = tmem + (uint32_t)((i + c) * OZ_BN);
-                                    const uint64_t db = dB + (uint64_t)((c * OZ_SLAB_B) >> 4) + 2 * kk;
-                                    const uint32_t idesc = nb == 4 ? IDESC4 : nb == 3 ? IDESC3 : nb == 2 ? IDESC2 : IDESC1;
-                                    tc_mma(acc, da + 2 * kk, db, idesc, (first && kk == 0) ? 0u : 1u, TC_BF16);
+                        for (int kk = 0; kk < OZ_KS / 16; kk++) {
+                            if (kk < nk16) {
+#pragma unroll
+                                for (int c = 0; c < OZ_S; c += MAXB) {
+                                    const int nb = min(MAXB, OZ_S - i - c);
+                                    if (nb > 0) {
+                                        const uint32_t acc = tmem + (uint32_t)((i + c) * BN);
+                                        const uint64_t db = dB + (uint64_t)((c * SLAB_B) >> 4) + 2 * kk;
+                                        tc_mma(acc, da + 2 * kk, db, tc_idesc(TC_BF16, BN * nb),
+                                               (first && kk == 0) ? 0u : 1u, TC_BF16);
+                                    }
                                 }
                             }
                         }
@@ -452,9 +480,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
             mbar_wait(smem_u32(&done), 0u, p.err);
         }
     } else {
-        // epilogue: warps 0-7.  Warp w drains TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 (output rows)
-        // for the columns of half w / 4; the store pass gives thread tid the elements tid + 256 q.
-        constexpr int NE = 32 * OZ_EPI_WARPS, PER = OZ_BM * OZ_BN / NE;
+        // epilogue: warps 0 .. EPIW - 1.  Warp w drains TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 (output
+        // rows) for the columns of part w / 4; the store pass gives thread tid the elements tid + 32 EPIW q.
+        constexpr int NE = 32 * EPIW, PER = OZ_BM * BN / NE;
         const double* Cinb = g.Cin ? g.Cin[b] + g.offCin : nullptr;
         const double* Cin2b = g.Cin2 ? g.Cin2[b] + g.offCin : nullptr;
         double* Cb = g.C[b] + g.offC;
@@ -463,19 +491,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
         // the batch entry passes through), loaded while the MMAs run; Cin may be C itself, and
         // every element is read before this CTA stores any
         double extra[PER];
+        const bool use_cin = Cinb && (!active || g.beta != 0.0);
+        const bool scale_cin = active && g.beta != 1.0;          // beta = 1 (the in-place updates): no product
+        const bool use_cin2 = active && Cin2b;
 #pragma unroll
         for (int q = 0; q < PER; q++) {
-            const int e = tid + NE * q, rr = e / OZ_BN, cc = e % OZ_BN;
+            const int e = tid + NE * q, rr = e / BN, cc = e % BN;
             const int r = m0 + rr, c = n0 + cc;
             double x = 0.0;
             if (r < g.m && c < g.n && !(skew && r < c)) {
                 const long long off = (long long)r * g.ldcin + c;
-                if (!active) {
-                    if (Cinb) x = Cinb[off];
-                } else {
-                    if (Cinb && g.beta != 0.0 && !(gj && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b)) x = g.beta * Cinb[off];
-                    if (Cin2b) x = fma(g.beta2, Cin2b[off], x);
+                if (use_cin && !(active && gj && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b)) {
+                    x = Cinb[off];
+                    if (scale_cin) x *= g.beta;
                 }
+                if (use_cin2) x = fma(g.beta2, Cin2b[off], x);
             }
             extra[q] = x;
         }
@@ -491,18 +521,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
             asm volatile("tcgen05.fence::after_thread_sync;");
             double* tile = reinterpret_cast<double*>(oz_smem_raw + (sbase - raw));
             const double alpha = g.alpha * (g.alpha_b ? g.alpha_b[b] : 1.0);
-            const int lq = warp & 3, half = warp >> 2;
+            constexpr int PCOLS = BN / (EPIW / 4);                 // columns per warp
+            const int lq = warp & 3, part = warp >> 2;          // lane quarter, column part
             const int rr0 = lq * 32 + lane, row = m0 + rr0;
             const int er = (active && row < g.m) ? p.ea[(size_t)bl * p.m_pad + row] : 0;
             const int ae = p.alpha_pow2 ? p.alpha_e : 0;
             const bool an = p.alpha_pow2 && p.alpha_neg;
             if (nslab > 0) {
 #pragma unroll 1
-                for (int cb = half * (OZ_BN / 8); cb < (half + 1) * (OZ_BN / 8); cb++) {
+                for (int cb = part * (PCOLS / 4); cb < (part + 1) * (PCOLS / 4); cb++) {
                     uint32_t u[OZ_G][4];
 #pragma unroll
                     for (int G = 0; G < OZ_G; G++) {
-                        const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(G * OZ_BN + cb * 4);
+                        const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(G * BN + cb * 4);
                         asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                                      : "=r"(u[G][0]), "=r"(u[G][1]), "=r"(u[G][2]), "=r"(u[G][3])
                                      : "r"(ta));
@@ -516,33 +547,33 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
                             v = oz_to_double(oz_combine(u, j), er + fc - 2107 + ae, an);
                             if (!p.alpha_pow2) v *= alpha;
                         }
-                        tile[rr0 * OZ_TS + c] = v;
+                        tile[rr0 * TS + c] = v;
                     }
                 }
             }
             asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
 #pragma unroll
             for (int q = 0; q < PER; q++) {
-                const int e = tid + NE * q, rr = e / OZ_BN, cc = e % OZ_BN;
+                const int e = tid + NE * q, rr = e / BN, cc = e % BN;
                 const int r = m0 + rr, c = n0 + cc;
                 if (r >= g.m || c >= g.n || (skew && r < c)) continue;
                 double v = extra[q];
                 if (active) {
-                    v += tile[rr * OZ_TS + cc];
+                    v += tile[rr * TS + cc];
                     if (r == c) v += g.diag;
                 }
                 if (skew && r == c) v = 0.0;
-                tile[rr * OZ_TS + cc] = v;            // kept for the mirrored block
+                tile[rr * TS + cc] = v;            // kept for the mirrored block
                 if (!gj || c < g.gj_k0 || c >= g.gj_k0 + g.gj_b) Cb[(long long)r * g.ldc + c] = v;
             }
             if (skew) {
                 // mirrored block: C[c][r] = -C[r][c] below the diagonal, rows of the mirror coalesced
                 asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
-                for (int e = tid; e < OZ_BM * OZ_BN; e += NE) {
+                for (int e = tid; e < OZ_BM * BN; e += NE) {
                     const int cc = e / OZ_BM, rr = e % OZ_BM;
                     const int r = m0 + rr, c = n0 + cc;
                     if (r >= g.m || c >= g.n || r <= c) continue;
-                    Cb[(long long)c * g.ldc + r] = -tile[rr * OZ_TS + cc];
+                    Cb[(long long)c * g.ldc + r] = -tile[rr * TS + cc];
                 }
             }
         } else if (tid == 0) {
@@ -551,8 +582,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == OZ_EPI_WARPS + 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512u));
+    if (warp == EPIW + 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS));
     }
 }
 
@@ -562,18 +593,19 @@ inline size_t oz_round(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // scratch bytes of one batch entry of an m x n x k product (slices and exponent fields)
 inline size_t oz_entry_bytes(int m, int n, int k) {
-    const size_t kp = oz_round((size_t)k, 8), mp = oz_round((size_t)m, OZ_BM), np = oz_round((size_t)n, OZ_BN);
+    const size_t kp = oz_round((size_t)k, 8), mp = oz_round((size_t)m, OZ_BM), np = oz_round((size_t)n, 64);
     return (size_t)OZ_S * 2 * (mp + np) * kp + 4 * (mp + np);
 }
 
 // Tensor map of a slice batch [nmat][rows_pad][kp] bf16 with x extent k (zero fill beyond),
 // box 64 x box_rows x 1 (128-byte rows, 128-byte swizzle)
-inline bool make_slice_map(CUtensorMap* map, const void* base, int k, int kp, int rows_pad, int nmat, int box_rows) {
+inline bool make_slice_map(CUtensorMap* map, const void* base, int k, int kp, int rows_pad, int nmat, int box_rows,
+                           int box_planes) {
     TmaEncodeFn fn = tma_encode_fn();
     if (!fn || !base || ((uintptr_t)base & 15) || (kp & 7)) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows_pad, (cuuint64_t)nmat};
     const cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)kp * rows_pad * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)OZ_KS, (cuuint32_t)box_rows, 1u};
+    const cuuint32_t box[3] = {(cuuint32_t)OZ_KS, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -586,12 +618,12 @@ inline void oz_prepare(const OzOperand& o, int bc, cudaStream_t st) {
     oz_slice_kernel<<<dim3((o.k + 31) / 32, o.rows_pad / 32, bc), 256, 0, st>>>(o);
 }
 
-// number of output tiles of one batch entry
-inline int oz_tiles(const GemmBatch& g) {
-    const int tmn = (g.m + OZ_BM - 1) / OZ_BM, tnn = (g.n + OZ_BN - 1) / OZ_BN;
+// number of output tiles of one batch entry (tile width bn)
+inline int oz_tiles(const GemmBatch& g, int bn) {
+    const int tmn = (g.m + OZ_BM - 1) / OZ_BM, tnn = (g.n + bn - 1) / bn;
     if (g.mode != GEMM_SKEW) return tmn * tnn;
     int t = 0;
-    for (int tm = 0; tm < tmn; tm++) t += std::min(2 * tm + 2, tnn);
+    for (int tm = 0; tm < tmn; tm++) t += std::min((tm + 1) * (OZ_BM / bn), tnn);
     return t;
 }
 
@@ -611,12 +643,14 @@ inline int oz_launches(const GemmBatch& g, const OzBuf& buf) {
 
 // one K chunk (k <= OZ_KC) of the emulated product, in batch chunks that fit the scratch
 inline cudaError_t gemm_oz_chunk(const GemmBatch& g, const OzBuf& buf, int* err, cudaStream_t st) {
-    const int kp = (int)oz_round(g.k, 8), mp = (int)oz_round(g.m, OZ_BM), np = (int)oz_round(g.n, OZ_BN);
+    const int kp = (int)oz_round(g.k, 8), mp = (int)oz_round(g.m, OZ_BM), np = (int)oz_round(g.n, 64);
+    const bool narrow = g.k <= OZ_KS;                    // one slab: the narrow form, two CTAs per SM
+    const int bn = narrow ? 32 : 64;
     const size_t sa = (size_t)OZ_S * mp * kp * 2, sb = (size_t)OZ_S * np * kp * 2;
     const size_t per = oz_entry_bytes(g.m, g.n, g.k);
     const int chunk = (int)std::min<size_t>(g.batch, buf.bytes > 8192 ? (buf.bytes - 8192) / per : 0);
     if (chunk <= 0) return gemm_f64(g, st);
-    const int tiles = oz_tiles(g);
+    const int tiles = oz_tiles(g, bn);
     for (int b0 = 0; b0 < g.batch; b0 += chunk) {
         const int bc = std::min(chunk, g.batch - b0);
         uint16_t* as = reinterpret_cast<uint16_t*>(buf.base);
@@ -624,15 +658,15 @@ inline cudaError_t gemm_oz_chunk(const GemmBatch& g, const OzBuf& buf, int* err,
         int* ea = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(bs) + oz_round((size_t)bc * sb, 1024));
         int* eb = ea + oz_round((size_t)bc * mp, 64);
         OzOperand oa{g.A, g.A2, g.sA2, g.offA, g.lda, g.transA ? 1 : 0, g.m, g.k, mp, kp, b0,
-                     g.active_flag, g.active_cmp, ea, as};
+                     g.active_flag, g.active_cmp, ea, as, 1};
         OzOperand ob{g.B, g.B2, g.sB2, g.offB, g.ldb, g.transB ? 0 : 1, g.n, g.k, np, kp, b0,
-                     g.active_flag, g.active_cmp, eb, bs};
+                     g.active_flag, g.active_cmp, eb, bs, 0};
         oz_prepare(oa, bc, st);
         oz_prepare(ob, bc, st);
         OzGemm p;
         std::memset(&p, 0, sizeof(p));
-        if (!make_slice_map(&p.ta, as, g.k, kp, mp, bc * OZ_S, OZ_BM) ||
-            !make_slice_map(&p.tb, bs, g.k, kp, np, bc * OZ_S, OZ_BN))
+        if (!make_slice_map(&p.ta, as, g.k, kp, mp, bc * OZ_S, OZ_BM, OZ_UNIT) ||
+            !make_slice_map(&p.tb, bs, g.k, kp, np, bc * OZ_S, bn, OZ_S))
             return cudaErrorInvalidValue;
         p.g = g; p.b0 = b0; p.m_pad = mp; p.n_pad = np; p.ea = ea; p.eb = eb; p.err = err;
         int ex = 0;
@@ -640,7 +674,10 @@ inline cudaError_t gemm_oz_chunk(const GemmBatch& g, const OzBuf& buf, int* err,
         if (!g.alpha_b && (fr == 0.5 || fr == -0.5)) {
             p.alpha_pow2 = 1; p.alpha_e = ex - 1; p.alpha_neg = g.alpha < 0.0;
         }
-        oz_gemm_kernel<<<dim3(tiles, bc), OZ_THREADS, OZ_SMEM, st>>>(p);
+        if (narrow)
+            oz_gemm_kernel<OZ_NARROW><<<dim3(tiles, bc), OzCfg<OZ_NARROW>::THREADS, OzCfg<OZ_NARROW>::SMEM, st>>>(p);
+        else
+            oz_gemm_kernel<OZ_WIDE><<<dim3(tiles, bc), OzCfg<OZ_WIDE>::THREADS, OzCfg<OZ_WIDE>::SMEM, st>>>(p);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
