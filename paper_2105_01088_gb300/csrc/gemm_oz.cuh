@@ -28,7 +28,7 @@
 //
 // Combination.  The eight group sums are converted to integers and combined
 // exactly, hi = sum_{G<4} v_G 2^(7 (3 - G)), lo = sum_{G>=4} v_G 2^(7 (7 - G)),
-// V = hi 2^28 + lo in 128-bit integer arithmetic; V is rounded once to 53 bits
+// V = hi 2^28 + lo as a pair of 64-bit words; V is rounded once to 53 bits
 // and given the exponent E_r + F_c - 2107 (plus that of alpha when alpha is a
 // power of two, else one multiplication), all in integer arithmetic on the bit
 // pattern.  The GemmBatch epilogue (beta Cin, beta2 Cin2, diag, FULL / SKEW / GJ
@@ -36,18 +36,21 @@
 //
 // Kernels per batch chunk: exponents of op(A) and of op(B), slices of each (a
 // 32 x 32 tile transpose through shared memory where the operand is stored
-// K-strided), then the product kernel: 128 x 64 output tile per CTA of 18 warps.
-// Warp 16 (lane 0) streams, per 64-element K slab, the eight B slices (64 x 128 B
-// each, one 64 KB TMA box, double-buffered: the next slab's is issued while the
-// current slab's MMAs run) and the A slices in pairs (two 128 x 128 B planes, one
-// 32 KB box; TMA issue costs about the same per box whatever its size, so boxes
-// are made large) through a three-deep ring (128-byte swizzle, zero fill beyond K); warp 17 (lane 0) issues the MMAs
-// into the eight accumulators (all 512 TMEM columns), one MMA of N up to 256
-// per A slice and K16 step (the B slices and the groups they feed are
-// adjacent); warps 0-15 load the tile's Cin terms while the MMAs run (for
-// in-place updates every Cin
-// element is read before the CTA stores any), then drain TMEM, combine, and
-// write the output through a shared-memory tile (coalesced rows).
+// K-strided), then the product kernel.  Its wide form takes a 128 x 64 output
+// tile per CTA of 18 warps, one CTA per SM; its narrow form (K <= 64, the
+// delayed factorisation updates) a 128 x 32 tile per CTA of 10 warps, two CTAs
+// per SM.  In both:
+//   * one producer lane loads, per 64-element K slab, the eight B slices as one
+//     TMA box (TMA issue costs about the same per box whatever its size, so
+//     boxes are made large) and the A slices in pairs (one 32 KB box per pair of
+//     adjacent planes) through a ring, 128-byte swizzle, zero fill beyond K;
+//   * one MMA lane issues, per A slice and K16 step, one MMA of N up to 256
+//     covering all the products of that slice (the B slices and the groups they
+//     feed are adjacent) into the eight accumulators;
+//   * the epilogue warps wait for the MMAs, issue the loads of the tile's Cin
+//     terms (for in-place updates every Cin element is read before the CTA
+//     stores any), drain TMEM and combine, and write the output through a
+//     shared-memory tile (coalesced rows).
 // Every mbarrier wait is bounded; on a timeout the launch records
 // SGS_DEV_TC_TIMEOUT in the error word, waits (bounded) for its loads and MMAs
 // in flight, frees TMEM and returns.
@@ -258,44 +261,43 @@ __device__ __forceinline__ void oz_tma_load(uint32_t dst, const CUtensorMap* map
 
 // The eight group sums (integers held exactly in fp32, or rounded to even integers for
 // the two lowest groups) of output column j, combined exactly:
-//   V = hi 2^28 + lo,  hi = sum_{G<4} v_G 2^(7 (3 - G)),  lo = sum_{G>=4} v_G 2^(7 (7 - G)),
-// |hi|, |lo| < 2^47, |V| < 2^76.
-__device__ __forceinline__ __int128 oz_combine(const uint32_t (&u)[OZ_G][4], int j) {
-    long long hi = 0, lo = 0;
+//   hi = sum_{G<4} v_G 2^(7 (3 - G)),  lo = sum_{G>=4} v_G 2^(7 (7 - G)),  |hi|, |lo| < 2^47,
+// the value being V = hi 2^28 + lo.
+__device__ __forceinline__ void oz_combine(const uint32_t (&u)[OZ_G][4], int j, long long& hi, long long& lo) {
+    hi = 0;
+    lo = 0;
 #pragma unroll
     for (int G = 0; G < 4; G++) hi = hi * 128 + (long long)__float2int_rn(__uint_as_float(u[G][j]));
 #pragma unroll
     for (int G = 4; G < 8; G++) lo = lo * 128 + (long long)__float2int_rn(__uint_as_float(u[G][j]));
-    return (__int128)hi * 268435456 + (__int128)lo;
 }
 
-// (-1)^neg V 2^e as a double, V rounded once to 53 bits (to nearest, ties to even), in
-// integer arithmetic; results outside the normal range take scalbn
-__device__ __forceinline__ double oz_to_double(__int128 V, int e, bool neg) {
-    if (V == 0) return 0.0;
-    bool sgn = V < 0;
-    if (neg) sgn = !sgn;
-    const unsigned __int128 A = V < 0 ? (unsigned __int128)(-V) : (unsigned __int128)V;
-    const unsigned long long ah = (unsigned long long)(A >> 64), al = (unsigned long long)A;
-    int p = ah ? 127 - __clzll((long long)ah) : 63 - __clzll((long long)al);     // leading bit
-    unsigned long long q;
-    if (p <= 52) {
-        q = al << (52 - p);
-    } else {
-        const int sh = p - 52;                                                    // 1 .. 75
-        const unsigned __int128 Q = A >> sh;
-        const unsigned __int128 R = A - (Q << sh);
-        const unsigned __int128 H = (unsigned __int128)1 << (sh - 1);
-        q = (unsigned long long)Q;
-        if (R > H || (R == H && (q & 1ull))) {
-            q++;
-            if (q == (1ull << 53)) { q >>= 1; p++; }
-        }
-    }
-    const int be = p + e + 1023;
-    if (be < 1 || be > 2046) return scalbn(sgn ? -(double)q : (double)q, p - 52 + e);
-    return __longlong_as_double((long long)(((unsigned long long)sgn << 63) | ((unsigned long long)be << 52) |
-                                            (q & 0xFFFFFFFFFFFFFull)));
+// (-1)^neg V 2^e as a double, V = hi 2^28 + lo (|V| < 2^76) rounded once to 53 bits (to
+// nearest, ties to even), in 64-bit integer arithmetic without data-dependent branches (so
+// the columns of a thread interleave); results outside the normal range take scalbn
+__device__ __forceinline__ double oz_to_double(long long hi, long long lo, int e, bool neg) {
+    // V as a two's complement pair (vh, vl)
+    const unsigned long long hl = (unsigned long long)hi << 28;
+    const unsigned long long vl = hl + (unsigned long long)lo;
+    const long long vh = (hi >> 36) + (lo >> 63) + (vl < hl ? 1ll : 0ll);
+    const bool sv = vh < 0;
+    // |V| = (mh, ml), mh < 2^12
+    const unsigned long long ml = sv ? 0ull - vl : vl;
+    const unsigned long long mh = sv ? ~(unsigned long long)vh + (vl == 0ull ? 1ull : 0ull) : (unsigned long long)vh;
+    const int p = mh ? 127 - __clzll((long long)mh) : 63 - __clzll((long long)ml);   // leading bit
+    const int sh = p - 52;                                                            // -52 .. 23
+    const int shr = sh > 0 ? sh : 0, shl = sh < 0 ? -sh : 0;
+    unsigned long long q = shr ? (ml >> shr) | (mh << (64 - shr)) : ml << shl;
+    const unsigned long long R = ml & ((1ull << shr) - 1ull), H = shr ? 1ull << (shr - 1) : 0ull;
+    q += (shr && (R > H || (R == H && (q & 1ull)))) ? 1ull : 0ull;
+    const bool ovf = (q >> 53) != 0ull;
+    q = ovf ? q >> 1 : q;
+    const int p2 = p + (ovf ? 1 : 0), be = p2 + e + 1023;
+    const bool sgn = sv != neg;
+    double r = __longlong_as_double((long long)(((unsigned long long)sgn << 63) | ((unsigned long long)be << 52) |
+                                                (q & 0xFFFFFFFFFFFFFull)));
+    if (be < 1 || be > 2046) r = scalbn(sgn ? -(double)q : (double)q, p2 - 52 + e);
+    return (ml | mh) ? r : 0.0;
 }
 
 template <int BN, int EPIW, int RING, bool BDBL>
@@ -487,28 +489,6 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
         const double* Cin2b = g.Cin2 ? g.Cin2[b] + g.offCin : nullptr;
         double* Cb = g.C[b] + g.offC;
         const bool skew = g.mode == GEMM_SKEW, gj = g.mode == GEMM_GJ;
-        // the additive terms of the thread's elements (beta Cin + beta2 Cin2, or Cin itself when
-        // the batch entry passes through), loaded while the MMAs run; Cin may be C itself, and
-        // every element is read before this CTA stores any
-        double extra[PER];
-        const bool use_cin = Cinb && (!active || g.beta != 0.0);
-        const bool scale_cin = active && g.beta != 1.0;          // beta = 1 (the in-place updates): no product
-        const bool use_cin2 = active && Cin2b;
-#pragma unroll
-        for (int q = 0; q < PER; q++) {
-            const int e = tid + NE * q, rr = e / BN, cc = e % BN;
-            const int r = m0 + rr, c = n0 + cc;
-            double x = 0.0;
-            if (r < g.m && c < g.n && !(skew && r < c)) {
-                const long long off = (long long)r * g.ldcin + c;
-                if (use_cin && !(active && gj && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b)) {
-                    x = Cinb[off];
-                    if (scale_cin) x *= g.beta;
-                }
-                if (use_cin2) x = fma(g.beta2, Cin2b[off], x);
-            }
-            extra[q] = x;
-        }
         bool ok = true;
         if (nslab > 0) {
             if (tid == 0) s_ok = mbar_wait_or_abort(smem_u32(&tfull), 0u, p.err) ? 1 : 0;
@@ -516,10 +496,27 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
             ok = s_ok != 0;
         }
         if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
             // every MMA has completed, so every load has been consumed: the stage buffers
             // become the (padded) FP64 output tile
-            asm volatile("tcgen05.fence::after_thread_sync;");
             double* tile = reinterpret_cast<double*>(oz_smem_raw + (sbase - raw));
+            // Cin's tile is copied into the free stage memory after the output tile with cp.async,
+            // overlapping the drain and combination (a barrier does not wait for these asynchronous
+            // copies, unlike ordinary loads); rows must start on 16 bytes, else the store pass reads
+            // Cin itself.  Cin may be C itself: every Cin element is read before this CTA stores any.
+            double* cin_s = tile + OZ_BM * TS;
+            const bool use_cin = Cinb && (!active || g.beta != 0.0);
+            const bool cin_async = use_cin && ((reinterpret_cast<uintptr_t>(Cinb) & 15) == 0) &&
+                                   ((g.ldcin & 1) == 0);
+            if (cin_async) {
+                for (int x = tid; x < OZ_BM * (BN / 2); x += NE) {
+                    const int rr = x / (BN / 2), c = n0 + 2 * (x % (BN / 2)), r = m0 + rr;
+                    const uint32_t bytes = r < g.m ? (c + 1 < g.n ? 16u : (c < g.n ? 8u : 0u)) : 0u;
+                    const double* src = bytes ? Cinb + (long long)r * g.ldcin + c : Cinb;
+                    cp_async16(smem_u32(cin_s + rr * BN + (c - n0)), src, bytes);
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            }
             const double alpha = g.alpha * (g.alpha_b ? g.alpha_b[b] : 1.0);
             constexpr int PCOLS = BN / (EPIW / 4);                 // columns per warp
             const int lq = warp & 3, part = warp >> 2;          // lane quarter, column part
@@ -544,21 +541,30 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
                         const int c = cb * 4 + j, fc = col_e[c];
                         double v = 0.0;
                         if (er > 0 && fc > 0) {
-                            v = oz_to_double(oz_combine(u, j), er + fc - 2107 + ae, an);
+                            long long hi, lo;
+                            oz_combine(u, j, hi, lo);
+                            v = oz_to_double(hi, lo, er + fc - 2107 + ae, an);
                             if (!p.alpha_pow2) v *= alpha;
                         }
                         tile[rr0 * TS + c] = v;
                     }
                 }
             }
+            if (cin_async) asm volatile("cp.async.wait_all;" ::: "memory");
             asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
-#pragma unroll
+            const bool scale_cin = active && g.beta != 1.0;          // beta = 1 (the in-place updates): no product
+#pragma unroll 4
             for (int q = 0; q < PER; q++) {
                 const int e = tid + NE * q, rr = e / BN, cc = e % BN;
                 const int r = m0 + rr, c = n0 + cc;
                 if (r >= g.m || c >= g.n || (skew && r < c)) continue;
-                double v = extra[q];
+                double v = 0.0;
+                if (use_cin && !(active && gj && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b)) {
+                    v = cin_async ? cin_s[rr * BN + cc] : Cinb[(long long)r * g.ldcin + c];
+                    if (scale_cin) v *= g.beta;
+                }
                 if (active) {
+                    if (Cin2b) v = fma(g.beta2, Cin2b[(long long)r * g.ldcin + c], v);
                     v += tile[rr * TS + cc];
                     if (r == c) v += g.diag;
                 }

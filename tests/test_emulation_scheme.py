@@ -97,3 +97,55 @@ def test_scheme_error_against_exact_product():
             exact = sum(Fraction(float(A[r, q])) * Fraction(float(B[q, c])) for q in range(k))
             bound = 4 * u * float(np.abs(A[r]) @ np.abs(B[:, c]))
             assert abs(Fraction(val) - exact) <= Fraction(bound), (r, c)
+
+
+def _to_double(hi, lo, e, neg):
+    """The combination's rounding of V = hi 2^28 + lo (|hi|, |lo| < 2^47) to a double
+    times 2^e, in the 64-bit word arithmetic the CUDA kernel uses (two's complement
+    pair, leading-bit search, shift with round to nearest even, exponent assembly)."""
+    import struct
+    m64 = (1 << 64) - 1
+    clz = lambda x: 64 - x.bit_length()
+    hl = (hi << 28) & m64
+    vl = (hl + (lo & m64)) & m64
+    vh = (hi >> 36) + (lo >> 63) + (1 if vl < hl else 0)
+    sv = vh < 0
+    ml = (0 - vl) & m64 if sv else vl
+    mh = (((~(vh & m64)) & m64) + (1 if vl == 0 else 0)) & m64 if sv else vh & m64
+    if (ml | mh) == 0:
+        return 0.0
+    p = (127 - clz(mh)) if mh else (63 - clz(ml))
+    sh = p - 52
+    shr, shl = max(sh, 0), max(-sh, 0)
+    q = (((ml >> shr) | ((mh << (64 - shr)) & m64)) & m64) if shr else ((ml << shl) & m64)
+    R = ml & ((1 << shr) - 1)
+    H = (1 << (shr - 1)) if shr else 0
+    if shr and (R > H or (R == H and (q & 1))):
+        q += 1
+    if q >> 53:
+        q >>= 1
+        p += 1
+    be = p + e + 1023
+    assert 1 <= be <= 2046
+    bits = (int(sv != neg) << 63) | (be << 52) | (q & ((1 << 52) - 1))
+    return struct.unpack('<d', struct.pack('<Q', bits))[0]
+
+
+def test_combination_rounds_once_to_nearest_even():
+    """Against exact rational rounding (Python's float of a Fraction is correctly
+    rounded): random operands, cancellation, exact ties at every shift."""
+    import random
+    rnd = random.Random(3)
+    cases = []
+    for _ in range(20000):
+        hi, lo = rnd.randint(-2 ** 46, 2 ** 46), rnd.randint(-2 ** 46, 2 ** 46)
+        cases.append((hi, lo))
+        small = rnd.randint(-2 ** 18, 2 ** 18)
+        cases.append((small, -small * 2 ** 28 + rnd.randint(-5, 5)))          # cancellation
+        cases.append((rnd.randint(2 ** 40, 2 ** 46), rnd.choice([1, -1]) * 2 ** rnd.randint(0, 40)))  # ties
+        cases.append((0, rnd.randint(-2 ** 46, 2 ** 46)))
+    for hi, lo in cases:
+        e, neg = rnd.randint(-100, 40), rnd.random() < 0.5
+        V = hi * 2 ** 28 + lo
+        ref = float(Fraction(V) * Fraction(2) ** e) * (-1 if neg else 1) if V else 0.0
+        assert _to_double(hi, lo, e, neg) == ref, (hi, lo, e, neg)
