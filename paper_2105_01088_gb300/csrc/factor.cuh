@@ -19,6 +19,8 @@ namespace sgs {
 
 // ---------------------------------------------------------------- Gauss-Jordan
 
+#define GJ_MAX_PANEL 64       // widest Gauss-Jordan panel
+
 struct GJPanelArgs {
     double* const* W;        // [batch] n x n working matrices (row-major)
     double* const* T;        // [batch] bb x n copy of the panel rows (update operand)
@@ -30,6 +32,80 @@ struct GJPanelArgs {
     double tiny;             // a pivot of magnitude <= tiny counts as singular
 };
 
+// The end of a Gauss-Jordan panel, after its columns are back in W: log |det| += the sum
+// of log |pivot_j|; the panel's row interchanges (k0 + j <-> piv_j, in order) applied to the
+// other columns of W as one permutation of the rows they touch (row rows[e] receives the old
+// row src[e]), staged through stage[0 .. cap); the update operand T (the pivot rows, panel
+// columns zeroed).
+__device__ void gj_panel_finish(const GJPanelArgs& a, double* W, int b, double* stage, int cap, const int* s_piv,
+                                const double* s_pabs, int* s_rows, int* s_src, int* s_nr, double* s_logdet,
+                                double* s_sign) {
+    const int n = a.n, k0 = a.k0, bb = a.bb;
+    if (threadIdx.x < 32) {         // log |det| += sum_j log |pivot_j|
+        double l = 0.0;
+        for (int j = threadIdx.x; j < bb; j += 32) l += log(s_pabs[j]);
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if (threadIdx.x == 0) *s_logdet += l;
+    }
+    // the panel's interchanges (k0 + j <-> piv_j, in order) on the other columns as one
+    // permutation of the rows they touch: row rows[e] receives the old row src[e]
+    __syncthreads();
+    if (threadIdx.x < 32) {         // warp 0: the list searches as ballots
+        const int lane = threadIdx.x;
+        int nr = 0;
+        for (int j = 0; j < bb; j++) {
+            const int c = k0 + j, p = s_piv[j];
+            if (p == c) continue;
+            unsigned mc = 0, mp = 0;
+            for (int e0 = 0; e0 < nr; e0 += 32) {
+                const int e = e0 + lane;
+                const int r = e < nr ? s_rows[e] : -1;
+                const unsigned bc = __ballot_sync(0xffffffffu, r == c), bp = __ballot_sync(0xffffffffu, r == p);
+                if (!mc && bc) mc = (unsigned)(e0 + __ffs(bc));       // 1 + index
+                if (!mp && bp) mp = (unsigned)(e0 + __ffs(bp));
+            }
+            int ic = (int)mc - 1, ip = (int)mp - 1;
+            if (ic < 0) { if (lane == 0) { s_rows[nr] = c; s_src[nr] = c; } ic = nr++; }
+            if (ip < 0) { if (lane == 0) { s_rows[nr] = p; s_src[nr] = p; } ip = nr++; }
+            __syncwarp();
+            if (lane == 0) {
+                const int t = s_src[ic];
+                s_src[ic] = s_src[ip];
+                s_src[ip] = t;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) *s_nr = nr;
+    }
+    __syncthreads();
+    const int nr = *s_nr;
+    if (nr > 0) {
+        // gather every touched row's new contents through the staging memory, a block of
+        // columns at a time, then scatter
+        const int qc = min(n, cap / nr);
+        for (int q0 = 0; q0 < n; q0 += qc) {
+            const int qn = min(qc, n - q0);
+            for (int x = threadIdx.x; x < nr * qn; x += blockDim.x) {
+                const int e = x / qn, q = q0 + x % qn;
+                if (q < k0 || q >= k0 + bb) stage[x] = W[(size_t)s_src[e] * n + q];
+            }
+            __syncthreads();
+            for (int x = threadIdx.x; x < nr * qn; x += blockDim.x) {
+                const int e = x / qn, q = q0 + x % qn;
+                if (q < k0 || q >= k0 + bb) W[(size_t)s_rows[e] * n + q] = stage[x];
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    double* T = a.T[b];
+    for (int e = threadIdx.x; e < bb * n; e += blockDim.x) {
+        int r = e / n, q = e % n;
+        T[(size_t)r * n + q] = (q >= k0 && q < k0 + bb) ? 0.0 : W[(size_t)(k0 + r) * n + q];
+    }
+    if (threadIdx.x == 0) { a.logdet[b] = *s_logdet; a.dsign[b] = *s_sign; }
+}
+
 __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
     extern __shared__ double sm[];
     const int ps = a.bb + 1;                   // odd row stride: column walks hit distinct banks
@@ -38,6 +114,8 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
     __shared__ double red_v[32];
     __shared__ int red_i[32];
     __shared__ double s_logdet, s_sign;
+    __shared__ int s_piv[GJ_MAX_PANEL], s_rows[2 * GJ_MAX_PANEL], s_src[2 * GJ_MAX_PANEL], s_nr;
+    __shared__ double s_pabs[GJ_MAX_PANEL], s_inv;
 
     const int b = blockIdx.x, n = a.n, k0 = a.k0, bb = a.bb;
     double* W = a.W[b];
@@ -68,33 +146,36 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
             if (threadIdx.x == 0) { atomicOr(a.err, SGS_DEV_SINGULAR); s_logdet = -INFINITY; }
             p = c;
         }
+        // rows c and p: interchanged now in the panel; on the other columns of W the panel's
+        // interchanges are applied together after the panel (nothing reads them before)
         if (p != c) {
             for (int q = threadIdx.x; q < bb; q += blockDim.x) {
                 double t = panel[c * ps + q];
                 panel[c * ps + q] = panel[p * ps + q];
                 panel[p * ps + q] = t;
             }
-            for (int q = threadIdx.x; q < n; q += blockDim.x) {
-                if (q >= k0 && q < k0 + bb) continue;
-                double t = W[(size_t)c * n + q];
-                W[(size_t)c * n + q] = W[(size_t)p * n + q];
-                W[(size_t)p * n + q] = t;
+        }
+        if (threadIdx.x == 0) { piv[c] = p; s_piv[j] = p; }
+        __syncthreads();
+        // warp 0 forms the pivot's reciprocal once (an FP64 division is many instructions on this
+        // part's FP64 pipe) and the scaled pivot row; |pivot| is kept and the logarithms are summed
+        // after the panel
+        if (threadIdx.x < 32) {
+            double pv = panel[c * ps + j];
+            const bool sing = !(mv > a.tiny);
+            if (sing) pv = 1.0;
+            double inv = 0.0;
+            if (threadIdx.x == 0) {
+                inv = 1.0 / pv;
+                s_inv = inv;
+                s_pabs[j] = sing ? 1.0 : fabs(pv);
+                s_sign *= (pv < 0.0 ? -1.0 : 1.0) * (p != c ? -1.0 : 1.0);
             }
-        }
-        if (threadIdx.x == 0) piv[c] = p;
-        __syncthreads();
-        double pv = panel[c * ps + j];
-        if (!(mv > a.tiny)) pv = 1.0;
-        if (threadIdx.x == 0) {
-            if (mv > a.tiny) s_logdet += log(fabs(pv));
-            s_sign *= (pv < 0.0 ? -1.0 : 1.0) * (p != c ? -1.0 : 1.0);
-        }
-        const double inv = 1.0 / pv;
-        for (int q = threadIdx.x; q < bb; q += blockDim.x) {
-            double v = (q == j) ? inv : panel[c * ps + q] * inv;
-            rowc[q] = v;
+            inv = __shfl_sync(0xffffffffu, inv, 0);
+            for (int q = threadIdx.x; q < bb; q += 32) rowc[q] = (q == j) ? inv : panel[c * ps + q] * inv;
         }
         __syncthreads();
+        const double inv = s_inv;
         for (int q = threadIdx.x; q < bb; q += blockDim.x) panel[c * ps + q] = rowc[q];
         for (int r = threadIdx.x; r < n; r += blockDim.x) {
             if (r == c) continue;
@@ -112,13 +193,7 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
         int r = e / bb, q = e % bb;
         W[(size_t)r * n + k0 + q] = panel[r * ps + q];
     }
-    __syncthreads();
-    double* T = a.T[b];
-    for (int e = threadIdx.x; e < bb * n; e += blockDim.x) {
-        int r = e / n, q = e % n;
-        T[(size_t)r * n + q] = (q >= k0 && q < k0 + bb) ? 0.0 : W[(size_t)(k0 + r) * n + q];
-    }
-    if (threadIdx.x == 0) { a.logdet[b] = s_logdet; a.dsign[b] = s_sign; }
+    gj_panel_finish(a, W, b, panel, n * ps, s_piv, s_pabs, s_rows, s_src, &s_nr, &s_logdet, &s_sign);
 }
 
 // Undo the row interchanges of Gauss-Jordan: inverse = X P, i.e. the column
@@ -161,6 +236,8 @@ struct PfPanelArgs {
     int bsmax;               // pack blocks are n x 4*bsmax apart (row stride 4*bs)
 };
 
+#define PF_MAX_PANEL 32       // widest Pfaffian panel (column pairs)
+
 // Columns of the antisymmetric Y are read as negated rows (coalesced); the
 // pending rank-2 updates of the panel are added on the fly.
 __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
@@ -173,7 +250,9 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
     double* rowTU = c1i + n;     // 4 x bs: T/U entries of the row being materialised
     __shared__ double red_v[32];
     __shared__ int red_i[32];
-    __shared__ double s_log, s_pr, s_pi;
+    __shared__ double s_log, s_pr, s_pi, s_ir, s_ii;
+    __shared__ double s_pvr[PF_MAX_PANEL], s_pvi[PF_MAX_PANEL];
+    __shared__ int s_pok[PF_MAX_PANEL], s_flip;
 
     const int b = blockIdx.x;
     double* Yr = a.Y[b];
@@ -187,6 +266,7 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
         s_log = (k0 == 0) ? 0.0 : a.logabs[b];
         s_pr = (k0 == 0) ? 1.0 : a.phase[2 * b];
         s_pi = (k0 == 0) ? 0.0 : a.phase[2 * b + 1];
+        s_flip = 0;
     }
 
     for (int s = 0; s < bs; s++) {
@@ -247,7 +327,7 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
             if (threadIdx.x == 0) {
                 double x = ckr[q]; ckr[q] = ckr[p]; ckr[p] = x;
                 x = cki[q]; cki[q] = cki[p]; cki[p] = x;
-                s_pr = -s_pr; s_pi = -s_pi;
+                s_flip ^= 1;      // a row/column interchange flips the sign (applied after the panel)
             }
         }
         __syncthreads();
@@ -272,22 +352,23 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
             c1r[i] = vr;
             c1i[i] = vi;
         }
-        // pivot Y[k][k+1] = -Y[k+1][k]
-        double pr = -ckr[k + 1], pi = -cki[k + 1];
-        if (!(mv > 0.0)) { pr = 1.0; pi = 0.0; }
-        const double pm2 = pr * pr + pi * pi;
+        // pivot Y[k][k+1] = -Y[k+1][k]: thread 0 forms 1/pivot once (an FP64 division is many
+        // instructions on this part's FP64 pipe) and keeps the pivot, whose logarithm and unit
+        // phase are accumulated after the panel in the same order
         if (threadIdx.x == 0) {
-            if (mv > 0.0) {
-                const double am = sqrt(pm2);
-                s_log += log(am);
-                const double ur = pr / am, ui = pi / am;
-                const double nr = s_pr * ur - s_pi * ui, ni = s_pr * ui + s_pi * ur;
-                s_pr = nr; s_pi = ni;
-            }
+            double pr = -ckr[k + 1], pi = -cki[k + 1];
+            const bool ok = mv > 0.0;
+            if (!ok) { pr = 1.0; pi = 0.0; }
+            const double pm2 = pr * pr + pi * pi;
+            s_ir = pr / pm2;
+            s_ii = -pi / pm2;
+            s_pvr[s] = pr;
+            s_pvi[s] = pi;
+            s_pok[s] = ok ? 1 : 0;
         }
         __syncthreads();
         // tau = (row k)/pivot = -(column k)/pivot, u = column k+1; zero above k+2
-        const double ir = pr / pm2, ii = -pi / pm2;   // 1/pivot
+        const double ir = s_ir, ii = s_ii;   // 1/pivot
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             double tr = 0.0, ti = 0.0, ur = 0.0, ui = 0.0;
             if (i >= k + 2) {
@@ -324,9 +405,21 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
         PBim[row + t] = ui; PBim[row + bs + t] = ur;  PBim[row + 2 * bs + t] = ti;  PBim[row + 3 * bs + t] = tr;
     }
     if (threadIdx.x == 0) {
-        a.logabs[b] = s_log;
-        a.phase[2 * b] = s_pr;
-        a.phase[2 * b + 1] = s_pi;
+        double lg = s_log, ph_r = s_pr, ph_i = s_pi;
+        for (int t = 0; t < bs; t++) {
+            if (!s_pok[t]) continue;
+            const double pr = s_pvr[t], pi = s_pvi[t];
+            const double am = sqrt(pr * pr + pi * pi);
+            lg += log(am);
+            const double ur = pr / am, ui = pi / am;
+            const double nr = ph_r * ur - ph_i * ui, ni = ph_r * ui + ph_i * ur;
+            ph_r = nr;
+            ph_i = ni;
+        }
+        if (s_flip) { ph_r = -ph_r; ph_i = -ph_i; }
+        a.logabs[b] = lg;
+        a.phase[2 * b] = ph_r;
+        a.phase[2 * b + 1] = ph_i;
     }
 }
 
