@@ -34,9 +34,10 @@
 // pattern.  The GemmBatch epilogue (beta Cin, beta2 Cin2, diag, FULL / SKEW / GJ
 // modes, pass-through of inactive batch entries) is applied as in gemm_f64.
 //
-// Kernels per batch chunk: exponents of op(A) and of op(B), slices of each (a
-// 32 x 32 tile transpose through shared memory where the operand is stored
-// K-strided), then the product kernel.  Its wide form takes a 128 x 64 output
+// Kernels per batch chunk: exponents and slices of op(A) and op(B) (one pass,
+// a warp per row, where the operand's K rows are contiguous; else an exponent
+// pass and a 32 x 32 tile transpose through shared memory), then the product
+// kernel.  Its wide form takes a 128 x 64 output
 // tile per CTA of 18 warps, one CTA per SM; its narrow form (K <= 64, the
 // delayed factorisation updates) a 128 x 32 tile per CTA of 10 warps, two CTAs
 // per SM.  In both:
@@ -203,8 +204,34 @@ __device__ __forceinline__ uint16_t oz_bf16_bits(int d) {
     return (uint16_t)(__float_as_uint((float)d) >> 16);
 }
 
-// slices of a 32 (rows) x 32 (K) tile; rows in [rows, rows_pad) are written as zeros,
-// K beyond k is left to the tensor map's zero fill
+// four digits (consecutive k) of one plane as one 8-byte word
+__device__ __forceinline__ unsigned long long oz_pack4(int d0, int d1, int d2, int d3) {
+    return (unsigned long long)oz_bf16_bits(d0) | ((unsigned long long)oz_bf16_bits(d1) << 16) |
+           ((unsigned long long)oz_bf16_bits(d2) << 32) | ((unsigned long long)oz_bf16_bits(d3) << 48);
+}
+
+// the eight planes of four consecutive k of row r starting at k (k + 3 < kp; entries at or
+// beyond o.k are zero digits, which the tensor map never reads)
+__device__ __forceinline__ void oz_store4(const OzOperand& o, int bl, int r, int k, const double (&v)[4], int E) {
+    int t[4][OZ_S];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        if (E > 0 && k + u < o.k) oz_digits(v[u], E, t[u]);
+        else {
+#pragma unroll
+            for (int i = 0; i < OZ_S; i++) t[u][i] = 0;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < OZ_S; i++) {
+        const int pl = o.interleave ? oz_plane(i) : i;
+        *reinterpret_cast<unsigned long long*>(o.slices + (((size_t)bl * OZ_S + pl) * o.rows_pad + r) * o.kp + k) =
+            oz_pack4(t[0][i], t[1][i], t[2][i], t[3][i]);
+    }
+}
+
+// slices of a strided operand, a 32 (rows) x 32 (K) tile per block (through shared memory, so
+// that both the reads and the writes are coalesced); rows in [rows, rows_pad) get zero digits
 __global__ void __launch_bounds__(256) oz_slice_kernel(OzOperand o) {
     __shared__ double tile[32][33];
     const int bl = blockIdx.z, b = o.b0 + bl;
@@ -224,22 +251,40 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(OzOperand o) {
         }
     }
     __syncthreads();
+    // thread: row rr = tid / 8, k = 4 (tid % 8) .. + 3
+    const int rr = threadIdx.x >> 3, kk = 4 * (threadIdx.x & 7), r = r0 + rr, k = k0 + kk;
+    if (r >= o.rows_pad || k >= o.kp) return;
+    const int E = r < o.rows ? o.expo[(size_t)bl * o.rows_pad + r] : 0;
+    const double v[4] = {tile[rr][kk], tile[rr][kk + 1], tile[rr][kk + 2], tile[rr][kk + 3]};
+    oz_store4(o, bl, r, k, v, E);
+}
+
+// contiguous rows (K <= 512): one warp per row takes the row into registers, reduces the
+// exponent field and writes the digits, four k per lane per step (one pass over the operand)
+__global__ void __launch_bounds__(256) oz_row_slice_kernel(OzOperand o) {
+    const int bl = blockIdx.y, b = o.b0 + bl;
+    if (!oz_active(o.active, o.active_cmp, b)) return;
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= o.rows_pad) return;
+    const double* x = o.X[b] + o.off;
+    const double* x2 = o.X2 ? o.X2[b] + o.off : nullptr;
+    double v[4][4];                      // k = 4 lane + 128 s + u, s < 4 (K <= 512)
+    int e = 0;
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-        const int rr = ty + 8 * j, r = r0 + rr, k = k0 + tx;
-        if (r >= o.rows_pad || k >= o.k) continue;
-        const int E = r < o.rows ? o.expo[(size_t)bl * o.rows_pad + r] : 0;
-        int t[OZ_S];
-        if (E > 0) oz_digits(tile[rr][tx], E, t);
-        else {
+    for (int s = 0; s < 4; s++)
 #pragma unroll
-            for (int i = 0; i < OZ_S; i++) t[i] = 0;
+        for (int u = 0; u < 4; u++) {
+            const int k = 128 * s + 4 * lane + u;
+            v[s][u] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0.0;
+            e = max(e, oz_expo_field(v[s][u]));
         }
 #pragma unroll
-        for (int i = 0; i < OZ_S; i++) {
-            const int pl = o.interleave ? oz_plane(i) : i;
-            o.slices[(((size_t)bl * OZ_S + pl) * o.rows_pad + r) * o.kp + k] = oz_bf16_bits(t[i]);
-        }
+    for (int sh = 16; sh > 0; sh >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, sh));
+    if (lane == 0 && r < o.rows) o.expo[(size_t)bl * o.rows_pad + r] = e;
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        const int k = 128 * s + 4 * lane;
+        if (k < o.kp) oz_store4(o, bl, r, k, v[s], r < o.rows ? e : 0);
     }
 }
 
@@ -618,10 +663,18 @@ inline bool make_slice_map(CUtensorMap* map, const void* base, int k, int kp, in
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-inline void oz_prepare(const OzOperand& o, int bc, cudaStream_t st) {
+// exponents and slices of one operand: long contiguous rows in one pass (a warp per row),
+// short or strided ones in two (32 x 32 tiles keep all lanes busy when K is small)
+inline bool oz_one_pass(const OzOperand& o) { return !o.strided && o.k >= 256 && o.k <= OZ_KC; }
+inline int oz_prepare(const OzOperand& o, int bc, cudaStream_t st) {
+    if (oz_one_pass(o)) {
+        oz_row_slice_kernel<<<dim3((o.rows_pad + 7) / 8, bc), 256, 0, st>>>(o);
+        return 1;
+    }
     if (o.strided) oz_expo_kernel<<<dim3((o.rows + 31) / 32, bc), 256, 0, st>>>(o);
     else oz_expo_kernel<<<dim3((o.rows + 7) / 8, bc), 256, 0, st>>>(o);
-    oz_slice_kernel<<<dim3((o.k + 31) / 32, o.rows_pad / 32, bc), 256, 0, st>>>(o);
+    oz_slice_kernel<<<dim3((o.kp + 31) / 32, o.rows_pad / 32, bc), 256, 0, st>>>(o);
+    return 2;
 }
 
 // number of output tiles of one batch entry (tile width bn)
@@ -633,7 +686,7 @@ inline int oz_tiles(const GemmBatch& g, int bn) {
     return t;
 }
 
-// launches of one product (5 per batch chunk and K chunk), for launch accounting
+// launches of one product, for launch accounting
 inline int oz_launches(const GemmBatch& g, const OzBuf& buf) {
     if (g.batch <= 0 || g.m <= 0 || g.n <= 0 || g.k <= 0 || !buf.base) return 1;
     if (g.mode == GEMM_GJ && g.k > OZ_KC) return 1;
@@ -642,7 +695,11 @@ inline int oz_launches(const GemmBatch& g, const OzBuf& buf) {
         const size_t per = oz_entry_bytes(g.m, g.n, std::min(OZ_KC, g.k - k0));
         const size_t chunk = std::min<size_t>(g.batch, buf.bytes > 8192 ? (buf.bytes - 8192) / per : 0);
         if (chunk == 0) return 1;
-        total += 5 * (int)((g.batch + chunk - 1) / chunk);
+        // per batch chunk: one slicing launch for an operand with contiguous K rows, two for a
+        // strided one, and the product
+        const int kc = std::min(OZ_KC, g.k - k0);
+        const int nl = ((!g.transA && kc >= 256) ? 1 : 2) + ((g.transB && kc >= 256) ? 1 : 2) + 1;
+        total += nl * (int)((g.batch + chunk - 1) / chunk);
     }
     return total;
 }
