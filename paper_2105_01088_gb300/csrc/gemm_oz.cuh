@@ -37,14 +37,15 @@
 // Kernels per batch chunk: exponents and slices of op(A) and op(B) (one pass,
 // a warp per row, where the operand's K rows are contiguous; else an exponent
 // pass and a 32 x 32 tile transpose through shared memory), then the product
-// kernel.  Its wide form takes a 128 x 64 output
-// tile per CTA of 18 warps, one CTA per SM; its narrow form (K <= 64, the
-// delayed factorisation updates) a 128 x 32 tile per CTA of 10 warps, two CTAs
-// per SM.  In both:
+// kernel.  The product kernel takes a 128 x 32 output tile per CTA of 10 warps
+// (256 TMEM columns, 97 KB of shared memory), so two CTAs share an SM and one's
+// epilogue overlaps the other's loads and MMAs; its MMA issue then keeps the
+// tensor pipe near its bf16 rate.  In the kernel:
 //   * one producer lane loads, per 64-element K slab, the eight B slices as one
 //     TMA box (TMA issue costs about the same per box whatever its size, so
 //     boxes are made large) and the A slices in pairs (one 32 KB box per pair of
 //     adjacent planes) through a ring, 128-byte swizzle, zero fill beyond K;
+//     the B buffer is reloaded once the previous slab's MMAs have released it;
 //   * one MMA lane issues, per A slice and K16 step, one MMA of N up to 256
 //     covering all the products of that slice (the B slices and the groups they
 //     feed are adjacent) into the eight accumulators;
@@ -73,16 +74,15 @@ namespace sgs {
 #define OZ_SLAB_A (OZ_BM * 128)
 
 // Kernel shapes: BN output columns per tile (TMEM: 8 BN columns), EPIW epilogue warps,
-// RING A-ring depth (units), BDBL double-buffered B slabs.  The wide form (64, 16, 3,
-// double) takes all of an SM; the narrow form (32, 8, 2, single) is for K <= 64 (one
-// slab: the delayed factorisation updates) and fits two CTAs per SM, so one CTA's
-// epilogue overlaps the other's loads and MMAs.
+// RING A-ring depth (units), BDBL double-buffered B slabs.  The form launched (32, 8, 2,
+// single) fits two CTAs per SM.  A 128 x 64 tile (64, 16, 3, double) takes all of an SM's
+// TMEM and shared memory; with its epilogue serialised after the main loop it measured
+// about half the throughput at K = 512, so it is not launched.
 template <int BN, int EPIW, int RING, bool BDBL> struct OzCfg {
     static constexpr int SLAB_B = BN * 128;
     static constexpr int SMEM = (BDBL ? 2 : 1) * OZ_S * SLAB_B + RING * OZ_UNIT * OZ_SLAB_A + 1024;
     static constexpr int THREADS = 32 * (EPIW + 2);
 };
-#define OZ_WIDE 64, 16, 3, true
 #define OZ_NARROW 32, 8, 2, false
 
 // device scratch of one owner (an instance, or a temporary context): slices and
@@ -707,8 +707,7 @@ inline int oz_launches(const GemmBatch& g, const OzBuf& buf) {
 // one K chunk (k <= OZ_KC) of the emulated product, in batch chunks that fit the scratch
 inline cudaError_t gemm_oz_chunk(const GemmBatch& g, const OzBuf& buf, int* err, cudaStream_t st) {
     const int kp = (int)oz_round(g.k, 8), mp = (int)oz_round(g.m, OZ_BM), np = (int)oz_round(g.n, 64);
-    const bool narrow = g.k <= OZ_KS;                    // one slab: the narrow form, two CTAs per SM
-    const int bn = narrow ? 32 : 64;
+    const int bn = 32;                                   // OZ_NARROW's tile width
     const size_t sa = (size_t)OZ_S * mp * kp * 2, sb = (size_t)OZ_S * np * kp * 2;
     const size_t per = oz_entry_bytes(g.m, g.n, g.k);
     const int chunk = (int)std::min<size_t>(g.batch, buf.bytes > 8192 ? (buf.bytes - 8192) / per : 0);
@@ -737,10 +736,7 @@ inline cudaError_t gemm_oz_chunk(const GemmBatch& g, const OzBuf& buf, int* err,
         if (!g.alpha_b && (fr == 0.5 || fr == -0.5)) {
             p.alpha_pow2 = 1; p.alpha_e = ex - 1; p.alpha_neg = g.alpha < 0.0;
         }
-        if (narrow)
-            oz_gemm_kernel<OZ_NARROW><<<dim3(tiles, bc), OzCfg<OZ_NARROW>::THREADS, OzCfg<OZ_NARROW>::SMEM, st>>>(p);
-        else
-            oz_gemm_kernel<OZ_WIDE><<<dim3(tiles, bc), OzCfg<OZ_WIDE>::THREADS, OzCfg<OZ_WIDE>::SMEM, st>>>(p);
+        oz_gemm_kernel<OZ_NARROW><<<dim3(tiles, bc), OzCfg<OZ_NARROW>::THREADS, OzCfg<OZ_NARROW>::SMEM, st>>>(p);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

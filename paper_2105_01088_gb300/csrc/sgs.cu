@@ -697,7 +697,6 @@ void set_kernel_attributes() {
         raise_smem_limit(gemm_tmap_kernel<TC_TF32>, optin);
         raise_smem_limit(gemm_tmap_kernel<TC_BF16>, optin);
         raise_smem_limit(gemm_tmap_kernel<TC_3XTF32>, optin);
-        raise_smem_limit(oz_gemm_kernel<OZ_WIDE>, optin);
         raise_smem_limit(oz_gemm_kernel<OZ_NARROW>, optin);
         cudaGetLastError();
     });
