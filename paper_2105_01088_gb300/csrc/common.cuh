@@ -34,35 +34,44 @@ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
     return cmk((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// Block-wide argmax of |v| (value, index); ties resolve to the smaller index.
+// Block-wide argmax of v (value, index); ties resolve to the smaller index.  v is a
+// magnitude (non-negative, or NaN with its sign bit clear) or the sentinel -1 of a thread
+// without candidates; the values are compared as their bit patterns, which order
+// non-negative doubles as the numbers do, in integer instructions (FP64 compares share
+// the FP64 pipe, which issues at a small fraction of the integer rate on this part).
 // red_v / red_i: shared arrays of at least blockDim.x/32 entries.
 __device__ __forceinline__ void block_argmax(double v, int idx, double* red_v, int* red_i,
                                              double& out_v, int& out_i) {
     const unsigned full = 0xffffffffu;
+    long long key = __double_as_longlong(v);
+    if (key < 0) key = -1;
     for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_down_sync(full, v, o);
-        int oi = __shfl_down_sync(full, idx, o);
-        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+        const long long ok = __shfl_down_sync(full, key, o);
+        const int oi = __shfl_down_sync(full, idx, o);
+        if (ok > key || (ok == key && oi < idx)) { key = ok; idx = oi; }
     }
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) { red_v[w] = v; red_i[w] = idx; }
+    if (lane == 0) { red_v[w] = __longlong_as_double(key); red_i[w] = idx; }
     __syncthreads();
     if (w == 0) {
         int nw = (blockDim.x + 31) >> 5;
-        v = lane < nw ? red_v[lane] : -1.0;
+        key = lane < nw ? __double_as_longlong(red_v[lane]) : -1ll;
         idx = lane < nw ? red_i[lane] : 0x7fffffff;
         for (int o = 16; o > 0; o >>= 1) {
-            double ov = __shfl_down_sync(full, v, o);
-            int oi = __shfl_down_sync(full, idx, o);
-            if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+            const long long ok = __shfl_down_sync(full, key, o);
+            const int oi = __shfl_down_sync(full, idx, o);
+            if (ok > key || (ok == key && oi < idx)) { key = ok; idx = oi; }
         }
-        if (lane == 0) { red_v[0] = v; red_i[0] = idx; }
+        if (lane == 0) { red_v[0] = key < 0 ? -1.0 : __longlong_as_double(key); red_i[0] = idx; }
     }
     __syncthreads();
     out_v = red_v[0];
     out_i = red_i[0];
     __syncthreads();
 }
+
+// the magnitude |x| as the bit pattern block_argmax compares (sign bit cleared)
+__device__ __forceinline__ long long abs_key(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll; }
 
 // Block-wide sum of doubles; red: shared array of >= 32 entries.
 __device__ __forceinline__ double block_sum(double v, double* red) {

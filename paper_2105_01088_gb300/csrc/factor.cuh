@@ -133,15 +133,15 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
 
     for (int j = 0; j < bb; j++) {
         const int c = k0 + j;
-        double best = -1.0;
+        long long best = -1;
         int bi = 0x7fffffff;
         for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
-            double v = fabs(panel[r * ps + j]);
+            const long long v = abs_key(panel[r * ps + j]);
             if (v > best) { best = v; bi = r; }
         }
         double mv;
         int p;
-        block_argmax(best, bi, red_v, red_i, mv, p);
+        block_argmax(best < 0 ? -1.0 : __longlong_as_double(best), bi, red_v, red_i, mv, p);
         if (!(mv > a.tiny)) {          // singular (or NaN): flag, keep going with p = c
             if (threadIdx.x == 0) { atomicOr(a.err, SGS_DEV_SINGULAR); s_logdet = -INFINITY; }
             p = c;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
         for (int r = threadIdx.x; r < n; r += blockDim.x) {
             if (r == c) continue;
             double f = panel[r * ps + j];
-            if (f != 0.0) {
+            if (abs_key(f) != 0) {               // an integer test: no FP64 compare
                 for (int q = 0; q < bb; q++)
                     if (q != j) panel[r * ps + q] -= f * rowc[q];
             }
@@ -238,6 +238,23 @@ struct PfPanelArgs {
 
 #define PF_MAX_PANEL 32       // widest Pfaffian panel (column pairs)
 
+// One pending rank-2 term of the panel on element (i, k): v += T[i][t] U[k][t] - U[i][t] T[k][t]
+// (complex), as four FMAs per component (FP64 issues at a small fraction of the other
+// pipes' rates on this part, so the count of FP64 instructions sets the panel's time).
+// rowTU holds row k's T and U entries: Tr, Ti, Ur, Ui at offsets 0, bs, 2 bs, 3 bs.
+__device__ __forceinline__ void pf_pending(double& vr, double& vi, double tr, double ti, double ur, double ui,
+                                           const double* rowTU, int bs, int t) {
+    const double Tkr = rowTU[t], Tki = rowTU[bs + t], Ukr = rowTU[2 * bs + t], Uki = rowTU[3 * bs + t];
+    vr = fma(tr, Ukr, vr);
+    vr = fma(-ti, Uki, vr);
+    vr = fma(-ur, Tkr, vr);
+    vr = fma(ui, Tki, vr);
+    vi = fma(tr, Uki, vi);
+    vi = fma(ti, Ukr, vi);
+    vi = fma(-ur, Tki, vi);
+    vi = fma(-ui, Tkr, vi);
+}
+
 // Columns of the antisymmetric Y are read as negated rows (coalesced); the
 // pending rank-2 updates of the panel are added on the fly.
 __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
@@ -279,26 +296,21 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
         }
         __syncthreads();
         // current column k: -Y[k][i] + sum_t (T[i][t] U[k][t] - U[i][t] T[k][t])
-        double best = -1.0;
+        long long best = -1;
         int bi = 0x7fffffff;
         for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
             double vr = -Yr[(size_t)k * n + i], vi = -Yi[(size_t)k * n + i];
-            for (int t = 0; t < s; t++) {
-                const double tr = Tr[(size_t)t * n + i], ti = Ti[(size_t)t * n + i];
-                const double ur = Ur[(size_t)t * n + i], ui = Ui[(size_t)t * n + i];
-                const double Ukr = rowTU[2 * bs + t], Uki = rowTU[3 * bs + t];
-                const double Tkr = rowTU[t], Tki = rowTU[bs + t];
-                vr += tr * Ukr - ti * Uki - (ur * Tkr - ui * Tki);
-                vi += tr * Uki + ti * Ukr - (ur * Tki + ui * Tkr);
-            }
+            for (int t = 0; t < s; t++)
+                pf_pending(vr, vi, Tr[(size_t)t * n + i], Ti[(size_t)t * n + i], Ur[(size_t)t * n + i],
+                           Ui[(size_t)t * n + i], rowTU, bs, t);
             ckr[i] = vr;
             cki[i] = vi;
-            const double m2 = vr * vr + vi * vi;
+            const long long m2 = abs_key(fma(vr, vr, vi * vi));
             if (m2 > best) { best = m2; bi = i; }
         }
         double mv;
         int p;
-        block_argmax(best, bi, red_v, red_i, mv, p);
+        block_argmax(best < 0 ? -1.0 : __longlong_as_double(best), bi, red_v, red_i, mv, p);
         if (!(mv > 0.0)) {
             if (threadIdx.x == 0) { atomicOr(a.err, SGS_DEV_PF_ZERO); s_log = -INFINITY; }
             p = k + 1;
@@ -341,14 +353,9 @@ __global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
         // current column k+1 (rows >= k+2): -Y[k+1][i] + pending
         for (int i = k + 2 + threadIdx.x; i < n; i += blockDim.x) {
             double vr = -Yr[(size_t)(k + 1) * n + i], vi = -Yi[(size_t)(k + 1) * n + i];
-            for (int t = 0; t < s; t++) {
-                const double tr = Tr[(size_t)t * n + i], ti = Ti[(size_t)t * n + i];
-                const double ur = Ur[(size_t)t * n + i], ui = Ui[(size_t)t * n + i];
-                const double Ukr = rowTU[2 * bs + t], Uki = rowTU[3 * bs + t];
-                const double Tkr = rowTU[t], Tki = rowTU[bs + t];
-                vr += tr * Ukr - ti * Uki - (ur * Tkr - ui * Tki);
-                vi += tr * Uki + ti * Ukr - (ur * Tki + ui * Tkr);
-            }
+            for (int t = 0; t < s; t++)
+                pf_pending(vr, vi, Tr[(size_t)t * n + i], Ti[(size_t)t * n + i], Ur[(size_t)t * n + i],
+                           Ui[(size_t)t * n + i], rowTU, bs, t);
             c1r[i] = vr;
             c1i[i] = vi;
         }

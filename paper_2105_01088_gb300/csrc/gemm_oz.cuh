@@ -305,44 +305,62 @@ __device__ __forceinline__ void oz_tma_load(uint32_t dst, const CUtensorMap* map
 }
 
 // The eight group sums (integers held exactly in fp32, or rounded to even integers for
-// the two lowest groups) of output column j, combined exactly:
-//   hi = sum_{G<4} v_G 2^(7 (3 - G)),  lo = sum_{G>=4} v_G 2^(7 (7 - G)),  |hi|, |lo| < 2^47,
-// the value being V = hi 2^28 + lo.
-__device__ __forceinline__ void oz_combine(const uint32_t (&u)[OZ_G][4], int j, long long& hi, long long& lo) {
-    hi = 0;
-    lo = 0;
+// the two lowest groups) of output column j, combined exactly into V = H 2^28 + L with
+// 0 <= L < 2^28: hi = sum_{G<4} v_G 2^(7 (3 - G)) and lo = sum_{G>=4} v_G 2^(7 (7 - G))
+// (|hi|, |lo| < 2^46, each a chain of 32 x 32 -> 64-bit multiply-adds), V = hi 2^28 + lo,
+// H = hi + floor(lo / 2^28), L = lo mod 2^28.
+__device__ __forceinline__ void oz_combine(const uint32_t (&u)[OZ_G][8], int j, long long& H, unsigned& L) {
+    int v[OZ_G];
 #pragma unroll
-    for (int G = 0; G < 4; G++) hi = hi * 128 + (long long)__float2int_rn(__uint_as_float(u[G][j]));
-#pragma unroll
-    for (int G = 4; G < 8; G++) lo = lo * 128 + (long long)__float2int_rn(__uint_as_float(u[G][j]));
+    for (int G = 0; G < OZ_G; G++) v[G] = __float2int_rn(__uint_as_float(u[G][j]));
+    const long long hi = (long long)v[0] * (1 << 21) + (long long)v[1] * (1 << 14) + (long long)v[2] * 128 + v[3];
+    const long long lo = (long long)v[4] * (1 << 21) + (long long)v[5] * (1 << 14) + (long long)v[6] * 128 + v[7];
+    H = hi + (lo >> 28);
+    L = (unsigned)lo & 0xFFFFFFFu;
 }
 
-// (-1)^neg V 2^e as a double, V = hi 2^28 + lo (|V| < 2^76) rounded once to 53 bits (to
-// nearest, ties to even), in 64-bit integer arithmetic without data-dependent branches (so
-// the columns of a thread interleave); results outside the normal range take scalbn
-__device__ __forceinline__ double oz_to_double(long long hi, long long lo, int e, bool neg) {
-    // V as a two's complement pair (vh, vl)
-    const unsigned long long hl = (unsigned long long)hi << 28;
-    const unsigned long long vl = hl + (unsigned long long)lo;
-    const long long vh = (hi >> 36) + (lo >> 63) + (vl < hl ? 1ll : 0ll);
-    const bool sv = vh < 0;
-    // |V| = (mh, ml), mh < 2^12
-    const unsigned long long ml = sv ? 0ull - vl : vl;
-    const unsigned long long mh = sv ? ~(unsigned long long)vh + (vl == 0ull ? 1ull : 0ull) : (unsigned long long)vh;
-    const int p = mh ? 127 - __clzll((long long)mh) : 63 - __clzll((long long)ml);   // leading bit
-    const int sh = p - 52;                                                            // -52 .. 23
-    const int shr = sh > 0 ? sh : 0, shl = sh < 0 ? -sh : 0;
-    unsigned long long q = shr ? (ml >> shr) | (mh << (64 - shr)) : ml << shl;
-    const unsigned long long R = ml & ((1ull << shr) - 1ull), H = shr ? 1ull << (shr - 1) : 0ull;
-    q += (shr && (R > H || (R == H && (q & 1ull)))) ? 1ull : 0ull;
-    const bool ovf = (q >> 53) != 0ull;
-    q = ovf ? q >> 1 : q;
-    const int p2 = p + (ovf ? 1 : 0), be = p2 + e + 1023;
+// +-q 2^e2 outside the normal range, out of line: inlined, the compiler may evaluate these
+// FP64 multiplications for every element and select, and FP64 issues at a small fraction
+// of the integer rate on this part
+__device__ __noinline__ double oz_scaled(unsigned long long q, bool sgn, int e2) {
+    return scalbn(sgn ? -(double)q : (double)q, e2);
+}
+
+// (-1)^neg V 2^e as a double, V = H 2^28 + L (|H| < 2^47, 0 <= L < 2^28), rounded once to
+// 53 bits (to nearest, ties to even) in integer arithmetic, with selects rather than
+// branches except for the rare |V| < 2^28: |V| = Hm 2^28 + Lm is left-justified into one
+// 64-bit word N (bits shifted out are kept as a sticky flag), N is rounded at its bit 11,
+// and the biased exponent is added onto the rounded significand (a carry out of the
+// significand moves into the exponent by itself).  Results outside the normal range take
+// scalbn.
+__device__ __forceinline__ double oz_to_double(long long H, unsigned L, int e, bool neg) {
+    const bool sv = H < 0;
+    const unsigned long long Hm = sv ? (unsigned long long)(L ? ~H : -H) : (unsigned long long)H;
+    const unsigned Lm = sv ? ((0x10000000u - L) & 0xFFFFFFFu) : L;
+    unsigned long long N;
+    unsigned sticky;
+    int P;                                         // leading bit of |V|
+    if (Hm) {
+        const int lz = __clzll((long long)Hm);     // 17 .. 63
+        const bool right = lz < 28;                // |V| has more than 64 bits: Lm loses 28 - lz bits
+        N = (Hm << lz) | (right ? (unsigned long long)(Lm >> (28 - lz)) : (unsigned long long)Lm << (lz - 28));
+        sticky = right ? (Lm << (lz + 4)) : 0u;
+        P = 91 - lz;
+    } else {
+        const int lz = __clz((int)Lm);             // Lm = 0 gives V = 0, handled below
+        N = (unsigned long long)Lm << ((lz + 32) & 63);
+        sticky = 0u;
+        P = 31 - lz;
+    }
+    unsigned long long q = N >> 11;
+    const unsigned rest = (unsigned)(N & 0x3FFull) | sticky;
+    q += ((N >> 10) & 1ull) & ((rest != 0u ? 1ull : 0ull) | (q & 1ull));
+    const int be = P + e + 1023;
     const bool sgn = sv != neg;
-    double r = __longlong_as_double((long long)(((unsigned long long)sgn << 63) | ((unsigned long long)be << 52) |
-                                                (q & 0xFFFFFFFFFFFFFull)));
-    if (be < 1 || be > 2046) r = scalbn(sgn ? -(double)q : (double)q, p2 - 52 + e);
-    return (ml | mh) ? r : 0.0;
+    double r = __longlong_as_double((long long)((((unsigned long long)sgn) << 63) +
+                                                ((unsigned long long)(be - 1) << 52) + q));
+    if (be < 1 || be > 2045) r = oz_scaled(q, sgn, P - 52 + e);
+    return (Hm | Lm) ? r : 0.0;
 }
 
 template <int BN, int EPIW, int RING, bool BDBL>
@@ -564,32 +582,36 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
             }
             const double alpha = g.alpha * (g.alpha_b ? g.alpha_b[b] : 1.0);
             constexpr int PCOLS = BN / (EPIW / 4);                 // columns per warp
+            static_assert(PCOLS % 8 == 0, "eight-column TMEM loads");
             const int lq = warp & 3, part = warp >> 2;          // lane quarter, column part
             const int rr0 = lq * 32 + lane, row = m0 + rr0;
             const int er = (active && row < g.m) ? p.ea[(size_t)bl * p.m_pad + row] : 0;
             const int ae = p.alpha_pow2 ? p.alpha_e : 0;
             const bool an = p.alpha_pow2 && p.alpha_neg;
             if (nslab > 0) {
+                // eight columns per pass: one 8-column TMEM load per group, then eight independent
+                // combinations
 #pragma unroll 1
-                for (int cb = part * (PCOLS / 4); cb < (part + 1) * (PCOLS / 4); cb++) {
-                    uint32_t u[OZ_G][4];
+                for (int cb = part * (PCOLS / 8); cb < (part + 1) * (PCOLS / 8); cb++) {
+                    uint32_t u[OZ_G][8];
 #pragma unroll
                     for (int G = 0; G < OZ_G; G++) {
-                        const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(G * BN + cb * 4);
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                                     : "=r"(u[G][0]), "=r"(u[G][1]), "=r"(u[G][2]), "=r"(u[G][3])
+                        const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(G * BN + cb * 8);
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(u[G][0]), "=r"(u[G][1]), "=r"(u[G][2]), "=r"(u[G][3]),
+                                       "=r"(u[G][4]), "=r"(u[G][5]), "=r"(u[G][6]), "=r"(u[G][7])
                                      : "r"(ta));
                     }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        const int c = cb * 4 + j, fc = col_e[c];
+                    for (int j = 0; j < 8; j++) {
+                        const int c = cb * 8 + j, fc = col_e[c];
                         double v = 0.0;
                         if (er > 0 && fc > 0) {
-                            long long hi, lo;
-                            oz_combine(u, j, hi, lo);
-                            v = oz_to_double(hi, lo, er + fc - 2107 + ae, an);
-                            if (!p.alpha_pow2) v *= alpha;
+                            long long H;
+                            unsigned L;
+                            oz_combine(u, j, H, L);
+                            v = oz_to_double(H, L, er + fc - 2107 + ae, an);
                         }
                         tile[rr0 * TS + c] = v;
                     }
@@ -598,24 +620,59 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
             if (cin_async) asm volatile("cp.async.wait_all;" ::: "memory");
             asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
             const bool scale_cin = active && g.beta != 1.0;          // beta = 1 (the in-place updates): no product
-#pragma unroll 4
-            for (int q = 0; q < PER; q++) {
-                const int e = tid + NE * q, rr = e / BN, cc = e % BN;
-                const int r = m0 + rr, c = n0 + cc;
-                if (r >= g.m || c >= g.n || (skew && r < c)) continue;
-                double v = 0.0;
-                if (use_cin && !(active && gj && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b)) {
-                    v = cin_async ? cin_s[rr * BN + cc] : Cinb[(long long)r * g.ldcin + c];
-                    if (scale_cin) v *= g.beta;
-                }
-                if (active) {
-                    if (Cin2b) v = fma(g.beta2, Cin2b[(long long)r * g.ldcin + c], v);
-                    v += tile[rr * TS + cc];
-                    if (r == c) v += g.diag;
-                }
+            const bool keep_tile = skew || (active && g.diag != 0.0);
+            // an element's final value: kept in the tile for the mirrored block and the diagonal,
+            // stored unless its column is one of the Gauss-Jordan panel's
+            auto emit = [&](int rr, int cc, int r, int c, double v) {
                 if (skew && r == c) v = 0.0;
-                tile[rr * TS + cc] = v;            // kept for the mirrored block
+                if (keep_tile) tile[rr * TS + cc] = v;
                 if (!gj || c < g.gj_k0 || c >= g.gj_k0 + g.gj_b) Cb[(long long)r * g.ldc + c] = v;
+            };
+            // The common forms get loops of their own, so that no FP64 instruction is issued where
+            // none is needed (FP64 issues at a small fraction of the integer rate on this part):
+            // the plain product, and the in-place update C = Cin + A B.
+            if (active && p.alpha_pow2 && !Cin2b && !use_cin) {
+#pragma unroll 4
+                for (int q = 0; q < PER; q++) {
+                    const int e = tid + NE * q, rr = e / BN, cc = e % BN, r = m0 + rr, c = n0 + cc;
+                    if (r >= g.m || c >= g.n || (skew && r < c)) continue;
+                    emit(rr, cc, r, c, tile[rr * TS + cc]);
+                }
+            } else if (active && p.alpha_pow2 && !Cin2b && use_cin && !scale_cin && cin_async) {
+#pragma unroll 4
+                for (int q = 0; q < PER; q++) {
+                    const int e = tid + NE * q, rr = e / BN, cc = e % BN, r = m0 + rr, c = n0 + cc;
+                    if (r >= g.m || c >= g.n || (skew && r < c)) continue;
+                    const double t = tile[rr * TS + cc];
+                    const bool gj_row = gj && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b;
+                    emit(rr, cc, r, c, gj_row ? t : cin_s[rr * BN + cc] + t);
+                }
+            } else {
+#pragma unroll 4
+                for (int q = 0; q < PER; q++) {
+                    const int e = tid + NE * q, rr = e / BN, cc = e % BN, r = m0 + rr, c = n0 + cc;
+                    if (r >= g.m || c >= g.n || (skew && r < c)) continue;
+                    double v = 0.0;
+                    if (use_cin && !(active && gj && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b)) {
+                        v = cin_async ? cin_s[rr * BN + cc] : Cinb[(long long)r * g.ldcin + c];
+                        if (scale_cin) v *= g.beta;
+                    }
+                    if (active) {
+                        if (Cin2b) v = fma(g.beta2, Cin2b[(long long)r * g.ldcin + c], v);
+                        double t = tile[rr * TS + cc];
+                        if (!p.alpha_pow2) t *= alpha;
+                        v += t;
+                    }
+                    emit(rr, cc, r, c, v);
+                }
+            }
+            if (active && g.diag != 0.0 && !skew) {
+                // the diagonal term, added to the stored values of the tile's diagonal elements
+                asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
+                const int c = n0 + tid, rr = c - m0;
+                if (tid < BN && rr >= 0 && rr < OZ_BM && c < g.m && c < g.n &&
+                    (!gj || c < g.gj_k0 || c >= g.gj_k0 + g.gj_b))
+                    Cb[(long long)c * g.ldc + c] = tile[rr * TS + tid] + g.diag;
             }
             if (skew) {
                 // mirrored block: C[c][r] = -C[r][c] below the diagonal, rows of the mirror coalesced

@@ -101,39 +101,48 @@ def test_scheme_error_against_exact_product():
 
 def _to_double(hi, lo, e, neg):
     """The combination's rounding of V = hi 2^28 + lo (|hi|, |lo| < 2^47) to a double
-    times 2^e, in the 64-bit word arithmetic the CUDA kernel uses (two's complement
-    pair, leading-bit search, shift with round to nearest even, exponent assembly)."""
+    times 2^e, in the integer word arithmetic the CUDA kernel uses: V = H 2^28 + L with
+    0 <= L < 2^28, |V| as (Hm, Lm), left-justified into a 64-bit word N with the bits
+    shifted out kept as a sticky flag, N rounded at its bit 11, and the biased exponent
+    added onto the rounded significand."""
     import struct
-    m64 = (1 << 64) - 1
-    clz = lambda x: 64 - x.bit_length()
-    hl = (hi << 28) & m64
-    vl = (hl + (lo & m64)) & m64
-    vh = (hi >> 36) + (lo >> 63) + (1 if vl < hl else 0)
-    sv = vh < 0
-    ml = (0 - vl) & m64 if sv else vl
-    mh = (((~(vh & m64)) & m64) + (1 if vl == 0 else 0)) & m64 if sv else vh & m64
-    if (ml | mh) == 0:
+    m64, m32 = (1 << 64) - 1, (1 << 32) - 1
+    clz64 = lambda x: 64 - x.bit_length()
+    clz32 = lambda x: 32 - x.bit_length()
+    H, L = hi + (lo >> 28), lo & 0xFFFFFFF
+    assert H * 2 ** 28 + L == hi * 2 ** 28 + lo and 0 <= L < 2 ** 28
+    sv = H < 0
+    Hm = ((~H) if L else -H) if sv else H
+    Lm = ((0x10000000 - L) & 0xFFFFFFF) if sv else L
+    assert Hm >= 0 and Hm * 2 ** 28 + Lm == abs(H * 2 ** 28 + L)
+    if Hm:
+        lz = clz64(Hm)
+        right = lz < 28
+        N = ((Hm << lz) & m64) | ((Lm >> (28 - lz)) if right else (Lm << (lz - 28)))
+        sticky = ((Lm << (lz + 4)) & m32) if right else 0
+        P = 91 - lz
+    else:
+        lz = clz32(Lm)
+        N = (Lm << ((lz + 32) & 63)) & m64
+        sticky = 0
+        P = 31 - lz
+    if (Hm | Lm) == 0:
         return 0.0
-    p = (127 - clz(mh)) if mh else (63 - clz(ml))
-    sh = p - 52
-    shr, shl = max(sh, 0), max(-sh, 0)
-    q = (((ml >> shr) | ((mh << (64 - shr)) & m64)) & m64) if shr else ((ml << shl) & m64)
-    R = ml & ((1 << shr) - 1)
-    H = (1 << (shr - 1)) if shr else 0
-    if shr and (R > H or (R == H and (q & 1))):
-        q += 1
-    if q >> 53:
-        q >>= 1
-        p += 1
-    be = p + e + 1023
-    assert 1 <= be <= 2046
-    bits = (int(sv != neg) << 63) | (be << 52) | (q & ((1 << 52) - 1))
+    assert N >> 63 == 1
+    q = N >> 11
+    rest = (N & 0x3FF) | sticky
+    q += ((N >> 10) & 1) & ((1 if rest else 0) | (q & 1))
+    be = P + e + 1023
+    assert 1 <= be <= 2045
+    sgn = int(sv != neg)
+    bits = (sgn << 63) + ((be - 1) << 52) + q
     return struct.unpack('<d', struct.pack('<Q', bits))[0]
 
 
 def test_combination_rounds_once_to_nearest_even():
     """Against exact rational rounding (Python's float of a Fraction is correctly
-    rounded): random operands, cancellation, exact ties at every shift."""
+    rounded): random operands, cancellation, exact ties at every shift, every length of
+    the high word (both justifications of the 64-bit word, both signs)."""
     import random
     rnd = random.Random(3)
     cases = []
@@ -144,6 +153,15 @@ def test_combination_rounds_once_to_nearest_even():
         cases.append((small, -small * 2 ** 28 + rnd.randint(-5, 5)))          # cancellation
         cases.append((rnd.randint(2 ** 40, 2 ** 46), rnd.choice([1, -1]) * 2 ** rnd.randint(0, 40)))  # ties
         cases.append((0, rnd.randint(-2 ** 46, 2 ** 46)))
+    for bits in range(1, 47):               # every length of H, with ties and near-ties in L
+        for _ in range(40):
+            H = rnd.randint(2 ** (bits - 1), 2 ** bits - 1) * rnd.choice([1, -1])
+            drop = max(bits + 28 - 53, 0)   # bits of |V| below the rounding point
+            L = rnd.randint(0, 2 ** 28 - 1)
+            if drop and rnd.random() < 0.5:
+                L = (L >> drop << drop) | (1 << (drop - 1)) | rnd.choice([0, 0, 1])
+            cases.append((H, L))
+            cases.append((H, -L))
     for hi, lo in cases:
         e, neg = rnd.randint(-100, 40), rnd.random() < 0.5
         V = hi * 2 ** 28 + lo

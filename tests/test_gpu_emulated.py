@@ -85,6 +85,30 @@ def test_epilogue_terms_and_batch_chunks(pkg):
     assert np.array_equal(C1, C2)
 
 
+EPILOGUES = [(1.0, None, 0.0), (1.0, None, 0.5), (-0.5, None, 0.0), (1.0, 1.0, 0.0), (1.0, 1.0, 0.5),
+             (-0.5, 1.0, 0.25), (4.0, 0.75, 0.0), (3.0, 1.0, -1.5)]
+
+
+@pytest.mark.parametrize("alpha,beta,diag", EPILOGUES)
+def test_epilogue_forms(pkg, alpha, beta, diag):
+    """Each form of the store pass (the plain product, the in-place update C = Cin + A B,
+    the general one), with alpha a power of two or not and with and without the diagonal
+    term, on ragged tiles of a rectangular product."""
+    rng = np.random.default_rng(int(abs(alpha) * 100 + (beta or 0) * 10 + diag * 4 + 50))
+    batch, m, n, k = 2, 150, 100, 40
+    A = rng.standard_normal((batch, m, k))
+    B = rng.standard_normal((batch, k, n))
+    Cin = None if beta is None else rng.standard_normal((batch, m, n))
+    C = pkg.batched_gemm(A, B, Cin=Cin, alpha=alpha, beta=beta or 0.0, diag=diag)
+    ref = alpha * _exact(A, B) + diag * np.eye(m, n)
+    bound = 4 * U * (abs(alpha) * (np.abs(A) @ np.abs(B)) + abs(diag) * np.eye(m, n))
+    if Cin is not None:
+        ref = ref + beta * Cin.astype(np.longdouble)
+        bound = bound + 4 * U * beta * np.abs(Cin)
+    err = np.abs(C.astype(np.longdouble) - ref).astype(np.float64)
+    assert np.all(err <= bound), (err / np.maximum(bound, 1e-300)).max()
+
+
 def test_antisymmetric_mode(pkg):
     rng = np.random.default_rng(9)
     batch, n = 2, 200
@@ -104,6 +128,12 @@ def test_antisymmetric_mode(pkg):
     assert np.all(err[:, low] <= bound[:, low])
     assert np.array_equal(C, -np.swapaxes(C, 1, 2))
     assert np.all(np.diagonal(C, axis1=1, axis2=2) == 0.0)
+    # without Cin (the plain product's store pass)
+    C0 = pkg.batched_gemm(A, G, mode=1)
+    err0 = np.abs(C0.astype(np.longdouble) - _exact(A, G)).astype(np.float64)
+    assert np.all(err0[:, low] <= 4 * U * (np.abs(A) @ np.abs(G))[:, low])
+    assert np.array_equal(C0, -np.swapaxes(C0, 1, 2))
+    assert np.all(np.diagonal(C0, axis1=1, axis2=2) == 0.0)
 
 
 def test_gauss_jordan_mode_matches_native_semantics(pkg):
