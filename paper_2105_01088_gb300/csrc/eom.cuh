@@ -6,6 +6,7 @@
 // and Delta F Delta = Gamma F Gamma comes from a per-state product; for beta !=
 // mu the pair (a, b) = (min, max) supplies Delta^{a,b} (receiver b) or its
 // complex conjugate Delta^{b,a} (receiver a), and likewise F, [Delta, F], Q.
+// The sum over beta runs in the order the two kernels below give it.
 #pragma once
 #include "common.cuh"
 #include "pair.cuh"
@@ -15,26 +16,115 @@ namespace sgs {
 // R: arithmetic type of the assembly.  The FP64 form assembles in double; the mixed
 // forms, whose dense products already carry tensor-core rounding, assemble in float
 // (FP64 arithmetic is slow on this part and the assembly would otherwise be bound by it).
+//
+// Every beta != mu term is linear in the pair's S^{-1}, Im Delta, Qr and Qi, so with the
+// per-(mu, beta) weights
+//   w0 = -4 a1x, w1 = -2 sgn a1y, w2 = 2 a2x, w3 = -2 sgn a2y, w4 = -4 a3x, w5 = -2 sgn a3y
+// (a_jx, a_jy = co[2j - 2], co[2j - 1]; sgn = -1 where mu is the pair's first state) the
+// sum over beta splits into
+//   D = sum_beta (w2 Qr + w3 Qi + w4 S^{-1} + w5 Im)          (elementwise)
+//   T = sum_beta (w0 S^{-1} + w1 Im)                          (elementwise)
+// and the beta != mu part of dGamma_kl is D_kl + A_kl sum_beta w2 - sum_q T[k][c_q] a_q (over
+// row l of A) - sum_q a_q T[c_q][l] (over row k of A), plus, on the rows and columns of the
+// impurity modes, the terms of the pairs' F_imp.
+// eom_pairs_kernel forms D (into dGamma) and T, six FMAs per pair and element;
+// eom_finish_kernel adds the sparse part, the beta = mu term and the impurity terms.
+
+// weights w0..w5 of one (mu, beta != mu) and the pair index, into shared memory
 template <typename R>
-__global__ void __launch_bounds__(256) eom_kernel(InstDev d, const double* si, const double* imd,
-                                                  const double* qr, const double* qi, const double* fimp,
-                                                  const double* fimp_state, const double* gfg,
-                                                  const double* coef, const int* pair_index, double* dgamma) {
+__device__ __forceinline__ void eom_weights(const InstDev& d, const double* coef, const int* pair_index, int mu,
+                                            R* sw, int* sp) {
+    const int M = d.M;
+    for (int be = threadIdx.x; be < M; be += blockDim.x) {
+        if (be == mu) { sp[be] = -1; continue; }
+        const int p = pair_index[mu * M + be];
+        const double sgn = (d.pa[p] == mu) ? -1.0 : 1.0;     // receiver a: complex conjugate
+        const double* co = coef + (size_t)(mu * M + be) * 6;
+        sw[6 * be + 0] = (R)(-4.0 * co[0]);
+        sw[6 * be + 1] = (R)(-2.0 * sgn * co[1]);
+        sw[6 * be + 2] = (R)(2.0 * co[2]);
+        sw[6 * be + 3] = (R)(-2.0 * sgn * co[3]);
+        sw[6 * be + 4] = (R)(-4.0 * co[4]);
+        sw[6 * be + 5] = (R)(-2.0 * sgn * co[5]);
+        sp[be] = p;
+    }
+}
+
+// dynamic shared memory of both assembly kernels: M x 6 weights and M pair indices
+template <typename R> inline size_t eom_smem(int M) { return (size_t)M * 6 * sizeof(R) + (size_t)M * sizeof(int); }
+
+template <typename R>
+__global__ void __launch_bounds__(256) eom_pairs_kernel(InstDev d, const double* si, const double* imd,
+                                                        const double* qr, const double* qi, const double* coef,
+                                                        const int* pair_index, double* tsum, double* dgamma) {
+    extern __shared__ double eom_sraw[];
+    const int mu = blockIdx.y, M = d.M;
+    R* sw = reinterpret_cast<R*>(eom_sraw);
+    int* sp = reinterpret_cast<int*>(sw + 6 * M);
+    eom_weights<R>(d, coef, pair_index, mu, sw, sp);
+    __syncthreads();
+    const size_t N = nn(d);
+    double* T = tsum + (size_t)mu * N;
+    double* out = dgamma + (size_t)mu * N;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+        R t = 0, acc = 0;
+        for (int be = 0; be < M; be++) {
+            const int p = sp[be];
+            if (p < 0) continue;
+            const size_t o = (size_t)p * N + e;
+            const R sv = (R)si[o], iv = (R)imd[o], qrv = (R)qr[o], qiv = (R)qi[o];
+            const R* w = sw + 6 * be;
+            t = fma(w[0], sv, t);
+            t = fma(w[1], iv, t);
+            acc = fma(w[2], qrv, acc);
+            acc = fma(w[3], qiv, acc);
+            acc = fma(w[4], sv, acc);
+            acc = fma(w[5], iv, acc);
+        }
+        T[e] = (double)t;
+        out[e] = (double)acc;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double* si, const double* imd,
+                                                         const double* fimp, const double* fimp_state,
+                                                         const double* gfg, const double* coef, const int* pair_index,
+                                                         const double* tsum, double* dgamma) {
+    extern __shared__ double eom_sraw[];
+    __shared__ R s_w2;
     const int mu = blockIdx.y;
     const int n = d.n, ni = d.nimp, M = d.M;
-    const double* gm = d.gamma + (size_t)mu * nn(d);
+    R* sw = reinterpret_cast<R*>(eom_sraw);
+    int* sp = reinterpret_cast<int*>(sw + 6 * M);
+    eom_weights<R>(d, coef, pair_index, mu, sw, sp);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R w = 0;
+        for (int be = 0; be < M; be++)
+            if (sp[be] >= 0) w += sw[6 * be + 2];
+        s_w2 = w;
+    }
+    __syncthreads();
+    const size_t N = nn(d);
+    const double* gm = d.gamma + (size_t)mu * N;
     const double* fs = fimp_state + (size_t)mu * ni * ni;
-    const double* gfgm = gfg + (size_t)mu * nn(d);
-    double* out = dgamma + (size_t)mu * nn(d);
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn(d); e += (size_t)gridDim.x * blockDim.x) {
+    const double* gfgm = gfg + (size_t)mu * N;
+    const double* T = tsum + (size_t)mu * N;
+    double* out = dgamma + (size_t)mu * N;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(e / n), l = (int)(e % n);
         const int sk = d.slot[k], sl = d.slot[l];
         // A_kl (row k of the CSR)
         R akl = 0;
         for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++)
             if (d.a_col[q] == l) akl = (R)d.a_val[q];
-        R acc = 0;
-        {   // beta = mu
+        R acc = (R)out[e];
+        acc = fma(akl, s_w2, acc);
+        // the pairs' commutator terms against A: -(T A^T)_kl - (A T)_kl
+        for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) acc = fma(-(R)T[(size_t)k * n + d.a_col[q]], (R)d.a_val[q], acc);
+        for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) acc = fma(-(R)d.a_val[q], (R)T[(size_t)d.a_col[q] * n + l], acc);
+        {   // beta = mu: Delta = Gamma_mu, Delta F Delta = Gamma F Gamma
             const double* co = coef + (size_t)(mu * M + mu) * 6;
             const R g = (R)gm[e];
             const R f = akl + ((sk >= 0 && sl >= 0) ? (R)fs[sk * ni + sl] : (R)0);
@@ -45,53 +135,37 @@ __global__ void __launch_bounds__(256) eom_kernel(InstDev d, const double* si, c
             if (sk >= 0) for (int m = 0; m < ni; m++) fg += (R)fs[sk * ni + m] * (R)gm[(size_t)d.imp[m] * n + l];
             acc += (R)2 * ((R)co[0] * (gf - fg) + (R)co[2] * ((R)gfgm[e] + f) + (R)co[4] * g);
         }
-        for (int be = 0; be < M; be++) {
-            if (be == mu) continue;
-            const int p = pair_index[mu * M + be];
-            const R sgn = (d.pa[p] == mu) ? (R)-1 : (R)1;    // receiver a: complex conjugate
-            const double* s = si + (size_t)p * nn(d);
-            const double* im = imd + (size_t)p * nn(d);
-            const double* fp = fimp + (size_t)p * ni * ni * 2;
-            // Delta = -2 S^{-1} + i sgn Im
-            auto dre = [&](int r, int c) -> R { return (R)-2 * (R)s[(size_t)r * n + c]; };
-            auto dim = [&](int r, int c) -> R { return sgn * (R)im[(size_t)r * n + c]; };
-            const R Dx = dre(k, l), Dy = dim(k, l);
-            R Fx = akl, Fy = 0;
-            if (sk >= 0 && sl >= 0) { Fx += (R)fp[2 * (sk * ni + sl)]; Fy += sgn * (R)fp[2 * (sk * ni + sl) + 1]; }
-            // C = Delta F - F Delta; the sparse (quadratic) part sums S^{-1} and Im against A
-            // first and scales by -2 and sgn once
-            R ss = 0, si_ = 0;
-            for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) {
-                const R a = (R)d.a_val[q];
-                ss -= (R)s[(size_t)k * n + d.a_col[q]] * a;
-                si_ -= (R)im[(size_t)k * n + d.a_col[q]] * a;
-            }
-            for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) {
-                const R a = (R)d.a_val[q];
-                ss -= a * (R)s[(size_t)d.a_col[q] * n + l];
-                si_ -= a * (R)im[(size_t)d.a_col[q] * n + l];
-            }
-            R dfx = (R)-2 * ss, dfy = sgn * si_, fdx = 0, fdy = 0;
-            if (sl >= 0)
-                for (int m = 0; m < ni; m++) {
-                    const R ax = dre(k, d.imp[m]), ay = dim(k, d.imp[m]);
-                    const R bx = (R)fp[2 * (m * ni + sl)], by = sgn * (R)fp[2 * (m * ni + sl) + 1];
-                    dfx += ax * bx - ay * by;
-                    dfy += ax * by + ay * bx;
+        if (sk >= 0 || sl >= 0) {
+            // rows and columns of the impurity modes: the pairs' F_imp terms of [Delta, F] and Q + F
+            for (int be = 0; be < M; be++) {
+                const int p = sp[be];
+                if (p < 0) continue;
+                const R sgn = (d.pa[p] == mu) ? (R)-1 : (R)1;
+                const double* s = si + (size_t)p * N;
+                const double* im = imd + (size_t)p * N;
+                const double* fp = fimp + (size_t)p * ni * ni * 2;
+                R dfx = 0, dfy = 0, fdx = 0, fdy = 0, Fx = 0, Fy = 0;
+                if (sl >= 0)
+                    for (int m = 0; m < ni; m++) {
+                        const R ax = (R)-2 * (R)s[(size_t)k * n + d.imp[m]], ay = sgn * (R)im[(size_t)k * n + d.imp[m]];
+                        const R bx = (R)fp[2 * (m * ni + sl)], by = sgn * (R)fp[2 * (m * ni + sl) + 1];
+                        dfx += ax * bx - ay * by;
+                        dfy += ax * by + ay * bx;
+                    }
+                if (sk >= 0)
+                    for (int m = 0; m < ni; m++) {
+                        const R ax = (R)fp[2 * (sk * ni + m)], ay = sgn * (R)fp[2 * (sk * ni + m) + 1];
+                        const R bx = (R)-2 * (R)s[(size_t)d.imp[m] * n + l], by = sgn * (R)im[(size_t)d.imp[m] * n + l];
+                        fdx += ax * bx - ay * by;
+                        fdy += ax * by + ay * bx;
+                    }
+                if (sk >= 0 && sl >= 0) {
+                    Fx = (R)fp[2 * (sk * ni + sl)];
+                    Fy = sgn * (R)fp[2 * (sk * ni + sl) + 1];
                 }
-            if (sk >= 0)
-                for (int m = 0; m < ni; m++) {
-                    const R ax = (R)fp[2 * (sk * ni + m)], ay = sgn * (R)fp[2 * (sk * ni + m) + 1];
-                    const R bx = dre(d.imp[m], l), by = dim(d.imp[m], l);
-                    fdx += ax * bx - ay * by;
-                    fdy += ax * by + ay * bx;
-                }
-            const R Cx = dfx - fdx, Cy = dfy - fdy;
-            const R QFx = (R)qr[(size_t)p * nn(d) + e] + Fx, QFy = sgn * (R)qi[(size_t)p * nn(d) + e] + Fy;
-            const double* co = coef + (size_t)(mu * M + be) * 6;
-            // 2 Re{a1 C + a2 (Q + F) + a3 Delta}
-            acc += (R)2 * ((R)co[0] * Cx - (R)co[1] * Cy + (R)co[2] * QFx - (R)co[3] * QFy + (R)co[4] * Dx -
-                           (R)co[5] * Dy);
+                const double* co = coef + (size_t)(mu * M + be) * 6;
+                acc += (R)2 * ((R)co[0] * (dfx - fdx) - (R)co[1] * (dfy - fdy) + (R)co[2] * Fx - (R)co[3] * Fy);
+            }
         }
         out[e] = (double)acc;
     }

@@ -1032,17 +1032,22 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     // algorithmic bytes: pair_q reads Si, Im, V (twice), X, Wr and writes Qr, Qi; the EOM
     // reads Si, Im, Qr, Qi once per receiver of each pair plus Gamma, GFG and writes dGamma
     c->stage_bytes[SGS_STAGE_EOM_ASSEMBLY] += 8.0 * nn * (7.0 * P + 8.0 * P + 3.0 * M);
+    // the sums over beta: D into dGamma, T into the work buffer (free at this point)
+    const dim3 eg(grid_chunks(nn, 256, 1024), M);
     if (I.tc_kind >= 0) {
-        eom_kernel<float><<<dim3(grid_chunks(nn, 256, 1024), M), 256, 0, st>>>(d, I.si, I.imd, I.xa, I.wr, I.fimp,
-                                                                              I.fimp_state, I.s[4], I.coef,
-                                                                              I.pair_index, I.dgamma);
-        antisymmetrise_kernel<<<dim3(grid_chunks(nn, 256, 1024), M), 256, 0, st>>>(I.dgamma, n);
+        eom_pairs_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef, I.pair_index,
+                                                                     I.work, I.dgamma);
+        eom_finish_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.fimp, I.fimp_state, I.s[4],
+                                                                      I.coef, I.pair_index, I.work, I.dgamma);
+        antisymmetrise_kernel<<<eg, 256, 0, st>>>(I.dgamma, n);
         counted();
-    } else
-        eom_kernel<double><<<dim3(grid_chunks(nn, 256, 1024), M), 256, 0, st>>>(d, I.si, I.imd, I.xa, I.wr, I.fimp,
-                                                                               I.fimp_state, I.s[4], I.coef,
-                                                                               I.pair_index, I.dgamma);
-    counted();
+    } else {
+        eom_pairs_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef,
+                                                                       I.pair_index, I.work, I.dgamma);
+        eom_finish_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.fimp, I.fimp_state, I.s[4],
+                                                                        I.coef, I.pair_index, I.work, I.dgamma);
+    }
+    counted(); counted();
     return cudaGetLastError();
 }
 
