@@ -152,8 +152,9 @@ int sgs_failed_instance(const sgs_ctx* ctx);
 
 /* Autotuning of the factorisation tile shapes.  With enable = 1, sgs_admit
  * (and sgs_add_state) times the candidate panel widths of the blocked
- * Gauss-Jordan inverse (8, 16, 32, 64 columns, as shared memory allows) and
- * of the blocked complex Pfaffian (8, 16, 32) on the new instance's own pairs,
+ * Gauss-Jordan inverse (8, 16, 24, 32, 48, 64 columns, as shared memory allows)
+ * and of the blocked complex Pfaffian (8, 12, 16, 24, 32 column pairs) on the new
+ * instance's own pairs,
  * with CUDA events, and keeps the fastest.  Choices are cached per (n, rank,
  * precision) for the process, so a shape is timed once; the scratch of tuned
  * instances is sized for the widest candidate.  Widths change results only

@@ -34,10 +34,9 @@
 // pattern.  The GemmBatch epilogue (beta Cin, beta2 Cin2, diag, FULL / SKEW / GJ
 // modes, pass-through of inactive batch entries) is applied as in gemm_f64.
 //
-// Kernels per batch chunk: exponents and slices of op(A) and op(B) (one pass,
-// a warp per row, where the operand's K rows are contiguous; else an exponent
-// pass and a 32 x 32 tile transpose through shared memory), then the product
-// kernel.  The product kernel takes a 128 x 32 output tile per CTA of 10 warps
+// Kernels per batch chunk: exponents and slices of op(A) and op(B), one pass over
+// each (a warp per row where the operand's K rows are contiguous and long, else a
+// block of whole rows at a time through shared memory), then the product kernel.  The product kernel takes a 128 x 32 output tile per CTA of 10 warps
 // (256 TMEM columns, 97 KB of shared memory), so two CTAs share an SM and one's
 // epilogue overlaps the other's loads and MMAs; its MMA issue then keeps the
 // tensor pipe near its bf16 rate.  In the kernel:
@@ -139,44 +138,9 @@ __device__ __forceinline__ bool oz_active(const int* flag, int cmp, int b) {
     return flag == nullptr || flag[b] > cmp;
 }
 
-// exponent field E_r = max_k field(op(X)[r][k]) of every K-major row.  Strided operands:
-// a block of 32 x 8 threads reduces 32 rows (threads along r read coalesced, eight k
-// apart); contiguous rows: one warp per row
-__global__ void __launch_bounds__(256) oz_expo_kernel(OzOperand o) {
-    const int bl = blockIdx.y, b = o.b0 + bl;
-    if (!oz_active(o.active, o.active_cmp, b)) return;
-    const double* x = o.X[b] + o.off;
-    const double* x2 = o.X2 ? o.X2[b] + o.off : nullptr;
-    if (o.strided) {
-        __shared__ int red[8][32];
-        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-        const int r = blockIdx.x * 32 + tx;
-        int e = 0;
-        if (r < o.rows) {
-#pragma unroll 4
-            for (int k = ty; k < o.k; k += 8) e = max(e, oz_expo_field(oz_load(o, x, x2, r, k)));
-        }
-        red[ty][tx] = e;
-        __syncthreads();
-        if (ty == 0 && r < o.rows) {
-#pragma unroll
-            for (int t = 1; t < 8; t++) e = max(e, red[t][tx]);
-            o.expo[(size_t)bl * o.rows_pad + r] = e;
-        }
-    } else {
-        const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-        if (r >= o.rows) return;
-        int e = 0;
-#pragma unroll 4
-        for (int k = lane; k < o.k; k += 32) e = max(e, oz_expo_field(oz_load(o, x, x2, r, k)));
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, s));
-        if (lane == 0) o.expo[(size_t)bl * o.rows_pad + r] = e;
-    }
-}
-
-// the eight digits of X = round(v 2^(1078 - E)) (E = the row's exponent field, E > 0)
-__device__ __forceinline__ void oz_digits(double v, int E, int t[OZ_S]) {
+// X = round(v 2^(1078 - E)) (E = the row's exponent field, E > 0), |X| <= 2^56, rounded half
+// up on the magnitude, from the bit pattern
+__device__ __forceinline__ long long oz_scaled(double v, int E) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(v);
     int f = (int)((u >> 52) & 0x7ff);
     unsigned long long m = u & 0xFFFFFFFFFFFFFull;
@@ -186,77 +150,120 @@ __device__ __forceinline__ void oz_digits(double v, int E, int t[OZ_S]) {
     unsigned long long a;
     if (sh >= 0) a = m << sh;
     else if (sh <= -63) a = 0;
-    else a = (m + (1ull << (-sh - 1))) >> (-sh);  // round half up on the magnitude
-    long long X = (long long)a;
-    if (u >> 63) X = -X;
+    else a = (m + (1ull << (-sh - 1))) >> (-sh);
+    const long long X = (long long)a;
+    return (u >> 63) ? -X : X;
+}
+
+// The eight balanced base-128 digits of X (|t_0| <= 128, t_i in [-64, 63] for i >= 1) as
+// floats, most significant first.  Offset form: with Y = X + sum_{j<7} 64 2^(7 j), the
+// fields u_j = (Y >> 7 j) & 127 are the low digits plus 64 (no carries cross them) and
+// Y >> 49 (arithmetic) is the top digit; a low digit reaches float as the float 2^23 + u_j
+// (built by OR-ing u_j into the pattern of 2^23) less 2^23 + 64, an exact FP32 subtraction.
+// Each digit has at most 8 significant bits, so a float's high half is its exact bf16.
+__device__ __forceinline__ void oz_digit_floats(double v, int E, float f[OZ_S]) {
+    const long long Y = oz_scaled(v, E) + 0x1020408102040ll;
+    f[0] = (float)(int)(Y >> 49);
 #pragma unroll
-    for (int i = OZ_S - 1; i >= 1; --i) {
-        int d = (int)(X & 127);
-        d = d >= 64 ? d - 128 : d;                // balanced digit in [-64, 63]
-        t[i] = d;
-        X = (X - d) >> 7;                         // exact: X - d is a multiple of 128
+    for (int i = 1; i < OZ_S; i++) {
+        const unsigned u = (unsigned)(Y >> (7 * (OZ_S - 1 - i))) & 127u;
+        f[i] = __uint_as_float(0x4B000000u | u) - 8388672.0f;
     }
-    t[0] = (int)X;                                // |t_0| <= 128
-}
-
-__device__ __forceinline__ uint16_t oz_bf16_bits(int d) {
-    // d has at most 8 significant bits, so the float's top half is the exact bf16
-    return (uint16_t)(__float_as_uint((float)d) >> 16);
-}
-
-// four digits (consecutive k) of one plane as one 8-byte word
-__device__ __forceinline__ unsigned long long oz_pack4(int d0, int d1, int d2, int d3) {
-    return (unsigned long long)oz_bf16_bits(d0) | ((unsigned long long)oz_bf16_bits(d1) << 16) |
-           ((unsigned long long)oz_bf16_bits(d2) << 32) | ((unsigned long long)oz_bf16_bits(d3) << 48);
 }
 
 // the eight planes of four consecutive k of row r starting at k (k + 3 < kp; entries at or
-// beyond o.k are zero digits, which the tensor map never reads)
+// beyond o.k are zero digits, which the tensor map never reads): per plane one 8-byte word
+// of four bf16, the high halves of the digits' floats
 __device__ __forceinline__ void oz_store4(const OzOperand& o, int bl, int r, int k, const double (&v)[4], int E) {
-    int t[4][OZ_S];
+    float f[4][OZ_S];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-        if (E > 0 && k + u < o.k) oz_digits(v[u], E, t[u]);
+        if (E > 0 && k + u < o.k) oz_digit_floats(v[u], E, f[u]);
         else {
 #pragma unroll
-            for (int i = 0; i < OZ_S; i++) t[u][i] = 0;
+            for (int i = 0; i < OZ_S; i++) f[u][i] = 0.0f;
         }
     }
 #pragma unroll
     for (int i = 0; i < OZ_S; i++) {
         const int pl = o.interleave ? oz_plane(i) : i;
+        const unsigned lo = __byte_perm(__float_as_uint(f[0][i]), __float_as_uint(f[1][i]), 0x7632);
+        const unsigned hi = __byte_perm(__float_as_uint(f[2][i]), __float_as_uint(f[3][i]), 0x7632);
         *reinterpret_cast<unsigned long long*>(o.slices + (((size_t)bl * OZ_S + pl) * o.rows_pad + r) * o.kp + k) =
-            oz_pack4(t[0][i], t[1][i], t[2][i], t[3][i]);
+            (unsigned long long)lo | ((unsigned long long)hi << 32);
     }
 }
 
-// slices of a strided operand, a 32 (rows) x 32 (K) tile per block (through shared memory, so
-// that both the reads and the writes are coalesced); rows in [rows, rows_pad) get zero digits
-__global__ void __launch_bounds__(256) oz_slice_kernel(OzOperand o) {
-    __shared__ double tile[32][33];
-    const int bl = blockIdx.z, b = o.b0 + bl;
+// Rows of a block of the one-pass slicer: rb K-major rows of kp doubles in shared memory
+// (at most OZ_BLK_BYTES), rb a power of two in 16 .. 128
+#define OZ_BLK_BYTES (68 * 1024)
+__host__ __device__ __forceinline__ int oz_block_rows(int kp) {
+    int rb = 128;
+    while (rb > 16 && (size_t)rb * (kp + 1) * 8 > OZ_BLK_BYTES) rb >>= 1;
+    return rb;
+}
+
+// Slices of an operand whose K-major rows are strided, or contiguous and short (K <= 512):
+// a block takes rb rows whole into shared memory (loads coalesced along r for a strided
+// operand, along k for a contiguous one), reduces every row's exponent field there and writes
+// the digits, one pass over the operand; rows in [rows, rows_pad) get zero digits
+__global__ void __launch_bounds__(256) oz_block_slice_kernel(OzOperand o) {
+    extern __shared__ double oz_blk[];
+    __shared__ int s_e[128];
+    const int bl = blockIdx.y, b = o.b0 + bl;
     if (!oz_active(o.active, o.active_cmp, b)) return;
     const double* x = o.X[b] + o.off;
     const double* x2 = o.X2 ? o.X2[b] + o.off : nullptr;
-    const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        if (o.strided) {
-            const int k = k0 + ty + 8 * j, r = r0 + tx;
-            tile[tx][ty + 8 * j] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0.0;
-        } else {
-            const int r = r0 + ty + 8 * j, k = k0 + tx;
-            tile[ty + 8 * j][tx] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0.0;
+    const int kp = o.kp, ts = kp + 1, rb = oz_block_rows(kp), r0 = blockIdx.x * rb;
+    const int total = rb * kp;
+    if (o.strided) {
+        // element idx: k = idx / rb, row idx % rb (rb consecutive doubles of one k)
+        const int sh = __ffs(rb) - 1;
+#pragma unroll 8
+        for (int idx = threadIdx.x; idx < total; idx += 256) {
+            const int k = idx >> sh, rr = idx & (rb - 1), r = r0 + rr;
+            oz_blk[rr * ts + k] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0.0;
+        }
+    } else {
+        // element idx: row idx / kp, k = idx % kp, stepped without divisions
+        const int dr = 256 / kp, dk = 256 - dr * kp;
+        int rr = threadIdx.x / kp, k = threadIdx.x - rr * kp;
+#pragma unroll 8
+        for (int idx = threadIdx.x; idx < total; idx += 256) {
+            const int r = r0 + rr;
+            oz_blk[rr * ts + k] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0.0;
+            rr += dr;
+            k += dk;
+            if (k >= kp) { k -= kp; rr++; }
         }
     }
     __syncthreads();
-    // thread: row rr = tid / 8, k = 4 (tid % 8) .. + 3
-    const int rr = threadIdx.x >> 3, kk = 4 * (threadIdx.x & 7), r = r0 + rr, k = k0 + kk;
-    if (r >= o.rows_pad || k >= o.kp) return;
-    const int E = r < o.rows ? o.expo[(size_t)bl * o.rows_pad + r] : 0;
-    const double v[4] = {tile[rr][kk], tile[rr][kk + 1], tile[rr][kk + 2], tile[rr][kk + 3]};
-    oz_store4(o, bl, r, k, v, E);
+    {   // exponent fields: 256 / rb consecutive threads per row, reduced by shuffles
+        const int tpr = 256 / rb, rr = threadIdx.x / tpr, q = threadIdx.x - rr * tpr, r = r0 + rr;
+        int e = 0;
+        for (int k = q; k < o.k; k += tpr) e = max(e, oz_expo_field(oz_blk[rr * ts + k]));
+        for (int w = tpr >> 1; w > 0; w >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, w));
+        if (q == 0) {
+            s_e[rr] = r < o.rows ? e : 0;
+            if (r < o.rows) o.expo[(size_t)bl * o.rows_pad + r] = e;
+        }
+    }
+    __syncthreads();
+    // digits, four consecutive k per step (kp is a multiple of 8)
+    const int cpr = kp >> 2;
+    const int dr = 256 / cpr, dc = 256 - dr * cpr;
+    int rr = threadIdx.x / cpr, c = threadIdx.x - rr * cpr;
+    for (int idx = threadIdx.x; idx < rb * cpr; idx += 256) {
+        const int r = r0 + rr, k = 4 * c;
+        if (r < o.rows_pad) {
+            const double* t = oz_blk + rr * ts + k;
+            const double v[4] = {t[0], t[1], t[2], t[3]};
+            oz_store4(o, bl, r, k, v, s_e[rr]);
+        }
+        rr += dr;
+        c += dc;
+        if (c >= cpr) { c -= cpr; rr++; }
+    }
 }
 
 // contiguous rows (K <= 512): one warp per row takes the row into registers, reduces the
@@ -720,18 +727,17 @@ inline bool make_slice_map(CUtensorMap* map, const void* base, int k, int kp, in
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// exponents and slices of one operand: long contiguous rows in one pass (a warp per row),
-// short or strided ones in two (32 x 32 tiles keep all lanes busy when K is small)
-inline bool oz_one_pass(const OzOperand& o) { return !o.strided && o.k >= 256 && o.k <= OZ_KC; }
-inline int oz_prepare(const OzOperand& o, int bc, cudaStream_t st) {
-    if (oz_one_pass(o)) {
+// exponents and slices of one operand, one pass: long contiguous rows a warp per row in
+// registers, the others (strided, or short) a block of rows at a time through shared memory
+inline bool oz_row_pass(const OzOperand& o) { return !o.strided && o.k >= 256 && o.k <= OZ_KC; }
+inline size_t oz_block_smem(int kp) { return (size_t)oz_block_rows(kp) * (kp + 1) * sizeof(double); }
+inline void oz_prepare(const OzOperand& o, int bc, cudaStream_t st) {
+    if (oz_row_pass(o)) {
         oz_row_slice_kernel<<<dim3((o.rows_pad + 7) / 8, bc), 256, 0, st>>>(o);
-        return 1;
+    } else {
+        const int rb = oz_block_rows(o.kp);
+        oz_block_slice_kernel<<<dim3((o.rows_pad + rb - 1) / rb, bc), 256, oz_block_smem(o.kp), st>>>(o);
     }
-    if (o.strided) oz_expo_kernel<<<dim3((o.rows + 31) / 32, bc), 256, 0, st>>>(o);
-    else oz_expo_kernel<<<dim3((o.rows + 7) / 8, bc), 256, 0, st>>>(o);
-    oz_slice_kernel<<<dim3((o.kp + 31) / 32, o.rows_pad / 32, bc), 256, 0, st>>>(o);
-    return 2;
 }
 
 // number of output tiles of one batch entry (tile width bn)
@@ -752,11 +758,8 @@ inline int oz_launches(const GemmBatch& g, const OzBuf& buf) {
         const size_t per = oz_entry_bytes(g.m, g.n, std::min(OZ_KC, g.k - k0));
         const size_t chunk = std::min<size_t>(g.batch, buf.bytes > 8192 ? (buf.bytes - 8192) / per : 0);
         if (chunk == 0) return 1;
-        // per batch chunk: one slicing launch for an operand with contiguous K rows, two for a
-        // strided one, and the product
-        const int kc = std::min(OZ_KC, g.k - k0);
-        const int nl = ((!g.transA && kc >= 256) ? 1 : 2) + ((g.transB && kc >= 256) ? 1 : 2) + 1;
-        total += nl * (int)((g.batch + chunk - 1) / chunk);
+        // per batch chunk: one slicing launch per operand and the product
+        total += 3 * (int)((g.batch + chunk - 1) / chunk);
     }
     return total;
 }

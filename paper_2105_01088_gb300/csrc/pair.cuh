@@ -178,7 +178,8 @@ __global__ void state_sparse_left_kernel(InstDev d, const double* fimp_state, do
     }
 }
 
-// L1 = Im[:, imp] Fi, L2 = Si[:, imp] Fi  (n x nimp each), Fi = Im Fimp^{a,b}
+// L1 = Im[:, imp] Fi, L2 = 4 Si[:, imp] Fi  (n x nimp each), Fi = Im Fimp^{a,b}; the factor 4
+// of L2's one use (Qi below) is applied here, exactly
 __global__ void pair_lr_kernel(InstDev d, const double* si, const double* imd, const double* fimp, double* lr) {
     const int p = blockIdx.y;
     const int n = d.n, ni = d.nimp;
@@ -196,14 +197,16 @@ __global__ void pair_lr_kernel(InstDev d, const double* si, const double* imd, c
             v2 += s[(size_t)k * n + d.imp[m]] * fi;
         }
         L1[e] = v1;
-        L2[e] = v2;
+        L2[e] = 4.0 * v2;
     }
 }
 
 // Q = Delta F Delta (real and imaginary planes) from X = D Wr D, Wr and V = D Wr
 // (T: double on the FP64 path, float on the tensor-core path):
 //   Qr = X + 4 Wr + 2 (L1 Si[imp,:] + Si[:,imp] L1^T)
-//   Qi = 4 L2 Si[imp,:] - L1 Im[imp,:] - 2 (V - V^T)
+//   Qi = L2 Si[imp,:] - L1 Im[imp,:] - 2 (V - V^T)       (L2 carries its factor 4)
+// as chains of FMAs (FP64 issues at a small fraction of the other pipes' rates on this
+// part, so the count of FP64 instructions sets this kernel's time)
 // On the FP64 path the outputs alias the inputs (qr_out = xa_in, qi_out = wr_in):
 // each element is read and then written by the same thread.
 template <typename T>
@@ -238,12 +241,14 @@ __global__ void __launch_bounds__(256) pair_q_kernel(InstDev d, const double* si
         double a1 = 0.0, a2 = 0.0;
         for (int m = 0; m < ni; m++) {
             const int im_m = d.imp[m];
-            const double s_ml = s[(size_t)im_m * n + l];
-            a1 += L1[k * ni + m] * s_ml + s[(size_t)k * n + im_m] * L1[l * ni + m];
-            a2 += 4.0 * L2[k * ni + m] * s_ml - L1[k * ni + m] * im[(size_t)im_m * n + l];
+            const double s_ml = s[(size_t)im_m * n + l], l1 = L1[k * ni + m];
+            a1 = fma(l1, s_ml, a1);
+            a1 = fma(s[(size_t)k * n + im_m], L1[l * ni + m], a1);
+            a2 = fma(L2[k * ni + m], s_ml, a2);
+            a2 = fma(-l1, im[(size_t)im_m * n + l], a2);
         }
-        const double qr = (double)X[e] + 4.0 * (double)W[e] + 2.0 * a1;
-        const double qi = a2 - 2.0 * ((double)v[e] - vt[tx][j]);      // V[l][k] = vt[l - l0][k - k0]
+        const double qr = fma(2.0, a1, fma(4.0, (double)W[e], (double)X[e]));
+        const double qi = fma(-2.0, (double)v[e] - vt[tx][j], a2);      // V[l][k] = vt[l - l0][k - k0]
         Qr[e] = qr;
         Qi[e] = qi;
     }

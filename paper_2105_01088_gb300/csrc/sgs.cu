@@ -349,13 +349,14 @@ std::vector<int> gj_candidates(int n) {
         limit = optin - (int)fa.sharedSizeBytes;
     }
     std::vector<int> v;
-    for (int b : {8, 16, 32, 64})
+    // 24 and 48 between the powers of two: 24 fits two panel CTAs per SM at n = 512
+    for (int b : {8, 16, 24, 32, 48, 64})
         if (b <= n && (size_t)n * (b + 1) * sizeof(double) + b * sizeof(double) <= (size_t)limit) v.push_back(b);
     return v;
 }
 std::vector<int> pf_candidates(int n) {
     std::vector<int> v;
-    for (int b : {8, 16, 32})
+    for (int b : {8, 12, 16, 24, 32})
         if (2 * b <= n) v.push_back(b);
     return v;
 }
@@ -698,6 +699,7 @@ void set_kernel_attributes() {
         raise_smem_limit(gemm_tmap_kernel<TC_BF16>, optin);
         raise_smem_limit(gemm_tmap_kernel<TC_3XTF32>, optin);
         raise_smem_limit(oz_gemm_kernel<OZ_NARROW>, optin);
+        raise_smem_limit(oz_block_slice_kernel, optin);
         cudaGetLastError();
     });
 }
@@ -714,6 +716,7 @@ inline cudaError_t tma_product(const TmaBatch& t, int kind, cudaStream_t st) {
 inline cudaError_t gemm(sgs_ctx* c, const GemmBatch& g, cudaStream_t st, double flops, const OzBuf* oz = nullptr,
                         int* oz_err = nullptr) {
     const bool emulate = g_gemm_fma == 2 && oz && oz->base && oz_err;
+    if (emulate) set_kernel_attributes();             // the kernels' shared-memory limits (once)
     if (emulate) for (int i = oz_launches(g, *oz); i > 0; i--) counted();
     else counted();
     auto run = [&]() { return emulate ? gemm_oz(g, *oz, oz_err, st) : gemm_f64(g, st); };

@@ -17,8 +17,8 @@ def expo_field(v):
     return 1 if (e == 0 and v != 0) else e
 
 
-def digits(v, E):
-    """Balanced base-128 digits of X = round(v 2^(1078 - E)), most significant first."""
+def scaled_int(v, E):
+    """X = round(v 2^(1078 - E)) (half up on the magnitude), from the bit pattern."""
     u = int(np.float64(v).view(np.uint64))
     f = (u >> 52) & 0x7FF
     m = u & ((1 << 52) - 1)
@@ -33,7 +33,12 @@ def digits(v, E):
         a = 0
     else:
         a = (m + (1 << (-sh - 1))) >> (-sh)
-    X = -a if u >> 63 else a
+    return -a if u >> 63 else a
+
+
+def digits(v, E):
+    """Balanced base-128 digits of X = round(v 2^(1078 - E)), most significant first."""
+    X = scaled_int(v, E)
     t = [0] * S
     for i in range(S - 1, 0, -1):
         d = X & 127
@@ -59,6 +64,29 @@ def test_digits_reconstruct_the_scaled_value():
         for d in t:
             f = np.float32(d)
             assert (f.view(np.uint32) & 0xFFFF) == 0
+
+
+def digits_offset_form(v, E):
+    """The kernels' form of the same digits: Y = X + sum_{j<7} 64 2^(7 j); the low seven
+    digits are the base-128 digits of Y less 64, the top digit is Y >> 49 (arithmetic),
+    and each low digit reaches bf16 as the float 2^23 + u less 2^23 + 64 (u = digit + 64)."""
+    Y = scaled_int(v, E) + sum(64 << (7 * j) for j in range(7))
+    t = [Y >> 49] + [((Y >> (7 * (S - 1 - i))) & 127) - 64 for i in range(1, S)]
+    for i in range(1, S):
+        u = t[i] + 64
+        f = np.float32(np.uint32(0x4B000000 | u).view(np.float32)) - np.float32(8388672.0)
+        assert f == np.float32(t[i])
+    return t
+
+
+def test_offset_form_gives_the_same_digits():
+    rng = np.random.default_rng(4)
+    vals = np.concatenate([rng.standard_normal(2000) * 10.0 ** rng.uniform(-12, 12, 2000),
+                           [0.0, -0.0, 1.0, -1.0, 2.0 ** -60, -(2.0 ** 30)]])
+    for E in (max(expo_field(v) for v in vals), 1023, 1050):
+        for v in vals:
+            if expo_field(v) <= E:
+                assert digits_offset_form(v, E) == digits(v, E)
 
 
 def test_group_sums_within_fp32_exact_range():
