@@ -57,6 +57,8 @@ def parse():
                          "0.125 per instance for the batched and serving workloads)")
     ap.add_argument("--tc-loader", default="tma", choices=["tma", "tmap", "cp"],
                     help="tensor-core operand staging: TMA one CTA per tile, TMA persistent, or cp.async")
+    ap.add_argument("--panel-widths", default="",
+                    help="GJ,PF: fix the factorisation panel widths after the autotuner (reproducible profiles)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--accuracy-steps", type=int, default=0,
                     help="run the FP64 form and --precision side by side for this many steps and report the "
@@ -244,6 +246,8 @@ def run_sgs(args):
     model = sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels)
     stream = torch.cuda.Stream()          # a capturable stream: steps replay a CUDA graph
     solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=prec, parity=w.parity, stream=stream, autotune=True)
+    if args.panel_widths:
+        solver.set_panel_widths(*[int(x) for x in args.panel_widths.split(",")])
     metric = f"imag-time steps/s at 2N={2 * p.n_modes},M={w.rank}"
     peak_fp64_mma = sgs.probe_peak(0)
     peak_fp64_fma = sgs.probe_peak(1)

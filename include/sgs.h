@@ -162,8 +162,16 @@ int sgs_failed_instance(const sgs_ctx* ctx);
 sgs_status sgs_set_autotune(sgs_ctx* ctx, int enable);
 
 /* Panel widths an instance uses; from_cache: -1 not tuned, 0 timed at
- * admission, 1 taken from the cache.  Any output may be NULL. */
+ * admission, 1 taken from the cache, 2 set by sgs_set_panel_widths.  Any
+ * output may be NULL. */
 sgs_status sgs_get_tuning(const sgs_ctx* ctx, int instance, int* gj_width, int* pf_width, int* from_cache);
+
+/* Fix the panel widths of a live instance (for reproducible timings and
+ * profiles): each must be one of the autotuner's candidates and fit the
+ * instance's scratch (an instance admitted with autotuning on has room for
+ * the widest).  Waits for the context's stream; drops a captured step graph.
+ * SGS_EINVAL otherwise. */
+sgs_status sgs_set_panel_widths(sgs_ctx* ctx, int instance, int gj_width, int pf_width);
 
 /* Rank growth (Sec. III C): append to the live instance `slot` the state
  * Q Gamma_src Q^T with Q = exp(K), a special orthogonal matrix.  The paper
@@ -342,7 +350,9 @@ int sgs_build_2ck(int L, double J, double t, double* A, int* quartic_idx, double
  *   every element; mode 1 (m = n) computes the strictly lower part and
  *   writes C and -C^T with a zero diagonal; mode 2 (m = n, Gauss-Jordan
  *   delayed update) leaves columns gj_k0 .. gj_k0 + gj_b - 1 of C unchanged
- *   and does not add Cin on rows in that range. */
+ *   and does not add Cin on rows in that range.  mode + 4 (k = n, trans_b = 0)
+ *   declares B antisymmetric: the emulated path then slices B's rows (op(B)'s
+ *   columns negated) and negates alpha; the other paths ignore it. */
 sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, double* logabsdet);
 sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase, double* logabs);
 sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, double* C);

@@ -67,6 +67,7 @@ SIGNATURES = {
     "sgs_health": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp]),
     "sgs_seeded_states": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, _dp, _dp]),
     "sgs_get_tuning": (ctypes.c_int, [_ctxp, ctypes.c_int, _ip, _ip, _ip]),
+    "sgs_set_panel_widths": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "sgs_set_graphs": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_energy": (ctypes.c_int, [_ctxp, _dp]),
     "sgs_correlator": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _dp]),
@@ -324,6 +325,11 @@ class Solver:
         self._check(_lib.sgs_get_tuning(self._ctx, slot, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
 
+    def set_panel_widths(self, gj_width, pf_width, slot=0):
+        """Fix a slot's panel widths (each one of the autotuner's candidates, within
+        the slot's scratch)."""
+        self._check(_lib.sgs_set_panel_widths(self._ctx, slot, int(gj_width), int(pf_width)))
+
     def add_state(self, K, src=-1, slot=0):
         """Rank growth (Sec. III C): append Q Gamma_src Q^T, Q = exp(K), to a
         slot (K antisymmetric [n, n]; src -1: the state of largest amplitude)."""
@@ -502,11 +508,12 @@ def batched_pfaffian(Y):
 
 
 def batched_gemm(A, B, Cin=None, alpha=1.0, beta=0.0, diag=0.0, trans_a=False, trans_b=False, mode=0,
-                 gj=(0, 1), C=None):
+                 gj=(0, 1), C=None, b_antisym=False):
     """batch C = alpha op(A) op(B) + beta Cin + diag I through the library's FP64
     product on the current path (mode 0 full, 1 antisymmetric, 2 Gauss-Jordan
     update with panel columns gj = (k0, b) left unchanged).  C (optional) holds
-    the output's initial values."""
+    the output's initial values.  b_antisym declares B antisymmetric (the
+    emulated path then slices its rows)."""
     A = np.ascontiguousarray(A, dtype=np.float64)
     B = np.ascontiguousarray(B, dtype=np.float64)
     b = A.shape[0]
@@ -515,7 +522,8 @@ def batched_gemm(A, B, Cin=None, alpha=1.0, beta=0.0, diag=0.0, trans_a=False, t
     out = np.zeros((b, m, n)) if C is None else np.array(C, dtype=np.float64, order="C", copy=True)
     cin = None if Cin is None else np.ascontiguousarray(Cin, dtype=np.float64)
     st = _lib.sgs_kernel_gemm(_ptr(A), _ptr(B), _ptr(cin) if cin is not None else None, m, n, k, int(trans_a),
-                              int(trans_b), alpha, beta, diag, mode, gj[0], gj[1], b, _ptr(out))
+                              int(trans_b), alpha, beta, diag, mode + (4 if b_antisym else 0), gj[0], gj[1], b,
+                              _ptr(out))
     if st != 0:
         raise SGSError(st, "batched gemm")
     return out

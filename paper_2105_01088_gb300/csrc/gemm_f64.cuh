@@ -35,6 +35,8 @@ struct GemmBatch {
     int active_cmp;                      //   otherwise C = Cin (pass-through)
     int mode; int gj_k0; int gj_b;
     int batch;
+    int b_antisym;                       // hint: B (and B2) antisymmetric, op(B)'s columns = -B's rows
+    long long offBr;                     // (emulated products) offset of op(B)'s K range in B's rows
 };
 
 #define GBM 64
@@ -257,7 +259,7 @@ inline cudaError_t gemm_f64(const GemmBatch& g, cudaStream_t st) {
 inline GemmBatch gemm_defaults() {
     GemmBatch g{};
     g.alpha = 1.0; g.beta = 0.0; g.diag = 0.0; g.sA2 = 0.0; g.sB2 = 0.0; g.Cin2 = nullptr; g.beta2 = 0.0;
-    g.mode = GEMM_FULL; g.active_flag = nullptr; g.alpha_b = nullptr; g.active_cmp = 0;
+    g.mode = GEMM_FULL; g.active_flag = nullptr; g.alpha_b = nullptr; g.active_cmp = 0; g.b_antisym = 0;
     return g;
 }
 

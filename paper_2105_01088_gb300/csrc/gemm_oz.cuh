@@ -120,18 +120,22 @@ __host__ __device__ __forceinline__ int oz_plane(int i) {
     return i < OZ_S / 2 ? 2 * i : 2 * (OZ_S - 1 - i) + 1;     // inverse of oz_order
 }
 
-__device__ __forceinline__ int oz_expo_field(double v) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+// The slicers carry the operand as 64-bit bit patterns: they only take its exponent field and
+// significand apart, and double-typed selects and moves of the loaded values cost issue
+// slots of the FP64 pipe, which issues at a small fraction of the integer rate on this part.
+__device__ __forceinline__ int oz_expo_field(unsigned long long u) {
     int e = (int)((u >> 52) & 0x7ff);
     if (e == 0 && (u << 1) != 0ull) e = 1;       // subnormal: scale of the smallest normal
     return e;
 }
 
-__device__ __forceinline__ double oz_load(const OzOperand& o, const double* x, const double* x2, int r, int k) {
+// element (r, k) of op(X) as its bit pattern (plus s2 times the same element of X2, the one
+// FP64 operation of the slicers)
+__device__ __forceinline__ unsigned long long oz_load(const OzOperand& o, const double* x, const double* x2, int r,
+                                                      int k) {
     const long long off = o.strided ? (long long)k * o.ld + r : (long long)r * o.ld + k;
-    double v = x[off];
-    if (x2) v = fma(o.s2, x2[off], v);
-    return v;
+    if (x2) return (unsigned long long)__double_as_longlong(fma(o.s2, x2[off], x[off]));
+    return reinterpret_cast<const unsigned long long*>(x)[off];
 }
 
 __device__ __forceinline__ bool oz_active(const int* flag, int cmp, int b) {
@@ -140,8 +144,7 @@ __device__ __forceinline__ bool oz_active(const int* flag, int cmp, int b) {
 
 // X = round(v 2^(1078 - E)) (E = the row's exponent field, E > 0), |X| <= 2^56, rounded half
 // up on the magnitude, from the bit pattern
-__device__ __forceinline__ long long oz_scaled(double v, int E) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+__device__ __forceinline__ long long oz_scaled(unsigned long long u, int E) {
     int f = (int)((u >> 52) & 0x7ff);
     unsigned long long m = u & 0xFFFFFFFFFFFFFull;
     if (f == 0) f = 1;
@@ -161,7 +164,7 @@ __device__ __forceinline__ long long oz_scaled(double v, int E) {
 // Y >> 49 (arithmetic) is the top digit; a low digit reaches float as the float 2^23 + u_j
 // (built by OR-ing u_j into the pattern of 2^23) less 2^23 + 64, an exact FP32 subtraction.
 // Each digit has at most 8 significant bits, so a float's high half is its exact bf16.
-__device__ __forceinline__ void oz_digit_floats(double v, int E, float f[OZ_S]) {
+__device__ __forceinline__ void oz_digit_floats(unsigned long long v, int E, float f[OZ_S]) {
     const long long Y = oz_scaled(v, E) + 0x1020408102040ll;
     f[0] = (float)(int)(Y >> 49);
 #pragma unroll
@@ -174,7 +177,8 @@ __device__ __forceinline__ void oz_digit_floats(double v, int E, float f[OZ_S]) 
 // the eight planes of four consecutive k of row r starting at k (k + 3 < kp; entries at or
 // beyond o.k are zero digits, which the tensor map never reads): per plane one 8-byte word
 // of four bf16, the high halves of the digits' floats
-__device__ __forceinline__ void oz_store4(const OzOperand& o, int bl, int r, int k, const double (&v)[4], int E) {
+__device__ __forceinline__ void oz_store4(const OzOperand& o, int bl, int r, int k, const unsigned long long (&v)[4],
+                                          int E) {
     float f[4][OZ_S];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
@@ -208,7 +212,7 @@ __host__ __device__ __forceinline__ int oz_block_rows(int kp) {
 // operand, along k for a contiguous one), reduces every row's exponent field there and writes
 // the digits, one pass over the operand; rows in [rows, rows_pad) get zero digits
 __global__ void __launch_bounds__(256) oz_block_slice_kernel(OzOperand o) {
-    extern __shared__ double oz_blk[];
+    extern __shared__ unsigned long long oz_blk[];
     __shared__ int s_e[128];
     const int bl = blockIdx.y, b = o.b0 + bl;
     if (!oz_active(o.active, o.active_cmp, b)) return;
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(256) oz_block_slice_kernel(OzOperand o) {
 #pragma unroll 8
         for (int idx = threadIdx.x; idx < total; idx += 256) {
             const int k = idx >> sh, rr = idx & (rb - 1), r = r0 + rr;
-            oz_blk[rr * ts + k] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0.0;
+            oz_blk[rr * ts + k] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0ull;
         }
     } else {
         // element idx: row idx / kp, k = idx % kp, stepped without divisions
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(256) oz_block_slice_kernel(OzOperand o) {
 #pragma unroll 8
         for (int idx = threadIdx.x; idx < total; idx += 256) {
             const int r = r0 + rr;
-            oz_blk[rr * ts + k] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0.0;
+            oz_blk[rr * ts + k] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0ull;
             rr += dr;
             k += dk;
             if (k >= kp) { k -= kp; rr++; }
@@ -256,8 +260,8 @@ __global__ void __launch_bounds__(256) oz_block_slice_kernel(OzOperand o) {
     for (int idx = threadIdx.x; idx < rb * cpr; idx += 256) {
         const int r = r0 + rr, k = 4 * c;
         if (r < o.rows_pad) {
-            const double* t = oz_blk + rr * ts + k;
-            const double v[4] = {t[0], t[1], t[2], t[3]};
+            const unsigned long long* t = oz_blk + rr * ts + k;
+            const unsigned long long v[4] = {t[0], t[1], t[2], t[3]};
             oz_store4(o, bl, r, k, v, s_e[rr]);
         }
         rr += dr;
@@ -275,14 +279,14 @@ __global__ void __launch_bounds__(256) oz_row_slice_kernel(OzOperand o) {
     if (r >= o.rows_pad) return;
     const double* x = o.X[b] + o.off;
     const double* x2 = o.X2 ? o.X2[b] + o.off : nullptr;
-    double v[4][4];                      // k = 4 lane + 128 s + u, s < 4 (K <= 512)
+    unsigned long long v[4][4];          // k = 4 lane + 128 s + u, s < 4 (K <= 512)
     int e = 0;
 #pragma unroll
     for (int s = 0; s < 4; s++)
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const int k = 128 * s + 4 * lane + u;
-            v[s][u] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0.0;
+            v[s][u] = (r < o.rows && k < o.k) ? oz_load(o, x, x2, r, k) : 0ull;
             e = max(e, oz_expo_field(v[s][u]));
         }
 #pragma unroll
@@ -329,7 +333,7 @@ __device__ __forceinline__ void oz_combine(const uint32_t (&u)[OZ_G][8], int j, 
 // +-q 2^e2 outside the normal range, out of line: inlined, the compiler may evaluate these
 // FP64 multiplications for every element and select, and FP64 issues at a small fraction
 // of the integer rate on this part
-__device__ __noinline__ double oz_scaled(unsigned long long q, bool sgn, int e2) {
+__device__ __noinline__ double oz_out_of_range(unsigned long long q, bool sgn, int e2) {
     return scalbn(sgn ? -(double)q : (double)q, e2);
 }
 
@@ -366,7 +370,7 @@ __device__ __forceinline__ double oz_to_double(long long H, unsigned L, int e, b
     const bool sgn = sv != neg;
     double r = __longlong_as_double((long long)((((unsigned long long)sgn) << 63) +
                                                 ((unsigned long long)(be - 1) << 52) + q));
-    if (be < 1 || be > 2045) r = oz_scaled(q, sgn, P - 52 + e);
+    if (be < 1 || be > 2045) r = oz_out_of_range(q, sgn, P - 52 + e);
     return (Hm | Lm) ? r : 0.0;
 }
 
@@ -730,7 +734,7 @@ inline bool make_slice_map(CUtensorMap* map, const void* base, int k, int kp, in
 // exponents and slices of one operand, one pass: long contiguous rows a warp per row in
 // registers, the others (strided, or short) a block of rows at a time through shared memory
 inline bool oz_row_pass(const OzOperand& o) { return !o.strided && o.k >= 256 && o.k <= OZ_KC; }
-inline size_t oz_block_smem(int kp) { return (size_t)oz_block_rows(kp) * (kp + 1) * sizeof(double); }
+inline size_t oz_block_smem(int kp) { return (size_t)oz_block_rows(kp) * (kp + 1) * 8; }
 inline void oz_prepare(const OzOperand& o, int bc, cudaStream_t st) {
     if (oz_row_pass(o)) {
         oz_row_slice_kernel<<<dim3((o.rows_pad + 7) / 8, bc), 256, 0, st>>>(o);
@@ -781,7 +785,10 @@ inline cudaError_t gemm_oz_chunk(const GemmBatch& g, const OzBuf& buf, int* err,
         int* eb = ea + oz_round((size_t)bc * mp, 64);
         OzOperand oa{g.A, g.A2, g.sA2, g.offA, g.lda, g.transA ? 1 : 0, g.m, g.k, mp, kp, b0,
                      g.active_flag, g.active_cmp, ea, as, 1};
-        OzOperand ob{g.B, g.B2, g.sB2, g.offB, g.ldb, g.transB ? 0 : 1, g.n, g.k, np, kp, b0,
+        // an antisymmetric B (not transposed): its K-major columns are its rows negated, so the
+        // rows are sliced (contiguous, one pass) and alpha changes sign
+        const bool b_rows = g.b_antisym && !g.transB;
+        OzOperand ob{g.B, g.B2, g.sB2, b_rows ? g.offBr : g.offB, g.ldb, (g.transB || b_rows) ? 0 : 1, g.n, g.k, np, kp, b0,
                      g.active_flag, g.active_cmp, eb, bs, 0};
         oz_prepare(oa, bc, st);
         oz_prepare(ob, bc, st);
@@ -791,10 +798,11 @@ inline cudaError_t gemm_oz_chunk(const GemmBatch& g, const OzBuf& buf, int* err,
             !make_slice_map(&p.tb, bs, g.k, kp, np, bc * OZ_S, bn, OZ_S))
             return cudaErrorInvalidValue;
         p.g = g; p.b0 = b0; p.m_pad = mp; p.n_pad = np; p.ea = ea; p.eb = eb; p.err = err;
+        if (b_rows) p.g.alpha = -g.alpha;
         int ex = 0;
-        const double fr = std::frexp(g.alpha, &ex);
+        const double fr = std::frexp(p.g.alpha, &ex);
         if (!g.alpha_b && (fr == 0.5 || fr == -0.5)) {
-            p.alpha_pow2 = 1; p.alpha_e = ex - 1; p.alpha_neg = g.alpha < 0.0;
+            p.alpha_pow2 = 1; p.alpha_e = ex - 1; p.alpha_neg = p.g.alpha < 0.0;
         }
         oz_gemm_kernel<OZ_NARROW><<<dim3(tiles, bc), OzCfg<OZ_NARROW>::THREADS, OzCfg<OZ_NARROW>::SMEM, st>>>(p);
         const cudaError_t e = cudaGetLastError();
@@ -816,6 +824,7 @@ inline cudaError_t gemm_oz(const GemmBatch& g, const OzBuf& buf, int* err, cudaS
         GemmBatch h = g;
         h.k = std::min(OZ_KC, g.k - k0);
         h.offA += g.transA ? (long long)k0 * g.lda : k0;
+        h.offBr = g.offB + k0;                         // the K range within B's rows (antisymmetric B)
         h.offB += g.transB ? k0 : (long long)k0 * g.ldb;
         if (k0 > 0) {
             h.Cin = (const double* const*)g.C; h.offCin = g.offC; h.ldcin = g.ldc; h.beta = 1.0;

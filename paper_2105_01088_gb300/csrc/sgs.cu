@@ -812,6 +812,7 @@ cudaError_t pair_delta(sgs_ctx* c, Instance& I, cudaStream_t st) {
     GemmBatch g = gb_basic(n, n, n, I.p_ga, n, I.p_si, n, I.p_imd, n, I.P);
     g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
     g.mode = GEMM_SKEW;
+    g.b_antisym = 1;        // S^{-1} (antisymmetric up to the inversion's rounding)
     return gemm(c, I, g, st, (double)n * n * n * I.P);   // antisymmetric product: half of 2 n^3
 }
 
@@ -1006,6 +1007,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         counted();
         GemmBatch g = gb_basic(n, n, n, I.p_work, n, I.p_si, n, I.p_wr, n, P);
         g.mode = GEMM_SKEW;
+        g.b_antisym = 1;    // S^{-1}
         if ((e = gemm(c, I, g, st, n3 * P)) != cudaSuccess) return e;
         // V = D Wr
         c->stage(SGS_STAGE_EOM_V);
@@ -1013,6 +1015,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         c->stage_bytes[SGS_STAGE_EOM_V] += 8.0 * nn * (2.0 * P + M);   // read Wr, write V; Gamma once
         g = gb_basic(n, n, n, I.p_ga, n, I.p_wr, n, I.p_va, n, P);
         g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
+        g.b_antisym = 1;    // Wr (an antisymmetric product)
         if ((e = gemm(c, I, g, st, 2.0 * n3 * P)) != cudaSuccess) return e;
         // X = V D
         c->stage(SGS_STAGE_EOM_X);
@@ -1020,6 +1023,7 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         g = gb_basic(n, n, n, I.p_va, n, I.p_ga, n, I.p_xa, n, P);
         g.B2 = (const double* const*)I.p_gb; g.sB2 = -1.0;
         g.mode = GEMM_SKEW;
+        g.b_antisym = 1;    // Gamma_a - Gamma_b
         if ((e = gemm(c, I, g, st, n3 * P)) != cudaSuccess) return e;
         c->stage(SGS_STAGE_EOM_ASSEMBLY);
         if (I.nimp > 0) {
@@ -1499,6 +1503,23 @@ sgs_status sgs_get_tuning(const sgs_ctx* c, int instance, int* gj_width, int* pf
     if (gj_width) *gj_width = I.gj_b;
     if (pf_width) *pf_width = I.pf_bs;
     if (from_cache) *from_cache = I.tuned_from_cache;
+    return SGS_OK;
+}
+
+sgs_status sgs_set_panel_widths(sgs_ctx* c, int instance, int gj_width, int pf_width) {
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
+    Instance& I = c->inst[instance];
+    const std::vector<int> gj = gj_candidates(I.n), pf = pf_candidates(I.n);
+    if (std::find(gj.begin(), gj.end(), gj_width) == gj.end() || gj_width > I.gj_cap ||
+        std::find(pf.begin(), pf.end(), pf_width) == pf.end() || pf_width > I.pf_cap) {
+        c->err = "panel width not a candidate, or wider than the instance's scratch";
+        return SGS_EINVAL;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const sgs_status s = set_panel_pointers(c, I, gj_width, pf_width);
+    if (s != SGS_OK) return s;
+    I.tuned_from_cache = 2;
+    c->drop_graph();     // the captured step launches the old panels
     return SGS_OK;
 }
 
@@ -2225,7 +2246,11 @@ sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, i
 sgs_status sgs_kernel_gemm(const double* A, const double* B, const double* Cin, int m, int n, int k, int trans_a,
                            int trans_b, double alpha, double beta, double diag, int mode, int gj_k0, int gj_b,
                            int batch, double* C) {
-    if (!A || !B || !C || m < 1 || n < 1 || k < 1 || batch < 1 || mode < 0 || mode > 2) return SGS_EINVAL;
+    if (!A || !B || !C || m < 1 || n < 1 || k < 1 || batch < 1 || mode < 0 || mode > 6 || (mode & 3) > 2)
+        return SGS_EINVAL;
+    const int b_antisym = mode >> 2;            // + 4: B antisymmetric (k = n)
+    mode &= 3;
+    if (b_antisym && (k != n || trans_b)) return SGS_EINVAL;
     if (mode == GEMM_SKEW && m != n) return SGS_EINVAL;
     if (mode == GEMM_GJ && (m != n || gj_k0 < 0 || gj_b < 1 || gj_k0 + gj_b > n)) return SGS_EINVAL;
     sgs_ctx tmp;
@@ -2252,7 +2277,7 @@ sgs_status sgs_kernel_gemm(const double* A, const double* B, const double* Cin, 
         cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
         GemmBatch g = gb_basic(m, n, k, PA, trans_a ? m : k, PB, trans_b ? k : n, PC, n, batch);
         g.transA = trans_a ? 1 : 0; g.transB = trans_b ? 1 : 0;
-        g.alpha = alpha; g.diag = diag; g.mode = mode; g.gj_k0 = gj_k0; g.gj_b = gj_b;
+        g.alpha = alpha; g.diag = diag; g.mode = mode; g.gj_k0 = gj_k0; g.gj_b = gj_b; g.b_antisym = b_antisym;
         if (PI) { g.Cin = (const double* const*)PI; g.ldcin = n; g.beta = beta; }
         set_kernel_attributes();
         const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(m, n, k));

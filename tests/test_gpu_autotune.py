@@ -42,3 +42,27 @@ def test_autotune_choices_cache_and_results(pkg):
     assert tuned.tuning(k1)[2] in (0, 1)
     tuned.close()
     plain.close()
+
+
+def test_fixed_panel_widths(pkg):
+    """Widths fixed after admission (reproducible profiles): any candidate within the
+    scratch, results equal to the tuned instance's up to rounding; others refused."""
+    import torch
+    p = inp.AndersonParams(n_bath=37, U=3.0, eps_d=-1.5, V=0.6)      # n = 152
+    rng = np.random.default_rng(62)
+    g = inp.clustered_pure_gammas(p.n_modes, 4, rng, 1, spread=1.0)
+    lam = inp.random_amplitudes(4, rng)
+    m = pkg.build_anderson(p.n_bath, p.U, p.eps_d, p.V)
+    st = torch.cuda.Stream()
+    s = pkg.Solver(m, g, lam, stream=st, autotune=True)
+    E0 = s.step(2)[0]
+    s.close()
+    s = pkg.Solver(m, g, lam, stream=st, autotune=True)
+    s.set_panel_widths(24, 12)
+    assert s.tuning(0) == (24, 12, 2)
+    E1 = s.step(2)[0]
+    assert np.abs(E1 - E0).max() <= 1e-12 * np.abs(E0).max()
+    with pytest.raises(pkg.SGSError):
+        s.set_panel_widths(20, 12)                     # not a candidate
+    assert s.tuning(0) == (24, 12, 2)
+    s.close()

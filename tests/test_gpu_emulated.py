@@ -136,6 +136,27 @@ def test_antisymmetric_mode(pkg):
     assert np.all(np.diagonal(C0, axis1=1, axis2=2) == 0.0)
 
 
+@pytest.mark.parametrize("n,mode,alpha", [(200, 0, 0.7), (200, 1, -0.5), (600, 0, 1.0), (600, 1, 0.3)])
+def test_antisymmetric_b_sliced_by_rows(pkg, n, mode, alpha):
+    """B declared antisymmetric: its rows are sliced in place of op(B)'s columns and alpha
+    changes sign; K = 600 runs in two chunks (the K range taken within B's rows)."""
+    rng = np.random.default_rng(n + 10 * mode)
+    batch = 2
+    G = rng.standard_normal((batch, n, n))
+    G = G - np.swapaxes(G, 1, 2)
+    S = rng.standard_normal((batch, n, n))
+    S = S - np.swapaxes(S, 1, 2)
+    A = np.matmul(G, S) if mode == 1 else rng.standard_normal((batch, n, n))
+    C = pkg.batched_gemm(A, G, alpha=alpha, mode=mode, b_antisym=True)
+    ref = alpha * _exact(A, G)
+    bound = 4 * U * abs(alpha) * (np.abs(A) @ np.abs(G))
+    err = np.abs(C.astype(np.longdouble) - ref).astype(np.float64)
+    sel = np.tril(np.ones((n, n), dtype=bool), -1) if mode == 1 else np.ones((n, n), dtype=bool)
+    assert np.all(err[:, sel] <= bound[:, sel]), (err / np.maximum(bound, 1e-300))[:, sel].max()
+    if mode == 1:
+        assert np.array_equal(C, -np.swapaxes(C, 1, 2))
+
+
 def test_gauss_jordan_mode_matches_native_semantics(pkg):
     """Columns of the panel stay as they were; rows of the panel start from 0."""
     rng = np.random.default_rng(11)
