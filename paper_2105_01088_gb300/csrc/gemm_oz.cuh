@@ -330,20 +330,14 @@ __device__ __forceinline__ void oz_combine(const uint32_t (&u)[OZ_G][8], int j, 
     L = (unsigned)lo & 0xFFFFFFFu;
 }
 
-// +-q 2^e2 outside the normal range, out of line: inlined, the compiler may evaluate these
-// FP64 multiplications for every element and select, and FP64 issues at a small fraction
-// of the integer rate on this part
-__device__ __noinline__ double oz_out_of_range(unsigned long long q, bool sgn, int e2) {
-    return scalbn(sgn ? -(double)q : (double)q, e2);
-}
-
 // (-1)^neg V 2^e as a double, V = H 2^28 + L (|H| < 2^47, 0 <= L < 2^28), rounded once to
 // 53 bits (to nearest, ties to even) in integer arithmetic, with selects rather than
 // branches except for the rare |V| < 2^28: |V| = Hm 2^28 + Lm is left-justified into one
 // 64-bit word N (bits shifted out are kept as a sticky flag), N is rounded at its bit 11,
 // and the biased exponent is added onto the rounded significand (a carry out of the
-// significand moves into the exponent by itself).  Results outside the normal range take
-// scalbn.
+// significand moves into the exponent by itself).  Results beyond the normal range become
+// infinities, and below it subnormals (q rounded once more), in the same integer arithmetic:
+// no call and no FP64 instruction, so the eight columns a thread combines interleave.
 __device__ __forceinline__ double oz_to_double(long long H, unsigned L, int e, bool neg) {
     const bool sv = H < 0;
     const unsigned long long Hm = sv ? (unsigned long long)(L ? ~H : -H) : (unsigned long long)H;
@@ -367,11 +361,21 @@ __device__ __forceinline__ double oz_to_double(long long H, unsigned L, int e, b
     const unsigned rest = (unsigned)(N & 0x3FFull) | sticky;
     q += ((N >> 10) & 1ull) & ((rest != 0u ? 1ull : 0ull) | (q & 1ull));
     const int be = P + e + 1023;
-    const bool sgn = sv != neg;
-    double r = __longlong_as_double((long long)((((unsigned long long)sgn) << 63) +
-                                                ((unsigned long long)(be - 1) << 52) + q));
-    if (be < 1 || be > 2045) r = oz_out_of_range(q, sgn, P - 52 + e);
-    return (Hm | Lm) ? r : 0.0;
+    const unsigned long long sbit = (unsigned long long)(sv != neg) << 63;
+    unsigned long long bits = sbit + ((unsigned long long)(be - 1) << 52) + q;   // be <= 2046: a carry out of
+    if (be > 2046) bits = sbit | 0x7FF0000000000000ull;                         // q overflows to infinity
+    if (be < 1) {
+        // subnormal: q 2^(be - 1) in units of 2^-1074, q rounded once more to nearest even
+        const int sh = 1 - be;
+        unsigned long long m = 0;
+        if (sh < 64) {
+            m = q >> sh;
+            const unsigned long long rem = q & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+            m += (rem > half || (rem == half && (m & 1ull))) ? 1ull : 0ull;
+        }
+        bits = sbit | m;                                  // m = 2^52: the smallest normal, exactly
+    }
+    return (Hm | Lm) ? __longlong_as_double((long long)bits) : 0.0;
 }
 
 template <int BN, int EPIW, int RING, bool BDBL>

@@ -155,16 +155,25 @@ def _to_double(hi, lo, e, neg):
         sticky = 0
         P = 31 - lz
     if (Hm | Lm) == 0:
-        return 0.0
+        return 0.0, 0, 0
     assert N >> 63 == 1
     q = N >> 11
     rest = (N & 0x3FF) | sticky
     q += ((N >> 10) & 1) & ((1 if rest else 0) | (q & 1))
     be = P + e + 1023
-    assert 1 <= be <= 2045
-    sgn = int(sv != neg)
-    bits = (sgn << 63) + ((be - 1) << 52) + q
-    return struct.unpack('<d', struct.pack('<Q', bits))[0]
+    sbit = int(sv != neg) << 63
+    bits = sbit + ((be - 1) << 52) + q
+    if be > 2046:
+        bits = sbit | 0x7FF0000000000000
+    if be < 1:                       # subnormal: q rounded once more, to nearest even
+        sh = 1 - be
+        m = 0
+        if sh < 64:
+            m = q >> sh
+            rem, half = q & ((1 << sh) - 1), 1 << (sh - 1)
+            m += 1 if (rem > half or (rem == half and (m & 1))) else 0
+        bits = sbit | m
+    return struct.unpack('<d', struct.pack('<Q', bits))[0], q, P
 
 
 def test_combination_rounds_once_to_nearest_even():
@@ -194,4 +203,27 @@ def test_combination_rounds_once_to_nearest_even():
         e, neg = rnd.randint(-100, 40), rnd.random() < 0.5
         V = hi * 2 ** 28 + lo
         ref = float(Fraction(V) * Fraction(2) ** e) * (-1 if neg else 1) if V else 0.0
-        assert _to_double(hi, lo, e, neg) == ref, (hi, lo, e, neg)
+        assert _to_double(hi, lo, e, neg)[0] == ref, (hi, lo, e, neg)
+
+
+def test_combination_outside_the_normal_range():
+    """Beyond the largest double: infinity.  Below the smallest normal: the 53-bit q rounded
+    once more to nearest even (the subnormal grid), i.e. Python's correctly rounded float of
+    q 2^(P - 52 + e), down to zero."""
+    import math
+    import random
+    rnd = random.Random(8)
+    for _ in range(20000):
+        hi, lo = rnd.randint(-2 ** 46, 2 ** 46), rnd.randint(-2 ** 46, 2 ** 46)
+        if hi == 0 and lo == 0:
+            continue
+        neg = rnd.random() < 0.5
+        _, q, P = _to_double(hi, lo, 0, neg)
+        sign = -1.0 if ((hi * 2 ** 28 + lo < 0) != neg) else 1.0
+        e_hi = rnd.randint(2047 - 1023 - P, 2047 - 1023 - P + 30)       # be >= 2047
+        got = _to_double(hi, lo, e_hi, neg)[0]
+        assert math.isinf(got) and math.copysign(1.0, got) == sign
+        e_lo = rnd.randint(-1023 - P - 60, -1023 - P)                   # be <= 0
+        got = _to_double(hi, lo, e_lo, neg)[0]
+        ref = sign * float(Fraction(q) * Fraction(2) ** (P - 52 + e_lo))
+        assert got == ref, (hi, lo, e_lo, neg, got, ref)
