@@ -330,52 +330,48 @@ __device__ __forceinline__ void oz_combine(const uint32_t (&u)[OZ_G][8], int j, 
     L = (unsigned)lo & 0xFFFFFFFu;
 }
 
-// (-1)^neg V 2^e as a double, V = H 2^28 + L (|H| < 2^47, 0 <= L < 2^28), rounded once to
-// 53 bits (to nearest, ties to even) in integer arithmetic, with selects rather than
-// branches except for the rare |V| < 2^28: |V| = Hm 2^28 + Lm is left-justified into one
-// 64-bit word N (bits shifted out are kept as a sticky flag), N is rounded at its bit 11,
-// and the biased exponent is added onto the rounded significand (a carry out of the
-// significand moves into the exponent by itself).  Results beyond the normal range become
-// infinities, and below it subnormals (q rounded once more), in the same integer arithmetic:
-// no call and no FP64 instruction, so the eight columns a thread combines interleave.
-__device__ __forceinline__ double oz_to_double(long long H, unsigned L, int e, bool neg) {
+// The bit pattern of (-1)^neg V 2^e as a double, V = H 2^28 + L (|H| < 2^47, 0 <= L < 2^28), rounded once to
+// 53 bits (to nearest, ties to even) in integer arithmetic: |V| = Hm 2^28 + Lm is
+// left-justified into one 64-bit word N (bits shifted out are kept as a sticky flag), N is
+// rounded at its bit 11, and the biased exponent is added onto the rounded significand (a
+// carry out of the significand moves into the exponent by itself).  Results beyond the
+// normal range become infinities, and below it subnormals (q rounded once more).  The code
+// is straight-line: both justifications of N (|V| of more or fewer than 64 bits), the case
+// |V| < 2^28 and the range ends are computed with shift amounts kept in range and selected,
+// with no branch and no FP64 instruction, so that the eight columns a thread combines
+// interleave.
+__device__ __forceinline__ unsigned long long oz_to_double_bits(long long H, unsigned L, int e, bool neg) {
     const bool sv = H < 0;
     const unsigned long long Hm = sv ? (unsigned long long)(L ? ~H : -H) : (unsigned long long)H;
     const unsigned Lm = sv ? ((0x10000000u - L) & 0xFFFFFFFu) : L;
-    unsigned long long N;
-    unsigned sticky;
-    int P;                                         // leading bit of |V|
-    if (Hm) {
-        const int lz = __clzll((long long)Hm);     // 17 .. 63
-        const bool right = lz < 28;                // |V| has more than 64 bits: Lm loses 28 - lz bits
-        N = (Hm << lz) | (right ? (unsigned long long)(Lm >> (28 - lz)) : (unsigned long long)Lm << (lz - 28));
-        sticky = right ? (Lm << (lz + 4)) : 0u;
-        P = 91 - lz;
-    } else {
-        const int lz = __clz((int)Lm);             // Lm = 0 gives V = 0, handled below
-        N = (unsigned long long)Lm << ((lz + 32) & 63);
-        sticky = 0u;
-        P = 31 - lz;
-    }
+    // |V| >= 2^28: from Hm's leading bit (lzh in 17 .. 63)
+    const int lzh = __clzll((long long)Hm) & 63;               // Hm = 0: 0, and unused
+    const bool right = lzh < 28;                               // Lm loses 28 - lzh bits
+    const unsigned long long low = right ? (unsigned long long)(Lm >> (right ? 28 - lzh : 0))
+                                         : (unsigned long long)Lm << (right ? 0 : lzh - 28);
+    const unsigned long long NH = (Hm << lzh) | low;
+    const unsigned stH = right ? (Lm << ((lzh + 4) & 31)) : 0u;
+    // |V| < 2^28: from Lm's
+    const int lzl = __clz((int)Lm);                            // Lm = 0: 32 (V = 0, handled below)
+    const unsigned long long NL = (unsigned long long)Lm << ((lzl + 32) & 63);
+    const bool hz = Hm == 0ull;
+    const unsigned long long N = hz ? NL : NH;
+    const unsigned sticky = hz ? 0u : stH;
+    const int P = hz ? 31 - lzl : 91 - lzh;                    // leading bit of |V|
     unsigned long long q = N >> 11;
     const unsigned rest = (unsigned)(N & 0x3FFull) | sticky;
     q += ((N >> 10) & 1ull) & ((rest != 0u ? 1ull : 0ull) | (q & 1ull));
     const int be = P + e + 1023;
     const unsigned long long sbit = (unsigned long long)(sv != neg) << 63;
     unsigned long long bits = sbit + ((unsigned long long)(be - 1) << 52) + q;   // be <= 2046: a carry out of
-    if (be > 2046) bits = sbit | 0x7FF0000000000000ull;                         // q overflows to infinity
-    if (be < 1) {
-        // subnormal: q 2^(be - 1) in units of 2^-1074, q rounded once more to nearest even
-        const int sh = 1 - be;
-        unsigned long long m = 0;
-        if (sh < 64) {
-            m = q >> sh;
-            const unsigned long long rem = q & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-            m += (rem > half || (rem == half && (m & 1ull))) ? 1ull : 0ull;
-        }
-        bits = sbit | m;                                  // m = 2^52: the smallest normal, exactly
-    }
-    return (Hm | Lm) ? __longlong_as_double((long long)bits) : 0.0;
+    bits = be > 2046 ? (sbit | 0x7FF0000000000000ull) : bits;                  // q overflows to infinity
+    // subnormal: q 2^(be - 1) in units of 2^-1074, q rounded once more to nearest even
+    const int sh = min(max(1 - be, 1), 63);
+    const unsigned long long ms = q >> sh, rem = q & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    const unsigned long long msub = (1 - be < 64) ? ms + ((rem > half || (rem == half && (ms & 1ull))) ? 1ull : 0ull)
+                                                  : 0ull;
+    bits = be < 1 ? (sbit | msub) : bits;                      // msub = 2^52: the smallest normal, exactly
+    return (Hm | Lm) ? bits : 0ull;
 }
 
 template <int BN, int EPIW, int RING, bool BDBL>
@@ -620,15 +616,13 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
+                        // computed for every column and selected (no branch between the columns)
                         const int c = cb * 8 + j, fc = col_e[c];
-                        double v = 0.0;
-                        if (er > 0 && fc > 0) {
-                            long long H;
-                            unsigned L;
-                            oz_combine(u, j, H, L);
-                            v = oz_to_double(H, L, er + fc - 2107 + ae, an);
-                        }
-                        tile[rr0 * TS + c] = v;
+                        long long H;
+                        unsigned L;
+                        oz_combine(u, j, H, L);
+                        const unsigned long long v = oz_to_double_bits(H, L, er + fc - 2107 + ae, an);
+                        reinterpret_cast<unsigned long long*>(tile)[rr0 * TS + c] = (er > 0 && fc > 0) ? v : 0ull;
                     }
                 }
             }

@@ -129,10 +129,12 @@ def test_scheme_error_against_exact_product():
 
 def _to_double(hi, lo, e, neg):
     """The combination's rounding of V = hi 2^28 + lo (|hi|, |lo| < 2^47) to a double
-    times 2^e, in the integer word arithmetic the CUDA kernel uses: V = H 2^28 + L with
-    0 <= L < 2^28, |V| as (Hm, Lm), left-justified into a 64-bit word N with the bits
-    shifted out kept as a sticky flag, N rounded at its bit 11, and the biased exponent
-    added onto the rounded significand."""
+    times 2^e, transcribing the CUDA kernel's straight-line integer arithmetic: V = H 2^28 + L
+    with 0 <= L < 2^28, |V| as (Hm, Lm); both justifications of the 64-bit word N and the
+    case Hm = 0 computed with shift amounts kept in range, then selected; N rounded at its
+    bit 11; the biased exponent added onto the rounded significand; infinity above the
+    normal range, the subnormal grid (q rounded once more) below it.  Returns the double and
+    the rounded significand q and leading-bit index P."""
     import struct
     m64, m32 = (1 << 64) - 1, (1 << 32) - 1
     clz64 = lambda x: 64 - x.bit_length()
@@ -140,20 +142,20 @@ def _to_double(hi, lo, e, neg):
     H, L = hi + (lo >> 28), lo & 0xFFFFFFF
     assert H * 2 ** 28 + L == hi * 2 ** 28 + lo and 0 <= L < 2 ** 28
     sv = H < 0
-    Hm = ((~H) if L else -H) if sv else H
+    Hm = (((~H) if L else -H) if sv else H) & m64
     Lm = ((0x10000000 - L) & 0xFFFFFFF) if sv else L
-    assert Hm >= 0 and Hm * 2 ** 28 + Lm == abs(H * 2 ** 28 + L)
-    if Hm:
-        lz = clz64(Hm)
-        right = lz < 28
-        N = ((Hm << lz) & m64) | ((Lm >> (28 - lz)) if right else (Lm << (lz - 28)))
-        sticky = ((Lm << (lz + 4)) & m32) if right else 0
-        P = 91 - lz
-    else:
-        lz = clz32(Lm)
-        N = (Lm << ((lz + 32) & 63)) & m64
-        sticky = 0
-        P = 31 - lz
+    assert Hm * 2 ** 28 + Lm == abs(H * 2 ** 28 + L)
+    lzh = clz64(Hm) & 63
+    right = lzh < 28
+    low = (Lm >> (28 - lzh if right else 0)) if right else ((Lm << (0 if right else lzh - 28)) & m64)
+    NH = ((Hm << lzh) & m64) | low
+    stH = ((Lm << ((lzh + 4) & 31)) & m32) if right else 0
+    lzl = clz32(Lm)
+    NL = (Lm << ((lzl + 32) & 63)) & m64
+    hz = Hm == 0
+    N = NL if hz else NH
+    sticky = 0 if hz else stH
+    P = 31 - lzl if hz else 91 - lzh
     if (Hm | Lm) == 0:
         return 0.0, 0, 0
     assert N >> 63 == 1
@@ -162,17 +164,14 @@ def _to_double(hi, lo, e, neg):
     q += ((N >> 10) & 1) & ((1 if rest else 0) | (q & 1))
     be = P + e + 1023
     sbit = int(sv != neg) << 63
-    bits = sbit + ((be - 1) << 52) + q
+    bits = (sbit + (((be - 1) << 52) & m64) + q) & m64
     if be > 2046:
         bits = sbit | 0x7FF0000000000000
-    if be < 1:                       # subnormal: q rounded once more, to nearest even
-        sh = 1 - be
-        m = 0
-        if sh < 64:
-            m = q >> sh
-            rem, half = q & ((1 << sh) - 1), 1 << (sh - 1)
-            m += 1 if (rem > half or (rem == half and (m & 1))) else 0
-        bits = sbit | m
+    sh = min(max(1 - be, 1), 63)
+    ms, rem, half = q >> sh, q & ((1 << sh) - 1), 1 << (sh - 1)
+    msub = ms + (1 if (rem > half or (rem == half and (ms & 1))) else 0) if (1 - be < 64) else 0
+    if be < 1:
+        bits = sbit | msub
     return struct.unpack('<d', struct.pack('<Q', bits))[0], q, P
 
 
