@@ -28,18 +28,20 @@
 //
 // Combination.  The eight group sums are converted to integers and combined
 // exactly, hi = sum_{G<4} v_G 2^(7 (3 - G)), lo = sum_{G>=4} v_G 2^(7 (7 - G)),
-// V = hi 2^28 + lo as a pair of 64-bit words; V is rounded once to 53 bits
+// V = hi 2^28 + lo = H 2^28 + L (0 <= L < 2^28); V is rounded once to 53 bits
 // and given the exponent E_r + F_c - 2107 (plus that of alpha when alpha is a
-// power of two, else one multiplication), all in integer arithmetic on the bit
-// pattern.  The GemmBatch epilogue (beta Cin, beta2 Cin2, diag, FULL / SKEW / GJ
-// modes, pass-through of inactive batch entries) is applied as in gemm_f64.
+// power of two, else one multiplication), all in straight-line integer
+// arithmetic on the bit pattern.  The GemmBatch epilogue (beta Cin, beta2 Cin2,
+// diag, FULL / SKEW / GJ modes, pass-through of inactive batch entries) is
+// applied as in gemm_f64, with no FP64 instruction beyond the additions the
+// epilogue terms need (FP64 issues at a small fraction of the integer rate).
 //
-// Kernels per batch chunk: exponents and slices of op(A) and op(B), one pass over
-// each (a warp per row where the operand's K rows are contiguous and long, else a
-// block of whole rows at a time through shared memory), then the product kernel.  The product kernel takes a 128 x 32 output tile per CTA of 10 warps
-// (256 TMEM columns, 97 KB of shared memory), so two CTAs share an SM and one's
-// epilogue overlaps the other's loads and MMAs; its MMA issue then keeps the
-// tensor pipe near its bf16 rate.  In the kernel:
+// Kernels per batch chunk: exponents and slices of op(A) and op(B), one pass
+// over each (a warp per row where the operand's K rows are contiguous and long,
+// else a block of whole rows at a time through shared memory), then the product
+// kernel.  It takes a 128 x 32 output tile per CTA of 10 warps (256 TMEM
+// columns, 97 KB of shared memory), so two CTAs share an SM and one's epilogue
+// overlaps the other's loads and MMAs.  In the kernel:
 //   * one producer lane loads, per 64-element K slab, the eight B slices as one
 //     TMA box (TMA issue costs about the same per box whatever its size, so
 //     boxes are made large) and the A slices in pairs (one 32 KB box per pair of
