@@ -109,6 +109,33 @@ def test_epilogue_forms(pkg, alpha, beta, diag):
     assert np.all(err <= bound), (err / np.maximum(bound, 1e-300)).max()
 
 
+@pytest.mark.parametrize("scale", [1e-158, 1e158])
+def test_results_below_and_beyond_the_normal_range(pkg, scale):
+    """Products of magnitude near 1e-316 come out on the subnormal grid (within one of its
+    units), those near 1e316 as infinities of the right sign; elements that cancel back into
+    the normal range keep the usual bound."""
+    rng = np.random.default_rng(21)
+    batch, m, n, k = 2, 130, 70, 40
+    A = rng.standard_normal((batch, m, k)) * scale
+    B = rng.standard_normal((batch, k, n)) * scale
+    C = pkg.batched_gemm(A, B)
+    ref = _exact(A, B)
+    if scale < 1:
+        bound = 4 * U * (np.abs(A) @ np.abs(B)) + 2.0 ** -1074
+        err = np.abs(C.astype(np.longdouble) - ref).astype(np.float64)
+        assert np.all(err <= bound), (err / bound).max()
+        assert np.all(np.abs(C) < 2.2250738585072014e-308)
+    else:
+        big = np.abs(ref) > np.longdouble("1e309")
+        assert big.mean() > 0.9
+        with np.errstate(over="ignore"):
+            sign = np.sign(ref[big].astype(np.float64))
+        assert np.all(np.isinf(C[big])) and np.all(np.sign(C[big]) == sign)
+        small = np.abs(ref) < np.longdouble("1e307")
+        bound = 4 * U * (np.abs(A).astype(np.longdouble) @ np.abs(B).astype(np.longdouble))
+        assert np.all(np.abs(C[small].astype(np.longdouble) - ref[small]) <= bound[small])
+
+
 def test_antisymmetric_mode(pkg):
     rng = np.random.default_rng(9)
     batch, n = 2, 200
