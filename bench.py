@@ -35,6 +35,15 @@ PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 DTYPES = {"fp64": "f64", "tf32": "f64+tf32", "bf16": "f64+bf16", "3xtf32": "f64+3xtf32"}
 
 
+def _sha256(path):
+    import hashlib
+    try:
+        with open(path, "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -323,9 +332,11 @@ def run_sgs(args):
             t = json.load(open(tfile)).get(key, {})
             # counters hold for the same shape, panel widths and FP64 path only
             # and for the same launch sequence (a changed step shows as another launch count)
+            # and only while the sources of the counted kernels are the ones captured
+            fresh = all(_sha256(os.path.join(ROOT, f)) == hsh for f, hsh in t.get("sources", {}).items())
             if (t.get("n") == n and t.get("rank") == w.rank and t.get("fp64_path") == args.fp64_path
                     and t.get("panel_widths_gj_pf") == list(solver.tuning(0)[:2])
-                    and t.get("launches_per_step") * args.steps == int(g_n)):
+                    and t.get("launches_per_step") * args.steps == int(g_n) and fresh):
                 traffic = t.get("bytes_per_launch")
         if args.fp64_path == "emulated":
             kern = ("oz_gemm_kernel with its slicing kernels (FP64 products emulated on the bf16 tensor cores; "
