@@ -11,8 +11,12 @@ larger than L2).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 
-Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
-of the workload (independent problems, no collective on the data path).
+Prints one JSON line (rank 0).  The line's value is the FP64 step (every
+product in FP64 arithmetic, emulated on the tensor cores: the library's
+default); its "mixed" object times the TF32 form of the same workload in the
+same run and states its energy and spin-correlator deviation from the FP64 run
+over the same steps.  Under torchrun each rank runs its own replica of the
+workload (independent problems, no collective on the data path).
 """
 import argparse
 import json
@@ -59,13 +63,13 @@ def parse():
     ap.add_argument("--max-steps", type=int, default=400, help="serving: step cap per solve")
     ap.add_argument("--serving-dtau", type=float, default=0.2, help="serving: imaginary-time step")
     ap.add_argument("--rank", type=int, default=0, help="override the ansatz rank M (profiling cases)")
-    ap.add_argument("--fp64-path", default="emulated", choices=["fma", "mma", "emulated"],
-                    help="FP64 products: FMA pipe, m8n8k4 MMA, or emulated on the bf16 tensor cores")
+    ap.add_argument("--fp64-path", default="emulated", choices=["fma", "emulated"],
+                    help="FP64 products: emulated on the bf16 tensor cores (the library's default) or FMA pipe")
     ap.add_argument("--emulation-scratch-gb", type=float, default=0.0,
                     help="emulated FP64 products: slice scratch per instance (GB; default 6 for one instance, "
                          "0.125 per instance for the batched and serving workloads)")
-    ap.add_argument("--tc-loader", default="tma", choices=["tma", "tmap", "cp"],
-                    help="tensor-core operand staging: TMA one CTA per tile, TMA persistent, or cp.async")
+    ap.add_argument("--mixed", default="tf32", choices=["tf32", "bf16", "3xtf32", "none"],
+                    help="mixed-precision form timed beside the FP64 line (the line's 'mixed' object)")
     ap.add_argument("--panel-widths", default="",
                     help="GJ,PF: fix the factorisation panel widths after the autotuner (reproducible profiles)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -217,19 +221,71 @@ def run_reference(args):
     return 0
 
 
-FP64_PATHS = {"mma": 0, "fma": 1, "emulated": 2}
+FP64_PATHS = {"emulated": 0, "fma": 1}
 
 
-def set_fp64_path(sgs, args):
-    sgs.set_fp64_gemm_path(FP64_PATHS[args.fp64_path])
-    if args.fp64_path == "emulated":
-        gb = args.emulation_scratch_gb or (0.125 if args.workload in ("batched", "serving") else 6.0)
-        sgs.set_emulation_scratch(int(gb * 1e9))
+def path_kwargs(args):
+    """Solver options for the FP64 products: the path and, when emulated, the slice scratch."""
+    gb = args.emulation_scratch_gb or (0.125 if args.workload in ("batched", "serving") else 6.0)
+    return {"fp64_path": FP64_PATHS[args.fp64_path],
+            "emulation_scratch": int(gb * 1e9) if args.fp64_path == "emulated" else 0}
 
 
-def dtype_of(args):
-    d = DTYPES[args.precision]
+def dtype_of(args, precision=None):
+    d = DTYPES[precision or args.precision]
     return d.replace("f64", "f64e", 1) if args.fp64_path == "emulated" else d
+
+
+def tc_roofline(prof, precision, n, pairs, steps, peaks):
+    """Roofline of the tensor-core V = D W product of the mixed forms (per pair 2 n^3
+    flops; algorithmic bytes = the two operands read once, hi and lo parts for 3xTF32,
+    and the fp32 product written once), from one profiled region of `steps` steps."""
+    if precision == "fp64" or prof["eom_v"][0] <= 0:
+        return None
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ratio = {"tf32": 1.1 / 2.25, "3xtf32": 1.1 / 2.25 / 3.0, "bf16": 1.0}[precision]
+    tc_peak = bf16 * ratio
+    v_ms, v_fl, _ = prof["eom_v"]
+    ldp = (n + 7) // 8 * 8
+    esz = 2 if precision == "bf16" else 4
+    parts = 2 if precision == "3xtf32" else 1
+    v_bytes = pairs * (2.0 * parts * n * ldp * esz + 4.0 * n * n) * steps
+    flops_s = v_fl / (v_ms * 1e-3)
+    bytes_s = v_bytes / (v_ms * 1e-3)
+    intensity = v_fl / v_bytes
+    hbm_bound = intensity * hbm * 1e9 / 1e12 < tc_peak
+    return {"bound": "hbm" if hbm_bound else "tensor",
+            "kernel": f"gemm_tma_kernel (TMA-fed tcgen05 {precision}, V = D W)",
+            "achieved": bytes_s / 1e9 if hbm_bound else flops_s / 1e12,
+            "peak": hbm if hbm_bound else tc_peak, "unit": "GB/s" if hbm_bound else "TFLOP/s",
+            "frac": (bytes_s / 1e9 / hbm) if hbm_bound else (flops_s / 1e12 / tc_peak),
+            "tflops": flops_s / 1e12, "tensor_peak_tflops": tc_peak,
+            "arithmetic_intensity_flops_per_byte": intensity,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs; tensor peak = bf16_tflops x nominal ratio "
+                           f"({precision}: {ratio:.3f})"}
+
+
+def timed_steps(torch, solver, stream, args, dist, local):
+    """Warm-up steps, then exactly args.steps steps between barriers and synchronisations,
+    CUDA events on the solver's stream and nvidia-smi clocks sampled meanwhile.  Returns
+    (energies of every step run, warm-up included, ms of the timed steps, clocks)."""
+    Ew = solver.step(args.warmup)
+    clocks = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    E = solver.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    return np.concatenate([Ew[0], E[0]]), e0.elapsed_time(e1), ck
 
 
 def run_sgs(args):
@@ -246,19 +302,17 @@ def run_sgs(args):
     import paper_2105_01088_gb300 as sgs
 
     sgs.use_torch_allocator()
-    set_fp64_path(sgs, args)
-    sgs.set_tc_loader(args.tc_loader != "cp", persistent=args.tc_loader == "tmap")
     w = workload(args.workload, args.rank)
     p = w.model
     prec = PRECISIONS[args.precision]
     g, lam = inp.initial_state(p.n_modes, w.rank, w.seed + 1000 * rank, w.parity)
     model = sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels)
     stream = torch.cuda.Stream()          # a capturable stream: steps replay a CUDA graph
-    solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=prec, parity=w.parity, stream=stream, autotune=True)
+    solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=prec, parity=w.parity, stream=stream, autotune=True,
+                        **path_kwargs(args))
     if args.panel_widths:
         solver.set_panel_widths(*[int(x) for x in args.panel_widths.split(",")])
     metric = f"imag-time steps/s at 2N={2 * p.n_modes},M={w.rank}"
-    peak_fp64_mma = sgs.probe_peak(0)
     peak_fp64_fma = sgs.probe_peak(1)
     peaks = {}
     try:
@@ -267,25 +321,11 @@ def run_sgs(args):
         pass
     # the emulated path issues 36 bf16 slice products per FP64 product: its ceiling is the
     # measured bf16 rate / 36
-    peak_fp64 = {"fma": peak_fp64_fma, "mma": peak_fp64_mma,
-                 "emulated": peaks.get("bf16_tflops", 1900.0) / 36.0}[args.fp64_path]
+    peak_fp64 = {"fma": peak_fp64_fma, "emulated": peaks.get("bf16_tflops", 1900.0) / 36.0}[args.fp64_path]
 
-    solver.step(args.warmup)
-    clocks = ClockSampler(local)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0.record(stream)
-    E = solver.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    E_all, ms, ck = timed_steps(torch, solver, stream, args, dist, local)
+    sites = list(range(0, min(p.n_bath + 1, 33)))
+    C_main = solver.correlator(sgs.SGS_CORR_SPIN_SPIN, sites)
     # second timed region of the same length with per-stage and per-GEMM-launch events (direct
     # launches) for the roofline of the dominant kernel
     solver.set_profiling(True)
@@ -319,8 +359,8 @@ def run_sgs(args):
     h2d = w.rank * n * n * 8
     d2h = w.rank * n * n * 8 + w.rank * 16 + 8
 
-    # roofline of the dominant kernel, gemm_f64_kernel (the FP64 m8n8k4 MMA GEMM: ~89% of the FP64 step's
-    # kernel time, most of the mixed step's): algorithmic flops of all its launches / their summed time
+    # roofline of the dominant kernel: every FP64 product of the step (all launches), algorithmic
+    # flops of all its launches / their summed time
     g_ms, g_fl, g_n = gemm_prof
     roof = None
     if g_ms > 0:
@@ -344,56 +384,57 @@ def run_sgs(args):
             src = ("MEASURED_PEAKS.json bf16_tflops / 36 (36 bf16 slice products per FP64 product); achieved = "
                    "algorithmic FP64 flops / time of the products including slicing")
         else:
-            kern = (f"gemm_f64_kernel (FP64 {args.fp64_path.upper()}; all its launches: Gauss-Jordan and "
-                    "Pfaffian updates, pair and state products)")
-            src = (f"measured live: FP64 {args.fp64_path.upper()} throughput probe (sgs_probe_peak "
-                   f"kind {1 if args.fp64_path == 'fma' else 0}); not in MEASURED_PEAKS.json")
+            kern = ("gemm_f64_kernel (FP64 FMA; all its launches: Gauss-Jordan and Pfaffian updates, pair and "
+                    "state products)")
+            src = "measured live: FP64 FMA throughput probe (sgs_probe_peak kind 1); not in MEASURED_PEAKS.json"
         roof = {"bound": "alu" if args.fp64_path == "fma" else "tensor", "achieved": achieved, "peak": peak_fp64,
                 "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": traffic, "kernel": kern,
                 "launches": int(g_n), "flops_per_launch": g_fl / max(g_n, 1), "ms_per_launch": g_ms / max(g_n, 1),
                 "peak_source": src}
-    tc_roof = None
-    if args.precision != "fp64" and prof["eom_v"][0] > 0:
-        # V = D W on the tensor cores, per pair: 2 n^3 flops; algorithmic bytes = the two operands
-        # (n x ldp, hi and lo parts for 3xTF32) read once and the fp32 product written once
-        bf16 = peaks.get("bf16_tflops", 1900.0)
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        ratio = {"tf32": 1.1 / 2.25, "3xtf32": 1.1 / 2.25 / 3.0, "bf16": 1.0}[args.precision]
-        tc_peak = bf16 * ratio
-        v_ms, v_fl, _ = prof["eom_v"]
-        ldp = (n + 7) // 8 * 8
-        esz = 2 if args.precision == "bf16" else 4
-        parts = 2 if args.precision == "3xtf32" else 1
-        pairs = w.rank * (w.rank - 1) // 2
-        v_bytes = pairs * (2.0 * parts * n * ldp * esz + 4.0 * n * n) * args.steps
-        flops_s = v_fl / (v_ms * 1e-3)
-        bytes_s = v_bytes / (v_ms * 1e-3)
-        intensity = v_fl / v_bytes
-        hbm_bound = intensity * hbm * 1e9 / 1e12 < tc_peak
-        kname = {"tma": "gemm_tma_kernel (TMA-fed", "tmap": "gemm_tmap_kernel (persistent TMA-fed",
-                 "cp": "gemm_tc_kernel (cp.async-fed"}[args.tc_loader]
-        tc_roof = {"bound": "hbm" if hbm_bound else "tensor",
-                   "kernel": f"{kname} tcgen05 {args.precision}, V = D W)",
-                   "achieved": bytes_s / 1e9 if hbm_bound else flops_s / 1e12,
-                   "peak": hbm if hbm_bound else tc_peak, "unit": "GB/s" if hbm_bound else "TFLOP/s",
-                   "frac": (bytes_s / 1e9 / hbm) if hbm_bound else (flops_s / 1e12 / tc_peak),
-                   "tflops": flops_s / 1e12, "tensor_peak_tflops": tc_peak,
-                   "arithmetic_intensity_flops_per_byte": intensity,
-                   "peak_source": "MEASURED_PEAKS.json hbm_gbs; tensor peak = bf16_tflops x nominal ratio "
-                                  f"({args.precision}: {ratio:.3f})"}
+    pairs = w.rank * (w.rank - 1) // 2
     stages = {s: {"ms_per_step": v[0] / args.steps, "tflops": (v[1] / (v[0] * 1e-3) / 1e12) if v[0] > 0 and v[1] > 0
                   else None} for s, v in prof.items()}
-
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype_of(args), "data": "synthetic",
             "config": dict(config_of(w, args.precision), fp64_products=args.fp64_path),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(launches), "roofline": roof, "tc_roofline": tc_roof, "clocks": ck, "stages": stages,
-            "energy_last": float(E[0, -1]), "panel_widths_gj_pf": list(solver.tuning(0)[:2]),
-            "fp64_mma_peak_tflops": peak_fp64_mma,
+            "gpu_launches": int(launches), "roofline": roof,
+            "tc_roofline": tc_roofline(prof, args.precision, n, pairs, args.steps, peaks), "clocks": ck,
+            "stages": stages, "energy_last": float(E_all[-1]), "panel_widths_gj_pf": list(solver.tuning(0)[:2]),
             "fp64_fma_peak_tflops": peak_fp64_fma}
     solver.close()
+
+    # the mixed form of the same workload from the same states: the same warm-up and timed steps
+    if args.mixed != "none" and args.precision == "fp64":
+        ms_solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=PRECISIONS[args.mixed], parity=w.parity,
+                               stream=stream, autotune=True, **path_kwargs(args))
+        Em_all, ms_m, ck_m = timed_steps(torch, ms_solver, stream, args, dist, local)
+        C_mixed = ms_solver.correlator(sgs.SGS_CORR_SPIN_SPIN, sites)
+        ms_solver.set_profiling(True)
+        ms_solver.step(args.steps)
+        prof_m, _, _ = ms_solver.profile()
+        ms_solver.set_profiling(False)
+        tm = torch.tensor([ms_m], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        msm_max = float(tm.item())
+        line["mixed"] = {
+            "precision": args.mixed, "dtype": dtype_of(args, args.mixed),
+            "value": world * args.steps / (msm_max * 1e-3), "unit": UNIT, "ms_per_step": msm_max / args.steps,
+            "speedup_vs_fp64": ms_max / msm_max,
+            "tc_roofline": tc_roofline(prof_m, args.mixed, n, pairs, args.steps, peaks), "clocks": ck_m,
+            "stages": {s: {"ms_per_step": v[0] / args.steps} for s, v in prof_m.items()},
+            "panel_widths_gj_pf": list(ms_solver.tuning(0)[:2]),
+            "accuracy_vs_fp64": {
+                "steps_compared": int(len(E_all)),
+                "energy_rel_diff_max": float(np.max(np.abs(Em_all - E_all)) / np.max(np.abs(E_all))),
+                "energy_rel_diff_last": float(abs(Em_all[-1] - E_all[-1]) / abs(E_all[-1])),
+                "corr_sites": sites, "corr_abs_diff_max": float(np.max(np.abs(C_mixed - C_main))),
+                "corr_max_abs": float(np.max(np.abs(C_main))),
+                "note": "the same initial states, warm-up and timed steps on both forms; C(r) of the states "
+                        "after the timed steps"}}
+        ms_solver.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_step, sample = oracle_sample(w, n_pairs=6, n_states=2)
         line["cpu_baseline"] = {"value": 1.0 / t_step, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
@@ -437,17 +478,17 @@ def run_serving(args):
     budget = int(torch.cuda.get_device_properties(0).total_memory * 0.5)
     # warm-up: one solve in each mode (kernel loading, allocator pools)
     for pr in (prec, 0):
-        w = sgs.Solver(stream=stream)
+        w = sgs.Solver(stream=stream, **path_kwargs(args))
         k = w.admit(reqs[0].model, reqs[0].gamma0, reqs[0].lambda0, 0.05, pr, 0, reqs[0].parity)
         w.step(3)
         w.close()
-    solver = sgs.Solver(stream=stream, hbm_budget=budget)
+    solver = sgs.Solver(stream=stream, hbm_budget=budget, **path_kwargs(args))
     # phase form of c_mu (Sec. III A): with the inverse form, random initial states (amplitudes down to
     # 1e-14) drive steps outside the exponential's range at these step sizes
     loop = ServingLoop(solver, dtau=args.serving_dtau, precision=prec, cmode=1, tol=1e-8, max_steps=args.max_steps)
     res = loop.run(reqs)
     solver.close()
-    seq = run_sequential(lambda: sgs.Solver(stream=stream), reqs, dtau=args.serving_dtau, precision=0, cmode=1,
+    seq = run_sequential(lambda: sgs.Solver(stream=stream, **path_kwargs(args)), reqs, dtau=args.serving_dtau, precision=0, cmode=1,
                          tol=1e-8, max_steps=args.max_steps)
     a, b = latency_stats(res), latency_stats(seq)
     dE = max((abs(x.energy - y.energy) / abs(y.energy) for x, y in zip(res, seq)
@@ -455,7 +496,7 @@ def run_serving(args):
     line = {"metric": "impurity solves/s (continuous batching, Poisson arrivals)", "value": a["throughput_per_s"],
             "unit": "solves/s", "n_gpus": 1, "steps": int(sum(r.steps for r in res)), "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPES[args.precision], "data": "synthetic",
+            "dtype": dtype_of(args), "data": "synthetic",
             "config": {"workload": f"serving: {args.requests} Anderson solves, Poisson rate {args.rate}/s, "
                                    "bath L ~ U{8..40}, M in {4, 8}, U ~ U[0,8], V ~ U[0.2,1], run to |dE| < 1e-8 "
                                    f"per step or {args.max_steps} steps at ds = {args.serving_dtau}, phase form of c_mu",
@@ -484,13 +525,11 @@ def run_batched(args):
     import paper_2105_01088_gb300 as sgs
 
     sgs.use_torch_allocator()
-    set_fp64_path(sgs, args)
-    sgs.set_tc_loader(args.tc_loader != "cp", persistent=args.tc_loader == "tmap")
     prec = PRECISIONS[args.precision]
     ws = inp.batched_workloads(args.instances, n_bath=(16, args.max_bath))
     mine = ws[rank::world]
     stream = torch.cuda.Stream()
-    solver = sgs.Solver(stream=stream, autotune=True)
+    solver = sgs.Solver(stream=stream, autotune=True, **path_kwargs(args))
     flops_per_step = 0.0
     for w in mine:
         p = w.model

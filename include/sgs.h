@@ -52,7 +52,7 @@ typedef enum {
 } sgs_status;
 
 typedef enum {
-    SGS_FP64 = 0,        /* every product in FP64 (FMA pipe by default, see sgs_set_fp64_gemm_path) */
+    SGS_FP64 = 0,        /* every product in FP64 (on the path sgs_options.fp64_path selects) */
     SGS_MIXED_TF32 = 1,  /* pair GEMMs of the equation of motion in TF32, FP32 accumulate */
     SGS_MIXED_BF16 = 2,  /* same in BF16 */
     SGS_FP32_3XTF32 = 3  /* same with the 3xTF32 split (about FP32 accuracy) */
@@ -62,6 +62,27 @@ typedef enum {
     SGS_C_INVERSE = 0,   /* c_mu = [lambda_mu conj(lt_mu)]^{-1}           (Sec. III A) */
     SGS_C_PHASE = 1      /* c_mu = lt_mu conj(lambda_mu) / |lambda_mu lt_mu|  (Sec. III A) */
 } sgs_cmode;
+
+/* Arithmetic of the FP64 products (every product of the step in SGS_FP64, the
+ * factorisations, Im Delta and the re-purification in the mixed forms), chosen
+ * per instance.  Both are FP64 products; they differ in how they round.
+ *  - SGS_FP64_EMULATED (default): on the bf16 tensor cores.  Each K-major row
+ *    of op(A) and column of op(B) is scaled by the power of two of its largest
+ *    entry and split into eight signed 7-bit integer slices (57 bits); the 36
+ *    slice products of combined weight above 2^-63 are summed exactly in fp32
+ *    TMEM accumulators (K in chunks of 512) and combined in 64-bit integers
+ *    with one final rounding.  Error of one product, per element:
+ *      |C_ij - (AB)_ij| <= u |(AB)_ij| + 2^-55 K max_k|A_ik| max_k|B_kj|
+ *    (u = 2^-53), plus u times any added terms (beta Cin, diag): normwise in
+ *    row i of A and column j of B, so an element whose terms are all far below
+ *    those maxima is less accurate than the K u sum_k |A_ik||B_kj| of a native
+ *    FP64 dot product.
+ *  - SGS_FP64_FMA: FP64 fused multiply-adds on the CUDA cores (the error of a
+ *    native FP64 dot product), about 6x slower on GB300 at 2N = 512. */
+typedef enum {
+    SGS_FP64_EMULATED = 0,
+    SGS_FP64_FMA = 1
+} sgs_fp64_path;
 
 /* Model, Sec. II A.  A: n x n row-major real antisymmetric, n = 2 * n_modes.
  * Quartic part: n_quartic monomials value[j] * c_i0 c_i1 c_i2 c_i3 with four
@@ -105,6 +126,9 @@ typedef struct {
     void* stream;
     int integrator;          /* sgs_integrator (0: the exponential step) */
     unsigned long long seed; /* initial states when gamma0 is NULL */
+    int fp64_path;           /* sgs_fp64_path of this instance's FP64 products (0: emulated) */
+    size_t emulation_scratch;/* SGS_FP64_EMULATED: bytes of operand-slice scratch this instance
+                                owns (0: 2 GiB; at least 1 MiB); larger batches run in chunks */
 } sgs_options;
 
 /* Create a context holding n_instances independent problems (models[i],
@@ -143,12 +167,16 @@ sgs_status sgs_seeded_states(int n_modes, int rank, unsigned long long seed, int
  * step. */
 sgs_status sgs_health(sgs_ctx* ctx, int instance, double* out);
 
-/* Index of the instance whose device-side error (SGS_ESINGULAR, SGS_ENOTCONV,
- * SGS_ETIMEOUT) ended the last call, or -1.  The other instances of that
- * sgs_step completed the failing step (their states advanced) but its
- * energies were not returned; a request loop retires the failed slot and
+/* Instances whose device-side error (SGS_ESINGULAR, SGS_ENOTCONV,
+ * SGS_ETIMEOUT) ended the last call.  sgs_failed_instance returns the first
+ * (the one sgs_last_error describes) or -1; sgs_failed_instances writes up to
+ * `capacity` slot ids to `slots` (may be NULL) and returns how many failed.
+ * Their error state is cleared.  The other instances of that sgs_step
+ * completed every step (their states advanced) and their rows of `energies`
+ * are written as on success; a request loop retires the failed slots and
  * carries on. */
 int sgs_failed_instance(const sgs_ctx* ctx);
+int sgs_failed_instances(const sgs_ctx* ctx, int* slots, int capacity);
 
 /* Autotuning of the factorisation tile shapes.  With enable = 1, sgs_admit
  * (and sgs_add_state) times the candidate panel widths of the blocked
@@ -191,15 +219,15 @@ sgs_status sgs_add_state(sgs_ctx* ctx, int slot, const double* K, int src);
 /* Graph replay (default on): the first sgs_step of a context captures one step
  * of every live instance into a CUDA graph (one branch per instance, so their
  * kernels overlap), later steps replay it; admit/retire re-capture.  Needs a
- * context stream other than the legacy default stream; off while profiling.
- * The capture keeps the FP64 GEMM path in force when it was taken. */
+ * context stream other than the legacy default stream; off while profiling. */
 sgs_status sgs_set_graphs(sgs_ctx* ctx, int enable);
 
 /* Advance every instance by n_steps imaginary-time steps (Sec. III C).
  * energies (may be NULL): [n_instances][n_steps], the energy E of the
  * states at the start of each step with optimal amplitudes.
- * Errors: SGS_ESINGULAR, SGS_ENOTCONV (state left as after the failing
- * step), SGS_ECUDA. */
+ * Errors: SGS_ESINGULAR, SGS_ENOTCONV, SGS_ETIMEOUT (a device-side failure
+ * of some instances, listed by sgs_failed_instances; their rows of
+ * `energies` are left untouched, every other row is written), SGS_ECUDA. */
 sgs_status sgs_step(sgs_ctx* ctx, int n_steps, double* energies);
 
 /* Energy of the current states with optimal amplitudes (Eq. eigLambda),
@@ -288,34 +316,6 @@ sgs_status sgs_get_profile(const sgs_ctx* ctx, double* ms, double* flops, double
  * kernel (their sum shows whether the two share one pipe). */
 sgs_status sgs_probe_peak(int kind, double* tflops);
 
-/* Compute path of every FP64 product (process-wide; path 2 is read when an
- * instance is admitted, which then owns its slice scratch): 1 = FP64 FMA on
- * the CUDA cores (default), 0 = the m8n8k4 FP64 MMA (both FP64; on GB300 they
- * share one pipe and FMA issues faster), 2 = emulated on the bf16 tensor
- * cores: each operand row is split into eight signed 7-bit integer slices
- * under a common power of two, the 36 slice products of combined weight above
- * 2^-63 are accumulated exactly in fp32 (K in chunks of 512) and combined in
- * 64-bit integers; the error is at most that of the FP64 kernel's own
- * rounding.  Any other nonzero value selects 1. */
-void sgs_set_fp64_gemm_path(int path);
-
-/* Emulated FP64 products (path 2): device scratch per instance for the
- * operand slices, 16 (m + n) k bytes per batch entry of an m x n x k product
- * (default cap 2 GiB; batches that do not fit run in chunks).  Read at
- * admission; at least 1 MiB. */
-void sgs_set_emulation_scratch(size_t bytes);
-
-/* Operand staging of the tensor-core products (process-wide, read when an
- * instance is admitted and at each launch): 1 = Tensor Memory Accelerator
- * tile loads into 128-byte-swizzled shared memory with an mbarrier pipeline,
- * one CTA per output tile (default); 2 = the same loads in a persistent
- * kernel, one CTA per SM looping over the tiles with two TMEM accumulators so
- * that one tile's epilogue overlaps the next tile's loads and MMAs; 0 =
- * cp.async copies into the unswizzled layout.  All three issue the same
- * tcgen05.mma sequence per tile, so results are identical.  Any other nonzero
- * value selects 1. */
-void sgs_set_tc_loader(int loader);
-
 /* Majorana form of the Anderson impurity of Sec. IV (H_0 + H_I) with
  * n_channels open bath chains of n_bath sites, hybridisation V, hopping t,
  * chemical potential mu, interaction U n_up n_dn and level eps_d on the
@@ -336,29 +336,41 @@ int sgs_build_anderson(int n_bath, int n_channels, double U, double eps_d, doubl
  * the number of modes N = 4L, or -1 on bad arguments (L < 2). */
 int sgs_build_2ck(int L, double J, double t, double* A, int* quartic_idx, double* quartic_val, double* e_const);
 
+/* Shared-memory set-up of the current device.  Kernels that keep large tiles in
+ * shared memory need their dynamic limit raised once per device, with that
+ * device current; the first call that launches them on a device does it, and
+ * so does this call.  For kernel i < n_out (0 Gauss-Jordan panel, 1 Pfaffian
+ * panel, 2 Renyi Pfaffian, 3-5 tensor-core product tf32 / bf16 / 3xtf32,
+ * 6 emulated FP64 product, 7 block slicer; n_out <= 8) it writes the limit
+ * in force to limit[i] and the device's opt-in maximum less the kernel's
+ * static shared memory to expected[i]. */
+sgs_status sgs_kernel_smem_limits(int n_out, int* limit, int* expected);
+
 /* Building blocks with host buffers, for tests and external callers.
+ * fp64_path (sgs_fp64_path) selects the arithmetic of their FP64 products.
  * sgs_kernel_inverse: batch n x n matrices -> inverses (Gauss-Jordan,
  *   partial pivoting, FP64) and log|det|.  Returns SGS_ESINGULAR on a zero
  *   pivot.
  * sgs_kernel_pfaffian: batch complex antisymmetric n x n matrices (re, im
  *   interleaved) -> Pf = phase * exp(logabs), phase as (re, im).
- * sgs_kernel_dgemm: batch C = A B (n x n, FP64).
  * sgs_kernel_gemm: batch C = alpha op(A) op(B) + beta Cin + diag I through the
- *   library's FP64 product on the current path, op(A) m x k, op(B) k x n, all
- *   row-major and contiguous per batch entry (A stored k x m if trans_a, B
- *   stored n x k if trans_b); Cin may be NULL.  C is in/out: mode 0 writes
- *   every element; mode 1 (m = n) computes the strictly lower part and
- *   writes C and -C^T with a zero diagonal; mode 2 (m = n, Gauss-Jordan
- *   delayed update) leaves columns gj_k0 .. gj_k0 + gj_b - 1 of C unchanged
- *   and does not add Cin on rows in that range.  mode + 4 (k = n, trans_b = 0)
- *   declares B antisymmetric: the emulated path then slices B's rows (op(B)'s
- *   columns negated) and negates alpha; the other paths ignore it. */
-sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, double* logabsdet);
-sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase, double* logabs);
-sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, double* C);
+ *   library's FP64 product, op(A) m x k, op(B) k x n, all row-major and
+ *   contiguous per batch entry (A stored k x m if trans_a, B stored n x k if
+ *   trans_b); Cin may be NULL.  C is in/out: mode 0 writes every element;
+ *   mode 1 (m = n) computes the strictly lower part and writes C and -C^T
+ *   with a zero diagonal; mode 2 (m = n, Gauss-Jordan delayed update) leaves
+ *   columns gj_k0 .. gj_k0 + gj_b - 1 of C unchanged and does not add Cin on
+ *   rows in that range.  mode + 4 (k = n, trans_b = 0) declares B
+ *   antisymmetric: the emulated path then slices B's rows (op(B)'s columns
+ *   negated) and negates alpha; the FMA path ignores it.
+ *   emulation_scratch: cap on the operand-slice scratch of the emulated path
+ *   (0: 2 GiB, at least 1 MiB); a batch that does not fit runs in chunks,
+ *   with bitwise the same result. */
+sgs_status sgs_kernel_inverse(const double* S, int n, int batch, int fp64_path, double* inv, double* logabsdet);
+sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, int fp64_path, double* phase, double* logabs);
 sgs_status sgs_kernel_gemm(const double* A, const double* B, const double* Cin, int m, int n, int k, int trans_a,
                            int trans_b, double alpha, double beta, double diag, int mode, int gj_k0, int gj_b,
-                           int batch, double* C);
+                           int batch, int fp64_path, size_t emulation_scratch, double* C);
 
 /* sgs_kernel_gemm_tc: batch C = A B on the tcgen05 tensor cores, A: m x k
  * row-major, Bt: n x k row-major (= B^T, the K-major form the tensor core
@@ -377,13 +389,19 @@ sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, i
  *   inv receives S^{-1}); logabsdet: DEVICE pointer to batch doubles
  *   (log|det S|); stream: a cudaStream_t or NULL (legacy default stream).
  * The call allocates nothing: its scratch is a file-scope device array of
- * about 4.9 MiB that every GPU loading the library holds until exit.
+ * about 5.0 MiB that every GPU loading the library holds until exit.  Its
+ * products run on the FP64 FMA pipe (the emulated path needs slice scratch).
  * Limits: 1 <= n <= 1024 and batch * n <= 32768; larger sizes return
- * SGS_EINVAL before any GPU work.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call shares the
- * array, so calls that overlap on the GPU (other streams, other host
- * threads) race; serialise them.  The call waits for its stream and returns
+ * SGS_EINVAL before any GPU work.  The first call on a device does the
+ * set-up: it looks up the array's device address (cudaGetSymbolAddress) and
+ * raises the panel kernel's shared-memory limit, with that device current;
+ * make that first call before any stream capture.  Under lazy module
+ * loading that first call may also load the library's device code, which
+ * creates the array then: a caller that needs every call free of device
+ * allocation makes one warm-up call per device first (a 1 x 1 inverse will
+ * do).  Every call shares the array and it keeps the last call's contents,
+ * so calls that overlap on the GPU (other streams, other host threads)
+ * race; serialise them.  The call waits for its stream and returns
  * SGS_ESINGULAR on a zero pivot, SGS_ECUDA on a CUDA error. */
 sgs_status sgs_kernel_inverse_static(const double* S, double* inv, double* logabsdet, int n, int batch,
                                      void* stream);

@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsgs.so")
 
 SGS_FP64, SGS_MIXED_TF32, SGS_MIXED_BF16, SGS_FP32_3XTF32 = 0, 1, 2, 3
+FP64_EMULATED, FP64_FMA = 0, 1          # sgs_fp64_path: arithmetic of the FP64 products
 SGS_C_INVERSE, SGS_C_PHASE = 0, 1
 SGS_INTEGRATOR_EXP, SGS_INTEGRATOR_EULER = 0, 1
 SGS_CORR_SPIN_SPIN, SGS_CORR_TWO_CHANNEL_K, SGS_CORR_RENYI2 = 0, 1, 2
@@ -42,7 +43,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int), ("dtau", ctypes.c_double), ("precision", ctypes.c_int),
                 ("cmode", ctypes.c_int), ("parity", ctypes.c_int), ("gamma0", ctypes.POINTER(ctypes.c_double)),
                 ("lambda0", ctypes.POINTER(ctypes.c_double)), ("stream", ctypes.c_void_p),
-                ("integrator", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+                ("integrator", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("fp64_path", ctypes.c_int),
+                ("emulation_scratch", ctypes.c_size_t)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -64,6 +66,7 @@ SIGNATURES = {
     "sgs_add_state": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, ctypes.c_int]),
     "sgs_set_autotune": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_failed_instance": (ctypes.c_int, [_ctxp]),
+    "sgs_failed_instances": (ctypes.c_int, [_ctxp, _ip, ctypes.c_int]),
     "sgs_health": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp]),
     "sgs_seeded_states": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, _dp, _dp]),
     "sgs_get_tuning": (ctypes.c_int, [_ctxp, ctypes.c_int, _ip, _ip, _ip]),
@@ -85,15 +88,12 @@ SIGNATURES = {
     "sgs_set_profiling": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_get_profile": (ctypes.c_int, [_ctxp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "sgs_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
-    "sgs_set_fp64_gemm_path": (None, [ctypes.c_int]),
-    "sgs_set_emulation_scratch": (None, [ctypes.c_size_t]),
-    "sgs_set_tc_loader": (None, [ctypes.c_int]),
-    "sgs_kernel_inverse": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
-    "sgs_kernel_pfaffian": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
-    "sgs_kernel_dgemm": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp]),
+    "sgs_kernel_smem_limits": (ctypes.c_int, [ctypes.c_int, _ip, _ip]),
+    "sgs_kernel_inverse": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]),
+    "sgs_kernel_pfaffian": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_gemm": (ctypes.c_int, [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]),
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, _dp]),
     "sgs_kernel_gemm_tc": (ctypes.c_int, [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, _dp]),
     "sgs_kernel_inverse_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -109,10 +109,6 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    # process-wide FP64 product path from the environment (0 MMA, 1 FMA, 2 emulated)
-    env = os.environ.get("SGS_FP64_GEMM_PATH")
-    if env is not None:
-        lib.sgs_set_fp64_gemm_path(int(env))
     return lib
 
 
@@ -237,11 +233,15 @@ class Solver:
     models: MajoranaModel or list; gamma0: [M, n, n] or list; lambda0: [M]
     complex or None.  stream: a CUDA stream handle (int), a torch stream, or
     None (a stream of the library's own).  hbm_budget: bytes the live slots may
-    hold (0: no budget).  Slots can be added (admit) and released (retire)
-    while others are live: continuous batching."""
+    hold (0: no budget).  fp64_path: FP64_EMULATED (default) or FP64_FMA for the
+    FP64 products of every slot this constructor admits; emulation_scratch:
+    slice scratch per slot (bytes, 0: the library's default).  Slots can be
+    added (admit) and released (retire) while others are live: continuous
+    batching."""
 
     def __init__(self, models=(), gamma0=(), lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE,
-                 parity=1, stream=None, hbm_budget=0, integrator=SGS_INTEGRATOR_EXP, autotune=False):
+                 parity=1, stream=None, hbm_budget=0, integrator=SGS_INTEGRATOR_EXP, autotune=False,
+                 fp64_path=FP64_EMULATED, emulation_scratch=0):
         if isinstance(models, MajoranaModel):
             models, gamma0, lambda0 = [models], [gamma0], [lambda0]
         models = list(models)
@@ -267,6 +267,7 @@ class Solver:
         self.shapes = []
         self.live = []
         self._keep = {}
+        self.fp64_path, self.emulation_scratch = int(fp64_path), int(emulation_scratch)
         for i, m, g, l0, dt, pr, cm, pa, it in zip(range(k), models, gamma0, lambda0, per(dtau), per(precision),
                                                    per(cmode), per(parity), per(integrator)):
             try:
@@ -280,10 +281,11 @@ class Solver:
         return len(self.shapes)
 
     def admit(self, model, gamma0, lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE, parity=1,
-              integrator=SGS_INTEGRATOR_EXP, rank=None, seed=0):
+              integrator=SGS_INTEGRATOR_EXP, rank=None, seed=0, fp64_path=None, emulation_scratch=None):
         """Add one problem; returns its slot.  gamma0 None: seeded random states of
-        the given rank, generated by the library.  Raises SGSError(SGS_ENOMEM) if it
-        does not fit the HBM budget (nothing is allocated then)."""
+        the given rank, generated by the library.  fp64_path / emulation_scratch:
+        None takes the solver's.  Raises SGSError(SGS_ENOMEM) if it does not fit the
+        HBM budget (nothing is allocated then)."""
         _check_slot_args(model, gamma0, parity, rank)
         g = None if gamma0 is None else np.ascontiguousarray(gamma0, dtype=np.float64)
         M = rank if g is None else g.shape[0]
@@ -292,7 +294,10 @@ class Solver:
             lam = np.ascontiguousarray(np.stack([np.real(lambda0), np.imag(lambda0)], -1), dtype=np.float64)
         mod = _Model(model.n_modes, _ptr(model.A), len(model.quartic_val), _ptr(model.quartic_idx, _ip),
                      _ptr(model.quartic_val), model.e_const)
-        opt = _Options(M, dtau, precision, cmode, parity, _ptr(g), _ptr(lam), None, integrator, int(seed))
+        path = self.fp64_path if fp64_path is None else int(fp64_path)
+        scratch = self.emulation_scratch if emulation_scratch is None else int(emulation_scratch)
+        opt = _Options(M, dtau, precision, cmode, parity, _ptr(g), _ptr(lam), None, integrator, int(seed), path,
+                       scratch)
         slot = ctypes.c_int(-1)
         st = _lib.sgs_admit(self._ctx, ctypes.byref(mod), ctypes.byref(opt), ctypes.byref(slot))
         if st != 0:
@@ -315,8 +320,15 @@ class Solver:
         return {"purity_residual": out[0], "nonfinite": int(out[1]), "gram_eig_ratio": out[2], "energy": out[3]}
 
     def failed_instance(self):
-        """Slot whose device-side error ended the last call (-1: none)."""
+        """First slot whose device-side error ended the last call (-1: none)."""
         return int(_lib.sgs_failed_instance(self._ctx))
+
+    def failed_instances(self):
+        """Every slot whose device-side error ended the last call."""
+        n = int(_lib.sgs_failed_instances(self._ctx, None, 0))
+        out = np.zeros(max(n, 1), dtype=np.int32)
+        _lib.sgs_failed_instances(self._ctx, _ptr(out, _ip), n)
+        return [int(x) for x in out[:n]]
 
     def tuning(self, slot=0):
         """(Gauss-Jordan panel width, Pfaffian panel width, source) of a slot;
@@ -346,9 +358,16 @@ class Solver:
 
     def step(self, n_steps=1) -> np.ndarray:
         """Advance every live slot; returns energies [n_slots, n_steps] (NaN rows
-        for retired slots)."""
+        for retired slots).  On a device-side failure of some slots the SGSError
+        carries ``energies`` (NaN rows for the failed ones) and ``failed`` (their
+        slots)."""
         E = np.full((self.n_instances, n_steps), np.nan)
-        self._check(_lib.sgs_step(self._ctx, n_steps, _ptr(E)))
+        st = _lib.sgs_step(self._ctx, n_steps, _ptr(E))
+        if st != 0:
+            err = SGSError(st, (_lib.sgs_last_error(self._ctx) or b"").decode())
+            err.energies = E
+            err.failed = self.failed_instances()
+            raise err
         return E
 
     def set_graphs(self, enable=True):
@@ -428,27 +447,15 @@ class Solver:
 
 # ------------------------------------------------------------ building blocks
 
-def set_tc_loader(use_tma=True, persistent=False):
-    """Tensor-core operand staging: TMA tile loads (default; persistent=True
-    selects the one-CTA-per-SM form) or cp.async."""
-    _lib.sgs_set_tc_loader((2 if persistent else 1) if use_tma else 0)
-
-
-FP64_MMA, FP64_FMA, FP64_EMULATED = 0, 1, 2
-
-
-def set_fp64_gemm_path(path=FP64_FMA):
-    """FP64 products on the FMA pipe (1, default), the m8n8k4 MMA (0), or
-    emulated on the bf16 tensor cores (2; read when an instance is admitted).
-    True / False select 1 / 0."""
-    if path is True or path is False:
-        path = int(path)
-    _lib.sgs_set_fp64_gemm_path(int(path))
-
-
-def set_emulation_scratch(nbytes):
-    """Per-instance slice scratch of the emulated FP64 path (read at admission)."""
-    _lib.sgs_set_emulation_scratch(int(nbytes))
+def smem_limits():
+    """[(dynamic shared-memory limit in force, opt-in maximum less static shared
+    memory)] of the library's large-shared-memory kernels on the current device."""
+    lim = np.zeros(8, dtype=np.int32)
+    exp = np.zeros(8, dtype=np.int32)
+    st = _lib.sgs_kernel_smem_limits(8, _ptr(lim, _ip), _ptr(exp, _ip))
+    if st != 0:
+        raise SGSError(st, "shared-memory limits")
+    return list(zip(lim.tolist(), exp.tolist()))
 
 
 def probe_peak(kind=0):
@@ -461,12 +468,12 @@ def probe_peak(kind=0):
     return float(out[0])
 
 
-def batched_inverse(S):
+def batched_inverse(S, fp64_path=FP64_EMULATED):
     S = np.ascontiguousarray(S, dtype=np.float64)
     b, n, _ = S.shape
     out = np.zeros_like(S)
     ld = np.zeros(b)
-    st = _lib.sgs_kernel_inverse(_ptr(S), n, b, _ptr(out), _ptr(ld))
+    st = _lib.sgs_kernel_inverse(_ptr(S), n, b, int(fp64_path), _ptr(out), _ptr(ld))
     if st != 0:
         raise SGSError(st, "batched inverse")
     return out, ld
@@ -495,25 +502,25 @@ def batched_gemm_tc(A, B, kind=0):
     return C
 
 
-def batched_pfaffian(Y):
+def batched_pfaffian(Y, fp64_path=FP64_EMULATED):
     Y = np.ascontiguousarray(Y, dtype=np.complex128)
     b, n, _ = Y.shape
     yv = Y.view(np.float64)
     ph = np.zeros((b, 2))
     la = np.zeros(b)
-    st = _lib.sgs_kernel_pfaffian(_ptr(yv), n, b, _ptr(ph), _ptr(la))
+    st = _lib.sgs_kernel_pfaffian(_ptr(yv), n, b, int(fp64_path), _ptr(ph), _ptr(la))
     if st != 0:
         raise SGSError(st, "batched pfaffian")
     return ph[:, 0] + 1j * ph[:, 1], la
 
 
 def batched_gemm(A, B, Cin=None, alpha=1.0, beta=0.0, diag=0.0, trans_a=False, trans_b=False, mode=0,
-                 gj=(0, 1), C=None, b_antisym=False):
+                 gj=(0, 1), C=None, b_antisym=False, fp64_path=FP64_EMULATED, emulation_scratch=0):
     """batch C = alpha op(A) op(B) + beta Cin + diag I through the library's FP64
-    product on the current path (mode 0 full, 1 antisymmetric, 2 Gauss-Jordan
-    update with panel columns gj = (k0, b) left unchanged).  C (optional) holds
-    the output's initial values.  b_antisym declares B antisymmetric (the
-    emulated path then slices its rows)."""
+    product (mode 0 full, 1 antisymmetric, 2 Gauss-Jordan update with panel
+    columns gj = (k0, b) left unchanged).  C (optional) holds the output's initial
+    values.  b_antisym declares B antisymmetric (the emulated path then slices its
+    rows); emulation_scratch caps the slice scratch (bytes, 0: default)."""
     A = np.ascontiguousarray(A, dtype=np.float64)
     B = np.ascontiguousarray(B, dtype=np.float64)
     b = A.shape[0]
@@ -523,18 +530,7 @@ def batched_gemm(A, B, Cin=None, alpha=1.0, beta=0.0, diag=0.0, trans_a=False, t
     cin = None if Cin is None else np.ascontiguousarray(Cin, dtype=np.float64)
     st = _lib.sgs_kernel_gemm(_ptr(A), _ptr(B), _ptr(cin) if cin is not None else None, m, n, k, int(trans_a),
                               int(trans_b), alpha, beta, diag, mode + (4 if b_antisym else 0), gj[0], gj[1], b,
-                              _ptr(out))
+                              int(fp64_path), int(emulation_scratch), _ptr(out))
     if st != 0:
         raise SGSError(st, "batched gemm")
     return out
-
-
-def batched_dgemm(A, B):
-    A = np.ascontiguousarray(A, dtype=np.float64)
-    B = np.ascontiguousarray(B, dtype=np.float64)
-    b, n, _ = A.shape
-    C = np.zeros_like(A)
-    st = _lib.sgs_kernel_dgemm(_ptr(A), _ptr(B), n, b, _ptr(C))
-    if st != 0:
-        raise SGSError(st, "batched dgemm")
-    return C

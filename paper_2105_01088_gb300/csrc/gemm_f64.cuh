@@ -1,9 +1,10 @@
-// Batched FP64 GEMM.  tcgen05 has no f64 kind.  On GB300 the FP64 FMA of the
-// CUDA cores and the m8n8k4 FP64 MMA (mma.sync .f64) share one FP64 pipe,
-// measured at 1.25 and 1.09 TFLOP/s; this kernel has both compute paths over
-// the same tiles (FMA by default) and every FP64 product of the step (pair
-// products, the delayed updates of the blocked factorisations, the per-state
-// exponential and purification) goes through it.
+// Batched FP64 GEMM on the FP64 FMA pipe of the CUDA cores (the native FP64
+// product path, SGS_FP64_FMA).  tcgen05 has no f64 kind.  On GB300 the FP64 FMA
+// of the CUDA cores and the m8n8k4 FP64 MMA (mma.sync .f64) share one FP64 pipe,
+// measured at 1.25 and 1.09 TFLOP/s, so the products issue FMAs.  Every FP64
+// product of the step (pair products, the delayed updates of the blocked
+// factorisations, the per-state exponential and purification) goes through it
+// on that path; the emulated path (gemm_oz.cuh) shares its batch descriptor.
 //
 // C_b = alpha * alpha_b[b] * op(A_b) op(B_b) + beta * Cin_b + beta2 * Cin2_b + diag * I
 // with A_b = A1_b + sA2 * A2_b (the pair difference Gamma_a - Gamma_b is
@@ -42,18 +43,11 @@ struct GemmBatch {
 #define GBM 64
 #define GBN 64
 #define GBK 16
-#define GAS 20   // padded row stride of the A tile (conflict-free m8n8k4 A fragments)
+#define GAS 20   // padded row stride of the A tile
 #define GBS 68   // padded row stride of the B tile
 
-__device__ __forceinline__ void dmma_8x8x4(double& c0, double& c1, double a, double b) {
-    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
-                 : "+d"(c0), "+d"(c1) : "d"(a), "d"(b));
-}
-
-// FMA = false: m8n8k4 FP64 MMA, 4 warps of 32x32.  FMA = true: FP64 FMA on the
-// CUDA cores, each thread a 4 x 8 register tile (rows 4*(t/8).., cols 8*(t%8)..);
-// on GB300 both share one FP64 pipe, FMA issuing at the higher rate.
-template <int TA, int TB, bool FMA>
+// Each thread accumulates a 4 x 8 register tile (rows 4*(t/8).., columns 8*(t%8)..).
+template <int TA, int TB>
 __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
     __shared__ __align__(16) double As[2][GBM * GAS];
     __shared__ __align__(16) double Bs[2][GBK * GBS];
@@ -73,8 +67,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
         tn = blockIdx.x % ntn;
     }
     const int m0 = tm * GBM, n0 = tn * GBN;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int tid = threadIdx.x;
 
     const bool active = (g.active_flag == nullptr) || (g.active_flag[b] > g.active_cmp);
     double alpha = g.alpha * (g.alpha_b ? g.alpha_b[b] : 1.0);
@@ -148,42 +141,25 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
         for (int kt = 0; kt < nk; kt++) {
             const int s = kt & 1;
             if (kt + 1 < nk) load_tiles((kt + 1) * GBK);
-            if (FMA) {
-                const int r0 = (tid >> 3) * 4, c0 = (tid & 7) * 8;
+            const int r0 = (tid >> 3) * 4, c0 = (tid & 7) * 8;
 #pragma unroll
-                for (int kk = 0; kk < GBK; kk++) {
-                    double af[4], bf[8];
+            for (int kk = 0; kk < GBK; kk++) {
+                double af[4], bf[8];
 #pragma unroll
-                    for (int i = 0; i < 4; i++) af[i] = As[s][(r0 + i) * GAS + kk];
+                for (int i = 0; i < 4; i++) af[i] = As[s][(r0 + i) * GAS + kk];
 #pragma unroll
-                    for (int j = 0; j < 8; j += 2) {
-                        const double2 v = *reinterpret_cast<const double2*>(&Bs[s][kk * GBS + c0 + j]);
-                        bf[j] = v.x;
-                        bf[j + 1] = v.y;
+                for (int j = 0; j < 8; j += 2) {
+                    const double2 v = *reinterpret_cast<const double2*>(&Bs[s][kk * GBS + c0 + j]);
+                    bf[j] = v.x;
+                    bf[j + 1] = v.y;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        acc[i][j][0] = fma(af[i], bf[2 * j], acc[i][j][0]);
+                        acc[i][j][1] = fma(af[i], bf[2 * j + 1], acc[i][j][1]);
                     }
-#pragma unroll
-                    for (int i = 0; i < 4; i++)
-#pragma unroll
-                        for (int j = 0; j < 4; j++) {
-                            acc[i][j][0] = fma(af[i], bf[2 * j], acc[i][j][0]);
-                            acc[i][j][1] = fma(af[i], bf[2 * j + 1], acc[i][j][1]);
-                        }
-                }
-            } else {
-#pragma unroll
-                for (int ks = 0; ks < GBK / 4; ks++) {
-                    double af[4], bf[4];
-#pragma unroll
-                    for (int i = 0; i < 4; i++)
-                        af[i] = As[s][(wm + i * 8 + (lane >> 2)) * GAS + ks * 4 + (lane & 3)];
-#pragma unroll
-                    for (int j = 0; j < 4; j++)
-                        bf[j] = Bs[s][(ks * 4 + (lane & 3)) * GBS + wn + j * 8 + (lane >> 2)];
-#pragma unroll
-                    for (int i = 0; i < 4; i++)
-#pragma unroll
-                        for (int j = 0; j < 4; j++) dmma_8x8x4(acc[i][j][0], acc[i][j][1], af[i], bf[j]);
-                }
             }
             if (kt + 1 < nk) store_tiles(s ^ 1);
             __syncthreads();
@@ -198,10 +174,10 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
     for (int i = 0; i < 4; i++) {
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const int r = FMA ? m0 + (tid >> 3) * 4 + i : m0 + wm + i * 8 + (lane >> 2);
+            const int r = m0 + (tid >> 3) * 4 + i;
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const int c = FMA ? n0 + (tid & 7) * 8 + 2 * j + h : n0 + wn + j * 8 + 2 * (lane & 3) + h;
+                const int c = n0 + (tid & 7) * 8 + 2 * j + h;
                 if (r >= g.m || c >= g.n) continue;
                 double v;
                 if (!active) {
@@ -234,25 +210,15 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
     }
 }
 
-// FP64 compute path of gemm_f64: 1 = FMA (default), 0 = m8n8k4 MMA
-inline int g_gemm_fma = 1;
-
 inline cudaError_t gemm_f64(const GemmBatch& g, cudaStream_t st) {
     if (g.batch <= 0 || g.m <= 0 || g.n <= 0) return cudaSuccess;
     const int tmn = (g.m + GBM - 1) / GBM, tnn = (g.n + GBN - 1) / GBN;
     unsigned gx = (g.mode == GEMM_SKEW) ? (unsigned)(tmn * (tmn + 1) / 2) : (unsigned)(tmn * tnn);
     dim3 grid(gx, g.batch);
-    if (g_gemm_fma) {
-        if (!g.transA && !g.transB) gemm_f64_kernel<0, 0, true><<<grid, 128, 0, st>>>(g);
-        else if (!g.transA && g.transB) gemm_f64_kernel<0, 1, true><<<grid, 128, 0, st>>>(g);
-        else if (g.transA && !g.transB) gemm_f64_kernel<1, 0, true><<<grid, 128, 0, st>>>(g);
-        else gemm_f64_kernel<1, 1, true><<<grid, 128, 0, st>>>(g);
-    } else {
-        if (!g.transA && !g.transB) gemm_f64_kernel<0, 0, false><<<grid, 128, 0, st>>>(g);
-        else if (!g.transA && g.transB) gemm_f64_kernel<0, 1, false><<<grid, 128, 0, st>>>(g);
-        else if (g.transA && !g.transB) gemm_f64_kernel<1, 0, false><<<grid, 128, 0, st>>>(g);
-        else gemm_f64_kernel<1, 1, false><<<grid, 128, 0, st>>>(g);
-    }
+    if (!g.transA && !g.transB) gemm_f64_kernel<0, 0><<<grid, 128, 0, st>>>(g);
+    else if (!g.transA && g.transB) gemm_f64_kernel<0, 1><<<grid, 128, 0, st>>>(g);
+    else if (g.transA && !g.transB) gemm_f64_kernel<1, 0><<<grid, 128, 0, st>>>(g);
+    else gemm_f64_kernel<1, 1><<<grid, 128, 0, st>>>(g);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@
 #pragma once
 #include <cuda.h>
 #include <mutex>
-#include "gemm_tc.cuh"
+#include "tcgen05.cuh"
 
 namespace sgs {
 
@@ -295,252 +295,6 @@ __global__ void __launch_bounds__(128) gemm_tma_kernel(const __grid_constant__ T
     }
 }
 
-// ---------------------------------------------------------------- persistent form
-//
-// The same products with one CTA per SM looping over output tiles, so that loads, MMAs
-// and the epilogue of consecutive tiles overlap: warp 4 (lane 0) streams the operand
-// slabs of all the CTA's tiles through the stage ring, warp 5 (lane 0) issues the MMAs
-// into one of two TMEM accumulators (256 columns), and warps 0-3 drain the other
-// accumulator: "full" / "empty" mbarriers per stage as before, plus "tmem full" (one
-// commit) and "tmem empty" (one arrive per epilogue warp) per accumulator.  Tiles are
-// taken round-robin (tile t, t + gridDim.x, ...); pass-through batches skip the loads and
-// MMAs.  Waits are bounded as in the one-tile form; on a timeout every role stops, the
-// producer waits (bounded) for its loads in flight and the MMA thread for its MMAs.
-
-template <int KIND>
-__global__ void __launch_bounds__(192, 1) gemm_tmap_kernel(const __grid_constant__ TmaBatch g) {
-    using Cfg = TmaCfg<KIND>;
-    using T = typename std::conditional<KIND == TC_BF16, __nv_bfloat16, float>::type;
-    constexpr int NST = Cfg::NST, SLAB = Cfg::SLAB, STAGE = Cfg::STAGE, NS = Cfg::NS;
-    constexpr int KSLAB = 128 / sizeof(T);
-    constexpr int KMMA = (KIND == TC_BF16) ? 16 : 8;
-    constexpr int NMMA = KSLAB / KMMA;
-    constexpr uint32_t IDESC = tc_idesc(KIND, TMA_BN);
-    constexpr int TS = TMA_BN + 1;
-    extern __shared__ uint8_t tmap_smem_raw[];
-    __shared__ uint64_t full[NST], empty[NST], tfull[2], tempty[2], done;
-    __shared__ uint32_t tmem_base;
-    __shared__ int skip, abort_flag, s_ok;
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0) skip = (*(volatile int*)g.err & SGS_DEV_TC_TIMEOUT) != 0;
-    __syncthreads();
-    if (skip) return;
-    const uint32_t raw = smem_u32(tmap_smem_raw);
-    const uint32_t sbase = (raw + 1023u) & ~1023u;
-    float* tile = reinterpret_cast<float*>(tmap_smem_raw + (sbase - raw) + NST * STAGE);
-    auto sA = [&](int s, int part) { return sbase + s * STAGE + part * SLAB; };
-    auto sB = [&](int s, int part) { return sbase + s * STAGE + (NS + part) * SLAB; };
-    const int tmn = (g.m + TMA_BM - 1) / TMA_BM, tnn = (g.n + TMA_BN - 1) / TMA_BN;
-    const int tpb = g.skew ? tmn * (tmn + 1) / 2 : tmn * tnn;
-    const int total = tpb * g.batch;
-    const int nk = (g.k + KSLAB - 1) / KSLAB;
-    auto decode = [&](int t, int& b, int& tm, int& tn) {
-        b = t / tpb;
-        const int q = t % tpb;
-        if (g.skew) {
-            tm = (int)((sqrt(8.0 * q + 1.0) - 1.0) * 0.5);
-            while ((tm + 1) * (tm + 2) / 2 <= q) ++tm;
-            while (tm * (tm + 1) / 2 > q) --tm;
-            tn = q - tm * (tm + 1) / 2;
-        } else {
-            tm = q / tnn;
-            tn = q % tnn;
-        }
-    };
-    auto is_pass = [&](int b) { return g.pass_flag && g.pass_flag[b] <= g.pass_cmp; };
-
-    if (warp == 5) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_base)), "r"(2u * TMA_BN));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) {
-        for (int s = 0; s < NST; s++) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[s])));
-        }
-        for (int q = 0; q < 2; q++) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&tfull[q])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" :: "r"(smem_u32(&tempty[q])));
-        }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&done)));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-        abort_flag = 0;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = tmem_base;
-
-    if (warp == 4) {
-        if (lane == 0) {        // producer
-            int gs = 0;
-            for (int t = blockIdx.x; t < total && !*(volatile int*)&abort_flag; t += gridDim.x) {
-                int b, tm, tn;
-                decode(t, b, tm, tn);
-                if (is_pass(b)) continue;
-                for (int kt = 0; kt < nk; kt++, gs++) {
-                    const int s = gs % NST;
-                    if (gs >= NST &&
-                        !mbar_wait_or_abort(smem_u32(&empty[s]), (uint32_t)((gs / NST - 1) & 1), g.err)) {
-                        abort_flag = 1;
-                        break;
-                    }
-                    mbar_expect_tx(smem_u32(&full[s]), (uint32_t)STAGE);
-                    const int kx = kt * KSLAB;
-                    tma_load_3d(sA(s, 0), &g.ta, kx, tm * TMA_BM, b, smem_u32(&full[s]));
-                    tma_load_3d(sB(s, 0), &g.tb, kx, tn * TMA_BN, b, smem_u32(&full[s]));
-                    if (KIND == TC_3XTF32) {
-                        tma_load_3d(sA(s, 1), &g.ta2, kx, tm * TMA_BM, b, smem_u32(&full[s]));
-                        tma_load_3d(sB(s, 1), &g.tb2, kx, tn * TMA_BN, b, smem_u32(&full[s]));
-                    }
-                }
-            }
-            // every load issued has landed before the CTA can leave
-            for (int q = (gs > NST ? gs - NST : 0); q < gs; q++)
-                mbar_wait(smem_u32(&full[q % NST]), (uint32_t)((q / NST) & 1), g.err);
-        }
-    } else if (warp == 5) {
-        if (lane == 0) {        // MMA issuer
-            int gs = 0, u = 0;
-            for (int t = blockIdx.x; t < total && !*(volatile int*)&abort_flag; t += gridDim.x, u++) {
-                int b, tm, tn;
-                decode(t, b, tm, tn);
-                if (is_pass(b)) { u--; continue; }
-                const int buf = u & 1;
-                if (u >= 2 && !mbar_wait_or_abort(smem_u32(&tempty[buf]), (uint32_t)((u / 2 - 1) & 1), g.err)) {
-                    abort_flag = 1;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t acc = tmem + (uint32_t)(buf * TMA_BN);
-                bool ok = true;
-                for (int kt = 0; kt < nk; kt++, gs++) {
-                    const int s = gs % NST;
-                    if (!mbar_wait_or_abort(smem_u32(&full[s]), (uint32_t)((gs / NST) & 1), g.err)) {
-                        ok = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    for (int j = 0; j < NMMA; j++) {
-                        const uint32_t koff = j * 32;
-                        const uint64_t da = tma_smem_desc(sA(s, 0) + koff);
-                        const uint64_t db = tma_smem_desc(sB(s, 0) + koff);
-                        tc_mma(acc, da, db, IDESC, (kt > 0 || j > 0) ? 1u : 0u, KIND);
-                        if (KIND == TC_3XTF32) {
-                            tc_mma(acc, da, tma_smem_desc(sB(s, 1) + koff), IDESC, 1u, KIND);
-                            tc_mma(acc, tma_smem_desc(sA(s, 1) + koff), db, IDESC, 1u, KIND);
-                        }
-                    }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                 :: "r"(smem_u32(&empty[s])) : "memory");
-                }
-                if (!ok) { abort_flag = 1; break; }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(smem_u32(&tfull[buf])) : "memory");
-            }
-            // every MMA issued has completed before TMEM is freed
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(&done)) : "memory");
-            mbar_wait(smem_u32(&done), 0u, g.err);
-        }
-    } else {
-        // epilogue: warps 0-3 (TMEM lanes 32 w .. 32 w + 31), named barrier 1 over 128 threads
-        int u = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x) {
-            int b, tm, tn;
-            decode(t, b, tm, tn);
-            const bool pass = is_pass(b);
-            const int m0 = tm * TMA_BM, n0 = tn * TMA_BN;
-            if (!pass) {
-                const int buf = u & 1;
-                if (tid == 0) s_ok = mbar_wait_or_abort(smem_u32(&tfull[buf]), (uint32_t)((u / 2) & 1), g.err) ? 1 : 0;
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                if (!s_ok) { if (tid == 0) abort_flag = 1; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const int r = warp * 32 + lane;
-                for (int c0 = 0; c0 < TMA_BN; c0 += 32) {
-                    uint32_t v[32];
-                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * TMA_BN) + c0;
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                                   "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                                   "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
-                                   "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-                                   "=r"(v[30]), "=r"(v[31])
-                                 : "r"(ta));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int j = 0; j < 32; j++) tile[r * TS + c0 + j] = __uint_as_float(v[j]);
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncwarp();
-                if (lane == 0)
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&tempty[buf])) : "memory");
-                u++;
-            } else {
-                for (int e = tid; e < TMA_BM * TMA_BN; e += 128) {
-                    const int rr = e / TMA_BN, cc = e % TMA_BN;
-                    const int row = m0 + rr, col = n0 + cc;
-                    tile[rr * TS + cc] = (row < g.m && col < g.n)
-                                             ? g.Cin[(size_t)b * g.cin_stride + (size_t)row * g.ldcin + col] : 0.0f;
-                }
-            }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            const float alpha = pass ? 1.0f : (float)g.alpha;
-            const bool extra = !pass && (g.Cin || g.diag != 0.0f);
-            auto put = [&](int row, int col, float x) {
-                if (g.out_f64) static_cast<double*>(g.C)[(size_t)b * g.c_stride + (size_t)row * g.ldc + col] = (double)x;
-                else static_cast<float*>(g.C)[(size_t)b * g.c_stride + (size_t)row * g.ldc + col] = x;
-            };
-            for (int e = tid; e < TMA_BM * TMA_BN; e += 128) {
-                const int rr = e / TMA_BN, cc = e % TMA_BN;
-                const int row = m0 + rr, col = n0 + cc;
-                if (row >= g.m || col >= g.n) continue;
-                if (!g.skew || tm != tn) {
-                    float x = alpha * tile[rr * TS + cc];
-                    if (extra) {
-                        if (g.Cin) x += g.beta * g.Cin[(size_t)b * g.cin_stride + (size_t)row * g.ldcin + col];
-                        if (row == col) x += g.diag;
-                        tile[rr * TS + cc] = x;
-                    }
-                    put(row, col, x);
-                } else {
-                    put(row, col, rr > cc ? alpha * tile[rr * TS + cc] : (rr < cc ? -alpha * tile[cc * TS + rr] : 0.0f));
-                }
-            }
-            if (g.CT) {
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                const float a2 = extra ? 1.0f : alpha;
-                for (int e = tid; e < TMA_BM * TMA_BN; e += 128) {
-                    const int cc = e / TMA_BM, rr = e % TMA_BM;
-                    const int row = n0 + cc, col = m0 + rr;
-                    if (row >= g.n || col >= g.m) continue;
-                    g.CT[(size_t)b * g.ct_stride + (size_t)row * g.ldct + col] = a2 * tile[rr * TS + cc];
-                }
-            }
-            if (g.skew && tm != tn) {
-                for (int e = tid; e < TMA_BM * TMA_BN; e += 128) {
-                    const int cc = e / TMA_BM, rr = e % TMA_BM;
-                    const int row = n0 + cc, col = m0 + rr;
-                    if (row >= g.n || col >= g.m) continue;
-                    put(row, col, -alpha * tile[rr * TS + cc]);
-                }
-            }
-            asm volatile("bar.sync 1, 128;" ::: "memory");       // the tile buffer is reused next
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (warp == 5) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2u * TMA_BN));
-    }
-}
-
 // ---------------------------------------------------------------- host side
 
 typedef CUresult (*TmaEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -581,36 +335,6 @@ inline cudaError_t gemm_tma_launch(const TmaBatch& g, cudaStream_t st) {
     const unsigned gx = g.skew ? (unsigned)(tmn * (tmn + 1) / 2) : (unsigned)(tmn * tnn);
     gemm_tma_kernel<KIND><<<dim3(gx, g.batch), 128, TmaCfg<KIND>::SMEM, st>>>(g);
     return cudaGetLastError();
-}
-
-template <int KIND> struct TmapCfg {
-    static constexpr int SMEM = TmaCfg<KIND>::NST * TmaCfg<KIND>::STAGE + TMA_BM * (TMA_BN + 1) * 4 + 1024;
-};
-
-template <int KIND>
-inline cudaError_t gemm_tmap_launch(const TmaBatch& g, cudaStream_t st) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    const int tmn = (g.m + TMA_BM - 1) / TMA_BM, tnn = (g.n + TMA_BN - 1) / TMA_BN;
-    const long long total = (long long)(g.skew ? tmn * (tmn + 1) / 2 : tmn * tnn) * g.batch;
-    const unsigned grid = (unsigned)std::min<long long>(total, sms);
-    gemm_tmap_kernel<KIND><<<grid, 192, TmapCfg<KIND>::SMEM, st>>>(g);
-    return cudaGetLastError();
-}
-
-// the persistent form (one CTA per SM over all tiles)
-inline cudaError_t gemm_tma_persistent(const TmaBatch& g, int kind, cudaStream_t st) {
-    if (g.batch <= 0 || g.m <= 0 || g.n <= 0) return cudaSuccess;
-    if (g.skew && g.m != g.n) return cudaErrorInvalidValue;
-    switch (kind) {
-        case TC_TF32: return gemm_tmap_launch<TC_TF32>(g, st);
-        case TC_BF16: return gemm_tmap_launch<TC_BF16>(g, st);
-        default: return gemm_tmap_launch<TC_3XTF32>(g, st);
-    }
 }
 
 inline cudaError_t gemm_tma(const TmaBatch& g, int kind, cudaStream_t st) {

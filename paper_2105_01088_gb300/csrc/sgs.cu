@@ -34,7 +34,6 @@
 #include "update_lp.cuh"
 #include "probe.cuh"
 #include "gemm_oz.cuh"
-#include "gemm_tc.cuh"
 #include "gemm_tma.cuh"
 #include "corr.cuh"
 #include "renyi.cuh"
@@ -50,9 +49,6 @@ namespace {
 long long g_launches = 0;
 inline void counted() { ++g_launches; }
 
-// staging of the tensor-core operands: 1 = TMA tensor loads (default), 0 = cp.async
-int g_tc_tma = 1;
-
 sgs_alloc_fn g_alloc = nullptr;
 sgs_free_fn g_release = nullptr;
 void* g_user = nullptr;
@@ -66,6 +62,8 @@ struct Instance {
     int N = 0, n = 0, M = 0, P = 0, Ppf = 0, nimp = 0, nq = 0, a_nnz = 0;
     double dtau = 0.0, e_const = 0.0;
     int prec = 0, cmode = 0, parity = 1, integrator = 0;
+    int fp64_path = SGS_FP64_EMULATED;  // arithmetic of the FP64 products (sgs_fp64_path)
+    size_t oz_cap = 0;                  // emulated products: slice scratch cap (bytes)
     int gj_b = 32, pf_bs = 16;          // panel widths of the Gauss-Jordan inverse and the Pfaffian
     int gj_cap = 32, pf_cap = 16;       // widest widths the scratch holds
     int tuned_from_cache = -1;          // -1 not tuned, 0 timed, 1 cached
@@ -163,7 +161,8 @@ struct sgs_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::string err;
-    int failed = -1;                    // instance whose device error ended the last call
+    int failed = -1;                    // first instance whose device error ended the last call
+    std::vector<int> failed_list;       // every instance whose device error ended the last call
     std::vector<void*> allocs;
     int device = 0;
     Instance* owner = nullptr;          // instance being set up: its allocations are its own
@@ -311,14 +310,17 @@ unsigned grid_chunks(size_t work, int threads, unsigned cap) {
 // emulated FP64 products (path 2): slice scratch of one instance, enough for its widest
 // batch (pairs, Pfaffian halves or states) of n x n x n products, capped per instance (the
 // products then run in batch chunks)
-size_t g_oz_cap = (size_t)2 << 30;
-size_t oz_scratch_bytes(int n, int M) {
+constexpr size_t OZ_DEFAULT_CAP = (size_t)2 << 30;
+size_t oz_cap_of(size_t requested) {
+    return requested ? std::max<size_t>(requested, (size_t)1 << 20) : OZ_DEFAULT_CAP;
+}
+size_t oz_scratch_bytes(int n, int M, size_t cap) {
     const size_t P = (size_t)M * (M - 1) / 2, Ppf = P > 0 ? P - (M - 1) : 0;
     const size_t batch = std::max<size_t>(std::max<size_t>(P, 2 * Ppf), std::max<size_t>((size_t)M, 1));
-    return std::min(batch * oz_entry_bytes(n, n, std::min(n, OZ_KC)) + 16384, g_oz_cap);
+    return std::min(batch * oz_entry_bytes(n, n, std::min(n, OZ_KC)) + 16384, cap);
 }
 
-size_t instance_bytes(int n, int M, int prec, int nimp, bool tune) {
+size_t instance_bytes(int n, int M, int prec, int nimp, bool tune, int fp64_path, size_t oz_cap) {
     const size_t nn = (size_t)n * n, P = (size_t)M * (M - 1) / 2, Ppf = P > 0 ? P - (M - 1) : 0;
     const size_t gj_b = tune ? 64 : 32, bs = tune ? 32 : 16;
     const size_t ni = std::max(nimp, 1);
@@ -332,22 +334,19 @@ size_t instance_bytes(int n, int M, int prec, int nimp, bool tune) {
         if (prec != SGS_FP32_3XTF32)
             bytes += (size_t)M * nn * 4 + (size_t)M * n * ldp * (9 * 4 + 10 * esz);   // mixed update
     }
-    if (g_gemm_fma == 2) bytes += oz_scratch_bytes(n, M);
+    if (fp64_path == SGS_FP64_EMULATED) bytes += oz_scratch_bytes(n, M, oz_cap);
     return bytes + (1 << 20);
 }
 
 // Candidate panel widths (the factorisations' tile shapes).  Gauss-Jordan: the panel
 // kernel keeps n x (b + 1) doubles in shared memory; Pfaffian: 2 b <= n.
 std::vector<int> gj_candidates(int n) {
-    static int limit = -1;
-    if (limit < 0) {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaFuncAttributes fa{};
-        cudaFuncGetAttributes(&fa, gj_panel_kernel);
-        limit = optin - (int)fa.sharedSizeBytes;
-    }
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, gj_panel_kernel);
+    const int limit = optin - (int)fa.sharedSizeBytes;
     std::vector<int> v;
     // 24 and 48 between the powers of two: 24 fits two panel CTAs per SM at n = 512
     for (int b : {8, 16, 24, 32, 48, 64})
@@ -405,6 +404,8 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.cmode = o.cmode;
     I.parity = o.parity;
     I.integrator = o.integrator;
+    I.fp64_path = o.fp64_path;
+    I.oz_cap = oz_cap_of(o.emulation_scratch);
     I.e_const = m.e_const;
     I.hA.assign(m.A, m.A + (size_t)n * n);
     I.hq_idx.assign(m.quartic_idx, m.quartic_idx + (m.n_quartic > 0 ? 4 * m.n_quartic : 0));
@@ -635,7 +636,7 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         I.tma_ok = prod(I.tma_w, I.t1_hi, I.t1_lo, I.si_hi, I.si_lo, I.wr32, 1) &&
                    prod(I.tma_v, I.d_hi, I.d_lo, I.wr_hi, I.wr_lo, I.va32, 0) &&
                    prod(I.tma_x, I.va_hi, I.va_lo, I.d_hi, I.d_lo, I.xa32, 1);
-        if (g_tc_tma && !I.tma_ok) { c->err = "tensor map encoding failed"; return SGS_ECUDA; }
+        if (!I.tma_ok) { c->err = "tensor map encoding failed"; return SGS_ECUDA; }
 
         // mixed-precision state update (TMA-fed products; TF32 and BF16 forms): 3xTF32 keeps
         // the FP64 update, since its products accumulate in fp32 and would hold the step to
@@ -659,9 +660,9 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
             I.u_ok = true;
         }
     }
-    if (g_gemm_fma == 2) {
+    if (I.fp64_path == SGS_FP64_EMULATED) {
         // emulated FP64 products: slice scratch for one batch chunk
-        const size_t b = oz_scratch_bytes(n, M);
+        const size_t b = oz_scratch_bytes(n, M, I.oz_cap);
         I.oz.base = static_cast<uint8_t*>(c->dalloc(b));
         if (!I.oz.base) { c->err = "device allocation failed (emulated-product scratch)"; return SGS_ENOMEM; }
         I.oz.bytes = b;
@@ -671,9 +672,10 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
 
 // ------------------------------------------------------------------ launches
 
-// Kernels with large dynamic shared memory: raise their limit once per process,
-// outside any stream capture (227 KB, the per-block maximum of sm_100-class GPUs).
-std::once_flag g_attr_once;
+// Kernels with large dynamic shared memory: raise their limit (227 KB, the per-block
+// maximum of sm_100-class GPUs) once per device, with that device current and outside
+// any stream capture.  The attribute belongs to the device's context, so each device
+// the library runs on is set up on its first use.
 template <class K>
 void raise_smem_limit(K kernel, int optin) {
     cudaFuncAttributes fa{};
@@ -681,41 +683,37 @@ void raise_smem_limit(K kernel, int optin) {
     // the limit applies to dynamic shared memory on top of the kernel's static shared memory
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
+constexpr int SGS_MAX_DEVICES = 64;
+std::mutex g_attr_mutex;
+bool g_attr_done[SGS_MAX_DEVICES] = {};
 void set_kernel_attributes() {
-    std::call_once(g_attr_once, [] {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        raise_smem_limit(gj_panel_kernel, optin);
-        raise_smem_limit(pf_panel_kernel, optin);
-        raise_smem_limit(renyi_pf_kernel, optin);
-        raise_smem_limit(gemm_tc_kernel<128, TC_TF32>, optin);
-        raise_smem_limit(gemm_tc_kernel<128, TC_BF16>, optin);
-        raise_smem_limit(gemm_tc_kernel<128, TC_3XTF32>, optin);
-        raise_smem_limit(gemm_tma_kernel<TC_TF32>, optin);
-        raise_smem_limit(gemm_tma_kernel<TC_BF16>, optin);
-        raise_smem_limit(gemm_tma_kernel<TC_3XTF32>, optin);
-        raise_smem_limit(gemm_tmap_kernel<TC_TF32>, optin);
-        raise_smem_limit(gemm_tmap_kernel<TC_BF16>, optin);
-        raise_smem_limit(gemm_tmap_kernel<TC_3XTF32>, optin);
-        raise_smem_limit(oz_gemm_kernel<OZ_NARROW>, optin);
-        raise_smem_limit(oz_block_slice_kernel, optin);
-        cudaGetLastError();
-    });
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SGS_MAX_DEVICES) return;
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (g_attr_done[dev]) return;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    raise_smem_limit(gj_panel_kernel, optin);
+    raise_smem_limit(pf_panel_kernel, optin);
+    raise_smem_limit(renyi_pf_kernel, optin);
+    raise_smem_limit(gemm_tma_kernel<TC_TF32>, optin);
+    raise_smem_limit(gemm_tma_kernel<TC_BF16>, optin);
+    raise_smem_limit(gemm_tma_kernel<TC_3XTF32>, optin);
+    raise_smem_limit(oz_gemm_kernel<OZ_NARROW>, optin);
+    raise_smem_limit(oz_block_slice_kernel, optin);
+    cudaGetLastError();
+    g_attr_done[dev] = true;
 }
 
-// a TMA-fed tensor-core product: one CTA per output tile, or (loader 2) the persistent
-// form with one CTA per SM
-inline cudaError_t tma_product(const TmaBatch& t, int kind, cudaStream_t st) {
-    return g_tc_tma == 2 ? gemm_tma_persistent(t, kind, st) : gemm_tma(t, kind, st);
-}
+inline cudaError_t tma_product(const TmaBatch& t, int kind, cudaStream_t st) { return gemm_tma(t, kind, st); }
 
 // every FP64 product of the library goes through here; flops = algorithmic work of
-// the launch (antisymmetric outputs count half), < 0 = not profiled
-// (path 2 with the owner's slice scratch: the emulated product on the bf16 tensor cores)
+// the launch (antisymmetric outputs count half), < 0 = not profiled.  With slice
+// scratch (an instance or call on the emulated path) the product runs emulated on
+// the bf16 tensor cores, otherwise on the FP64 FMA pipe.
 inline cudaError_t gemm(sgs_ctx* c, const GemmBatch& g, cudaStream_t st, double flops, const OzBuf* oz = nullptr,
                         int* oz_err = nullptr) {
-    const bool emulate = g_gemm_fma == 2 && oz && oz->base && oz_err;
+    const bool emulate = oz && oz->base && oz_err;
     if (emulate) set_kernel_attributes();             // the kernels' shared-memory limits (once)
     if (emulate) for (int i = oz_launches(g, *oz); i > 0; i--) counted();
     else counted();
@@ -964,34 +962,21 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
                                                                   (const double* const*)I.p_gb, I.q_d_hi, I.q_d_lo,
                                                                   n, ldp, kind);
         counted(); counted(); counted(); counted();
-        TcBatch t{};
-        t.m = n; t.n = n; t.k = n; t.lda = ldp; t.ldb = ldp; t.ldc = n; t.alpha = -1.0; t.out_f64 = 0;
-        t.err = I.err; t.batch = P;
-        t.A = (const void* const*)I.q_t1_hi; t.A2 = (const void* const*)I.q_t1_lo;
-        t.B = (const void* const*)I.q_si_hi; t.B2 = (const void* const*)I.q_si_lo;
-        t.C = I.q_wr32; t.skew = 1;
-        const bool tma = g_tc_tma && I.tma_ok;
-        if ((e = tma ? tma_product(I.tma_w, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        if ((e = tma_product(I.tma_w, kind, st)) != cudaSuccess) return e;
         counted();
         lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_wr32, nullptr, I.q_wr_hi,
                                                                  I.q_wr_lo, n, ldp, kind);
         counted();
         c->stage(SGS_STAGE_EOM_V);
         c->stage_flops[SGS_STAGE_EOM_V] += 2.0 * n3 * P;
-        t.A = (const void* const*)I.q_d_hi; t.A2 = (const void* const*)I.q_d_lo;
-        t.B = (const void* const*)I.q_wr_hi; t.B2 = (const void* const*)I.q_wr_lo;
-        t.C = I.q_va32; t.skew = 0;
-        if ((e = tma ? tma_product(I.tma_v, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        if ((e = tma_product(I.tma_v, kind, st)) != cudaSuccess) return e;
         counted();
         c->stage(SGS_STAGE_EOM_X);
         c->stage_flops[SGS_STAGE_EOM_X] += n3 * P;
         lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_va32, nullptr, I.q_va_hi,
                                                                  I.q_va_lo, n, ldp, kind);
         counted();
-        t.A = (const void* const*)I.q_va_hi; t.A2 = (const void* const*)I.q_va_lo;
-        t.B = (const void* const*)I.q_d_hi; t.B2 = (const void* const*)I.q_d_lo;
-        t.C = I.q_xa32; t.skew = 1;
-        if ((e = tma ? tma_product(I.tma_x, kind, st) : gemm_tc(t, kind, st)) != cudaSuccess) return e;
+        if ((e = tma_product(I.tma_x, kind, st)) != cudaSuccess) return e;
         counted();
         c->stage(SGS_STAGE_EOM_ASSEMBLY);
         if (I.nimp > 0) {
@@ -1249,39 +1234,43 @@ cudaError_t update_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Reads and clears the device error word of every live instance.  Every instance whose
+// word was set is listed in c->failed_list (c->failed is the first); the status and
+// message are those of the first, and the message counts the others.
 sgs_status check_device_error(sgs_ctx* c) {
     c->failed = -1;
+    c->failed_list.clear();
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    sgs_status first = SGS_OK;
     for (size_t i = 0; i < c->inst.size(); i++) {
         if (!c->inst[i].live) continue;
         int e = 0;
         CUDA_TRY(c, cudaMemcpy(&e, c->inst[i].err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (e) {
-            CUDA_TRY(c, cudaMemset(c->inst[i].err, 0, sizeof(int)));
-            c->failed = (int)i;
-            char buf[160];
-            if (e & SGS_DEV_SINGULAR) {
-                snprintf(buf, sizeof buf, "instance %zu: two ansatz states have a singular Gamma_a + Gamma_b", i);
-                c->err = buf;
-                return SGS_ESINGULAR;
-            }
-            if (e & SGS_DEV_TC_TIMEOUT) {
-                snprintf(buf, sizeof buf, "instance %zu: a bounded tensor-core pipeline wait ran out", i);
-                c->err = buf;
-                return SGS_ETIMEOUT;
-            }
-            if (e & SGS_DEV_PF_ZERO) {
-                snprintf(buf, sizeof buf, "instance %zu: a state is orthogonal to the reference state", i);
-                c->err = buf;
-                return SGS_ESINGULAR;
-            }
+        if (!e) continue;
+        CUDA_TRY(c, cudaMemset(c->inst[i].err, 0, sizeof(int)));
+        c->failed_list.push_back((int)i);
+        if (first != SGS_OK) continue;
+        c->failed = (int)i;
+        char buf[160];
+        if (e & SGS_DEV_SINGULAR) {
+            snprintf(buf, sizeof buf, "instance %zu: two ansatz states have a singular Gamma_a + Gamma_b", i);
+            first = SGS_ESINGULAR;
+        } else if (e & SGS_DEV_TC_TIMEOUT) {
+            snprintf(buf, sizeof buf, "instance %zu: a bounded tensor-core pipeline wait ran out", i);
+            first = SGS_ETIMEOUT;
+        } else if (e & SGS_DEV_PF_ZERO) {
+            snprintf(buf, sizeof buf, "instance %zu: a state is orthogonal to the reference state", i);
+            first = SGS_ESINGULAR;
+        } else {
             snprintf(buf, sizeof buf, "instance %zu: %s", i,
                      (e & SGS_DEV_EIG) ? "amplitude solver did not converge" : "exponential step out of range");
-            c->err = buf;
-            return SGS_ENOTCONV;
+            first = SGS_ENOTCONV;
         }
+        c->err = buf;
     }
-    return SGS_OK;
+    if (c->failed_list.size() > 1)
+        c->err += " (and " + std::to_string(c->failed_list.size() - 1) + " more failed instance(s))";
+    return first;
 }
 
 sgs_status ensure_ehist(sgs_ctx* c, Instance& I, int n) {
@@ -1368,6 +1357,7 @@ sgs_status check_args(const sgs_model& m, const sgs_options& o) {
     if (o.rank < 1 || o.rank > SGS_MAX_RANK || (o.parity != 1 && o.parity != -1)) return SGS_EINVAL;
     if (o.precision < 0 || o.precision > 3 || (o.cmode != 0 && o.cmode != 1)) return SGS_EINVAL;
     if (o.integrator != SGS_INTEGRATOR_EXP && o.integrator != SGS_INTEGRATOR_EULER) return SGS_EINVAL;
+    if (o.fp64_path != SGS_FP64_EMULATED && o.fp64_path != SGS_FP64_FMA) return SGS_EINVAL;
     if (o.gamma0) {           // finite and antisymmetric (purity is reported by sgs_health)
         const int n = 2 * m.n_modes;
         for (int mu = 0; mu < o.rank; mu++) {
@@ -1408,7 +1398,8 @@ sgs_status sgs_admit(sgs_ctx* c, const sgs_model* model, const sgs_options* opt,
     *slot = -1;
     sgs_status s = check_args(*model, *opt);
     if (s != SGS_OK) { c->err = "invalid model, options or initial states (non-finite or not antisymmetric)"; return s; }
-    const size_t need = instance_bytes(2 * model->n_modes, opt->rank, opt->precision, 16, c->autotune);
+    const size_t need = instance_bytes(2 * model->n_modes, opt->rank, opt->precision, 16, c->autotune,
+                                       opt->fp64_path, oz_cap_of(opt->emulation_scratch));
     if (c->budget && c->bytes_in_use + need > c->budget) {
         c->err = "over the HBM budget: " + std::to_string(c->bytes_in_use + need) + " > " + std::to_string(c->budget);
         return SGS_ENOMEM;
@@ -1455,6 +1446,14 @@ sgs_status sgs_retire(sgs_ctx* c, int slot) {
 size_t sgs_bytes_in_use(const sgs_ctx* c) { return c ? c->bytes_in_use : 0; }
 
 int sgs_failed_instance(const sgs_ctx* c) { return c ? c->failed : -1; }
+
+int sgs_failed_instances(const sgs_ctx* c, int* slots, int capacity) {
+    if (!c) return 0;
+    const int n = (int)c->failed_list.size();
+    if (slots)
+        for (int i = 0; i < std::min(n, capacity); i++) slots[i] = c->failed_list[i];
+    return n;
+}
 
 sgs_status sgs_health(sgs_ctx* c, int instance, double* out) {
     if (!c || !out || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
@@ -1548,7 +1547,7 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
             if (a > best) { best = a; src = mu; }
         }
     }
-    const size_t need = instance_bytes(n, M + 1, I.prec, 16, c->autotune);
+    const size_t need = instance_bytes(n, M + 1, I.prec, 16, c->autotune, I.fp64_path, I.oz_cap);
     if (c->budget && c->bytes_in_use - I.bytes + need > c->budget) {
         c->err = "over the HBM budget: " + std::to_string(c->bytes_in_use - I.bytes + need) + " > " +
                  std::to_string(c->budget);
@@ -1557,7 +1556,8 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
     // the grown instance: same model and options, rank M + 1, states filled on the device
     Instance J;
     sgs_model m{I.N, I.hA.data(), (int)I.hq_val.size(), I.hq_idx.data(), I.hq_val.data(), I.e_const};
-    sgs_options o{M + 1, I.dtau, I.prec, I.cmode, I.parity, nullptr, nullptr, nullptr, I.integrator, 0};
+    sgs_options o{M + 1, I.dtau, I.prec, I.cmode, I.parity, nullptr, nullptr, nullptr, I.integrator, 0,
+                  I.fp64_path, I.oz_cap};
     c->owner = &J;
     sgs_status s = setup_instance(c, J, m, o);
     c->owner = nullptr;
@@ -1698,14 +1698,15 @@ sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
     c->launches += g_launches - l0;
     sgs_status s = check_device_error(c);
     c->collect();
-    if (s != SGS_OK) return s;
+    // the energies of the instances that completed every step, also when others failed
     if (energies) {
         for (size_t i = 0; i < c->inst.size(); i++)
-            if (c->inst[i].live)
+            if (c->inst[i].live &&
+                std::find(c->failed_list.begin(), c->failed_list.end(), (int)i) == c->failed_list.end())
                 CUDA_TRY(c, cudaMemcpy(energies + i * n_steps, c->inst[i].Ehist, n_steps * sizeof(double),
                                        cudaMemcpyDeviceToHost));
     }
-    return SGS_OK;
+    return s;
 }
 
 sgs_status sgs_energy(sgs_ctx* c, double* energies) {
@@ -1959,10 +1960,25 @@ sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double*
     return SGS_OK;
 }
 
-void sgs_set_fp64_gemm_path(int path) { g_gemm_fma = (path == 2) ? 2 : (path ? 1 : 0); }
-void sgs_set_emulation_scratch(size_t bytes) { g_oz_cap = std::max<size_t>(bytes, (size_t)1 << 20); }
-
-void sgs_set_tc_loader(int loader) { g_tc_tma = loader == 2 ? 2 : (loader ? 1 : 0); }
+sgs_status sgs_kernel_smem_limits(int n_out, int* limit, int* expected) {
+    const void* k[] = {(const void*)gj_panel_kernel, (const void*)pf_panel_kernel, (const void*)renyi_pf_kernel,
+                       (const void*)gemm_tma_kernel<TC_TF32>, (const void*)gemm_tma_kernel<TC_BF16>,
+                       (const void*)gemm_tma_kernel<TC_3XTF32>, (const void*)oz_gemm_kernel<OZ_NARROW>,
+                       (const void*)oz_block_slice_kernel};
+    const int nk = (int)(sizeof(k) / sizeof(k[0]));
+    if (!limit || !expected || n_out < 1 || n_out > nk) return SGS_EINVAL;
+    set_kernel_attributes();
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SGS_ECUDA;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return SGS_ECUDA;
+    for (int i = 0; i < n_out; i++) {
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, k[i]) != cudaSuccess) return SGS_ECUDA;
+        limit[i] = fa.maxDynamicSharedSizeBytes;
+        expected[i] = optin - (int)fa.sharedSizeBytes;
+    }
+    return SGS_OK;
+}
 
 sgs_status sgs_set_graphs(sgs_ctx* c, int enable) {
     if (!c) return SGS_EINVAL;
@@ -2101,54 +2117,17 @@ int sgs_build_2ck(int L, double J, double t, double* A, int* quartic_idx, double
 
 }  // extern "C"
 
-// slice scratch of a temporary context for the emulated FP64 path (empty on the other paths)
-static OzBuf tmp_oz(sgs_ctx& tmp, size_t need) {
+// slice scratch of a temporary context for the emulated FP64 path (empty on the FMA path)
+static OzBuf tmp_oz(sgs_ctx& tmp, size_t need, int fp64_path, size_t cap) {
     OzBuf o;
-    if (g_gemm_fma != 2) return o;
-    const size_t b = std::min(need + 16384, g_oz_cap);
+    if (fp64_path != SGS_FP64_EMULATED) return o;
+    const size_t b = std::min(need + 16384, oz_cap_of(cap));
     o.base = static_cast<uint8_t*>(tmp.dalloc(b));
     o.bytes = o.base ? b : 0;
     return o;
 }
 
 extern "C" {
-
-sgs_status sgs_kernel_dgemm(const double* A, const double* B, int n, int batch, double* C) {
-    if (!A || !B || !C || n < 1 || batch < 1) return SGS_EINVAL;
-    sgs_ctx tmp;
-    cudaStreamCreateWithFlags(&tmp.stream, cudaStreamNonBlocking);
-    tmp.own_stream = true;
-    const size_t nn = (size_t)n * n;
-    double *dA = tmp.alloc<double>(batch * nn), *dB = tmp.alloc<double>(batch * nn), *dC = tmp.alloc<double>(batch * nn);
-    sgs_status st = SGS_OK;
-    if (!dA || !dB || !dC) st = SGS_ENOMEM;
-    if (st == SGS_OK) {
-        std::vector<double*> pa, pb, pc;
-        for (int b = 0; b < batch; b++) { pa.push_back(dA + b * nn); pb.push_back(dB + b * nn); pc.push_back(dC + b * nn); }
-        double **PA = upload_ptrs(&tmp, pa), **PB = upload_ptrs(&tmp, pb), **PC = upload_ptrs(&tmp, pc);
-        cudaMemcpyAsync(dA, A, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
-        cudaMemcpyAsync(dB, B, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
-        GemmBatch g = gb_basic(n, n, n, PA, n, PB, n, PC, n, batch);
-        const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(n, n, n));
-        int* err = tmp.alloc<int>(1);
-        int herr = 0;
-        if (!err) st = SGS_ENOMEM;
-        else {
-            set_kernel_attributes();
-            cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
-            if (gemm(nullptr, g, tmp.stream, -1.0, &oz, err) != cudaSuccess) st = SGS_ECUDA;
-            cudaMemcpyAsync(C, dC, batch * nn * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
-            cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, tmp.stream);
-            if (cudaStreamSynchronize(tmp.stream) != cudaSuccess) st = SGS_ECUDA;
-            else if (herr) st = SGS_ETIMEOUT;
-        }
-    }
-    cudaStreamSynchronize(tmp.stream);
-    tmp.release_all();
-    cudaStreamDestroy(tmp.stream);
-    tmp.stream = nullptr;
-    return st;
-}
 
 sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, int k, int batch, int kind,
                               double* C) {
@@ -2200,23 +2179,7 @@ sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, i
         cudaMemcpyAsync(dA, ha.data(), ha.size(), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemcpyAsync(dB, hb.data(), hb.size(), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
-        std::vector<const void*> pa, pb, pa2, pb2;
-        std::vector<void*> pc;
-        for (int b = 0; b < batch; b++) {
-            pa.push_back((const uint8_t*)dA + b * na * esz);
-            pb.push_back((const uint8_t*)dB + b * nb * esz);
-            pa2.push_back((const uint8_t*)dA + (batch + b) * na * esz);
-            pb2.push_back((const uint8_t*)dB + (batch + b) * nb * esz);
-            pc.push_back(dC + b * nc);
-        }
-        TcBatch g{};
-        g.m = m; g.n = n; g.k = k;
-        g.A = upload_ptrs(&tmp, pa); g.lda = k;
-        g.B = upload_ptrs(&tmp, pb); g.ldb = k;
-        g.A2 = upload_ptrs(&tmp, pa2); g.B2 = upload_ptrs(&tmp, pb2);
-        g.C = upload_ptrs(&tmp, pc); g.ldc = n;
-        g.alpha = 1.0; g.out_f64 = 1; g.skew = 0; g.err = err; g.batch = batch;
-        if (g_tc_tma) {
+        {
             TmaBatch t{};
             const bool bf = kind == TC_BF16, split = kind == TC_3XTF32;
             bool ok = make_operand_map(&t.ta, dA, bf, k, m, batch) && make_operand_map(&t.tb, dB, bf, k, n, batch);
@@ -2226,8 +2189,6 @@ sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, i
             t.m = m; t.n = n; t.k = k; t.alpha = 1.0; t.C = dC; t.c_stride = (long long)nc; t.ldc = n;
             t.out_f64 = 1; t.skew = 0; t.err = err; t.batch = batch;
             if (!ok || tma_product(t, kind, tmp.stream) != cudaSuccess) st = SGS_ECUDA;
-        } else if (gemm_tc(g, kind, tmp.stream) != cudaSuccess) {
-            st = SGS_ECUDA;
         }
         counted();
         int herr = 0;
@@ -2245,9 +2206,10 @@ sgs_status sgs_kernel_gemm_tc(const double* A, const double* Bt, int m, int n, i
 
 sgs_status sgs_kernel_gemm(const double* A, const double* B, const double* Cin, int m, int n, int k, int trans_a,
                            int trans_b, double alpha, double beta, double diag, int mode, int gj_k0, int gj_b,
-                           int batch, double* C) {
+                           int batch, int fp64_path, size_t emulation_scratch, double* C) {
     if (!A || !B || !C || m < 1 || n < 1 || k < 1 || batch < 1 || mode < 0 || mode > 6 || (mode & 3) > 2)
         return SGS_EINVAL;
+    if (fp64_path != SGS_FP64_EMULATED && fp64_path != SGS_FP64_FMA) return SGS_EINVAL;
     const int b_antisym = mode >> 2;            // + 4: B antisymmetric (k = n)
     mode &= 3;
     if (b_antisym && (k != n || trans_b)) return SGS_EINVAL;
@@ -2280,7 +2242,7 @@ sgs_status sgs_kernel_gemm(const double* A, const double* B, const double* Cin, 
         g.alpha = alpha; g.diag = diag; g.mode = mode; g.gj_k0 = gj_k0; g.gj_b = gj_b; g.b_antisym = b_antisym;
         if (PI) { g.Cin = (const double* const*)PI; g.ldcin = n; g.beta = beta; }
         set_kernel_attributes();
-        const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(m, n, k));
+        const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(m, n, k), fp64_path, emulation_scratch);
         if (gemm(nullptr, g, tmp.stream, -1.0, &oz, err) != cudaSuccess) st = SGS_ECUDA;
         int herr = 0;
         cudaMemcpyAsync(C, dC, batch * nc * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
@@ -2295,8 +2257,9 @@ sgs_status sgs_kernel_gemm(const double* A, const double* B, const double* Cin, 
     return st;
 }
 
-sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, double* logabsdet) {
+sgs_status sgs_kernel_inverse(const double* S, int n, int batch, int fp64_path, double* inv, double* logabsdet) {
     if (!S || !inv || n < 1 || batch < 1) return SGS_EINVAL;
+    if (fp64_path != SGS_FP64_EMULATED && fp64_path != SGS_FP64_FMA) return SGS_EINVAL;
     sgs_ctx tmp;
     cudaStreamCreateWithFlags(&tmp.stream, cudaStreamNonBlocking);
     const size_t nn = (size_t)n * n;
@@ -2312,7 +2275,7 @@ sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, do
         double **PW = upload_ptrs(&tmp, pw), **PT = upload_ptrs(&tmp, pt), **PO = upload_ptrs(&tmp, po);
         cudaMemcpyAsync(W, S, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
-        const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(n, n, bsz));
+        const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(n, n, bsz), fp64_path, 0);
         if (launch_gj(nullptr, n, batch, bsz, PW, PT, piv, ld, ds, err, 0.0, tmp.stream, &oz) != cudaSuccess)
             st = SGS_ECUDA;
         gj_perm_kernel<<<(batch + 127) / 128, 128, 0, tmp.stream>>>(piv, perm, n, batch);
@@ -2332,8 +2295,9 @@ sgs_status sgs_kernel_inverse(const double* S, int n, int batch, double* inv, do
     return st;
 }
 
-sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase, double* logabs) {
+sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, int fp64_path, double* phase, double* logabs) {
     if (!Y || !phase || !logabs || n < 2 || (n & 1) || batch < 1) return SGS_EINVAL;
+    if (fp64_path != SGS_FP64_EMULATED && fp64_path != SGS_FP64_FMA) return SGS_EINVAL;
     sgs_ctx tmp;
     cudaStreamCreateWithFlags(&tmp.stream, cudaStreamNonBlocking);
     const size_t nn = (size_t)n * n;
@@ -2364,7 +2328,7 @@ sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase,
         double **UA = upload_ptrs(&tmp, ua), **UB = upload_ptrs(&tmp, ub), **UC = upload_ptrs(&tmp, uc);
         cudaMemcpyAsync(W, planes.data(), planes.size() * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
-        const OzBuf oz = tmp_oz(tmp, (size_t)2 * batch * oz_entry_bytes(n, n, 4 * bs));
+        const OzBuf oz = tmp_oz(tmp, (size_t)2 * batch * oz_entry_bytes(n, n, 4 * bs), fp64_path, 0);
         if (launch_pf(nullptr, n, batch, bs, PY, PTU, PPK, UA, UB, UC, la, ph, err, tmp.stream, &oz) != cudaSuccess)
             st = SGS_ECUDA;
         int herr = 0;
@@ -2397,7 +2361,8 @@ sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, double* phase,
 // carve-up of the array (offsets in doubles, each a multiple of 32 = 256 bytes)
 #define SGS_STATIC_OFF_T 0                                                        // batch*n*16 doubles
 #define SGS_STATIC_OFF_PIV (SGS_STATIC_OFF_T + SGS_STATIC_MAX_BATCH_N * SGS_STATIC_PANEL)   // batch*n ints
-#define SGS_STATIC_OFF_SIGN (SGS_STATIC_OFF_PIV + SGS_STATIC_MAX_BATCH_N / 2)              // batch doubles
+#define SGS_STATIC_OFF_PERM (SGS_STATIC_OFF_PIV + SGS_STATIC_MAX_BATCH_N / 2)              // batch*n ints
+#define SGS_STATIC_OFF_SIGN (SGS_STATIC_OFF_PERM + SGS_STATIC_MAX_BATCH_N / 2)             // batch doubles
 #define SGS_STATIC_OFF_PTR (SGS_STATIC_OFF_SIGN + SGS_STATIC_MAX_BATCH_N)                  // 2*batch pointers
 #define SGS_STATIC_OFF_ERR (SGS_STATIC_OFF_PTR + 2 * SGS_STATIC_MAX_BATCH_N)               // one int
 #define SGS_STATIC_DOUBLES (SGS_STATIC_OFF_ERR + 32)                                       // ~4.9 MiB
@@ -2416,20 +2381,20 @@ __global__ void static_fill_ptrs_kernel(double* inv, double* scratch, int n, int
     T[b] = scratch + SGS_STATIC_OFF_T + (size_t)b * SGS_STATIC_PANEL * n;
 }
 
-// undo the Gauss-Jordan row interchanges in place: column swaps in reverse order
-__global__ void static_unpermute_kernel(double* inv, const int* piv, int n) {
-    const int b = blockIdx.x;
-    double* A = inv + (size_t)b * n * n;
-    const int* pv = piv + (size_t)b * n;
-    for (int j = n - 1; j >= 0; j--) {
-        const int p = pv[j];
-        if (p != j) {
-            for (int r = threadIdx.x; r < n; r += blockDim.x) {
-                double t = A[(size_t)r * n + j];
-                A[(size_t)r * n + j] = A[(size_t)r * n + p];
-                A[(size_t)r * n + p] = t;
-            }
-        }
+// undo the Gauss-Jordan row interchanges in place: with perm from gj_perm_kernel (the
+// column swaps applied in reverse order to the identity), row r of the inverse is
+// row r of the eliminated matrix gathered through perm.  Each block owns whole rows
+// (blockIdx.x, blockIdx.x + gridDim.x, ...) of matrix blockIdx.y: a row is read into
+// shared memory (n doubles) and written back permuted, both coalesced.
+__global__ void static_unpermute_kernel(double* inv, const int* perm, int n) {
+    extern __shared__ double row[];
+    const int b = blockIdx.y;
+    const int* pm = perm + (size_t)b * n;
+    for (int r = blockIdx.x; r < n; r += gridDim.x) {
+        double* A = inv + ((size_t)b * n + r) * n;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) row[c] = A[c];
+        __syncthreads();
+        for (int c = threadIdx.x; c < n; c += blockDim.x) A[c] = row[pm[c]];
         __syncthreads();
     }
 }
@@ -2461,6 +2426,7 @@ extern "C" sgs_status sgs_kernel_inverse_static(const double* S, double* inv, do
     double** W = reinterpret_cast<double**>(base + SGS_STATIC_OFF_PTR);
     double** T = W + batch;
     int* piv = reinterpret_cast<int*>(base + SGS_STATIC_OFF_PIV);
+    int* perm = reinterpret_cast<int*>(base + SGS_STATIC_OFF_PERM);
     double* dsign = base + SGS_STATIC_OFF_SIGN;
     int* err = reinterpret_cast<int*>(base + SGS_STATIC_OFF_ERR);
     // the array keeps the previous call's contents: the error word must start at 0
@@ -2471,8 +2437,10 @@ extern "C" sgs_status sgs_kernel_inverse_static(const double* S, double* inv, do
     counted();
     if (launch_gj(nullptr, n, batch, SGS_STATIC_PANEL, W, T, piv, logabsdet, dsign, err, 0.0, st) != cudaSuccess)
         return SGS_ECUDA;
-    static_unpermute_kernel<<<batch, 256, 0, st>>>(inv, piv, n);
-    counted();
+    gj_perm_kernel<<<(batch + 127) / 128, 128, 0, st>>>(piv, perm, n, batch);
+    static_unpermute_kernel<<<dim3((unsigned)std::min(n, 64), batch), 256, (size_t)n * sizeof(double), st>>>(inv, perm,
+                                                                                                      n);
+    counted(); counted();
     int herr = 0;
     if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SGS_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return SGS_ECUDA;

@@ -107,20 +107,28 @@ class ServingLoop:
             try:
                 E = self.solver.step(1)
             except Exception as e:                          # noqa: BLE001 (status carried on the error)
-                bad = self.solver.failed_instance() if hasattr(self.solver, "failed_instance") else -1
-                if getattr(e, "status", None) not in SGS_DEVICE_FAILURES or bad not in live:
+                # device-side failures of some slots: the error lists them and carries the
+                # energies of the others, which took the step
+                bad = list(getattr(e, "failed", None) or [])
+                if not bad and hasattr(self.solver, "failed_instance"):
+                    bad = [self.solver.failed_instance()]
+                E = getattr(e, "energies", None)
+                if (getattr(e, "status", None) not in SGS_DEVICE_FAILURES or not bad
+                        or any(x not in live for x in bad)):
                     raise
-                # that slot's solve failed: retire it and report it; the others took the step
-                # (their energies of this step are not available)
-                st = live.pop(bad)
-                self.solver.retire(bad)
-                req = st[0]
                 now = self.clock() - t0
-                results.append(Result(req.rid, req.arrival, st[1], now, st[2], float("nan"), False, st[4], str(e)))
-                self.failures.append(req.rid)
-                for other in live.values():
-                    other[2] += 1
-                continue
+                for slot in bad:
+                    st = live.pop(slot)
+                    self.solver.retire(slot)
+                    req = st[0]
+                    results.append(Result(req.rid, req.arrival, st[1], now, st[2], float("nan"), False, st[4],
+                                          str(e)))
+                    self.failures.append(req.rid)
+                if E is None:                               # no energies for the others: count the step
+                    for other in live.values():
+                        other[2] += 1
+                        other[3] = None
+                    continue
             now = self.clock() - t0
             for slot in list(live):
                 st = live[slot]

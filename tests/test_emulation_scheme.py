@@ -103,17 +103,19 @@ def test_group_sums_within_fp32_exact_range():
     assert KC * 2 * 2.0 ** (-7 * 8) <= 2.0 ** -46
 
 
-def test_scheme_error_against_exact_product():
-    rng = np.random.default_rng(1)
-    m, n, k = 6, 5, 40
-    A = rng.standard_normal((m, k)) * 10.0 ** rng.uniform(-4, 4, (m, 1))
-    B = rng.standard_normal((k, n)) * 10.0 ** rng.uniform(-4, 4, (1, n))
-    A[0, 3] *= 1e-12
+def scheme_product(A, B):
+    """The emulated product op(A) op(B) in exact integer arithmetic, as the kernels
+    compute it for one K chunk (K <= 512): digits under each row's and column's
+    power of two, the 36 slice products of groups G = i + j <= 7 summed per group,
+    each group sum through an fp32 accumulator, the groups combined exactly and
+    rounded once to a double."""
+    m, k = A.shape
+    n = B.shape[1]
     Ea = [max(expo_field(v) for v in A[r]) for r in range(m)]
     Eb = [max(expo_field(v) for v in B[:, c]) for c in range(n)]
     ta = [[digits(A[r, q], Ea[r]) for q in range(k)] for r in range(m)]
     tb = [[digits(B[q, c], Eb[c]) for q in range(k)] for c in range(n)]
-    u = 2.0 ** -53
+    C = np.zeros((m, n))
     for r in range(m):
         for c in range(n):
             acc = [sum(ta[r][q][i] * tb[c][q][G - i] for q in range(k) for i in range(G + 1)) for G in range(8)]
@@ -121,10 +123,77 @@ def test_scheme_error_against_exact_product():
             hi = ((acc[0] * 128 + acc[1]) * 128 + acc[2]) * 128 + acc[3]
             lo = ((acc[4] * 128 + acc[5]) * 128 + acc[6]) * 128 + acc[7]
             t = float(Fraction(hi) * 2 ** 28 + lo)                   # one rounding
-            val = t * 2.0 ** (Ea[r] + Eb[c] - 2107)
-            exact = sum(Fraction(float(A[r, q])) * Fraction(float(B[q, c])) for q in range(k))
-            bound = 4 * u * float(np.abs(A[r]) @ np.abs(B[:, c]))
-            assert abs(Fraction(val) - exact) <= Fraction(bound), (r, c)
+            C[r, c] = t * 2.0 ** (Ea[r] + Eb[c] - 2107)
+    return C
+
+
+def _exact_product(A, B):
+    return [[sum(Fraction(float(A[r, q])) * Fraction(float(B[q, c])) for q in range(A.shape[1]))
+             for c in range(B.shape[1])] for r in range(A.shape[0])]
+
+
+def normwise_bound(A, B, exact):
+    """|C_ij - (AB)_ij| <= u |(AB)_ij| + K 2^-52 max_k |A_ik| max_k |B_kj| (one K chunk)."""
+    k = A.shape[1]
+    ra = np.abs(A).max(axis=1)
+    cb = np.abs(B).max(axis=0)
+    return [[Fraction(2.0 ** -53) * abs(exact[r][c]) + Fraction(k * 2.0 ** -52 * float(ra[r] * cb[c]))
+             for c in range(B.shape[1])] for r in range(A.shape[0])]
+
+
+def test_scheme_error_against_exact_product():
+    rng = np.random.default_rng(1)
+    m, n, k = 6, 5, 40
+    A = rng.standard_normal((m, k)) * 10.0 ** rng.uniform(-4, 4, (m, 1))
+    B = rng.standard_normal((k, n)) * 10.0 ** rng.uniform(-4, 4, (1, n))
+    A[0, 3] *= 1e-12
+    C = scheme_product(A, B)
+    exact = _exact_product(A, B)
+    bound = normwise_bound(A, B, exact)
+    for r in range(m):
+        for c in range(n):
+            assert abs(Fraction(C[r, c]) - exact[r][c]) <= bound[r][c], (r, c)
+
+
+def test_uneven_row_exceeds_the_elementwise_bound_and_meets_the_normwise_one():
+    """a = [1, 1.23e-9] against b = [0, 1]: the exact product is the small entry
+    alone, which the row's scale keeps to 2^-57 of 1 only.  The error is far above
+    the elementwise bound 4 u |a||b| of an FP64 dot product and within the normwise
+    bound of the scheme."""
+    A = np.array([[1.0, 1.23e-9]])
+    B = np.array([[0.0], [1.0]])
+    C = scheme_product(A, B)
+    exact = _exact_product(A, B)
+    err = abs(Fraction(C[0, 0]) - exact[0][0])
+    assert err > 1e6 * Fraction(4 * 2.0 ** -53 * 1.23e-9)
+    assert err <= normwise_bound(A, B, exact)[0][0]
+
+
+def test_normwise_bound_on_adversarial_operands():
+    """Rows with one entry of order one and the rest spread over 1e-3 .. 1e-15,
+    columns that zero or keep the large entry, K up to 512 (one chunk, where the
+    fp32 group sums of G = 6 can exceed 2^24 and round): the bound holds and is
+    within a modest factor of the error for the worst element."""
+    rng = np.random.default_rng(6)
+    worst = 0.0
+    for k in (3, 64, 512):
+        m, n = 3, 3
+        A = rng.standard_normal((m, k)) * 10.0 ** rng.uniform(-15, -3, (m, k))
+        A[:, 0] = rng.uniform(1.0, 2.0, m)
+        B = rng.standard_normal((k, n)) * 10.0 ** rng.uniform(-15, 0, (k, n))
+        B[0, 0] = 0.0
+        if k == 512:                     # all-maximal digits: the fp32 group sums round
+            A[1] = 2.0 - 2.0 ** -52
+            B[:, 2] = -(2.0 - 2.0 ** -52)
+        C = scheme_product(A, B)
+        exact = _exact_product(A, B)
+        bound = normwise_bound(A, B, exact)
+        for r in range(m):
+            for c in range(n):
+                err = abs(Fraction(C[r, c]) - exact[r][c])
+                assert err <= bound[r][c], (k, r, c)
+                worst = max(worst, float(err / bound[r][c]))
+    assert worst > 1e-3
 
 
 def _to_double(hi, lo, e, neg):

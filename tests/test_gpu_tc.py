@@ -30,62 +30,20 @@ def test_tc_gemm_matches_numpy(pkg, kind, m, n, k, batch):
     assert np.abs(ref).max() > 0 and np.abs(C - ref).max() < 0.05 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2])
-def test_tma_and_cp_async_staging_agree(pkg, kind):
-    """The TMA-fed kernel (128-byte swizzle, mbarrier pipeline) and the
-    cp.async-fed one issue the same MMA sequence: identical results, ragged
-    tiles and K tails included."""
-    rng = np.random.default_rng(kind + 5)
-    A = rng.standard_normal((3, 300, 104))
-    B = rng.standard_normal((3, 104, 200))
-    pkg.set_tc_loader(True)
-    C1 = pkg.batched_gemm_tc(A, B, kind)
-    pkg.set_tc_loader(False)
-    try:
-        C2 = pkg.batched_gemm_tc(A, B, kind)
-    finally:
-        pkg.set_tc_loader(True)
-    assert np.array_equal(C1, C2)
-    assert np.all(np.abs(C1 - A @ B) <= BOUND[kind] * (np.abs(A) @ np.abs(B)) + 1e-30)
-
-
-@pytest.mark.parametrize("kind", [0, 1, 2])
-def test_persistent_tma_kernel_agrees(pkg, kind):
-    """The persistent form (one CTA per SM looping over tiles, two TMEM
-    accumulators) gives the one-tile-per-CTA results bit for bit: 240 ragged
-    tiles over 152 SMs, so CTAs take one or two tiles and both accumulators."""
-    rng = np.random.default_rng(kind + 11)
-    A = rng.standard_normal((40, 300, 136))
-    B = rng.standard_normal((40, 136, 200))
-    pkg.set_tc_loader(True)
-    C1 = pkg.batched_gemm_tc(A, B, kind)
-    pkg.set_tc_loader(True, persistent=True)
-    try:
-        C2 = pkg.batched_gemm_tc(A, B, kind)
-    finally:
-        pkg.set_tc_loader(True)
-    assert np.array_equal(C1, C2)
-    assert np.all(np.abs(C1 - A @ B) <= BOUND[kind] * (np.abs(A) @ np.abs(B)) + 1e-30)
-
-
 @pytest.mark.parametrize("prec", [1, 2, 3])
-def test_mixed_step_identical_under_both_stagings(pkg, prec):
-    """The loader switch applies to the equation of motion's products (and the
-    persistent form to the state update's TMA-fed products too).  All three
-    stagings give identical steps."""
+def test_mixed_step_is_deterministic(pkg, prec):
+    """The tensor-core products have a fixed reduction order: two runs of the same
+    mixed-precision steps (ragged 128-tiles at n = 164) agree bit for bit."""
     import sgs_inputs as inp
-    p = inp.AndersonParams(n_bath=40, U=4.0, eps_d=-2.0, V=0.5)        # n = 164: ragged 128-tiles
+    p = inp.AndersonParams(n_bath=40, U=4.0, eps_d=-2.0, V=0.5)
     rng = np.random.default_rng(3)
     g = inp.clustered_pure_gammas(p.n_modes, 5, rng, 1, spread=1.0)
     m = pkg.build_anderson(p.n_bath, p.U, p.eps_d, p.V)
     out = []
-    for tma, pers in ((True, False), (False, False), (True, True)):
-        pkg.set_tc_loader(tma, persistent=pers)
+    for _ in range(2):
         s = pkg.Solver(m, g, None, precision=prec)
         E = s.step(2)
         out.append((E, s.derivative(), s.get_state()[0]))
         s.close()
-    pkg.set_tc_loader(True)
-    for other in out[1:]:
-        for x, y in zip(out[0], other):
-            assert np.array_equal(x, y)
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)

@@ -120,3 +120,39 @@ def test_failed_solve_is_retired_and_reported():
     assert ("retire", 1, bad.finished) in s.log
     for r in (res[0], res[2]):                      # the others finish normally
         assert r.converged and not r.failed and abs(r.energy - (1.0 + r.rid)) < 1e-5
+
+
+class TwoFailSolver(FakeSolver):
+    """Slots 0 and 2 fail in the same step (their second); the error carries the
+    other slots' energies of that step, as Solver.step's does."""
+
+    def __init__(self, clock):
+        super().__init__(clock, capacity=4)
+
+    def step(self, n):
+        if len(self.slots) > 2 and self.live[0] and self.live[2] and self.slots[0][1] == 1:
+            E = super().step(n)
+            E[[0, 2], 0] = np.nan
+            e = RuntimeError("SGS_ESINGULAR: instance 0: ... (and 1 more failed instance(s))")
+            e.status = 3
+            e.failed = [0, 2]
+            e.energies = E
+            raise e
+        return super().step(n)
+
+
+def test_two_slots_failing_in_one_step():
+    clk = FakeClock()
+    s = TwoFailSolver(clk)
+    loop = ServingLoop(s, tol=1e-6, max_steps=100, clock=clk, sleep=clk.sleep, keep_energies=True)
+    res = loop.run(_reqs([0.0, 0.0, 0.0, 0.0]))
+    assert sorted(loop.failures) == [0, 2]
+    for r in (res[0], res[2]):
+        assert r.failed.startswith("SGS_ESINGULAR") and np.isnan(r.energy)
+        assert ("retire", r.rid, r.finished) in s.log
+    for r in (res[1], res[3]):
+        # the healthy slots keep the energy of the failing step: consecutive energies, one per step
+        assert r.converged and not r.failed
+        assert len(r.energies) == r.steps
+        k = np.arange(1, r.steps + 1)
+        assert np.allclose(r.energies, (1.0 + r.rid) * (1.0 - 0.5 ** k))
