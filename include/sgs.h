@@ -129,6 +129,8 @@ typedef struct {
     int fp64_path;           /* sgs_fp64_path of this instance's FP64 products (0: emulated) */
     size_t emulation_scratch;/* SGS_FP64_EMULATED: bytes of operand-slice scratch this instance
                                 owns (0: 2 GiB; at least 1 MiB); larger batches run in chunks */
+    int shard_rank;          /* pair sharding (sgs_shard_pairs): this rank of shard_world; */
+    int shard_world;         /*   shard_world <= 1: not sharded */
 } sgs_options;
 
 /* Create a context holding n_instances independent problems (models[i],
@@ -240,6 +242,37 @@ typedef enum {
     SGS_CORR_RENYI2 = 2          /* S_2 of the impurity plus the first l sites (App. B); sites[i] = l */
 } sgs_corr_kind;
 
+/* Pair-sharded step: one problem over several ranks (one GPU each).  The
+ * pairs are independent units (Sec. III C), so an instance admitted with
+ * shard_world = W > 1 holds the pairs whose index in the order (0, 1),
+ * (0, 2), ..., (M - 2, M - 1) is shard_rank modulo W, and adds the own
+ * (beta = mu) terms of the states mu with mu modulo W = shard_rank.  Every
+ * rank holds all M states.  One step is three calls with two sums over the
+ * ranks between them, which the caller makes (e.g. an all-reduce):
+ *   1. sgs_shard_pairs(ctx, i, gh): the pair pass (A1-A5) over this rank's
+ *      pairs; writes this rank's share of G and h to gh = [G | h], each
+ *      [M][M] complex (re, im), zero where another rank holds the pair.
+ *      Summed over the ranks, gh is the whole (G, h).
+ *   2. sgs_shard_eom(ctx, i, gh, dgamma, energy): takes the summed gh, solves
+ *      the amplitudes (the same solve on every rank), writes the energy E of
+ *      the states (host double, may be NULL) and this rank's share of
+ *      dGamma/ds to dgamma ([M][n][n]): the terms of its pairs and of its own
+ *      states (Eq. EOM-Gamma3 is linear in them).  Summed over the ranks,
+ *      dgamma is dGamma/ds.
+ *   3. sgs_shard_update(ctx, i, dgamma): takes the summed dgamma and applies
+ *      the orthogonal update and re-purification to every state (App. A), the
+ *      same on every rank, so the states stay equal across ranks without
+ *      another exchange.
+ * gh and dgamma may be host or device pointers (copies by cudaMemcpyDefault);
+ * device buffers on the context's device let the sums run as NCCL
+ * collectives.  A sharded instance does not step through sgs_step or
+ * sgs_energy (SGS_EINVAL if one is live in the context) and has no
+ * observables or rank growth.  Results equal the unsharded step's up to the
+ * order of the sums.  Errors as sgs_step. */
+sgs_status sgs_shard_pairs(sgs_ctx* ctx, int instance, double* gh);
+sgs_status sgs_shard_eom(sgs_ctx* ctx, int instance, const double* gh, double* dgamma, double* energy);
+sgs_status sgs_shard_update(sgs_ctx* ctx, int instance, const double* dgamma);
+
 /* Observables of the current SGS state of one instance, evaluated on its
  * current covariance matrices with optimal amplitudes (a pair pass runs
  * first; the states are not changed).  out: [n_sites].  Sites are spinful
@@ -335,6 +368,16 @@ int sgs_build_anderson(int n_bath, int n_channels, double U, double eps_d, doubl
  * quartic monomials of H_J (idx [24][4], val [24]) and e_const (0).  Returns
  * the number of modes N = 4L, or -1 on bad arguments (L < 2). */
 int sgs_build_2ck(int L, double J, double t, double* A, int* quartic_idx, double* quartic_val, double* e_const);
+
+/* Failure path of the library's bounded device waits.  Every wait of its
+ * kernels (the tensor-core pipelines' mbarrier waits, 2 s) gives up after a
+ * time limit: the kernel sets an error bit, drains its own work in flight and
+ * returns, and the call reports SGS_ETIMEOUT with the context still usable.
+ * This probe runs that wait on its own on a device flag that nothing sets,
+ * with limit_ns (1e3 .. 1e10) in place of 2 s: it returns SGS_ETIMEOUT when
+ * the wait ran out as it should, and the device time of the launch in
+ * *elapsed_ms (may be NULL).  SGS_EINVAL for a limit out of range. */
+sgs_status sgs_probe_wait(unsigned long long limit_ns, double* elapsed_ms);
 
 /* Shared-memory set-up of the current device.  Kernels that keep large tiles in
  * shared memory need their dynamic limit raised once per device, with that

@@ -357,7 +357,19 @@ def coupling_constants(G, lam, mode=C_INVERSE, tiny=1e-300):
     return lt, c
 
 
-def eom(model, gammas, G, h, E, lam, mode=C_INVERSE, mus=None):
+def eom_term(model, gammas, G, h, E, lam, mu, beta):
+    """The beta term of the sum of Eq. (EOM-Gamma3) for receiver mu,
+    lambda_beta [ 2i G_mu,beta [D, F] + 2 G_mu,beta (D F D + F) - (h_mu,beta - E G_mu,beta) D ],
+    with D = Delta^{beta,mu}, F = F^{beta,mu} and Delta^{mu,mu} = Gamma^mu (Sec. III B)."""
+    D = gammas[mu].astype(np.complex128) if beta == mu else transition_matrix(gammas[beta], gammas[mu])
+    F = fock_matrix(model, D)
+    term = (2j * G[mu, beta] * (D @ F - F @ D)
+            + 2.0 * G[mu, beta] * (D @ F @ D + F)
+            - (h[mu, beta] - E * G[mu, beta]) * D)
+    return lam[beta] * term
+
+
+def eom(model, gammas, G, h, E, lam, mode=C_INVERSE, mus=None, betas=None):
     """d Gamma^mu / ds of Eq. (EOM-Gamma3), for every state mu:
 
     2 Re{ lt_mu^* c_mu sum_beta lambda_beta [ 2i G_mu,beta [D, F]
@@ -365,20 +377,17 @@ def eom(model, gammas, G, h, E, lam, mode=C_INVERSE, mus=None):
 
     with D = Delta^{beta,mu}, F = F^{beta,mu}; "+ c.c." of the paper is
     X + X^* = 2 Re X.  Delta^{mu,mu} = Gamma^mu (Sec. III B).  ``mus``: the
-    states to evaluate (default all).
+    states to evaluate (default all).  ``betas(mu)``: the terms of the sum to
+    take (default all beta); the expression is linear in them, so sums over a
+    partition of the beta add up to the whole.
     """
     M = len(gammas)
     lt, c = coupling_constants(G, lam, mode)
     out = []
     for mu in (range(M) if mus is None else mus):
         acc = np.zeros((model.n, model.n), dtype=np.complex128)
-        for beta in range(M):
-            D = gammas[mu].astype(np.complex128) if beta == mu else transition_matrix(gammas[beta], gammas[mu])
-            F = fock_matrix(model, D)
-            term = (2j * G[mu, beta] * (D @ F - F @ D)
-                    + 2.0 * G[mu, beta] * (D @ F @ D + F)
-                    - (h[mu, beta] - E * G[mu, beta]) * D)
-            acc += lam[beta] * term
+        for beta in (range(M) if betas is None else betas(mu)):
+            acc += eom_term(model, gammas, G, h, E, lam, mu, beta)
         out.append(2.0 * np.real(np.conj(lt[mu]) * c[mu] * acc))
     return out
 

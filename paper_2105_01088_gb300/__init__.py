@@ -44,7 +44,7 @@ class _Options(ctypes.Structure):
                 ("cmode", ctypes.c_int), ("parity", ctypes.c_int), ("gamma0", ctypes.POINTER(ctypes.c_double)),
                 ("lambda0", ctypes.POINTER(ctypes.c_double)), ("stream", ctypes.c_void_p),
                 ("integrator", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("fp64_path", ctypes.c_int),
-                ("emulation_scratch", ctypes.c_size_t)]
+                ("emulation_scratch", ctypes.c_size_t), ("shard_rank", ctypes.c_int), ("shard_world", ctypes.c_int)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -73,6 +73,9 @@ SIGNATURES = {
     "sgs_set_panel_widths": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "sgs_set_graphs": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "sgs_energy": (ctypes.c_int, [_ctxp, _dp]),
+    "sgs_shard_pairs": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_void_p]),
+    "sgs_shard_eom": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, _dp]),
+    "sgs_shard_update": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_void_p]),
     "sgs_correlator": (ctypes.c_int, [_ctxp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _dp]),
     "sgs_variance": (ctypes.c_int, [_ctxp, ctypes.c_int, _dp, _dp]),
     "sgs_free": (None, [_ctxp]),
@@ -89,6 +92,7 @@ SIGNATURES = {
     "sgs_get_profile": (ctypes.c_int, [_ctxp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]),
     "sgs_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
     "sgs_kernel_smem_limits": (ctypes.c_int, [ctypes.c_int, _ip, _ip]),
+    "sgs_probe_wait": (ctypes.c_int, [ctypes.c_ulonglong, _dp]),
     "sgs_kernel_inverse": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_pfaffian": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]),
     "sgs_kernel_gemm": (ctypes.c_int, [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -281,11 +285,13 @@ class Solver:
         return len(self.shapes)
 
     def admit(self, model, gamma0, lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE, parity=1,
-              integrator=SGS_INTEGRATOR_EXP, rank=None, seed=0, fp64_path=None, emulation_scratch=None):
+              integrator=SGS_INTEGRATOR_EXP, rank=None, seed=0, fp64_path=None, emulation_scratch=None,
+              shard=(0, 1)):
         """Add one problem; returns its slot.  gamma0 None: seeded random states of
         the given rank, generated by the library.  fp64_path / emulation_scratch:
-        None takes the solver's.  Raises SGSError(SGS_ENOMEM) if it does not fit the
-        HBM budget (nothing is allocated then)."""
+        None takes the solver's.  shard = (rank, world): this rank's share of a
+        pair-sharded step (sharded.py).  Raises SGSError(SGS_ENOMEM) if it does not
+        fit the HBM budget (nothing is allocated then)."""
         _check_slot_args(model, gamma0, parity, rank)
         g = None if gamma0 is None else np.ascontiguousarray(gamma0, dtype=np.float64)
         M = rank if g is None else g.shape[0]
@@ -297,7 +303,7 @@ class Solver:
         path = self.fp64_path if fp64_path is None else int(fp64_path)
         scratch = self.emulation_scratch if emulation_scratch is None else int(emulation_scratch)
         opt = _Options(M, dtau, precision, cmode, parity, _ptr(g), _ptr(lam), None, integrator, int(seed), path,
-                       scratch)
+                       scratch, int(shard[0]), int(shard[1]))
         slot = ctypes.c_int(-1)
         st = _lib.sgs_admit(self._ctx, ctypes.byref(mod), ctypes.byref(opt), ctypes.byref(slot))
         if st != 0:
@@ -369,6 +375,22 @@ class Solver:
             err.failed = self.failed_instances()
             raise err
         return E
+
+    def shard_pairs(self, gh_ptr, slot=0):
+        """Stage 1 of a pair-sharded step: this rank's share of [G | h] into gh_ptr."""
+        self._check(_lib.sgs_shard_pairs(self._ctx, slot, ctypes.c_void_p(gh_ptr)))
+
+    def shard_eom(self, gh_ptr, dgamma_ptr, slot=0):
+        """Stage 2: amplitudes from the summed gh, this rank's share of dGamma/ds into
+        dgamma_ptr; returns the energy."""
+        e = np.zeros(1)
+        self._check(_lib.sgs_shard_eom(self._ctx, slot, ctypes.c_void_p(gh_ptr), ctypes.c_void_p(dgamma_ptr),
+                                       _ptr(e)))
+        return float(e[0])
+
+    def shard_update(self, dgamma_ptr, slot=0):
+        """Stage 3: the update of every state from the summed dGamma/ds."""
+        self._check(_lib.sgs_shard_update(self._ctx, slot, ctypes.c_void_p(dgamma_ptr)))
 
     def set_graphs(self, enable=True):
         """Replay a captured CUDA graph of one step (default on)."""
@@ -446,6 +468,13 @@ class Solver:
 
 
 # ------------------------------------------------------------ building blocks
+
+def probe_wait(limit_ns):
+    """Run the bounded device wait on a flag nothing sets; returns (status, device ms)."""
+    ms = np.zeros(1)
+    st = _lib.sgs_probe_wait(int(limit_ns), _ptr(ms))
+    return int(st), float(ms[0])
+
 
 def smem_limits():
     """[(dynamic shared-memory limit in force, opt-in maximum less static shared

@@ -30,7 +30,9 @@ namespace sgs {
 // eom_pairs_kernel forms D (into dGamma) and T, six FMAs per pair and element;
 // eom_finish_kernel adds the sparse part, the beta = mu term and the impurity terms.
 
-// weights w0..w5 of one (mu, beta != mu) and the pair index, into shared memory
+// weights w0..w5 of one (mu, beta != mu) and the pair index, into shared memory; a pair
+// this instance does not hold (index -1: another rank's share of a pair-sharded step)
+// contributes nothing here
 template <typename R>
 __device__ __forceinline__ void eom_weights(const InstDev& d, const double* coef, const int* pair_index, int mu,
                                             R* sw, int* sp) {
@@ -38,6 +40,7 @@ __device__ __forceinline__ void eom_weights(const InstDev& d, const double* coef
     for (int be = threadIdx.x; be < M; be += blockDim.x) {
         if (be == mu) { sp[be] = -1; continue; }
         const int p = pair_index[mu * M + be];
+        if (p < 0) { sp[be] = -1; continue; }
         const double sgn = (d.pa[p] == mu) ? -1.0 : 1.0;     // receiver a: complex conjugate
         const double* co = coef + (size_t)(mu * M + be) * 6;
         sw[6 * be + 0] = (R)(-4.0 * co[0]);
@@ -86,11 +89,13 @@ __global__ void __launch_bounds__(256) eom_pairs_kernel(InstDev d, const double*
     }
 }
 
+// self_mask (may be nullptr): state mu's beta = mu term is added only where self_mask[mu] != 0
+// (a pair-sharded step adds it on one rank, so that the ranks' partial sums add up to dGamma)
 template <typename R>
 __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double* si, const double* imd,
                                                          const double* fimp, const double* fimp_state,
                                                          const double* gfg, const double* coef, const int* pair_index,
-                                                         const double* tsum, double* dgamma) {
+                                                         const double* tsum, double* dgamma, const int* self_mask) {
     extern __shared__ double eom_sraw[];
     __shared__ R s_w2;
     const int mu = blockIdx.y;
@@ -107,6 +112,7 @@ __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double
     }
     __syncthreads();
     const size_t N = nn(d);
+    const bool self_term = self_mask == nullptr || self_mask[mu] != 0;
     const double* gm = d.gamma + (size_t)mu * N;
     const double* fs = fimp_state + (size_t)mu * ni * ni;
     const double* gfgm = gfg + (size_t)mu * N;
@@ -124,7 +130,7 @@ __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double
         // the pairs' commutator terms against A: -(T A^T)_kl - (A T)_kl
         for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) acc = fma(-(R)T[(size_t)k * n + d.a_col[q]], (R)d.a_val[q], acc);
         for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) acc = fma(-(R)d.a_val[q], (R)T[(size_t)d.a_col[q] * n + l], acc);
-        {   // beta = mu: Delta = Gamma_mu, Delta F Delta = Gamma F Gamma
+        if (self_term) {   // beta = mu: Delta = Gamma_mu, Delta F Delta = Gamma F Gamma
             const double* co = coef + (size_t)(mu * M + mu) * 6;
             const R g = (R)gm[e];
             const R f = akl + ((sk >= 0 && sl >= 0) ? (R)fs[sk * ni + sl] : (R)0);

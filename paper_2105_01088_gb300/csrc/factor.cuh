@@ -196,6 +196,19 @@ __global__ void __launch_bounds__(512) gj_panel_kernel(GJPanelArgs a) {
     gj_panel_finish(a, W, b, panel, n * ps, s_piv, s_pabs, s_rows, s_src, &s_nr, &s_logdet, &s_sign);
 }
 
+// Rows p0 .. p0 + K - 1, columns t0 .. t0 + w - 1 of every W into T (K x w, row stride w):
+// the pivot rows of the target columns of a delayed Gauss-Jordan update, taken before the
+// update overwrites them.  Reads and writes run along the rows.
+__global__ void gj_gather_rows_kernel(double* const* W, double* const* T, int n, int p0, int K, int t0, int w) {
+    const double* src = W[blockIdx.y];
+    double* dst = T[blockIdx.y];
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)K * w;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / w), q = (int)(e % w);
+        dst[e] = src[(size_t)(p0 + k) * n + t0 + q];
+    }
+}
+
 // Undo the row interchanges of Gauss-Jordan: inverse = X P, i.e. the column
 // interchanges applied in reverse order.  perm[c] = source column of column c.
 __global__ void gj_perm_kernel(const int* piv, int* perm, int n, int batch) {

@@ -13,7 +13,8 @@
 // Output modes: FULL; SKEW (only lower tiles computed, each written to
 // C[r][c] and -C[c][r], zero diagonal: used where the product is skew by
 // construction); GJ (Gauss-Jordan delayed update: rows inside the panel
-// start from 0, columns inside the panel are not written).
+// start from 0, and unless gj_cols = 0 columns inside the panel are not
+// written).
 #pragma once
 #include "common.cuh"
 
@@ -35,6 +36,8 @@ struct GemmBatch {
     const int* active_flag;              // optional: batch b computes only if active_flag[b] > active_cmp
     int active_cmp;                      //   otherwise C = Cin (pass-through)
     int mode; int gj_k0; int gj_b;
+    int gj_cols;                         // GJ: 1 = output columns gj_k0 .. gj_k0 + gj_b - 1 not written
+                                         //     (the panel's own), 0 = every output column written
     int batch;
     int b_antisym;                       // hint: B (and B2) antisymmetric, op(B)'s columns = -B's rows
     long long offBr;                     // (emulated products) offset of op(B)'s K range in B's rows
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
                 if (g.mode == GEMM_FULL) {
                     Cb[(long long)r * g.ldc + c] = v;
                 } else if (g.mode == GEMM_GJ) {
-                    if (c < g.gj_k0 || c >= g.gj_k0 + g.gj_b) Cb[(long long)r * g.ldc + c] = v;
+                    if (!g.gj_cols || c < g.gj_k0 || c >= g.gj_k0 + g.gj_b) Cb[(long long)r * g.ldc + c] = v;
                 } else {  // SKEW
                     if (tm == tn && r <= c) {
                         if (r == c) Cb[(long long)r * g.ldc + c] = 0.0;
@@ -226,6 +229,7 @@ inline GemmBatch gemm_defaults() {
     GemmBatch g{};
     g.alpha = 1.0; g.beta = 0.0; g.diag = 0.0; g.sA2 = 0.0; g.sB2 = 0.0; g.Cin2 = nullptr; g.beta2 = 0.0;
     g.mode = GEMM_FULL; g.active_flag = nullptr; g.alpha_b = nullptr; g.active_cmp = 0; g.b_antisym = 0;
+    g.gj_cols = 1;
     return g;
 }
 

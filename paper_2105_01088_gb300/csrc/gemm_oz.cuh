@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
             auto emit = [&](int rr, int cc, int r, int c, double v) {
                 if (skew && r == c) v = 0.0;
                 if (keep_tile) tile[rr * TS + cc] = v;
-                if (!gj || c < g.gj_k0 || c >= g.gj_k0 + g.gj_b) Cb[(long long)r * g.ldc + c] = v;
+                if (!gj || !g.gj_cols || c < g.gj_k0 || c >= g.gj_k0 + g.gj_b) Cb[(long long)r * g.ldc + c] = v;
             };
             // The common forms get loops of their own, so that no FP64 instruction is issued where
             // none is needed (FP64 issues at a small fraction of the integer rate on this part):
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
                 asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
                 const int c = n0 + tid, rr = c - m0;
                 if (tid < BN && rr >= 0 && rr < OZ_BM && c < g.m && c < g.n &&
-                    (!gj || c < g.gj_k0 || c >= g.gj_k0 + g.gj_b))
+                    (!gj || !g.gj_cols || c < g.gj_k0 || c >= g.gj_k0 + g.gj_b))
                     Cb[(long long)c * g.ldc + c] = tile[rr * TS + tid] + g.diag;
             }
             if (skew) {

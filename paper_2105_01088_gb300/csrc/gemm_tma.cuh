@@ -78,19 +78,7 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
 // bounded wait that also gives up as soon as another CTA has recorded a timeout (so a
 // failing launch drains quickly); used only where giving up leaves nothing in flight
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, int* err) {
-    const uint64_t t0 = global_ns();
-    for (uint32_t it = 0;; it++) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.b32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
-        if ((it & 255u) == 255u) {
-            if (*(volatile int*)err & SGS_DEV_TC_TIMEOUT) return false;
-            if (global_ns() - t0 > 2000000000ull) break;
-        }
-    }
-    atomicOr(err, SGS_DEV_TC_TIMEOUT);
-    return false;
+    return bounded_wait([&] { return mbar_try_wait(bar, parity); }, SGS_WAIT_LIMIT_NS, err, true);
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {

@@ -63,6 +63,8 @@ struct Instance {
     double dtau = 0.0, e_const = 0.0;
     int prec = 0, cmode = 0, parity = 1, integrator = 0;
     int fp64_path = SGS_FP64_EMULATED;  // arithmetic of the FP64 products (sgs_fp64_path)
+    int shard_rank = 0, shard_world = 1; // pair sharding: this instance holds pairs p % world == rank
+    int* self_mask = nullptr;           // sharded: [M], 1 where this rank adds state mu's own term
     size_t oz_cap = 0;                  // emulated products: slice scratch cap (bytes)
     int gj_b = 32, pf_bs = 16;          // panel widths of the Gauss-Jordan inverse and the Pfaffian
     int gj_cap = 32, pf_cap = 16;       // widest widths the scratch holds
@@ -132,6 +134,7 @@ struct Instance {
          **q_wr32 = nullptr, **q_va32 = nullptr, **q_xa32 = nullptr;
 
     // pointer arrays (device)
+    double **p_tup = nullptr;           // recursive Gauss-Jordan: pivot rows of an update (second half of work)
     double **p_work = nullptr, **p_tbuf = nullptr, **p_si = nullptr, **p_imd = nullptr, **p_wr = nullptr,
            **p_va = nullptr, **p_xa = nullptr, **p_ga = nullptr, **p_gb = nullptr;
     double **p_Y = nullptr, **p_TU = nullptr, **p_pack = nullptr;
@@ -398,7 +401,6 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.N = m.n_modes;
     I.n = n;
     I.M = o.rank;
-    I.P = o.rank * (o.rank - 1) / 2;
     I.dtau = o.dtau;
     I.prec = o.precision;
     I.cmode = o.cmode;
@@ -406,6 +408,8 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.integrator = o.integrator;
     I.fp64_path = o.fp64_path;
     I.oz_cap = oz_cap_of(o.emulation_scratch);
+    I.shard_world = o.shard_world > 1 ? o.shard_world : 1;
+    I.shard_rank = I.shard_world > 1 ? o.shard_rank : 0;
     I.e_const = m.e_const;
     I.hA.assign(m.A, m.A + (size_t)n * n);
     I.hq_idx.assign(m.quartic_idx, m.quartic_idx + (m.n_quartic > 0 ? 4 * m.n_quartic : 0));
@@ -476,16 +480,23 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     std::vector<int> slot(n, -1);
     for (int j = 0; j < I.nimp; j++) slot[impv[j]] = j;
 
-    // pairs
-    const int M = I.M, P = I.P;
-    std::vector<int> pa, pb, pair_pf(std::max(P, 1), -1), pf_pair, pidx((size_t)M * M, -1);
+    // pairs (a, b), a < b, in the order (0, 1), (0, 2), ..., (M - 2, M - 1); a sharded instance
+    // holds the pairs whose index in that order is rank modulo world
+    const int M = I.M;
+    std::vector<int> pa, pb, pair_pf, pf_pair, pidx((size_t)M * M, -1);
+    int gp = 0;
     for (int a = 0; a < M; a++)
-        for (int b = a + 1; b < M; b++) {
+        for (int b = a + 1; b < M; b++, gp++) {
+            if (gp % I.shard_world != I.shard_rank) continue;
             int p = (int)pa.size();
             pa.push_back(a); pb.push_back(b);
             pidx[a * M + b] = pidx[b * M + a] = p;
+            pair_pf.push_back(-1);
             if (a >= 1) { pair_pf[p] = (int)pf_pair.size(); pf_pair.push_back(p); }
         }
+    I.P = (int)pa.size();
+    const int P = I.P;
+    if (pair_pf.empty()) pair_pf.push_back(-1);
     I.Ppf = (int)pf_pair.size();
     I.h_pa = pa;
     I.h_pb = pb;
@@ -523,6 +534,13 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.Ecur = c->alloc<double>(1);
     I.eigscratch = c->alloc<double>(6 * (size_t)(2 * M) * (2 * M) + 8 * 2 * M);
     I.err = c->alloc<int>(1);
+    if (I.shard_world > 1) {
+        I.self_mask = c->alloc<int>(M);
+        if (!I.self_mask) { c->err = "device allocation failed"; return SGS_ENOMEM; }
+        std::vector<int> mask(M);
+        for (int mu = 0; mu < M; mu++) mask[mu] = (mu % I.shard_world == I.shard_rank) ? 1 : 0;
+        CUDA_TRY(c, cudaMemcpyAsync(I.self_mask, mask.data(), M * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    }
     void* check[] = {I.gamma, I.dgamma, I.work, I.si, I.imd, I.wr, I.va, I.xa, I.tbuf, I.pfTU, I.pfpack, I.s[0],
                      I.s[1], I.s[2], I.s[3], I.s[4], I.eigscratch, I.err, I.lr, I.fimp};
     for (void* p : check)
@@ -576,6 +594,9 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         gb.push_back(I.gamma + pb[p] * nn);
     }
     if (P > 0) {
+        std::vector<double*> tup;
+        for (int p = 0; p < P; p++) tup.push_back(I.work + (size_t)P * nn + (size_t)p * nn);
+        I.p_tup = upload_ptrs(c, tup);
         I.p_work = upload_ptrs(c, w); I.p_si = upload_ptrs(c, s_);
         I.p_imd = upload_ptrs(c, im); I.p_wr = upload_ptrs(c, wr); I.p_va = upload_ptrs(c, va);
         I.p_xa = upload_ptrs(c, xa); I.p_ga = upload_ptrs(c, ga); I.p_gb = upload_ptrs(c, gb);
@@ -760,6 +781,55 @@ cudaError_t launch_gj(sgs_ctx* c, int n, int batch, int bsz, double** W, double*
     return cudaGetLastError();
 }
 
+// The delayed Gauss-Jordan update of target columns t0 .. t0 + w - 1 by the eliminated columns
+// p0 .. p0 + K - 1 (their pivot rows p0 .. p0 + K - 1): W[:, t] <- W[:, p] T + W[:, t] with the
+// pivot rows replaced rather than added to, T = the target columns' pivot rows before the update.
+cudaError_t gj_update(sgs_ctx* c, int n, int batch, double** W, double** Tup, int p0, int K, int t0, int w,
+                      cudaStream_t st, const OzBuf* oz, int* err) {
+    gj_gather_rows_kernel<<<dim3(grid_chunks((size_t)K * w, 256, 64), batch), 256, 0, st>>>(W, Tup, n, p0, K, t0, w);
+    counted();
+    GemmBatch g = gb_basic(n, w, K, W, n, Tup, w, W, n, batch);
+    g.offA = p0;
+    g.offC = t0;
+    g.Cin = (const double* const*)W; g.offCin = t0; g.ldcin = n; g.beta = 1.0;
+    g.mode = GEMM_GJ; g.gj_k0 = p0; g.gj_b = K; g.gj_cols = 0;
+    return gemm(c, g, st, 2.0 * n * (double)w * K * batch, oz, err);
+}
+
+// Recursive blocked Gauss-Jordan of columns c0 .. c1 - 1: the left half, its transformation
+// applied to the right half's columns (one product of K = the left half's width), the right
+// half, its transformation applied to the left half's columns; columns of at most `leaf` are a
+// panel (gj_panel_kernel).  Columns outside c0 .. c1 - 1 receive only the row interchanges
+// (the panels apply them to every other column); their update by this range is the caller's.
+// Every level updates n x n / 2 elements per matrix, about log2(n / leaf) levels in all,
+// against n / leaf full n x n updates of the one-level blocked form.
+cudaError_t gj_recurse(sgs_ctx* c, int n, int batch, int leaf, int c0, int c1, double** W, double** T, double** Tup,
+                       int* piv, double* logdet, double* dsign, int* err, double tiny, cudaStream_t st,
+                       const OzBuf* oz) {
+    if (c1 - c0 <= leaf) {
+        const int bb = c1 - c0;
+        GJPanelArgs a{W, T, piv, logdet, dsign, err, n, c0, bb, tiny};
+        gj_panel_kernel<<<batch, 512, (size_t)n * (bb + 1) * sizeof(double) + bb * sizeof(double), st>>>(a);
+        counted();
+        return cudaGetLastError();
+    }
+    const int leaves = (c1 - c0 + leaf - 1) / leaf;
+    const int m = c0 + ((leaves + 1) / 2) * leaf;
+    cudaError_t e = gj_recurse(c, n, batch, leaf, c0, m, W, T, Tup, piv, logdet, dsign, err, tiny, st, oz);
+    if (e == cudaSuccess) e = gj_update(c, n, batch, W, Tup, c0, m - c0, m, c1 - m, st, oz, err);
+    if (e == cudaSuccess) e = gj_recurse(c, n, batch, leaf, m, c1, W, T, Tup, piv, logdet, dsign, err, tiny, st, oz);
+    if (e == cudaSuccess) e = gj_update(c, n, batch, W, Tup, m, c1 - m, c0, m - c0, st, oz, err);
+    return e;
+}
+
+// S^{-1} in place in W by the recursive form; Tup: per matrix n * n / 4 doubles of scratch
+cudaError_t launch_gj_recursive(sgs_ctx* c, int n, int batch, int leaf, double** W, double** T, double** Tup,
+                                int* piv, double* logdet, double* dsign, int* err, double tiny, cudaStream_t st,
+                                const OzBuf* oz) {
+    set_kernel_attributes();
+    return gj_recurse(c, n, batch, leaf, 0, n, W, T, Tup, piv, logdet, dsign, err, tiny, st, oz);
+}
+
 cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, double** TU, double** PK, double** upA,
                       double** upB, double** upC, double* logabs, double* phase, int* err, cudaStream_t st,
                       const OzBuf* oz = nullptr) {
@@ -796,7 +866,8 @@ cudaError_t pair_inverse(sgs_ctx* c, Instance& I, cudaStream_t st) {
     const size_t nn = (size_t)n * n;
     pair_sum_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.dev(), I.work);
     counted();
-    cudaError_t e = launch_gj(c, n, P, I.gj_b, I.p_work, I.p_tbuf, I.piv, I.logdet, I.dsign, I.err, 1e-12, st, &I.oz);
+    cudaError_t e = launch_gj_recursive(c, n, P, I.gj_b, I.p_work, I.p_tbuf, I.p_tup, I.piv, I.logdet, I.dsign,
+                                        I.err, 1e-12, st, &I.oz);
     if (e != cudaSuccess) return e;
     gj_perm_kernel<<<(P + 127) / 128, 128, 0, st>>>(I.piv, I.perm, n, P);
     gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.p_work, I.p_si, I.perm, n);
@@ -824,8 +895,9 @@ cudaError_t pair_phase(sgs_ctx* c, Instance& I, cudaStream_t st) {
                      I.err, st, &I.oz);
 }
 
-// pair pass + amplitude solve for one instance; E -> Ehist[slot]
-cudaError_t pair_pass(sgs_ctx* c, Instance& I, double* Eout, cudaStream_t st) {
+// pair pass (A1-A5) of one instance: S^{-1}, Im Delta, phase Pfaffians, then G, h and the
+// impurity blocks of F for its pairs and states
+cudaError_t pair_products(sgs_ctx* c, Instance& I, cudaStream_t st) {
     const int n = I.n, P = I.P, M = I.M;
     const double n3 = (double)n * n * n;
     InstDev d = I.dev();
@@ -845,10 +917,40 @@ cudaError_t pair_pass(sgs_ctx* c, Instance& I, double* Eout, cudaStream_t st) {
     }
     c->stage(SGS_STAGE_AMPLITUDES);
     pair_gh_kernel<<<P + M, 256, 0, st>>>(d, I.si, I.imd, I.logdet, I.pfphase, I.Gm, I.hm, I.fimp, I.fimp_state);
-    AmpArgs aa{M, I.Gm, I.hm, I.eigscratch, Eout, I.lam, I.lt, I.coef, I.cmode, 1e-12, I.err};
-    amp_solve_kernel<<<1, 256, 0, st>>>(aa);
-    counted(); counted();
+    counted();
     return cudaGetLastError();
+}
+
+// amplitude solve (A6) on the instance's G, h; E -> Eout
+cudaError_t amplitudes(Instance& I, double* Eout, cudaStream_t st) {
+    AmpArgs aa{I.M, I.Gm, I.hm, I.eigscratch, Eout, I.lam, I.lt, I.coef, I.cmode, 1e-12, I.err};
+    amp_solve_kernel<<<1, 256, 0, st>>>(aa);
+    counted();
+    return cudaGetLastError();
+}
+
+// pair pass + amplitude solve for one instance; E -> Eout
+cudaError_t pair_pass(sgs_ctx* c, Instance& I, double* Eout, cudaStream_t st) {
+    cudaError_t e = pair_products(c, I, st);
+    if (e != cudaSuccess) return e;
+    return amplitudes(I, Eout, st);
+}
+
+// a pair-sharded instance's share of (G, h) for the sum over ranks: out = [G | h], each
+// [M][M] complex; entries of pairs this rank does not hold are zero (memset before the pair
+// pass), the diagonal (state mu's own G_mu,mu = 1 and h_mu,mu) is kept on the rank that adds
+// state mu's own terms and zeroed elsewhere
+__global__ void shard_export_gh_kernel(const double* Gm, const double* hm, int M, const int* self_mask,
+                                       double* out) {
+    const int MM = M * M;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < MM; e += gridDim.x * blockDim.x) {
+        const int a = e / M, b = e % M;
+        const bool keep = a != b || self_mask[a] != 0;
+        out[2 * e] = keep ? Gm[2 * e] : 0.0;
+        out[2 * e + 1] = keep ? Gm[2 * e + 1] : 0.0;
+        out[2 * MM + 2 * e] = keep ? hm[2 * e] : 0.0;
+        out[2 * MM + 2 * e + 1] = keep ? hm[2 * e + 1] : 0.0;
+    }
 }
 
 // ------------------------------------------------------------------ autotuning
@@ -1030,14 +1132,16 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         eom_pairs_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef, I.pair_index,
                                                                      I.work, I.dgamma);
         eom_finish_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.fimp, I.fimp_state, I.s[4],
-                                                                      I.coef, I.pair_index, I.work, I.dgamma);
+                                                                      I.coef, I.pair_index, I.work, I.dgamma,
+                                                                      I.self_mask);
         antisymmetrise_kernel<<<eg, 256, 0, st>>>(I.dgamma, n);
         counted();
     } else {
         eom_pairs_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef,
                                                                        I.pair_index, I.work, I.dgamma);
         eom_finish_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.fimp, I.fimp_state, I.s[4],
-                                                                        I.coef, I.pair_index, I.work, I.dgamma);
+                                                                        I.coef, I.pair_index, I.work, I.dgamma,
+                                                                        I.self_mask);
     }
     counted(); counted();
     return cudaGetLastError();
@@ -1273,6 +1377,12 @@ sgs_status check_device_error(sgs_ctx* c) {
     return first;
 }
 
+bool any_sharded(const sgs_ctx* c) {
+    for (const auto& I : c->inst)
+        if (I.live && I.shard_world > 1) return true;
+    return false;
+}
+
 sgs_status ensure_ehist(sgs_ctx* c, Instance& I, int n) {
     if (I.Ecap >= n) return SGS_OK;
     double* p = c->alloc<double>(n);
@@ -1358,6 +1468,8 @@ sgs_status check_args(const sgs_model& m, const sgs_options& o) {
     if (o.precision < 0 || o.precision > 3 || (o.cmode != 0 && o.cmode != 1)) return SGS_EINVAL;
     if (o.integrator != SGS_INTEGRATOR_EXP && o.integrator != SGS_INTEGRATOR_EULER) return SGS_EINVAL;
     if (o.fp64_path != SGS_FP64_EMULATED && o.fp64_path != SGS_FP64_FMA) return SGS_EINVAL;
+    if (o.shard_world < 0 || (o.shard_world > 1 && (o.shard_rank < 0 || o.shard_rank >= o.shard_world)))
+        return SGS_EINVAL;
     if (o.gamma0) {           // finite and antisymmetric (purity is reported by sgs_health)
         const int n = 2 * m.n_modes;
         for (int mu = 0; mu < o.rank; mu++) {
@@ -1524,6 +1636,7 @@ sgs_status sgs_set_panel_widths(sgs_ctx* c, int instance, int gj_width, int pf_w
 
 sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
     if (!c || slot < 0 || slot >= (int)c->inst.size() || !c->inst[slot].live || !K) return SGS_EINVAL;
+    if (c->inst[slot].shard_world > 1) { c->err = "rank growth is not available on a pair-sharded instance"; return SGS_EINVAL; }
     const int n = c->inst[slot].n, M = c->inst[slot].M;
     if (M + 1 > SGS_MAX_RANK) { c->err = "the rank is already at its maximum"; return SGS_EINVAL; }
     if (src < -1 || src >= M) { c->err = "src out of range"; return SGS_EINVAL; }
@@ -1635,6 +1748,7 @@ sgs_status sgs_init(const sgs_model* models, const sgs_options* opts, int n_inst
 
 sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
     if (!c || n_steps < 0) return SGS_EINVAL;
+    if (any_sharded(c)) { c->err = "a pair-sharded instance steps through sgs_shard_pairs/eom/update"; return SGS_EINVAL; }
     for (auto& I : c->inst) {
         if (!I.live) continue;
         c->owner = &I;
@@ -1711,6 +1825,7 @@ sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
 
 sgs_status sgs_energy(sgs_ctx* c, double* energies) {
     if (!c) return SGS_EINVAL;
+    if (any_sharded(c)) { c->err = "a pair-sharded instance steps through sgs_shard_pairs/eom/update"; return SGS_EINVAL; }
     const long long l0 = g_launches;
     for (auto& I : c->inst)
         if (I.live) CUDA_TRY(c, pair_pass(c, I, I.Ecur, c->stream));
@@ -1726,8 +1841,82 @@ sgs_status sgs_energy(sgs_ctx* c, double* energies) {
     return SGS_OK;
 }
 
+// ---------------------------------------------------------------- pair-sharded step
+
+namespace {
+sgs_status shard_instance(sgs_ctx* c, int instance, Instance** out) {
+    if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
+    if (c->inst[instance].shard_world <= 1) { c->err = "not a pair-sharded instance"; return SGS_EINVAL; }
+    *out = &c->inst[instance];
+    return SGS_OK;
+}
+}  // namespace
+
+sgs_status sgs_shard_pairs(sgs_ctx* c, int instance, double* gh) {
+    Instance* Ip = nullptr;
+    sgs_status s = shard_instance(c, instance, &Ip);
+    if (s != SGS_OK) return s;
+    if (!gh) return SGS_EINVAL;
+    Instance& I = *Ip;
+    cudaStream_t st = c->stream;
+    const long long l0 = g_launches;
+    CUDA_TRY(c, cudaMemsetAsync(I.Gm, 0, 2 * (size_t)I.M * I.M * sizeof(double), st));
+    CUDA_TRY(c, cudaMemsetAsync(I.hm, 0, 2 * (size_t)I.M * I.M * sizeof(double), st));
+    CUDA_TRY(c, pair_products(c, I, st));
+    shard_export_gh_kernel<<<grid_chunks((size_t)I.M * I.M, 256, 64), 256, 0, st>>>(I.Gm, I.hm, I.M, I.self_mask, gh);
+    counted();
+    CUDA_TRY(c, cudaGetLastError());
+    c->stage(-1);
+    c->launches += g_launches - l0;
+    s = check_device_error(c);
+    c->collect();
+    return s;
+}
+
+sgs_status sgs_shard_eom(sgs_ctx* c, int instance, const double* gh, double* dgamma, double* energy) {
+    Instance* Ip = nullptr;
+    sgs_status s = shard_instance(c, instance, &Ip);
+    if (s != SGS_OK) return s;
+    if (!gh || !dgamma) return SGS_EINVAL;
+    Instance& I = *Ip;
+    cudaStream_t st = c->stream;
+    const long long l0 = g_launches;
+    const size_t mm2 = 2 * (size_t)I.M * I.M, nn = (size_t)I.n * I.n;
+    CUDA_TRY(c, cudaMemcpyAsync(I.Gm, gh, mm2 * sizeof(double), cudaMemcpyDefault, st));
+    CUDA_TRY(c, cudaMemcpyAsync(I.hm, gh + mm2, mm2 * sizeof(double), cudaMemcpyDefault, st));
+    c->stage(SGS_STAGE_AMPLITUDES);
+    CUDA_TRY(c, amplitudes(I, I.Ecur, st));
+    CUDA_TRY(c, eom_pass(c, I, st));
+    c->stage(-1);
+    CUDA_TRY(c, cudaMemcpyAsync(dgamma, I.dgamma, (size_t)I.M * nn * sizeof(double), cudaMemcpyDefault, st));
+    c->launches += g_launches - l0;
+    s = check_device_error(c);
+    c->collect();
+    if (s != SGS_OK) return s;
+    if (energy) CUDA_TRY(c, cudaMemcpy(energy, I.Ecur, sizeof(double), cudaMemcpyDeviceToHost));
+    return SGS_OK;
+}
+
+sgs_status sgs_shard_update(sgs_ctx* c, int instance, const double* dgamma) {
+    Instance* Ip = nullptr;
+    sgs_status s = shard_instance(c, instance, &Ip);
+    if (s != SGS_OK) return s;
+    if (!dgamma) return SGS_EINVAL;
+    Instance& I = *Ip;
+    cudaStream_t st = c->stream;
+    const long long l0 = g_launches;
+    CUDA_TRY(c, cudaMemcpyAsync(I.dgamma, dgamma, (size_t)I.M * I.n * I.n * sizeof(double), cudaMemcpyDefault, st));
+    CUDA_TRY(c, update_pass(c, I, st));
+    c->stage(-1);
+    c->launches += g_launches - l0;
+    s = check_device_error(c);
+    c->collect();
+    return s;
+}
+
 sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const int* sites, int n_sites, double* out) {
     if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live || !sites || !out || n_sites < 0) return SGS_EINVAL;
+    if (c->inst[instance].shard_world > 1) { c->err = "observables need every pair: not on a pair-sharded instance"; return SGS_EINVAL; }
     if (n_sites == 0) return SGS_OK;
     Instance& I = c->inst[instance];
     const int nsite_tot = I.n / 4;          // spinful sites: modes 2s, 2s+1 -> Majoranas 4s..4s+3
@@ -1829,6 +2018,7 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
 sgs_status sgs_variance(sgs_ctx* c, int instance, double* energy, double* variance) {
     if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
     Instance& I = c->inst[instance];
+    if (I.shard_world > 1) { c->err = "observables need every pair: not on a pair-sharded instance"; return SGS_EINVAL; }
     if (I.nc > VAR_MAX_MON) { c->err = "more quartic monomials than the variance kernel handles"; return SGS_EINVAL; }
     CUDA_TRY(c, pair_pass(c, I, I.Ecur, c->stream));
     c->stage(-1);
@@ -1958,6 +2148,40 @@ sgs_status sgs_get_profile(const sgs_ctx* cc, double* ms, double* flops, double*
         gemm_f64[2] = (double)c->gemm_count;
     }
     return SGS_OK;
+}
+
+sgs_status sgs_probe_wait(unsigned long long limit_ns, double* elapsed_ms) {
+    if (limit_ns < 1000ull || limit_ns > 10000000000ull) return SGS_EINVAL;
+    int* buf = nullptr;
+    if (cudaMalloc(&buf, 2 * sizeof(int)) != cudaSuccess) return SGS_ENOMEM;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sgs_status s = SGS_OK;
+    int err = 0;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess || cudaMemsetAsync(buf, 0, 2 * sizeof(int), st) != cudaSuccess) {
+        s = SGS_ECUDA;
+    } else {
+        cudaEventRecord(e0, st);
+        wait_probe_kernel<<<1, 32, 0, st>>>(buf, limit_ns, buf + 1);      // the flag buf[0] stays 0
+        counted();
+        cudaEventRecord(e1, st);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&err, buf + 1, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            s = SGS_ECUDA;
+        } else {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (elapsed_ms) *elapsed_ms = ms;
+            s = (err & SGS_DEV_TC_TIMEOUT) ? SGS_ETIMEOUT : SGS_OK;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(buf);
+    return s;
 }
 
 sgs_status sgs_kernel_smem_limits(int n_out, int* limit, int* expected) {
@@ -2264,19 +2488,26 @@ sgs_status sgs_kernel_inverse(const double* S, int n, int batch, int fp64_path, 
     cudaStreamCreateWithFlags(&tmp.stream, cudaStreamNonBlocking);
     const size_t nn = (size_t)n * n;
     const int bsz = (n <= 640) ? std::min(32, n) : 16;
+    const size_t qn = (size_t)n * n / 4 + n;             // recursive form: pivot rows of the widest update
     double *W = tmp.alloc<double>(batch * nn), *O = tmp.alloc<double>(batch * nn), *T = tmp.alloc<double>((size_t)batch * bsz * n);
+    double* U = tmp.alloc<double>(batch * qn);
     int *piv = tmp.alloc<int>((size_t)batch * n), *perm = tmp.alloc<int>((size_t)batch * n), *err = tmp.alloc<int>(1);
     double *ld = tmp.alloc<double>(batch), *ds = tmp.alloc<double>(batch);
     sgs_status st = SGS_OK;
-    if (!W || !O || !T || !piv || !perm || !err || !ld || !ds) st = SGS_ENOMEM;
+    if (!W || !O || !T || !U || !piv || !perm || !err || !ld || !ds) st = SGS_ENOMEM;
     if (st == SGS_OK) {
-        std::vector<double*> pw, pt, po;
-        for (int b = 0; b < batch; b++) { pw.push_back(W + b * nn); pt.push_back(T + (size_t)b * bsz * n); po.push_back(O + b * nn); }
+        std::vector<double*> pw, pt, po, pu;
+        for (int b = 0; b < batch; b++) {
+            pw.push_back(W + b * nn); pt.push_back(T + (size_t)b * bsz * n); po.push_back(O + b * nn);
+            pu.push_back(U + b * qn);
+        }
         double **PW = upload_ptrs(&tmp, pw), **PT = upload_ptrs(&tmp, pt), **PO = upload_ptrs(&tmp, po);
+        double** PU = upload_ptrs(&tmp, pu);
         cudaMemcpyAsync(W, S, batch * nn * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);
         cudaMemsetAsync(err, 0, sizeof(int), tmp.stream);
-        const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(n, n, bsz), fp64_path, 0);
-        if (launch_gj(nullptr, n, batch, bsz, PW, PT, piv, ld, ds, err, 0.0, tmp.stream, &oz) != cudaSuccess)
+        const OzBuf oz = tmp_oz(tmp, (size_t)batch * oz_entry_bytes(n, n, std::min(n, n / 2 + bsz)), fp64_path, 0);
+        if (launch_gj_recursive(nullptr, n, batch, bsz, PW, PT, PU, piv, ld, ds, err, 0.0, tmp.stream, &oz) !=
+            cudaSuccess)
             st = SGS_ECUDA;
         gj_perm_kernel<<<(batch + 127) / 128, 128, 0, tmp.stream>>>(piv, perm, n, batch);
         gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), batch), 256, 0, tmp.stream>>>(PW, PO, perm, n);

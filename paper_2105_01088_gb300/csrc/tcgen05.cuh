@@ -56,19 +56,45 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// bounded wait on an mbarrier phase (2 s of wall time); returns false and sets the
-// error word on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+// Every wait of the library's device code is bounded: `done()` is polled until it holds or
+// limit_ns of wall time (the global timer) have passed; then SGS_DEV_TC_TIMEOUT is set in the
+// error word and the wait returns false, and the caller drains its own work and returns.
+// With abort_on_flag, a wait also gives up once another thread of the launch has recorded a
+// timeout (checked every 256 polls).
+constexpr uint64_t SGS_WAIT_LIMIT_NS = 2000000000ull;     // pipeline waits: 2 s
+
+template <class Done>
+__device__ __forceinline__ bool bounded_wait(Done done, uint64_t limit_ns, int* err, bool abort_on_flag) {
     const uint64_t t0 = global_ns();
-    while (true) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.b32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
-        if (global_ns() - t0 > 2000000000ull) break;
+    for (uint32_t it = 0;; it++) {
+        if (done()) return true;
+        if ((it & 255u) == 255u) {
+            if (abort_on_flag && (*(volatile int*)err & SGS_DEV_TC_TIMEOUT)) return false;
+            if (global_ns() - t0 > limit_ns) break;
+        }
     }
     atomicOr(err, SGS_DEV_TC_TIMEOUT);
     return false;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.b32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// bounded wait on an mbarrier phase (2 s); returns false and sets the error word on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+    return bounded_wait([&] { return mbar_try_wait(bar, parity); }, SGS_WAIT_LIMIT_NS, err, false);
+}
+
+// A wait on a flag in global memory that nothing sets, bounded by limit_ns: the failure
+// path every pipeline wait takes, run on its own (sgs_probe_wait).  One thread waits and
+// records the timeout; the launch then returns like a timed-out pipeline.
+__global__ void wait_probe_kernel(const int* flag, unsigned long long limit_ns, int* err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    bounded_wait([&] { return *(const volatile int*)flag != 0; }, limit_ns, err, false);
 }
 
 }  // namespace sgs

@@ -48,3 +48,18 @@ def test_admission_rejects_bad_states(pkg):
     assert e.value.status == 1
     assert s.admit(m, g, lam) == 0                      # the context stays usable
     s.close()
+
+
+@pytest.mark.parametrize("limit_ms", [1, 20])
+def test_bounded_wait_runs_out_and_the_context_stays_usable(pkg, limit_ms):
+    """A device wait on a flag that nothing sets gives up after its limit, records the
+    timeout and returns: the call reports SGS_ETIMEOUT (5), the launch lasted about the
+    limit, and the next library call on the device works."""
+    import paper_2105_01088_gb300 as pkg
+    st, ms = pkg.probe_wait(limit_ms * 1_000_000)
+    assert st == 5
+    assert 0.9 * limit_ms <= ms <= limit_ms + 50.0
+    A = np.random.default_rng(1).standard_normal((1, 64, 64))
+    C = pkg.batched_gemm(A, A)
+    assert np.abs(C - A @ A).max() < 1e-12 * np.abs(A @ A).max() * 8
+    assert pkg.probe_wait(10)[0] == 1               # limit below 1 us: rejected before any launch
