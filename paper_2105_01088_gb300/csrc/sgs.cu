@@ -362,7 +362,7 @@ std::vector<int> pf_candidates(int n) {
         if (2 * b <= n) v.push_back(b);
     return v;
 }
-int default_gj_width(int n) { return std::min((n <= 640) ? 32 : 16, n); }
+int default_gj_width(int n) { return std::min(16, n); }   // leaf of the recursive form
 int default_pf_width(int n) { return (2 * 16 > n) ? n / 2 : 16; }
 
 // Pointer arrays of the Gauss-Jordan panel rows and the Pfaffian panel vectors and
