@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--mixed", default="tf32", choices=["tf32", "bf16", "3xtf32", "none"],
                     help="mixed-precision form timed beside the FP64 line (the line's 'mixed' object)")
     ap.add_argument("--panel-widths", default="",
-                    help="GJ,PF: fixed factorisation panel widths instead of the autotuner's (reproducible profiles)")
+                    help="GJ,PF: fix the factorisation panel widths after the autotuner (reproducible profiles)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--accuracy-steps", type=int, default=0,
                     help="run the FP64 form and --precision side by side for this many steps and report the "
@@ -308,9 +308,8 @@ def run_sgs(args):
     g, lam = inp.initial_state(p.n_modes, w.rank, w.seed + 1000 * rank, w.parity)
     model = sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels)
     stream = torch.cuda.Stream()          # a capturable stream: steps replay a CUDA graph
-    # fixed panel widths (reproducible profiles) skip the autotuner's trial runs
-    solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=prec, parity=w.parity, stream=stream,
-                        autotune=not args.panel_widths, **path_kwargs(args))
+    solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=prec, parity=w.parity, stream=stream, autotune=True,
+                        **path_kwargs(args))
     if args.panel_widths:
         solver.set_panel_widths(*[int(x) for x in args.panel_widths.split(",")])
     metric = f"imag-time steps/s at 2N={2 * p.n_modes},M={w.rank}"
@@ -409,7 +408,7 @@ def run_sgs(args):
     # the mixed form of the same workload from the same states: the same warm-up and timed steps
     if args.mixed != "none" and args.precision == "fp64":
         ms_solver = sgs.Solver(model, g, lam, dtau=w.dtau, precision=PRECISIONS[args.mixed], parity=w.parity,
-                               stream=stream, autotune=not args.panel_widths, **path_kwargs(args))
+                               stream=stream, autotune=True, **path_kwargs(args))
         if args.panel_widths:
             ms_solver.set_panel_widths(*[int(x) for x in args.panel_widths.split(",")])
         Em_all, ms_m, ck_m = timed_steps(torch, ms_solver, stream, args, dist, local)

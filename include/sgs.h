@@ -182,7 +182,7 @@ int sgs_failed_instances(const sgs_ctx* ctx, int* slots, int capacity);
 
 /* Autotuning of the factorisation tile shapes.  With enable = 1, sgs_admit
  * (and sgs_add_state) times the candidate panel widths of the blocked
- * Gauss-Jordan inverse (8, 16, 24, 32, 48, 64 columns, as shared memory allows)
+ * Gauss-Jordan inverse (leaf panels of 8, 12, 16, 20, 24, 32, 48, 64 columns, as shared memory allows)
  * and of the blocked complex Pfaffian (8, 12, 16, 24, 32 column pairs) on the new
  * instance's own pairs,
  * with CUDA events, and keeps the fastest.  Choices are cached per (n, rank,

@@ -269,8 +269,11 @@ __device__ __forceinline__ void pf_pending(double& vr, double& vi, double tr, do
 }
 
 // Columns of the antisymmetric Y are read as negated rows (coalesced); the
-// pending rank-2 updates of the panel are added on the fly.
-__global__ void __launch_bounds__(512) pf_panel_kernel(PfPanelArgs a) {
+// pending rank-2 updates of the panel are added on the fly.  Launched with
+// PF_PANEL_THREADS threads: four CTAs fit an SM (registers and shared memory),
+// so up to 608 matrices run in one wave on 152 SMs.
+#define PF_PANEL_THREADS 256
+__global__ void __launch_bounds__(PF_PANEL_THREADS, 4) pf_panel_kernel(PfPanelArgs a) {
     extern __shared__ double sm[];
     const int n = a.n, k0 = a.k0, bs = a.bs;
     double* ckr = sm;            // current column k (real)

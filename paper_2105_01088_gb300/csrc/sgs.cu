@@ -351,8 +351,9 @@ std::vector<int> gj_candidates(int n) {
     cudaFuncGetAttributes(&fa, gj_panel_kernel);
     const int limit = optin - (int)fa.sharedSizeBytes;
     std::vector<int> v;
-    // 24 and 48 between the powers of two: 24 fits two panel CTAs per SM at n = 512
-    for (int b : {8, 16, 24, 32, 48, 64})
+    // between the powers of two: at n = 512 a panel of 12 columns fits four panel CTAs per SM
+    // (one wave for up to 608 matrices), 20 three, 24 two
+    for (int b : {8, 12, 16, 20, 24, 32, 48, 64})
         if (b <= n && (size_t)n * (b + 1) * sizeof(double) + b * sizeof(double) <= (size_t)limit) v.push_back(b);
     return v;
 }
@@ -838,7 +839,7 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
     for (int k0 = 0; k0 < n; k0 += 2 * bsmax) {
         const int bs = std::min(bsmax, (n - k0) / 2);
         PfPanelArgs a{Y, TU, PK, logabs, phase, err, n, k0, bs, bsmax};
-        pf_panel_kernel<<<batch, 512, smem, st>>>(a);
+        pf_panel_kernel<<<batch, PF_PANEL_THREADS, smem, st>>>(a);
         counted();
         const int e0 = k0 + 2 * bs;
         if (e0 >= n) break;
