@@ -87,8 +87,17 @@ typedef enum {
 /* Model, Sec. II A.  A: n x n row-major real antisymmetric, n = 2 * n_modes.
  * Quartic part: n_quartic monomials value[j] * c_i0 c_i1 c_i2 c_i3 with four
  * distinct indices idx[4j..4j+3]; the library antisymmetrises them into U
- * (U_{pi(i)} = sgn(pi) value / 24).  At most 16 distinct Majoranas may
- * appear in quartic terms (the impurity block). */
+ * (U_{pi(i)} = sgn(pi) value / 24).  Interaction terms of more than four
+ * Majoranas (Sec. II A allows them; Sec. III C estimates their cost): term j
+ * is v_j i^(r mod 2) c_s1 ... c_s(2r) with 2r = higher_len[j] (6 or 8)
+ * distinct indices taken in order from higher_idx (concatenated) and
+ * v_j = higher_val[j] real (the factor i^(r mod 2) makes it Hermitian).
+ * Their expectation is the Pfaffian of the 2r x 2r sub-block of the
+ * transition matrix, their share of the Fock matrix its derivative.  At most
+ * 16 distinct Majoranas may appear in interaction terms (the impurity block),
+ * and at most SGS_MAX_HIGHER higher terms.  A zero-initialised tail
+ * (n_higher = 0) means none. */
+#define SGS_MAX_HIGHER 64
 typedef struct {
     int n_modes;
     const double* A;
@@ -96,6 +105,10 @@ typedef struct {
     const int* quartic_idx;
     const double* quartic_val;
     double e_const;
+    int n_higher;
+    const int* higher_len;
+    const int* higher_idx;
+    const double* higher_val;
 } sgs_model;
 
 typedef enum {
@@ -294,7 +307,8 @@ sgs_status sgs_correlator(sgs_ctx* ctx, int instance, sgs_corr_kind kind, const 
  * transition matrix in O(n^2) per pair (the quadratic part of H must be
  * sparse for that bound; at most 64 distinct quartic monomials).  The paper
  * extrapolates the energy linearly in delta_H^2 -> 0.  energy, variance: host
- * doubles, either may be NULL.  Errors: SGS_EINVAL, SGS_ESINGULAR, SGS_ECUDA. */
+ * doubles, either may be NULL.  Errors: SGS_EINVAL (also for a model with
+ * terms of more than four Majoranas), SGS_ESINGULAR, SGS_ECUDA. */
 sgs_status sgs_variance(sgs_ctx* ctx, int instance, double* energy, double* variance);
 
 void sgs_free(sgs_ctx* ctx);

@@ -45,18 +45,27 @@ import scipy.linalg
 
 
 class MajoranaModel:
-    """H = e_const + i sum_kl A_kl c_k c_l + sum_klpq U_klpq c_k c_l c_p c_q.
+    """H = e_const + i sum_kl A_kl c_k c_l + sum_klpq U_klpq c_k c_l c_p c_q
+         + sum_j v_j i^(r_j mod 2) c_{s_j1} ... c_{s_j(2 r_j)}.
 
     ``A`` is the real skew 2N x 2N matrix of Sec. II A.  The quartic tensor is
     kept as its non-zero antisymmetrised entries: ``quartic`` is a list of
     ((k, l, p, q), value) with the value of U_klpq for every ordering of each
     monomial's four distinct indices (Sec. II A: U is skew under exchange of
-    neighbouring indices, hence fully antisymmetric).
+    neighbouring indices, hence fully antisymmetric).  ``higher`` holds
+    interaction terms of more than four Majoranas (Sec. II A allows them; Sec.
+    III C estimates their cost), as (indices, v): 2r distinct indices, r >= 3,
+    and a real v; the factor i^(r mod 2) makes the term Hermitian, since the
+    product of 2r distinct Majoranas is Hermitian for even r and anti-Hermitian
+    for odd r.
     """
 
-    def __init__(self, A, quartic, e_const):
+    def __init__(self, A, quartic, e_const, higher=()):
         self.A = np.asarray(A, dtype=np.float64)
         self.quartic = list(quartic)
+        self.higher = [(tuple(int(x) for x in idx), float(v)) for idx, v in higher]
+        for idx, _ in self.higher:
+            assert len(idx) % 2 == 0 and len(idx) >= 6 and len(set(idx)) == len(idx)
         self.e_const = float(e_const)
         self.n = self.A.shape[0]
         self.N = self.n // 2
@@ -248,24 +257,50 @@ def transition_matrix(Ga, Gb):
     return np.linalg.solve(S.T, rhs.T).T
 
 
+def _higher_phase(r):
+    """i^(r mod 2) (the term's factor) times i^r (the Pfaffian of i Delta): a sign."""
+    return (-1.0) ** ((r + r % 2) // 2)
+
+
 def wick_energy_density(model, Dlt):
     """<phi_b|H|phi_a> / <phi_b|phi_a> for the transition matrix Delta^{a,b}:
-    e_const + Tr(A Delta) - 3 sum_klpq U_klpq Delta_kl Delta_pq.
-    (Generalised Wick theorem of Sec. III B: two-point elements i Delta_kl,
-    four-point elements the Pfaffian of the 4x4 sub-block of i Delta.)"""
+    e_const + Tr(A Delta) - 3 sum_klpq U_klpq Delta_kl Delta_pq, plus for each
+    term of 2r > 4 Majoranas v i^(r mod 2) Pf(i Delta_S) = v (-1)^((r + r mod 2)/2)
+    Pf(Delta_S), Delta_S the sub-block on the term's indices in its order.
+    (Generalised Wick theorem of Sec. III B: two-point elements i Delta_kl, an
+    element of n distinct Majoranas the Pfaffian of the n x n sub-block of
+    i Delta.)"""
     e = model.e_const + np.sum(model.A * Dlt.T)
     q = 0.0
     for (k, l, p, r), v in model.quartic:
         q += v * Dlt[k, l] * Dlt[p, r]
-    return e - 3.0 * q
+    e = e - 3.0 * q
+    for idx, v in model.higher:
+        e = e + v * _higher_phase(len(idx) // 2) * pfaffian(Dlt[np.ix_(idx, idx)])
+    return e
 
 
 def fock_matrix(model, Dlt):
     """Generalised Fock matrix F^{a,b}_kl = A_kl + 6 sum_mn U_klmn Delta^{a,b}_mn
-    (Sec. III B)."""
+    (Sec. III B): F_kl = A_kl - (1/2) dE/dDelta_kl, the derivative of the Wick
+    energy with Delta_kl and Delta_lk = -Delta_kl moving together.  For a term of
+    2r > 4 Majoranas on positions a < b of its index list S, dPf(Delta_S)/dDelta_ab
+    = (-1)^(a + b + 1) Pf(Delta_S without rows and columns a, b)."""
     F = model.A.astype(np.complex128 if np.iscomplexobj(Dlt) else np.float64).copy()
     for (k, l, m, r), v in model.quartic:
         F[k, l] += 6.0 * v * Dlt[m, r]
+    if model.higher:
+        F = F.astype(np.complex128) if np.iscomplexobj(Dlt) else F
+    for idx, v in model.higher:
+        c = v * _higher_phase(len(idx) // 2)
+        sub = Dlt[np.ix_(idx, idx)]
+        m = len(idx)
+        for a in range(m):
+            for b in range(a + 1, m):
+                rest = [x for x in range(m) if x != a and x != b]
+                d = (-1.0) ** (a + b + 1) * pfaffian(sub[np.ix_(rest, rest)])
+                F[idx[a], idx[b]] += -0.5 * c * d
+                F[idx[b], idx[a]] -= -0.5 * c * d
     return F
 
 
@@ -542,7 +577,10 @@ def _dpf4(X, C):
 
 def hamiltonian_square_density(model, Dlt):
     """<H^2> in the transition state with matrix Dlt: <phi_a|H^2|phi_b> / G_ab
-    for Dlt = Delta^{b,a} (Gamma_a itself for a = b)."""
+    for Dlt = Delta^{b,a} (Gamma_a itself for a = b).  Quadratic and quartic
+    terms only."""
+    if model.higher:
+        raise NotImplementedError("the variance covers quadratic and quartic terms")
     A = model.A
     n = model.n
     e = model.e_const

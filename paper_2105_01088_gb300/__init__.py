@@ -36,7 +36,9 @@ class SGSError(RuntimeError):
 class _Model(ctypes.Structure):
     _fields_ = [("n_modes", ctypes.c_int), ("A", ctypes.POINTER(ctypes.c_double)), ("n_quartic", ctypes.c_int),
                 ("quartic_idx", ctypes.POINTER(ctypes.c_int)), ("quartic_val", ctypes.POINTER(ctypes.c_double)),
-                ("e_const", ctypes.c_double)]
+                ("e_const", ctypes.c_double), ("n_higher", ctypes.c_int),
+                ("higher_len", ctypes.POINTER(ctypes.c_int)), ("higher_idx", ctypes.POINTER(ctypes.c_int)),
+                ("higher_val", ctypes.POINTER(ctypes.c_double))]
 
 
 class _Options(ctypes.Structure):
@@ -165,15 +167,32 @@ def use_torch_allocator():
 
 class MajoranaModel:
     """Model in the library's input form: A (n x n), quartic monomials
-    (idx [q, 4], val [q]) and the constant e_const (Sec. II A)."""
+    (idx [q, 4], val [q]), the constant e_const (Sec. II A) and terms of six or
+    eight Majoranas, ``higher`` = [(indices, v)] for v i^(r mod 2) c_s1 ... c_s2r."""
 
-    def __init__(self, A, quartic_idx, quartic_val, e_const):
+    def __init__(self, A, quartic_idx, quartic_val, e_const, higher=()):
         self.A = np.ascontiguousarray(A, dtype=np.float64)
         self.quartic_idx = np.ascontiguousarray(np.asarray(quartic_idx, dtype=np.int32).reshape(-1, 4))
         self.quartic_val = np.ascontiguousarray(quartic_val, dtype=np.float64).reshape(-1)
         self.e_const = float(e_const)
+        self.higher = [(tuple(int(x) for x in idx), float(v)) for idx, v in higher]
         self.n = self.A.shape[0]
         self.n_modes = self.n // 2
+
+    def with_higher(self, higher):
+        """The same model plus terms of six or eight Majoranas."""
+        return MajoranaModel(self.A, self.quartic_idx, self.quartic_val, self.e_const, list(self.higher) + list(higher))
+
+    def _struct(self):
+        """The sgs_model of this model and the arrays it points into (kept alive by the caller)."""
+        hl = np.ascontiguousarray([len(i) for i, _ in self.higher], dtype=np.int32)
+        hi = np.ascontiguousarray([x for i, _ in self.higher for x in i], dtype=np.int32)
+        hv = np.ascontiguousarray([v for _, v in self.higher], dtype=np.float64)
+        keep = (hl, hi, hv)
+        nh = len(self.higher)
+        return _Model(self.n_modes, _ptr(self.A), len(self.quartic_val), _ptr(self.quartic_idx, _ip),
+                      _ptr(self.quartic_val), self.e_const, nh, _ptr(hl, _ip) if nh else None,
+                      _ptr(hi, _ip) if nh else None, _ptr(hv) if nh else None), keep
 
 
 def build_anderson(n_bath, U, eps_d, V, t=1.0, mu=0.0, n_channels=1) -> MajoranaModel:
@@ -298,8 +317,7 @@ class Solver:
         lam = None
         if lambda0 is not None:
             lam = np.ascontiguousarray(np.stack([np.real(lambda0), np.imag(lambda0)], -1), dtype=np.float64)
-        mod = _Model(model.n_modes, _ptr(model.A), len(model.quartic_val), _ptr(model.quartic_idx, _ip),
-                     _ptr(model.quartic_val), model.e_const)
+        mod, _keep = model._struct()
         path = self.fp64_path if fp64_path is None else int(fp64_path)
         scratch = self.emulation_scratch if emulation_scratch is None else int(emulation_scratch)
         opt = _Options(M, dtau, precision, cmode, parity, _ptr(g), _ptr(lam), None, integrator, int(seed), path,

@@ -33,7 +33,46 @@ struct InstDev {
     const double* q_val;    // [nq]
     const int* imp;         // [nimp] impurity Majoranas
     const int* slot;        // [n] slot in imp, or -1
+    int nh;                 // interaction terms of more than four Majoranas
+    const int* h_len;       // [nh] 6 or 8
+    const int* h_off;       // [nh] offset of each term's indices in h_idx
+    const int* h_idx;       // indices, each term in its own order
+    const double* h_val;    // [nh] v (-1)^((r + r mod 2) / 2): the energy is h_val Pf(Delta_S)
 };
+
+#define SGS_MAX_TERM 8      // Majoranas in one interaction term
+
+// Pfaffian of a small complex antisymmetric matrix X (m <= SGS_MAX_TERM, m even,
+// row-major, destroyed) by Parlett-Reid elimination with pivoting; 0 for a zero pivot
+__device__ inline cplx small_pf(cplx* X, int m) {
+    cplx pf = cmk(1.0, 0.0);
+    for (int k = 0; k + 1 < m; k += 2) {
+        int p = k + 1;
+        double best = cabs2(X[(k + 1) * m + k]);
+        for (int j = k + 2; j < m; j++) {
+            const double v = cabs2(X[j * m + k]);
+            if (v > best) { best = v; p = j; }
+        }
+        if (p != k + 1) {
+            for (int j = 0; j < m; j++) { cplx t = X[(k + 1) * m + j]; X[(k + 1) * m + j] = X[p * m + j]; X[p * m + j] = t; }
+            for (int j = 0; j < m; j++) { cplx t = X[j * m + k + 1]; X[j * m + k + 1] = X[j * m + p]; X[j * m + p] = t; }
+            pf = cscale(pf, -1.0);
+        }
+        const cplx piv = X[k * m + k + 1];
+        const double pm2 = cabs2(piv);
+        if (!(pm2 > 0.0)) return cmk(0.0, 0.0);
+        pf = cmul(pf, piv);
+        const cplx inv = cscale(cconj(piv), 1.0 / pm2);
+        for (int i = k + 2; i < m; i++) {
+            const cplx ti = cmul(X[k * m + i], inv), ui = X[i * m + k + 1];
+            for (int j = k + 2; j < m; j++) {
+                const cplx tj = cmul(X[k * m + j], inv), uj = X[j * m + k + 1];
+                X[i * m + j] = cadd(X[i * m + j], cadd(cmul(ti, uj), cscale(cmul(ui, tj), -1.0)));
+            }
+        }
+    }
+    return pf;
+}
 
 __device__ __forceinline__ size_t nn(const InstDev& d) { return (size_t)d.n * d.n; }
 
@@ -106,7 +145,39 @@ __global__ void __launch_bounds__(256) pair_gh_kernel(InstDev d, const double* s
             int s0 = d.slot[ix[0]], s1 = d.slot[ix[1]];
             F[s0 * ni + s1] = cadd(F[s0 * ni + s1], cscale(x, 6.0 * v));
         }
-        cplx dens = cmk(d.e_const + tr_r - 3.0 * q.x, tr_i - 3.0 * q.y);
+        // terms of six or eight Majoranas: energy h_val Pf(Delta_S); Fock entries
+        // F_{s_a s_b} = -(1/2) h_val (-1)^(a + b + 1) Pf(Delta_S without a, b) (a < b), antisymmetric
+        cplx qh = cmk(0.0, 0.0);
+        for (int t = 0; t < d.nh; t++) {
+            const int m = d.h_len[t];
+            const int* ix = d.h_idx + d.h_off[t];
+            const double v = d.h_val[t];
+            cplx S[SGS_MAX_TERM * SGS_MAX_TERM], X[SGS_MAX_TERM * SGS_MAX_TERM];
+            for (int i = 0; i < m; i++)
+                for (int j = 0; j < m; j++) S[i * m + j] = (i == j) ? cmk(0.0, 0.0) : delta(ix[i], ix[j]);
+            for (int e = 0; e < m * m; e++) X[e] = S[e];
+            qh = cadd(qh, cscale(small_pf(X, m), v));
+            const int mm = m - 2;
+            for (int a = 0; a < m; a++)
+                for (int b = a + 1; b < m; b++) {
+                    int r = 0;
+                    for (int i = 0; i < m; i++) {
+                        if (i == a || i == b) continue;
+                        int c = 0;
+                        for (int j = 0; j < m; j++) {
+                            if (j == a || j == b) continue;
+                            X[r * mm + c++] = S[i * m + j];
+                        }
+                        r++;
+                    }
+                    const double sgn = ((a + b + 1) & 1) ? -1.0 : 1.0;
+                    const cplx f = cscale(small_pf(X, mm), -0.5 * v * sgn);
+                    const int s0 = d.slot[ix[a]], s1 = d.slot[ix[b]];
+                    F[s0 * ni + s1] = cadd(F[s0 * ni + s1], f);
+                    F[s1 * ni + s0] = cadd(F[s1 * ni + s0], cscale(f, -1.0));
+                }
+        }
+        cplx dens = cmk(d.e_const + tr_r - 3.0 * q.x + qh.x, tr_i - 3.0 * q.y + qh.y);
         const int M = d.M;
         if (diag) {
             Gm[2 * (a * M + a)] = 1.0;

@@ -72,6 +72,11 @@ struct Instance {
     std::vector<int> h_pa, h_pb;
     std::vector<double> hA, hq_val;     // host copy of the model: rank growth rebuilds the instance
     std::vector<int> hq_idx;
+    std::vector<int> hh_len, hh_idx;    // terms of more than four Majoranas (host copy)
+    std::vector<double> hh_val;
+    int nh = 0;
+    int *h_len = nullptr, *h_off = nullptr, *h_idx = nullptr;
+    double* h_val = nullptr;
 
     double *gamma = nullptr, *dgamma = nullptr;
     int *pa = nullptr, *pb = nullptr, *pf_pair = nullptr, *pair_pf = nullptr, *pair_index = nullptr;
@@ -148,6 +153,7 @@ struct Instance {
         d.pa = pa; d.pb = pb; d.pf_pair = pf_pair; d.pair_pf = pair_pf; d.gamma = gamma;
         d.a_rowptr = a_rowptr; d.a_row = a_row; d.a_col = a_col; d.a_nnz = a_nnz; d.a_val = a_val;
         d.q_idx = q_idx; d.q_val = q_val; d.imp = imp; d.slot = slot;
+        d.nh = nh; d.h_len = h_len; d.h_off = h_off; d.h_idx = h_idx; d.h_val = h_val;
         return d;
     }
 };
@@ -461,8 +467,37 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         }
         qval.push_back(kv.second);
     }
+    // terms of more than four Majoranas: 6 or 8 distinct indices each, energy v (-1)^((r + r mod 2)/2)
+    // Pf(Delta_S) for the term v i^(r mod 2) c_s1 ... c_s2r
+    std::vector<int> hoff;
+    std::vector<double> hval;
+    I.hh_len.clear(); I.hh_idx.clear(); I.hh_val.clear();
+    if (m.n_higher < 0 || m.n_higher > SGS_MAX_HIGHER ||
+        (m.n_higher > 0 && (!m.higher_len || !m.higher_idx || !m.higher_val))) {
+        c->err = "bad higher interaction terms";
+        return SGS_EINVAL;
+    }
+    for (int j = 0, off = 0; j < m.n_higher; j++) {
+        const int len = m.higher_len[j];
+        if (len != 6 && len != 8) { c->err = "a higher interaction term has 6 or 8 Majoranas"; return SGS_EINVAL; }
+        const int* ix = m.higher_idx + off;
+        for (int a = 0; a < len; a++) {
+            if (ix[a] < 0 || ix[a] >= n) { c->err = "higher term index out of range"; return SGS_EINVAL; }
+            for (int b = a + 1; b < len; b++)
+                if (ix[a] == ix[b]) { c->err = "a higher term needs distinct Majoranas"; return SGS_EINVAL; }
+            if (std::find(impv.begin(), impv.end(), ix[a]) == impv.end()) impv.push_back(ix[a]);
+        }
+        const int r = len / 2;
+        hoff.push_back((int)I.hh_idx.size());
+        I.hh_len.push_back(len);
+        I.hh_idx.insert(I.hh_idx.end(), ix, ix + len);
+        I.hh_val.push_back(m.higher_val[j]);
+        hval.push_back((((r + r % 2) / 2) % 2 ? -1.0 : 1.0) * m.higher_val[j]);
+        off += len;
+    }
+    I.nh = m.n_higher;
     std::sort(impv.begin(), impv.end());
-    if ((int)impv.size() > SGS_MAX_IMP) { c->err = "more than 16 Majoranas in quartic terms"; return SGS_EINVAL; }
+    if ((int)impv.size() > SGS_MAX_IMP) { c->err = "more than 16 Majoranas in interaction terms"; return SGS_EINVAL; }
     // canonical monomials: coefficient of c_k c_l c_p c_q (k < l < p < q) = 24 U_klpq
     std::vector<int> cidx;
     std::vector<double> cval;
@@ -515,6 +550,11 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.q_idx = c->alloc<int>(std::max(4 * I.nq, 4)); I.q_val = c->alloc<double>(std::max(I.nq, 1));
     I.c_idx = c->alloc<int>(std::max(4 * I.nc, 4)); I.c_val = c->alloc<double>(std::max(I.nc, 1));
     I.imp = c->alloc<int>(ni); I.slot = c->alloc<int>(n);
+    if (I.nh > 0) {
+        I.h_len = c->alloc<int>(I.nh); I.h_off = c->alloc<int>(I.nh); I.h_idx = c->alloc<int>(I.hh_idx.size());
+        I.h_val = c->alloc<double>(I.nh);
+        if (!I.h_len || !I.h_off || !I.h_idx || !I.h_val) { c->err = "device allocation failed"; return SGS_ENOMEM; }
+    }
     I.work = c->alloc<double>(Pm * 2 * nn);
     I.si = c->alloc<double>(Pm * nn); I.imd = c->alloc<double>(Pm * nn);
     I.wr = c->alloc<double>(Pm * nn); I.va = c->alloc<double>(Pm * nn); I.xa = c->alloc<double>(Pm * nn);
@@ -577,6 +617,13 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         CUDA_TRY(c, cudaMemcpyAsync(I.c_val, cval.data(), I.nc * sizeof(double), cudaMemcpyHostToDevice, st));
     }
     CUDA_TRY(c, cudaMemcpyAsync(I.slot, slot.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (I.nh > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(I.h_len, I.hh_len.data(), I.nh * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(I.h_off, hoff.data(), I.nh * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(I.h_idx, I.hh_idx.data(), I.hh_idx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(I.h_val, hval.data(), I.nh * sizeof(double), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(c, cudaStreamSynchronize(st));     // hoff and hval are host temporaries
+    }
     std::vector<double> lam0(2 * M, 0.0);
     if (o.lambda0) std::memcpy(lam0.data(), o.lambda0, 2 * M * sizeof(double));
     CUDA_TRY(c, cudaMemcpyAsync(I.lam, lam0.data(), 2 * M * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1669,7 +1716,8 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
     }
     // the grown instance: same model and options, rank M + 1, states filled on the device
     Instance J;
-    sgs_model m{I.N, I.hA.data(), (int)I.hq_val.size(), I.hq_idx.data(), I.hq_val.data(), I.e_const};
+    sgs_model m{I.N, I.hA.data(), (int)I.hq_val.size(), I.hq_idx.data(), I.hq_val.data(), I.e_const,
+                I.nh, I.hh_len.data(), I.hh_idx.data(), I.hh_val.data()};
     sgs_options o{M + 1, I.dtau, I.prec, I.cmode, I.parity, nullptr, nullptr, nullptr, I.integrator, 0,
                   I.fp64_path, I.oz_cap};
     c->owner = &J;
@@ -2021,6 +2069,7 @@ sgs_status sgs_variance(sgs_ctx* c, int instance, double* energy, double* varian
     Instance& I = c->inst[instance];
     if (I.shard_world > 1) { c->err = "observables need every pair: not on a pair-sharded instance"; return SGS_EINVAL; }
     if (I.nc > VAR_MAX_MON) { c->err = "more quartic monomials than the variance kernel handles"; return SGS_EINVAL; }
+    if (I.nh > 0) { c->err = "the variance covers quadratic and quartic terms"; return SGS_EINVAL; }
     CUDA_TRY(c, pair_pass(c, I, I.Ecur, c->stream));
     c->stage(-1);
     const size_t rows = (size_t)I.P + I.M;

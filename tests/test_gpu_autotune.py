@@ -63,6 +63,6 @@ def test_fixed_panel_widths(pkg):
     E1 = s.step(2)[0]
     assert np.abs(E1 - E0).max() <= 1e-12 * np.abs(E0).max()
     with pytest.raises(pkg.SGSError):
-        s.set_panel_widths(20, 12)                     # not a candidate
+        s.set_panel_widths(28, 12)                     # not a candidate
     assert s.tuning(0) == (24, 12, 2)
     s.close()

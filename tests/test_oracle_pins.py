@@ -26,7 +26,22 @@ def _fock_operator(model):
                 H = H + (1j * model.A[k, l]) * (c[k] @ c[l])
     for (k, l, p, q), v in model.quartic:
         H = H + v * (c[k] @ c[l] @ c[p] @ c[q])
+    for idx, v in model.higher:
+        r = len(idx) // 2
+        prod = c[idx[0]]
+        for x in idx[1:]:
+            prod = prod @ c[x]
+        H = H + (v * (1j ** (r % 2))) * prod
     return H.tocsr()
+
+
+def _higher_model():
+    """A two-site Anderson model (N = 4 modes) plus one term of six and one of eight
+    Majoranas in scrambled index orders (Sec. II A: interaction terms of more than
+    four Majoranas)."""
+    base = orc.anderson_model(1, 2.0, -1.0, 0.5)
+    higher = [((5, 0, 3, 6, 1, 2), 0.37), ((7, 1, 2, 4, 0, 6, 3, 5), -0.21), ((2, 7, 4, 1, 6, 0), -0.15)]
+    return orc.MajoranaModel(base.A, base.quartic, base.e_const, higher)
 
 
 # ---------------------------------------------------------------- model (Sec. II A, IV)
@@ -175,7 +190,53 @@ def test_energy_is_rayleigh_quotient_and_variational():
     assert E >= fock.ground_energy(H) - 1e-12
 
 
+def test_higher_terms_hermitian_and_matched_by_fock():
+    """Terms of six and eight Majoranas: the Fock operator is Hermitian (the factor
+    i^(r mod 2)), and G, h of Gaussian states match Fock-space matrix elements."""
+    model = _higher_model()
+    H = _fock_operator(model)
+    assert abs(H - H.conj().T).max() < 1e-14
+    gammas, vecs = _states(4, 4, 77)
+    G, h = orc.gram_and_hamiltonian(model, gammas)
+    assert np.abs(G - fock.gram(vecs)).max() < 1e-12
+    assert np.abs(h - fock.hmat(vecs, H)).max() < 1e-12
+    # the terms matter: without them h changes by much more than the bar
+    G0, h0 = orc.gram_and_hamiltonian(orc.MajoranaModel(model.A, model.quartic, model.e_const), gammas)
+    assert np.abs(h - h0).max() > 1e-2
+
+
 # ---------------------------------------------------------------- equation of motion
+
+
+@pytest.mark.parametrize("mode", [orc.C_INVERSE, orc.C_PHASE])
+def test_eom_with_higher_terms_matches_fock_flow(mode):
+    """Eq. (EOM-Gamma3) with F the derivative of the Wick energy holds for terms of
+    six and eight Majoranas: the matrix flow equals the Fock-space flow."""
+    model = _higher_model()
+    H = _fock_operator(model)
+    gammas, vecs = _states(4, 3, 43)
+    E, lam, G, h = orc.energy(model, gammas)
+    dG = orc.eom(model, gammas, G, h, E, lam, mode)
+    ref = fock.eom_bruteforce(vecs, lam, H, "inverse" if mode == orc.C_INVERSE else "phase")
+    for a, b, g in zip(dG, ref, gammas):
+        assert np.abs(a - b).max() < 1e-11 * max(1.0, np.abs(b).max())
+        assert np.abs(a @ g + g @ a).max() < 1e-11 * max(1.0, np.abs(a).max())
+
+
+def test_higher_fock_matrix_is_the_energy_derivative():
+    """F - A = -(1/2) dE/dDelta_kl (both entries moving) by central differences on a
+    random complex antisymmetric Delta, for the quartic and the higher terms."""
+    model = _higher_model()
+    rng = _rng(5)
+    X = rng.standard_normal((8, 8)) + 1j * rng.standard_normal((8, 8))
+    X = 0.5 * (X - X.T)
+    F = orc.fock_matrix(model, X)
+    h = 1e-6
+    for k, l in [(0, 1), (2, 5), (3, 7), (6, 4)]:
+        dX = np.zeros_like(X)
+        dX[k, l], dX[l, k] = h, -h
+        num = (orc.wick_energy_density(model, X + dX) - orc.wick_energy_density(model, X - dX)) / (2 * h)
+        assert abs((F[k, l] - model.A[k, l]) - (-0.5 * num)) < 1e-7 * max(1.0, abs(num))
 
 @pytest.mark.parametrize("mode", [orc.C_INVERSE, orc.C_PHASE])
 def test_eom_matches_fock_flow(mode):
