@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sgs", choices=["sgs", "reference"])
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
-    ap.add_argument("--workload", default="large", choices=["large", "small", "two_channel", "serving", "batched"])
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "small", "two_channel", "siam_L500", "serving", "batched"])
     ap.add_argument("--instances", type=int, default=256, help="batched: number of independent instances")
     ap.add_argument("--max-bath", type=int, default=64, help="batched: bath length L ~ U{16..max-bath}")
     ap.add_argument("--rate", type=float, default=100.0, help="serving: Poisson arrival rate (requests/s)")
@@ -81,7 +82,7 @@ def parse():
 
 def workload(name, rank=0):
     import dataclasses
-    w = {"large": inp.LARGE, "small": inp.SMALL, "two_channel": inp.TWO_CHANNEL}[name]
+    w = {"large": inp.LARGE, "small": inp.SMALL, "two_channel": inp.TWO_CHANNEL, "siam_L500": inp.SIAM_L500}[name]
     if rank > 0:
         w = dataclasses.replace(w, rank=rank, name=f"{w.name.rsplit('_M', 1)[0]}_M{rank}")
     return w
@@ -514,7 +515,10 @@ def run_serving(args):
 def run_batched(args):
     """Many independent uneven instances advanced together: every step replays one
     captured graph whose branches are the instances (their kernels overlap on the
-    device).  Instances are dealt round-robin to ranks (no collective)."""
+    device).  Instances that do not fit the device together run in waves: each wave
+    admits instances in order while they fit an HBM budget, takes the warm-up and the
+    timed steps, and is released.  Instances are dealt round-robin to ranks (no
+    collective)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -531,51 +535,66 @@ def run_batched(args):
     ws = inp.batched_workloads(args.instances, n_bath=(16, args.max_bath))
     mine = ws[rank::world]
     stream = torch.cuda.Stream()
-    solver = sgs.Solver(stream=stream, autotune=True, **path_kwargs(args))
+    budget = int(torch.cuda.mem_get_info()[0] * 0.8)
+    autotune = args.max_bath <= 64          # the capped default tunes each shape; the full range takes defaults
+    ms_total, waves, launches, finite, shapes = 0.0, [], 0, True, {}
     flops_per_step = 0.0
-    for w in mine:
-        p = w.model
-        # clustered states (order-one overlaps, as rank growth produces them): random pure states
-        # of unrelated orientation give amplitudes near 1e-14, whose c_mu = 1/(lambda lambda-tilde*)
-        # turns the first steps into rotations far outside a small step
-        rng = np.random.default_rng(w.seed)
-        g = inp.clustered_pure_gammas(p.n_modes, w.rank, rng, w.parity, spread=1.0)
-        lam = inp.random_amplitudes(w.rank, rng)
-        # phase form of c_mu (Sec. III A): the inverse form divides by the amplitude, and from these
-        # starts it drives rotations with ||X||_F of 1e2..1e3 per step
-        solver.admit(sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels), g, lam, w.dtau,
-                     prec, 1, w.parity)
-        n, M = 2 * p.n_modes, w.rank
-        # dense work per step (the algorithmic count of the pair and state stages, in n^3 units)
-        flops_per_step += n ** 3 * (M * (M - 1) / 2 * (2 + 1 + 4 / 3 + 1 + 2 + 1) * 2 + M * 60)
-    solver.step(args.warmup)
-    solver.set_profiling(False)           # resets the launch counter; graphs stay on
-    clocks = ClockSampler(local)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    ck = None
+    pending = list(mine)
+    while pending:
+        solver = sgs.Solver(stream=stream, autotune=autotune, hbm_budget=budget, **path_kwargs(args))
+        wave = []
+        while pending:
+            w = pending[0]
+            p = w.model
+            # clustered states (order-one overlaps, as rank growth produces them): random pure states
+            # of unrelated orientation give amplitudes near 1e-14, whose c_mu = 1/(lambda lambda-tilde*)
+            # turns the first steps into rotations far outside a small step
+            rng = np.random.default_rng(w.seed)
+            g = inp.clustered_pure_gammas(p.n_modes, w.rank, rng, w.parity, spread=1.0)
+            lam = inp.random_amplitudes(w.rank, rng)
+            # phase form of c_mu (Sec. III A): the inverse form divides by the amplitude, and from these
+            # starts it drives rotations with ||X||_F of 1e2..1e3 per step
+            try:
+                solver.admit(sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels), g, lam,
+                             w.dtau, prec, 1, w.parity)
+            except sgs.SGSError as e:
+                if e.status == 2 and wave:
+                    break                   # the budget is full: run this wave
+                raise
+            pending.pop(0)
+            wave.append(w)
+            n, M = 2 * p.n_modes, w.rank
+            # dense work per step (the algorithmic count of the pair and state stages, in n^3 units)
+            flops_per_step += n ** 3 * (M * (M - 1) / 2 * (2 + 1 + 4 / 3 + 1 + 2 + 1) * 2 + M * 60)
+        solver.step(args.warmup)
+        solver.set_profiling(False)           # resets the launch counter; graphs stay on
+        clocks = ClockSampler(local)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        clocks.start()
+        e0.record(stream)
+        E = solver.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wck = clocks.stop()
+        ck = wck if ck is None or (wck.get("sm_mhz") or 0) < (ck.get("sm_mhz") or 1e9) else ck
+        ms = e0.elapsed_time(e1)
+        ms_total += ms
+        launches += solver.profile()[1]
+        finite = finite and bool(np.isfinite(E).all())
+        for k in range(solver.n_instances):
+            gj, pf, _ = solver.tuning(k)
+            shapes[f"{gj}/{pf}"] = shapes.get(f"{gj}/{pf}", 0) + 1
+        waves.append({"instances": len(wave), "bytes": solver.bytes_in_use(), "ms_per_step": ms / args.steps})
+        solver.close()
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0.record(stream)
-    E = solver.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    launches = solver.profile()[1]
-    shapes = {}
-    for k in range(solver.n_instances):
-        gj, pf, _ = solver.tuning(k)
-        shapes[f"{gj}/{pf}"] = shapes.get(f"{gj}/{pf}", 0) + 1
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    finite = bool(np.isfinite(E).all())
-    solver.close()
     value = len(ws) * args.steps / (ms_max * 1e-3)
     ns = [2 * w.model.n_modes for w in ws]
     line = {"metric": "instance-steps/s (batched uneven impurity instances)", "value": value,
@@ -586,11 +605,14 @@ def run_batched(args):
                                    "M in {8,16,32}, U ~ U[0,8], eps_d = -U/2, V ~ U[0.2,1], ds = 0.05",
                        "n_range": [min(ns), max(ns)], "precision": args.precision,
                        "inputs": "clustered pure states O_mu = exp(K_mu) O around one Haar O, random phases",
-                       "c_mu": "phase form (Sec. III A)", "autotune": True,
+                       "c_mu": "phase form (Sec. III A)", "autotune": autotune,
+                       "hbm_budget_bytes": budget,
+                       "waves": waves,
+                       "timed": "the steps of each wave (CUDA events on the library's stream); admission excluded",
                        "l2": "inputs larger than L2 (tens of GB resident)"},
             "gpu_launches": launches, "clocks": ck, "all_energies_finite": finite,
             "panel_widths_gj_pf": shapes,
-            "dense_tflops_per_s": flops_per_step * len(ws) / max(len(mine), 1) * args.steps / (ms_max * 1e-3) / 1e12}
+            "dense_tflops_per_s": flops_per_step / max(len(mine), 1) * len(ws) * args.steps / (ms_max * 1e-3) / 1e12}
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -144,6 +144,8 @@ typedef struct {
                                 owns (0: 2 GiB; at least 1 MiB); larger batches run in chunks */
     int shard_rank;          /* pair sharding (sgs_shard_pairs): this rank of shard_world; */
     int shard_world;         /*   shard_world <= 1: not sharded */
+    int pair_chunk;          /* bounded memory: the per-pair buffers hold this many pairs and a step
+                                runs the pairs in chunks of that size (0: all pairs at once) */
 } sgs_options;
 
 /* Create a context holding n_instances independent problems (models[i],

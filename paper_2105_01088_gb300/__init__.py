@@ -46,7 +46,8 @@ class _Options(ctypes.Structure):
                 ("cmode", ctypes.c_int), ("parity", ctypes.c_int), ("gamma0", ctypes.POINTER(ctypes.c_double)),
                 ("lambda0", ctypes.POINTER(ctypes.c_double)), ("stream", ctypes.c_void_p),
                 ("integrator", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("fp64_path", ctypes.c_int),
-                ("emulation_scratch", ctypes.c_size_t), ("shard_rank", ctypes.c_int), ("shard_world", ctypes.c_int)]
+                ("emulation_scratch", ctypes.c_size_t), ("shard_rank", ctypes.c_int), ("shard_world", ctypes.c_int),
+                ("pair_chunk", ctypes.c_int)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -264,7 +265,7 @@ class Solver:
 
     def __init__(self, models=(), gamma0=(), lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE,
                  parity=1, stream=None, hbm_budget=0, integrator=SGS_INTEGRATOR_EXP, autotune=False,
-                 fp64_path=FP64_EMULATED, emulation_scratch=0):
+                 fp64_path=FP64_EMULATED, emulation_scratch=0, pair_chunk=0):
         if isinstance(models, MajoranaModel):
             models, gamma0, lambda0 = [models], [gamma0], [lambda0]
         models = list(models)
@@ -291,6 +292,7 @@ class Solver:
         self.live = []
         self._keep = {}
         self.fp64_path, self.emulation_scratch = int(fp64_path), int(emulation_scratch)
+        self.pair_chunk = int(pair_chunk)
         for i, m, g, l0, dt, pr, cm, pa, it in zip(range(k), models, gamma0, lambda0, per(dtau), per(precision),
                                                    per(cmode), per(parity), per(integrator)):
             try:
@@ -305,12 +307,14 @@ class Solver:
 
     def admit(self, model, gamma0, lambda0=None, dtau=0.05, precision=SGS_FP64, cmode=SGS_C_INVERSE, parity=1,
               integrator=SGS_INTEGRATOR_EXP, rank=None, seed=0, fp64_path=None, emulation_scratch=None,
-              shard=(0, 1)):
+              shard=(0, 1), pair_chunk=None):
         """Add one problem; returns its slot.  gamma0 None: seeded random states of
         the given rank, generated by the library.  fp64_path / emulation_scratch:
         None takes the solver's.  shard = (rank, world): this rank's share of a
-        pair-sharded step (sharded.py).  Raises SGSError(SGS_ENOMEM) if it does not
-        fit the HBM budget (nothing is allocated then)."""
+        pair-sharded step (sharded.py).  pair_chunk: per-pair buffers for this many
+        pairs, the step running the pairs in chunks (bounded memory; None takes the
+        solver's, 0 all pairs).  Raises SGSError(SGS_ENOMEM) if it does not fit the
+        HBM budget (nothing is allocated then)."""
         _check_slot_args(model, gamma0, parity, rank)
         g = None if gamma0 is None else np.ascontiguousarray(gamma0, dtype=np.float64)
         M = rank if g is None else g.shape[0]
@@ -320,8 +324,9 @@ class Solver:
         mod, _keep = model._struct()
         path = self.fp64_path if fp64_path is None else int(fp64_path)
         scratch = self.emulation_scratch if emulation_scratch is None else int(emulation_scratch)
+        chunk = self.pair_chunk if pair_chunk is None else int(pair_chunk)
         opt = _Options(M, dtau, precision, cmode, parity, _ptr(g), _ptr(lam), None, integrator, int(seed), path,
-                       scratch, int(shard[0]), int(shard[1]))
+                       scratch, int(shard[0]), int(shard[1]), chunk)
         slot = ctypes.c_int(-1)
         st = _lib.sgs_admit(self._ctx, ctypes.byref(mod), ctypes.byref(opt), ctypes.byref(slot))
         if st != 0:

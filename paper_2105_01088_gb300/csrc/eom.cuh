@@ -30,17 +30,17 @@ namespace sgs {
 // eom_pairs_kernel forms D (into dGamma) and T, six FMAs per pair and element;
 // eom_finish_kernel adds the sparse part, the beta = mu term and the impurity terms.
 
-// weights w0..w5 of one (mu, beta != mu) and the pair index, into shared memory; a pair
-// this instance does not hold (index -1: another rank's share of a pair-sharded step)
-// contributes nothing here
+// weights w0..w5 of one (mu, beta != mu) and the pair's index in the view, into shared
+// memory; a pair outside the view (another chunk of pairs) or not held at all (index -1:
+// another rank's share of a pair-sharded step) contributes nothing here
 template <typename R>
 __device__ __forceinline__ void eom_weights(const InstDev& d, const double* coef, const int* pair_index, int mu,
                                             R* sw, int* sp) {
     const int M = d.M;
     for (int be = threadIdx.x; be < M; be += blockDim.x) {
         if (be == mu) { sp[be] = -1; continue; }
-        const int p = pair_index[mu * M + be];
-        if (p < 0) { sp[be] = -1; continue; }
+        const int p = pair_index[mu * M + be] - d.p_off;
+        if (p < 0 || p >= d.p_cnt) { sp[be] = -1; continue; }
         const double sgn = (d.pa[p] == mu) ? -1.0 : 1.0;     // receiver a: complex conjugate
         const double* co = coef + (size_t)(mu * M + be) * 6;
         sw[6 * be + 0] = (R)(-4.0 * co[0]);
@@ -56,10 +56,12 @@ __device__ __forceinline__ void eom_weights(const InstDev& d, const double* coef
 // dynamic shared memory of both assembly kernels: M x 6 weights and M pair indices
 template <typename R> inline size_t eom_smem(int M) { return (size_t)M * 6 * sizeof(R) + (size_t)M * sizeof(int); }
 
+// accumulate = 1 adds onto tsum and dgamma (the pairs in chunks), 0 overwrites them
 template <typename R>
 __global__ void __launch_bounds__(256) eom_pairs_kernel(InstDev d, const double* si, const double* imd,
                                                         const double* qr, const double* qi, const double* coef,
-                                                        const int* pair_index, double* tsum, double* dgamma) {
+                                                        const int* pair_index, double* tsum, double* dgamma,
+                                                        int accumulate) {
     extern __shared__ double eom_sraw[];
     const int mu = blockIdx.y, M = d.M;
     R* sw = reinterpret_cast<R*>(eom_sraw);
@@ -84,10 +86,19 @@ __global__ void __launch_bounds__(256) eom_pairs_kernel(InstDev d, const double*
             acc = fma(w[4], sv, acc);
             acc = fma(w[5], iv, acc);
         }
-        T[e] = (double)t;
-        out[e] = (double)acc;
+        if (accumulate) {
+            T[e] += (double)t;
+            out[e] += (double)acc;
+        } else {
+            T[e] = (double)t;
+            out[e] = (double)acc;
+        }
     }
 }
+
+// parts of eom_finish_kernel: the pairs' impurity terms (per chunk of pairs), the rest (the
+// sparse A terms on the summed T and sum w2 of every pair, and the beta = mu term), or both
+enum { EOM_FINISH_PAIRS = 1, EOM_FINISH_REST = 2, EOM_FINISH_ALL = 3 };
 
 // self_mask (may be nullptr): state mu's beta = mu term is added only where self_mask[mu] != 0
 // (a pair-sharded step adds it on one rank, so that the ranks' partial sums add up to dGamma)
@@ -95,7 +106,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double* si, const double* imd,
                                                          const double* fimp, const double* fimp_state,
                                                          const double* gfg, const double* coef, const int* pair_index,
-                                                         const double* tsum, double* dgamma, const int* self_mask) {
+                                                         const double* tsum, double* dgamma, const int* self_mask,
+                                                         int part) {
     extern __shared__ double eom_sraw[];
     __shared__ R s_w2;
     const int mu = blockIdx.y;
@@ -112,7 +124,8 @@ __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double
     }
     __syncthreads();
     const size_t N = nn(d);
-    const bool self_term = self_mask == nullptr || self_mask[mu] != 0;
+    const bool rest = (part & EOM_FINISH_REST) != 0, pair_imp = (part & EOM_FINISH_PAIRS) != 0;
+    const bool self_term = rest && (self_mask == nullptr || self_mask[mu] != 0);
     const double* gm = d.gamma + (size_t)mu * N;
     const double* fs = fimp_state + (size_t)mu * ni * ni;
     const double* gfgm = gfg + (size_t)mu * N;
@@ -121,15 +134,18 @@ __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(e / n), l = (int)(e % n);
         const int sk = d.slot[k], sl = d.slot[l];
+        if (!rest && sk < 0 && sl < 0) continue;            // the pairs' impurity terms only
         // A_kl (row k of the CSR)
         R akl = 0;
         for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++)
             if (d.a_col[q] == l) akl = (R)d.a_val[q];
         R acc = (R)out[e];
-        acc = fma(akl, s_w2, acc);
-        // the pairs' commutator terms against A: -(T A^T)_kl - (A T)_kl
-        for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) acc = fma(-(R)T[(size_t)k * n + d.a_col[q]], (R)d.a_val[q], acc);
-        for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) acc = fma(-(R)d.a_val[q], (R)T[(size_t)d.a_col[q] * n + l], acc);
+        if (rest) {
+            acc = fma(akl, s_w2, acc);
+            // the pairs' commutator terms against A: -(T A^T)_kl - (A T)_kl
+            for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) acc = fma(-(R)T[(size_t)k * n + d.a_col[q]], (R)d.a_val[q], acc);
+            for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) acc = fma(-(R)d.a_val[q], (R)T[(size_t)d.a_col[q] * n + l], acc);
+        }
         if (self_term) {   // beta = mu: Delta = Gamma_mu, Delta F Delta = Gamma F Gamma
             const double* co = coef + (size_t)(mu * M + mu) * 6;
             const R g = (R)gm[e];
@@ -141,7 +157,7 @@ __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double
             if (sk >= 0) for (int m = 0; m < ni; m++) fg += (R)fs[sk * ni + m] * (R)gm[(size_t)d.imp[m] * n + l];
             acc += (R)2 * ((R)co[0] * (gf - fg) + (R)co[2] * ((R)gfgm[e] + f) + (R)co[4] * g);
         }
-        if (sk >= 0 || sl >= 0) {
+        if (pair_imp && (sk >= 0 || sl >= 0)) {
             // rows and columns of the impurity modes: the pairs' F_imp terms of [Delta, F] and Q + F
             for (int be = 0; be < M; be++) {
                 const int p = sp[be];

@@ -33,6 +33,8 @@ struct InstDev {
     const double* q_val;    // [nq]
     const int* imp;         // [nimp] impurity Majoranas
     const int* slot;        // [n] slot in imp, or -1
+    int p_off, p_cnt;       // the pairs this view holds: global pair indices p_off .. p_off + p_cnt - 1
+                            // (pair_index is global; pa, pb, pair_pf and the per-pair buffers are the view's)
     int nh;                 // interaction terms of more than four Majoranas
     const int* h_len;       // [nh] 6 or 8
     const int* h_off;       // [nh] offset of each term's indices in h_idx

@@ -64,6 +64,16 @@ struct Instance {
     int prec = 0, cmode = 0, parity = 1, integrator = 0;
     int fp64_path = SGS_FP64_EMULATED;  // arithmetic of the FP64 products (sgs_fp64_path)
     int shard_rank = 0, shard_world = 1; // pair sharding: this instance holds pairs p % world == rank
+    // pairs in chunks (bounded memory): per-pair buffers hold Pc pairs; the step runs the pair pass
+    // chunk by chunk for (G, h), then again for the equation of motion (recomputing S^-1, Im Delta)
+    int Pc = 0, Ppfc = 0;               // pairs and phase-Pfaffian entries the per-pair buffers hold
+    std::vector<int> ch_off, ch_cnt, ch_pfoff, ch_pfcnt;
+    int cur = 0;                        // the chunk the pair kernels see (view)
+    int nch() const { return (int)ch_off.size(); }
+    int coff() const { return ch_off.empty() ? 0 : ch_off[cur]; }
+    int ccnt() const { return ch_cnt.empty() ? 0 : ch_cnt[cur]; }
+    int cpfoff() const { return ch_pfoff.empty() ? 0 : ch_pfoff[cur]; }
+    int cpfcnt() const { return ch_pfcnt.empty() ? 0 : ch_pfcnt[cur]; }
     int* self_mask = nullptr;           // sharded: [M], 1 where this rank adds state mu's own term
     size_t oz_cap = 0;                  // emulated products: slice scratch cap (bytes)
     int gj_b = 32, pf_bs = 16;          // panel widths of the Gauss-Jordan inverse and the Pfaffian
@@ -146,14 +156,22 @@ struct Instance {
     double **p_upA = nullptr, **p_upB = nullptr, **p_upC = nullptr;   // Pfaffian update (2 Ppf)
     double **p_gamma = nullptr, **p_dgamma = nullptr, **p_s[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
+    // the current chunk's view of the pairs (all pairs when unchunked)
     InstDev dev() const {
         InstDev d{};
-        d.n = n; d.N = N; d.M = M; d.P = P; d.Ppf = Ppf; d.nimp = nimp; d.nq = nq;
+        d.n = n; d.N = N; d.M = M; d.P = ccnt(); d.Ppf = cpfcnt(); d.nimp = nimp; d.nq = nq;
         d.e_const = e_const; d.parity = (double)parity;
-        d.pa = pa; d.pb = pb; d.pf_pair = pf_pair; d.pair_pf = pair_pf; d.gamma = gamma;
+        d.pa = pa + coff(); d.pb = pb + coff(); d.pf_pair = pf_pair + cpfoff(); d.pair_pf = pair_pf + coff();
+        d.p_off = coff(); d.p_cnt = ccnt(); d.gamma = gamma;
         d.a_rowptr = a_rowptr; d.a_row = a_row; d.a_col = a_col; d.a_nnz = a_nnz; d.a_val = a_val;
         d.q_idx = q_idx; d.q_val = q_val; d.imp = imp; d.slot = slot;
         d.nh = nh; d.h_len = h_len; d.h_off = h_off; d.h_idx = h_idx; d.h_val = h_val;
+        return d;
+    }
+    // every pair (the sums over all pairs of the assembly's last part; no per-pair buffer is read)
+    InstDev dev_all() const {
+        InstDev d = dev();
+        d.P = P; d.Ppf = Ppf; d.pa = pa; d.pb = pb; d.pair_pf = pair_pf; d.p_off = 0; d.p_cnt = P;
         return d;
     }
 };
@@ -323,14 +341,15 @@ constexpr size_t OZ_DEFAULT_CAP = (size_t)2 << 30;
 size_t oz_cap_of(size_t requested) {
     return requested ? std::max<size_t>(requested, (size_t)1 << 20) : OZ_DEFAULT_CAP;
 }
-size_t oz_scratch_bytes(int n, int M, size_t cap) {
-    const size_t P = (size_t)M * (M - 1) / 2, Ppf = P > 0 ? P - (M - 1) : 0;
+size_t oz_scratch_bytes(int n, int M, size_t cap, size_t pair_cap) {
+    const size_t P = std::min<size_t>((size_t)M * (M - 1) / 2, pair_cap), Ppf = P;
     const size_t batch = std::max<size_t>(std::max<size_t>(P, 2 * Ppf), std::max<size_t>((size_t)M, 1));
     return std::min(batch * oz_entry_bytes(n, n, std::min(n, OZ_KC)) + 16384, cap);
 }
 
-size_t instance_bytes(int n, int M, int prec, int nimp, bool tune, int fp64_path, size_t oz_cap) {
-    const size_t nn = (size_t)n * n, P = (size_t)M * (M - 1) / 2, Ppf = P > 0 ? P - (M - 1) : 0;
+size_t instance_bytes(int n, int M, int prec, int nimp, bool tune, int fp64_path, size_t oz_cap, int pair_chunk) {
+    const size_t Pall = (size_t)M * (M - 1) / 2;
+    const size_t nn = (size_t)n * n, P = pair_chunk > 0 ? std::min<size_t>(Pall, pair_chunk) : Pall, Ppf = P;
     const size_t gj_b = tune ? 64 : 32, bs = tune ? 32 : 16;
     const size_t ni = std::max(nimp, 1);
     size_t d = 7 * (size_t)M * nn + std::max<size_t>(P, 1) * nn * 7 + P * gj_b * n + Ppf * 20 * n * bs +
@@ -343,7 +362,7 @@ size_t instance_bytes(int n, int M, int prec, int nimp, bool tune, int fp64_path
         if (prec != SGS_FP32_3XTF32)
             bytes += (size_t)M * nn * 4 + (size_t)M * n * ldp * (9 * 4 + 10 * esz);   // mixed update
     }
-    if (fp64_path == SGS_FP64_EMULATED) bytes += oz_scratch_bytes(n, M, oz_cap);
+    if (fp64_path == SGS_FP64_EMULATED) bytes += oz_scratch_bytes(n, M, oz_cap, P);
     return bytes + (1 << 20);
 }
 
@@ -363,20 +382,28 @@ std::vector<int> gj_candidates(int n) {
         if (b <= n && (size_t)n * (b + 1) * sizeof(double) + b * sizeof(double) <= (size_t)limit) v.push_back(b);
     return v;
 }
+// leaf of the recursive form: 16 columns, or the widest candidate below it whose panel
+// fits shared memory (large n)
+int default_gj_width(int n) {
+    int w = std::min(8, n);
+    for (int b : gj_candidates(n))
+        if (b <= 16) w = std::max(w, b);
+    return std::min(w, n);
+}
 std::vector<int> pf_candidates(int n) {
     std::vector<int> v;
     for (int b : {8, 12, 16, 24, 32})
         if (2 * b <= n) v.push_back(b);
     return v;
 }
-int default_gj_width(int n) { return std::min(16, n); }   // leaf of the recursive form
+
 int default_pf_width(int n) { return (2 * 16 > n) ? n / 2 : 16; }
 
 // Pointer arrays of the Gauss-Jordan panel rows and the Pfaffian panel vectors and
 // packed update operands for panel widths (gj_b, pf_bs); the scratch they point into is
 // sized for the widest candidate the instance may use.
 sgs_status set_panel_pointers(sgs_ctx* c, Instance& I, int gj_b, int pf_bs) {
-    const int n = I.n, P = I.P;
+    const int n = I.n, P = I.Pc, Ppf = I.Ppfc;    // one chunk of pairs
     const size_t nn = (size_t)n * n;
     I.gj_b = gj_b;
     I.pf_bs = pf_bs;
@@ -387,14 +414,18 @@ sgs_status set_panel_pointers(sgs_ctx* c, Instance& I, int gj_b, int pf_bs) {
     if (P > 0 && !(I.p_tbuf = upload_ptrs(c, t))) { c->owner = prev; return SGS_ENOMEM; }
     std::vector<double*> Y, TU, PK, upA, upB, upC;
     const size_t blk = (size_t)n * 4 * pf_bs;
-    for (int q = 0; q < I.Ppf; q++) {
+    for (int q = 0; q < Ppf; q++) {
         Y.push_back(I.work + (size_t)q * 2 * nn);
         TU.push_back(I.pfTU + (size_t)q * 4 * n * pf_bs);
         PK.push_back(I.pfpack + (size_t)q * 4 * blk);
     }
-    for (int q = 0; q < I.Ppf; q++) { upA.push_back(PK[q]); upB.push_back(PK[q] + blk); upC.push_back(Y[q]); }
-    for (int q = 0; q < I.Ppf; q++) { upA.push_back(PK[q] + 2 * blk); upB.push_back(PK[q] + 3 * blk); upC.push_back(Y[q] + nn); }
-    if (I.Ppf > 0) {
+    // the trailing updates' operands, real and imaginary planes of each entry next to each other, so
+    // that the first 2 k entries serve a chunk of k phase Pfaffians
+    for (int q = 0; q < Ppf; q++) {
+        upA.push_back(PK[q]); upB.push_back(PK[q] + blk); upC.push_back(Y[q]);
+        upA.push_back(PK[q] + 2 * blk); upB.push_back(PK[q] + 3 * blk); upC.push_back(Y[q] + nn);
+    }
+    if (Ppf > 0) {
         I.p_Y = upload_ptrs(c, Y); I.p_TU = upload_ptrs(c, TU); I.p_pack = upload_ptrs(c, PK);
         I.p_upA = upload_ptrs(c, upA); I.p_upB = upload_ptrs(c, upB); I.p_upC = upload_ptrs(c, upC);
         if (!I.p_Y || !I.p_TU || !I.p_pack || !I.p_upA || !I.p_upB || !I.p_upC) { c->owner = prev; return SGS_ENOMEM; }
@@ -532,14 +563,33 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         }
     I.P = (int)pa.size();
     const int P = I.P;
-    if (pair_pf.empty()) pair_pf.push_back(-1);
     I.Ppf = (int)pf_pair.size();
     I.h_pa = pa;
     I.h_pb = pb;
+    // chunks of at most Pc consecutive pairs; the phase-Pfaffian entries (pairs with a >= 1) of each
+    // chunk are listed by their index in the chunk, and pair_pf maps a pair to its chunk's entry
+    I.Pc = (o.pair_chunk > 0 && o.pair_chunk < P) ? o.pair_chunk : P;
+    I.ch_off.clear(); I.ch_cnt.clear(); I.ch_pfoff.clear(); I.ch_pfcnt.clear();
+    pf_pair.clear();
+    I.Ppfc = 0;
+    for (int off = 0; off < std::max(P, 1); off += std::max(I.Pc, 1)) {
+        const int cnt = std::min(I.Pc, P - off);
+        I.ch_off.push_back(off); I.ch_cnt.push_back(std::max(cnt, 0)); I.ch_pfoff.push_back((int)pf_pair.size());
+        int k = 0;
+        for (int j = 0; j < cnt; j++) {
+            pair_pf[off + j] = -1;
+            if (pa[off + j] >= 1) { pair_pf[off + j] = k++; pf_pair.push_back(j); }
+        }
+        I.ch_pfcnt.push_back(k);
+        I.Ppfc = std::max(I.Ppfc, k);
+    }
+    I.cur = 0;
+    if (pair_pf.empty()) pair_pf.push_back(-1);
+    const int Pc = I.Pc;
 
     const size_t nn = (size_t)n * n;
-    const size_t Pm = std::max(P, 1);
-    const size_t Pf = std::max(I.Ppf, 1);
+    const size_t Pm = std::max(P, 1), Pcm = std::max(Pc, 1);
+    const size_t Pf = std::max(I.Ppf, 1), Pfc = std::max(I.Ppfc, 1);
     const int ni = std::max(I.nimp, 1);
     I.gamma = c->alloc<double>(M * nn);
     I.dgamma = c->alloc<double>(M * nn);
@@ -555,17 +605,19 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         I.h_val = c->alloc<double>(I.nh);
         if (!I.h_len || !I.h_off || !I.h_idx || !I.h_val) { c->err = "device allocation failed"; return SGS_ENOMEM; }
     }
-    I.work = c->alloc<double>(Pm * 2 * nn);
-    I.si = c->alloc<double>(Pm * nn); I.imd = c->alloc<double>(Pm * nn);
-    I.wr = c->alloc<double>(Pm * nn); I.va = c->alloc<double>(Pm * nn); I.xa = c->alloc<double>(Pm * nn);
-    I.tbuf = c->alloc<double>(Pm * I.gj_cap * n);
-    I.piv = c->alloc<int>(Pm * n); I.perm = c->alloc<int>(Pm * n);
-    I.logdet = c->alloc<double>(Pm); I.dsign = c->alloc<double>(Pm);
-    I.pfTU = c->alloc<double>(Pf * 4 * n * I.pf_cap);
-    I.pfpack = c->alloc<double>(Pf * 4 * n * 4 * I.pf_cap);
-    I.pflog = c->alloc<double>(Pf); I.pfphase = c->alloc<double>(2 * Pf);
+    // per-pair buffers hold one chunk; the impurity blocks of F are kept for every pair (the
+    // equation-of-motion pass of a chunked step reads the amplitude pass's)
+    I.work = c->alloc<double>(Pcm * 2 * nn);
+    I.si = c->alloc<double>(Pcm * nn); I.imd = c->alloc<double>(Pcm * nn);
+    I.wr = c->alloc<double>(Pcm * nn); I.va = c->alloc<double>(Pcm * nn); I.xa = c->alloc<double>(Pcm * nn);
+    I.tbuf = c->alloc<double>(Pcm * I.gj_cap * n);
+    I.piv = c->alloc<int>(Pcm * n); I.perm = c->alloc<int>(Pcm * n);
+    I.logdet = c->alloc<double>(Pcm); I.dsign = c->alloc<double>(Pcm);
+    I.pfTU = c->alloc<double>(Pfc * 4 * n * I.pf_cap);
+    I.pfpack = c->alloc<double>(Pfc * 4 * n * 4 * I.pf_cap);
+    I.pflog = c->alloc<double>(Pfc); I.pfphase = c->alloc<double>(2 * Pfc);
     I.fimp = c->alloc<double>(Pm * ni * ni * 2); I.fimp_state = c->alloc<double>((size_t)M * ni * ni);
-    I.lr = c->alloc<double>(Pm * 2 * n * ni);
+    I.lr = c->alloc<double>(Pcm * 2 * n * ni);
     for (int j = 0; j < 5; j++) I.s[j] = c->alloc<double>(M * nn);
     I.sq = c->alloc<int>(M); I.scale = c->alloc<double>(M);
     I.Gm = c->alloc<double>(2 * M * M); I.hm = c->alloc<double>(2 * M * M);
@@ -598,8 +650,8 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         CUDA_TRY(c, cudaMemcpyAsync(I.pb, pb.data(), P * sizeof(int), cudaMemcpyHostToDevice, st));
         CUDA_TRY(c, cudaMemcpyAsync(I.pair_pf, pair_pf.data(), P * sizeof(int), cudaMemcpyHostToDevice, st));
     }
-    if (I.Ppf > 0)
-        CUDA_TRY(c, cudaMemcpyAsync(I.pf_pair, pf_pair.data(), I.Ppf * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!pf_pair.empty())
+        CUDA_TRY(c, cudaMemcpyAsync(I.pf_pair, pf_pair.data(), pf_pair.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     CUDA_TRY(c, cudaMemcpyAsync(I.pair_index, pidx.data(), (size_t)M * M * sizeof(int), cudaMemcpyHostToDevice, st));
     CUDA_TRY(c, cudaMemcpyAsync(I.a_rowptr, rowptr.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
     if (I.a_nnz > 0) {
@@ -629,21 +681,23 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     CUDA_TRY(c, cudaMemcpyAsync(I.lam, lam0.data(), 2 * M * sizeof(double), cudaMemcpyHostToDevice, st));
     CUDA_TRY(c, cudaMemsetAsync(I.err, 0, sizeof(int), st));
 
-    // pointer arrays
+    // pointer arrays: the per-pair buffers of one chunk (index in the chunk), the states of every pair
     std::vector<double*> w, s_, im, wr, va, xa, ga, gb;
-    for (int p = 0; p < P; p++) {
+    for (int p = 0; p < Pc; p++) {
         w.push_back(I.work + p * nn);
         s_.push_back(I.si + p * nn);
         im.push_back(I.imd + p * nn);
         wr.push_back(I.wr + p * nn);
         va.push_back(I.va + p * nn);
         xa.push_back(I.xa + p * nn);
+    }
+    for (int p = 0; p < P; p++) {
         ga.push_back(I.gamma + pa[p] * nn);
         gb.push_back(I.gamma + pb[p] * nn);
     }
     if (P > 0) {
         std::vector<double*> tup;
-        for (int p = 0; p < P; p++) tup.push_back(I.work + (size_t)P * nn + (size_t)p * nn);
+        for (int p = 0; p < Pc; p++) tup.push_back(I.work + (size_t)Pc * nn + (size_t)p * nn);
         I.p_tup = upload_ptrs(c, tup);
         I.p_work = upload_ptrs(c, w); I.p_si = upload_ptrs(c, s_);
         I.p_imd = upload_ptrs(c, im); I.p_wr = upload_ptrs(c, wr); I.p_va = upload_ptrs(c, va);
@@ -666,9 +720,9 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         const bool split = I.tc_kind == TC_3XTF32;
         I.ldp = (n + 7) & ~7;
         const size_t lpn = (size_t)n * I.ldp;           // elements of one padded operand
-        const size_t bytes = (size_t)P * lpn * esz;
+        const size_t bytes = (size_t)Pc * lpn * esz;
         I.si_hi = c->dalloc(bytes); I.t1_hi = c->dalloc(bytes); I.d_hi = c->dalloc(bytes);
-        I.wr32 = c->alloc<float>(P * nn); I.va32 = c->alloc<float>(P * nn); I.xa32 = c->alloc<float>(P * nn);
+        I.wr32 = c->alloc<float>(Pc * nn); I.va32 = c->alloc<float>(Pc * nn); I.xa32 = c->alloc<float>(Pc * nn);
         // fp32 results become operands through a rounding conversion (TF32: to nearest)
         I.wr_hi = c->dalloc(bytes);
         I.va_hi = c->dalloc(bytes);
@@ -683,7 +737,7 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         }
         auto arr = [&](void* base, size_t stride) {
             std::vector<void*> v;
-            for (int p = 0; p < P; p++) v.push_back(base ? (uint8_t*)base + p * stride : nullptr);
+            for (int p = 0; p < Pc; p++) v.push_back(base ? (uint8_t*)base + p * stride : nullptr);
             return upload_ptrs(c, v);
         };
         const size_t lp = lpn * esz, f4 = nn * 4;
@@ -693,13 +747,13 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         I.q_wr32 = arr(I.wr32, f4); I.q_va32 = arr(I.va32, f4); I.q_xa32 = arr(I.xa32, f4);
         I.q_si_lo = arr(I.si_lo, lp); I.q_t1_lo = arr(I.t1_lo, lp); I.q_d_lo = arr(I.d_lo, lp);
         I.q_wr_lo = arr(I.wr_lo, lp); I.q_va_lo = arr(I.va_lo, lp);
-        // tensor maps of the contiguous operand batches [P][n][ldp]
+        // tensor maps of the contiguous operand batches [Pc][n][ldp] (one chunk of pairs)
         const bool bf = I.tc_kind == TC_BF16;
         auto prod = [&](TmaBatch& t, void* A, void* A2, void* B, void* B2, float* C, int skew) {
-            bool ok = make_operand_map(&t.ta, A, bf, I.ldp, n, P) && make_operand_map(&t.tb, B, bf, I.ldp, n, P);
-            if (split) ok = ok && make_operand_map(&t.ta2, A2, bf, I.ldp, n, P) && make_operand_map(&t.tb2, B2, bf, I.ldp, n, P);
+            bool ok = make_operand_map(&t.ta, A, bf, I.ldp, n, Pc) && make_operand_map(&t.tb, B, bf, I.ldp, n, Pc);
+            if (split) ok = ok && make_operand_map(&t.ta2, A2, bf, I.ldp, n, Pc) && make_operand_map(&t.tb2, B2, bf, I.ldp, n, Pc);
             t.m = n; t.n = n; t.k = n; t.alpha = -1.0; t.C = C; t.c_stride = (long long)nn; t.ldc = n;
-            t.out_f64 = 0; t.skew = skew; t.err = I.err; t.batch = P;
+            t.out_f64 = 0; t.skew = skew; t.err = I.err; t.batch = Pc;
             return ok;
         };
         I.tma_ok = prod(I.tma_w, I.t1_hi, I.t1_lo, I.si_hi, I.si_lo, I.wr32, 1) &&
@@ -731,7 +785,7 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     }
     if (I.fp64_path == SGS_FP64_EMULATED) {
         // emulated FP64 products: slice scratch for one batch chunk
-        const size_t b = oz_scratch_bytes(n, M, I.oz_cap);
+        const size_t b = oz_scratch_bytes(n, M, I.oz_cap, Pc);
         I.oz.base = static_cast<uint8_t*>(c->dalloc(b));
         if (!I.oz.base) { c->err = "device allocation failed (emulated-product scratch)"; return SGS_ENOMEM; }
         I.oz.bytes = b;
@@ -910,7 +964,7 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
 // log|det S|, sign.  S has entries of magnitude <= 2; two states of opposite parity give a
 // pivot at rounding level (~1e-15), same-parity pairs O(0.1).
 cudaError_t pair_inverse(sgs_ctx* c, Instance& I, cudaStream_t st) {
-    const int n = I.n, P = I.P;
+    const int n = I.n, P = I.ccnt();
     const size_t nn = (size_t)n * n;
     pair_sum_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.dev(), I.work);
     counted();
@@ -925,48 +979,62 @@ cudaError_t pair_inverse(sgs_ctx* c, Instance& I, cudaStream_t st) {
 
 // Im Delta^{a,b} = (G_a - G_b) S^{-1}
 cudaError_t pair_delta(sgs_ctx* c, Instance& I, cudaStream_t st) {
-    const int n = I.n;
-    GemmBatch g = gb_basic(n, n, n, I.p_ga, n, I.p_si, n, I.p_imd, n, I.P);
-    g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
+    const int n = I.n, P = I.ccnt();
+    GemmBatch g = gb_basic(n, n, n, I.p_ga + I.coff(), n, I.p_si, n, I.p_imd, n, P);
+    g.A2 = (const double* const*)(I.p_gb + I.coff()); g.sA2 = -1.0;
     g.mode = GEMM_SKEW;
     g.b_antisym = 1;        // S^{-1} (antisymmetric up to the inversion's rounding)
-    return gemm(c, I, g, st, (double)n * n * n * I.P);   // antisymmetric product: half of 2 n^3
+    return gemm(c, I, g, st, (double)n * n * n * P);   // antisymmetric product: half of 2 n^3
 }
 
 // phase Pfaffians Pf(Gamma_0 + Delta^{a,b}) of the pairs without the reference state
 cudaError_t pair_phase(sgs_ctx* c, Instance& I, cudaStream_t st) {
     const int n = I.n;
     const size_t nn = (size_t)n * n;
-    pf_build_kernel<<<dim3(grid_chunks(nn, 256, 64), I.Ppf), 256, 0, st>>>(I.dev(), I.si, I.imd, I.work);
+    pf_build_kernel<<<dim3(grid_chunks(nn, 256, 64), I.cpfcnt()), 256, 0, st>>>(I.dev(), I.si, I.imd, I.work);
     counted();
-    return launch_pf(c, n, I.Ppf, I.pf_bs, I.p_Y, I.p_TU, I.p_pack, I.p_upA, I.p_upB, I.p_upC, I.pflog, I.pfphase,
-                     I.err, st, &I.oz);
+    return launch_pf(c, n, I.cpfcnt(), I.pf_bs, I.p_Y, I.p_TU, I.p_pack, I.p_upA, I.p_upB, I.p_upC, I.pflog,
+                     I.pfphase, I.err, st, &I.oz);
 }
 
-// pair pass (A1-A5) of one instance: S^{-1}, Im Delta, phase Pfaffians, then G, h and the
-// impurity blocks of F for its pairs and states
+// S^{-1} and Im Delta of the current chunk's pairs (A1, A2, A4)
+cudaError_t pair_factors(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    const double n3 = (double)I.n * I.n * I.n;
+    const int P = I.ccnt();
+    if (P == 0) return cudaSuccess;
+    c->stage(SGS_STAGE_PAIR_INVERSE);
+    c->stage_flops[SGS_STAGE_PAIR_INVERSE] += 2.0 * n3 * P;
+    cudaError_t e = pair_inverse(c, I, st);
+    if (e != cudaSuccess) return e;
+    c->stage(SGS_STAGE_PAIR_DELTA);
+    c->stage_flops[SGS_STAGE_PAIR_DELTA] += n3 * P;
+    return pair_delta(c, I, st);
+}
+
+// pair pass (A1-A5) of one instance, chunk by chunk: S^{-1}, Im Delta, phase Pfaffians, then G, h
+// and the impurity blocks of F for its pairs (and, with the first chunk, for its states)
 cudaError_t pair_products(sgs_ctx* c, Instance& I, cudaStream_t st) {
-    const int n = I.n, P = I.P, M = I.M;
+    const int n = I.n, M = I.M;
     const double n3 = (double)n * n * n;
-    InstDev d = I.dev();
-    if (P > 0) {
-        c->stage(SGS_STAGE_PAIR_INVERSE);
-        c->stage_flops[SGS_STAGE_PAIR_INVERSE] += 2.0 * n3 * P;
-        cudaError_t e = pair_inverse(c, I, st);
+    const int ni = std::max(I.nimp, 1);
+    for (int ch = 0; ch < I.nch(); ch++) {
+        I.cur = ch;
+        const int P = I.ccnt();
+        cudaError_t e = pair_factors(c, I, st);
         if (e != cudaSuccess) return e;
-        c->stage(SGS_STAGE_PAIR_DELTA);
-        c->stage_flops[SGS_STAGE_PAIR_DELTA] += n3 * P;
-        if ((e = pair_delta(c, I, st)) != cudaSuccess) return e;
-        if (I.Ppf > 0) {
+        if (I.cpfcnt() > 0) {
             c->stage(SGS_STAGE_PHASE_PFAFFIAN);
-            c->stage_flops[SGS_STAGE_PHASE_PFAFFIAN] += 4.0 / 3.0 * n3 * I.Ppf;
+            c->stage_flops[SGS_STAGE_PHASE_PFAFFIAN] += 4.0 / 3.0 * n3 * I.cpfcnt();
             if ((e = pair_phase(c, I, st)) != cudaSuccess) return e;
         }
+        c->stage(SGS_STAGE_AMPLITUDES);
+        pair_gh_kernel<<<P + (ch == 0 ? M : 0), 256, 0, st>>>(I.dev(), I.si, I.imd, I.logdet, I.pfphase, I.Gm, I.hm,
+                                                              I.fimp + (size_t)I.coff() * ni * ni * 2, I.fimp_state);
+        counted();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    c->stage(SGS_STAGE_AMPLITUDES);
-    pair_gh_kernel<<<P + M, 256, 0, st>>>(d, I.si, I.imd, I.logdet, I.pfphase, I.Gm, I.hm, I.fimp, I.fimp_state);
-    counted();
-    return cudaGetLastError();
+    I.cur = 0;
+    return cudaSuccess;
 }
 
 // amplitude solve (A6) on the instance's G, h; E -> Eout
@@ -1081,64 +1149,63 @@ sgs_status autotune_instance(sgs_ctx* c, Instance& I) {
     return SGS_OK;
 }
 
-cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
-    const int n = I.n, P = I.P, M = I.M;
+// the pair part of the equation of motion for the current chunk's pairs: the dense products W, V,
+// X, the low-rank impurity terms and the Delta F Delta planes Q (into xa, wr)
+cudaError_t eom_pair_chunk(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    const int n = I.n, P = I.ccnt();
     const size_t nn = (size_t)n * n;
     const double n3 = (double)n * n * n;
+    const int ni = std::max(I.nimp, 1);
+    const double* fimp = I.fimp + (size_t)I.coff() * ni * ni * 2;
+    double** ga = I.p_ga + I.coff();
+    double** gb = I.p_gb + I.coff();
     InstDev d = I.dev();
     cudaError_t e;
     c->stage(SGS_STAGE_EOM_W);
-    c->stage_flops[SGS_STAGE_EOM_W] += n3 * P + n3 * M;   // Wr, Gamma F Gamma: antisymmetric
-    // per state: T2 = F Gamma (s0), GFG = Gamma T2 (s4)
-    state_sparse_left_kernel<<<dim3(grid_chunks(nn, 256, 256), M), 256, 0, st>>>(d, I.fimp_state, I.s[0]);
-    counted();
-    {
-        GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_s[0], n, I.p_s[4], n, M);
-        g.mode = GEMM_SKEW;
-        if ((e = gemm(c, I, g, st, n3 * M)) != cudaSuccess) return e;
-    }
-    if (P > 0 && I.tc_kind >= 0) {
+    c->stage_flops[SGS_STAGE_EOM_W] += n3 * P;   // Wr: antisymmetric
+    if (I.tc_kind >= 0) {
         // tensor-core path: W = T1 S^{-1}, V = D W, X = V D, every B antisymmetric, so its
         // K-major form is -B and alpha = -1
         const int kind = I.tc_kind;
         const unsigned gch = grid_chunks(nn, 256, 64);
-        pair_sparse_right_kernel<<<dim3(gch, P), 256, 0, st>>>(d, I.si, I.fimp, I.work);
+        pair_sparse_right_kernel<<<dim3(gch, P), 256, 0, st>>>(d, I.si, fimp, I.work);
         const int ldp = I.ldp;
         lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_si, nullptr, I.q_si_hi,
                                                                   I.q_si_lo, n, ldp, kind);
         lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_work, nullptr, I.q_t1_hi,
                                                                   I.q_t1_lo, n, ldp, kind);
-        lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_ga,
-                                                                  (const double* const*)I.p_gb, I.q_d_hi, I.q_d_lo,
-                                                                  n, ldp, kind);
+        lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)ga, (const double* const*)gb,
+                                                                  I.q_d_hi, I.q_d_lo, n, ldp, kind);
         counted(); counted(); counted(); counted();
-        if ((e = tma_product(I.tma_w, kind, st)) != cudaSuccess) return e;
+        TmaBatch tw = I.tma_w, tv = I.tma_v, tx = I.tma_x;
+        tw.batch = tv.batch = tx.batch = P;
+        if ((e = tma_product(tw, kind, st)) != cudaSuccess) return e;
         counted();
         lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_wr32, nullptr, I.q_wr_hi,
                                                                  I.q_wr_lo, n, ldp, kind);
         counted();
         c->stage(SGS_STAGE_EOM_V);
         c->stage_flops[SGS_STAGE_EOM_V] += 2.0 * n3 * P;
-        if ((e = tma_product(I.tma_v, kind, st)) != cudaSuccess) return e;
+        if ((e = tma_product(tv, kind, st)) != cudaSuccess) return e;
         counted();
         c->stage(SGS_STAGE_EOM_X);
         c->stage_flops[SGS_STAGE_EOM_X] += n3 * P;
         lp_convert_kernel<float><<<dim3(gch, P), 256, 0, st>>>((const float* const*)I.q_va32, nullptr, I.q_va_hi,
                                                                  I.q_va_lo, n, ldp, kind);
         counted();
-        if ((e = tma_product(I.tma_x, kind, st)) != cudaSuccess) return e;
+        if ((e = tma_product(tx, kind, st)) != cudaSuccess) return e;
         counted();
         c->stage(SGS_STAGE_EOM_ASSEMBLY);
         if (I.nimp > 0) {
-            pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.fimp, I.lr);
+            pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, fimp, I.lr);
             counted();
         }
         const unsigned qt = (unsigned)(((n + 31) / 32) * ((n + 31) / 32));
         pair_q_kernel<float><<<dim3(qt, P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va32, I.xa32, I.wr32, I.xa, I.wr);
         counted();
-    } else if (P > 0) {
+    } else {
         // T1 = S^{-1} (A + Re Fimp)  (into work), Wr = T1 S^{-1}
-        pair_sparse_right_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.si, I.fimp, I.work);
+        pair_sparse_right_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.si, fimp, I.work);
         counted();
         GemmBatch g = gb_basic(n, n, n, I.p_work, n, I.p_si, n, I.p_wr, n, P);
         g.mode = GEMM_SKEW;
@@ -1147,51 +1214,100 @@ cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
         // V = D Wr
         c->stage(SGS_STAGE_EOM_V);
         c->stage_flops[SGS_STAGE_EOM_V] += 2.0 * n3 * P;
-        c->stage_bytes[SGS_STAGE_EOM_V] += 8.0 * nn * (2.0 * P + M);   // read Wr, write V; Gamma once
-        g = gb_basic(n, n, n, I.p_ga, n, I.p_wr, n, I.p_va, n, P);
-        g.A2 = (const double* const*)I.p_gb; g.sA2 = -1.0;
+        c->stage_bytes[SGS_STAGE_EOM_V] += 8.0 * nn * (2.0 * P + I.M);   // read Wr, write V; Gamma once
+        g = gb_basic(n, n, n, ga, n, I.p_wr, n, I.p_va, n, P);
+        g.A2 = (const double* const*)gb; g.sA2 = -1.0;
         g.b_antisym = 1;    // Wr (an antisymmetric product)
         if ((e = gemm(c, I, g, st, 2.0 * n3 * P)) != cudaSuccess) return e;
         // X = V D
         c->stage(SGS_STAGE_EOM_X);
         c->stage_flops[SGS_STAGE_EOM_X] += n3 * P;
-        g = gb_basic(n, n, n, I.p_va, n, I.p_ga, n, I.p_xa, n, P);
-        g.B2 = (const double* const*)I.p_gb; g.sB2 = -1.0;
+        g = gb_basic(n, n, n, I.p_va, n, ga, n, I.p_xa, n, P);
+        g.B2 = (const double* const*)gb; g.sB2 = -1.0;
         g.mode = GEMM_SKEW;
         g.b_antisym = 1;    // Gamma_a - Gamma_b
         if ((e = gemm(c, I, g, st, n3 * P)) != cudaSuccess) return e;
         c->stage(SGS_STAGE_EOM_ASSEMBLY);
         if (I.nimp > 0) {
-            pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, I.fimp, I.lr);
+            pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, fimp, I.lr);
             counted();
         }
         pair_q_kernel<double><<<dim3((unsigned)(((n + 31) / 32) * ((n + 31) / 32)), P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va, I.xa,
                                                                                    I.wr, I.xa, I.wr);
         counted();
-    } else {
+    }
+    return cudaGetLastError();
+}
+
+// Equation of motion of every state (A7).  The pairs' part runs chunk by chunk, last chunk first:
+// its S^{-1} and Im Delta are still those of the pair pass; the other chunks recompute theirs.
+// The pair sums D (into dGamma) and T (into s1) accumulate over the chunks; the last part of the
+// assembly (sparse terms on T, the beta = mu terms) runs once.
+cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    const int n = I.n, M = I.M;
+    const size_t nn = (size_t)n * n;
+    const double n3 = (double)n * n * n;
+    const int ni = std::max(I.nimp, 1);
+    cudaError_t e;
+    c->stage(SGS_STAGE_EOM_W);
+    c->stage_flops[SGS_STAGE_EOM_W] += n3 * M;   // Gamma F Gamma: antisymmetric
+    // per state: T2 = F Gamma (s0), GFG = Gamma T2 (s4)
+    state_sparse_left_kernel<<<dim3(grid_chunks(nn, 256, 256), M), 256, 0, st>>>(I.dev(), I.fimp_state, I.s[0]);
+    counted();
+    {
+        GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_s[0], n, I.p_s[4], n, M);
+        g.mode = GEMM_SKEW;
+        if ((e = gemm(c, I, g, st, n3 * M)) != cudaSuccess) return e;
+    }
+    const int nch = I.nch();
+    const bool chunked = nch > 1;
+    const dim3 eg(grid_chunks(nn, 256, 1024), M);
+    double* tsum = I.s[1];
+    for (int ch = nch - 1; ch >= 0; ch--) {
+        I.cur = ch;
+        if (chunked && ch != nch - 1 && (e = pair_factors(c, I, st)) != cudaSuccess) return e;
+        if (I.ccnt() > 0 && (e = eom_pair_chunk(c, I, st)) != cudaSuccess) return e;
         c->stage(SGS_STAGE_EOM_ASSEMBLY);
+        const InstDev d = I.dev();
+        const double* fimp = I.fimp + (size_t)I.coff() * ni * ni * 2;
+        const int acc = ch != nch - 1;
+        const int part = chunked ? EOM_FINISH_PAIRS : EOM_FINISH_ALL;
+        // the sums over beta: D into dGamma, T into s1
+        if (I.tc_kind >= 0) {
+            eom_pairs_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef,
+                                                                         I.pair_index, tsum, I.dgamma, acc);
+            eom_finish_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, fimp, I.fimp_state, I.s[4],
+                                                                          I.coef, I.pair_index, tsum, I.dgamma,
+                                                                          I.self_mask, part);
+        } else {
+            eom_pairs_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef,
+                                                                           I.pair_index, tsum, I.dgamma, acc);
+            eom_finish_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, fimp, I.fimp_state, I.s[4],
+                                                                            I.coef, I.pair_index, tsum, I.dgamma,
+                                                                            I.self_mask, part);
+        }
+        counted(); counted();
+    }
+    I.cur = 0;
+    if (chunked) {
+        const InstDev d = I.dev_all();
+        if (I.tc_kind >= 0)
+            eom_finish_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.fimp, I.fimp_state, I.s[4],
+                                                                          I.coef, I.pair_index, tsum, I.dgamma,
+                                                                          I.self_mask, EOM_FINISH_REST);
+        else
+            eom_finish_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.fimp, I.fimp_state,
+                                                                            I.s[4], I.coef, I.pair_index, tsum,
+                                                                            I.dgamma, I.self_mask, EOM_FINISH_REST);
+        counted();
+    }
+    if (I.tc_kind >= 0) {
+        antisymmetrise_kernel<<<eg, 256, 0, st>>>(I.dgamma, n);
+        counted();
     }
     // algorithmic bytes: pair_q reads Si, Im, V (twice), X, Wr and writes Qr, Qi; the EOM
     // reads Si, Im, Qr, Qi once per receiver of each pair plus Gamma, GFG and writes dGamma
-    c->stage_bytes[SGS_STAGE_EOM_ASSEMBLY] += 8.0 * nn * (7.0 * P + 8.0 * P + 3.0 * M);
-    // the sums over beta: D into dGamma, T into the work buffer (free at this point)
-    const dim3 eg(grid_chunks(nn, 256, 1024), M);
-    if (I.tc_kind >= 0) {
-        eom_pairs_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef, I.pair_index,
-                                                                     I.work, I.dgamma);
-        eom_finish_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.fimp, I.fimp_state, I.s[4],
-                                                                      I.coef, I.pair_index, I.work, I.dgamma,
-                                                                      I.self_mask);
-        antisymmetrise_kernel<<<eg, 256, 0, st>>>(I.dgamma, n);
-        counted();
-    } else {
-        eom_pairs_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef,
-                                                                       I.pair_index, I.work, I.dgamma);
-        eom_finish_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.fimp, I.fimp_state, I.s[4],
-                                                                        I.coef, I.pair_index, I.work, I.dgamma,
-                                                                        I.self_mask);
-    }
-    counted(); counted();
+    c->stage_bytes[SGS_STAGE_EOM_ASSEMBLY] += 8.0 * nn * (7.0 * I.P + 8.0 * I.P + 3.0 * M);
     return cudaGetLastError();
 }
 
@@ -1518,6 +1634,7 @@ sgs_status check_args(const sgs_model& m, const sgs_options& o) {
     if (o.fp64_path != SGS_FP64_EMULATED && o.fp64_path != SGS_FP64_FMA) return SGS_EINVAL;
     if (o.shard_world < 0 || (o.shard_world > 1 && (o.shard_rank < 0 || o.shard_rank >= o.shard_world)))
         return SGS_EINVAL;
+    if (o.pair_chunk < 0) return SGS_EINVAL;
     if (o.gamma0) {           // finite and antisymmetric (purity is reported by sgs_health)
         const int n = 2 * m.n_modes;
         for (int mu = 0; mu < o.rank; mu++) {
@@ -1559,7 +1676,7 @@ sgs_status sgs_admit(sgs_ctx* c, const sgs_model* model, const sgs_options* opt,
     sgs_status s = check_args(*model, *opt);
     if (s != SGS_OK) { c->err = "invalid model, options or initial states (non-finite or not antisymmetric)"; return s; }
     const size_t need = instance_bytes(2 * model->n_modes, opt->rank, opt->precision, 16, c->autotune,
-                                       opt->fp64_path, oz_cap_of(opt->emulation_scratch));
+                                       opt->fp64_path, oz_cap_of(opt->emulation_scratch), opt->pair_chunk);
     if (c->budget && c->bytes_in_use + need > c->budget) {
         c->err = "over the HBM budget: " + std::to_string(c->bytes_in_use + need) + " > " + std::to_string(c->budget);
         return SGS_ENOMEM;
@@ -1684,7 +1801,10 @@ sgs_status sgs_set_panel_widths(sgs_ctx* c, int instance, int gj_width, int pf_w
 
 sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
     if (!c || slot < 0 || slot >= (int)c->inst.size() || !c->inst[slot].live || !K) return SGS_EINVAL;
-    if (c->inst[slot].shard_world > 1) { c->err = "rank growth is not available on a pair-sharded instance"; return SGS_EINVAL; }
+    if (c->inst[slot].shard_world > 1 || c->inst[slot].nch() > 1) {
+        c->err = "rank growth is not available on a pair-sharded or pair-chunked instance";
+        return SGS_EINVAL;
+    }
     const int n = c->inst[slot].n, M = c->inst[slot].M;
     if (M + 1 > SGS_MAX_RANK) { c->err = "the rank is already at its maximum"; return SGS_EINVAL; }
     if (src < -1 || src >= M) { c->err = "src out of range"; return SGS_EINVAL; }
@@ -1708,7 +1828,7 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
             if (a > best) { best = a; src = mu; }
         }
     }
-    const size_t need = instance_bytes(n, M + 1, I.prec, 16, c->autotune, I.fp64_path, I.oz_cap);
+    const size_t need = instance_bytes(n, M + 1, I.prec, 16, c->autotune, I.fp64_path, I.oz_cap, 0);
     if (c->budget && c->bytes_in_use - I.bytes + need > c->budget) {
         c->err = "over the HBM budget: " + std::to_string(c->bytes_in_use - I.bytes + need) + " > " +
                  std::to_string(c->budget);
@@ -1719,7 +1839,7 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
     sgs_model m{I.N, I.hA.data(), (int)I.hq_val.size(), I.hq_idx.data(), I.hq_val.data(), I.e_const,
                 I.nh, I.hh_len.data(), I.hh_idx.data(), I.hh_val.data()};
     sgs_options o{M + 1, I.dtau, I.prec, I.cmode, I.parity, nullptr, nullptr, nullptr, I.integrator, 0,
-                  I.fp64_path, I.oz_cap};
+                  I.fp64_path, I.oz_cap, 0, 1, 0};
     c->owner = &J;
     sgs_status s = setup_instance(c, J, m, o);
     c->owner = nullptr;
@@ -1965,7 +2085,10 @@ sgs_status sgs_shard_update(sgs_ctx* c, int instance, const double* dgamma) {
 
 sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const int* sites, int n_sites, double* out) {
     if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live || !sites || !out || n_sites < 0) return SGS_EINVAL;
-    if (c->inst[instance].shard_world > 1) { c->err = "observables need every pair: not on a pair-sharded instance"; return SGS_EINVAL; }
+    if (c->inst[instance].shard_world > 1 || c->inst[instance].nch() > 1) {
+        c->err = "observables need every pair at once: not on a pair-sharded or pair-chunked instance";
+        return SGS_EINVAL;
+    }
     if (n_sites == 0) return SGS_OK;
     Instance& I = c->inst[instance];
     const int nsite_tot = I.n / 4;          // spinful sites: modes 2s, 2s+1 -> Majoranas 4s..4s+3
@@ -2067,7 +2190,10 @@ sgs_status sgs_correlator(sgs_ctx* c, int instance, sgs_corr_kind kind, const in
 sgs_status sgs_variance(sgs_ctx* c, int instance, double* energy, double* variance) {
     if (!c || instance < 0 || instance >= (int)c->inst.size() || !c->inst[instance].live) return SGS_EINVAL;
     Instance& I = c->inst[instance];
-    if (I.shard_world > 1) { c->err = "observables need every pair: not on a pair-sharded instance"; return SGS_EINVAL; }
+    if (I.shard_world > 1 || I.nch() > 1) {
+        c->err = "observables need every pair at once: not on a pair-sharded or pair-chunked instance";
+        return SGS_EINVAL;
+    }
     if (I.nc > VAR_MAX_MON) { c->err = "more quartic monomials than the variance kernel handles"; return SGS_EINVAL; }
     if (I.nh > 0) { c->err = "the variance covers quadratic and quartic terms"; return SGS_EINVAL; }
     CUDA_TRY(c, pair_pass(c, I, I.Ecur, c->stream));

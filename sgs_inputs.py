@@ -173,6 +173,10 @@ LARGE = Workload("anderson_L128_M32", AndersonParams(n_bath=127, U=4.0, eps_d=-2
 TWO_CHANNEL = Workload("two_channel_L201_M64",
                        AndersonParams(n_bath=100, U=8.0, eps_d=-4.0, V=0.6, n_channels=2), rank=64,
                        dtau=0.05, n_steps=1000, seed=3, parity=-1)
+# the system of Sec. IV A's energy extrapolation: L = 500 sites (impurity + 499 bath sites), U = t = 1,
+# U / Gamma = 5 with Gamma = t'^2 / t, mu = 0, eps_d = -U/2; rank 16, the largest rank the paper reports there
+SIAM_L500 = Workload("siam_L500_M16", AndersonParams(n_bath=499, U=1.0, eps_d=-0.5, V=0.2 ** 0.5), rank=16,
+                     dtau=0.05, n_steps=0, seed=5)
 
 
 def batched_workloads(n_instances: int = 256, seed: int = 4, dtau: float = 0.05, n_bath=(16, 256),
