@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=16, help="serving: number of requests")
     ap.add_argument("--max-steps", type=int, default=400, help="serving: step cap per solve")
     ap.add_argument("--serving-dtau", type=float, default=0.2, help="serving: imaginary-time step")
+    ap.add_argument("--serving-mix", default="scaled", choices=["scaled", "configured"],
+                    help="serving: request sizes L ~ U{8..40}, M in {4, 8} (scaled) or L ~ U{16..256}, "
+                         "M in {8, 16, 32} (the batched workload's mix)")
     ap.add_argument("--rank", type=int, default=0, help="override the ansatz rank M (profiling cases)")
     ap.add_argument("--fp64-path", default="emulated", choices=["fma", "emulated"],
                     help="FP64 products: emulated on the bf16 tensor cores (the library's default) or FMA pipe")
@@ -474,8 +477,12 @@ def run_serving(args):
     sgs.use_torch_allocator()
     prec = PRECISIONS[args.precision]
     reqs = []
-    for i, (t, p, M, seed, par) in enumerate(inp.serving_requests(args.rate, args.requests, seed=7)):
-        g, lam = inp.initial_state(p.n_modes, M, seed, par)
+    mix = dict(n_bath=(16, 256), ranks=(8, 16, 32)) if args.serving_mix == "configured" else {}
+    for i, (t, p, M, seed, par) in enumerate(inp.serving_requests(args.rate, args.requests, seed=7, **mix)):
+        if args.serving_mix == "configured":
+            g, lam = clustered_states_device(p.n_modes, M, seed, par)
+        else:
+            g, lam = inp.initial_state(p.n_modes, M, seed, par)
         reqs.append(Request(i, t, sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V), g, lam, par))
     stream = torch.cuda.Stream()
     budget = int(torch.cuda.get_device_properties(0).total_memory * 0.5)
@@ -501,7 +508,9 @@ def run_serving(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype_of(args), "data": "synthetic",
             "config": {"workload": f"serving: {args.requests} Anderson solves, Poisson rate {args.rate}/s, "
-                                   "bath L ~ U{8..40}, M in {4, 8}, U ~ U[0,8], V ~ U[0.2,1], run to |dE| < 1e-8 "
+                                   + ("bath L ~ U{16..256}, M in {8, 16, 32} (clustered initial states)"
+                                      if args.serving_mix == "configured" else "bath L ~ U{8..40}, M in {4, 8}")
+                                   + ", U ~ U[0,8], V ~ U[0.2,1], run to |dE| < 1e-8 "
                                    f"per step or {args.max_steps} steps at ds = {args.serving_dtau}, phase form of c_mu",
                        "hbm_budget_bytes": budget},
             "latency": {"p50_s": a["p50_s"], "p99_s": a["p99_s"], "mean_s": a["mean_s"]},
@@ -510,6 +519,36 @@ def run_serving(args):
             "max_rel_energy_diff_vs_sequential_fp64": dE}
     print(json.dumps(line))
     return 0
+
+
+def clustered_states_device(n_modes, M, seed, parity, spread=1.0):
+    """The clustered pure states of sgs_inputs.clustered_pure_gammas (Gamma_mu = O_mu Gamma_0 O_mu^T,
+    O_mu = exp(K_mu), K_mu antisymmetric N(0, (spread / n)^2), Gamma_0 = O J O^T with O Haar from
+    the QR of a normal matrix, the first column negated for the parity), drawn with a seeded torch
+    generator on the device: the host's dense exponentials of n ~ 1000 matrices would take longer
+    than the benchmark.  Returns host arrays (gamma [M, n, n], lambda [M])."""
+    import torch
+    n = 2 * n_modes
+    gen = torch.Generator(device="cuda").manual_seed(int(seed))
+    X = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=gen)
+    Q, R = torch.linalg.qr(X)
+    Q = Q * torch.sign(torch.diagonal(R))
+    if (torch.linalg.det(Q) > 0) != (parity > 0):
+        Q[:, 0] = -Q[:, 0]
+    J = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    idx = torch.arange(0, n, 2, device="cuda")
+    J[idx, idx + 1] = 1.0
+    J[idx + 1, idx] = -1.0
+    base = Q @ J @ Q.T
+    out = []
+    for _ in range(M):
+        K = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=gen) * (spread / n)
+        O = torch.linalg.matrix_exp(K - K.T)
+        G = O @ base @ O.T
+        out.append(0.5 * (G - G.T))
+    g = torch.stack(out).cpu().numpy()
+    th = torch.rand(M, dtype=torch.float64, device="cuda", generator=gen).cpu().numpy() * 2.0 * np.pi
+    return np.ascontiguousarray(g), np.exp(1j * th)
 
 
 def run_batched(args):
@@ -550,9 +589,12 @@ def run_batched(args):
             # clustered states (order-one overlaps, as rank growth produces them): random pure states
             # of unrelated orientation give amplitudes near 1e-14, whose c_mu = 1/(lambda lambda-tilde*)
             # turns the first steps into rotations far outside a small step
-            rng = np.random.default_rng(w.seed)
-            g = inp.clustered_pure_gammas(p.n_modes, w.rank, rng, w.parity, spread=1.0)
-            lam = inp.random_amplitudes(w.rank, rng)
+            if args.max_bath <= 64:
+                rng = np.random.default_rng(w.seed)
+                g = inp.clustered_pure_gammas(p.n_modes, w.rank, rng, w.parity, spread=1.0)
+                lam = inp.random_amplitudes(w.rank, rng)
+            else:
+                g, lam = clustered_states_device(p.n_modes, w.rank, w.seed, w.parity)
             # phase form of c_mu (Sec. III A): the inverse form divides by the amplitude, and from these
             # starts it drives rotations with ||X||_F of 1e2..1e3 per step
             try:
@@ -604,7 +646,8 @@ def run_batched(args):
             "config": {"workload": f"batched: {len(ws)} Anderson instances, bath L ~ U{{16..{args.max_bath}}}, "
                                    "M in {8,16,32}, U ~ U[0,8], eps_d = -U/2, V ~ U[0.2,1], ds = 0.05",
                        "n_range": [min(ns), max(ns)], "precision": args.precision,
-                       "inputs": "clustered pure states O_mu = exp(K_mu) O around one Haar O, random phases",
+                       "inputs": "clustered pure states O_mu = exp(K_mu) O around one Haar O, random phases"
+                                 + ("" if args.max_bath <= 64 else " (drawn on the device with a seeded torch generator)"),
                        "c_mu": "phase form (Sec. III A)", "autotune": autotune,
                        "hbm_budget_bytes": budget,
                        "waves": waves,

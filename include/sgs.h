@@ -360,9 +360,10 @@ sgs_status sgs_get_profile(const sgs_ctx* ctx, double* ms, double* flops, double
                            double* gemm_f64);
 
 /* Measured throughput (TFLOP/s) of an FP64 pipe of the current device:
- * kind 0 = the m8n8k4 FP64 MMA (the path of every FP64 product here),
- * kind 1 = FP64 FMA on the CUDA cores, kind 2 = both interleaved in one
- * kernel (their sum shows whether the two share one pipe). */
+ * kind 0 = the m8n8k4 FP64 MMA (mma.sync .f64), kind 1 = FP64 FMA on the
+ * CUDA cores (the pipe of the SGS_FP64_FMA products and of the
+ * factorisations' panels), kind 2 = both interleaved in one kernel (their sum
+ * shows whether the two share one pipe). */
 sgs_status sgs_probe_peak(int kind, double* tflops);
 
 /* Majorana form of the Anderson impurity of Sec. IV (H_0 + H_I) with

@@ -108,9 +108,14 @@ __global__ void pf_build_kernel(InstDev d, const double* si, const double* imd, 
 //   G_ab = |G_ab| e^{i phi}, log|G_ab| = (-N log 2 + log|det S|/2)/2,
 //   phase from Pf(Gamma_0) Pf(Gamma_0 + Delta^{a,b}) (reference gauge), and
 //   h_ba = G_ba (e_const + Tr(A Delta^{a,b}) - 3 sum U Delta Delta).
+// parts: GH_FOCK (the impurity blocks of F and the energy density, into dens), GH_GRAM (G and h
+// from dens, log|det S| and the phase Pfaffian), or both.  The equation of motion's products need
+// only the first, so they may run while the phase Pfaffians are computed.
+enum { GH_FOCK = 1, GH_GRAM = 2, GH_ALL = 3 };
 __global__ void __launch_bounds__(256) pair_gh_kernel(InstDev d, const double* si, const double* imd,
                                                       const double* logdet, const double* pfphase,
-                                                      double* Gm, double* hm, double* fimp, double* fimp_state) {
+                                                      double* Gm, double* hm, double* fimp, double* fimp_state,
+                                                      int part, double* dens_buf) {
     __shared__ double red[32];
     const int blk = blockIdx.x;
     const bool diag = blk >= d.P;
@@ -118,6 +123,41 @@ __global__ void __launch_bounds__(256) pair_gh_kernel(InstDev d, const double* s
     const int a = diag ? blk - d.P : d.pa[p];
     const int bq = diag ? a : d.pb[p];
     const int n = d.n;
+    if (!(part & GH_FOCK)) {
+        // G and h from the stored energy density
+        if (threadIdx.x == 0) {
+            const int M = d.M;
+            const cplx dens = cmk(dens_buf[2 * blk], dens_buf[2 * blk + 1]);
+            if (diag) {
+                Gm[2 * (a * M + a)] = 1.0;
+                Gm[2 * (a * M + a) + 1] = 0.0;
+                hm[2 * (a * M + a)] = dens.x;
+                hm[2 * (a * M + a) + 1] = 0.0;
+            } else {
+                double ld = logdet[p];
+                double mag = (ld == -INFINITY || ld != ld) ? 0.0 : exp(0.5 * (-d.N * 0.6931471805599453 + 0.5 * ld));
+                cplx ph = cmk(1.0, 0.0);
+                int q2 = d.pair_pf[p];
+                if (q2 >= 0) {
+                    ph = cmk(d.parity * pfphase[2 * q2], d.parity * pfphase[2 * q2 + 1]);
+                    double m2 = sqrt(cabs2(ph));
+                    ph = m2 > 0.0 ? cscale(ph, 1.0 / m2) : cmk(0.0, 0.0);
+                }
+                cplx gab = cscale(ph, mag);
+                cplx gba = cconj(gab);
+                cplx hba = cmul(gba, dens);
+                Gm[2 * (a * M + bq)] = gab.x;
+                Gm[2 * (a * M + bq) + 1] = gab.y;
+                Gm[2 * (bq * M + a)] = gba.x;
+                Gm[2 * (bq * M + a) + 1] = gba.y;
+                hm[2 * (bq * M + a)] = hba.x;
+                hm[2 * (bq * M + a) + 1] = hba.y;
+                hm[2 * (a * M + bq)] = hba.x;
+                hm[2 * (a * M + bq) + 1] = -hba.y;
+            }
+        }
+        return;
+    }
     const double* dr = diag ? d.gamma + (size_t)a * nn(d) : si + (size_t)p * nn(d);
     const double* di = diag ? nullptr : imd + (size_t)p * nn(d);
     // Delta^{a,b}[k][l] = -2 Si[k][l] + i Im[k][l];  Delta^{a,a} = Gamma_a
@@ -181,6 +221,17 @@ __global__ void __launch_bounds__(256) pair_gh_kernel(InstDev d, const double* s
         }
         cplx dens = cmk(d.e_const + tr_r - 3.0 * q.x + qh.x, tr_i - 3.0 * q.y + qh.y);
         const int M = d.M;
+        if (!(part & GH_GRAM)) {
+            dens_buf[2 * blk] = dens.x;
+            dens_buf[2 * blk + 1] = dens.y;
+            if (diag) {
+                for (int e = 0; e < ni * ni; e++) fimp_state[(size_t)a * ni * ni + e] = F[e].x;
+            } else {
+                double* fp = fimp + (size_t)p * ni * ni * 2;
+                for (int e = 0; e < ni * ni; e++) { fp[2 * e] = F[e].x; fp[2 * e + 1] = F[e].y; }
+            }
+            return;
+        }
         if (diag) {
             Gm[2 * (a * M + a)] = 1.0;
             Gm[2 * (a * M + a) + 1] = 0.0;

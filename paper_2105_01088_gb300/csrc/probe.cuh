@@ -1,6 +1,7 @@
 // Throughput probes of the FP64 pipes, so that the FP64 roofline is measured
-// on the device at hand: the m8n8k4 FP64 MMA (the path every FP64 product of
-// the step takes) and plain FP64 FMA.  Fixed-length loops, one store each.
+// on the device at hand: the m8n8k4 FP64 MMA and plain FP64 FMA (the pipe of
+// the FMA-path products and of the factorisations' panels).  Fixed-length
+// loops, one store each.
 #pragma once
 #include "common.cuh"
 

@@ -59,6 +59,10 @@ struct Instance {
     size_t bytes = 0;
     cudaStream_t st = nullptr;          // branch stream of the captured step
     cudaEvent_t join = nullptr;
+    // the equation of motion's products run on a side stream while the phase Pfaffians run
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    double* dens = nullptr;             // [P + M] complex energy densities (between the two parts of pair_gh)
     int N = 0, n = 0, M = 0, P = 0, Ppf = 0, nimp = 0, nq = 0, a_nnz = 0;
     double dtau = 0.0, e_const = 0.0;
     int prec = 0, cmode = 0, parity = 1, integrator = 0;
@@ -125,6 +129,8 @@ struct Instance {
     double* eigscratch = nullptr;
     int* err = nullptr;
     OzBuf oz;                           // emulated FP64 products: slice scratch (path 2 only)
+    OzBuf oz2;                          // the side stream's slice scratch (unchunked instances)
+    int oz_side = 0;                    // 1 while the side stream's products are enqueued
 
     // tensor-core (mixed precision) operands of the equation of motion, per pair:
     // low-precision hi (fp32 or bf16) and lo (3xTF32) parts of S^{-1}, T1 = S^{-1} F,
@@ -362,7 +368,7 @@ size_t instance_bytes(int n, int M, int prec, int nimp, bool tune, int fp64_path
         if (prec != SGS_FP32_3XTF32)
             bytes += (size_t)M * nn * 4 + (size_t)M * n * ldp * (9 * 4 + 10 * esz);   // mixed update
     }
-    if (fp64_path == SGS_FP64_EMULATED) bytes += oz_scratch_bytes(n, M, oz_cap, P);
+    if (fp64_path == SGS_FP64_EMULATED) bytes += oz_scratch_bytes(n, M, oz_cap, P) * (P == Pall ? 2 : 1);
     return bytes + (1 << 20);
 }
 
@@ -627,6 +633,7 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
     I.Ecur = c->alloc<double>(1);
     I.eigscratch = c->alloc<double>(6 * (size_t)(2 * M) * (2 * M) + 8 * 2 * M);
     I.err = c->alloc<int>(1);
+    I.dens = c->alloc<double>(2 * ((size_t)Pcm + M));
     if (I.shard_world > 1) {
         I.self_mask = c->alloc<int>(M);
         if (!I.self_mask) { c->err = "device allocation failed"; return SGS_ENOMEM; }
@@ -784,11 +791,16 @@ sgs_status setup_instance(sgs_ctx* c, Instance& I, const sgs_model& m, const sgs
         }
     }
     if (I.fp64_path == SGS_FP64_EMULATED) {
-        // emulated FP64 products: slice scratch for one batch chunk
+        // emulated FP64 products: slice scratch for one batch chunk, and one for the side stream
         const size_t b = oz_scratch_bytes(n, M, I.oz_cap, Pc);
         I.oz.base = static_cast<uint8_t*>(c->dalloc(b));
         if (!I.oz.base) { c->err = "device allocation failed (emulated-product scratch)"; return SGS_ENOMEM; }
         I.oz.bytes = b;
+        if (I.nch() == 1 && P > 0) {
+            I.oz2.base = static_cast<uint8_t*>(c->dalloc(b));
+            if (!I.oz2.base) { c->err = "device allocation failed (emulated-product scratch)"; return SGS_ENOMEM; }
+            I.oz2.bytes = b;
+        }
     }
     return SGS_OK;
 }
@@ -854,7 +866,7 @@ inline cudaError_t gemm(sgs_ctx* c, const GemmBatch& g, cudaStream_t st, double 
     return run();
 }
 inline cudaError_t gemm(sgs_ctx* c, Instance& I, const GemmBatch& g, cudaStream_t st, double flops) {
-    return gemm(c, g, st, flops, &I.oz, I.err);
+    return gemm(c, g, st, flops, I.oz_side ? &I.oz2 : &I.oz, I.err);
 }
 
 GemmBatch gb_basic(int m, int n, int k, double** A, int lda, double** B, int ldb, double** C, int ldc, int batch) {
@@ -1029,7 +1041,8 @@ cudaError_t pair_products(sgs_ctx* c, Instance& I, cudaStream_t st) {
         }
         c->stage(SGS_STAGE_AMPLITUDES);
         pair_gh_kernel<<<P + (ch == 0 ? M : 0), 256, 0, st>>>(I.dev(), I.si, I.imd, I.logdet, I.pfphase, I.Gm, I.hm,
-                                                              I.fimp + (size_t)I.coff() * ni * ni * 2, I.fimp_state);
+                                                              I.fimp + (size_t)I.coff() * ni * ni * 2, I.fimp_state,
+                                                              GH_ALL, I.dens);
         counted();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -1168,11 +1181,11 @@ cudaError_t eom_pair_chunk(sgs_ctx* c, Instance& I, cudaStream_t st) {
         // K-major form is -B and alpha = -1
         const int kind = I.tc_kind;
         const unsigned gch = grid_chunks(nn, 256, 64);
-        pair_sparse_right_kernel<<<dim3(gch, P), 256, 0, st>>>(d, I.si, fimp, I.work);
+        pair_sparse_right_kernel<<<dim3(gch, P), 256, 0, st>>>(d, I.si, fimp, I.va);   // T1 (V later)
         const int ldp = I.ldp;
         lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_si, nullptr, I.q_si_hi,
                                                                   I.q_si_lo, n, ldp, kind);
-        lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_work, nullptr, I.q_t1_hi,
+        lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)I.p_va, nullptr, I.q_t1_hi,
                                                                   I.q_t1_lo, n, ldp, kind);
         lp_convert_kernel<double><<<dim3(gch, P), 256, 0, st>>>((const double* const*)ga, (const double* const*)gb,
                                                                   I.q_d_hi, I.q_d_lo, n, ldp, kind);
@@ -1204,10 +1217,10 @@ cudaError_t eom_pair_chunk(sgs_ctx* c, Instance& I, cudaStream_t st) {
         pair_q_kernel<float><<<dim3(qt, P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va32, I.xa32, I.wr32, I.xa, I.wr);
         counted();
     } else {
-        // T1 = S^{-1} (A + Re Fimp)  (into work), Wr = T1 S^{-1}
-        pair_sparse_right_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.si, fimp, I.work);
+        // T1 = S^{-1} (A + Re Fimp)  (into va; V later), Wr = T1 S^{-1}
+        pair_sparse_right_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(d, I.si, fimp, I.va);
         counted();
-        GemmBatch g = gb_basic(n, n, n, I.p_work, n, I.p_si, n, I.p_wr, n, P);
+        GemmBatch g = gb_basic(n, n, n, I.p_va, n, I.p_si, n, I.p_wr, n, P);
         g.mode = GEMM_SKEW;
         g.b_antisym = 1;    // S^{-1}
         if ((e = gemm(c, I, g, st, n3 * P)) != cudaSuccess) return e;
@@ -1239,76 +1252,82 @@ cudaError_t eom_pair_chunk(sgs_ctx* c, Instance& I, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Equation of motion of every state (A7).  The pairs' part runs chunk by chunk, last chunk first:
-// its S^{-1} and Im Delta are still those of the pair pass; the other chunks recompute theirs.
-// The pair sums D (into dGamma) and T (into s1) accumulate over the chunks; the last part of the
-// assembly (sparse terms on T, the beta = mu terms) runs once.
-cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
+// the states' part of the equation of motion: T2 = F Gamma (s0), GFG = Gamma T2 (s4)
+cudaError_t eom_states(sgs_ctx* c, Instance& I, cudaStream_t st) {
     const int n = I.n, M = I.M;
     const size_t nn = (size_t)n * n;
     const double n3 = (double)n * n * n;
-    const int ni = std::max(I.nimp, 1);
-    cudaError_t e;
     c->stage(SGS_STAGE_EOM_W);
     c->stage_flops[SGS_STAGE_EOM_W] += n3 * M;   // Gamma F Gamma: antisymmetric
-    // per state: T2 = F Gamma (s0), GFG = Gamma T2 (s4)
     state_sparse_left_kernel<<<dim3(grid_chunks(nn, 256, 256), M), 256, 0, st>>>(I.dev(), I.fimp_state, I.s[0]);
     counted();
-    {
-        GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_s[0], n, I.p_s[4], n, M);
-        g.mode = GEMM_SKEW;
-        if ((e = gemm(c, I, g, st, n3 * M)) != cudaSuccess) return e;
-    }
-    const int nch = I.nch();
-    const bool chunked = nch > 1;
+    GemmBatch g = gb_basic(n, n, n, I.p_gamma, n, I.p_s[0], n, I.p_s[4], n, M);
+    g.mode = GEMM_SKEW;
+    return gemm(c, I, g, st, n3 * M);
+}
+
+// the sums over beta of the current chunk's pairs: D into dGamma, T into s1 (accumulate: add onto
+// them), and the finish part given
+void eom_sums(sgs_ctx* c, Instance& I, cudaStream_t st, int accumulate, int part, const InstDev& d) {
+    const int n = I.n, M = I.M;
+    const size_t nn = (size_t)n * n;
+    const int ni = std::max(I.nimp, 1);
     const dim3 eg(grid_chunks(nn, 256, 1024), M);
+    const double* fimp = I.fimp + (size_t)d.p_off * ni * ni * 2;
     double* tsum = I.s[1];
-    for (int ch = nch - 1; ch >= 0; ch--) {
-        I.cur = ch;
-        if (chunked && ch != nch - 1 && (e = pair_factors(c, I, st)) != cudaSuccess) return e;
-        if (I.ccnt() > 0 && (e = eom_pair_chunk(c, I, st)) != cudaSuccess) return e;
-        c->stage(SGS_STAGE_EOM_ASSEMBLY);
-        const InstDev d = I.dev();
-        const double* fimp = I.fimp + (size_t)I.coff() * ni * ni * 2;
-        const int acc = ch != nch - 1;
-        const int part = chunked ? EOM_FINISH_PAIRS : EOM_FINISH_ALL;
-        // the sums over beta: D into dGamma, T into s1
-        if (I.tc_kind >= 0) {
-            eom_pairs_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef,
-                                                                         I.pair_index, tsum, I.dgamma, acc);
-            eom_finish_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, fimp, I.fimp_state, I.s[4],
-                                                                          I.coef, I.pair_index, tsum, I.dgamma,
-                                                                          I.self_mask, part);
-        } else {
-            eom_pairs_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef,
-                                                                           I.pair_index, tsum, I.dgamma, acc);
-            eom_finish_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, fimp, I.fimp_state, I.s[4],
-                                                                            I.coef, I.pair_index, tsum, I.dgamma,
-                                                                            I.self_mask, part);
-        }
-        counted(); counted();
-    }
-    I.cur = 0;
-    if (chunked) {
-        const InstDev d = I.dev_all();
+    if (part & EOM_FINISH_PAIRS) {
         if (I.tc_kind >= 0)
-            eom_finish_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.fimp, I.fimp_state, I.s[4],
-                                                                          I.coef, I.pair_index, tsum, I.dgamma,
-                                                                          I.self_mask, EOM_FINISH_REST);
+            eom_pairs_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef,
+                                                                         I.pair_index, tsum, I.dgamma, accumulate);
         else
-            eom_finish_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.fimp, I.fimp_state,
-                                                                            I.s[4], I.coef, I.pair_index, tsum,
-                                                                            I.dgamma, I.self_mask, EOM_FINISH_REST);
+            eom_pairs_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, I.xa, I.wr, I.coef,
+                                                                           I.pair_index, tsum, I.dgamma, accumulate);
         counted();
     }
+    if (I.tc_kind >= 0)
+        eom_finish_kernel<float><<<eg, 256, eom_smem<float>(M), st>>>(d, I.si, I.imd, fimp, I.fimp_state, I.s[4],
+                                                                      I.coef, I.pair_index, tsum, I.dgamma,
+                                                                      I.self_mask, part);
+    else
+        eom_finish_kernel<double><<<eg, 256, eom_smem<double>(M), st>>>(d, I.si, I.imd, fimp, I.fimp_state, I.s[4],
+                                                                        I.coef, I.pair_index, tsum, I.dgamma,
+                                                                        I.self_mask, part);
+    counted();
+}
+
+// the end of the assembly: the float forms' exact antisymmetrisation, byte accounting
+cudaError_t eom_close(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    const int n = I.n, M = I.M;
+    const size_t nn = (size_t)n * n;
     if (I.tc_kind >= 0) {
-        antisymmetrise_kernel<<<eg, 256, 0, st>>>(I.dgamma, n);
+        antisymmetrise_kernel<<<dim3(grid_chunks(nn, 256, 1024), M), 256, 0, st>>>(I.dgamma, n);
         counted();
     }
     // algorithmic bytes: pair_q reads Si, Im, V (twice), X, Wr and writes Qr, Qi; the EOM
     // reads Si, Im, Qr, Qi once per receiver of each pair plus Gamma, GFG and writes dGamma
     c->stage_bytes[SGS_STAGE_EOM_ASSEMBLY] += 8.0 * nn * (7.0 * I.P + 8.0 * I.P + 3.0 * M);
     return cudaGetLastError();
+}
+
+// Equation of motion of every state (A7).  The pairs' part runs chunk by chunk, last chunk first:
+// its S^{-1} and Im Delta are still those of the pair pass; the other chunks recompute theirs.
+// The pair sums D (into dGamma) and T (into s1) accumulate over the chunks; the last part of the
+// assembly (sparse terms on T, the beta = mu terms) runs once.
+cudaError_t eom_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    cudaError_t e = eom_states(c, I, st);
+    if (e != cudaSuccess) return e;
+    const int nch = I.nch();
+    const bool chunked = nch > 1;
+    for (int ch = nch - 1; ch >= 0; ch--) {
+        I.cur = ch;
+        if (chunked && ch != nch - 1 && (e = pair_factors(c, I, st)) != cudaSuccess) return e;
+        if (I.ccnt() > 0 && (e = eom_pair_chunk(c, I, st)) != cudaSuccess) return e;
+        c->stage(SGS_STAGE_EOM_ASSEMBLY);
+        eom_sums(c, I, st, ch != nch - 1, chunked ? EOM_FINISH_PAIRS : EOM_FINISH_ALL, I.dev());
+    }
+    I.cur = 0;
+    if (chunked) eom_sums(c, I, st, 0, EOM_FINISH_REST, I.dev_all());
+    return eom_close(c, I, st);
 }
 
 // exp(X_s) for the first `batch` states (App. A), X_s = 2^-s X in s1 as exp_prepare_kernel
@@ -1500,6 +1519,59 @@ cudaError_t update_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
     if ((e = polar_pass(c, I, 1, st, 2)) != cudaSuccess) return e;
     I.steps_since_profile++;
     return cudaGetLastError();
+}
+
+// One step of an instance.  Unchunked instances fork after S^{-1} and Im Delta: the equation of
+// motion's products (they need the pairs' Fock blocks, not the overlaps or the amplitudes) run on a
+// side stream with their own slice scratch while the main stream computes the phase Pfaffians, G, h
+// and the amplitudes; the assembly waits for both.  The Pfaffians' FP64 panels and the products'
+// tensor-core work then share the GPU.  Chunked instances, and every instance while stage profiles
+// are taken (their stage events are on one stream), run the stages in order.  E -> Ecur.
+cudaError_t step_instance(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    const bool overlap = I.nch() == 1 && I.P > 0 && !c->prof;
+    if (!overlap) {
+        cudaError_t e = pair_pass(c, I, I.Ecur, st);
+        if (e == cudaSuccess) e = eom_pass(c, I, st);
+        if (e == cudaSuccess) e = update_pass(c, I, st);
+        return e;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!I.st2) e = cudaStreamCreateWithFlags(&I.st2, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !I.ev_fork) e = cudaEventCreateWithFlags(&I.ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !I.ev_join) e = cudaEventCreateWithFlags(&I.ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    I.cur = 0;
+    const int M = I.M, ni = std::max(I.nimp, 1);
+    (void)ni;
+    if ((e = pair_factors(c, I, st)) != cudaSuccess) return e;
+    pair_gh_kernel<<<I.P + M, 256, 0, st>>>(I.dev(), I.si, I.imd, I.logdet, I.pfphase, I.Gm, I.hm, I.fimp,
+                                            I.fimp_state, GH_FOCK, I.dens);
+    counted();
+    if ((e = cudaEventRecord(I.ev_fork, st)) != cudaSuccess) return e;
+    // side stream: the products of the equation of motion
+    if ((e = cudaStreamWaitEvent(I.st2, I.ev_fork, 0)) != cudaSuccess) return e;
+    I.oz_side = 1;
+    e = eom_states(c, I, I.st2);
+    if (e == cudaSuccess) e = eom_pair_chunk(c, I, I.st2);
+    I.oz_side = 0;
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(I.ev_join, I.st2)) != cudaSuccess) return e;
+    // main stream: overlaps, amplitudes
+    if (I.Ppf > 0) {
+        c->stage(SGS_STAGE_PHASE_PFAFFIAN);
+        c->stage_flops[SGS_STAGE_PHASE_PFAFFIAN] += 4.0 / 3.0 * (double)I.n * I.n * I.n * I.Ppf;
+        if ((e = pair_phase(c, I, st)) != cudaSuccess) return e;
+    }
+    c->stage(SGS_STAGE_AMPLITUDES);
+    pair_gh_kernel<<<I.P + M, 256, 0, st>>>(I.dev(), I.si, I.imd, I.logdet, I.pfphase, I.Gm, I.hm, I.fimp,
+                                            I.fimp_state, GH_GRAM, I.dens);
+    counted();
+    if ((e = amplitudes(I, I.Ecur, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, I.ev_join, 0)) != cudaSuccess) return e;
+    c->stage(SGS_STAGE_EOM_ASSEMBLY);
+    eom_sums(c, I, st, 0, EOM_FINISH_ALL, I.dev());
+    if ((e = eom_close(c, I, st)) != cudaSuccess) return e;
+    return update_pass(c, I, st);
 }
 
 // Reads and clears the device error word of every live instance.  Every instance whose
@@ -1887,6 +1959,8 @@ sgs_status sgs_add_state(sgs_ctx* c, int slot, const double* K, int src) {
     }
     J.st = I.st; J.join = I.join;        // the slot keeps its branch stream and event
     I.st = nullptr; I.join = nullptr;
+    J.st2 = I.st2; J.ev_fork = I.ev_fork; J.ev_join = I.ev_join;
+    I.st2 = nullptr; I.ev_fork = nullptr; I.ev_join = nullptr;
     c->release_instance(I);
     c->inst[slot] = std::move(J);
     c->drop_graph();
@@ -1942,9 +2016,7 @@ sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
         for (auto& I : c->inst) {
             if (!I.live) continue;
             if (ce == cudaSuccess) ce = cudaStreamWaitEvent(I.st, c->fork, 0);
-            if (ce == cudaSuccess) ce = pair_pass(c, I, I.Ecur, I.st);
-            if (ce == cudaSuccess) ce = eom_pass(c, I, I.st);
-            if (ce == cudaSuccess) ce = update_pass(c, I, I.st);
+            if (ce == cudaSuccess) ce = step_instance(c, I, I.st);
             if (ce == cudaSuccess) ce = cudaEventRecord(I.join, I.st);
             if (ce == cudaSuccess) ce = cudaStreamWaitEvent(c->stream, I.join, 0);
         }
@@ -1969,11 +2041,9 @@ sgs_status sgs_step(sgs_ctx* c, int n_steps, double* energies) {
         } else {
             for (auto& I : c->inst) {
                 if (!I.live) continue;
-                CUDA_TRY(c, pair_pass(c, I, I.Ecur, c->stream));
+                CUDA_TRY(c, step_instance(c, I, c->stream));
                 CUDA_TRY(c, cudaMemcpyAsync(I.Ehist + step, I.Ecur, sizeof(double), cudaMemcpyDeviceToDevice,
                                             c->stream));
-                CUDA_TRY(c, eom_pass(c, I, c->stream));
-                CUDA_TRY(c, update_pass(c, I, c->stream));
             }
         }
     }
@@ -2233,6 +2303,9 @@ void sgs_free(sgs_ctx* c) {
         c->release_instance(I);
         if (I.st) cudaStreamDestroy(I.st);
         if (I.join) cudaEventDestroy(I.join);
+        if (I.st2) cudaStreamDestroy(I.st2);
+        if (I.ev_fork) cudaEventDestroy(I.ev_fork);
+        if (I.ev_join) cudaEventDestroy(I.ev_join);
     }
     if (c->fork) cudaEventDestroy(c->fork);
     c->release_all();
