@@ -91,3 +91,45 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     __syncthreads();
     return r;
 }
+
+// 32 x 32 tiles on or below the diagonal of an n x n matrix, numbered row by row:
+// tile t is (K, L) with K >= L.  The antisymmetric results of the equation of motion
+// are computed on these tiles only and mirrored (X_lk = -X_kl, zero diagonal).
+__host__ __device__ __forceinline__ int lower_tile_count(int n) {
+    const int t = (n + 31) / 32;
+    return t * (t + 1) / 2;
+}
+__device__ __forceinline__ void lower_tile(int t, int& K, int& L) {
+    int k = 0;
+    while ((k + 1) * (k + 2) / 2 <= t) k++;
+    K = k;
+    L = t - k * (k + 1) / 2;
+}
+
+// Store a 32 x 32 tile of an antisymmetric matrix x (n x n) and its mirror from the
+// shared tile s[j][c] = x[k0 + j][l0 + c] (entries valid strictly below the diagonal):
+// tile (K, L) directly and tile (L, K) as -s^T; on a diagonal tile (K = L) the upper
+// part is the negated transpose and the diagonal zero.  256 threads; the caller
+// synchronises before (s complete) and after (s reused).
+__device__ __forceinline__ void store_antisym_tile(double* x, int n, int k0, int l0, const double (*s)[33],
+                                                   const unsigned char (*have)[33] = nullptr) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int j = ty; j < 32; j += 8) {
+        const int k = k0 + j, l = l0 + tx;
+        if (k < n && l < n) {
+            if (k0 != l0) {
+                if (!have || have[j][tx]) x[(size_t)k * n + l] = s[j][tx];
+            } else if (k > l) {
+                if (!have || have[j][tx]) x[(size_t)k * n + l] = s[j][tx];
+            } else if (k < l) {
+                if (!have || have[tx][j]) x[(size_t)k * n + l] = -s[tx][j];
+            } else {
+                if (!have || have[j][tx]) x[(size_t)k * n + l] = 0.0;
+            }
+        }
+        if (k0 != l0) {
+            const int r = l0 + j, c = k0 + tx;       // mirror: x[r][c] = -x[c][r] = -s[tx][j]
+            if (r < n && c < n && (!have || have[tx][j])) x[(size_t)r * n + c] = -s[tx][j];
+        }
+    }
+}

@@ -29,6 +29,9 @@ namespace sgs {
 // impurity modes, the terms of the pairs' F_imp.
 // eom_pairs_kernel forms D (into dGamma) and T, six FMAs per pair and element;
 // eom_finish_kernel adds the sparse part, the beta = mu term and the impurity terms.
+// D, T and dGamma are antisymmetric (every term is), so both kernels compute the
+// strictly lower entries of a tile pair (K >= L) and store them with their mirror:
+// grid (lower_tile_count(n), M), 256 threads.
 
 // weights w0..w5 of one (mu, beta != mu) and the pair's index in the view, into shared
 // memory; a pair outside the view (another chunk of pairs) or not held at all (index -1:
@@ -63,15 +66,22 @@ __global__ void __launch_bounds__(256) eom_pairs_kernel(InstDev d, const double*
                                                         const int* pair_index, double* tsum, double* dgamma,
                                                         int accumulate) {
     extern __shared__ double eom_sraw[];
-    const int mu = blockIdx.y, M = d.M;
+    __shared__ double st[2][32][33];
+    const int mu = blockIdx.y, M = d.M, n = d.n;
     R* sw = reinterpret_cast<R*>(eom_sraw);
     int* sp = reinterpret_cast<int*>(sw + 6 * M);
     eom_weights<R>(d, coef, pair_index, mu, sw, sp);
     __syncthreads();
+    int K, L;
+    lower_tile(blockIdx.x, K, L);
+    const int k0 = K * 32, l0 = L * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const size_t N = nn(d);
     double* T = tsum + (size_t)mu * N;
     double* out = dgamma + (size_t)mu * N;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+    for (int j = ty; j < 32; j += 8) {
+        const int k = k0 + j, l = l0 + tx;
+        if (k >= n || l >= n || k <= l) continue;
+        const size_t e = (size_t)k * n + l;
         R t = 0, acc = 0;
         for (int be = 0; be < M; be++) {
             const int p = sp[be];
@@ -86,14 +96,12 @@ __global__ void __launch_bounds__(256) eom_pairs_kernel(InstDev d, const double*
             acc = fma(w[4], sv, acc);
             acc = fma(w[5], iv, acc);
         }
-        if (accumulate) {
-            T[e] += (double)t;
-            out[e] += (double)acc;
-        } else {
-            T[e] = (double)t;
-            out[e] = (double)acc;
-        }
+        st[0][j][tx] = accumulate ? T[e] + (double)t : (double)t;
+        st[1][j][tx] = accumulate ? out[e] + (double)acc : (double)acc;
     }
+    __syncthreads();
+    store_antisym_tile(T, n, k0, l0, st[0]);
+    store_antisym_tile(out, n, k0, l0, st[1]);
 }
 
 // parts of eom_finish_kernel: the pairs' impurity terms (per chunk of pairs), the rest (the
@@ -110,6 +118,8 @@ __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double
                                                          int part) {
     extern __shared__ double eom_sraw[];
     __shared__ R s_w2;
+    __shared__ double sf[32][33];
+    __shared__ unsigned char sh[32][33];
     const int mu = blockIdx.y;
     const int n = d.n, ni = d.nimp, M = d.M;
     R* sw = reinterpret_cast<R*>(eom_sraw);
@@ -131,8 +141,19 @@ __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double
     const double* gfgm = gfg + (size_t)mu * N;
     const double* T = tsum + (size_t)mu * N;
     double* out = dgamma + (size_t)mu * N;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e / n), l = (int)(e % n);
+    int K, L;
+    lower_tile(blockIdx.x, K, L);
+    const int k0 = K * 32, l0 = L * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int j = ty; j < 32; j += 8) {
+        const int k = k0 + j, l = l0 + tx;
+        sh[j][tx] = 0;
+        if (k >= n || l >= n || k < l) continue;
+        if (k == l) {                                       // the diagonal is zero
+            sf[j][tx] = 0.0;
+            sh[j][tx] = 1;
+            continue;
+        }
+        const size_t e = (size_t)k * n + l;
         const int sk = d.slot[k], sl = d.slot[l];
         if (!rest && sk < 0 && sl < 0) continue;            // the pairs' impurity terms only
         // A_kl (row k of the CSR)
@@ -189,22 +210,11 @@ __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double
                 acc += (R)2 * ((R)co[0] * (dfx - fdx) - (R)co[1] * (dfy - fdy) + (R)co[2] * Fx - (R)co[3] * Fy);
             }
         }
-        out[e] = (double)acc;
+        sf[j][tx] = (double)acc;
+        sh[j][tx] = 1;
     }
-}
-
-// dGamma <- (dGamma - dGamma^T) / 2: the float assembly of the mixed forms computes each
-// element on its own, so its rounding leaves a symmetric part of relative size 1e-7 that the
-// exact dGamma (tangent to the pure states) does not have
-__global__ void antisymmetrise_kernel(double* a, int n) {
-    double* x = a + (size_t)blockIdx.y * n * n;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)n * n; e += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e / n), l = (int)(e % n);
-        if (k > l) continue;
-        const double v = k == l ? 0.0 : 0.5 * (x[e] - x[(size_t)l * n + k]);
-        x[e] = v;
-        x[(size_t)l * n + k] = -v;
-    }
+    __syncthreads();
+    store_antisym_tile(out, n, k0, l0, sf, sh);
 }
 
 }  // namespace sgs

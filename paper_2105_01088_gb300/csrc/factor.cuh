@@ -417,15 +417,33 @@ __global__ void __launch_bounds__(PF_PANEL_THREADS, 4) pf_panel_kernel(PfPanelAr
     double* PBre = PAre + blk;
     double* PAim = PBre + blk;
     double* PBim = PAim + blk;
-    for (int e = threadIdx.x; e < (n - e0) * bs; e += blockDim.x) {
-        const int t = e / (n - e0), i = e0 + e % (n - e0);
-        const double tr = Tr[(size_t)t * n + i], ti = Ti[(size_t)t * n + i];
-        const double ur = Ur[(size_t)t * n + i], ui = Ui[(size_t)t * n + i];
-        const size_t row = (size_t)i * kk;
-        PAre[row + t] = tr; PAre[row + bs + t] = -ti; PAre[row + 2 * bs + t] = -ur; PAre[row + 3 * bs + t] = ui;
-        PBre[row + t] = ur; PBre[row + bs + t] = ui;  PBre[row + 2 * bs + t] = tr;  PBre[row + 3 * bs + t] = ti;
-        PAim[row + t] = tr; PAim[row + bs + t] = ti;  PAim[row + 2 * bs + t] = -ur; PAim[row + 3 * bs + t] = -ui;
-        PBim[row + t] = ui; PBim[row + bs + t] = ur;  PBim[row + 2 * bs + t] = ti;  PBim[row + 3 * bs + t] = tr;
+    // rows are staged through the column buffers (4 n doubles, free now), R rows at a time
+    // with an odd row stride: T/U read along i and the packs written along their rows,
+    // both coalesced, with streaming stores (the packs are read once, by the next kernel,
+    // and should not push the T/U vectors of CTAs still in their panel out of L2)
+    int R = n / bs - 1;
+    if (R < 1) R = 1;
+    const int rs = R | 1;                       // 4 bs rs <= 4 n
+    double* stg = sm;
+    for (int i0 = e0; i0 < n; i0 += R) {
+        const int rn = min(R, n - i0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 4 * bs * rn; e += blockDim.x) {
+            const int r = e % rn, qt = e / rn;  // qt = plane * bs + t; planes Tr, Ti, Ur, Ui
+            stg[qt * rs + r] = Tr[(size_t)(qt / bs) * n * bs + (size_t)(qt % bs) * n + i0 + r];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rn * kk; e += blockDim.x) {
+            const int r = e / kk, c = e % kk, blk = c / bs, t = c % bs;
+            const double* v = stg + r;          // v[(plane * bs + t) * rs]: plane 0 Tr, 1 Ti, 2 Ur, 3 Ui
+            const size_t o = (size_t)(i0 + r) * kk + c;
+            // A_re = [Tr, -Ti, -Ur, Ui], B_re = [Ur, Ui, Tr, Ti], A_im = [Tr, Ti, -Ur, -Ui], B_im = [Ui, Ur, Ti, Tr]
+            const double x = v[(blk * bs + t) * rs];
+            __stcs(PAre + o, (blk == 1 || blk == 2) ? -x : x);
+            __stcs(PAim + o, blk >= 2 ? -x : x);
+            __stcs(PBre + o, v[(((blk + 2) & 3) * bs + t) * rs]);
+            __stcs(PBim + o, v[((3 - blk) * bs + t) * rs]);
+        }
     }
     if (threadIdx.x == 0) {
         double lg = s_log, ph_r = s_pr, ph_i = s_pi;

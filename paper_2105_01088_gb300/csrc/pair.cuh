@@ -330,19 +330,25 @@ __global__ void pair_lr_kernel(InstDev d, const double* si, const double* imd, c
 //   Qr = X + 4 Wr + 2 (L1 Si[imp,:] + Si[:,imp] L1^T)
 //   Qi = L2 Si[imp,:] - L1 Im[imp,:] - 2 (V - V^T)       (L2 carries its factor 4)
 // as chains of FMAs (FP64 issues at a small fraction of the other pipes' rates on this
-// part, so the count of FP64 instructions sets this kernel's time)
-// On the FP64 path the outputs alias the inputs (qr_out = xa_in, qi_out = wr_in):
-// each element is read and then written by the same thread.
+// part, so the count of FP64 instructions sets this kernel's time).  Both planes are
+// antisymmetric (Delta and F are), so one CTA computes the strictly lower entries of a
+// tile pair (K >= L) and stores them with their mirror: half the FP64 work of computing
+// every entry.
+// On the FP64 path the outputs alias the inputs (qr_out = xa_in, qi_out = wr_in): a CTA
+// reads its tile (K, L) of X and Wr before it writes tiles (K, L) and (L, K), which no
+// other CTA touches.
 template <typename T>
 __global__ void __launch_bounds__(256) pair_q_kernel(InstDev d, const double* si, const double* imd, const double* lr,
                                                      const T* va, const T* xa_in, const T* wr_in, double* qr_out,
                                                      double* qi_out) {
-    // 32 x 32 output tiles; V^T is staged through shared memory so both reads of V coalesce
+    // V^T is staged through shared memory so both reads of V coalesce
     __shared__ double vt[32][33];
+    __shared__ double sq[2][32][33];
     const int p = blockIdx.y;
     const int n = d.n, ni = d.nimp;
-    const int ntile = (n + 31) / 32;
-    const int k0 = (blockIdx.x / ntile) * 32, l0 = (blockIdx.x % ntile) * 32;
+    int K, L;
+    lower_tile(blockIdx.x, K, L);
+    const int k0 = K * 32, l0 = L * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const double* s = si + (size_t)p * nn(d);
     const double* im = imd + (size_t)p * nn(d);
@@ -360,7 +366,7 @@ __global__ void __launch_bounds__(256) pair_q_kernel(InstDev d, const double* si
     __syncthreads();
     for (int j = ty; j < 32; j += 8) {
         const int k = k0 + j, l = l0 + tx;
-        if (k >= n || l >= n) continue;
+        if (k >= n || l >= n || k <= l) continue;
         const size_t e = (size_t)k * n + l;
         double a1 = 0.0, a2 = 0.0;
         for (int m = 0; m < ni; m++) {
@@ -371,11 +377,12 @@ __global__ void __launch_bounds__(256) pair_q_kernel(InstDev d, const double* si
             a2 = fma(L2[k * ni + m], s_ml, a2);
             a2 = fma(-l1, im[(size_t)im_m * n + l], a2);
         }
-        const double qr = fma(2.0, a1, fma(4.0, (double)W[e], (double)X[e]));
-        const double qi = fma(-2.0, (double)v[e] - vt[tx][j], a2);      // V[l][k] = vt[l - l0][k - k0]
-        Qr[e] = qr;
-        Qi[e] = qi;
+        sq[0][j][tx] = fma(2.0, a1, fma(4.0, (double)W[e], (double)X[e]));
+        sq[1][j][tx] = fma(-2.0, (double)v[e] - vt[tx][j], a2);      // V[l][k] = vt[l - l0][k - k0]
     }
+    __syncthreads();
+    store_antisym_tile(Qr, n, k0, l0, sq[0]);
+    store_antisym_tile(Qi, n, k0, l0, sq[1]);
 }
 
 // Tensor-core operands from FP64 (or fp32) data: x = src - src2 (src2 optional)

@@ -1213,8 +1213,7 @@ cudaError_t eom_pair_chunk(sgs_ctx* c, Instance& I, cudaStream_t st) {
             pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, fimp, I.lr);
             counted();
         }
-        const unsigned qt = (unsigned)(((n + 31) / 32) * ((n + 31) / 32));
-        pair_q_kernel<float><<<dim3(qt, P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va32, I.xa32, I.wr32, I.xa, I.wr);
+        pair_q_kernel<float><<<dim3(lower_tile_count(n), P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va32, I.xa32, I.wr32, I.xa, I.wr);
         counted();
     } else {
         // T1 = S^{-1} (A + Re Fimp)  (into va; V later), Wr = T1 S^{-1}
@@ -1245,8 +1244,8 @@ cudaError_t eom_pair_chunk(sgs_ctx* c, Instance& I, cudaStream_t st) {
             pair_lr_kernel<<<dim3(grid_chunks((size_t)n * I.nimp, 256, 64), P), 256, 0, st>>>(d, I.si, I.imd, fimp, I.lr);
             counted();
         }
-        pair_q_kernel<double><<<dim3((unsigned)(((n + 31) / 32) * ((n + 31) / 32)), P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va, I.xa,
-                                                                                   I.wr, I.xa, I.wr);
+        pair_q_kernel<double><<<dim3(lower_tile_count(n), P), 256, 0, st>>>(d, I.si, I.imd, I.lr, I.va, I.xa, I.wr,
+                                                                            I.xa, I.wr);
         counted();
     }
     return cudaGetLastError();
@@ -1270,9 +1269,8 @@ cudaError_t eom_states(sgs_ctx* c, Instance& I, cudaStream_t st) {
 // them), and the finish part given
 void eom_sums(sgs_ctx* c, Instance& I, cudaStream_t st, int accumulate, int part, const InstDev& d) {
     const int n = I.n, M = I.M;
-    const size_t nn = (size_t)n * n;
     const int ni = std::max(I.nimp, 1);
-    const dim3 eg(grid_chunks(nn, 256, 1024), M);
+    const dim3 eg(lower_tile_count(n), M);
     const double* fimp = I.fimp + (size_t)d.p_off * ni * ni * 2;
     double* tsum = I.s[1];
     if (part & EOM_FINISH_PAIRS) {
@@ -1295,14 +1293,11 @@ void eom_sums(sgs_ctx* c, Instance& I, cudaStream_t st, int accumulate, int part
     counted();
 }
 
-// the end of the assembly: the float forms' exact antisymmetrisation, byte accounting
+// the end of the assembly: byte accounting (the assembly kernels store dGamma exactly
+// antisymmetric, the float forms included)
 cudaError_t eom_close(sgs_ctx* c, Instance& I, cudaStream_t st) {
     const int n = I.n, M = I.M;
     const size_t nn = (size_t)n * n;
-    if (I.tc_kind >= 0) {
-        antisymmetrise_kernel<<<dim3(grid_chunks(nn, 256, 1024), M), 256, 0, st>>>(I.dgamma, n);
-        counted();
-    }
     // algorithmic bytes: pair_q reads Si, Im, V (twice), X, Wr and writes Qr, Qi; the EOM
     // reads Si, Im, Qr, Qi once per receiver of each pair plus Gamma, GFG and writes dGamma
     c->stage_bytes[SGS_STAGE_EOM_ASSEMBLY] += 8.0 * nn * (7.0 * I.P + 8.0 * I.P + 3.0 * M);
