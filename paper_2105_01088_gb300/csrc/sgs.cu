@@ -59,7 +59,8 @@ struct Instance {
     size_t bytes = 0;
     cudaStream_t st = nullptr;          // branch stream of the captured step
     cudaEvent_t join = nullptr;
-    // the equation of motion's products run on a side stream while the phase Pfaffians run
+    // the equation of motion's products run on a side stream while the phase Pfaffians run, and
+    // the second half of the pairs' Gauss-Jordan inverses before them
     cudaStream_t st2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double* dens = nullptr;             // [P + M] complex energy densities (between the two parts of pair_gh)
@@ -128,7 +129,7 @@ struct Instance {
     double **r_Y = nullptr, **r_TU = nullptr, **r_PK = nullptr, **r_upA = nullptr, **r_upB = nullptr, **r_upC = nullptr;
     double* eigscratch = nullptr;
     int* err = nullptr;
-    OzBuf oz;                           // emulated FP64 products: slice scratch (path 2 only)
+    OzBuf oz;                           // emulated FP64 products: slice scratch (SGS_FP64_EMULATED only)
     OzBuf oz2;                          // the side stream's slice scratch (unchunked instances)
     int oz_side = 0;                    // 1 while the side stream's products are enqueued
 
@@ -972,31 +973,42 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
     return cudaGetLastError();
 }
 
-// S = Gamma_a + Gamma_b for every pair, its Gauss-Jordan inverse (pivoted, FP64) and
-// log|det S|, sign.  S has entries of magnitude <= 2; two states of opposite parity give a
+// Gauss-Jordan inverses (pivoted, FP64) of pairs p0 .. p0 + cnt - 1 of the current chunk, whose
+// S = Gamma_a + Gamma_b is in the work matrices, with log|det S| and its sign; S^{-1} gathered out
+// of the pivoted form.  S has entries of magnitude <= 2; two states of opposite parity give a
 // pivot at rounding level (~1e-15), same-parity pairs O(0.1).
-cudaError_t pair_inverse(sgs_ctx* c, Instance& I, cudaStream_t st) {
-    const int n = I.n, P = I.ccnt();
-    const size_t nn = (size_t)n * n;
-    pair_sum_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.dev(), I.work);
-    counted();
-    cudaError_t e = launch_gj_recursive(c, n, P, I.gj_b, I.p_work, I.p_tbuf, I.p_tup, I.piv, I.logdet, I.dsign,
-                                        I.err, 1e-12, st, &I.oz);
+cudaError_t inverse_range(sgs_ctx* c, Instance& I, int p0, int cnt, cudaStream_t st, const OzBuf* oz) {
+    const int n = I.n;
+    const size_t nn = (size_t)n * n, po = (size_t)p0 * n;
+    cudaError_t e = launch_gj_recursive(c, n, cnt, I.gj_b, I.p_work + p0, I.p_tbuf + p0, I.p_tup + p0, I.piv + po,
+                                        I.logdet + p0, I.dsign + p0, I.err, 1e-12, st, oz);
     if (e != cudaSuccess) return e;
-    gj_perm_kernel<<<(P + 127) / 128, 128, 0, st>>>(I.piv, I.perm, n, P);
-    gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), P), 256, 0, st>>>(I.p_work, I.p_si, I.perm, n);
+    gj_perm_kernel<<<(cnt + 127) / 128, 128, 0, st>>>(I.piv + po, I.perm + po, n, cnt);
+    gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), cnt), 256, 0, st>>>(I.p_work + p0, I.p_si + p0, I.perm + po, n);
     counted(); counted();
     return cudaGetLastError();
 }
 
-// Im Delta^{a,b} = (G_a - G_b) S^{-1}
-cudaError_t pair_delta(sgs_ctx* c, Instance& I, cudaStream_t st) {
-    const int n = I.n, P = I.ccnt();
-    GemmBatch g = gb_basic(n, n, n, I.p_ga + I.coff(), n, I.p_si, n, I.p_imd, n, P);
-    g.A2 = (const double* const*)(I.p_gb + I.coff()); g.sA2 = -1.0;
+// S = Gamma_a + Gamma_b and S^{-1} for every pair of the current chunk
+cudaError_t pair_inverse(sgs_ctx* c, Instance& I, cudaStream_t st) {
+    const size_t nn = (size_t)I.n * I.n;
+    pair_sum_kernel<<<dim3(grid_chunks(nn, 256, 64), I.ccnt()), 256, 0, st>>>(I.dev(), I.work);
+    counted();
+    return inverse_range(c, I, 0, I.ccnt(), st, &I.oz);
+}
+
+// Im Delta^{a,b} = (G_a - G_b) S^{-1} of pairs p0 .. p0 + cnt - 1 of the current chunk (side: with
+// the side stream's slice scratch)
+cudaError_t delta_range(sgs_ctx* c, Instance& I, int p0, int cnt, cudaStream_t st, int side) {
+    const int n = I.n;
+    GemmBatch g = gb_basic(n, n, n, I.p_ga + I.coff() + p0, n, I.p_si + p0, n, I.p_imd + p0, n, cnt);
+    g.A2 = (const double* const*)(I.p_gb + I.coff() + p0); g.sA2 = -1.0;
     g.mode = GEMM_SKEW;
     g.b_antisym = 1;        // S^{-1} (antisymmetric up to the inversion's rounding)
-    return gemm(c, I, g, st, (double)n * n * n * P);   // antisymmetric product: half of 2 n^3
+    I.oz_side = side;
+    const cudaError_t e = gemm(c, I, g, st, (double)n * n * n * cnt);   // antisymmetric product: half of 2 n^3
+    I.oz_side = 0;
+    return e;
 }
 
 // phase Pfaffians Pf(Gamma_0 + Delta^{a,b}) of the pairs without the reference state
@@ -1009,18 +1021,35 @@ cudaError_t pair_phase(sgs_ctx* c, Instance& I, cudaStream_t st) {
                      I.pfphase, I.err, st, &I.oz);
 }
 
-// S^{-1} and Im Delta of the current chunk's pairs (A1, A2, A4)
-cudaError_t pair_factors(sgs_ctx* c, Instance& I, cudaStream_t st) {
+// S^{-1} and Im Delta of the current chunk's pairs (A1, A2, A4).  split: the pairs in two halves,
+// the second on the instance's side stream with the side slice scratch, so that one half's
+// Gauss-Jordan panels (FP64 pipe) run beside the other half's emulated products (tensor and
+// integer pipes)
+cudaError_t pair_factors(sgs_ctx* c, Instance& I, cudaStream_t st, bool split = false) {
     const double n3 = (double)I.n * I.n * I.n;
     const int P = I.ccnt();
     if (P == 0) return cudaSuccess;
     c->stage(SGS_STAGE_PAIR_INVERSE);
     c->stage_flops[SGS_STAGE_PAIR_INVERSE] += 2.0 * n3 * P;
-    cudaError_t e = pair_inverse(c, I, st);
-    if (e != cudaSuccess) return e;
-    c->stage(SGS_STAGE_PAIR_DELTA);
+    cudaError_t e;
+    if (!(split && P >= 2 && I.st2 && I.oz2.base)) {
+        if ((e = pair_inverse(c, I, st)) != cudaSuccess) return e;
+        c->stage(SGS_STAGE_PAIR_DELTA);
+        c->stage_flops[SGS_STAGE_PAIR_DELTA] += n3 * P;
+        return delta_range(c, I, 0, P, st, 0);
+    }
     c->stage_flops[SGS_STAGE_PAIR_DELTA] += n3 * P;
-    return pair_delta(c, I, st);
+    const int PA = (P + 1) / 2, PB = P - PA;
+    pair_sum_kernel<<<dim3(grid_chunks((size_t)I.n * I.n, 256, 64), P), 256, 0, st>>>(I.dev(), I.work);
+    counted();
+    if ((e = cudaEventRecord(I.ev_fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(I.st2, I.ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = inverse_range(c, I, 0, PA, st, &I.oz)) != cudaSuccess) return e;
+    if ((e = inverse_range(c, I, PA, PB, I.st2, &I.oz2)) != cudaSuccess) return e;
+    if ((e = delta_range(c, I, 0, PA, st, 0)) != cudaSuccess) return e;
+    if ((e = delta_range(c, I, PA, PB, I.st2, 1)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(I.ev_join, I.st2)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(st, I.ev_join, 0);
 }
 
 // pair pass (A1-A5) of one instance, chunk by chunk: S^{-1}, Im Delta, phase Pfaffians, then G, h
@@ -1139,7 +1168,7 @@ sgs_status autotune_instance(sgs_ctx* c, Instance& I) {
         status = set_panel_pointers(c, I, gj, pf);
         cudaError_t e = cudaSuccess;
         if (status == SGS_OK) e = pair_inverse(c, I, st);
-        if (e == cudaSuccess) e = pair_delta(c, I, st);
+        if (e == cudaSuccess) e = delta_range(c, I, 0, I.ccnt(), st, 0);
         if (e != cudaSuccess) { c->err = std::string("autotune: ") + cudaGetErrorString(e); status = SGS_ECUDA; }
         best = 1e30f;
         for (int b : pf_candidates(I.n)) {
@@ -1519,9 +1548,12 @@ cudaError_t update_pass(sgs_ctx* c, Instance& I, cudaStream_t st) {
 // One step of an instance.  Unchunked instances fork after S^{-1} and Im Delta: the equation of
 // motion's products (they need the pairs' Fock blocks, not the overlaps or the amplitudes) run on a
 // side stream with their own slice scratch while the main stream computes the phase Pfaffians, G, h
-// and the amplitudes; the assembly waits for both.  The Pfaffians' FP64 panels and the products'
-// tensor-core work then share the GPU.  Chunked instances, and every instance while stage profiles
-// are taken (their stage events are on one stream), run the stages in order.  E -> Ecur.
+// and the amplitudes; the assembly waits for both.  Before the fork the Gauss-Jordan inverses run as
+// two halves of the pairs on the two streams.  In both places the FP64 panels of one stream share
+// the GPU with the tensor-core products of the other (a third stream that split the Pfaffians too
+// measured no faster: the Pfaffian phase already overlaps the products).  Chunked instances, and every
+// instance while stage profiles are taken (their stage events are on one stream), run the stages
+// in order.  E -> Ecur.
 cudaError_t step_instance(sgs_ctx* c, Instance& I, cudaStream_t st) {
     const bool overlap = I.nch() == 1 && I.P > 0 && !c->prof;
     if (!overlap) {
@@ -1538,7 +1570,7 @@ cudaError_t step_instance(sgs_ctx* c, Instance& I, cudaStream_t st) {
     I.cur = 0;
     const int M = I.M, ni = std::max(I.nimp, 1);
     (void)ni;
-    if ((e = pair_factors(c, I, st)) != cudaSuccess) return e;
+    if ((e = pair_factors(c, I, st, true)) != cudaSuccess) return e;
     pair_gh_kernel<<<I.P + M, 256, 0, st>>>(I.dev(), I.si, I.imd, I.logdet, I.pfphase, I.Gm, I.hm, I.fimp,
                                             I.fimp_state, GH_FOCK, I.dens);
     counted();
