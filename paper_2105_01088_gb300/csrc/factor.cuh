@@ -14,6 +14,7 @@
 //    is two real DMMA GEMMs (real and imaginary parts, k = 4b).
 #pragma once
 #include "common.cuh"
+#include "oz_digits.cuh"
 
 namespace sgs {
 
@@ -247,9 +248,31 @@ struct PfPanelArgs {
     int* err;
     int n, k0, bs;           // bs = elimination steps in this panel
     int bsmax;               // pack blocks are n x 4*bsmax apart (row stride 4*bs)
+    // emulated trailing update: with sa set the panel writes the update's operands as the
+    // slices and exponent fields the product reads (entries 2 b, 2 b + 1: the real and
+    // imaginary parts of matrix b; m = n - k0 - 2 bs rows, K = 4 bs; A slices [entry][OZ_S]
+    // [mp][4 bs] in oz_plane order, B slices [entry][OZ_S][np][4 bs], exponents [entry][mp]
+    // and [entry][np]) instead of the FP64 packs
+    uint16_t* sa;
+    uint16_t* sb;
+    int* ea;
+    int* eb;
+    int mp, np;
 };
 
 #define PF_MAX_PANEL 32       // widest Pfaffian panel (column pairs)
+
+// four digits per plane (w[i][0] | w[i][1] << 32: columns col .. col + 3 of slice i) into a slice
+// batch [entry][OZ_S][rp][kk], planes in oz_plane order (inter, A operands) or natural order
+__device__ __forceinline__ void pf_put_digits(uint16_t* base, int rp, int entry, int row, int kk, int col, bool inter,
+                                              const unsigned (&w)[OZ_S][2]) {
+#pragma unroll
+    for (int i = 0; i < OZ_S; i++) {
+        const int pl = inter ? oz_plane(i) : i;
+        __stcs(reinterpret_cast<unsigned long long*>(base + (((size_t)entry * OZ_S + pl) * rp + row) * kk + col),
+               (unsigned long long)w[i][0] | ((unsigned long long)w[i][1] << 32));
+    }
+}
 
 // One pending rank-2 term of the panel on element (i, k): v += T[i][t] U[k][t] - U[i][t] T[k][t]
 // (complex), as four FMAs per component (FP64 issues at a small fraction of the other
@@ -421,8 +444,11 @@ __global__ void __launch_bounds__(PF_PANEL_THREADS, 4) pf_panel_kernel(PfPanelAr
     // with an odd row stride: T/U read along i and the packs written along their rows,
     // both coalesced, with streaming stores (the packs are read once, by the next kernel,
     // and should not push the T/U vectors of CTAs still in their panel out of L2)
+    const bool sliced = a.sa != nullptr;
+    __shared__ int s_E[32];
     int R = n / bs - 1;
     if (R < 1) R = 1;
+    if (sliced && R > 32) R = 32;
     const int rs = R | 1;                       // 4 bs rs <= 4 n
     double* stg = sm;
     for (int i0 = e0; i0 < n; i0 += R) {
@@ -433,16 +459,92 @@ __global__ void __launch_bounds__(PF_PANEL_THREADS, 4) pf_panel_kernel(PfPanelAr
             stg[qt * rs + r] = Tr[(size_t)(qt / bs) * n * bs + (size_t)(qt % bs) * n + i0 + r];
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < rn * kk; e += blockDim.x) {
-            const int r = e / kk, c = e % kk, blk = c / bs, t = c % bs;
-            const double* v = stg + r;          // v[(plane * bs + t) * rs]: plane 0 Tr, 1 Ti, 2 Ur, 3 Ui
-            const size_t o = (size_t)(i0 + r) * kk + c;
-            // A_re = [Tr, -Ti, -Ur, Ui], B_re = [Ur, Ui, Tr, Ti], A_im = [Tr, Ti, -Ur, -Ui], B_im = [Ui, Ur, Ti, Tr]
-            const double x = v[(blk * bs + t) * rs];
-            __stcs(PAre + o, (blk == 1 || blk == 2) ? -x : x);
-            __stcs(PAim + o, blk >= 2 ? -x : x);
-            __stcs(PBre + o, v[(((blk + 2) & 3) * bs + t) * rs]);
-            __stcs(PBim + o, v[((3 - blk) * bs + t) * rs]);
+        if (!sliced) {
+            for (int e = threadIdx.x; e < rn * kk; e += blockDim.x) {
+                const int r = e / kk, c = e % kk, blk = c / bs, t = c % bs;
+                const double* v = stg + r;      // v[(plane * bs + t) * rs]: plane 0 Tr, 1 Ti, 2 Ur, 3 Ui
+                const size_t o = (size_t)(i0 + r) * kk + c;
+                // A_re = [Tr, -Ti, -Ur, Ui], B_re = [Ur, Ui, Tr, Ti], A_im = [Tr, Ti, -Ur, -Ui], B_im = [Ui, Ur, Ti, Tr]
+                const double x = v[(blk * bs + t) * rs];
+                __stcs(PAre + o, (blk == 1 || blk == 2) ? -x : x);
+                __stcs(PAim + o, blk >= 2 ? -x : x);
+                __stcs(PBre + o, v[(((blk + 2) & 3) * bs + t) * rs]);
+                __stcs(PBim + o, v[((3 - blk) * bs + t) * rs]);
+            }
+            continue;
+        }
+        // slices: every pack row is a signed permutation of the same 4 bs values, so the four
+        // packs share the row's exponent field (the largest of them), one warp per row
+        for (int r = threadIdx.x >> 5; r < rn; r += blockDim.x >> 5) {
+            int ef = 0;
+            for (int q = threadIdx.x & 31; q < kk; q += 32)
+                ef = max(ef, oz_expo_field((unsigned long long)__double_as_longlong(stg[q * rs + r])));
+            for (int w = 16; w > 0; w >>= 1) ef = max(ef, __shfl_xor_sync(0xffffffffu, ef, w));
+            if ((threadIdx.x & 31) == 0) {
+                s_E[r] = ef;
+                const int row = i0 + r - e0;
+                a.ea[(size_t)(2 * b) * a.mp + row] = ef;
+                a.ea[(size_t)(2 * b + 1) * a.mp + row] = ef;
+                a.eb[(size_t)(2 * b) * a.np + row] = ef;
+                a.eb[(size_t)(2 * b + 1) * a.np + row] = ef;
+            }
+        }
+        __syncthreads();
+        // digits of four consecutive values t .. t + 3 of one source plane (Tr, Ti, Ur, Ui) of one
+        // row per thread, once per sign the packs take them with (as the slicers write them: one
+        // 8-byte word of four bf16 per plane).  Plane src sits in block src of A_re = [Tr, -Ti,
+        // -Ur, Ui] and A_im = [Tr, Ti, -Ur, -Ui], block (src + 2) & 3 of B_re = [Ur, Ui, Tr, Ti]
+        // and block 3 - src of B_im = [Ui, Ur, Ti, Tr]
+        const int t4n = bs >> 2;
+        for (int e = threadIdx.x; e < rn * 4 * t4n; e += blockDim.x) {
+            const int t = 4 * (e % t4n), src = (e / t4n) & 3, r = e / (4 * t4n);
+            const int E = s_E[r], row = i0 + r - e0;
+            const bool nre = src == 1 || src == 2, nim = src >= 2;
+#pragma unroll 1
+            for (int sg = 0; sg < 2; sg++) {
+                if (sg == 1 && !nre && !nim) break;
+                unsigned w[OZ_S][2];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const double x = stg[(src * bs + t + u) * rs + r];
+                    float f[OZ_S];
+                    if (E > 0) oz_digit_floats((unsigned long long)__double_as_longlong(sg ? -x : x), E, f);
+                    else {
+#pragma unroll
+                        for (int i = 0; i < OZ_S; i++) f[i] = 0.0f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < OZ_S; i++) {
+                        const unsigned h = __float_as_uint(f[i]) >> 16;
+                        if (u & 1) w[i][u >> 1] |= h << 16;
+                        else w[i][u >> 1] = h;
+                    }
+                }
+                // pk 0, 1: A_re, A_im (block src, the sign they take); 2, 3: B_re, B_im (positive)
+#pragma unroll 1
+                for (int pk = 0; pk < 4; pk++) {
+                    const bool take = pk == 0 ? nre == (sg == 1) : pk == 1 ? nim == (sg == 1) : sg == 0;
+                    if (!take) continue;
+                    const int blk = pk < 2 ? src : pk == 2 ? ((src + 2) & 3) : 3 - src;
+                    pf_put_digits(pk < 2 ? a.sa : a.sb, pk < 2 ? a.mp : a.np, 2 * b + (pk & 1), row, kk, blk * bs + t,
+                                  pk < 2, w);
+                }
+            }
+        }
+    }
+    if (sliced && e0 < n) {
+        // zero digits on the padding rows m .. mp - 1 (A) and m .. np - 1 (B), as the slicers write
+        const int m = n - e0, c4n = kk >> 2;
+        const int za = (a.mp - m) * c4n, zb = (a.np - m) * c4n;
+        for (int e = threadIdx.x; e < 2 * OZ_S * (za + zb); e += blockDim.x) {
+            const int ep = e / (OZ_S * (za + zb)), x = e % (OZ_S * (za + zb));
+            const int pl = x / (za + zb), y = x % (za + zb);
+            const bool isA = y < za;
+            const int z = isA ? y : y - za, row = m + z / c4n, c = 4 * (z % c4n);
+            uint16_t* base = isA ? a.sa : a.sb;
+            const int rp = isA ? a.mp : a.np;
+            __stcs(reinterpret_cast<unsigned long long*>(base + (((size_t)(2 * b + ep) * OZ_S + pl) * rp + row) * kk + c),
+                   0ull);
         }
     }
     if (threadIdx.x == 0) {

@@ -3,8 +3,9 @@
 // Oishi and Rump, Numer. Algorithms 59 (2012); its tensor-core forms by Mukunoki
 // et al. and Ootomo et al.).  GB300's FP64 pipe issues about 1.25 TFLOP/s while
 // its bf16 tensor cores issue over 2 PFLOP/s, so the products of the step run
-// here when the emulated path is selected; results are at least as accurate as
-// the FP64 FMA kernel's (see the error budget below).
+// here when the emulated path is selected.  The error bound is normwise per row
+// of op(A) and column of op(B) (the error budget below), not elementwise like
+// that of the FP64 FMA kernel.
 //
 // Slicing.  Every row r of op(A) (K-major) gets the exponent field E_r of its
 // largest element, so |a_rk| < 2^(E_r - 1022).  The element is rounded to the
@@ -60,13 +61,13 @@
 #pragma once
 #include "gemm_f64.cuh"
 #include "gemm_tma.cuh"
+#include "oz_digits.cuh"
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 
 namespace sgs {
 
-#define OZ_S 8                // slices per operand
 #define OZ_G 8                // accumulator groups G = i + j <= 7
 #define OZ_BM 128
 #define OZ_KS 64              // K elements of one 128-byte slab row
@@ -111,25 +112,7 @@ struct OzOperand {
     int interleave;           // 1: slice i in plane oz_plane(i) (A operands), 0: plane i (B operands)
 };
 
-// Order in which the A slices of a slab are taken: 0 first (it opens every accumulator),
-// then long and short rows of the product triangle in pairs, (0, 7) (1, 6) (2, 5) (3, 4):
-// every pair feeds nine 64-column groups.  A operands store slice oz_order(t) in plane t,
-// so that each pair is two adjacent planes, one TMA box.
-__host__ __device__ __forceinline__ int oz_order(int t) {
-    return (t & 1) ? (OZ_S - 1 - (t >> 1)) : (t >> 1);       // 0 7 1 6 2 5 3 4
-}
-__host__ __device__ __forceinline__ int oz_plane(int i) {
-    return i < OZ_S / 2 ? 2 * i : 2 * (OZ_S - 1 - i) + 1;     // inverse of oz_order
-}
 
-// The slicers carry the operand as 64-bit bit patterns: they only take its exponent field and
-// significand apart, and double-typed selects and moves of the loaded values cost issue
-// slots of the FP64 pipe, which issues at a small fraction of the integer rate on this part.
-__device__ __forceinline__ int oz_expo_field(unsigned long long u) {
-    int e = (int)((u >> 52) & 0x7ff);
-    if (e == 0 && (u << 1) != 0ull) e = 1;       // subnormal: scale of the smallest normal
-    return e;
-}
 
 // element (r, k) of op(X) as its bit pattern (plus s2 times the same element of X2, the one
 // FP64 operation of the slicers)
@@ -144,37 +127,7 @@ __device__ __forceinline__ bool oz_active(const int* flag, int cmp, int b) {
     return flag == nullptr || flag[b] > cmp;
 }
 
-// X = round(v 2^(1078 - E)) (E = the row's exponent field, E > 0), |X| <= 2^56, rounded half
-// up on the magnitude, from the bit pattern
-__device__ __forceinline__ long long oz_scaled(unsigned long long u, int E) {
-    int f = (int)((u >> 52) & 0x7ff);
-    unsigned long long m = u & 0xFFFFFFFFFFFFFull;
-    if (f == 0) f = 1;
-    else m |= 1ull << 52;
-    const int sh = f - E + 3;                     // v 2^(1078 - E) = m 2^sh, sh <= 3
-    unsigned long long a;
-    if (sh >= 0) a = m << sh;
-    else if (sh <= -63) a = 0;
-    else a = (m + (1ull << (-sh - 1))) >> (-sh);
-    const long long X = (long long)a;
-    return (u >> 63) ? -X : X;
-}
 
-// The eight balanced base-128 digits of X (|t_0| <= 128, t_i in [-64, 63] for i >= 1) as
-// floats, most significant first.  Offset form: with Y = X + sum_{j<7} 64 2^(7 j), the
-// fields u_j = (Y >> 7 j) & 127 are the low digits plus 64 (no carries cross them) and
-// Y >> 49 (arithmetic) is the top digit; a low digit reaches float as the float 2^23 + u_j
-// (built by OR-ing u_j into the pattern of 2^23) less 2^23 + 64, an exact FP32 subtraction.
-// Each digit has at most 8 significant bits, so a float's high half is its exact bf16.
-__device__ __forceinline__ void oz_digit_floats(unsigned long long v, int E, float f[OZ_S]) {
-    const long long Y = oz_scaled(v, E) + 0x1020408102040ll;
-    f[0] = (float)(int)(Y >> 49);
-#pragma unroll
-    for (int i = 1; i < OZ_S; i++) {
-        const unsigned u = (unsigned)(Y >> (7 * (OZ_S - 1 - i))) & 127u;
-        f[i] = __uint_as_float(0x4B000000u | u) - 8388672.0f;
-    }
-}
 
 // the eight planes of four consecutive k of row r starting at k (k + 3 < kp; entries at or
 // beyond o.k are zero digits, which the tensor map never reads): per plane one 8-byte word
@@ -768,47 +721,86 @@ inline int oz_launches(const GemmBatch& g, const OzBuf& buf) {
     return total;
 }
 
+// where the slices and exponent fields of a batch chunk of bc entries of an m x n x k product
+// lie in the scratch: A slices [bc][OZ_S][mp][kp] (planes in oz_plane order), B slices
+// [bc][OZ_S][np][kp] (natural order), exponent fields [bc][mp] and [bc][np]
+struct OzLayout {
+    uint16_t* as;
+    uint16_t* bs;
+    int* ea;
+    int* eb;
+    int mp, np, kp;
+};
+inline OzLayout oz_layout(int m, int n, int k, const OzBuf& buf, int bc) {
+    OzLayout L;
+    L.kp = (int)oz_round(k, 8);
+    L.mp = (int)oz_round(m, OZ_BM);
+    L.np = (int)oz_round(n, 64);
+    const size_t sa = (size_t)OZ_S * L.mp * L.kp * 2, sb = (size_t)OZ_S * L.np * L.kp * 2;
+    L.as = reinterpret_cast<uint16_t*>(buf.base);
+    L.bs = reinterpret_cast<uint16_t*>(buf.base + oz_round((size_t)bc * sa, 1024));
+    L.ea = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(L.bs) + oz_round((size_t)bc * sb, 1024));
+    L.eb = L.ea + oz_round((size_t)bc * L.mp, 64);
+    return L;
+}
+
+// batch entries of one K chunk (k <= OZ_KC) whose slices fit the scratch at once
+inline int oz_chunk_entries(const GemmBatch& g, const OzBuf& buf) {
+    const size_t per = oz_entry_bytes(g.m, g.n, g.k);
+    return (int)std::min<size_t>(g.batch, buf.bytes > 8192 ? (buf.bytes - 8192) / per : 0);
+}
+
+// the product kernel on slices in place (layout L) for batch entries b0 .. b0 + bc - 1;
+// b_rows: B's slices are its rows (an antisymmetric B), so alpha changes sign
+inline cudaError_t oz_product(const GemmBatch& g, const OzLayout& L, int b0, int bc, bool b_rows, int* err,
+                              cudaStream_t st) {
+    const int bn = 32;                                   // OZ_NARROW's tile width
+    OzGemm p;
+    std::memset(&p, 0, sizeof(p));
+    if (!make_slice_map(&p.ta, L.as, g.k, L.kp, L.mp, bc * OZ_S, OZ_BM, OZ_UNIT) ||
+        !make_slice_map(&p.tb, L.bs, g.k, L.kp, L.np, bc * OZ_S, bn, OZ_S))
+        return cudaErrorInvalidValue;
+    p.g = g; p.b0 = b0; p.m_pad = L.mp; p.n_pad = L.np; p.ea = L.ea; p.eb = L.eb; p.err = err;
+    if (b_rows) p.g.alpha = -g.alpha;
+    int ex = 0;
+    const double fr = std::frexp(p.g.alpha, &ex);
+    if (!g.alpha_b && (fr == 0.5 || fr == -0.5)) {
+        p.alpha_pow2 = 1; p.alpha_e = ex - 1; p.alpha_neg = p.g.alpha < 0.0;
+    }
+    oz_gemm_kernel<OZ_NARROW><<<dim3(oz_tiles(g, bn), bc), OzCfg<OZ_NARROW>::THREADS, OzCfg<OZ_NARROW>::SMEM, st>>>(p);
+    return cudaGetLastError();
+}
+
 // one K chunk (k <= OZ_KC) of the emulated product, in batch chunks that fit the scratch
 inline cudaError_t gemm_oz_chunk(const GemmBatch& g, const OzBuf& buf, int* err, cudaStream_t st) {
-    const int kp = (int)oz_round(g.k, 8), mp = (int)oz_round(g.m, OZ_BM), np = (int)oz_round(g.n, 64);
-    const int bn = 32;                                   // OZ_NARROW's tile width
-    const size_t sa = (size_t)OZ_S * mp * kp * 2, sb = (size_t)OZ_S * np * kp * 2;
-    const size_t per = oz_entry_bytes(g.m, g.n, g.k);
-    const int chunk = (int)std::min<size_t>(g.batch, buf.bytes > 8192 ? (buf.bytes - 8192) / per : 0);
+    const int chunk = oz_chunk_entries(g, buf);
     if (chunk <= 0) return gemm_f64(g, st);
-    const int tiles = oz_tiles(g, bn);
     for (int b0 = 0; b0 < g.batch; b0 += chunk) {
         const int bc = std::min(chunk, g.batch - b0);
-        uint16_t* as = reinterpret_cast<uint16_t*>(buf.base);
-        uint16_t* bs = reinterpret_cast<uint16_t*>(buf.base + oz_round((size_t)bc * sa, 1024));
-        int* ea = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(bs) + oz_round((size_t)bc * sb, 1024));
-        int* eb = ea + oz_round((size_t)bc * mp, 64);
-        OzOperand oa{g.A, g.A2, g.sA2, g.offA, g.lda, g.transA ? 1 : 0, g.m, g.k, mp, kp, b0,
-                     g.active_flag, g.active_cmp, ea, as, 1};
+        const OzLayout L = oz_layout(g.m, g.n, g.k, buf, bc);
+        OzOperand oa{g.A, g.A2, g.sA2, g.offA, g.lda, g.transA ? 1 : 0, g.m, g.k, L.mp, L.kp, b0,
+                     g.active_flag, g.active_cmp, L.ea, L.as, 1};
         // an antisymmetric B (not transposed): its K-major columns are its rows negated, so the
         // rows are sliced (contiguous, one pass) and alpha changes sign
         const bool b_rows = g.b_antisym && !g.transB;
-        OzOperand ob{g.B, g.B2, g.sB2, b_rows ? g.offBr : g.offB, g.ldb, (g.transB || b_rows) ? 0 : 1, g.n, g.k, np, kp, b0,
-                     g.active_flag, g.active_cmp, eb, bs, 0};
+        OzOperand ob{g.B, g.B2, g.sB2, b_rows ? g.offBr : g.offB, g.ldb, (g.transB || b_rows) ? 0 : 1, g.n, g.k, L.np,
+                     L.kp, b0, g.active_flag, g.active_cmp, L.eb, L.bs, 0};
         oz_prepare(oa, bc, st);
         oz_prepare(ob, bc, st);
-        OzGemm p;
-        std::memset(&p, 0, sizeof(p));
-        if (!make_slice_map(&p.ta, as, g.k, kp, mp, bc * OZ_S, OZ_BM, OZ_UNIT) ||
-            !make_slice_map(&p.tb, bs, g.k, kp, np, bc * OZ_S, bn, OZ_S))
-            return cudaErrorInvalidValue;
-        p.g = g; p.b0 = b0; p.m_pad = mp; p.n_pad = np; p.ea = ea; p.eb = eb; p.err = err;
-        if (b_rows) p.g.alpha = -g.alpha;
-        int ex = 0;
-        const double fr = std::frexp(p.g.alpha, &ex);
-        if (!g.alpha_b && (fr == 0.5 || fr == -0.5)) {
-            p.alpha_pow2 = 1; p.alpha_e = ex - 1; p.alpha_neg = p.g.alpha < 0.0;
-        }
-        oz_gemm_kernel<OZ_NARROW><<<dim3(tiles, bc), OzCfg<OZ_NARROW>::THREADS, OzCfg<OZ_NARROW>::SMEM, st>>>(p);
-        const cudaError_t e = cudaGetLastError();
+        const cudaError_t e = oz_product(g, L, b0, bc, b_rows, err, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// The product on operands a producer kernel has already sliced into buf (layout oz_layout of
+// the whole batch): k <= OZ_KC, every entry in one chunk (oz_chunk_entries(g, buf) == batch)
+inline cudaError_t gemm_oz_presliced(const GemmBatch& g, const OzBuf& buf, int* err, cudaStream_t st) {
+    if (g.batch <= 0 || g.m <= 0 || g.n <= 0) return cudaSuccess;
+    if (g.k <= 0 || g.k > OZ_KC || !buf.base || !err || oz_chunk_entries(g, buf) < g.batch ||
+        (g.mode == GEMM_SKEW && g.m != g.n))
+        return cudaErrorInvalidValue;
+    return oz_product(g, oz_layout(g.m, g.n, g.k, buf, g.batch), 0, g.batch, g.b_antisym && !g.transB, err, st);
 }
 
 // the emulated product; K beyond OZ_KC runs as further launches that add onto C (the

@@ -847,13 +847,18 @@ inline cudaError_t tma_product(const TmaBatch& t, int kind, cudaStream_t st) { r
 // the launch (antisymmetric outputs count half), < 0 = not profiled.  With slice
 // scratch (an instance or call on the emulated path) the product runs emulated on
 // the bf16 tensor cores, otherwise on the FP64 FMA pipe.
+// presliced: the operands' slices are already in *oz (gemm_oz_presliced; their producer sliced
+// them, so the product's time below excludes the slicing)
 inline cudaError_t gemm(sgs_ctx* c, const GemmBatch& g, cudaStream_t st, double flops, const OzBuf* oz = nullptr,
-                        int* oz_err = nullptr) {
+                        int* oz_err = nullptr, bool presliced = false) {
     const bool emulate = oz && oz->base && oz_err;
     if (emulate) set_kernel_attributes();             // the kernels' shared-memory limits (once)
-    if (emulate) for (int i = oz_launches(g, *oz); i > 0; i--) counted();
+    if (emulate && !presliced) for (int i = oz_launches(g, *oz); i > 0; i--) counted();
     else counted();
-    auto run = [&]() { return emulate ? gemm_oz(g, *oz, oz_err, st) : gemm_f64(g, st); };
+    auto run = [&]() {
+        if (emulate && presliced) return gemm_oz_presliced(g, *oz, oz_err, st);
+        return emulate ? gemm_oz(g, *oz, oz_err, st) : gemm_f64(g, st);
+    };
     if (c && c->prof && flops >= 0.0) {
         cudaEvent_t a = c->next_event(), b = c->next_event();
         cudaEventRecord(a, st);
@@ -945,6 +950,7 @@ cudaError_t launch_gj_recursive(sgs_ctx* c, int n, int batch, int leaf, double**
     return gj_recurse(c, n, batch, leaf, 0, n, W, T, Tup, piv, logdet, dsign, err, tiny, st, oz);
 }
 
+// upA, upB, upC: 2 batch entries, 2 b and 2 b + 1 the real and imaginary parts of matrix b's update
 cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, double** TU, double** PK, double** upA,
                       double** upB, double** upC, double* logabs, double* phase, int* err, cudaStream_t st,
                       const OzBuf* oz = nullptr) {
@@ -952,12 +958,19 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
     set_kernel_attributes();
     for (int k0 = 0; k0 < n; k0 += 2 * bsmax) {
         const int bs = std::min(bsmax, (n - k0) / 2);
-        PfPanelArgs a{Y, TU, PK, logabs, phase, err, n, k0, bs, bsmax};
+        const int e0 = k0 + 2 * bs;
+        PfPanelArgs a{Y, TU, PK, logabs, phase, err, n, k0, bs, bsmax, nullptr, nullptr, nullptr, nullptr, 0, 0};
+        GemmBatch g = gb_basic(n - e0, n - e0, 4 * bs, upA, 4 * bs, upB, 4 * bs, upC, n, 2 * batch);
+        // emulated update: the panel writes the operands' slices itself when the whole batch
+        // fits the slice scratch (no FP64 packs, no slicing launches)
+        const bool sliced = e0 < n && oz && oz->base && err && bs % 4 == 0 && oz_chunk_entries(g, *oz) >= g.batch;
+        if (sliced) {
+            const OzLayout L = oz_layout(g.m, g.n, g.k, *oz, g.batch);
+            a.sa = L.as; a.sb = L.bs; a.ea = L.ea; a.eb = L.eb; a.mp = L.mp; a.np = L.np;
+        }
         pf_panel_kernel<<<batch, PF_PANEL_THREADS, smem, st>>>(a);
         counted();
-        const int e0 = k0 + 2 * bs;
         if (e0 >= n) break;
-        GemmBatch g = gb_basic(n - e0, n - e0, 4 * bs, upA, 4 * bs, upB, 4 * bs, upC, n, 2 * batch);
         g.offA = (long long)e0 * 4 * bs;
         g.offB = (long long)e0 * 4 * bs;
         g.transB = 1;
@@ -967,7 +980,7 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
         // block it updates: compute the lower tiles and mirror them
         g.mode = GEMM_SKEW;
         const double m2 = (double)(n - e0) * (n - e0);
-        cudaError_t e = gemm(c, g, st, m2 * 4.0 * bs * 2 * batch, oz, err);
+        const cudaError_t e = gemm(c, g, st, m2 * 4.0 * bs * 2 * batch, oz, err, sliced);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -1680,8 +1693,10 @@ sgs_status renyi_large(sgs_ctx* c, Instance& I, const double* blocks, const doub
             tu.push_back(TU + (size_t)q * 4 * m * bs);
             pk.push_back(PK + (size_t)q * 4 * blk);
         }
-        for (long long q = 0; q < chunk; q++) { upA.push_back(pk[q]); upB.push_back(pk[q] + blk); upC.push_back(y[q]); }
-        for (long long q = 0; q < chunk; q++) { upA.push_back(pk[q] + 2 * blk); upB.push_back(pk[q] + 3 * blk); upC.push_back(y[q] + mm); }
+        for (long long q = 0; q < chunk; q++) {     // entries 2 q, 2 q + 1: real and imaginary parts
+            upA.push_back(pk[q]); upB.push_back(pk[q] + blk); upC.push_back(y[q]);
+            upA.push_back(pk[q] + 2 * blk); upB.push_back(pk[q] + 3 * blk); upC.push_back(y[q] + mm);
+        }
         I.r_Y = upload_ptrs(c, y); I.r_TU = upload_ptrs(c, tu); I.r_PK = upload_ptrs(c, pk);
         I.r_upA = upload_ptrs(c, upA); I.r_upB = upload_ptrs(c, upB); I.r_upC = upload_ptrs(c, upC);
         I.renyi_err = c->alloc<int>(1);
@@ -2829,8 +2844,10 @@ sgs_status sgs_kernel_pfaffian(const double* Y, int n, int batch, int fp64_path,
         for (int b = 0; b < batch; b++) {
             py.push_back(W + b * 2 * nn); ptu.push_back(TU + (size_t)b * 4 * n * bs); ppk.push_back(PK + (size_t)b * 4 * blk);
         }
-        for (int b = 0; b < batch; b++) { ua.push_back(ppk[b]); ub.push_back(ppk[b] + blk); uc.push_back(py[b]); }
-        for (int b = 0; b < batch; b++) { ua.push_back(ppk[b] + 2 * blk); ub.push_back(ppk[b] + 3 * blk); uc.push_back(py[b] + nn); }
+        for (int b = 0; b < batch; b++) {           // entries 2 b, 2 b + 1: real and imaginary parts
+            ua.push_back(ppk[b]); ub.push_back(ppk[b] + blk); uc.push_back(py[b]);
+            ua.push_back(ppk[b] + 2 * blk); ub.push_back(ppk[b] + 3 * blk); uc.push_back(py[b] + nn);
+        }
         double **PY = upload_ptrs(&tmp, py), **PTU = upload_ptrs(&tmp, ptu), **PPK = upload_ptrs(&tmp, ppk);
         double **UA = upload_ptrs(&tmp, ua), **UB = upload_ptrs(&tmp, ub), **UC = upload_ptrs(&tmp, uc);
         cudaMemcpyAsync(W, planes.data(), planes.size() * sizeof(double), cudaMemcpyHostToDevice, tmp.stream);

@@ -307,3 +307,24 @@ def test_trajectory_and_mixed_form(pkg):
         out.append(s.step(3)[0])
         s.close()
     assert np.abs(out[0] - out[1]).max() <= 1e-9 * np.abs(out[1]).max()
+
+
+def test_panel_written_slices_equal_the_slicers(pkg):
+    """The Pfaffian panel writes the slices of its trailing update itself when the whole
+    batch fits the slice scratch; with a scratch too small for that the update takes the
+    FP64 packs through the slicing kernels in batch chunks.  Both take the same digits and
+    exponents, so G, h, dGamma and the energy agree to the bit."""
+    p = inp.AndersonParams(n_bath=20, U=3.0, eps_d=-1.5, V=0.7)          # n = 84, 6 phase Pfaffians
+    rng = np.random.default_rng(41)
+    g = inp.clustered_pure_gammas(p.n_modes, 5, rng, 1, spread=1.0)
+    lam = inp.random_amplitudes(5, rng)
+    m = pkg.build_anderson(p.n_bath, p.U, p.eps_d, p.V)
+    out = []
+    for cap in (0, 3 << 19):                     # default, and 1.5 MiB (12 update entries need 2.4 MB)
+        s = pkg.Solver(m, g, lam, dtau=0.05, fp64_path=EMU, emulation_scratch=cap)
+        E = s.step(2)[0]
+        Gg, hg = s.pair_matrices()
+        out.append((E, Gg, hg, s.derivative()))
+        s.close()
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
