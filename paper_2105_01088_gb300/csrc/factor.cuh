@@ -33,6 +33,26 @@ struct GJPanelArgs {
     double tiny;             // a pivot of magnitude <= tiny counts as singular
 };
 
+// bf16 digits of four values into w (w[i][0] | w[i][1] << 32: the four digits of slice i), zero
+// where E = 0 or the value is absent (present[u] false)
+__device__ __forceinline__ void oz_digits4(const double (&v)[4], const bool (&present)[4], int E, unsigned (&w)[OZ_S][2]) {
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        float f[OZ_S];
+        if (E > 0 && present[u]) oz_digit_floats((unsigned long long)__double_as_longlong(v[u]), E, f);
+        else {
+#pragma unroll
+            for (int i = 0; i < OZ_S; i++) f[i] = 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < OZ_S; i++) {
+            const unsigned h = __float_as_uint(f[i]) >> 16;
+            if (u & 1) w[i][u >> 1] |= h << 16;
+            else w[i][u >> 1] = h;
+        }
+    }
+}
+
 // The end of a Gauss-Jordan panel, after its columns are back in W: log |det| += the sum
 // of log |pivot_j|; the panel's row interchanges (k0 + j <-> piv_j, in order) applied to the
 // other columns of W as one permutation of the rows they touch (row rows[e] receives the old
@@ -207,6 +227,88 @@ __global__ void gj_gather_rows_kernel(double* const* W, double* const* T, int n,
          e += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(e / w), q = (int)(e % w);
         dst[e] = src[(size_t)(p0 + k) * n + t0 + q];
+    }
+}
+
+// Both operands of a Gauss-Jordan update of small K and w (both <= 64), written directly as the
+// slices the emulated product reads: A = columns p0 .. p0 + K - 1 of W (rows of K values;
+// [batch][OZ_S][mp][kp], planes in oz_plane order, exponent fields [batch][mp]) and B = rows
+// p0 .. p0 + K - 1 of the target columns t0 .. t0 + w - 1, op(B) column j (the K entries of
+// column t0 + j) as row j ([batch][OZ_S][np][kp], natural plane order, exponent fields
+// [batch][np]).  Padding rows and columns K .. kp - 1 get zero digits, as the slicers write
+// them.  Grid (mp / GJ_SLICE_ROWS + 1, batch): a block of A rows per CTA, four consecutive
+// columns of one row per thread; the last CTA of each matrix takes B.  One launch instead of
+// the pivot-row gather and two slicing launches.
+#define GJ_SLICE_ROWS 64
+__global__ void __launch_bounds__(256) gj_update_slice_kernel(double* const* W, int n, int p0, int K, int t0, int w,
+                                                              uint16_t* sa, int* ea, int mp, uint16_t* sb, int* eb,
+                                                              int np, int kp) {
+    __shared__ double tile[64][65];              // B: tile[j][k]
+    __shared__ int s_e[64];
+    const int b = blockIdx.y;
+    const double* src = W[b];
+    const int c4 = kp >> 2;
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) s_e[j] = 0;
+    if (blockIdx.x < gridDim.x - 1) {
+        const int r0 = blockIdx.x * GJ_SLICE_ROWS;
+        __syncthreads();
+        for (int e = threadIdx.x; e < GJ_SLICE_ROWS * c4; e += blockDim.x) {
+            const int rr = e / c4, c = 4 * (e % c4), r = r0 + rr;
+            int ef = 0;
+            if (r < n)
+                for (int u = 0; u < 4 && c + u < K; u++)
+                    ef = max(ef, oz_expo_field((unsigned long long)__double_as_longlong(src[(size_t)r * n + p0 + c + u])));
+            if (ef) atomicMax(&s_e[rr], ef);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < GJ_SLICE_ROWS * c4; e += blockDim.x) {
+            const int rr = e / c4, c = 4 * (e % c4), r = r0 + rr;
+            if (r >= mp) continue;
+            const int ef = s_e[rr];
+            if (c == 0 && r < n) ea[(size_t)b * mp + r] = ef;
+            double v[4];
+            bool pr[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                pr[u] = r < n && c + u < K;
+                v[u] = pr[u] ? src[(size_t)r * n + p0 + c + u] : 0.0;
+            }
+            unsigned wd[OZ_S][2];
+            oz_digits4(v, pr, ef, wd);
+#pragma unroll
+            for (int i = 0; i < OZ_S; i++)
+                *reinterpret_cast<unsigned long long*>(sa + (((size_t)b * OZ_S + oz_plane(i)) * mp + r) * kp + c) =
+                    (unsigned long long)wd[i][0] | ((unsigned long long)wd[i][1] << 32);
+        }
+        return;
+    }
+    for (int e = threadIdx.x; e < K * w; e += blockDim.x) {
+        const int k = e / w, j = e % w;           // along the rows of W
+        tile[j][k] = src[(size_t)(p0 + k) * n + t0 + j];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < w; j += blockDim.x) {
+        int ef = 0;
+        for (int k = 0; k < K; k++) ef = max(ef, oz_expo_field((unsigned long long)__double_as_longlong(tile[j][k])));
+        s_e[j] = ef;
+        eb[(size_t)b * np + j] = ef;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < np * c4; e += blockDim.x) {
+        const int j = e / c4, c = 4 * (e % c4);
+        double v[4];
+        bool pr[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            pr[u] = j < w && c + u < K;
+            v[u] = pr[u] ? tile[j][c + u] : 0.0;
+        }
+        unsigned wd[OZ_S][2];
+        oz_digits4(v, pr, j < w ? s_e[j] : 0, wd);
+#pragma unroll
+        for (int i = 0; i < OZ_S; i++)
+            *reinterpret_cast<unsigned long long*>(sb + (((size_t)b * OZ_S + i) * np + j) * kp + c) =
+                (unsigned long long)wd[i][0] | ((unsigned long long)wd[i][1] << 32);
     }
 }
 

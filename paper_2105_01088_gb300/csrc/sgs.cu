@@ -904,16 +904,39 @@ cudaError_t launch_gj(sgs_ctx* c, int n, int batch, int bsz, double** W, double*
 // The delayed Gauss-Jordan update of target columns t0 .. t0 + w - 1 by the eliminated columns
 // p0 .. p0 + K - 1 (their pivot rows p0 .. p0 + K - 1): W[:, t] <- W[:, p] T + W[:, t] with the
 // pivot rows replaced rather than added to, T = the target columns' pivot rows before the update.
-cudaError_t gj_update(sgs_ctx* c, int n, int batch, double** W, double** Tup, int p0, int K, int t0, int w,
-                      cudaStream_t st, const OzBuf* oz, int* err) {
-    gj_gather_rows_kernel<<<dim3(grid_chunks((size_t)K * w, 256, 64), batch), 256, 0, st>>>(W, Tup, n, p0, K, t0, w);
-    counted();
+GemmBatch gj_update_batch(int n, int batch, double** W, double** Tup, int p0, int K, int t0, int w) {
     GemmBatch g = gb_basic(n, w, K, W, n, Tup, w, W, n, batch);
     g.offA = p0;
     g.offC = t0;
     g.Cin = (const double* const*)W; g.offCin = t0; g.ldcin = n; g.beta = 1.0;
     g.mode = GEMM_GJ; g.gj_k0 = p0; g.gj_b = K; g.gj_cols = 0;
-    return gemm(c, g, st, 2.0 * n * (double)w * K * batch, oz, err);
+    return g;
+}
+
+// whether an emulated update of w target columns by K eliminated columns takes both operands'
+// slices from one kernel (gj_update_slice_kernel): small K and w, the whole batch in the slice
+// scratch
+bool gj_presliced(const OzBuf* oz, const int* err, int n, int batch, int K, int w) {
+    if (!oz || !oz->base || !err || K > 64 || w > 64 || K < 1 || w < 1) return false;
+    return oz_chunk_entries(gj_update_batch(n, batch, nullptr, nullptr, 0, K, 0, w), *oz) >= batch;
+}
+
+// columns t0 .. t0 + w - 1 of every W updated by the eliminated columns p0 .. p0 + K - 1
+cudaError_t gj_update(sgs_ctx* c, int n, int batch, double** W, double** Tup, int p0, int K, int t0, int w,
+                      cudaStream_t st, const OzBuf* oz, int* err) {
+    const GemmBatch g = gj_update_batch(n, batch, W, Tup, p0, K, t0, w);
+    const bool presliced = gj_presliced(oz, err, n, batch, K, w);
+    if (presliced) {
+        const OzLayout L = oz_layout(n, w, K, *oz, batch);
+        gj_update_slice_kernel<<<dim3((L.mp + GJ_SLICE_ROWS - 1) / GJ_SLICE_ROWS + 1, batch), 256, 0, st>>>(
+            W, n, p0, K, t0, w, L.as, L.ea, L.mp, L.bs, L.eb, L.np, L.kp);
+        counted();
+    } else {
+        gj_gather_rows_kernel<<<dim3(grid_chunks((size_t)K * w, 256, 64), batch), 256, 0, st>>>(W, Tup, n, p0, K, t0,
+                                                                                               w);
+        counted();
+    }
+    return gemm(c, g, st, 2.0 * n * (double)w * K * batch, oz, err, presliced);
 }
 
 // Recursive blocked Gauss-Jordan of columns c0 .. c1 - 1: the left half, its transformation

@@ -54,3 +54,33 @@ def lambda_error_bound(Go, ho, Eo, lo, Gg, hg):
 def dgamma_rtol(bound, lo, mu, base=1e-10):
     """Relative tolerance of dGamma^mu (to its largest entry)."""
     return base + 2.0 * bound[mu] / max(abs(lo[mu]), 1e-300)
+
+
+def overlap_error_bars(ga, gb, g0, delta, rtol=1e-10):
+    """Bars for one pair element G_ab = |G_ab| e^{i phi} computed twice (two
+    implementations, two roundings), from the conditioning of the two
+    factorisations it comes from (Sec. II B: the magnitude from
+    log|det(Gamma_a + Gamma_b)|, the phase from Pf(Gamma_0 + Delta^{a,b})).
+
+    A backward-stable factorisation of X returns the log-determinant of
+    X + dX with |dX|_2 <= n u |X|_2, and to first order
+    d log det X = tr(X^-1 dX), so |d log|det X|| <= n u |X|_2 sum_i 1/sigma_i(X).
+    The log of a Pfaffian moves by half that.  With two computations:
+
+        | log|G_gpu| - log|G_ref| | <= rtol + n u |S|_2 sum 1/sigma_i(S)
+        | arg(G_gpu / G_ref) |      <= rtol + n u |Y|_2 sum 1/sigma_i(Y)
+
+    S = Gamma_a + Gamma_b, Y = Gamma_0 + Delta^{a,b} (no phase Pfaffian for
+    a pair with the reference state 0: pass g0 = None).  The bound is worst
+    case over the direction of the rounding, so it is loose for a nearly
+    singular Y; nothing in it is fitted to a measured result.
+    Returns (magnitude bar, phase bar)."""
+    S = ga + gb
+    n = S.shape[0]
+    sv = np.linalg.svd(S, compute_uv=False)
+    mag = rtol + n * U * sv[0] * np.sum(1.0 / sv)
+    ph = rtol
+    if g0 is not None:
+        sy = np.linalg.svd(g0 + delta, compute_uv=False)
+        ph += n * U * sy[0] * np.sum(1.0 / sy)
+    return mag, ph

@@ -3,6 +3,7 @@ perturbing (G, h) and re-solving with the oracle moves lambda as the formula of
 tests/amplitude_conditioning.py predicts, and never by more than its bound."""
 import numpy as np
 
+import sgs_inputs as inp
 from amplitude_conditioning import amplitude_sensitivity, lambda_error_bound
 from oracle import sgs_oracle as orc
 
@@ -63,3 +64,36 @@ def test_bound_catches_a_dropped_term():
     bound = lambda_error_bound(G, h, E, lam, G, h + dh)
     assert np.all(act <= bound)
     assert act.max() > 1e-3 * bound.max()
+
+
+def test_overlap_error_bars_bound_perturbed_factorisations():
+    """The bars of overlap_error_bars hold for inputs perturbed by the backward error they
+    assume (n u |X|_2, random direction) and fail for a perturbation 1e4 times larger in
+    the worst direction: the first-order log-determinant identity is what they rest on."""
+    from amplitude_conditioning import U, overlap_error_bars
+    rng = np.random.default_rng(8)
+    n_modes = 12
+    g = [inp.random_pure_gamma(n_modes, rng, 1) for _ in range(3)]
+    D = orc.transition_matrix(g[1], g[2])
+    mag, ph = overlap_error_bars(g[1], g[2], g[0], D, rtol=0.0)
+    S = g[1] + g[2]
+    Y = g[0] + D
+    n = S.shape[0]
+    for _ in range(20):
+        E = rng.standard_normal((n, n))
+        E = E - E.T
+        dS = E * (n * U * np.linalg.norm(S, 2) / np.linalg.norm(E, 2))
+        d_mag = abs(0.5 * (np.linalg.slogdet(S + dS)[1] - np.linalg.slogdet(S)[1]))
+        assert d_mag <= mag
+        F = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        F = F - F.T
+        dY = F * (n * U * np.linalg.norm(Y, 2) / np.linalg.norm(F, 2))
+        p0, _ = orc.pfaffian_log(Y)
+        p1, _ = orc.pfaffian_log(Y + dY)
+        assert abs(np.angle(p1 / p0)) <= ph
+    # along the smallest singular direction a 1e4 times larger perturbation breaks the bar
+    Us, sv, Vt = np.linalg.svd(S)
+    k = np.argmin(sv)
+    P = np.outer(Us[:, k], Vt[k])
+    dS = (P - P.T) * (1e4 * n * U * sv[0] * np.sum(1.0 / sv))
+    assert abs(0.5 * (np.linalg.slogdet(S + dS)[1] - np.linalg.slogdet(S)[1])) > mag

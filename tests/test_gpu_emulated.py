@@ -309,18 +309,23 @@ def test_trajectory_and_mixed_form(pkg):
     assert np.abs(out[0] - out[1]).max() <= 1e-9 * np.abs(out[1]).max()
 
 
-def test_panel_written_slices_equal_the_slicers(pkg):
-    """The Pfaffian panel writes the slices of its trailing update itself when the whole
-    batch fits the slice scratch; with a scratch too small for that the update takes the
-    FP64 packs through the slicing kernels in batch chunks.  Both take the same digits and
-    exponents, so G, h, dGamma and the energy agree to the bit."""
-    p = inp.AndersonParams(n_bath=20, U=3.0, eps_d=-1.5, V=0.7)          # n = 84, 6 phase Pfaffians
+@pytest.mark.parametrize("M,cap", [(5, 3 << 19), (9, 600 << 10)])
+def test_panel_written_slices_equal_the_slicers(pkg, M, cap):
+    """The Pfaffian panel writes the slices of its trailing update, and one kernel writes both
+    operands' slices of a Gauss-Jordan update of K, w <= 64, when the whole batch fits the
+    slice scratch; with a scratch too small for that the updates take their FP64 operands
+    through the slicing kernels in batch chunks.  Both take the same digits and
+    exponents, so G, h, dGamma and the energy agree to the bit.  n = 84: M = 5 has 6 phase
+    Pfaffians (12 update entries, 2.4 MB, beyond 1.5 MiB); M = 9 has 28 (56 entries) and
+    halves of 18 pairs whose leaf updates (50 KB an entry) exceed 600 KiB, while one entry of
+    every product (at most 361 KB) fits both caps."""
+    p = inp.AndersonParams(n_bath=20, U=3.0, eps_d=-1.5, V=0.7)
     rng = np.random.default_rng(41)
-    g = inp.clustered_pure_gammas(p.n_modes, 5, rng, 1, spread=1.0)
-    lam = inp.random_amplitudes(5, rng)
+    g = inp.clustered_pure_gammas(p.n_modes, M, rng, 1, spread=1.0)
+    lam = inp.random_amplitudes(M, rng)
     m = pkg.build_anderson(p.n_bath, p.U, p.eps_d, p.V)
     out = []
-    for cap in (0, 3 << 19):                     # default, and 1.5 MiB (12 update entries need 2.4 MB)
+    for cap in (0, cap):
         s = pkg.Solver(m, g, lam, dtau=0.05, fp64_path=EMU, emulation_scratch=cap)
         E = s.step(2)[0]
         Gg, hg = s.pair_matrices()

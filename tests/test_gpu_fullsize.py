@@ -1,6 +1,8 @@
 """Parity at the benchmark's full size (2N = 512, M = 32, in the bench's launch
 configuration: graph replay on a stream of its own) on outputs the oracle can
-compute one at a time: sampled pair elements G_ab and h_ba, the energy of the
+compute one at a time: sampled pair elements G_ab and h_ba (magnitude and phase
+against bars from the conditioning of Gamma_a + Gamma_b and Gamma_0 + Delta:
+the overlaps of these random states are as small as 1e-40), the energy of the
 GPU's (G, h), dGamma of sampled states and their updated Gamma.  Both
 arithmetics of the FP64 products are covered: the emulated products (the
 library's default and the bench's) with the panel widths the bench's
@@ -12,7 +14,7 @@ import numpy as np
 import pytest
 
 import sgs_inputs as inp
-from amplitude_conditioning import dgamma_rtol, lambda_error_bound
+from amplitude_conditioning import dgamma_rtol, lambda_error_bound, overlap_error_bars
 from oracle import sgs_oracle as orc
 
 pytestmark = pytest.mark.gpu
@@ -60,8 +62,12 @@ def test_large_workload_sampled_outputs(pkg, large, variant):
     pairs = [(0, 5), (0, 31), (3, 4), (7, 19), (12, 30), (30, 31)]
     for a, b in pairs:
         Go, hbo = orc.pair_elements(model, list(g), a, b)
-        assert abs(G[a, b] - Go) <= RTOL * abs(Go), (a, b)
-        assert abs(h[b, a] - hbo) <= RTOL * abs(hbo), (a, b)
+        # magnitude and phase against bars from the conditioning of the two factorisations
+        # they come from (overlap_error_bars); h_ba = conj(G_ab) Wick(Delta) carries both
+        mag, ph = overlap_error_bars(g[a], g[b], g[0] if a != 0 else None, orc.transition_matrix(g[a], g[b]), RTOL)
+        assert abs(np.log(abs(G[a, b]) / abs(Go))) <= mag, (a, b, mag)
+        assert abs(np.angle(G[a, b] / Go)) <= ph, (a, b, ph)
+        assert abs(h[b, a] - hbo) <= (mag + ph + RTOL) * abs(hbo), (a, b)
     for a in rng.choice(32, 3, replace=False):
         assert abs(h[a, a] - orc.wick_energy_density(model, g[a])) <= RTOL * abs(h[a, a])
     # the energy and amplitudes of the GPU's (G, h) by the oracle's solve
