@@ -401,7 +401,8 @@ sgs_status sgs_probe_wait(unsigned long long limit_ns, double* elapsed_ms);
  * device current; the first call that launches them on a device does it, and
  * so does this call.  For kernel i < n_out (0 Gauss-Jordan panel, 1 Pfaffian
  * panel, 2 Renyi Pfaffian, 3-5 tensor-core product tf32 / bf16 / 3xtf32,
- * 6 emulated FP64 product, 7 block slicer; n_out <= 8) it writes the limit
+ * 6 emulated FP64 product, 7 block slicer, 8 emulated FP64 product of
+ * 16-column tiles; n_out <= 9) it writes the limit
  * in force to limit[i] and the device's opt-in maximum less the kernel's
  * static shared memory to expected[i]. */
 sgs_status sgs_kernel_smem_limits(int n_out, int* limit, int* expected);

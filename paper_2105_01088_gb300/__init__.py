@@ -502,9 +502,9 @@ def probe_wait(limit_ns):
 def smem_limits():
     """[(dynamic shared-memory limit in force, opt-in maximum less static shared
     memory)] of the library's large-shared-memory kernels on the current device."""
-    lim = np.zeros(8, dtype=np.int32)
-    exp = np.zeros(8, dtype=np.int32)
-    st = _lib.sgs_kernel_smem_limits(8, _ptr(lim, _ip), _ptr(exp, _ip))
+    lim = np.zeros(9, dtype=np.int32)
+    exp = np.zeros(9, dtype=np.int32)
+    st = _lib.sgs_kernel_smem_limits(9, _ptr(lim, _ip), _ptr(exp, _ip))
     if st != 0:
         raise SGSError(st, "shared-memory limits")
     return list(zip(lim.tolist(), exp.tolist()))

@@ -86,6 +86,9 @@ template <int BN, int EPIW, int RING, bool BDBL> struct OzCfg {
     static constexpr int THREADS = 32 * (EPIW + 2);
 };
 #define OZ_NARROW 32, 8, 2, false
+// 128 x 16 tiles for products of at most 16 output columns (the Gauss-Jordan leaf updates):
+// half the epilogue of a 128 x 32 tile whose other half would be discarded
+#define OZ_NARROW16 16, 8, 2, false
 
 // device scratch of one owner (an instance, or a temporary context): slices and
 // exponent fields of one batch chunk
@@ -754,7 +757,7 @@ inline int oz_chunk_entries(const GemmBatch& g, const OzBuf& buf) {
 // b_rows: B's slices are its rows (an antisymmetric B), so alpha changes sign
 inline cudaError_t oz_product(const GemmBatch& g, const OzLayout& L, int b0, int bc, bool b_rows, int* err,
                               cudaStream_t st) {
-    const int bn = 32;                                   // OZ_NARROW's tile width
+    const int bn = g.n <= 16 ? 16 : 32;                  // OZ_NARROW16's or OZ_NARROW's tile width
     OzGemm p;
     std::memset(&p, 0, sizeof(p));
     if (!make_slice_map(&p.ta, L.as, g.k, L.kp, L.mp, bc * OZ_S, OZ_BM, OZ_UNIT) ||
@@ -767,7 +770,11 @@ inline cudaError_t oz_product(const GemmBatch& g, const OzLayout& L, int b0, int
     if (!g.alpha_b && (fr == 0.5 || fr == -0.5)) {
         p.alpha_pow2 = 1; p.alpha_e = ex - 1; p.alpha_neg = p.g.alpha < 0.0;
     }
-    oz_gemm_kernel<OZ_NARROW><<<dim3(oz_tiles(g, bn), bc), OzCfg<OZ_NARROW>::THREADS, OzCfg<OZ_NARROW>::SMEM, st>>>(p);
+    if (bn == 16)
+        oz_gemm_kernel<OZ_NARROW16>
+            <<<dim3(oz_tiles(g, bn), bc), OzCfg<OZ_NARROW16>::THREADS, OzCfg<OZ_NARROW16>::SMEM, st>>>(p);
+    else
+        oz_gemm_kernel<OZ_NARROW><<<dim3(oz_tiles(g, bn), bc), OzCfg<OZ_NARROW>::THREADS, OzCfg<OZ_NARROW>::SMEM, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -836,6 +836,7 @@ void set_kernel_attributes() {
     raise_smem_limit(gemm_tma_kernel<TC_BF16>, optin);
     raise_smem_limit(gemm_tma_kernel<TC_3XTF32>, optin);
     raise_smem_limit(oz_gemm_kernel<OZ_NARROW>, optin);
+    raise_smem_limit(oz_gemm_kernel<OZ_NARROW16>, optin);
     raise_smem_limit(oz_block_slice_kernel, optin);
     cudaGetLastError();
     g_attr_done[dev] = true;
@@ -2502,7 +2503,7 @@ sgs_status sgs_kernel_smem_limits(int n_out, int* limit, int* expected) {
     const void* k[] = {(const void*)gj_panel_kernel, (const void*)pf_panel_kernel, (const void*)renyi_pf_kernel,
                        (const void*)gemm_tma_kernel<TC_TF32>, (const void*)gemm_tma_kernel<TC_BF16>,
                        (const void*)gemm_tma_kernel<TC_3XTF32>, (const void*)oz_gemm_kernel<OZ_NARROW>,
-                       (const void*)oz_block_slice_kernel};
+                       (const void*)oz_block_slice_kernel, (const void*)oz_gemm_kernel<OZ_NARROW16>};
     const int nk = (int)(sizeof(k) / sizeof(k[0]));
     if (!limit || !expected || n_out < 1 || n_out > nk) return SGS_EINVAL;
     set_kernel_attributes();

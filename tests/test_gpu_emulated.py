@@ -79,6 +79,8 @@ SHAPES = [
     (1, 96, 80, 300, True, True),
     (2, 64, 64, 512, False, False),        # one full K chunk
     (1, 96, 80, 804, False, True),         # K in two chunks
+    (3, 512, 16, 16, False, False),        # 128 x 16 tiles (n <= 16): a Gauss-Jordan leaf update's shape
+    (2, 300, 7, 40, True, True),           # 128 x 16 tiles, ragged rows and columns
 ]
 
 
@@ -235,6 +237,24 @@ def test_antisymmetric_b_sliced_by_rows(pkg, n, mode, alpha):
     assert np.all(err[:, sel] <= bound[:, sel]), (err / np.maximum(bound, 1e-300))[:, sel].max()
     if mode == 1:
         assert np.array_equal(C, -np.swapaxes(C, 1, 2))
+
+
+def test_narrow_tiles_antisymmetric_mode(pkg):
+    """Products of at most 16 output columns run on 128 x 16 tiles (SHAPES has two plain ones):
+    a 16 x 16 antisymmetric product, lower tiles computed and mirrored.  The Gauss-Jordan
+    updates of 16 target columns take the same tiles inside every inverse of n >= 32
+    (test_inverse_emulated, the step tests)."""
+    rng = np.random.default_rng(12)
+    batch = 3
+    G = rng.standard_normal((batch, 16, 16))
+    G = G - np.swapaxes(G, 1, 2)
+    S = rng.standard_normal((batch, 16, 16))
+    S = S - np.swapaxes(S, 1, 2)
+    A = np.matmul(G, S)
+    C = pkg.batched_gemm(A, G, mode=1, fp64_path=EMU)
+    low = np.tril(np.ones((16, 16), dtype=bool), -1)
+    assert np.all(_err(C, _exact(A, G))[:, low] <= emulated_bound(A, G)[:, low])
+    assert np.array_equal(C, -np.swapaxes(C, 1, 2))
 
 
 def test_gauss_jordan_mode_matches_native_semantics(pkg):
