@@ -314,16 +314,26 @@ __global__ void __launch_bounds__(256) gj_update_slice_kernel(double* const* W, 
 
 // Undo the row interchanges of Gauss-Jordan: inverse = X P, i.e. the column
 // interchanges applied in reverse order.  perm[c] = source column of column c.
+// One block per matrix: the pivots and the permutation in shared memory (2 n ints of dynamic
+// shared memory), the serial interchanges by one thread there.
 __global__ void gj_perm_kernel(const int* piv, int* perm, int n, int batch) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ int gj_pm[];
+    int* pm = gj_pm;
+    int* pv = gj_pm + n;
+    const int b = blockIdx.x;
     if (b >= batch) return;
-    const int* pv = piv + (size_t)b * n;
-    int* pm = perm + (size_t)b * n;
-    for (int c = 0; c < n; c++) pm[c] = c;
-    for (int j = n - 1; j >= 0; j--) {
-        int p = pv[j];
-        if (p != j) { int t = pm[j]; pm[j] = pm[p]; pm[p] = t; }
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        pm[c] = c;
+        pv[c] = piv[(size_t)b * n + c];
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int j = n - 1; j >= 0; j--) {
+            const int p = pv[j];
+            if (p != j) { const int t = pm[j]; pm[j] = pm[p]; pm[p] = t; }
+        }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) perm[(size_t)b * n + c] = pm[c];
 }
 
 __global__ void gj_gather_kernel(double* const* W, double* const* out, const int* perm, int n) {

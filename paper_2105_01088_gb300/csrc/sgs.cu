@@ -1020,7 +1020,7 @@ cudaError_t inverse_range(sgs_ctx* c, Instance& I, int p0, int cnt, cudaStream_t
     cudaError_t e = launch_gj_recursive(c, n, cnt, I.gj_b, I.p_work + p0, I.p_tbuf + p0, I.p_tup + p0, I.piv + po,
                                         I.logdet + p0, I.dsign + p0, I.err, 1e-12, st, oz);
     if (e != cudaSuccess) return e;
-    gj_perm_kernel<<<(cnt + 127) / 128, 128, 0, st>>>(I.piv + po, I.perm + po, n, cnt);
+    gj_perm_kernel<<<cnt, 128, 2 * (size_t)n * sizeof(int), st>>>(I.piv + po, I.perm + po, n, cnt);
     gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), cnt), 256, 0, st>>>(I.p_work + p0, I.p_si + p0, I.perm + po, n);
     counted(); counted();
     return cudaGetLastError();
@@ -2824,7 +2824,7 @@ sgs_status sgs_kernel_inverse(const double* S, int n, int batch, int fp64_path, 
         if (launch_gj_recursive(nullptr, n, batch, bsz, PW, PT, PU, piv, ld, ds, err, 0.0, tmp.stream, &oz) !=
             cudaSuccess)
             st = SGS_ECUDA;
-        gj_perm_kernel<<<(batch + 127) / 128, 128, 0, tmp.stream>>>(piv, perm, n, batch);
+        gj_perm_kernel<<<batch, 128, 2 * (size_t)n * sizeof(int), tmp.stream>>>(piv, perm, n, batch);
         gj_gather_kernel<<<dim3(grid_chunks(nn, 256, 64), batch), 256, 0, tmp.stream>>>(PW, PO, perm, n);
         cudaMemcpyAsync(inv, O, batch * nn * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
         if (logabsdet) cudaMemcpyAsync(logabsdet, ld, batch * sizeof(double), cudaMemcpyDeviceToHost, tmp.stream);
@@ -2985,7 +2985,7 @@ extern "C" sgs_status sgs_kernel_inverse_static(const double* S, double* inv, do
     counted();
     if (launch_gj(nullptr, n, batch, SGS_STATIC_PANEL, W, T, piv, logabsdet, dsign, err, 0.0, st) != cudaSuccess)
         return SGS_ECUDA;
-    gj_perm_kernel<<<(batch + 127) / 128, 128, 0, st>>>(piv, perm, n, batch);
+    gj_perm_kernel<<<batch, 128, 2 * (size_t)n * sizeof(int), st>>>(piv, perm, n, batch);   // 8 KB at n = 1024
     static_unpermute_kernel<<<dim3((unsigned)std::min(n, 64), batch), 256, (size_t)n * sizeof(double), st>>>(inv, perm,
                                                                                                       n);
     counted(); counted();
