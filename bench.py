@@ -273,8 +273,10 @@ def tc_roofline(prof, precision, n, pairs, steps, peaks):
 def timed_steps(torch, solver, stream, args, dist, local):
     """Warm-up steps, then exactly args.steps steps between barriers and synchronisations,
     CUDA events on the solver's stream and nvidia-smi clocks sampled meanwhile.  Returns
-    (energies of every step run, warm-up included, ms of the timed steps, clocks)."""
+    (energies of every step run, warm-up included, ms of the timed steps, clocks, the library's
+    kernel launches in the timed steps)."""
     Ew = solver.step(args.warmup)
+    solver.set_profiling(False)                   # resets the launch counter (profiling stays off)
     clocks = ClockSampler(local)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -289,7 +291,7 @@ def timed_steps(torch, solver, stream, args, dist, local):
     if dist:
         dist.barrier()
     ck = clocks.stop()
-    return np.concatenate([Ew[0], E[0]]), e0.elapsed_time(e1), ck
+    return np.concatenate([Ew[0], E[0]]), e0.elapsed_time(e1), ck, solver.profile()[1]
 
 
 def run_sgs(args):
@@ -327,14 +329,14 @@ def run_sgs(args):
     # measured bf16 rate / 36
     peak_fp64 = {"fma": peak_fp64_fma, "emulated": peaks.get("bf16_tflops", 1900.0) / 36.0}[args.fp64_path]
 
-    E_all, ms, ck = timed_steps(torch, solver, stream, args, dist, local)
+    E_all, ms, ck, launches_timed = timed_steps(torch, solver, stream, args, dist, local)
     sites = list(range(0, min(p.n_bath + 1, 33)))
     C_main = solver.correlator(sgs.SGS_CORR_SPIN_SPIN, sites)
     # second timed region of the same length with per-stage and per-GEMM-launch events (direct
     # launches) for the roofline of the dominant kernel
     solver.set_profiling(True)
     solver.step(args.steps)
-    prof, launches, gemm_prof = solver.profile()
+    prof, _, gemm_prof = solver.profile()
     solver.set_profiling(False)
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if dist:
@@ -403,7 +405,7 @@ def run_sgs(args):
             "vs_baseline": None, "dtype": dtype_of(args), "data": "synthetic",
             "config": dict(config_of(w, args.precision), fp64_products=args.fp64_path),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(launches), "roofline": roof,
+            "gpu_launches": int(launches_timed), "roofline": roof,
             "tc_roofline": tc_roofline(prof, args.precision, n, pairs, args.steps, peaks), "clocks": ck,
             "stages": stages, "energy_last": float(E_all[-1]), "panel_widths_gj_pf": list(solver.tuning(0)[:2]),
             "fp64_fma_peak_tflops": peak_fp64_fma}
@@ -415,7 +417,7 @@ def run_sgs(args):
                                stream=stream, autotune=True, **path_kwargs(args))
         if args.panel_widths:
             ms_solver.set_panel_widths(*[int(x) for x in args.panel_widths.split(",")])
-        Em_all, ms_m, ck_m = timed_steps(torch, ms_solver, stream, args, dist, local)
+        Em_all, ms_m, ck_m, _ = timed_steps(torch, ms_solver, stream, args, dist, local)
         C_mixed = ms_solver.correlator(sgs.SGS_CORR_SPIN_SPIN, sites)
         ms_solver.set_profiling(True)
         ms_solver.step(args.steps)
