@@ -332,6 +332,33 @@ __device__ __forceinline__ unsigned long long oz_to_double_bits(long long H, uns
     return (Hm | Lm) ? bits : 0ull;
 }
 
+// oz_to_double_bits where the result is known to be a normal number (biased exponent P + e + 1023 in
+// 1 .. 2046 for every leading-bit position P of |V| that can occur, 0 .. 74): the same bits, without
+// the selects of the range ends
+__device__ __forceinline__ unsigned long long oz_to_double_bits_normal(long long H, unsigned L, int e, bool neg) {
+    const bool sv = H < 0;
+    const unsigned long long Hm = sv ? (unsigned long long)(L ? ~H : -H) : (unsigned long long)H;
+    const unsigned Lm = sv ? ((0x10000000u - L) & 0xFFFFFFFu) : L;
+    const int lzh = __clzll((long long)Hm) & 63;
+    const bool right = lzh < 28;
+    const unsigned long long low = right ? (unsigned long long)(Lm >> (right ? 28 - lzh : 0))
+                                         : (unsigned long long)Lm << (right ? 0 : lzh - 28);
+    const unsigned long long NH = (Hm << lzh) | low;
+    const unsigned stH = right ? (Lm << ((lzh + 4) & 31)) : 0u;
+    const int lzl = __clz((int)Lm);
+    const unsigned long long NL = (unsigned long long)Lm << ((lzl + 32) & 63);
+    const bool hz = Hm == 0ull;
+    const unsigned long long N = hz ? NL : NH;
+    const unsigned sticky = hz ? 0u : stH;
+    const int P = hz ? 31 - lzl : 91 - lzh;
+    unsigned long long q = N >> 11;
+    const unsigned rest = (unsigned)(N & 0x3FFull) | sticky;
+    q += ((N >> 10) & 1ull) & ((rest != 0u ? 1ull : 0ull) | (q & 1ull));
+    const unsigned long long sbit = (unsigned long long)(sv != neg) << 63;
+    const unsigned long long bits = sbit + ((unsigned long long)(P + e + 1022) << 52) + q;
+    return (Hm | Lm) ? bits : 0ull;
+}
+
 template <int BN, int EPIW, int RING, bool BDBL>
 __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(const __grid_constant__ OzGemm p) {
     constexpr int SLAB_B = BN * 128, TS = BN + 1, NB = BDBL ? 2 : 1;
@@ -339,7 +366,7 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
     extern __shared__ uint8_t oz_smem_raw[];
     __shared__ uint64_t bfull[2], bempty[2], afull[RING], aempty[RING], tfull, done;
     __shared__ uint32_t tmem_base;
-    __shared__ int skip, abort_flag, s_ok;
+    __shared__ int skip, abort_flag, s_ok, s_fcmin, s_fcmax;
     __shared__ int col_e[BN];
 
     const GemmBatch& g = p.g;
@@ -523,7 +550,15 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
         const bool skew = g.mode == GEMM_SKEW, gj = g.mode == GEMM_GJ;
         bool ok = true;
         if (nslab > 0) {
-            if (tid == 0) s_ok = mbar_wait_or_abort(smem_u32(&tfull), 0u, p.err) ? 1 : 0;
+            if (tid == 0) {
+                // the range of the tile's nonzero column exponent fields (for the normal-range test)
+                int lo = 4096, hi = 0;
+                for (int c = 0; c < BN; c++)
+                    if (col_e[c] > 0) { lo = min(lo, col_e[c]); hi = max(hi, col_e[c]); }
+                s_fcmin = lo;
+                s_fcmax = hi;
+                s_ok = mbar_wait_or_abort(smem_u32(&tfull), 0u, p.err) ? 1 : 0;
+            }
             asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
             ok = s_ok != 0;
         }
@@ -557,6 +592,13 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
             const int er = (active && row < g.m) ? p.ea[(size_t)bl * p.m_pad + row] : 0;
             const int ae = p.alpha_pow2 ? p.alpha_e : 0;
             const bool an = p.alpha_pow2 && p.alpha_neg;
+            // every result of this warp's rows is a normal number: with e = er + fc - 2107 + ae and
+            // the leading bit P of |V| in 0 .. 74, the biased exponent P + e + 1023 stays in 1 .. 2046
+            // (rows or columns with a zero exponent field give zeros either way); then the
+            // combination takes the form without the range-end selects (the same bits)
+            const bool row_normal = er == 0 || s_fcmax == 0 ||
+                                    (er + s_fcmin - 2107 + ae + 1023 >= 1 && er + s_fcmax - 2107 + ae + 1023 + 74 <= 2046);
+            const bool fast = __all_sync(0xffffffffu, row_normal);
             if (nslab > 0) {
                 // eight columns per pass: one 8-column TMEM load per group, then eight independent
                 // combinations
@@ -579,7 +621,8 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
                         long long H;
                         unsigned L;
                         oz_combine(u, j, H, L);
-                        const unsigned long long v = oz_to_double_bits(H, L, er + fc - 2107 + ae, an);
+                        const unsigned long long v = fast ? oz_to_double_bits_normal(H, L, er + fc - 2107 + ae, an)
+                                                          : oz_to_double_bits(H, L, er + fc - 2107 + ae, an);
                         reinterpret_cast<unsigned long long*>(tile)[rr0 * TS + c] = (er > 0 && fc > 0) ? v : 0ull;
                     }
                 }
