@@ -37,6 +37,8 @@ struct GemmBatch {
     int active_cmp;                      //   otherwise C = Cin (pass-through)
     int mode; int gj_k0; int gj_b;
     int gj_cols;                         // GJ: 1 = output columns gj_k0 .. gj_k0 + gj_b - 1 not written
+    int gj_acc;                          // GJ: 1 = rows gj_k0 .. gj_k0 + gj_b - 1 add Cin like the others
+                                         // (a later K chunk of a Gauss-Jordan update)
                                          //     (the panel's own), 0 = every output column written
     int batch;
     int b_antisym;                       // hint: B (and B2) antisymmetric, op(B)'s columns = -B's rows
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
                     v = alpha * acc[i][j][h];
                     if (Cinb && g.beta != 0.0) {
                         bool use = true;
-                        if (g.mode == GEMM_GJ && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b) use = false;
+                        if (g.mode == GEMM_GJ && !g.gj_acc && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b) use = false;
                         if (use) v += g.beta * Cinb[(long long)r * g.ldcin + c];
                     }
                     if (Cin2b) v += g.beta2 * Cin2b[(long long)r * g.ldcin + c];
@@ -230,6 +232,7 @@ inline GemmBatch gemm_defaults() {
     g.alpha = 1.0; g.beta = 0.0; g.diag = 0.0; g.sA2 = 0.0; g.sB2 = 0.0; g.Cin2 = nullptr; g.beta2 = 0.0;
     g.mode = GEMM_FULL; g.active_flag = nullptr; g.alpha_b = nullptr; g.active_cmp = 0; g.b_antisym = 0;
     g.gj_cols = 1;
+    g.gj_acc = 0;
     return g;
 }
 

@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
                     const int e = tid + NE * q, rr = e / BN, cc = e % BN, r = m0 + rr, c = n0 + cc;
                     if (r >= g.m || c >= g.n || (skew && r < c)) continue;
                     const double t = tile[rr * TS + cc];
-                    const bool gj_row = gj && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b;
+                    const bool gj_row = gj && !g.gj_acc && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b;
                     emit(rr, cc, r, c, gj_row ? t : cin_s[rr * BN + cc] + t);
                 }
             } else {
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
                     const int e = tid + NE * q, rr = e / BN, cc = e % BN, r = m0 + rr, c = n0 + cc;
                     if (r >= g.m || c >= g.n || (skew && r < c)) continue;
                     double v = 0.0;
-                    if (use_cin && !(active && gj && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b)) {
+                    if (use_cin && !(active && gj && !g.gj_acc && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b)) {
                         v = cin_async ? cin_s[rr * BN + cc] : Cinb[(long long)r * g.ldcin + c];
                         if (scale_cin) v *= g.beta;
                     }
@@ -755,7 +755,6 @@ inline int oz_tiles(const GemmBatch& g, int bn) {
 // launches of one product, for launch accounting
 inline int oz_launches(const GemmBatch& g, const OzBuf& buf) {
     if (g.batch <= 0 || g.m <= 0 || g.n <= 0 || g.k <= 0 || !buf.base) return 1;
-    if (g.mode == GEMM_GJ && g.k > OZ_KC) return 1;
     int total = 0;
     for (int k0 = 0; k0 < g.k; k0 += OZ_KC) {
         const size_t per = oz_entry_bytes(g.m, g.n, std::min(OZ_KC, g.k - k0));
@@ -860,7 +859,6 @@ inline cudaError_t gemm_oz(const GemmBatch& g, const OzBuf& buf, int* err, cudaS
     if (g.batch <= 0 || g.m <= 0 || g.n <= 0) return cudaSuccess;
     if (g.k <= 0 || !buf.base || !err) return gemm_f64(g, st);
     if (g.mode == GEMM_SKEW && g.m != g.n) return cudaErrorInvalidValue;
-    if (g.mode == GEMM_GJ && g.k > OZ_KC) return gemm_f64(g, st);
     if (oz_entry_bytes(g.m, g.n, std::min(g.k, OZ_KC)) + 8192 > buf.bytes) return gemm_f64(g, st);
     for (int k0 = 0; k0 < g.k; k0 += OZ_KC) {
         GemmBatch h = g;
@@ -871,6 +869,7 @@ inline cudaError_t gemm_oz(const GemmBatch& g, const OzBuf& buf, int* err, cudaS
         if (k0 > 0) {
             h.Cin = (const double* const*)g.C; h.offCin = g.offC; h.ldcin = g.ldc; h.beta = 1.0;
             h.Cin2 = nullptr; h.beta2 = 0.0; h.diag = 0.0;
+            h.gj_acc = 1;          // a Gauss-Jordan update's pivot rows hold the first chunk's product now
         }
         const cudaError_t e = gemm_oz_chunk(h, buf, err, st);
         if (e != cudaSuccess) return e;

@@ -257,10 +257,12 @@ def test_narrow_tiles_antisymmetric_mode(pkg):
     assert np.array_equal(C, -np.swapaxes(C, 1, 2))
 
 
-def test_gauss_jordan_mode_matches_native_semantics(pkg):
-    """Columns of the panel stay as they were; rows of the panel start from 0."""
-    rng = np.random.default_rng(11)
-    batch, n, k0, b = 2, 192, 64, 32
+@pytest.mark.parametrize("n,k0,b", [(192, 64, 32), (700, 50, 600)])
+def test_gauss_jordan_mode_matches_native_semantics(pkg, n, k0, b):
+    """Columns of the panel stay as they were; rows of the panel start from 0.  K = 600 runs
+    as two K chunks: the second adds onto the pivot rows the first replaced."""
+    rng = np.random.default_rng(11 + b)
+    batch = 2
     A = rng.standard_normal((batch, n, b))
     B = rng.standard_normal((batch, b, n))
     W = rng.standard_normal((batch, n, n))
