@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--impl", default="sgs", choices=["sgs", "reference"])
     ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
     ap.add_argument("--workload", default="large",
-                    choices=["large", "small", "two_channel", "siam_L500", "serving", "batched"])
+                    choices=["large", "small", "two_channel", "siam_L500", "serving", "batched", "siam_estar"])
     ap.add_argument("--instances", type=int, default=256, help="batched: number of independent instances")
     ap.add_argument("--max-bath", type=int, default=64, help="batched: bath length L ~ U{16..max-bath}")
     ap.add_argument("--rate", type=float, default=100.0, help="serving: Poisson arrival rate (requests/s)")
@@ -67,6 +67,10 @@ def parse():
                     help="serving: request sizes L ~ U{8..40}, M in {4, 8} (scaled) or L ~ U{16..256}, "
                          "M in {8, 16, 32} (the batched workload's mix)")
     ap.add_argument("--rank", type=int, default=0, help="override the ansatz rank M (profiling cases)")
+    ap.add_argument("--estar-rank", type=int, default=8, help="siam_estar: largest rank of the growth")
+    ap.add_argument("--estar-steps", type=int, default=200, help="siam_estar: steps per rank")
+    ap.add_argument("--estar-ds", type=float, default=0.1, help="siam_estar: imaginary-time step")
+    ap.add_argument("--estar-knorm", type=float, default=0.1, help="siam_estar: ||K||_F of an added state's generator")
     ap.add_argument("--fp64-path", default="emulated", choices=["fma", "emulated"],
                     help="FP64 products: emulated on the bf16 tensor cores (the library's default) or FMA pipe")
     ap.add_argument("--emulation-scratch-gb", type=float, default=0.0,
@@ -553,6 +557,69 @@ def clustered_states_device(n_modes, M, seed, parity, spread=1.0):
     return np.ascontiguousarray(g), np.exp(1j * th)
 
 
+def run_estar(args):
+    """The ground-state energy estimate of Sec. IV A on its system (SIAM, L = 500 sites, U = t = 1,
+    U / Gamma = 5, particle-hole symmetric), bounded: the rank grows from 1 to --estar-rank by the
+    schedule of Sec. III C (growth.grow), --estar-steps steps per rank from the U = 0 ground state
+    (one Gaussian, +-polar(A): the sign of lower energy), the variance delta_H^2 (Eq. residual) at
+    the end of each rank, and E* the intercept of the linear fit of E against delta_H^2 over the
+    ranks (growth.extrapolate_energy; the paper fits only points below 2e-5)."""
+    import torch
+    import paper_2105_01088_gb300 as sgs
+    from paper_2105_01088_gb300.growth import extrapolate_energy, grow
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    sgs.use_torch_allocator()
+    p = inp.SIAM_L500.model
+    model = sgs.build_anderson(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels)
+    # the U = 0 ground state: Gamma = +-A |A|^-1 (the polar factor of A), the sign of the lower energy
+    A = torch.tensor(model.A, dtype=torch.float64, device="cuda")
+    U_, _, Vh = torch.linalg.svd(A)
+    P = (U_ @ Vh).cpu().numpy()
+    P = 0.5 * (P - P.T)
+    stream = torch.cuda.Stream()
+    best = None
+    for sign in (1.0, -1.0):
+        g = (sign * P)[None]
+        ph, _ = sgs.batched_pfaffian(g.astype(np.complex128))
+        parity = 1 if ph[0].real > 0 else -1
+        s = sgs.Solver(model, g, None, dtau=args.estar_ds, parity=parity, stream=stream, cmode=1)
+        e = s.variance(0)[0]                  # <H> of the current state, computed on the device
+        s.close()
+        if best is None or e < best[0]:
+            best = (e, g, parity)
+    e0, g0, parity = best
+    solver = sgs.Solver(model, g0, None, dtau=args.estar_ds, parity=parity, stream=stream, cmode=1,
+                        **path_kwargs(args))
+    rng = np.random.default_rng(11)
+    t0 = time.perf_counter()
+    out = grow(solver, 0, args.estar_rank, args.estar_steps, args.estar_knorm, rng, with_variance=True)
+    wall = time.perf_counter() - t0
+    solver.close()
+    ranks = [int(r) for r, _, _ in out]
+    ev = [(float(v[0]), float(v[1])) for _, _, v in out]
+    E = [x[0] for x in ev]
+    var = [x[1] for x in ev]
+    try:
+        est, sigma = extrapolate_energy(E, var, var_max=float("inf"))
+    except ValueError:
+        est, sigma = float("nan"), float("nan")
+    paper = -635.3490861
+    line = {"metric": "ground-state energy estimate E* (Sec. IV A)", "value": est, "unit": "t",
+            "sigma": sigma, "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "dtype": dtype_of(args),
+            "config": {"workload": f"SIAM L = 500 (2N = 2000), U = t = 1, U/Gamma = 5, eps_d = -U/2, mu = 0; ranks 1.."
+                                   f"{args.estar_rank}, {args.estar_steps} steps per rank at ds = {args.estar_ds}, "
+                                   f"||K||_F = {args.estar_knorm}, phase form of c_mu, from the U = 0 ground state",
+                       "fit": "all ranks (the paper fits only delta_H^2 < 2e-5)"},
+            "paper_E_star": paper, "paper_sigma": 4e-7, "difference_to_paper": est - paper,
+            "ranks": ranks, "energies": E, "variances": var, "E_U0_state": e0, "wall_s": wall,
+            "steps": int(sum(len(x[1]) for x in out))}
+    print(json.dumps(line))
+    return 0
+
+
 def run_batched(args):
     """Many independent uneven instances advanced together: every step replays one
     captured graph whose branches are the instances (their kernels overlap on the
@@ -713,6 +780,8 @@ def main():
         return run_serving(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "siam_estar":
+        return run_estar(args)
     return run_sgs(args)
 
 
