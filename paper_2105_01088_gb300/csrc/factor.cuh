@@ -4,14 +4,15 @@
 //    (Eq. def-delta-matrix needs S^{-1}; |Pf S| = |det S|^{1/2} gives the
 //    overlap magnitude of Sec. II B).  Blocked: a panel kernel eliminates b
 //    columns of every matrix (one CTA per matrix, panel in shared memory),
-//    then one batched DMMA GEMM applies the delayed rank-b update to the
+//    then one batched product applies the delayed rank-b update to the
 //    rest of each matrix.
 //  * Complex Pfaffian of Y = Gamma_0 + Delta^{a,b} (the phase of the overlap
 //    in the reference gauge of Sec. II B) by Parlett-Reid elimination with
 //    pivoting, blocked the same way: the panel kernel performs b elimination
 //    steps, materialising the two columns each step needs from the stored
-//    matrix plus the pending rank-2 updates, and the rank-2b trailing update
-//    is two real DMMA GEMMs (real and imaginary parts, k = 4b).
+//    matrix (its upper triangle, the only part kept current) plus the pending
+//    rank-2 updates, and the rank-2b trailing update is a batch of two real
+//    products per matrix (real and imaginary parts, k = 4b).
 #pragma once
 #include "common.cuh"
 #include "oz_digits.cuh"
@@ -468,17 +469,27 @@ __global__ void __launch_bounds__(PF_PANEL_THREADS, 4) pf_panel_kernel(PfPanelAr
         }
         if (p != k + 1) {
             const int q = k + 1;
-            // symmetric interchange q <-> p on the live part (rows/cols >= k)
-            for (int j = k + threadIdx.x; j < n; j += blockDim.x) {
+            // symmetric interchange q <-> p on the upper triangle of the live part, the only part the
+            // panels read (row k is done: its entries are in ckr, cki); the trailing update reads its
+            // Cin there too (cin_trans), so the lower triangle is left stale.  With q < p:
+            //   row entries beyond p:    Y[q][j] <-> Y[p][j]                       (j > p)
+            //   between q and p:         Y'[q][c] = -Y[c][p], Y'[c][p] = -Y[q][c]  (q < c < p)
+            //   the pair:                Y'[q][p] = -Y[q][p]
+            for (int j = p + 1 + threadIdx.x; j < n; j += blockDim.x) {
                 double t;
                 t = Yr[(size_t)q * n + j]; Yr[(size_t)q * n + j] = Yr[(size_t)p * n + j]; Yr[(size_t)p * n + j] = t;
                 t = Yi[(size_t)q * n + j]; Yi[(size_t)q * n + j] = Yi[(size_t)p * n + j]; Yi[(size_t)p * n + j] = t;
             }
-            __syncthreads();
-            for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-                double t;
-                t = Yr[(size_t)i * n + q]; Yr[(size_t)i * n + q] = Yr[(size_t)i * n + p]; Yr[(size_t)i * n + p] = t;
-                t = Yi[(size_t)i * n + q]; Yi[(size_t)i * n + q] = Yi[(size_t)i * n + p]; Yi[(size_t)i * n + p] = t;
+            for (int c = q + 1 + threadIdx.x; c < p; c += blockDim.x) {
+                const double ar = Yr[(size_t)q * n + c], ai = Yi[(size_t)q * n + c];
+                Yr[(size_t)q * n + c] = -Yr[(size_t)c * n + p];
+                Yi[(size_t)q * n + c] = -Yi[(size_t)c * n + p];
+                Yr[(size_t)c * n + p] = -ar;
+                Yi[(size_t)c * n + p] = -ai;
+            }
+            if (threadIdx.x == 0) {
+                Yr[(size_t)q * n + p] = -Yr[(size_t)q * n + p];
+                Yi[(size_t)q * n + p] = -Yi[(size_t)q * n + p];
             }
             for (int t = threadIdx.x; t < s; t += blockDim.x) {
                 double x;

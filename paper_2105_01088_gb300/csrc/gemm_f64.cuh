@@ -39,6 +39,9 @@ struct GemmBatch {
     int gj_cols;                         // GJ: 1 = output columns gj_k0 .. gj_k0 + gj_b - 1 not written
     int gj_acc;                          // GJ: 1 = rows gj_k0 .. gj_k0 + gj_b - 1 add Cin like the others
                                          // (a later K chunk of a Gauss-Jordan update)
+    int cin_trans;                       // 1: Cin element (r, c) is read at Cin[b][offCin + c ldcin + r]
+                                         // (every batch entry active; the Pfaffian's updates read the
+                                         // upper triangle, with beta = -1)
                                          //     (the panel's own), 0 = every output column written
     int batch;
     int b_antisym;                       // hint: B (and B2) antisymmetric, op(B)'s columns = -B's rows
@@ -186,14 +189,14 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmBatch g) {
                 if (r >= g.m || c >= g.n) continue;
                 double v;
                 if (!active) {
-                    v = Cinb ? Cinb[(long long)r * g.ldcin + c] : 0.0;
+                    v = Cinb ? Cinb[g.cin_trans ? (long long)c * g.ldcin + r : (long long)r * g.ldcin + c] : 0.0;
                     if (g.mode == GEMM_SKEW && r < c) continue;
                 } else {
                     v = alpha * acc[i][j][h];
                     if (Cinb && g.beta != 0.0) {
                         bool use = true;
                         if (g.mode == GEMM_GJ && !g.gj_acc && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b) use = false;
-                        if (use) v += g.beta * Cinb[(long long)r * g.ldcin + c];
+                        if (use) v += g.beta * Cinb[g.cin_trans ? (long long)c * g.ldcin + r : (long long)r * g.ldcin + c];
                     }
                     if (Cin2b) v += g.beta2 * Cin2b[(long long)r * g.ldcin + c];
                     if (r == c) v += g.diag;
@@ -233,6 +236,7 @@ inline GemmBatch gemm_defaults() {
     g.mode = GEMM_FULL; g.active_flag = nullptr; g.alpha_b = nullptr; g.active_cmp = 0; g.b_antisym = 0;
     g.gj_cols = 1;
     g.gj_acc = 0;
+    g.cin_trans = 0;
     return g;
 }
 

@@ -573,9 +573,24 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
             // Cin itself.  Cin may be C itself: every Cin element is read before this CTA stores any.
             double* cin_s = tile + OZ_BM * TS;
             const bool use_cin = Cinb && (!active || g.beta != 0.0);
+            const bool ct = g.cin_trans != 0;
             const bool cin_async = use_cin && ((reinterpret_cast<uintptr_t>(Cinb) & 15) == 0) &&
                                    ((g.ldcin & 1) == 0);
-            if (cin_async) {
+            // transposed Cin: element (rr, cc) at cin_s[cc OZ_BM + (rr ^ 2 (cc & 7))], copied 16 bytes
+            // (two rows) at a time along the memory rows; the swizzle spreads the reads of consecutive
+            // cc over eight bank pairs
+            auto cin_smem = [&](int rr, int cc) {
+                return ct ? cin_s[cc * OZ_BM + (rr ^ ((cc & 7) << 1))] : cin_s[rr * BN + cc];
+            };
+            if (cin_async && ct) {
+                for (int x = tid; x < BN * (OZ_BM / 2); x += NE) {
+                    const int cc = x / (OZ_BM / 2), rp = 2 * (x % (OZ_BM / 2)), r = m0 + rp, c = n0 + cc;
+                    const uint32_t bytes = c < g.n ? (r + 1 < g.m ? 16u : (r < g.m ? 8u : 0u)) : 0u;
+                    const double* src = bytes ? Cinb + (long long)c * g.ldcin + r : Cinb;
+                    cp_async16(smem_u32(cin_s + cc * OZ_BM + (rp ^ ((cc & 7) << 1))), src, bytes);
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            } else if (cin_async) {
                 for (int x = tid; x < OZ_BM * (BN / 2); x += NE) {
                     const int rr = x / (BN / 2), c = n0 + 2 * (x % (BN / 2)), r = m0 + rr;
                     const uint32_t bytes = r < g.m ? (c + 1 < g.n ? 16u : (c < g.n ? 8u : 0u)) : 0u;
@@ -630,6 +645,7 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
             if (cin_async) asm volatile("cp.async.wait_all;" ::: "memory");
             asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
             const bool scale_cin = active && g.beta != 1.0;          // beta = 1 (the in-place updates): no product
+            const bool cin_neg = active && ct && g.beta == -1.0;     // Cin(r, c) = -Cin^T: a subtraction
             const bool keep_tile = skew || (active && g.diag != 0.0);
             // an element's final value: kept in the tile for the mirrored block and the diagonal,
             // stored unless its column is one of the Gauss-Jordan panel's
@@ -648,14 +664,15 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
                     if (r >= g.m || c >= g.n || (skew && r < c)) continue;
                     emit(rr, cc, r, c, tile[rr * TS + cc]);
                 }
-            } else if (active && p.alpha_pow2 && !Cin2b && use_cin && !scale_cin && cin_async) {
+            } else if (active && p.alpha_pow2 && !Cin2b && use_cin && (!scale_cin || cin_neg) && cin_async) {
 #pragma unroll 4
                 for (int q = 0; q < PER; q++) {
                     const int e = tid + NE * q, rr = e / BN, cc = e % BN, r = m0 + rr, c = n0 + cc;
                     if (r >= g.m || c >= g.n || (skew && r < c)) continue;
                     const double t = tile[rr * TS + cc];
                     const bool gj_row = gj && !g.gj_acc && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b;
-                    emit(rr, cc, r, c, gj_row ? t : cin_s[rr * BN + cc] + t);
+                    const double ci = cin_smem(rr, cc);
+                    emit(rr, cc, r, c, gj_row ? t : (cin_neg ? t - ci : ci + t));
                 }
             } else {
 #pragma unroll 4
@@ -664,7 +681,8 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
                     if (r >= g.m || c >= g.n || (skew && r < c)) continue;
                     double v = 0.0;
                     if (use_cin && !(active && gj && !g.gj_acc && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b)) {
-                        v = cin_async ? cin_s[rr * BN + cc] : Cinb[(long long)r * g.ldcin + c];
+                        v = cin_async ? cin_smem(rr, cc)
+                                      : Cinb[ct ? (long long)c * g.ldcin + r : (long long)r * g.ldcin + c];
                         if (scale_cin) v *= g.beta;
                     }
                     if (active) {

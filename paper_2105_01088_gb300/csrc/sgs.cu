@@ -999,9 +999,11 @@ cudaError_t launch_pf(sgs_ctx* c, int n, int batch, int bsmax, double** Y, doubl
         g.offB = (long long)e0 * 4 * bs;
         g.transB = 1;
         g.offC = (long long)e0 * n + e0;
-        g.Cin = (const double* const*)upC; g.offCin = g.offC; g.ldcin = n; g.beta = 1.0;
         // the rank-2b complex update T U^T - U T^T is antisymmetric, as is the trailing
-        // block it updates: compute the lower tiles and mirror them
+        // block it updates: compute the lower tiles and mirror them.  The panels keep only the
+        // upper triangle current, so Cin(r, c) = -Y[c][r]: read transposed with beta = -1
+        g.Cin = (const double* const*)upC; g.offCin = g.offC; g.ldcin = n; g.beta = -1.0;
+        g.cin_trans = 1;
         g.mode = GEMM_SKEW;
         const double m2 = (double)(n - e0) * (n - e0);
         const cudaError_t e = gemm(c, g, st, m2 * 4.0 * bs * 2 * batch, oz, err, sliced);
