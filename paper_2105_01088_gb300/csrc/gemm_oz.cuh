@@ -579,8 +579,10 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
             // transposed Cin: element (rr, cc) at cin_s[cc OZ_BM + (rr ^ 2 (cc & 7))], copied 16 bytes
             // (two rows) at a time along the memory rows; the swizzle spreads the reads of consecutive
             // cc over eight bank pairs
+            // one load at an integer-selected index (a select between two loaded doubles would issue
+            // on the FP64 pipe)
             auto cin_smem = [&](int rr, int cc) {
-                return ct ? cin_s[cc * OZ_BM + (rr ^ ((cc & 7) << 1))] : cin_s[rr * BN + cc];
+                return cin_s[ct ? cc * OZ_BM + (rr ^ ((cc & 7) << 1)) : rr * BN + cc];
             };
             if (cin_async && ct) {
                 for (int x = tid; x < BN * (OZ_BM / 2); x += NE) {
@@ -645,7 +647,9 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
             if (cin_async) asm volatile("cp.async.wait_all;" ::: "memory");
             asm volatile("bar.sync 1, %0;" :: "n"(NE) : "memory");
             const bool scale_cin = active && g.beta != 1.0;          // beta = 1 (the in-place updates): no product
-            const bool cin_neg = active && ct && g.beta == -1.0;     // Cin(r, c) = -Cin^T: a subtraction
+            // Cin(r, c) = -Cin^T: the sign bit flipped by an integer XOR, then the one addition
+            const unsigned long long cin_sign = (active && ct && g.beta == -1.0) ? 0x8000000000000000ull : 0ull;
+            const bool cin_neg = cin_sign != 0ull;
             const bool keep_tile = skew || (active && g.diag != 0.0);
             // an element's final value: kept in the tile for the mirrored block and the diagonal,
             // stored unless its column is one of the Gauss-Jordan panel's
@@ -671,8 +675,8 @@ __global__ void __launch_bounds__(32 * (EPIW + 2), BDBL ? 1 : 2) oz_gemm_kernel(
                     if (r >= g.m || c >= g.n || (skew && r < c)) continue;
                     const double t = tile[rr * TS + cc];
                     const bool gj_row = gj && !g.gj_acc && r >= g.gj_k0 && r < g.gj_k0 + g.gj_b;
-                    const double ci = cin_smem(rr, cc);
-                    emit(rr, cc, r, c, gj_row ? t : (cin_neg ? t - ci : ci + t));
+                    const double ci = __longlong_as_double(__double_as_longlong(cin_smem(rr, cc)) ^ (long long)cin_sign);
+                    emit(rr, cc, r, c, gj_row ? t : ci + t);
                 }
             } else {
 #pragma unroll 4
