@@ -156,24 +156,38 @@ __global__ void __launch_bounds__(256) eom_finish_kernel(InstDev d, const double
         const size_t e = (size_t)k * n + l;
         const int sk = d.slot[k], sl = d.slot[l];
         if (!rest && sk < 0 && sl < 0) continue;            // the pairs' impurity terms only
-        // A_kl (row k of the CSR)
-        R akl = 0;
-        for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++)
-            if (d.a_col[q] == l) akl = (R)d.a_val[q];
+        // one pass over each of the CSR rows l and k of A (read-only loads) for A_kl, the pairs'
+        // commutator terms against A, -(T A^T)_kl - (A T)_kl, and the beta = mu term's
+        // (Gamma F)_kl, (F Gamma)_kl: the T and Gamma loads of a row entry issue together
+        R akl = 0, ta = 0, at = 0, gf = 0, fg = 0;
+        {
+            const int q0 = __ldg(d.a_rowptr + l), q1 = __ldg(d.a_rowptr + l + 1);
+            for (int q = q0; q < q1; q++) {
+                const int cq = __ldg(d.a_col + q);
+                const R v = (R)__ldg(d.a_val + q);
+                if (rest) ta = fma((R)T[(size_t)k * n + cq], v, ta);
+                if (self_term) gf = fma(-(R)gm[(size_t)k * n + cq], v, gf);
+            }
+        }
+        {
+            const int q0 = __ldg(d.a_rowptr + k), q1 = __ldg(d.a_rowptr + k + 1);
+            for (int q = q0; q < q1; q++) {
+                const int cq = __ldg(d.a_col + q);
+                const R v = (R)__ldg(d.a_val + q);
+                if (cq == l) akl = v;
+                if (rest) at = fma(v, (R)T[(size_t)cq * n + l], at);
+                if (self_term) fg = fma(v, (R)gm[(size_t)cq * n + l], fg);
+            }
+        }
         R acc = (R)out[e];
         if (rest) {
             acc = fma(akl, s_w2, acc);
-            // the pairs' commutator terms against A: -(T A^T)_kl - (A T)_kl
-            for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) acc = fma(-(R)T[(size_t)k * n + d.a_col[q]], (R)d.a_val[q], acc);
-            for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) acc = fma(-(R)d.a_val[q], (R)T[(size_t)d.a_col[q] * n + l], acc);
+            acc = acc - ta - at;
         }
         if (self_term) {   // beta = mu: Delta = Gamma_mu, Delta F Delta = Gamma F Gamma
             const double* co = coef + (size_t)(mu * M + mu) * 6;
             const R g = (R)gm[e];
             const R f = akl + ((sk >= 0 && sl >= 0) ? (R)fs[sk * ni + sl] : (R)0);
-            R gf = 0, fg = 0;   // (Gamma F)_kl, (F Gamma)_kl
-            for (int q = d.a_rowptr[l]; q < d.a_rowptr[l + 1]; q++) gf -= (R)gm[(size_t)k * n + d.a_col[q]] * (R)d.a_val[q];
-            for (int q = d.a_rowptr[k]; q < d.a_rowptr[k + 1]; q++) fg += (R)d.a_val[q] * (R)gm[(size_t)d.a_col[q] * n + l];
             if (sl >= 0) for (int m = 0; m < ni; m++) gf += (R)gm[(size_t)k * n + d.imp[m]] * (R)fs[m * ni + sl];
             if (sk >= 0) for (int m = 0; m < ni; m++) fg += (R)fs[sk * ni + m] * (R)gm[(size_t)d.imp[m] * n + l];
             acc += (R)2 * ((R)co[0] * (gf - fg) + (R)co[2] * ((R)gfgm[e] + f) + (R)co[4] * g);
