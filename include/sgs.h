@@ -72,13 +72,13 @@ typedef enum {
  *    slice products of combined weight above 2^-63 are summed exactly in fp32
  *    TMEM accumulators (K in chunks of 512) and combined in 64-bit integers
  *    with one final rounding.  Error of one product, per element:
- *      |C_ij - (AB)_ij| <= u |(AB)_ij| + 2^-55 K max_k|A_ik| max_k|B_kj|
+ *      |C_ij - (AB)_ij| <= u |(AB)_ij| + K 2^-52 max_k|A_ik| max_k|B_kj|
  *    (u = 2^-53), plus u times any added terms (beta Cin, diag): normwise in
  *    row i of A and column j of B, so an element whose terms are all far below
  *    those maxima is less accurate than the K u sum_k |A_ik||B_kj| of a native
  *    FP64 dot product.
  *  - SGS_FP64_FMA: FP64 fused multiply-adds on the CUDA cores (the error of a
- *    native FP64 dot product), about 6x slower on GB300 at 2N = 512. */
+ *    native FP64 dot product), about 8x slower on GB300 at 2N = 512. */
 typedef enum {
     SGS_FP64_EMULATED = 0,
     SGS_FP64_FMA = 1
