@@ -129,3 +129,41 @@ def test_dropping_the_second_update_is_caught():
 
     broken(W, 0, n)
     assert np.abs(unpermute(W, piv) - np.linalg.inv(S)).max() > 1e-3
+
+
+def update_chunked(W, p0, K, t0, w, kc):
+    """update() in K chunks of kc (the emulated product's chunks of 512): the first chunk replaces
+    the pivot rows like update(), the later ones add onto every row (gj_acc)."""
+    T = W[p0:p0 + K, t0:t0 + w].copy()
+    keep = np.ones(W.shape[0], bool)
+    keep[p0:p0 + K] = False
+    out = None
+    for c0 in range(0, K, kc):
+        c1 = min(K, c0 + kc)
+        prod = W[:, p0 + c0:p0 + c1] @ T[c0:c1]
+        if out is None:
+            out = prod + np.where(keep[:, None], W[:, t0:t0 + w], 0.0)
+        else:
+            out = out + prod
+    W[:, t0:t0 + w] = out
+
+
+@pytest.mark.parametrize("K,kc", [(10, 4), (12, 12), (13, 5)])
+def test_k_chunked_update_equals_one_update(K, kc):
+    rng = np.random.default_rng(K + kc)
+    n, p0, t0, w = 40, 6, 25, 9
+    W = rng.standard_normal((n, n))
+    a, b = W.copy(), W.copy()
+    update(a, p0, K, t0, w)
+    update_chunked(b, p0, K, t0, w, kc)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    # a later chunk that replaced the pivot rows again would drop the first chunk's product
+    if kc < K:
+        c = W.copy()
+        T = c[p0:p0 + K, t0:t0 + w].copy()
+        keep = np.ones(n, bool)
+        keep[p0:p0 + K] = False
+        out = c[:, p0:p0 + kc] @ T[:kc] + np.where(keep[:, None], c[:, t0:t0 + w], 0.0)
+        out2 = c[:, p0 + kc:p0 + K] @ T[kc:] + np.where(keep[:, None], out, 0.0)
+        c[:, t0:t0 + w] = out2
+        assert np.abs(c - a).max() > 1e-6
