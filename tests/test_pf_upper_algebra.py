@@ -105,3 +105,26 @@ def test_row_swap_alone_is_caught():
     ref_phase, ref_log = orc.pfaffian_log(Y)
     bad = blocked_pfaffian(Y, 4, upper_swap=False)
     assert abs(np.log(abs(bad)) - ref_log) > 1e-6 or abs(bad / abs(bad) - ref_phase) > 1e-6
+
+
+def test_update_packs_give_the_rank_2b_update():
+    """The four packs the panel writes (as FP64 or as slices), with the source plane and sign of
+    each block as the panel takes them (A_re: block src, negated for Ti and Ur; A_im: block src,
+    negated for Ur and Ui; B_re: plane (blk + 2) & 3; B_im: plane 3 - blk; planes Tr, Ti, Ur, Ui),
+    give Re and Im of T U^T - U T^T as A_re B_re^T and A_im B_im^T."""
+    rng = np.random.default_rng(5)
+    bs, n = 5, 11
+    T = rng.standard_normal((bs, n)) + 1j * rng.standard_normal((bs, n))
+    U = rng.standard_normal((bs, n)) + 1j * rng.standard_normal((bs, n))
+    planes = [T.real, T.imag, U.real, U.imag]
+
+    def pack(src_of, neg_of):
+        return np.concatenate([(-1.0 if neg_of(b) else 1.0) * planes[src_of(b)].T for b in range(4)], axis=1)
+
+    A_re = pack(lambda b: b, lambda b: b in (1, 2))
+    A_im = pack(lambda b: b, lambda b: b >= 2)
+    B_re = pack(lambda b: (b + 2) & 3, lambda b: False)
+    B_im = pack(lambda b: 3 - b, lambda b: False)
+    ref = T.T @ U - U.T @ T
+    assert np.abs(A_re @ B_re.T - ref.real).max() < 1e-13
+    assert np.abs(A_im @ B_im.T - ref.imag).max() < 1e-13
