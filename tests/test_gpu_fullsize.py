@@ -5,9 +5,9 @@ against bars from the conditioning of Gamma_a + Gamma_b and Gamma_0 + Delta:
 the overlaps of these random states are as small as 1e-40), the energy of the
 GPU's (G, h), dGamma of sampled states and their updated Gamma.  Both
 arithmetics of the FP64 products are covered: the emulated products (the
-library's default and the bench's) with the panel widths the bench's
-autotuner picks on GB300 (Gauss-Jordan 48, Pfaffian 16) and with the autotuner
-itself, and the FP64 FMA products.  A 20-step trajectory compares the two
+library's default and the bench's) with the autotuner (it picks 16 / 16 on
+GB300) and with a wider Gauss-Jordan leaf fixed (48 / 16), and the FP64 FMA
+products.  A 20-step trajectory compares the two
 arithmetics with each other.  At the largest rank (M = 64) on a small chain
 the whole pair pass is compared."""
 import numpy as np
@@ -37,7 +37,7 @@ def large():
 
 
 VARIANTS = {
-    "emulated_bench_widths": (0, (48, 16)),
+    "emulated_gj48": (0, (48, 16)),
     "emulated_autotuned": (0, None),
     "fma_autotuned": (1, None),
 }
