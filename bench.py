@@ -160,37 +160,42 @@ class ClockSampler:
 # --------------------------------------------------------------------- CPU oracle sample
 
 def oracle_sample(w, n_pairs=4, n_states=1):
-    """Time the FP64 oracle on a bounded sample of one step of the workload:
-    n_pairs pair evaluations (overlap with phase, transition matrix, Wick
-    energy, both receivers' EOM terms) and n_states state updates, then scale
-    to the step's M(M-1)/2 pairs and M states.  Returns (seconds per step, sample)."""
+    """Time the FP64 oracle, as it stands, on a bounded sample of one step of
+    the workload: n_pairs pair evaluations (the oracle's pair_elements: overlap
+    with phase, transition matrix, Wick energy; and its eom_term for both
+    receivers of the pair) and n_states state evaluations (eom_term of the
+    state's own term, orthogonal step, purification), then scale to the step's
+    M(M-1)/2 pairs and M states.  Returns (seconds per step, sample)."""
     from oracle import sgs_oracle as orc
     p = w.model
     model = orc.anderson_model(p.n_bath, p.U, p.eps_d, p.V, p.t, p.mu, p.n_channels)
-    g, _ = inp.initial_state(p.n_modes, max(n_pairs + 1, 2), w.seed, w.parity)
+    m = max(n_pairs + 1, n_states + 1, 2)
+    g, _ = inp.initial_state(p.n_modes, m, w.seed, w.parity)
     gam = list(g)
+    # the amplitude problem's values only scale the terms: unit Gram matrix and amplitudes
+    G = np.eye(m, dtype=np.complex128)
+    h = np.zeros((m, m), dtype=np.complex128)
+    lam = np.ones(m, dtype=np.complex128)
     t0 = time.perf_counter()
-    pf0, _ = orc.pfaffian_log(gam[0])
     for k in range(n_pairs):
-        a, b = 1 + (k % (len(gam) - 1)), 1 + ((k + 1) % (len(gam) - 1))
+        a, b = 1 + (k % (m - 1)), 1 + ((k + 1) % (m - 1))
         if a == b:
             b = 0
-        orc.log_overlap_magnitude(gam[a], gam[b])
-        D = orc.transition_matrix(gam[a], gam[b])
-        orc.pfaffian_log(gam[0] + D)
-        orc.wick_energy_density(model, D)
-        for X in (D, D.conj()):          # both receivers of the pair
-            F = orc.fock_matrix(model, X)
-            _ = 2j * (X @ F - F @ X) + 2.0 * (X @ F @ X + F) - X
+        a, b = min(a, b), max(a, b)
+        G[a, b], h[b, a] = orc.pair_elements(model, gam, a, b)
+        orc.eom_term(model, gam, G, h, 0.0, lam, b, a)      # both receivers of the pair
+        orc.eom_term(model, gam, G, h, 0.0, lam, a, b)
     t_pairs = (time.perf_counter() - t0) / n_pairs
     t0 = time.perf_counter()
     for k in range(n_states):
+        orc.eom_term(model, gam, G, h, 0.0, lam, k, k)
+        # a tangent direction of the same size as a step's: the commutator of two states
         dG = 0.01 * (gam[k] @ gam[k + 1] - gam[k + 1] @ gam[k])
         orc.purify(orc.orthogonal_step(gam[k], dG, w.dtau))
     t_states = (time.perf_counter() - t0) / n_states
     M = w.rank
     t_step = t_pairs * M * (M - 1) / 2 + t_states * M
-    sample = (f"{n_pairs} pair evaluations + {n_states} state update(s) of the {w.name} step, "
+    sample = (f"{n_pairs} pair evaluations + {n_states} state evaluation(s) of the {w.name} step, "
               f"scaled to {M * (M - 1) // 2} pairs + {M} states")
     return t_step, sample
 
@@ -460,7 +465,7 @@ def run_sgs(args):
                                timeout=600)
             t1 = float(r.stdout.strip().splitlines()[-1])
             line["cpu_baseline_1_thread"] = {"value": 1.0 / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                             "sample": "2 pair evaluations + 1 state update, scaled to the step"}
+                                             "sample": "2 pair evaluations + 1 state evaluation, scaled to the step"}
         except (subprocess.SubprocessError, ValueError, IndexError):
             line["cpu_baseline_1_thread"] = None
     if rank == 0:
