@@ -237,6 +237,30 @@ def run_reference(args):
 FP64_PATHS = {"emulated": 0, "fma": 1}
 
 
+def traffic_per_launch(tfile, precision, fp64_path, n, rank, widths, launches, steps, root=ROOT):
+    """DRAM bytes per FP64 product call from a committed ncu capture, or None.
+    The counters hold for the same shape, panel widths and FP64 path only, for
+    the same launch sequence (a changed step shows as another launch count),
+    and only while the sources of the counted kernels are the ones captured."""
+    if not os.path.exists(tfile):
+        return None
+    try:
+        with open(tfile) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    key = f"oz_all_{precision}" if fp64_path == "emulated" else f"gemm_f64_all_{precision}"
+    t = rec.get(key)
+    if not t or not t.get("sources"):
+        return None
+    fresh = all(_sha256(os.path.join(root, f)) == hsh for f, hsh in t["sources"].items())
+    if (fresh and t.get("n") == n and t.get("rank") == rank and t.get("fp64_path") == fp64_path
+            and t.get("panel_widths_gj_pf") == list(widths)
+            and t.get("launches_per_step", -1) * steps == launches):
+        return t.get("bytes_per_launch")
+    return None
+
+
 def path_kwargs(args):
     """Solver options for the FP64 products: the path and, when emulated, the slice scratch."""
     gb = args.emulation_scratch_gb or (0.125 if args.workload in ("batched", "serving") else 6.0)
@@ -380,19 +404,8 @@ def run_sgs(args):
     roof = None
     if g_ms > 0:
         achieved = g_fl / (g_ms * 1e-3) / 1e12
-        traffic = None
-        tfile = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tfile):
-            key = f"oz_all_{args.precision}" if args.fp64_path == "emulated" else f"gemm_f64_all_{args.precision}"
-            t = json.load(open(tfile)).get(key, {})
-            # counters hold for the same shape, panel widths and FP64 path only
-            # and for the same launch sequence (a changed step shows as another launch count)
-            # and only while the sources of the counted kernels are the ones captured
-            fresh = all(_sha256(os.path.join(ROOT, f)) == hsh for f, hsh in t.get("sources", {}).items())
-            if (t.get("n") == n and t.get("rank") == w.rank and t.get("fp64_path") == args.fp64_path
-                    and t.get("panel_widths_gj_pf") == list(solver.tuning(0)[:2])
-                    and t.get("launches_per_step") * args.steps == int(g_n) and fresh):
-                traffic = t.get("bytes_per_launch")
+        traffic = traffic_per_launch(os.path.join(ROOT, "profiles", "traffic.json"), args.precision,
+                                     args.fp64_path, n, w.rank, list(solver.tuning(0)[:2]), int(g_n), args.steps)
         if args.fp64_path == "emulated":
             kern = ("oz_gemm_kernel with its slicing kernels (FP64 products emulated on the bf16 tensor cores; "
                     "all FP64 products: Gauss-Jordan and Pfaffian updates, pair and state products)")

@@ -1,6 +1,7 @@
-"""Host logic of bench.py's reference arm (CPU): the oracle sample calls the
-oracle's own pair and state functions and scales them to the step, and the
-reference line carries the keys of the bench contract."""
+"""Host logic of bench.py (CPU): the reference arm's oracle sample calls the
+oracle's own pair and state functions and scales them to the step, the
+reference line carries the keys of the bench contract, and the roofline's
+DRAM traffic is taken from a capture only while it describes the timed step."""
 import json
 import os
 import subprocess
@@ -100,3 +101,29 @@ def test_reference_arm_other_ranks_exit_quietly():
                        timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def _traffic_file(tmp_path, sources_sha):
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source")
+    rec = {"oz_all_fp64": {"n": 512, "rank": 32, "panel_widths_gj_pf": [16, 16], "fp64_path": "emulated",
+                           "launches_per_step": 92, "bytes_per_launch": 123.0,
+                           "sources": {"k.cu": sources_sha(src)}}}
+    f = tmp_path / "traffic.json"
+    f.write_text(json.dumps(rec))
+    return str(f), src
+
+
+def test_traffic_reported_only_for_the_captured_step(tmp_path):
+    """The bench's `traffic` comes from the capture only for the captured shape, panel widths, FP64
+    path and launch count, and only while the counted kernels' sources are unchanged."""
+    f, src = _traffic_file(tmp_path, lambda p: bench._sha256(str(p)))
+    root = str(tmp_path)
+    base = dict(precision="fp64", fp64_path="emulated", n=512, rank=32, widths=[16, 16], launches=92 * 5, steps=5)
+    assert bench.traffic_per_launch(f, root=root, **base) == 123.0
+    for k, v in (("n", 256), ("rank", 12), ("widths", [12, 16]), ("fp64_path", "fma"), ("launches", 92 * 5 + 1),
+                 ("precision", "tf32")):
+        assert bench.traffic_per_launch(f, root=root, **dict(base, **{k: v})) is None, k
+    src.write_text("kernel source, changed")
+    assert bench.traffic_per_launch(f, root=root, **base) is None
+    assert bench.traffic_per_launch(str(tmp_path / "absent.json"), root=root, **base) is None
