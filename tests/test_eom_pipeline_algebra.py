@@ -35,14 +35,18 @@ def own_term(model, Gm, co, imp):
     return 2.0 * (co[0] * (gf - fg) + co[2] * (GFG + Fr) + co[4] * Gm)
 
 
-def composed_eom(model, gammas, cmode, plant_no_conj=False):
+def composed_eom(model, gammas, cmode, plant_no_conj=False, amplitudes=None):
     """plant_no_conj: a planted mistake, receiver a of each pair takes Delta^{a,b} itself where its
-    term needs the conjugate Delta^{b,a}."""
+    term needs the conjugate Delta^{b,a}.  amplitudes: (G, h, E, lambda) to use (default: the
+    oracle's)."""
     M = len(gammas)
     n = model.n
     imp = interacting_modes(model)
-    G, h = orc.gram_and_hamiltonian(model, gammas)
-    E, lam = orc.solve_amplitudes(G, h)
+    if amplitudes is None:
+        G, h = orc.gram_and_hamiltonian(model, gammas)
+        E, lam = orc.solve_amplitudes(G, h)
+    else:
+        G, h, E, lam = amplitudes
     co3 = coefficients(G, h, E, lam, cmode)
     coef = np.zeros((M, M, 6))
     coef[..., 0::2] = co3.real
