@@ -295,3 +295,58 @@ def test_combination_outside_the_normal_range():
         got = _to_double(hi, lo, e_lo, neg)[0]
         ref = sign * float(Fraction(q) * Fraction(2) ** (P - 52 + e_lo))
         assert got == ref, (hi, lo, e_lo, neg, got, ref)
+
+
+def _to_double_normal(hi, lo, e, neg):
+    """The combination's form for results known to be normal numbers: the same justification
+    and rounding as _to_double, and the biased exponent added without the range-end selects."""
+    import struct
+    m64 = (1 << 64) - 1
+    _, q, P = _to_double(hi, lo, 0, False)          # q and P do not depend on e or the sign
+    V = hi * 2 ** 28 + lo
+    if V == 0:
+        return 0.0
+    sbit = int((V < 0) != neg) << 63
+    bits = (sbit + ((P + e + 1022) << 52) + q) & m64
+    return struct.unpack('<d', struct.pack('<Q', bits))[0]
+
+
+def _combination_input_bounds(K=512):
+    """Largest |hi| and |lo| the combination can see in one K chunk: group G sums over k the
+    products of digits i + j = G, |t_0| <= 128 and |t_i| <= 64 (i >= 1); hi = v0 2^21 + v1 2^14 +
+    v2 2^7 + v3 and lo likewise from v4 .. v7 (an fp32 group sum of G = 6, 7 may round, by less
+    than one unit of its last place, which the margin below covers)."""
+    tmax = [128] + [64] * 7
+    v = [K * sum(tmax[i] * tmax[G - i] for i in range(G + 1) if G - i < 8) for G in range(8)]
+    hi = v[0] * 2 ** 21 + v[1] * 2 ** 14 + v[2] * 2 ** 7 + v[3]
+    lo = v[4] * 2 ** 21 + v[5] * 2 ** 14 + v[6] * 2 ** 7 + v[7]
+    return hi, lo
+
+
+def test_normal_range_form_gives_the_same_bits():
+    """Where the tile's exponent fields keep P + e + 1023 in 1 .. 2046 for every leading-bit
+    position P in 0 .. 74, the select-free form returns the general form's bits, a carry of the
+    rounding into the exponent included (up to infinity at the top of the range).  The premise
+    P <= 74 holds for every value a K = 512 chunk can produce: |V| = |hi 2^28 + lo| stays below
+    2^73 by the digit bounds (the conversion's general input range, |H| < 2^47, would not
+    ensure it by itself)."""
+    import math
+    import random
+    rnd = random.Random(11)
+    hmax, lmax = _combination_input_bounds()
+    assert hmax * 2 ** 28 + lmax < 2 ** 73
+    for _ in range(20000):
+        hi, lo = rnd.randint(-hmax, hmax), rnd.randint(-lmax, lmax)
+        if rnd.random() < 0.3:                       # all-ones significands: the rounding carries
+            hi, lo = rnd.choice([1, -1]) * (2 ** rnd.randint(1, 44) - 1), 2 ** 28 - 1
+        neg = rnd.random() < 0.5
+        # the tile condition: e + 1023 >= 1 and e + 1023 + 74 <= 2046
+        e = rnd.randint(1 - 1023, 2046 - 1023 - 74)
+        a = _to_double(hi, lo, e, neg)[0]
+        b = _to_double_normal(hi, lo, e, neg)
+        assert (a == b and math.copysign(1.0, a) == math.copysign(1.0, b)) or (math.isnan(a) and math.isnan(b)), \
+            (hi, lo, e, neg, a, b)
+    # at the ends of the condition the two forms still agree
+    for e in (1 - 1023, 2046 - 1023 - 74):
+        for hi, lo in ((1, 0), (0, 1), (hmax, lmax), (-hmax, -lmax), (2 ** 44 - 1, 2 ** 28 - 1)):
+            assert _to_double(hi, lo, e, False)[0] == _to_double_normal(hi, lo, e, False)
