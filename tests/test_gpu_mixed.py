@@ -2,10 +2,11 @@
 against the FP64 oracle (GPU).  The factorisations, the phase Pfaffian, the
 Wick energies and the re-purification stay FP64, so the energy of a given
 set of states is FP64-exact; only dGamma/ds (hence the trajectory) carries
-the products' rounding.  Stated tolerances (measured margins in the design doc):
-dGamma relative to its largest entry: TF32 1e-2, BF16 6e-2, 3xTF32 1e-5;
-energy after 20 steps of the small workload, relative: TF32 2e-4, BF16
-2e-3, 3xTF32 1e-7."""
+the products' rounding.  Stated tolerances, with the values measured on a
+GB300 in brackets: dGamma relative to its largest entry: TF32 1e-2 (2.9e-4),
+BF16 6e-2 (2.3e-3), 3xTF32 1e-5 (1.9e-6); energy after 20 steps of the small
+workload, relative: TF32 2e-4 (2.9e-5), BF16 2e-3 (5.7e-5), 3xTF32 1e-7
+(4.5e-8)."""
 import numpy as np
 import pytest
 
