@@ -19,7 +19,7 @@ An all-reduce moves the bytes of a reduce-scatter plus an all-gather, so
 summing dGamma/ds everywhere costs the exchange of reducing it to owners and
 gathering the updated states; the price is that every rank runs the per-state
 update.  The library does stages 1-3 (sgs_shard_pairs / eom / update); this
-module is the host driver that makes the two sums with torch.distributed.
+module is the host-side loop that makes the two sums with torch.distributed.
 Any backend object with the three stage methods can be driven, which lets the
 partition and the reductions be tested on CPU ranks (gloo).
 """
