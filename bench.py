@@ -219,7 +219,7 @@ def run_reference(args):
     times = []
     sample = ""
     for _ in range(args.steps):
-        t, sample = oracle_sample(w, n_pairs=2, n_states=1)
+        t, sample = oracle_sample(w, n_pairs=4, n_states=1)
         times.append(t)
     t_step = float(np.mean(times))
     value = 1.0 / t_step
@@ -466,19 +466,19 @@ def run_sgs(args):
                         "after the timed steps"}}
         ms_solver.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_step, sample = oracle_sample(w, n_pairs=6, n_states=2)
+        t_step, sample = oracle_sample(w, n_pairs=24, n_states=4)
         line["cpu_baseline"] = {"value": 1.0 / t_step, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                                 "sample": sample}
         # the same sample with one BLAS thread, in a child process (thread counts are fixed at import)
         env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
         code = ("import bench, sgs_inputs; w = bench.workload(%r, %d); "
-                "t, s = bench.oracle_sample(w, n_pairs=2, n_states=1); print(t)" % (args.workload, args.rank))
+                "t, s = bench.oracle_sample(w, n_pairs=8, n_states=2); print(t)" % (args.workload, args.rank))
         try:
             r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
                                timeout=600)
             t1 = float(r.stdout.strip().splitlines()[-1])
             line["cpu_baseline_1_thread"] = {"value": 1.0 / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                             "sample": "2 pair evaluations + 1 state evaluation, scaled to the step"}
+                                             "sample": "8 pair evaluations + 2 state evaluations, scaled to the step"}
         except (subprocess.SubprocessError, ValueError, IndexError):
             line["cpu_baseline_1_thread"] = None
     if rank == 0:
