@@ -1,8 +1,9 @@
 """Host logic of the pair-sharded step (CPU): the partition of the pairs and the
-two sums over ranks, driven by paper_2105_01088_gb300.sharded on two gloo
-ranks, with a stand-in backend that evaluates each stage's share with the
-oracle.  Summed over the ranks, the shares must give the single-rank oracle
-step: energies to 1e-12 relative and the states to 1e-10."""
+two sums over ranks, driven by paper_2105_01088_gb300.sharded on two and three
+gloo ranks (ranks without pairs included), with a stand-in backend that
+evaluates each stage's share with the oracle.  Summed over the ranks, the
+shares must give the single-rank oracle step: energies to 1e-12 relative and
+the states to 1e-10."""
 import os
 import socket
 
@@ -57,20 +58,20 @@ class OracleShard:
         self.g = [orc.purify(orc.orthogonal_step(g, d, self.dtau)) for g, d in zip(self.g, dG)]
 
 
-def _case():
+def _case(M=5):
     p = inp.AndersonParams(n_bath=4, U=2.0, eps_d=-1.0, V=0.5)           # n = 20
     rng = np.random.default_rng(31)
-    g = inp.clustered_pure_gammas(p.n_modes, 5, rng, 1, spread=1.0)
+    g = inp.clustered_pure_gammas(p.n_modes, M, rng, 1, spread=1.0)
     return p, g
 
 
-def _worker(rank, world, port, out_dir, n_steps):
+def _worker(rank, world, port, out_dir, n_steps, M=5):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        p, g = _case()
+        p, g = _case(M)
         model = orc.anderson_model(p.n_bath, p.U, p.eps_d, p.V)
         backend = OracleShard(model, g, rank, world, 0.05)
         E = ShardedStep(backend).step(n_steps)
@@ -95,18 +96,22 @@ def test_partition_covers_every_pair_once():
             assert max(sizes) - min(sizes) <= 1             # balanced
 
 
-@pytest.mark.parametrize("world", [2])
-def test_two_gloo_ranks_equal_the_single_rank_step(tmp_path, world):
+@pytest.mark.parametrize("world,M", [(2, 5), (3, 5), (3, 2)])
+def test_gloo_ranks_equal_the_single_rank_step(tmp_path, world, M):
+    """Two ranks; three ranks with shares of 4, 3 and 3 pairs; and three ranks for two states,
+    where ranks 1 and 2 hold no pair and rank 2 no state of its own (its shares are zero)."""
     import torch.multiprocessing as mp
     n_steps = 2
-    mp.spawn(_worker, args=(world, _free_port(), str(tmp_path), n_steps), nprocs=world, join=True)
-    p, g = _case()
+    sizes = [len(local_pairs(M, r, world)) for r in range(world)]
+    assert sizes == {(2, 5): [5, 5], (3, 5): [4, 3, 3], (3, 2): [1, 0, 0]}[(world, M)]
+    mp.spawn(_worker, args=(world, _free_port(), str(tmp_path), n_steps, M), nprocs=world, join=True)
+    p, g = _case(M)
     model = orc.anderson_model(p.n_bath, p.U, p.eps_d, p.V)
     Eo, _, go = orc.run(model, list(g), 0.05, n_steps)
-    for r in range(world):
-        res = np.load(tmp_path / f"rank{r}.npz")
-        assert np.all(np.abs(res["E"] - Eo) <= 1e-12 * np.abs(Eo))
-        assert np.abs(res["g"] - np.stack(go)).max() <= 1e-10
+    res = [np.load(tmp_path / f"rank{r}.npz") for r in range(world)]
+    for r in res:
+        assert np.all(np.abs(r["E"] - Eo) <= 1e-12 * np.abs(Eo))
+        assert np.abs(r["g"] - np.stack(go)).max() <= 1e-10
     # and the ranks agree with each other exactly (the same sums, the same update)
-    r0, r1 = np.load(tmp_path / "rank0.npz"), np.load(tmp_path / "rank1.npz")
-    assert np.array_equal(r0["g"], r1["g"]) and np.array_equal(r0["E"], r1["E"])
+    for r in res[1:]:
+        assert np.array_equal(res[0]["g"], r["g"]) and np.array_equal(res[0]["E"], r["E"])
