@@ -156,3 +156,67 @@ def test_two_slots_failing_in_one_step():
         assert len(r.energies) == r.steps
         k = np.arange(1, r.steps + 1)
         assert np.allclose(r.energies, (1.0 + r.rid) * (1.0 - 0.5 ** k))
+
+
+class FailNoEnergiesSolver(FakeSolver):
+    """Slot 1 fails in its third step, and the error carries no energies for the
+    others (as when the failure is reported before the energies were read back)."""
+
+    def __init__(self, clock, status=4):
+        super().__init__(clock, capacity=4)
+        self.status = status
+
+    def step(self, n):
+        if len(self.slots) > 1 and self.live[1] and self.slots[1][1] == 2:
+            super().step(n)                       # the step ran for every slot
+            e = RuntimeError("failed")
+            e.status = self.status
+            e.failed = [1]
+            raise e
+        return super().step(n)
+
+
+def test_failure_without_energies_counts_the_step_for_the_others():
+    clk = FakeClock()
+    s = FailNoEnergiesSolver(clk)
+    loop = ServingLoop(s, tol=1e-6, max_steps=100, clock=clk, sleep=clk.sleep, keep_energies=True)
+    res = loop.run(_reqs([0.0, 0.0, 0.0]))
+    assert loop.failures == [1] and res[1].failed and res[1].steps == 2
+    for r in (res[0], res[2]):
+        # one step without an energy: the convergence test restarts from the next energy
+        assert r.converged and not r.failed
+        assert len(r.energies) == r.steps - 1
+        k = np.concatenate([np.arange(1, 3), np.arange(4, r.steps + 1)])
+        assert np.allclose(r.energies, (1.0 + r.rid) * (1.0 - 0.5 ** k))
+
+
+def test_a_failure_that_is_not_a_solve_failure_propagates():
+    clk = FakeClock()
+    s = FailNoEnergiesSolver(clk, status=6)           # a CUDA runtime error: not one slot's solve
+    loop = ServingLoop(s, tol=1e-6, max_steps=100, clock=clk, sleep=clk.sleep)
+    try:
+        loop.run(_reqs([0.0, 0.0]))
+    except RuntimeError as e:
+        assert e.status == 6
+    else:
+        raise AssertionError("the error was swallowed")
+
+
+def test_sequential_baseline_reports_a_failed_solve_and_goes_on():
+    clk = FakeClock()
+
+    class OneShot(FakeSolver):
+        calls = 0
+
+        def step(self, n):
+            OneShot.calls += 1
+            if OneShot.calls == 3:
+                e = RuntimeError("SGS_ENOTCONV: amplitudes")
+                e.status = 4
+                raise e
+            return super().step(n)
+
+    res = run_sequential(lambda: OneShot(clk), _reqs([0.0, 0.0]), tol=1e-6, max_steps=100, clock=clk,
+                         sleep=clk.sleep)
+    assert res[0].failed.startswith("SGS_ENOTCONV") and np.isnan(res[0].energy) and res[0].steps == 2
+    assert res[1].converged and not res[1].failed
