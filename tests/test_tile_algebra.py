@@ -98,3 +98,30 @@ def test_masked_store_keeps_what_was_not_computed():
     got = assemble(A, n, rng, mask=mask, init=before)
     want = np.where(mask, A, before)                # both zero on the diagonal
     assert np.array_equal(got, want)
+
+
+def decode_pair_of_pairs(q):
+    """The Renyi kernels' decode of a block index q = v (v + 1) / 2 + u, u <= v: a double
+    square root, then integer corrections in both directions."""
+    import math
+    v = int((math.sqrt(8.0 * float(q) + 1.0) - 1.0) * 0.5)
+    while (v + 1) * (v + 2) // 2 <= q:
+        v += 1
+    while v * (v + 1) // 2 > q:
+        v -= 1
+    return q - v * (v + 1) // 2, v
+
+
+def test_pair_of_pairs_decode_is_exact():
+    """Every q of a launch maps to one (u, v) with u <= v, in order, including indices far past
+    any rank the library admits (where the square root's rounding needs the corrections)."""
+    q = 0
+    for v in range(300):
+        for u in range(v + 1):
+            assert decode_pair_of_pairs(q) == (u, v)
+            q += 1
+    rng = np.random.default_rng(2)
+    for v in list(rng.integers(1, 2 ** 26, 2000)) + [2 ** 26 - 1, 94906265, 94906266]:
+        v = int(v)
+        for u in (0, v // 2, v):
+            assert decode_pair_of_pairs(v * (v + 1) // 2 + u) == (u, v)
