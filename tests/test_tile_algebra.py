@@ -6,7 +6,8 @@ entries strictly below the diagonal and stores them with their mirror
 diagonal tile the upper part as the negated transpose and a zero diagonal.
 An optional mask keeps entries the block did not compute.  The transcription
 must rebuild any antisymmetric matrix exactly, ragged edges included, from
-tiles whose upper and diagonal entries hold garbage."""
+tiles whose upper and diagonal entries hold garbage.  Also the Renyi kernels'
+decode of a block index into a pair of pairs (u <= v)."""
 import numpy as np
 import pytest
 
