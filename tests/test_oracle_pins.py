@@ -97,6 +97,35 @@ def test_pfaffian_closed_forms():
         assert abs(orc.pfaffian(Bm @ X @ Bm.T) - np.linalg.det(Bm) * p) < 1e-9 * abs(np.linalg.det(Bm) * p)
 
 
+def _pf_by_matchings(A):
+    """The definition: the sum over perfect matchings of {0..n-1}, each the product of
+    A[i, j] over its pairs (i < j) with the sign of the permutation (i1 j1 i2 j2 ...)."""
+    n = A.shape[0]
+
+    def rec(rest):
+        if not rest:
+            return 1.0
+        i, tot = rest[0], 0.0
+        for pos in range(1, len(rest)):
+            j = rest[pos]
+            # moving j next to i crosses pos - 1 indices
+            tot += (-1) ** (pos - 1) * A[i, j] * rec(rest[1:pos] + rest[pos + 1:])
+        return tot
+
+    return rec(list(range(n)))
+
+
+def test_pfaffian_equals_the_sum_over_perfect_matchings():
+    rng = _rng(4)
+    for n in (2, 4, 6, 8):
+        X = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        X = X - X.T
+        ref = _pf_by_matchings(X)
+        assert abs(orc.pfaffian(X) - ref) < 1e-12 * max(1.0, abs(ref))
+        phase, logmag = orc.pfaffian_log(X)
+        assert abs(phase * np.exp(logmag) - ref) < 1e-12 * max(1.0, abs(ref))
+
+
 # ---------------------------------------------------------------- pair quantities vs Fock
 
 def _states(N, M, seed, parity=1):
