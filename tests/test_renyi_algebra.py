@@ -83,6 +83,9 @@ def test_transition_form_equals_the_papers_form_term_by_term(NA):
                            / (G[a, b] * G[c, d]))
                     got = kernel_term(gammas, lam, G, a, b, c, d, NA)
                     assert abs(got - ref) < 1e-11 * max(1e-3, abs(ref)), (a, b, c, d)
+                    # the symmetry that halves the kernel's count: T^{cd}_{ab} = T^{ab}_{cd}, no conjugate
+                    swap = kernel_term(gammas, lam, G, c, d, a, b, NA)
+                    assert abs(swap - got) < 1e-12 * max(1e-3, abs(got))
                     total += got
     assert abs(-math.log(total.real) - orc.renyi2(gammas, lam, G, NA)) < 1e-10
 
