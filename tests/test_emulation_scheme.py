@@ -66,6 +66,21 @@ def test_digits_reconstruct_the_scaled_value():
             assert (f.view(np.uint32) & 0xFFFF) == 0
 
 
+def test_rows_of_subnormals_keep_their_values():
+    """A subnormal entry's exponent field counts as 1 (the scale of the smallest normal), so a
+    row whose largest entry is subnormal is sliced exactly, not dropped as a zero row."""
+    tiny = 2.0 ** -1074
+    for row in ([tiny, -3 * tiny, 1e-310, -2.2e-308], [1e-310, 0.0, -0.0], [2.0 ** -1022, 1e-315]):
+        E = max(expo_field(v) for v in row)
+        assert E == 1
+        scale = Fraction(2) ** (E - 1022)
+        for v in row:
+            t = digits(v, E)
+            rec = scale * sum(Fraction(d) * Fraction(2) ** (-BETA * (i + 1)) for i, d in enumerate(t))
+            assert rec == Fraction(float(v))                 # exact: subnormals are multiples of 2^-1074
+            assert digits_offset_form(v, E) == t
+
+
 def digits_offset_form(v, E):
     """The kernels' form of the same digits: Y = X + sum_{j<7} 64 2^(7 j); the low seven
     digits are the base-128 digits of Y less 64, the top digit is Y >> 49 (arithmetic),
